@@ -1,0 +1,193 @@
+/*
+ * galnb.h -- C ABI of the GB300 N-body/SPH interaction library.
+ *
+ * The calls follow the statement of the problem in Hirashima et al.,
+ * "The First Star-by-star N-body/Hydrodynamics Simulation of Our Galaxy
+ * Coupling with a Surrogate Model" (SC'25, arXiv 2510.23330):
+ *   - particles carry position, velocity, mass and a per-particle softening
+ *     (Sec. 3.5, Eq. 1 and the paragraph after it), an ID used to replace
+ *     particles (Sec. 3.2, step 4) and, for gas, an internal energy;
+ *   - positions are stored in FP64 and interactions are evaluated in FP32 on
+ *     offsets relative to the receiving group (Sec. 4.3);
+ *   - gravity is the softened pair force of Eq. 1 summed directly or by a
+ *     Barnes-Hut tree with groups sharing one interaction list (Sec. 3.4,
+ *     Sec. 5.2.2, 5.2.4);
+ *   - SPH needs a kernel size, a density/pressure pass and a hydro-force pass
+ *     (Sec. 5.2.5, Table 3, Table 4);
+ *   - particles advance with the second-order leapfrog at a shared timestep
+ *     (Sec. 3.2).
+ *
+ * Conventions shared by every call:
+ *   - Return value: GNB_OK (0) or a negative GNB_E* code.  No call aborts or
+ *     throws; gnb_last_error() gives a one-line reason for the last failure.
+ *   - Ownership: the library copies every input into its own device arrays
+ *     and never keeps a caller pointer.  Outputs are copied into caller
+ *     buffers, in the caller's original particle order.
+ *   - on_device: 0 means the pointers are host memory; 1 means they are
+ *     device memory of the current CUDA device, readable on cfg.cuda_stream.
+ *   - Streams: all device work of a context is issued on cfg.cuda_stream
+ *     (NULL means the legacy default stream).  Every call returns only when
+ *     its work has finished on that stream.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef GALNB_H
+#define GALNB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GNB_OK 0
+#define GNB_EINVAL (-1)    /* bad argument (null pointer, bad size, NaN position, ...) */
+#define GNB_ENOMEM (-2)    /* device allocation failed */
+#define GNB_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define GNB_ESTATE (-4)    /* call made in the wrong order (e.g. force before particles) */
+#define GNB_ECAPACITY (-5) /* an internal list stayed over capacity after retries */
+#define GNB_ETIMEOUT (-6)  /* a bounded device-side wait ran out */
+#define GNB_EMISMATCH (-7) /* replacement IDs or count differ from the particles held */
+
+/* Particle types (Sec. 1: stars and dark matter are collisionless, gas is SPH). */
+#define GNB_STAR 0
+#define GNB_GAS 1
+
+/* Gravity modes of gnb_compute_gravity / gnb_step_kdk. */
+#define GNB_GRAV_DIRECT 0  /* O(N^2) sum of Eq. 1 over all particles */
+#define GNB_GRAV_TREE 1    /* Barnes-Hut group walk, particle-particle + particle-cell */
+
+typedef struct gnb_ctx gnb_ctx;
+
+/* Run parameters.  gnb_config_default() fills the defaults in brackets. */
+typedef struct gnb_config {
+    double G;          /* gravitational constant [1] */
+    double theta;      /* opening angle of the Barnes-Hut test [0.5] */
+    double gamma;      /* adiabatic index of the ideal-gas EOS [5/3] */
+    double alpha_visc; /* artificial-viscosity coefficient [1] */
+    int n_leaf;        /* a cell with more particles than this is split [16] */
+    int n_group;       /* particles sharing one interaction list, n_g [64] */
+    int n_ngb;         /* SPH neighbours, self included; only 64 is supported [64] */
+    int multipole;     /* 0 = monopole, 1 = monopole + quadrupole [1] */
+    double nfw_ms;     /* static NFW halo mass scale 4 pi rho_s r_s^3; 0 disables [0] */
+    double nfw_rs;     /* NFW scale radius [8] */
+    void *cuda_stream; /* cudaStream_t for all work; NULL = default stream [NULL] */
+} gnb_config;
+
+/* Fields readable with gnb_get.  Element type and count in brackets; n is
+ * the particle count, "gas" rows are ordered like the gas particles in the
+ * caller's original order. */
+enum gnb_field {
+    GNB_F_X = 0, GNB_F_Y, GNB_F_Z,  /* position [double, n] */
+    GNB_F_VX, GNB_F_VY, GNB_F_VZ,   /* velocity [float, n] */
+    GNB_F_AX, GNB_F_AY, GNB_F_AZ,   /* total acceleration [float, n] */
+    GNB_F_POT,                      /* self-gravity potential phi [float, n] */
+    GNB_F_U,                        /* internal energy, 0 for stars [float, n] */
+    GNB_F_DUDT,                     /* du/dt, 0 for stars [float, n] */
+    GNB_F_RHO,                      /* SPH density, 0 for stars [float, n] */
+    GNB_F_PRES,                     /* pressure, 0 for stars [float, n] */
+    GNB_F_CS,                       /* sound speed, 0 for stars [float, n] */
+    GNB_F_H2,                       /* squared kernel support h^2, 0 for stars [double, n] */
+    GNB_F_KEY,                      /* Morton key of the last tree build [uint64, n] */
+    GNB_F_ORDER,                    /* original index of the particle at each sorted slot [int64, n] */
+    GNB_F_NBR,                      /* neighbour lists: n_ngb original indices per gas particle,
+                                       ascending [int64, n_gas * n_ngb] */
+    GNB_F_NODES,                    /* tree nodes, breadth-first: 4 int64 per node
+                                       (level, prefix, first, count) [int64, 4 * nodes] */
+    GNB_F_GROUPS,                   /* groups: node index of each group, ascending first
+                                       particle [int64, groups] */
+    GNB_F_ID,                       /* particle IDs [int64, n] */
+    GNB_F_AGRAV_X, GNB_F_AGRAV_Y, GNB_F_AGRAV_Z, /* self-gravity part of a [float, n] */
+    GNB_F_COUNT_
+};
+
+/* Counters readable with gnb_stats (int64 out[GNB_S_COUNT_]). */
+enum gnb_stat {
+    GNB_S_N = 0,        /* particles */
+    GNB_S_NGAS,         /* gas particles */
+    GNB_S_NODES,        /* gravity tree nodes */
+    GNB_S_GROUPS,       /* gravity groups */
+    GNB_S_NPP,          /* particle-particle interactions of the last gravity pass */
+    GNB_S_NPC,          /* particle-cell interactions of the last gravity pass */
+    GNB_S_GAS_NODES,    /* hydro tree nodes */
+    GNB_S_KNN_PASSES,   /* kernel-size search passes of the last density call */
+    GNB_S_NSYM,         /* entries of the symmetric SPH force lists */
+    GNB_S_MAXLEVEL,     /* deepest tree level */
+    GNB_S_COUNT_
+};
+
+/* Fill cfg with the defaults listed in gnb_config. */
+void gnb_config_default(gnb_config *cfg);
+
+/* Create a context on the current CUDA device.  *out is set on success.
+ * Errors: GNB_EINVAL (null or invalid cfg), GNB_ECUDA. */
+int gnb_create(gnb_ctx **out, const gnb_config *cfg);
+
+/* Free a context and all its device memory (NULL is ignored). */
+void gnb_destroy(gnb_ctx *ctx);
+
+/* Load n particles (Sec. 3.5: position, mass, softening per particle;
+ * Sec. 3.2: IDs).  Arrays are SoA of length n; u is read for gas only.
+ * Positions are FP64 (Sec. 4.3), velocities and the other fields FP32.
+ * Clears all derived state.  Errors: GNB_EINVAL (n < 1, null pointer,
+ * non-finite position, type not in {0,1}, n_ngb > number of gas particles
+ * when gas exists), GNB_ENOMEM, GNB_ECUDA. */
+int gnb_set_particles(gnb_ctx *ctx, int64_t n, const int64_t *id, const uint8_t *type,
+                      const double *x, const double *y, const double *z,
+                      const float *vx, const float *vy, const float *vz,
+                      const float *m, const float *eps, const float *u, int on_device);
+
+/* Sort particles along the Morton curve and build the octree, its cell
+ * moments and the groups (Sec. 3.4, 5.2.2).  Errors: GNB_ESTATE (no
+ * particles), GNB_ECUDA. */
+int gnb_build_tree(gnb_ctx *ctx);
+
+/* Self-gravity (Eq. 1) of every particle, plus the static NFW halo when
+ * enabled; mode is GNB_GRAV_DIRECT or GNB_GRAV_TREE.  Builds the tree first
+ * if needed.  Writes acceleration and potential.  Errors: GNB_EINVAL (mode),
+ * GNB_ESTATE, GNB_ECUDA. */
+int gnb_compute_gravity(gnb_ctx *ctx, int mode);
+
+/* SPH kernel size (exact n_ngb nearest gas neighbours, Sec. 5.2.5), density
+ * and pressure (Table 3 "density and pressure").  Builds the tree first if
+ * needed.  Errors: GNB_ESTATE, GNB_ECAPACITY, GNB_ECUDA. */
+int gnb_compute_sph_density(gnb_ctx *ctx);
+
+/* SPH pressure force, artificial viscosity and du/dt over the symmetric
+ * neighbour sets (Table 3 "hydro force").  Adds the hydro acceleration to
+ * the total acceleration.  Requires gnb_compute_sph_density since the last
+ * change of positions.  Errors: GNB_ESTATE, GNB_ECUDA. */
+int gnb_compute_sph_force(gnb_ctx *ctx);
+
+/* Total force evaluation: tree build, gravity (mode), NFW, SPH density and
+ * force.  Errors: as the calls above. */
+int gnb_compute_forces(gnb_ctx *ctx, int gravity_mode);
+
+/* nsteps kick-drift-kick leapfrog steps with shared timestep dt (Sec. 3.2):
+ * half kick, drift (FP64 positions), full force evaluation with predicted
+ * gas velocity and energy, half kick.  Forces at the start are computed
+ * first if they are not current.  Errors: GNB_EINVAL (dt not finite,
+ * nsteps < 0, mode), GNB_ESTATE, GNB_ECAPACITY, GNB_ECUDA. */
+int gnb_step_kdk(gnb_ctx *ctx, double dt, int nsteps, int gravity_mode);
+
+/* Copy one field into dst, which holds cap elements of the field's type.
+ * Errors: GNB_EINVAL (field, cap too small, null dst), GNB_ESTATE (field
+ * not computed yet), GNB_ECUDA. */
+int gnb_get(gnb_ctx *ctx, int field, void *dst, int64_t cap, int on_device);
+
+/* FP64 totals: out = {E_kin, E_pot (1/2 sum m phi), E_ext (sum m Phi_nfw),
+ * E_th (sum m u over gas), P_x, P_y, P_z, L_x, L_y, L_z}.  Requires a force
+ * evaluation at the current positions.  Errors: GNB_ESTATE, GNB_ECUDA. */
+int gnb_diagnostics(gnb_ctx *ctx, double out[10]);
+
+/* Counters of the last passes (enum gnb_stat).  Errors: GNB_EINVAL. */
+int gnb_stats(gnb_ctx *ctx, int64_t out[GNB_S_COUNT_]);
+
+/* One-line description of the last error of ctx ("" if none; a static
+ * string if ctx is NULL). */
+const char *gnb_last_error(const gnb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GALNB_H */

@@ -62,6 +62,8 @@ _i32 = C.POINTER(C.c_int32)
 
 def _declare(L):
     L.orc_direct_gravity.argtypes = [C.c_int64] + [_d] * 5 + [C.c_double] + [_d] * 5
+    L.orc_direct_gravity_sample.argtypes = ([C.c_int64] + [_d] * 5 + [C.c_double, C.c_int64, _i64]
+                                            + [_d] * 5)
     L.orc_root_box.argtypes = [C.c_int64, _d, _d, _d, _d, _d]
     L.orc_morton.argtypes = [C.c_int64, _d, _d, _d, _d, C.c_double, _u64, _i32, _i32, _i32]
     L.orc_sort_order.argtypes = [C.c_int64, _u64, _i64]
@@ -113,6 +115,19 @@ def direct_gravity(p: dict, G: float = 1.0) -> dict:
     lib().orc_direct_gravity(n, _p(x, np.float64), _p(y, np.float64), _p(z, np.float64),
                              _p(m, np.float64), _p(e, np.float64), G,
                              *(_p(out[k], np.float64) for k in ("ax", "ay", "az", "phi", "asum")))
+    return out
+
+
+def direct_gravity_sample(p: dict, sample, G: float = 1.0) -> dict:
+    """Eq. 1 direct sum for the listed particles only."""
+    n = p["x"].shape[0]
+    x, y, z, m, e = (f64(p[k]) for k in ("x", "y", "z", "m", "eps"))
+    sample = np.ascontiguousarray(sample, dtype=np.int64)
+    ns = sample.shape[0]
+    out = {k: np.zeros(ns) for k in ("ax", "ay", "az", "phi", "asum")}
+    lib().orc_direct_gravity_sample(n, _p(x, np.float64), _p(y, np.float64), _p(z, np.float64),
+                                    _p(m, np.float64), _p(e, np.float64), G, ns, _p(sample, np.int64),
+                                    *(_p(out[k], np.float64) for k in ("ax", "ay", "az", "phi", "asum")))
     return out
 
 

@@ -624,3 +624,30 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Eq. 1 direct sum for the ns particles listed in `sample` only (used to
+ * check full-size runs on a subsample).  Outputs have length ns. */
+void orc_direct_gravity_sample(int64_t n, const double *x, const double *y, const double *z,
+                               const double *m, const double *eps, double G, int64_t ns,
+                               const int64_t *sample, double *ax, double *ay, double *az,
+                               double *phi, double *asum)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t s = 0; s < ns; s++) {
+        int64_t i = sample[s];
+        double sx = 0, sy = 0, sz = 0, sp = 0, sa = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
+            double r2 = dx * dx + dy * dy + dz * dz + eps[i] * eps[i] + eps[j] * eps[j];
+            double rinv = 1.0 / sqrt(r2);
+            double f = G * m[j] * rinv * rinv * rinv;
+            sx -= f * dx;
+            sy -= f * dy;
+            sz -= f * dz;
+            sp -= G * m[j] * rinv;
+            sa += f * sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        ax[s] = sx; ay[s] = sy; az[s] = sz; phi[s] = sp; asum[s] = sa;
+    }
+}

@@ -1,0 +1,562 @@
+// capi.cu -- C ABI of the GB300 N-body/SPH library (declared in galnb.h).
+//
+// The calls follow the problem statement of Hirashima et al. (SC'25, arXiv
+// 2510.23330): particles with FP64 positions, FP32 velocity, mass and
+// per-particle softening (Sec. 3.5, 4.3); tree build (Sec. 3.4); gravity,
+// SPH density and force (Table 3); shared-timestep leapfrog (Sec. 3.2).
+// All device work runs on cfg.cuda_stream; each call ends with one stream
+// synchronisation and a check of the device status word.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gnb {
+
+int fail(gnb_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_check(gnb_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return GNB_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(c, GNB_ENOMEM, m);
+    return fail(c, GNB_ECUDA, m);
+}
+
+void dfree(gnb_ctx *, void *p)
+{
+    if (p) cudaFree(p);
+}
+
+static void parr_free(gnb_ctx *c, PArr &p)
+{
+    void *all[] = {p.x, p.y, p.z, p.h2, p.id, p.vx, p.vy, p.vz, p.m, p.eps, p.u, p.rx, p.ry, p.rz,
+                   p.vpx, p.vpy, p.vpz, p.up, p.orig, p.grank, p.cx, p.cy, p.cz, p.type};
+    for (void *q : all) dfree(c, q);
+    p = PArr();
+}
+
+static int parr_alloc(gnb_ctx *c, PArr &p, size_t n)
+{
+    GNB_TRY(dalloc(c, &p.x, n)); GNB_TRY(dalloc(c, &p.y, n)); GNB_TRY(dalloc(c, &p.z, n));
+    GNB_TRY(dalloc(c, &p.h2, n)); GNB_TRY(dalloc(c, &p.id, n));
+    GNB_TRY(dalloc(c, &p.vx, n)); GNB_TRY(dalloc(c, &p.vy, n)); GNB_TRY(dalloc(c, &p.vz, n));
+    GNB_TRY(dalloc(c, &p.m, n)); GNB_TRY(dalloc(c, &p.eps, n)); GNB_TRY(dalloc(c, &p.u, n));
+    GNB_TRY(dalloc(c, &p.rx, n)); GNB_TRY(dalloc(c, &p.ry, n)); GNB_TRY(dalloc(c, &p.rz, n));
+    GNB_TRY(dalloc(c, &p.vpx, n)); GNB_TRY(dalloc(c, &p.vpy, n)); GNB_TRY(dalloc(c, &p.vpz, n));
+    GNB_TRY(dalloc(c, &p.up, n));
+    GNB_TRY(dalloc(c, &p.orig, n)); GNB_TRY(dalloc(c, &p.grank, n));
+    GNB_TRY(dalloc(c, &p.cx, n)); GNB_TRY(dalloc(c, &p.cy, n)); GNB_TRY(dalloc(c, &p.cz, n));
+    GNB_TRY(dalloc(c, &p.type, n));
+    return GNB_OK;
+}
+
+static void free_particles(gnb_ctx *c)
+{
+    parr_free(c, c->P[0]);
+    parr_free(c, c->P[1]);
+    void *all[] = {c->ax, c->ay, c->az, c->pot, c->dudt, c->gax, c->gay, c->gaz, c->pext, c->rho, c->pres,
+                   c->cs, c->key, c->skey, c->skey2, c->sval, c->sval2, c->slot_of_orig, c->src, c->rs_counts,
+                   c->gas_flag, c->pscan, c->tmp_out};
+    for (void *q : all) dfree(c, q);
+    c->ax = c->ay = c->az = c->pot = c->dudt = c->gax = c->gay = c->gaz = c->pext = nullptr;
+    c->rho = c->pres = c->cs = nullptr;
+    c->key = c->skey = c->skey2 = nullptr;
+    c->sval = c->sval2 = c->slot_of_orig = c->src = c->rs_counts = c->gas_flag = c->pscan = nullptr;
+    c->tmp_out = nullptr;
+    tree_free(c, c->t);
+    c->cap = 0;
+}
+
+static void free_gas(gnb_ctx *c)
+{
+    void *all[] = {c->gslot, c->gkey, c->gcx, c->gcy, c->gcz, c->ggrank, c->grx, c->gry, c->grz, c->gx, c->gy,
+                   c->gz, c->gm, c->gvx, c->gvy, c->gvz, c->gu, c->gh2, c->gh, c->g64, c->grho, c->gP, c->gcs,
+                   c->gRprev, c->gE, c->nbr, c->nd2, c->mut, c->rcnt, c->roff, c->rfill, c->rlist, c->hax,
+                   c->hay, c->haz, c->hdu, c->kflag, c->kR, c->kRb, c->kitem};
+    for (void *q : all) dfree(c, q);
+    c->gslot = nullptr; c->gkey = nullptr; c->gcx = c->gcy = c->gcz = c->ggrank = nullptr;
+    c->grx = c->gry = c->grz = nullptr; c->gx = c->gy = c->gz = nullptr;
+    c->gm = c->gvx = c->gvy = c->gvz = c->gu = nullptr; c->gh2 = nullptr; c->gh = nullptr; c->g64 = nullptr;
+    c->grho = c->gP = c->gcs = c->gRprev = c->gE = nullptr; c->nbr = nullptr; c->nd2 = nullptr; c->mut = nullptr;
+    c->rcnt = c->roff = c->rfill = c->rlist = nullptr; c->hax = c->hay = c->haz = c->hdu = nullptr;
+    c->kflag = nullptr; c->kR = nullptr; c->kRb = nullptr; c->kitem = nullptr;
+    tree_free(c, c->gt);
+    c->gcap = 0;
+}
+
+static int alloc_particles(gnb_ctx *c, int64_t n)
+{
+    if (c->cap >= n) return GNB_OK;
+    free_particles(c);
+    size_t N = (size_t)n;
+    GNB_TRY(parr_alloc(c, c->P[0], N));
+    GNB_TRY(parr_alloc(c, c->P[1], N));
+    GNB_TRY(dalloc(c, &c->ax, N)); GNB_TRY(dalloc(c, &c->ay, N)); GNB_TRY(dalloc(c, &c->az, N));
+    GNB_TRY(dalloc(c, &c->pot, N)); GNB_TRY(dalloc(c, &c->dudt, N));
+    GNB_TRY(dalloc(c, &c->gax, N)); GNB_TRY(dalloc(c, &c->gay, N)); GNB_TRY(dalloc(c, &c->gaz, N));
+    GNB_TRY(dalloc(c, &c->pext, N)); GNB_TRY(dalloc(c, &c->rho, N)); GNB_TRY(dalloc(c, &c->pres, N));
+    GNB_TRY(dalloc(c, &c->cs, N));
+    GNB_TRY(dalloc(c, &c->key, N)); GNB_TRY(dalloc(c, &c->skey, N)); GNB_TRY(dalloc(c, &c->skey2, N));
+    GNB_TRY(dalloc(c, &c->sval, N)); GNB_TRY(dalloc(c, &c->sval2, N));
+    GNB_TRY(dalloc(c, &c->slot_of_orig, N)); GNB_TRY(dalloc(c, &c->src, N));
+    GNB_TRY(dalloc(c, &c->gas_flag, N + 1)); GNB_TRY(dalloc(c, &c->pscan, N + 1));
+    GNB_TRY(dalloc(c, &c->tmp_out, 8 * N + 64));
+    int ntiles = (int)((n + 2047) / 2048);
+    GNB_TRY(dalloc(c, &c->rs_counts, (size_t)ntiles * 256));
+    c->cap = n;
+    return GNB_OK;
+}
+
+static int alloc_gas(gnb_ctx *c, int64_t ng)
+{
+    if (c->gcap >= ng && c->gslot) return GNB_OK;
+    free_gas(c);
+    size_t G = (size_t)(ng > 0 ? ng : 1);
+    GNB_TRY(dalloc(c, &c->gslot, G)); GNB_TRY(dalloc(c, &c->gkey, G));
+    GNB_TRY(dalloc(c, &c->gcx, G)); GNB_TRY(dalloc(c, &c->gcy, G)); GNB_TRY(dalloc(c, &c->gcz, G));
+    GNB_TRY(dalloc(c, &c->ggrank, G));
+    GNB_TRY(dalloc(c, &c->grx, G)); GNB_TRY(dalloc(c, &c->gry, G)); GNB_TRY(dalloc(c, &c->grz, G));
+    GNB_TRY(dalloc(c, &c->gx, G)); GNB_TRY(dalloc(c, &c->gy, G)); GNB_TRY(dalloc(c, &c->gz, G));
+    GNB_TRY(dalloc(c, &c->gm, G)); GNB_TRY(dalloc(c, &c->gvx, G)); GNB_TRY(dalloc(c, &c->gvy, G));
+    GNB_TRY(dalloc(c, &c->gvz, G)); GNB_TRY(dalloc(c, &c->gu, G));
+    GNB_TRY(dalloc(c, &c->gh2, G)); GNB_TRY(dalloc(c, &c->gh, G)); GNB_TRY(dalloc(c, &c->g64, G));
+    GNB_TRY(dalloc(c, &c->grho, G)); GNB_TRY(dalloc(c, &c->gP, G)); GNB_TRY(dalloc(c, &c->gcs, G));
+    GNB_TRY(dalloc(c, &c->gRprev, G)); GNB_TRY(dalloc(c, &c->gE, G));
+    GNB_TRY(dalloc(c, &c->nbr, G * 64)); GNB_TRY(dalloc(c, &c->nd2, G * 64)); GNB_TRY(dalloc(c, &c->mut, G));
+    GNB_TRY(dalloc(c, &c->rcnt, G + 1)); GNB_TRY(dalloc(c, &c->roff, G + 1)); GNB_TRY(dalloc(c, &c->rfill, G + 1));
+    GNB_TRY(dalloc(c, &c->rlist, G * 64));
+    cudaMemset(c->nbr, 0, sizeof(int) * G * 64);  // list entries are always valid indices
+    GNB_TRY(dalloc(c, &c->hax, G)); GNB_TRY(dalloc(c, &c->hay, G)); GNB_TRY(dalloc(c, &c->haz, G));
+    GNB_TRY(dalloc(c, &c->hdu, G));
+    GNB_TRY(dalloc(c, &c->kflag, 2 * G + 1)); GNB_TRY(dalloc(c, &c->kR, 2 * G + 1));
+    GNB_TRY(dalloc(c, &c->kRb, 2 * G + 1)); GNB_TRY(dalloc(c, &c->kitem, 2 * G + 1));
+    c->gcap = ng;
+    return GNB_OK;
+}
+
+// After a synchronisation: translate and clear the device status word.
+static int check_status(gnb_ctx *c)
+{
+    GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "stream synchronize"));
+    GNB_TRY(cuda_check(c, cudaGetLastError(), "kernel"));
+    int st = 0;
+    GNB_TRY(cuda_check(c, cudaMemcpy(&st, c->status_d, sizeof(int), cudaMemcpyDeviceToHost), "status read"));
+    if (st == 0) return GNB_OK;
+    cudaMemset(c->status_d, 0, sizeof(int));
+    if (st & ST_BAD_INPUT) return fail(c, GNB_EINVAL, "non-finite particle position");
+    if (st & ST_TREE_OVERFLOW) return fail(c, GNB_ECAPACITY, "tree node capacity exceeded");
+    if (st & ST_STACK_OVERFLOW) return fail(c, GNB_ECAPACITY, "tree walk stack overflow");
+    if (st & ST_KNN_OVERFLOW) return fail(c, GNB_ECAPACITY, "kNN selection buffer overflow");
+    return fail(c, GNB_ECAPACITY, "device status " + std::to_string(st));
+}
+
+// ---------------------------------------------------------------- kernels used by set_particles
+__global__ void k_set_init(PArr p, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    p.orig[i] = i;
+    p.h2[i] = 0.0;
+    p.vpx[i] = p.vx[i]; p.vpy[i] = p.vy[i]; p.vpz[i] = p.vz[i];
+    if (p.type[i] != GNB_GAS) p.u[i] = 0.f;
+    p.up[i] = p.u[i];
+}
+
+__global__ void k_validate(PArr p, int n, int *bad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b = 0;
+    if (!isfinite(p.x[i]) || !isfinite(p.y[i]) || !isfinite(p.z[i])) b |= 1;
+    if (p.type[i] > 1) b |= 2;
+    if (!(p.m[i] > 0.f) || !isfinite(p.m[i])) b |= 4;
+    if (!(p.eps[i] >= 0.f) || !isfinite(p.eps[i])) b |= 8;
+    if (p.eps[i] == 0.f) b |= 16;
+    if (b) atomicOr(bad, b);
+}
+
+__global__ void k_gas_flag_in(const uint8_t *__restrict__ type, int *__restrict__ flag, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = type[i] == GNB_GAS;
+}
+
+__global__ void k_grank(const uint8_t *__restrict__ type, const int *__restrict__ off, int n, int *__restrict__ grank)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) grank[i] = type[i] == GNB_GAS ? off[i] : -1;
+}
+
+}  // namespace gnb
+
+using namespace gnb;
+
+extern "C" {
+
+void gnb_config_default(gnb_config *cfg)
+{
+    if (!cfg) return;
+    cfg->G = 1.0;
+    cfg->theta = 0.5;
+    cfg->gamma = 5.0 / 3.0;
+    cfg->alpha_visc = 1.0;
+    cfg->n_leaf = 16;
+    cfg->n_group = 64;
+    cfg->n_ngb = 64;
+    cfg->multipole = 1;
+    cfg->nfw_ms = 0.0;
+    cfg->nfw_rs = 8.0;
+    cfg->cuda_stream = nullptr;
+}
+
+int gnb_create(gnb_ctx **out, const gnb_config *cfg)
+{
+    if (!out || !cfg) return GNB_EINVAL;
+    *out = nullptr;
+    if (!(cfg->theta >= 0.0) || !(cfg->G > 0.0) || cfg->n_leaf < 1 || cfg->n_leaf > 255 || cfg->n_group < 1 ||
+        cfg->n_ngb != 64 || !(cfg->gamma > 1.0) || !(cfg->alpha_visc >= 0.0) || !(cfg->nfw_ms >= 0.0) ||
+        (cfg->nfw_ms > 0.0 && !(cfg->nfw_rs > 0.0)))
+        return GNB_EINVAL;
+    gnb_ctx *c = new (std::nothrow) gnb_ctx();
+    if (!c) return GNB_ENOMEM;
+    c->cfg = *cfg;
+    c->s = (cudaStream_t)cfg->cuda_stream;
+    int rc = GNB_OK;
+    if ((rc = dalloc(c, &c->status_d, 4)) || (rc = dalloc(c, &c->n_d, 4)) || (rc = dalloc(c, &c->ngas_d, 4)) ||
+        (rc = dalloc(c, &c->counters_d, 8)) || (rc = dalloc(c, &c->work_d, 8)) || (rc = dalloc(c, &c->box_d, 8)) ||
+        (rc = dalloc(c, &c->mm_d, 8)) || (rc = dalloc(c, &c->red_d, 256 * 10 + 16)) ||
+        (rc = dalloc(c, &c->rs_total, 256)) || (rc = dalloc(c, &c->rtot_d, 4)) ||
+        (rc = dalloc(c, &c->scan_part, 1100)) || (rc = dalloc(c, &c->scan_poff, 1100))) {
+        gnb_destroy(c);
+        return rc;
+    }
+    if (cudaMallocHost((void **)&c->pinned_i, 64 * sizeof(int)) != cudaSuccess) {
+        gnb_destroy(c);
+        return GNB_ENOMEM;
+    }
+    cudaMemset(c->status_d, 0, 4 * sizeof(int));
+    cudaMemset(c->counters_d, 0, 8 * sizeof(unsigned long long));
+    *out = c;
+    return GNB_OK;
+}
+
+void gnb_destroy(gnb_ctx *c)
+{
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    else cudaDeviceSynchronize();
+    free_particles(c);
+    free_gas(c);
+    void *all[] = {c->status_d, c->n_d, c->ngas_d, c->counters_d, c->work_d, c->box_d, c->mm_d, c->red_d,
+                   c->rs_total, c->rtot_d, c->scan_part, c->scan_poff};
+    for (void *q : all) dfree(c, q);
+    if (c->pinned_i) cudaFreeHost(c->pinned_i);
+    delete c;
+}
+
+int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *type, const double *x,
+                      const double *y, const double *z, const float *vx, const float *vy, const float *vz,
+                      const float *m, const float *eps, const float *u, int on_device)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (n < 1 || n > (1ll << 30)) return fail(c, GNB_EINVAL, "particle count out of range");
+    if (!id || !type || !x || !y || !z || !vx || !vy || !vz || !m || !eps || !u)
+        return fail(c, GNB_EINVAL, "null array");
+    c->have_particles = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = false;
+    c->sphf_valid = false;
+    c->have_h = false;
+    GNB_TRY(alloc_particles(c, n));
+    c->cur = 0;
+    PArr &p = c->P[0];
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t N = (size_t)n;
+    struct { void *d; const void *s; size_t b; } cp[] = {
+        {p.id, id, 8 * N}, {p.type, type, N}, {p.x, x, 8 * N}, {p.y, y, 8 * N}, {p.z, z, 8 * N},
+        {p.vx, vx, 4 * N}, {p.vy, vy, 4 * N}, {p.vz, vz, 4 * N}, {p.m, m, 4 * N}, {p.eps, eps, 4 * N},
+        {p.u, u, 4 * N}};
+    for (auto &q : cp) GNB_TRY(cuda_check(c, cudaMemcpyAsync(q.d, q.s, q.b, k, c->s), "particle copy"));
+    int ni = (int)n;
+    int nb = (ni + 255) / 256;
+    c->pinned_i[0] = ni;
+    cudaMemcpyAsync(c->n_d, c->pinned_i, sizeof(int), cudaMemcpyHostToDevice, c->s);
+    cudaMemsetAsync(c->work_d, 0, sizeof(int), c->s);
+    k_validate<<<nb, 256, 0, c->s>>>(p, ni, c->work_d);
+    k_set_init<<<nb, 256, 0, c->s>>>(p, ni);
+    k_gas_flag_in<<<nb, 256, 0, c->s>>>(p.type, c->gas_flag, ni);
+    GNB_TRY(device_scan(c, c->gas_flag, c->pscan, c->n_d, ni, c->ngas_d));
+    k_grank<<<nb, 256, 0, c->s>>>(p.type, c->pscan, ni, p.grank);
+    GNB_LAUNCH_CHECK(c, "set particles");
+    cudaMemcpyAsync(c->pinned_i + 1, c->work_d, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(c->pinned_i + 2, c->ngas_d, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "set particles sync"));
+    int bad = c->pinned_i[1];
+    int ng = c->pinned_i[2];
+    if (bad & 1) return fail(c, GNB_EINVAL, "non-finite position");
+    if (bad & 2) return fail(c, GNB_EINVAL, "particle type not in {0, 1}");
+    if (bad & 4) return fail(c, GNB_EINVAL, "mass must be positive and finite");
+    if (bad & 8) return fail(c, GNB_EINVAL, "softening must be non-negative and finite");
+    if (ng > 0 && ng < c->cfg.n_ngb) return fail(c, GNB_EINVAL, "fewer gas particles than SPH neighbours");
+    c->min_eps_zero = (bad & 16) != 0;
+    c->n = n;
+    c->n_gas = ng;
+    GNB_TRY(alloc_gas(c, ng));
+    c->stats[GNB_S_N] = n;
+    c->stats[GNB_S_NGAS] = ng;
+    c->have_particles = true;
+    return GNB_OK;
+}
+
+}  // extern "C"
+
+namespace gnb {
+
+static int do_build(gnb_ctx *c)
+{
+    GNB_TRY(morton_and_sort(c));
+    PArr &a = c->P[c->cur];
+    GNB_TRY(build_tree(c, c->t, c->skey, (int)c->n, c->n_d, c->cfg.n_leaf, c->cfg.n_group, a.cx, a.cy, a.cz, a.rx,
+                       a.ry, a.rz, a.m, a.eps, true));
+    c->tree_valid = true;
+    c->stats[GNB_S_NODES] = c->t.nnodes;
+    return GNB_OK;
+}
+
+static int read_groups(gnb_ctx *c)
+{
+    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->pinned_i + 8, c->t.ngroups_d, sizeof(int), cudaMemcpyDeviceToHost, c->s),
+                       "groups count"));
+    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->pinned_i + 9, c->t.lvl, sizeof(int) * (GNB_MAXLEV + 2),
+                                          cudaMemcpyDeviceToHost, c->s), "levels"));
+    GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "groups sync"));
+    c->t.ngroups = c->pinned_i[8];
+    c->stats[GNB_S_GROUPS] = c->t.ngroups;
+    int maxlev = 0;
+    for (int l = 0; l <= GNB_MAXLEV; l++)
+        if (c->pinned_i[9 + l + 1] > c->pinned_i[9 + l]) maxlev = l;
+    c->stats[GNB_S_MAXLEVEL] = maxlev;
+    return GNB_OK;
+}
+
+static int do_gravity(gnb_ctx *c, int mode)
+{
+    cudaMemsetAsync(c->counters_d, 0, 2 * sizeof(unsigned long long), c->s);
+    if (mode == GNB_GRAV_TREE) GNB_TRY(gravity_tree(c));
+    else GNB_TRY(gravity_direct(c));
+    GNB_TRY(gravity_nfw(c));
+    GNB_TRY(zero_forces(c));
+    c->gravity_valid = true;
+    c->last_grav_mode = mode;
+    return GNB_OK;
+}
+
+static int do_forces(gnb_ctx *c, int mode)
+{
+    GNB_TRY(do_build(c));
+    GNB_TRY(do_gravity(c, mode));
+    GNB_TRY(sph_density(c));
+    c->density_valid = true;
+    GNB_TRY(sph_force(c));
+    c->force_valid = true;
+    c->sphf_valid = true;
+    return GNB_OK;
+}
+
+static int finish(gnb_ctx *c, int rc)
+{
+    if (rc != GNB_OK) {
+        cudaStreamSynchronize(c->s);
+        cudaGetLastError();
+        cudaMemset(c->status_d, 0, sizeof(int));
+        return rc;
+    }
+    return check_status(c);
+}
+
+}  // namespace gnb
+
+extern "C" {
+
+int gnb_build_tree(gnb_ctx *c)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    int rc = do_build(c);
+    if (rc == GNB_OK) rc = read_groups(c);
+    c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    return finish(c, rc);
+}
+
+int gnb_compute_gravity(gnb_ctx *c, int mode)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (mode != GNB_GRAV_DIRECT && mode != GNB_GRAV_TREE) return fail(c, GNB_EINVAL, "gravity mode");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    int rc = GNB_OK;
+    if (!c->tree_valid) rc = do_build(c);
+    if (rc == GNB_OK) rc = do_gravity(c, mode);
+    if (rc == GNB_OK) rc = read_groups(c);
+    c->force_valid = false;
+    return finish(c, rc);
+}
+
+int gnb_compute_sph_density(gnb_ctx *c)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    int rc = GNB_OK;
+    if (!c->tree_valid) rc = do_build(c);
+    if (rc == GNB_OK) rc = sph_density(c);
+    if (rc == GNB_OK) c->density_valid = true;
+    c->force_valid = false;
+    return finish(c, rc);
+}
+
+int gnb_compute_sph_force(gnb_ctx *c)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed for the current positions");
+    int rc = GNB_OK;
+    if (!c->gravity_valid) {
+        size_t b = sizeof(float) * (size_t)c->n;
+        cudaMemsetAsync(c->ax, 0, b, c->s); cudaMemsetAsync(c->ay, 0, b, c->s); cudaMemsetAsync(c->az, 0, b, c->s);
+        cudaMemsetAsync(c->dudt, 0, b, c->s);
+    }
+    rc = sph_force(c);
+    if (rc == GNB_OK) { c->force_valid = c->gravity_valid; c->sphf_valid = true; }
+    return finish(c, rc);
+}
+
+int gnb_compute_forces(gnb_ctx *c, int mode)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (mode != GNB_GRAV_DIRECT && mode != GNB_GRAV_TREE) return fail(c, GNB_EINVAL, "gravity mode");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    int rc = do_forces(c, mode);
+    if (rc == GNB_OK) rc = read_groups(c);
+    return finish(c, rc);
+}
+
+int gnb_step_kdk(gnb_ctx *c, double dt, int nsteps, int mode)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!std::isfinite(dt) || nsteps < 0) return fail(c, GNB_EINVAL, "dt or nsteps");
+    if (mode != GNB_GRAV_DIRECT && mode != GNB_GRAV_TREE) return fail(c, GNB_EINVAL, "gravity mode");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    int rc = GNB_OK;
+    if (!c->force_valid || c->last_grav_mode != mode) {
+        rc = do_forces(c, mode);
+        if (rc != GNB_OK) return finish(c, rc);
+    }
+    float hdt = (float)(0.5 * dt);
+    for (int s = 0; s < nsteps && rc == GNB_OK; s++) {
+        rc = kick(c, hdt, true);
+        if (rc == GNB_OK) rc = drift(c, dt);
+        if (rc == GNB_OK) rc = predict(c, hdt);
+        c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+        c->use_pred = true;
+        if (rc == GNB_OK) rc = do_forces(c, mode);
+        c->use_pred = false;
+        if (rc == GNB_OK) rc = kick(c, hdt, true);
+    }
+    if (rc == GNB_OK) rc = read_groups(c);
+    return finish(c, rc);
+}
+
+static int64_t field_count(gnb_ctx *c, int f, size_t *esz)
+{
+    switch (f) {
+    case GNB_F_X: case GNB_F_Y: case GNB_F_Z: case GNB_F_H2: *esz = 8; return c->n;
+    case GNB_F_KEY: case GNB_F_ORDER: case GNB_F_ID: *esz = 8; return c->n;
+    case GNB_F_NBR: *esz = 8; return c->n_gas * 64;
+    case GNB_F_NODES: *esz = 8; return 4 * (int64_t)c->t.nnodes;
+    case GNB_F_GROUPS: *esz = 8; return c->t.ngroups;
+    default: *esz = 4; return c->n;
+    }
+}
+
+int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!dst || field < 0 || field >= GNB_F_COUNT_) return fail(c, GNB_EINVAL, "field or destination");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    bool need_tree = field == GNB_F_KEY || field == GNB_F_ORDER || field == GNB_F_NODES || field == GNB_F_GROUPS;
+    bool need_grav = field == GNB_F_AX || field == GNB_F_AY || field == GNB_F_AZ || field == GNB_F_POT ||
+                     field == GNB_F_AGRAV_X || field == GNB_F_AGRAV_Y || field == GNB_F_AGRAV_Z;
+    bool need_den = field == GNB_F_RHO || field == GNB_F_PRES || field == GNB_F_CS || field == GNB_F_H2 ||
+                    field == GNB_F_NBR;
+    if (need_tree && !c->tree_valid) return fail(c, GNB_ESTATE, "tree not built");
+    bool total_acc = field == GNB_F_AX || field == GNB_F_AY || field == GNB_F_AZ;
+    if (need_grav && !c->gravity_valid && !(total_acc && c->sphf_valid))
+        return fail(c, GNB_ESTATE, "forces not computed");
+    if (need_den && !c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed");
+    if (field == GNB_F_DUDT && !c->sphf_valid) return fail(c, GNB_ESTATE, "SPH force not computed");
+    size_t esz;
+    int64_t cnt = field_count(c, field, &esz);
+    if (cap < cnt) return fail(c, GNB_EINVAL, "destination too small");
+    if (cnt == 0) return GNB_OK;
+    int rc;
+    if (on_device) {
+        rc = scatter_out(c, field, dst);
+    } else {
+        void *tmp = c->tmp_out;
+        bool own = false;
+        if ((size_t)cnt * esz > (size_t)c->cap * 8 + 64 * 8) {
+            if (cudaMalloc(&tmp, (size_t)cnt * esz) != cudaSuccess) return fail(c, GNB_ENOMEM, "export buffer");
+            own = true;
+        }
+        rc = scatter_out(c, field, tmp);
+        if (rc == GNB_OK)
+            rc = cuda_check(c, cudaMemcpyAsync(dst, tmp, (size_t)cnt * esz, cudaMemcpyDeviceToHost, c->s), "export copy");
+        if (rc == GNB_OK) rc = cuda_check(c, cudaStreamSynchronize(c->s), "export sync");
+        if (own) cudaFree(tmp);
+    }
+    return finish(c, rc);
+}
+
+int gnb_diagnostics(gnb_ctx *c, double out[10])
+{
+    if (!c || !out) return GNB_EINVAL;
+    c->err.clear();
+    if (!c->gravity_valid) return fail(c, GNB_ESTATE, "forces not computed");
+    return finish(c, diagnostics(c, out));
+}
+
+int gnb_stats(gnb_ctx *c, int64_t out[GNB_S_COUNT_])
+{
+    if (!c || !out) return GNB_EINVAL;
+    unsigned long long h[2] = {0, 0};
+    if (c->counters_d) {
+        cudaStreamSynchronize(c->s);
+        cudaMemcpy(h, c->counters_d, sizeof(h), cudaMemcpyDeviceToHost);
+    }
+    c->stats[GNB_S_NPP] = (int64_t)h[0];
+    c->stats[GNB_S_NPC] = (int64_t)h[1];
+    int rt = 0;
+    if (c->rtot_d && c->n_gas > 0) cudaMemcpy(&rt, c->rtot_d, sizeof(int), cudaMemcpyDeviceToHost);
+    c->stats[GNB_S_NSYM] = (int64_t)c->n_gas * 63 + rt;
+    for (int k = 0; k < GNB_S_COUNT_; k++) out[k] = c->stats[k];
+    return GNB_OK;
+}
+
+const char *gnb_last_error(const gnb_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+}  // extern "C"

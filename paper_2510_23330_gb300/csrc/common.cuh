@@ -1,0 +1,230 @@
+// common.cuh -- internal declarations of the GB300 N-body/SPH library.
+//
+// Device data layout (all arrays live in HBM, structure of arrays, particles
+// in Morton order after every tree build):
+//   x, y, z      double   master positions (Sec. 4.3: FP64 storage)
+//   cx, cy, cz   int32    Morton grid cell of the particle (21 bits per axis)
+//   rx, ry, rz   float    residual x - (lo + c*unit), in [0, unit)
+//   vx, vy, vz   float    velocity; m, eps, u float; type uint8; id int64
+//   orig         int32    index of the particle in the caller's arrays
+//   grank        int32    rank among gas particles in the caller's order
+// Pair arithmetic uses the exact integer cell difference plus the FP32
+// residual difference, so an FP32 offset between any two particles carries
+// one rounding (relative 2^-24) without FP64 arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/galnb.h"
+
+#define GNB_MAXLEV 21
+#define GNB_GRID_MAX 2097151
+
+namespace gnb {
+
+// Device-side status word bits (set by kernels, read by the host).
+enum : int {
+    ST_TREE_OVERFLOW = 1,
+    ST_STACK_OVERFLOW = 2,
+    ST_KNN_OVERFLOW = 4,
+    ST_SYM_OVERFLOW = 8,
+    ST_BAD_INPUT = 16,
+};
+
+struct Tree {
+    int cap = 0;       // node capacity
+    int nnodes = 0;    // nodes of the last build (host copy)
+    int maxlev = 0;
+    // node arrays
+    int4 *na = nullptr;   // {first, count, child, (nchild << 8) | level}
+    int4 *nb = nullptr;   // {corner x, corner y, corner z, parent}
+    float4 *mo0 = nullptr; // {com_off x, y, z (rel. to corner, physical), M}
+    float4 *mo1 = nullptr; // {Qxx, Qyy, Qzz, Qxy}
+    float4 *mo2 = nullptr; // {Qxz, Qyz, eps2, 0}
+    int *lvl = nullptr;    // device: level begin offsets [GNB_MAXLEV + 2]
+    int *partial = nullptr;
+    int *poff = nullptr;
+    int *gmark = nullptr;  // per particle: node starting a group there, else -1
+    int *gflag = nullptr, *goff = nullptr;  // group compaction scratch
+    int *groups = nullptr; // group node ids, ascending first particle
+    int *ngroups_d = nullptr;
+    int ngroups = 0;
+};
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace gnb
+
+namespace gnb {
+// Per-particle arrays that move with the particle when the set is re-sorted.
+struct PArr {
+    double *x = nullptr, *y = nullptr, *z = nullptr, *h2 = nullptr;
+    int64_t *id = nullptr;
+    float *vx = nullptr, *vy = nullptr, *vz = nullptr, *m = nullptr, *eps = nullptr, *u = nullptr;
+    float *rx = nullptr, *ry = nullptr, *rz = nullptr;
+    float *vpx = nullptr, *vpy = nullptr, *vpz = nullptr, *up = nullptr;  // predicted v, u
+    int *orig = nullptr, *grank = nullptr, *cx = nullptr, *cy = nullptr, *cz = nullptr;
+    uint8_t *type = nullptr;
+};
+}  // namespace gnb
+
+struct gnb_ctx {
+    gnb_config cfg;
+    cudaStream_t s = nullptr;
+    std::string err;
+    int64_t n = 0, n_gas = 0;
+    int64_t cap = 0;          // particle capacity
+    bool min_eps_zero = false;
+
+    gnb::PArr P[2];
+    int cur = 0;              // P[cur] holds the particles
+    // per-slot results of the last force evaluation (not permuted)
+    float *ax = nullptr, *ay = nullptr, *az = nullptr, *pot = nullptr, *dudt = nullptr;
+    float *gax = nullptr, *gay = nullptr, *gaz = nullptr;  // self-gravity part
+    float *pext = nullptr;                                  // external potential
+    float *rho = nullptr, *pres = nullptr, *cs = nullptr;   // gas fields per slot
+    // sort scratch
+    uint64_t *key = nullptr, *skey = nullptr, *skey2 = nullptr;
+    int *sval = nullptr, *sval2 = nullptr, *slot_of_orig = nullptr, *src = nullptr;
+    int *pscan = nullptr;     // per-slot scan scratch
+    unsigned char *tmp_out = nullptr;  // export staging (8 bytes per particle)
+    int *rs_counts = nullptr, *rs_total = nullptr;
+    int rs_tiles_cap = 0;
+    // root box: device {lo[3], L, unit} plus min/max scratch
+    double *box_d = nullptr;
+    unsigned long long *mm_d = nullptr;
+    double lo[3] = {0, 0, 0}, L = 1, unit = 1;
+    // gravity tree
+    gnb::Tree t;
+    // hydro (gas) arrays, gas order = Morton order of the gas particles
+    int64_t gcap = 0;
+    int *gslot = nullptr;         // particle slot of each gas particle
+    int *gas_flag = nullptr, *ngas_d = nullptr;
+    uint64_t *gkey = nullptr;
+    gnb::Tree gt;                 // hydro tree over gas
+    int *gcx = nullptr, *gcy = nullptr, *gcz = nullptr, *ggrank = nullptr;
+    float *grx = nullptr, *gry = nullptr, *grz = nullptr;
+    double *gx = nullptr, *gy = nullptr, *gz = nullptr;
+    float *gm = nullptr, *gvx = nullptr, *gvy = nullptr, *gvz = nullptr, *gu = nullptr;
+    double *gh2 = nullptr;        // exact FP64 d^2 of the n_ngb-th neighbour
+    float *gh = nullptr;          // h in FP32
+    int *g64 = nullptr;           // gas rank of the n_ngb-th neighbour
+    float *grho = nullptr, *gP = nullptr, *gcs = nullptr;
+    float *gRprev = nullptr;      // search radius hint per gas particle
+    float *gE = nullptr;          // FP32 distance error bound used for the particle's list
+    unsigned long long *mut = nullptr;  // per gas particle: mutual-neighbour bits
+    int *nbr = nullptr;           // n_gas * 64 gas indices
+    float *nd2 = nullptr;         // n_gas * 64 FP32 d^2
+    int *rcnt = nullptr, *roff = nullptr, *rfill = nullptr, *rlist = nullptr;
+    int *rtot_d = nullptr;
+    int64_t rlist_cap = 0;
+    float *hax = nullptr, *hay = nullptr, *haz = nullptr, *hdu = nullptr;
+    int *kflag = nullptr;         // per hydro group: needs another pass
+    float *kR = nullptr;          // per hydro group search radius
+    float2 *kRb = nullptr;        // per hydro group radius bracket (too small, too large)
+    int2 *kitem = nullptr;        // kNN work items (first, count); groups then split particles
+    int *kcount_d = nullptr;
+
+    // status / counters
+    int *status_d = nullptr;
+    int *n_d = nullptr;                        // device copy of n
+    unsigned long long *counters_d = nullptr;  // [8]
+    int *work_d = nullptr;                     // work counters of persistent kernels [8]
+    int *scan_part = nullptr, *scan_poff = nullptr;  // device_scan scratch [1100]
+    int *pinned_i = nullptr;                   // pinned host scratch [64]
+    double *red_d = nullptr;                   // reduction scratch
+    int64_t stats[GNB_S_COUNT_] = {0};
+
+    // state flags
+    bool have_particles = false, tree_valid = false, gravity_valid = false;
+    bool density_valid = false, force_valid = false, have_h = false, sphf_valid = false;
+    bool use_pred = false;      // SPH uses predicted v, u (inside a KDK step)
+    int last_grav_mode = -1;
+};
+
+namespace gnb {
+
+// host helpers (capi.cu)
+int fail(gnb_ctx *c, int code, const std::string &msg);
+int cuda_check(gnb_ctx *c, cudaError_t e, const char *what);
+void dfree(gnb_ctx *c, void *p);
+
+// Device allocation of count elements; GNB_ENOMEM on failure.
+template <class T>
+inline int dalloc(gnb_ctx *c, T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, GNB_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    return GNB_OK;
+}
+
+// sort.cu
+int morton_and_sort(gnb_ctx *c);
+int root_box(gnb_ctx *c);
+// tree.cu
+int build_tree(gnb_ctx *c, Tree &t, const uint64_t *skey, int n, const int *n_d, int n_leaf,
+               int n_group, const int *pcx, const int *pcy, const int *pcz, const float *prx,
+               const float *pry, const float *prz, const float *pm, const float *peps,
+               bool moments);
+int tree_alloc(gnb_ctx *c, Tree &t, int cap);
+void tree_free(gnb_ctx *c, Tree &t);
+int device_scan(gnb_ctx *c, const int *in, int *out, const int *n_d, int nmax, int *total_d);
+// gravity.cu
+int gravity_tree(gnb_ctx *c);
+int gravity_direct(gnb_ctx *c);
+int gravity_nfw(gnb_ctx *c);
+// sph.cu
+int sph_density(gnb_ctx *c);
+int sph_force(gnb_ctx *c);
+// integrate.cu
+int kick(gnb_ctx *c, float hdt, bool gas_u);
+int drift(gnb_ctx *c, double dt);
+int predict(gnb_ctx *c, float hdt);
+int diagnostics(gnb_ctx *c, double out[10]);
+int scatter_out(gnb_ctx *c, int field, void *dst_dev);
+int zero_forces(gnb_ctx *c);
+
+}  // namespace gnb
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#define GNB_LAUNCH_CHECK(c, what)                                                    \
+    do {                                                                             \
+        cudaError_t e_ = cudaGetLastError();                                         \
+        if (e_ != cudaSuccess) return gnb::cuda_check((c), e_, (what));              \
+    } while (0)
+
+#define GNB_TRY(expr)                 \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_ != GNB_OK) return rc_; \
+    } while (0)
+
+__device__ __forceinline__ float fsqr(float a) { return a * a; }
+
+// Offset of a particle from a reference grid point: the integer cell
+// difference is exact in FP32 (|d| < 2^24) and scaling by the power-of-two
+// unit is exact, so the FMA rounds once.
+__device__ __forceinline__ float grid_off(int c, int cref, float r, float unit)
+{
+    return __fmaf_rn((float)(c - cref), unit, r);
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}

@@ -1,0 +1,319 @@
+// sort.cu -- root box, Morton keys and the space-filling-curve sort
+// (tree construction, Sec. 3.4 and 5.2.2 of Hirashima et al., SC'25).
+//
+// Root box: lo_k = min x_k, ext = max_k(max x_k - lo_k), L = 2^ceil(log2 ext)
+// (L = 1 when ext = 0), unit = L / 2^21.  Cell c_k = min(floor((x_k - lo_k) *
+// 2^21 / L), 2^21 - 1) from exact FP64 operations; the key interleaves bit b
+// of c_x, c_y, c_z at 3b+2, 3b+1, 3b.  Particles are ordered by (key, caller
+// index): the keys are scattered to caller order and sorted by a stable LSD
+// radix sort, so equal keys keep caller order.
+#include "common.cuh"
+
+namespace gnb {
+
+// ---------------------------------------------------------------- root box
+__device__ __forceinline__ unsigned long long dbl_to_ord(double v)
+{
+    long long b = __double_as_longlong(v);
+    return b >= 0 ? ((unsigned long long)b ^ 0x8000000000000000ull) : ~(unsigned long long)b;
+}
+__device__ __forceinline__ double ord_to_dbl(unsigned long long o)
+{
+    long long b = (o & 0x8000000000000000ull) ? (long long)(o ^ 0x8000000000000000ull)
+                                              : (long long)~o;
+    return __longlong_as_double(b);
+}
+
+__global__ void k_mm_init(unsigned long long *mm)
+{
+    int t = threadIdx.x;
+    if (t < 3) mm[t] = ~0ull;        // min
+    else if (t < 6) mm[t] = 0ull;    // max
+    else if (t == 6) mm[t] = 0ull;   // non-finite flag
+}
+
+__global__ void k_minmax(const double *__restrict__ x, const double *__restrict__ y,
+                         const double *__restrict__ z, int n, unsigned long long *mm)
+{
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double v[3] = {x[i], y[i], z[i]};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            bad |= !isfinite(v[a]);
+            unsigned long long o = dbl_to_ord(v[a]);
+            mn[a] = o < mn[a] ? o : mn[a];
+            mx[a] = o > mx[a] ? o : mx[a];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long p = __shfl_xor_sync(0xffffffffu, mn[a], o);
+            unsigned long long q = __shfl_xor_sync(0xffffffffu, mx[a], o);
+            mn[a] = p < mn[a] ? p : mn[a];
+            mx[a] = q > mx[a] ? q : mx[a];
+        }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            atomicMin(&mm[a], mn[a]);
+            atomicMax(&mm[3 + a], mx[a]);
+        }
+        if (bad) atomicExch(&mm[6], 1ull);
+    }
+}
+
+// box = {lo_x, lo_y, lo_z, L, unit}
+__global__ void k_box_finalize(const unsigned long long *mm, double *box, int *status)
+{
+    if (threadIdx.x != 0) return;
+    if (mm[6]) atomicOr(status, ST_BAD_INPUT);
+    double ext = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double lo = ord_to_dbl(mm[a]), hi = ord_to_dbl(mm[3 + a]);
+        box[a] = lo;
+        double e = __dsub_rn(hi, lo);
+        ext = e > ext ? e : ext;
+    }
+    double L = 1.0;
+    if (ext > 0.0) {
+        while (L < ext) L *= 2.0;
+        while (L / 2.0 >= ext) L /= 2.0;
+    }
+    box[3] = L;
+    box[4] = L / 2097152.0;
+}
+
+int root_box(gnb_ctx *c)
+{
+    int n = (int)c->n;
+    k_mm_init<<<1, 32, 0, c->s>>>(c->mm_d);
+    int blocks = (n + 255) / 256;
+    if (blocks > 1216) blocks = 1216;
+    k_minmax<<<blocks, 256, 0, c->s>>>(c->P[c->cur].x, c->P[c->cur].y, c->P[c->cur].z, n, c->mm_d);
+    k_box_finalize<<<1, 32, 0, c->s>>>(c->mm_d, c->box_d, c->status_d);
+    GNB_LAUNCH_CHECK(c, "root box");
+    return GNB_OK;
+}
+
+// ---------------------------------------------------------------- Morton
+__host__ __device__ __forceinline__ uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ int cell_of(double x, double lo, double scale, double unit, float *r)
+{
+    double d = __dsub_rn(x, lo);
+    double f = floor(__dmul_rn(d, scale));
+    int c = f < 0.0 ? 0 : (f > (double)GNB_GRID_MAX ? GNB_GRID_MAX : (int)f);
+    *r = (float)__dsub_rn(d, __dmul_rn((double)c, unit));
+    return c;
+}
+
+// Keys, cells and residuals of every slot; keys and the slot map are also
+// scattered to caller order for the sort.
+__global__ void k_morton(PArr p, int n, const double *__restrict__ box, uint64_t *__restrict__ key,
+                         uint64_t *__restrict__ keyo, int *__restrict__ valo,
+                         int *__restrict__ slot_of_orig)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double lo0 = box[0], lo1 = box[1], lo2 = box[2], L = box[3], unit = box[4];
+    double scale = 2097152.0 / L;
+    float r0, r1, r2;
+    int c0 = cell_of(p.x[i], lo0, scale, unit, &r0);
+    int c1 = cell_of(p.y[i], lo1, scale, unit, &r1);
+    int c2 = cell_of(p.z[i], lo2, scale, unit, &r2);
+    p.cx[i] = c0; p.cy[i] = c1; p.cz[i] = c2;
+    p.rx[i] = r0; p.ry[i] = r1; p.rz[i] = r2;
+    uint64_t k = (spread3(c0) << 2) | (spread3(c1) << 1) | spread3(c2);
+    key[i] = k;
+    int o = p.orig[i];
+    keyo[o] = k;
+    valo[o] = o;
+    slot_of_orig[o] = i;
+}
+
+// ---------------------------------------------------------------- radix sort
+// Stable LSD radix sort of (64-bit key, 32-bit value), 8 bits per pass.
+// Tiles of RS_TILE keys; per pass: digit histogram per tile, per-digit scan
+// over tiles, stable scatter with per-warp match ranks.
+#define RS_THREADS 256
+#define RS_ITEMS 8
+#define RS_TILE (RS_THREADS * RS_ITEMS)
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restrict__ k, int n, int shift,
+                                                       int *__restrict__ counts, int ntiles,
+                                                       int *__restrict__ total)
+{
+    __shared__ int h[256];
+    int t = threadIdx.x, tile = blockIdx.x;
+    h[t] = 0;
+    __syncthreads();
+    int base = tile * RS_TILE;
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        int i = base + r * RS_THREADS + t;
+        if (i < n) atomicAdd(&h[(int)((k[i] >> shift) & 255u)], 1);
+    }
+    __syncthreads();
+    int v = h[t];
+    counts[t * ntiles + tile] = v;
+    if (v) atomicAdd(&total[t], v);
+}
+
+// One block per digit: offs[d][tile] = base(d) + sum_{t' < tile} counts[d][t'].
+__global__ void __launch_bounds__(1024) k_rs_scan(int *__restrict__ counts, int ntiles,
+                                                  const int *__restrict__ total)
+{
+    __shared__ int wsum[32];
+    __shared__ int s_base, s_carry;
+    int d = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t < 32) {
+        int acc = 0;
+        for (int e = lane; e < d; e += 32) acc += total[e];
+        acc = warp_sum(acc);
+        if (lane == 0) { s_base = acc; s_carry = 0; }
+    }
+    __syncthreads();
+    int *row = counts + (size_t)d * ntiles;
+    for (int b0 = 0; b0 < ntiles; b0 += 1024) {
+        int i = b0 + t;
+        int v = i < ntiles ? row[i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        int excl = x - v + (w > 0 ? wsum[w - 1] : 0);
+        if (i < ntiles) row[i] = s_base + s_carry + excl;
+        __syncthreads();
+        if (t == 0) s_carry += wsum[31];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__restrict__ kin,
+                                                          const int *__restrict__ vin,
+                                                          uint64_t *__restrict__ kout,
+                                                          int *__restrict__ vout, int n, int shift,
+                                                          const int *__restrict__ offs, int ntiles)
+{
+    __shared__ int s_w[8][256];
+    __shared__ int s_run[256];
+    __shared__ int s_off[256];
+    int t = threadIdx.x, tile = blockIdx.x, w = t >> 5, lane = t & 31;
+    s_run[t] = 0;
+    s_off[t] = offs[t * ntiles + tile];
+    unsigned lt = (1u << lane) - 1u;
+    int base = tile * RS_TILE;
+    for (int r = 0; r < RS_ITEMS; r++) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) s_w[q][t] = 0;
+        __syncthreads();
+        int i = base + r * RS_THREADS + t;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0ull;
+        int d = valid ? (int)((key >> shift) & 255u) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lt);
+        if (valid && rank == 0) s_w[w][d] = __popc(peers);
+        __syncthreads();
+        {
+            int run = s_run[t];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                int cnt = s_w[q][t];
+                s_w[q][t] = run;
+                run += cnt;
+            }
+            s_run[t] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            int dst = s_off[d] + s_w[w][d] + rank;
+            kout[dst] = key;
+            vout[dst] = vin[i];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- permute
+// New slot i takes old slot src[i] = slot_of_orig[sorted caller index].
+__global__ void k_src(const int *__restrict__ sval, const int *__restrict__ slot_of_orig,
+                      int *__restrict__ src, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) src[i] = slot_of_orig[sval[i]];
+}
+
+__global__ void k_permute(PArr a, PArr b, const int *__restrict__ src, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = src[i];
+    b.x[i] = a.x[s]; b.y[i] = a.y[s]; b.z[i] = a.z[s]; b.h2[i] = a.h2[s]; b.id[i] = a.id[s];
+    b.vx[i] = a.vx[s]; b.vy[i] = a.vy[s]; b.vz[i] = a.vz[s];
+    b.m[i] = a.m[s]; b.eps[i] = a.eps[s]; b.u[i] = a.u[s];
+    b.rx[i] = a.rx[s]; b.ry[i] = a.ry[s]; b.rz[i] = a.rz[s];
+    b.vpx[i] = a.vpx[s]; b.vpy[i] = a.vpy[s]; b.vpz[i] = a.vpz[s]; b.up[i] = a.up[s];
+    b.orig[i] = a.orig[s]; b.grank[i] = a.grank[s];
+    b.cx[i] = a.cx[s]; b.cy[i] = a.cy[s]; b.cz[i] = a.cz[s];
+    b.type[i] = a.type[s];
+}
+
+int morton_and_sort(gnb_ctx *c)
+{
+    int n = (int)c->n;
+    GNB_TRY(root_box(c));
+    int nb = (n + 255) / 256;
+    PArr &a = c->P[c->cur];
+    k_morton<<<nb, 256, 0, c->s>>>(a, n, c->box_d, c->key, c->skey, c->sval, c->slot_of_orig);
+    GNB_LAUNCH_CHECK(c, "morton");
+    int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    uint64_t *kin = c->skey, *kout = c->skey2;
+    int *vin = c->sval, *vout = c->sval2;
+    for (int pass = 0; pass < 8; pass++) {
+        int shift = 8 * pass;
+        cudaMemsetAsync(c->rs_total, 0, 256 * sizeof(int), c->s);
+        k_rs_hist<<<ntiles, RS_THREADS, 0, c->s>>>(kin, n, shift, c->rs_counts, ntiles, c->rs_total);
+        k_rs_scan<<<256, 1024, 0, c->s>>>(c->rs_counts, ntiles, c->rs_total);
+        k_rs_scatter<<<ntiles, RS_THREADS, 0, c->s>>>(kin, vin, kout, vout, n, shift, c->rs_counts,
+                                                      ntiles);
+        uint64_t *tk = kin; kin = kout; kout = tk;
+        int *tv = vin; vin = vout; vout = tv;
+    }
+    GNB_LAUNCH_CHECK(c, "radix sort");
+    // after 8 passes the sorted data is back in skey / sval
+    k_src<<<nb, 256, 0, c->s>>>(vin, c->slot_of_orig, c->src, n);
+    PArr &b = c->P[1 - c->cur];
+    k_permute<<<nb, 256, 0, c->s>>>(a, b, c->src, n);
+    GNB_LAUNCH_CHECK(c, "permute");
+    c->cur = 1 - c->cur;
+    return GNB_OK;
+}
+
+}  // namespace gnb

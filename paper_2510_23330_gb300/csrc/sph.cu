@@ -1,0 +1,754 @@
+// sph.cu -- SPH kernel size, density/pressure and hydro force
+// (Sec. 5.2.5, Table 3 "kernel size", "density and pressure", "hydro force"
+// and Table 4 of Hirashima et al., SC'25).
+//
+// Kernel size: the support h_i of gas particle i is the distance to its
+// n_ngb-th nearest gas neighbour (self included), neighbours ordered by
+// (d^2, gas rank) with d^2 = (dx*dx + dy*dy) + dz*dz in FP64.  The paper
+// iterates a search until it converges; here one CTA per hydro-tree group
+// gathers every gas particle within a search radius R of the group into
+// shared memory, and each warp selects the neighbours of one particle:
+//   1. FP32 distances d (exact grid offsets, error |d - D| <= E, proven
+//      bound E = 2^-17 A^2 with A the largest offset in the group),
+//   2. a 64-bin histogram and an in-bucket rank give the exact 64th smallest
+//      FP32 value t,
+//   3. entries with d < t - 2E are certainly neighbours, entries with
+//      d > t + 2E certainly not; only the few in between get the exact FP64
+//      d^2 and are ranked by (d^2, gas rank).
+// A group whose radius holds fewer than n_ngb particles for some member, or
+// more candidates than fit, retries with a bisected radius (the paper's
+// "usually twice").  Density and the ideal-gas EOS are fused in.
+//
+// Force: symmetric SPH over S_i = N_i u {j : i in N_j}.  The reverse part is
+// built from the non-mutual pairs only, so N_i and R_i are disjoint.
+#include "common.cuh"
+
+namespace gnb {
+
+#define KN_THREADS 128
+#define KN_WARPS (KN_THREADS / 32)
+#define KN_CAP 2048
+#define KN_STACK 2048
+#define KN_BKT 256
+#define KN_U 64
+#define NGB 64
+
+__device__ __forceinline__ float kern_w(float r, float hinv)
+{
+    float q = r * hinv;
+    float s = 2.546479089470325f * hinv * hinv * hinv;  // 8/pi h^-3
+    if (q <= 0.5f) return s * (1.f - 6.f * q * q + 6.f * q * q * q);
+    if (q <= 1.f) { float t = 1.f - q; return s * 2.f * t * t * t; }
+    return 0.f;
+}
+
+__device__ __forceinline__ float kern_dw(float r, float hinv)
+{
+    float q = r * hinv;
+    float s = 2.546479089470325f * hinv * hinv * hinv * hinv;
+    if (q <= 0.5f) return s * (-12.f * q + 18.f * q * q);
+    if (q <= 1.f) { float t = 1.f - q; return -6.f * s * t * t; }
+    return 0.f;
+}
+
+// ---------------------------------------------------------------- gas extraction
+__global__ void k_gas_flag(const uint8_t *__restrict__ type, int *__restrict__ flag, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = type[i] == GNB_GAS;
+}
+
+__global__ void k_gas_compact(const int *__restrict__ flag, const int *__restrict__ off, int n,
+                              int *__restrict__ gslot)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) gslot[off[i]] = i;
+}
+
+struct GasGather {
+    const uint64_t *skey;
+    PArr p;
+    const int *gslot;
+    uint64_t *gkey;
+    int *gcx, *gcy, *gcz, *ggrank;
+    float *grx, *gry, *grz, *gm, *gvx, *gvy, *gvz, *gu, *gRprev;
+    double *gx, *gy, *gz;
+    int ng;
+    int pred;
+    int have_h;
+};
+
+__global__ void k_gas_gather(GasGather g)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.ng) return;
+    int s = g.gslot[k];
+    g.gkey[k] = g.skey[s];
+    g.gcx[k] = g.p.cx[s]; g.gcy[k] = g.p.cy[s]; g.gcz[k] = g.p.cz[s];
+    g.grx[k] = g.p.rx[s]; g.gry[k] = g.p.ry[s]; g.grz[k] = g.p.rz[s];
+    g.gx[k] = g.p.x[s]; g.gy[k] = g.p.y[s]; g.gz[k] = g.p.z[s];
+    g.gm[k] = g.p.m[s];
+    g.ggrank[k] = g.p.grank[s];
+    if (g.pred) {
+        g.gvx[k] = g.p.vpx[s]; g.gvy[k] = g.p.vpy[s]; g.gvz[k] = g.p.vpz[s]; g.gu[k] = g.p.up[s];
+    } else {
+        g.gvx[k] = g.p.vx[s]; g.gvy[k] = g.p.vy[s]; g.gvz[k] = g.p.vz[s]; g.gu[k] = g.p.u[s];
+    }
+    g.gRprev[k] = g.have_h ? (float)sqrt(g.p.h2[s]) : 0.f;
+}
+
+// ---------------------------------------------------------------- search radius
+// Initial radius per hydro group: 1.1 x the largest previous support in the
+// group, or, without history, a density estimate from the smallest ancestor
+// cell holding at least n_ngb particles.
+__global__ void k_knn_init(Tree t, const float *__restrict__ hprev, int have_h, const double *__restrict__ box,
+                           float *__restrict__ kR, float2 *__restrict__ kRb, int *__restrict__ kflag,
+                           int2 *__restrict__ kitem, int *__restrict__ nitems)
+{
+    int ng = *t.ngroups_d;
+    float unit = (float)box[4];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nitems = ng;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        int node = t.groups[g];
+        int4 a = t.na[node];
+        kitem[g] = make_int2(a.x, a.y);
+        float R = 0.f;
+        if (have_h) {
+            for (int i = a.x; i < a.x + a.y; i++) R = fmaxf(R, hprev[i]);
+            R *= 1.1f;
+        }
+        if (!(R > 0.f)) {
+            int q = node;
+            while (t.na[q].y < NGB && t.nb[q].w >= 0) q = t.nb[q].w;
+            int4 aq = t.na[q];
+            int lev = aq.w & 255;
+            float side = (float)(1 << (GNB_MAXLEV - lev)) * unit;
+            R = 0.9f * side * cbrtf((float)NGB / (float)max(aq.y, 1));
+        }
+        kR[g] = R;
+        kRb[g] = make_float2(0.f, 0.f);
+        kflag[g] = 1;
+    }
+}
+
+// Work items: a hydro group, or a single particle split off a group whose
+// candidates did not fit at the radius its members need.
+struct KnnParams {
+    int4 *na, *nb;
+    int2 *item;
+    int *nitems;       // live count (splits append here)
+    const int *nsnap;  // count at the start of this pass (only these are processed)
+    int item_cap;
+    const int *gcx, *gcy, *gcz, *ggrank;
+    const float *grx, *gry, *grz, *gm, *gu;
+    const double *gx, *gy, *gz;
+    const double *box;
+    float *kR;
+    float2 *kRb;
+    int *kflag;
+    int *next;
+    int *remaining;
+    int *status;
+    int *nbr;
+    float *nd2;
+    double *h2;
+    float *h, *E, *rho, *P, *cs;
+    int *g64;
+    float gamma;
+};
+
+struct KnnSmem {
+    float4 cand[KN_CAP];
+    int stack[KN_STACK];
+    int hist[KN_WARPS][64];
+    float bkt[KN_WARPS][KN_BKT];
+    int bn[KN_WARPS];
+    int un[KN_WARPS];
+    int ui[KN_WARPS][KN_U];
+    double uD[KN_WARPS][KN_U];
+    int nc, sp, g, under, over, bmin[3], bmax[3];
+    unsigned amax;
+};
+
+__device__ __forceinline__ float d2f(float4 c, float xi, float yi, float zi)
+{
+    float dx = c.x - xi, dy = c.y - yi, dz = c.z - zi;
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
+}
+
+__device__ __forceinline__ double exact_d2(const double *x, const double *y, const double *z, int i, int j)
+{
+    double dx = __dsub_rn(x[i], x[j]), dy = __dsub_rn(y[i], y[j]), dz = __dsub_rn(z[i], z[j]);
+    double a = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    return __dadd_rn(a, __dmul_rn(dz, dz));
+}
+
+__global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    KnnSmem &S = *reinterpret_cast<KnnSmem *>(smem_raw);
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const float unit = (float)p.box[4];
+    const int ngroups = *p.nsnap;
+    const unsigned ltmask = (1u << lane) - 1u;
+    for (;;) {
+        __syncthreads();  // every thread has read the previous S.g
+        if (tid == 0) S.g = atomicAdd(p.next, 1);
+        __syncthreads();
+        const int gi = S.g;
+        if (gi >= ngroups) break;
+        if (p.kflag[gi] == 0) continue;  // uniform
+        const int2 gitem = p.item[gi];
+        const int4 ga = make_int4(gitem.x, gitem.y, 0, 0);
+        const float R = p.kR[gi];
+        if (tid < 3) { S.bmin[tid] = 0x7fffffff; S.bmax[tid] = -1; }
+        if (tid == 0) { S.nc = 0; S.sp = 1; S.stack[0] = 0; S.under = 0; S.over = 0; S.amax = 0u; }
+        __syncthreads();
+        for (int i = ga.x + tid; i < ga.x + ga.y; i += KN_THREADS) {
+            atomicMin(&S.bmin[0], p.gcx[i]); atomicMax(&S.bmax[0], p.gcx[i]);
+            atomicMin(&S.bmin[1], p.gcy[i]); atomicMax(&S.bmax[1], p.gcy[i]);
+            atomicMin(&S.bmin[2], p.gcz[i]); atomicMax(&S.bmax[2], p.gcz[i]);
+        }
+        __syncthreads();
+        const int b0[3] = {S.bmin[0], S.bmin[1], S.bmin[2]}, b1[3] = {S.bmax[0], S.bmax[1], S.bmax[2]};
+        const int gref[3] = {(b0[0] + b1[0]) >> 1, (b0[1] + b1[1]) >> 1, (b0[2] + b1[2]) >> 1};
+        // group box in offset coordinates: [lo_k, hi_k)
+        float blo[3], bhi[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            blo[a] = (float)(b0[a] - gref[a]) * unit;
+            bhi[a] = (float)(b1[a] + 1 - gref[a]) * unit;
+        }
+        const double Rg = (double)R / (double)unit;  // radius in grid units
+        const double Rg2m = Rg * Rg * (1.0 + 1e-5) + 4.0;
+        const float R2stage = R * R * (1.f + 1e-4f) + 4.f * unit * unit;
+        // gather candidates within R of the group box
+        for (;;) {
+            __syncthreads();
+            int sp = S.sp;
+            if (sp == 0) break;
+            int k = min(KN_THREADS, sp);
+            int room = (KN_STACK - sp) / 7;
+            k = min(k, max(room, 1));
+            int node = tid < k ? S.stack[sp - k + tid] : -1;
+            __syncthreads();
+            if (tid == 0) S.sp = sp - k;
+            __syncthreads();
+            if (node >= 0) {
+                int4 a = p.na[node];
+                int4 C = p.nb[node];
+                int lev = a.w & 255, nch = a.w >> 8;
+                long long s = 1ll << (GNB_MAXLEV - lev);
+                int cc[3] = {C.x, C.y, C.z};
+                double gap2 = 0.0;
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    long long gp = 0;
+                    if ((long long)cc[q] > (long long)b1[q] + 1) gp = cc[q] - ((long long)b1[q] + 1);
+                    else if ((long long)b0[q] > cc[q] + s) gp = b0[q] - (cc[q] + s);
+                    gap2 += (double)gp * (double)gp;
+                }
+                if (gap2 <= Rg2m) {
+                    if (nch > 0) {
+                        int b = atomicAdd(&S.sp, nch);
+                        if (b + nch <= KN_STACK) {
+                            for (int q = 0; q < nch; q++) S.stack[b + q] = a.z + q;
+                        } else {
+                            atomicSub(&S.sp, nch);
+                            S.over = 1;
+                        }
+                    } else {
+                        for (int j = a.x; j < a.x + a.y; j++) {
+                            float ox = grid_off(p.gcx[j], gref[0], p.grx[j], unit);
+                            float oy = grid_off(p.gcy[j], gref[1], p.gry[j], unit);
+                            float oz = grid_off(p.gcz[j], gref[2], p.grz[j], unit);
+                            float gx = fmaxf(0.f, fmaxf(blo[0] - ox, ox - bhi[0]));
+                            float gy = fmaxf(0.f, fmaxf(blo[1] - oy, oy - bhi[1]));
+                            float gz = fmaxf(0.f, fmaxf(blo[2] - oz, oz - bhi[2]));
+                            if (gx * gx + gy * gy + gz * gz <= R2stage) {
+                                int slot = atomicAdd(&S.nc, 1);
+                                if (slot < KN_CAP) {
+                                    S.cand[slot] = make_float4(ox, oy, oz, __int_as_float(j));
+                                    float a2 = ox * ox + oy * oy + oz * oz;
+                                    atomicMax(&S.amax, __float_as_uint(a2));
+                                } else {
+                                    S.over = 1;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const int nc = min(S.nc, KN_CAP);
+        if (!S.over) {
+            // group particles also bound the offsets
+            for (int i = ga.x + tid; i < ga.x + ga.y; i += KN_THREADS) {
+                float ox = grid_off(p.gcx[i], gref[0], p.grx[i], unit);
+                float oy = grid_off(p.gcy[i], gref[1], p.gry[i], unit);
+                float oz = grid_off(p.gcz[i], gref[2], p.grz[i], unit);
+                atomicMax(&S.amax, __float_as_uint(ox * ox + oy * oy + oz * oz));
+            }
+            __syncthreads();
+            const float A2 = __uint_as_float(S.amax) + 4.f * unit * unit;
+            const float E = A2 * 7.62939453125e-06f;  // 2^-17 A^2
+            const float R2 = R * R;
+            const float thrR = R2 - E;
+            for (int i = ga.x + w; i < ga.x + ga.y; i += KN_WARPS) {
+                const float xi = grid_off(p.gcx[i], gref[0], p.grx[i], unit);
+                const float yi = grid_off(p.gcy[i], gref[1], p.gry[i], unit);
+                const float zi = grid_off(p.gcz[i], gref[2], p.grz[i], unit);
+                __syncwarp();  // the previous particle's scratch is no longer read
+                if (lane == 0) { S.bn[w] = 0; S.un[w] = 0; }
+                int cnt = 0;
+                for (int c = lane; c < nc; c += 32) cnt += d2f(S.cand[c], xi, yi, zi) <= thrR;
+                cnt = warp_sum(cnt);
+                if (cnt < NGB) {
+                    if (lane == 0) S.under = 1;
+                    continue;
+                }
+                // bucket holding the 64th smallest; shrink this particle's
+                // radius to that bucket while the bucket is too full to rank
+                float R2i = R2, inv64 = 64.f / R2;
+                int bstar = -1, kth = 0;
+                bool ok = false;
+                for (int it = 0; it < 16; it++) {
+                    __syncwarp();
+                    S.hist[w][lane] = 0;
+                    S.hist[w][lane + 32] = 0;
+                    __syncwarp();
+                    inv64 = 64.f / R2i;
+                    for (int c = lane; c < nc; c += 32) {
+                        float d = d2f(S.cand[c], xi, yi, zi);
+                        if (d <= R2i) atomicAdd(&S.hist[w][min(63, (int)(d * inv64))], 1);
+                    }
+                    __syncwarp();
+                    int h0 = S.hist[w][2 * lane], h1 = S.hist[w][2 * lane + 1];
+                    int sum = h0 + h1, inc = sum;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        int y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    int exc = inc - sum;
+                    int mybin = -1, mybefore = 0;
+                    if (exc < NGB && NGB <= exc + h0) { mybin = 2 * lane; mybefore = exc; }
+                    else if (exc + h0 < NGB && NGB <= inc) { mybin = 2 * lane + 1; mybefore = exc + h0; }
+                    unsigned bal = __ballot_sync(0xffffffffu, mybin >= 0);
+                    if (bal == 0u) break;
+                    int src = __ffs(bal) - 1;
+                    bstar = __shfl_sync(0xffffffffu, mybin, src);
+                    kth = NGB - __shfl_sync(0xffffffffu, mybefore, src);  // 1-based rank in bucket
+                    if (S.hist[w][bstar] <= KN_BKT) { ok = true; break; }
+                    R2i = R2i * (float)(bstar + 1) * (1.f / 64.f) * (1.f + 1e-6f);
+                }
+                if (!ok) {
+                    if (lane == 0) atomicOr(p.status, ST_KNN_OVERFLOW);
+                    continue;
+                }
+                for (int c = lane; c < nc; c += 32) {
+                    float d = d2f(S.cand[c], xi, yi, zi);
+                    if (d <= R2i && min(63, (int)(d * inv64)) == bstar) {
+                        int slot = atomicAdd(&S.bn[w], 1);
+                        if (slot < KN_BKT) S.bkt[w][slot] = d;
+                    }
+                }
+                __syncwarp();
+                const int nb = S.bn[w];
+                if (nb > KN_BKT) {
+                    if (lane == 0) atomicOr(p.status, ST_KNN_OVERFLOW);
+                    continue;
+                }
+                // t = kth smallest value in the bucket (ties by position)
+                float t = 0.f;
+                bool found = false;
+                for (int e = lane; e < nb; e += 32) {
+                    float de = S.bkt[w][e];
+                    int r = 0;
+                    for (int f = 0; f < nb; f++) {
+                        float df = S.bkt[w][f];
+                        r += (df < de) || (df == de && f < e);
+                    }
+                    if (r == kth - 1) { t = de; found = true; }
+                }
+                unsigned fb = __ballot_sync(0xffffffffu, found);
+                if (fb == 0u) {  // cannot happen when the histogram is consistent
+                    if (lane == 0) atomicOr(p.status, ST_KNN_OVERFLOW);
+                    continue;
+                }
+                t = __shfl_sync(0xffffffffu, t, __ffs(fb) - 1);
+                const float lo = t - 2.f * E, hi = t + 2.f * E;
+                // classify: sure members written directly, uncertain ones collected
+                int nS = 0;
+                int *outn = p.nbr + (size_t)i * NGB;
+                float *outd = p.nd2 + (size_t)i * NGB;
+                for (int c0 = 0; c0 < nc; c0 += 32) {
+                    int c = c0 + lane;
+                    float d = 3.0e38f;
+                    int j = -1;
+                    if (c < nc) {
+                        float4 cv = S.cand[c];
+                        d = d2f(cv, xi, yi, zi);
+                        j = __float_as_int(cv.w);
+                    }
+                    bool sure = d < lo;
+                    unsigned sb = __ballot_sync(0xffffffffu, sure);
+                    if (sure) {
+                        int pos = nS + __popc(sb & ltmask);
+                        if (pos < NGB) { outn[pos] = j; outd[pos] = d; }
+                    }
+                    nS += __popc(sb);
+                    if (!sure && d <= hi) {
+                        int slot = atomicAdd(&S.un[w], 1);
+                        if (slot < KN_U) S.ui[w][slot] = j;
+                    }
+                }
+                __syncwarp();
+                const int nu = S.un[w];
+                if (nu > KN_U || nS >= NGB) {
+                    if (lane == 0) atomicOr(p.status, ST_KNN_OVERFLOW);
+                    continue;
+                }
+                for (int e = lane; e < nu; e += 32) S.uD[w][e] = exact_d2(p.gx, p.gy, p.gz, i, S.ui[w][e]);
+                __syncwarp();
+                const int need = NGB - nS;
+                double hsq = 0.0;
+                int h64 = -1;
+                bool have = false;
+                for (int e = lane; e < nu; e += 32) {
+                    double De = S.uD[w][e];
+                    int je = S.ui[w][e];
+                    int ge = p.ggrank[je];
+                    int r = 0;
+                    for (int f = 0; f < nu; f++) {
+                        double Df = S.uD[w][f];
+                        int gf = p.ggrank[S.ui[w][f]];
+                        r += (Df < De) || (Df == De && gf < ge);
+                    }
+                    if (r < need) {
+                        outn[nS + r] = je;
+                        outd[nS + r] = (float)De;
+                    }
+                    if (r == need - 1) { hsq = De; h64 = ge; have = true; }
+                }
+                unsigned hb = __ballot_sync(0xffffffffu, have);
+                if (hb == 0u) {  // error bound violated: fewer uncertain entries than needed
+                    if (lane == 0) atomicOr(p.status, ST_KNN_OVERFLOW);
+                    continue;
+                }
+                int hs = __ffs(hb) - 1;
+                hsq = __shfl_sync(0xffffffffu, hsq, hs);
+                h64 = __shfl_sync(0xffffffffu, h64, hs);
+                __syncwarp();
+                // density and EOS over the 64 neighbours
+                const float hh = (float)sqrt(hsq);
+                const float hinv = 1.f / hh;
+                float rs = 0.f;
+                for (int e = lane; e < NGB; e += 32) {
+                    int j = outn[e];
+                    rs += p.gm[j] * kern_w(sqrtf(outd[e]), hinv);
+                }
+                rs = warp_sum(rs);
+                if (lane == 0) {
+                    float u = p.gu[i];
+                    float P = (p.gamma - 1.f) * rs * u;
+                    p.h2[i] = hsq;
+                    p.h[i] = hh;
+                    p.g64[i] = h64;
+                    p.E[i] = E;
+                    p.rho[i] = rs;
+                    p.P[i] = P;
+                    p.cs[i] = sqrtf(p.gamma * P / rs);
+                }
+            }
+        }
+        __syncthreads();
+        if (S.over && ga.y > 1) {
+            // the members need a radius whose candidates do not fit: hand
+            // each particle to its own work item
+            __syncthreads();
+            if (tid == 0) {
+                S.g = atomicAdd(p.nitems, ga.y);
+                p.kflag[gi] = 0;
+                atomicAdd(p.remaining, 1);
+            }
+            __syncthreads();
+            const int base = S.g;
+            for (int k = tid; k < ga.y; k += KN_THREADS) {
+                if (base + k < p.item_cap) {
+                    p.item[base + k] = make_int2(ga.x + k, 1);
+                    p.kR[base + k] = R;
+                    p.kRb[base + k] = make_float2(0.f, 0.f);
+                    p.kflag[base + k] = 1;
+                } else {
+                    atomicOr(p.status, ST_KNN_OVERFLOW);
+                }
+            }
+            continue;
+        }
+        if (tid == 0) {
+            float2 rb = p.kRb[gi];
+            int done = 1;
+            if (S.over) {
+                rb.y = R;
+                p.kR[gi] = rb.x > 0.f ? 0.5f * (R + rb.x) : 0.6f * R;
+                done = 0;
+            } else if (S.under) {
+                rb.x = R;
+                p.kR[gi] = rb.y > 0.f ? 0.5f * (R + rb.y) : 1.6f * R;
+                done = 0;
+            }
+            p.kRb[gi] = rb;
+            p.kflag[gi] = done ? 0 : 1;
+            if (!done) atomicAdd(p.remaining, 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- symmetric lists
+// Bit k of mut[i] is set when entry k of N_i is mutual (i in N_j too), using
+// (d^2, gas rank) <= (h_j^2, rank of j's n_ngb-th neighbour); FP32 decides
+// unless d lies within the error bound of h_j^2, then FP64 decides.
+__global__ void k_mutual(int ng, const int *__restrict__ nbr, const float *__restrict__ nd2,
+                         const float *__restrict__ E, const double *__restrict__ h2, const int *__restrict__ g64,
+                         const int *__restrict__ grank, const double *__restrict__ x, const double *__restrict__ y,
+                         const double *__restrict__ z, unsigned long long *__restrict__ mut, int *__restrict__ rcnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ng) return;
+    unsigned long long mask = 0ull;
+    float Ei = E[i];
+    int gi = grank[i];
+    for (int k = 0; k < NGB; k++) {
+        int j = nbr[(size_t)i * NGB + k];
+        if (j == i) { mask |= 1ull << k; continue; }
+        double d = (double)nd2[(size_t)i * NGB + k];
+        double hj = h2[j];
+        double e = 2.0 * (double)Ei;
+        bool m;
+        if (d + e < hj) m = true;
+        else if (d - e > hj) m = false;
+        else {
+            double D = exact_d2(x, y, z, i, j);
+            m = (D < hj) || (D == hj && gi <= g64[j]);
+        }
+        if (m) mask |= 1ull << k;
+        else atomicAdd(&rcnt[j], 1);
+    }
+    mut[i] = mask;
+}
+
+__global__ void k_rev_fill(int ng, const int *__restrict__ nbr, const unsigned long long *__restrict__ mut,
+                           const int *__restrict__ roff, int *__restrict__ rfill, int *__restrict__ rlist)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ng) return;
+    unsigned long long mask = mut[i];
+    for (int k = 0; k < NGB; k++) {
+        if (mask & (1ull << k)) continue;
+        int j = nbr[(size_t)i * NGB + k];
+        int s = atomicAdd(&rfill[j], 1);
+        rlist[roff[j] + s] = i;
+    }
+}
+
+// ---------------------------------------------------------------- force
+struct ForceParams {
+    int ng;
+    const int *nbr, *roff, *rcnt, *rlist;
+    const int *gcx, *gcy, *gcz;
+    const float *grx, *gry, *grz, *gm, *gvx, *gvy, *gvz, *h, *rho, *P, *cs;
+    const double *box;
+    float alpha;
+    float *ax, *ay, *az, *du;
+};
+
+__device__ __forceinline__ void pair_force(const ForceParams &p, int i, int j, float unit, int ci0, int ci1, int ci2,
+                                           float ri0, float ri1, float ri2, float vi0, float vi1, float vi2,
+                                           float hinv_i, float pi_, float rhoi, float csi, float &a0, float &a1,
+                                           float &a2, float &du)
+{
+    float dx = __fmaf_rn((float)(ci0 - p.gcx[j]), unit, ri0 - p.grx[j]);
+    float dy = __fmaf_rn((float)(ci1 - p.gcy[j]), unit, ri1 - p.gry[j]);
+    float dz = __fmaf_rn((float)(ci2 - p.gcz[j]), unit, ri2 - p.grz[j]);
+    float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
+    float r = sqrtf(r2);
+    float rinv = r > 0.f ? 1.f / r : 0.f;
+    float hj = p.h[j];
+    float dwi = kern_dw(r, hinv_i), dwj = kern_dw(r, 1.f / hj);
+    float rhoj = p.rho[j];
+    float pj_ = p.P[j] / (rhoj * rhoj);
+    float vx = vi0 - p.gvx[j], vy = vi1 - p.gvy[j], vz = vi2 - p.gvz[j];
+    float w = (vx * dx + vy * dy + vz * dz) * rinv;
+    float visc = 0.f;
+    if (w < 0.f) {
+        float vsig = csi + p.cs[j] - 3.f * w;
+        visc = -0.5f * p.alpha * vsig * w / (0.5f * (rhoi + rhoj));
+    }
+    float dwbar = 0.5f * (dwi + dwj);
+    float mj = p.gm[j];
+    float f = mj * (pi_ * dwi + pj_ * dwj + visc * dwbar) * rinv;
+    a0 -= f * dx;
+    a1 -= f * dy;
+    a2 -= f * dz;
+    du += mj * (pi_ * dwi + 0.5f * visc * dwbar) * w;
+}
+
+__global__ void k_force(ForceParams p)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.ng) return;
+    const float unit = (float)p.box[4];
+    int ci0 = p.gcx[i], ci1 = p.gcy[i], ci2 = p.gcz[i];
+    float ri0 = p.grx[i], ri1 = p.gry[i], ri2 = p.grz[i];
+    float vi0 = p.gvx[i], vi1 = p.gvy[i], vi2 = p.gvz[i];
+    float hinv = 1.f / p.h[i], rhoi = p.rho[i], csi = p.cs[i];
+    float pi_ = p.P[i] / (rhoi * rhoi);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, du = 0.f;
+    const int *nb = p.nbr + (size_t)i * NGB;
+    for (int k = 0; k < NGB; k++) {
+        int j = nb[k];
+        if (j == i) continue;
+        pair_force(p, i, j, unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1, a2, du);
+    }
+    int b = p.roff[i], e = b + p.rcnt[i];
+    for (int k = b; k < e; k++)
+        pair_force(p, i, p.rlist[k], unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1,
+                   a2, du);
+    p.ax[i] = a0;
+    p.ay[i] = a1;
+    p.az[i] = a2;
+    p.du[i] = du;
+}
+
+// hydro results back to particle slots
+__global__ void k_gas_scatter(int ng, const int *__restrict__ gslot, const float *__restrict__ hax,
+                              const float *__restrict__ hay, const float *__restrict__ haz,
+                              const float *__restrict__ hdu, float *__restrict__ ax, float *__restrict__ ay,
+                              float *__restrict__ az, float *__restrict__ dudt)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ng) return;
+    int s = gslot[k];
+    ax[s] += hax[k];
+    ay[s] += hay[k];
+    az[s] += haz[k];
+    dudt[s] = hdu[k];
+}
+
+__global__ void k_gas_scatter_density(int ng, const int *__restrict__ gslot, const float *__restrict__ grho,
+                                      const float *__restrict__ gP, const float *__restrict__ gcs,
+                                      const double *__restrict__ gh2, float *__restrict__ rho,
+                                      float *__restrict__ pres, float *__restrict__ cs, double *__restrict__ h2)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ng) return;
+    int s = gslot[k];
+    rho[s] = grho[k];
+    pres[s] = gP[k];
+    cs[s] = gcs[k];
+    h2[s] = gh2[k];
+}
+
+// ---------------------------------------------------------------- host
+static int g_knn_blocks = 0;
+
+int sph_density(gnb_ctx *c)
+{
+    int n = (int)c->n, ng = (int)c->n_gas;
+    if (ng == 0) return GNB_OK;
+    PArr &a = c->P[c->cur];
+    int nb = (n + 255) / 256, gb = (ng + 255) / 256;
+    // gas slots in Morton order
+    k_gas_flag<<<nb, 256, 0, c->s>>>(a.type, c->gas_flag, n);
+    GNB_TRY(device_scan(c, c->gas_flag, c->pscan, c->n_d, n, nullptr));
+    k_gas_compact<<<nb, 256, 0, c->s>>>(c->gas_flag, c->pscan, n, c->gslot);
+    GasGather gg;
+    gg.skey = c->skey; gg.p = a; gg.gslot = c->gslot; gg.gkey = c->gkey;
+    gg.gcx = c->gcx; gg.gcy = c->gcy; gg.gcz = c->gcz; gg.ggrank = c->ggrank;
+    gg.grx = c->grx; gg.gry = c->gry; gg.grz = c->grz; gg.gm = c->gm;
+    gg.gvx = c->gvx; gg.gvy = c->gvy; gg.gvz = c->gvz; gg.gu = c->gu; gg.gRprev = c->gRprev;
+    gg.gx = c->gx; gg.gy = c->gy; gg.gz = c->gz;
+    gg.ng = ng; gg.pred = c->use_pred ? 1 : 0; gg.have_h = c->have_h ? 1 : 0;
+    k_gas_gather<<<gb, 256, 0, c->s>>>(gg);
+    GNB_LAUNCH_CHECK(c, "gas gather");
+    // hydro tree and groups of <= 32 gas particles
+    GNB_TRY(build_tree(c, c->gt, c->gkey, ng, c->ngas_d, c->cfg.n_leaf, 32, c->gcx, c->gcy, c->gcz, c->grx,
+                       c->gry, c->grz, c->gm, c->gm, false));
+    // work_d: [0] next item, [1] items left unfinished, [2] live item count, [3] per-pass snapshot
+    k_knn_init<<<304, 256, 0, c->s>>>(c->gt, c->gRprev, c->have_h ? 1 : 0, c->box_d, c->kR,
+                                      c->kRb, c->kflag, c->kitem, c->work_d + 2);
+    GNB_LAUNCH_CHECK(c, "knn init");
+    KnnParams p;
+    p.na = c->gt.na; p.nb = c->gt.nb; p.item = c->kitem; p.nitems = c->work_d + 2; p.nsnap = c->work_d + 3;
+    p.item_cap = (int)(2 * c->gcap + 1);
+    p.gcx = c->gcx; p.gcy = c->gcy; p.gcz = c->gcz; p.ggrank = c->ggrank;
+    p.grx = c->grx; p.gry = c->gry; p.grz = c->grz; p.gm = c->gm; p.gu = c->gu;
+    p.gx = c->gx; p.gy = c->gy; p.gz = c->gz; p.box = c->box_d;
+    p.kR = c->kR; p.kRb = c->kRb; p.kflag = c->kflag;
+    p.next = c->work_d; p.remaining = c->work_d + 1; p.status = c->status_d;
+    p.nbr = c->nbr; p.nd2 = c->nd2; p.h2 = c->gh2; p.h = c->gh; p.E = c->gE; p.rho = c->grho; p.P = c->gP;
+    p.cs = c->gcs; p.g64 = c->g64; p.gamma = (float)c->cfg.gamma;
+    size_t smem = sizeof(KnnSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(c, e, "knn smem attribute");
+    if (g_knn_blocks == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_knn, KN_THREADS, smem);
+        g_knn_blocks = sms * (per > 0 ? per : 1);
+    }
+    int passes = 0;
+    const int rounds = 12;
+    for (int round = 0; round < rounds; round++) {
+        // three device passes per host check; converged items are skipped
+        for (int q = 0; q < 3; q++) {
+            cudaMemsetAsync(c->work_d, 0, 2 * sizeof(int), c->s);
+            cudaMemcpyAsync(c->work_d + 3, c->work_d + 2, sizeof(int), cudaMemcpyDeviceToDevice, c->s);
+            k_knn<<<g_knn_blocks, KN_THREADS, smem, c->s>>>(p);
+            passes++;
+        }
+        GNB_LAUNCH_CHECK(c, "knn");
+        cudaMemcpyAsync(c->pinned_i, c->work_d + 1, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+        cudaMemcpyAsync(c->pinned_i + 1, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+        GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "knn sync"));
+        if (c->pinned_i[1] & ST_KNN_OVERFLOW) return fail(c, GNB_ECAPACITY, "kNN selection buffer overflow");
+        if (c->pinned_i[0] == 0) break;
+        if (round == rounds - 1) return fail(c, GNB_ECAPACITY, "kNN search radius did not converge");
+    }
+    c->stats[GNB_S_KNN_PASSES] = passes;
+    c->stats[GNB_S_GAS_NODES] = c->gt.nnodes;
+    k_gas_scatter_density<<<gb, 256, 0, c->s>>>(ng, c->gslot, c->grho, c->gP, c->gcs, c->gh2, c->rho, c->pres,
+                                                c->cs, a.h2);
+    GNB_LAUNCH_CHECK(c, "density scatter");
+    c->have_h = true;
+    return GNB_OK;
+}
+
+int sph_force(gnb_ctx *c)
+{
+    int ng = (int)c->n_gas;
+    if (ng == 0) return GNB_OK;
+    int gb = (ng + 255) / 256;
+    cudaMemsetAsync(c->rcnt, 0, sizeof(int) * ng, c->s);
+    k_mutual<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->nd2, c->gE, c->gh2, c->g64, c->ggrank, c->gx, c->gy, c->gz,
+                                   c->mut, c->rcnt);
+    GNB_TRY(device_scan(c, c->rcnt, c->roff, c->ngas_d, ng, c->rtot_d));
+    cudaMemsetAsync(c->rfill, 0, sizeof(int) * ng, c->s);
+    k_rev_fill<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->mut, c->roff, c->rfill, c->rlist);
+    GNB_LAUNCH_CHECK(c, "symmetric lists");
+    ForceParams p;
+    p.ng = ng; p.nbr = c->nbr; p.roff = c->roff; p.rcnt = c->rcnt; p.rlist = c->rlist;
+    p.gcx = c->gcx; p.gcy = c->gcy; p.gcz = c->gcz; p.grx = c->grx; p.gry = c->gry; p.grz = c->grz;
+    p.gm = c->gm; p.gvx = c->gvx; p.gvy = c->gvy; p.gvz = c->gvz; p.h = c->gh; p.rho = c->grho; p.P = c->gP;
+    p.cs = c->gcs; p.box = c->box_d; p.alpha = (float)c->cfg.alpha_visc;
+    p.ax = c->hax; p.ay = c->hay; p.az = c->haz; p.du = c->hdu;
+    k_force<<<(ng + 127) / 128, 128, 0, c->s>>>(p);
+    k_gas_scatter<<<gb, 256, 0, c->s>>>(ng, c->gslot, c->hax, c->hay, c->haz, c->hdu, c->ax, c->ay, c->az,
+                                        c->dudt);
+    GNB_LAUNCH_CHECK(c, "sph force");
+    return GNB_OK;
+}
+
+}  // namespace gnb

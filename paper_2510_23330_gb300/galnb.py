@@ -1,0 +1,277 @@
+"""Thin ctypes binding of the C ABI in ``include/galnb.h``.
+
+Every ``gnb_*`` function here has the C function's name and arguments and only
+marshals them; all work runs in ``libgalnb.so``.  There is no fallback: if the
+library cannot be built or loaded, ``lib()`` raises.  ``Context`` is a small
+convenience wrapper that turns numpy or torch arrays into the pointers the C
+calls take and raises ``GalnbError`` on a non-zero return code.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GNB_OK = 0
+GNB_EINVAL = -1
+GNB_ENOMEM = -2
+GNB_ECUDA = -3
+GNB_ESTATE = -4
+GNB_ECAPACITY = -5
+GNB_ETIMEOUT = -6
+GNB_EMISMATCH = -7
+
+GNB_STAR = 0
+GNB_GAS = 1
+GNB_GRAV_DIRECT = 0
+GNB_GRAV_TREE = 1
+
+FIELDS = ["X", "Y", "Z", "VX", "VY", "VZ", "AX", "AY", "AZ", "POT", "U", "DUDT", "RHO", "PRES", "CS", "H2",
+          "KEY", "ORDER", "NBR", "NODES", "GROUPS", "ID", "AGRAV_X", "AGRAV_Y", "AGRAV_Z"]
+F = {name: i for i, name in enumerate(FIELDS)}
+FIELD_DTYPE = {"X": np.float64, "Y": np.float64, "Z": np.float64, "H2": np.float64, "KEY": np.uint64,
+               "ORDER": np.int64, "NBR": np.int64, "NODES": np.int64, "GROUPS": np.int64, "ID": np.int64}
+STATS = ["N", "NGAS", "NODES", "GROUPS", "NPP", "NPC", "GAS_NODES", "KNN_PASSES", "NSYM", "MAXLEVEL"]
+
+
+class gnb_config(C.Structure):
+    _fields_ = [("G", C.c_double), ("theta", C.c_double), ("gamma", C.c_double), ("alpha_visc", C.c_double),
+                ("n_leaf", C.c_int), ("n_group", C.c_int), ("n_ngb", C.c_int), ("multipole", C.c_int),
+                ("nfw_ms", C.c_double), ("nfw_rs", C.c_double), ("cuda_stream", C.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = C.c_void_p
+
+
+def lib():
+    """Load libgalnb.so, building it first if the sources changed."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _declare(L):
+    L.gnb_config_default.argtypes = [C.POINTER(gnb_config)]
+    L.gnb_config_default.restype = None
+    L.gnb_create.argtypes = [C.POINTER(_vp), C.POINTER(gnb_config)]
+    L.gnb_destroy.argtypes = [_vp]
+    L.gnb_destroy.restype = None
+    L.gnb_set_particles.argtypes = [_vp, C.c_int64] + [_vp] * 11 + [C.c_int]
+    L.gnb_build_tree.argtypes = [_vp]
+    L.gnb_compute_gravity.argtypes = [_vp, C.c_int]
+    L.gnb_compute_sph_density.argtypes = [_vp]
+    L.gnb_compute_sph_force.argtypes = [_vp]
+    L.gnb_compute_forces.argtypes = [_vp, C.c_int]
+    L.gnb_step_kdk.argtypes = [_vp, C.c_double, C.c_int, C.c_int]
+    L.gnb_get.argtypes = [_vp, C.c_int, _vp, C.c_int64, C.c_int]
+    L.gnb_diagnostics.argtypes = [_vp, C.POINTER(C.c_double)]
+    L.gnb_stats.argtypes = [_vp, C.POINTER(C.c_int64)]
+    L.gnb_last_error.argtypes = [_vp]
+    L.gnb_last_error.restype = C.c_char_p
+    for name in ("gnb_create", "gnb_set_particles", "gnb_build_tree", "gnb_compute_gravity",
+                 "gnb_compute_sph_density", "gnb_compute_sph_force", "gnb_compute_forces", "gnb_step_kdk",
+                 "gnb_get", "gnb_diagnostics", "gnb_stats"):
+        getattr(L, name).restype = C.c_int
+
+
+# -------------------------------------------------------------- same-name calls
+def gnb_config_default(cfg):
+    lib().gnb_config_default(C.byref(cfg))
+
+
+def gnb_create(out, cfg):
+    return lib().gnb_create(out, C.byref(cfg))
+
+
+def gnb_destroy(ctx):
+    lib().gnb_destroy(ctx)
+
+
+def gnb_set_particles(ctx, n, id, type, x, y, z, vx, vy, vz, m, eps, u, on_device):
+    return lib().gnb_set_particles(ctx, n, id, type, x, y, z, vx, vy, vz, m, eps, u, on_device)
+
+
+def gnb_build_tree(ctx):
+    return lib().gnb_build_tree(ctx)
+
+
+def gnb_compute_gravity(ctx, mode):
+    return lib().gnb_compute_gravity(ctx, mode)
+
+
+def gnb_compute_sph_density(ctx):
+    return lib().gnb_compute_sph_density(ctx)
+
+
+def gnb_compute_sph_force(ctx):
+    return lib().gnb_compute_sph_force(ctx)
+
+
+def gnb_compute_forces(ctx, mode):
+    return lib().gnb_compute_forces(ctx, mode)
+
+
+def gnb_step_kdk(ctx, dt, nsteps, mode):
+    return lib().gnb_step_kdk(ctx, dt, nsteps, mode)
+
+
+def gnb_get(ctx, field, dst, cap, on_device):
+    return lib().gnb_get(ctx, field, dst, cap, on_device)
+
+
+def gnb_diagnostics(ctx, out):
+    return lib().gnb_diagnostics(ctx, out)
+
+
+def gnb_stats(ctx, out):
+    return lib().gnb_stats(ctx, out)
+
+
+def gnb_last_error(ctx):
+    r = lib().gnb_last_error(ctx)
+    return r.decode() if r else ""
+
+
+# -------------------------------------------------------------- convenience wrapper
+class GalnbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"galnb error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(type(a))
+
+
+class Context:
+    """Owner of one gnb_ctx.  ``stream`` is a cudaStream_t as an int (e.g.
+    ``torch.cuda.current_stream().cuda_stream``) or None."""
+
+    _DT = {"id": np.int64, "type": np.uint8, "x": np.float64, "y": np.float64, "z": np.float64,
+           "vx": np.float32, "vy": np.float32, "vz": np.float32, "m": np.float32, "eps": np.float32,
+           "u": np.float32}
+
+    def __init__(self, stream=None, **params):
+        cfg = gnb_config()
+        gnb_config_default(cfg)
+        for k, v in params.items():
+            if not hasattr(cfg, k):
+                raise KeyError(k)
+            setattr(cfg, k, v)
+        cfg.cuda_stream = stream
+        self.cfg = cfg
+        h = _vp()
+        rc = gnb_create(C.byref(h), cfg)
+        if rc != GNB_OK:
+            raise GalnbError(rc, "gnb_create failed")
+        self.h = h
+        self.n = 0
+        self.n_gas = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            gnb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc):
+        if rc != GNB_OK:
+            raise GalnbError(rc, gnb_last_error(self.h))
+
+    def set_particles(self, p: dict):
+        keys = ("id", "type", "x", "y", "z", "vx", "vy", "vz", "m", "eps", "u")
+        arrs = []
+        for k in keys:
+            a = p[k]
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=self._DT[k])
+            arrs.append(a)
+        ptrs = [_ptr(a) for a in arrs]
+        on_dev = {d for _, d in ptrs}
+        if len(on_dev) != 1:
+            raise ValueError("all arrays must be on the same side (host or device)")
+        n = int(arrs[2].shape[0])
+        self._keep = arrs
+        self._chk(gnb_set_particles(self.h, n, *[q for q, _ in ptrs], on_dev.pop()))
+        self.n = n
+        self.n_gas = int(self.stats()["NGAS"])
+
+    def build_tree(self):
+        self._chk(gnb_build_tree(self.h))
+
+    def compute_gravity(self, mode=GNB_GRAV_TREE):
+        self._chk(gnb_compute_gravity(self.h, mode))
+
+    def compute_sph_density(self):
+        self._chk(gnb_compute_sph_density(self.h))
+
+    def compute_sph_force(self):
+        self._chk(gnb_compute_sph_force(self.h))
+
+    def compute_forces(self, mode=GNB_GRAV_TREE):
+        self._chk(gnb_compute_forces(self.h, mode))
+
+    def step_kdk(self, dt, nsteps=1, mode=GNB_GRAV_TREE):
+        self._chk(gnb_step_kdk(self.h, float(dt), int(nsteps), mode))
+
+    def count(self, field):
+        st = self.stats()
+        if field == "NBR":
+            return self.n_gas * 64
+        if field == "NODES":
+            return 4 * st["NODES"]
+        if field == "GROUPS":
+            return st["GROUPS"]
+        return self.n
+
+    def get(self, field, out=None):
+        """Field in the caller's particle order as numpy (or into ``out``,
+        a host array or a device tensor)."""
+        fid = F[field]
+        if out is None:
+            out = np.empty(self.count(field), dtype=FIELD_DTYPE.get(field, np.float32))
+        ptr, dev = _ptr(out)
+        cap = out.numel() if hasattr(out, "numel") else out.size
+        self._chk(gnb_get(self.h, fid, ptr, cap, dev))
+        if field == "NBR" and isinstance(out, np.ndarray):
+            return out.reshape(self.n_gas, 64)
+        if field == "NODES" and isinstance(out, np.ndarray):
+            return out.reshape(-1, 4)
+        return out
+
+    def diagnostics(self):
+        out = (C.c_double * 10)()
+        self._chk(gnb_diagnostics(self.h, out))
+        return np.array(out[:])
+
+    def stats(self):
+        out = (C.c_int64 * len(STATS))()
+        self._chk(gnb_stats(self.h, out))
+        return dict(zip(STATS, out[:]))
