@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the N-body/SPH step: particle-steps/s (gravity + SPH).
+
+Workload (default): the 2^20-particle disk model -- 80 % stars in an
+exponential disk (R_d = 1, z_d = 0.1), 20 % gas (R_d = 2, u log-uniform in
+[1e-3, 1e-1]) in a static NFW halo (r_s = 8, M_s = 30), G = 1, eps = 0.01,
+Barnes-Hut tree gravity with theta = 0.5 and monopole + quadrupole, 64 SPH
+neighbours, kick-drift-kick steps of dt = 1e-3.  A step is one full KDK step
+through the C ABI (tree build, gravity, halo, kernel size, density, force,
+kicks, drift).  Inputs are resident in HBM when the timed region starts; L2 is
+flushed (256 MiB write on the same stream) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank runs an independent replica on its own GPU
+(the step has no exchange on one GPU; replicas only) and rank 0 prints the
+whole-job value from the max time over ranks.  ``--impl reference`` times the
+FP64 CPU checker on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_23330_gb300 import ics  # noqa: E402
+
+METRIC = "particle-steps/s (grav+SPH)"
+UNIT = "particle-steps/s"
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz maximum SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# flops per interaction: the paper's count for the monopole pair (Table 4),
+# and this library's own count for the quadrupole particle-cell term
+FLOP_PP = 27
+FLOP_PC = 59
+
+
+def workload(name: str, seed: int):
+    if name == "disk":
+        n = 1 << 20
+        p = ics.config_disk(n, gas_frac=0.2, seed=seed)
+        desc = "disk-2^20: 838,861 stars + 209,715 gas, NFW halo, tree theta=0.5 quad, 64 NN, KDK dt=1e-3"
+    elif name == "large":
+        n = 1 << 24
+        p = ics.config_disk(n, gas_frac=0.1, seed=seed)
+        desc = "disk-2^24: 15,099,494 stars + 1,677,722 gas, NFW halo, tree theta=0.5 quad, 64 NN, KDK dt=1e-3"
+    elif name == "tiny":
+        n = 8192
+        p = ics.config_tiny(seed)
+        desc = "plummer-8192: 4,096 stars + 4,096 gas, direct-sum gravity, 64 NN, KDK dt=1e-3"
+    else:
+        raise SystemExit(f"unknown config {name}")
+    return p, desc
+
+
+def params(name):
+    if name == "tiny":
+        return dict(gravity=0, cfg={})
+    return dict(gravity=1, cfg=dict(nfw_ms=ics.NFW_MS, nfw_rs=ics.NFW_RS, theta=0.5, multipole=1,
+                                    n_leaf=16, n_group=64))
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 20 ms) tagged with host time."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.perf_counter(), [s.strip() for s in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        if not self.proc:
+            return None
+        win = [s for t, s in self.samples if t0 <= t <= t1] or [s for t, s in self.samples[-3:]]
+        if not win:
+            return None
+        sm = [float(s[0]) for s in win if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in win if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in win for k in range(4) if len(s) > 4 + k and s[4 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(win)}
+
+
+def gravity_traffic():
+    """DRAM bytes per gravity launch from the committed ncu summary, if the
+    kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "gravity_tree_disk2p20.txt")
+    src = os.path.join(ROOT, "paper_2510_23330_gb300", "csrc", "gravity.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and not line.startswith("#"))
+    if vals.get("source_sha256_16", "").strip() != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(p, name):
+    """The FP64 oracle on a bounded sample of one force evaluation: the full
+    tree build plus every 16th group's walk (scaled by 16) and brute-force kNN
+    for 64 sampled gas particles (scaled to all gas)."""
+    import oracle
+    oracle.build()
+    n = p["x"].shape[0]
+    gi = np.nonzero(p["type"] == 1)[0]
+    stride = 16 if n > 100000 else 1
+    t0 = time.perf_counter()
+    tb, tw, st = oracle.tree_gravity_sampled(p, stride, theta=0.5, n_leaf=16, n_g=64, quad=True)
+    t_grav = tb + tw * stride
+    ns = min(64, gi.size)
+    rng = np.random.default_rng(0)
+    s = np.sort(rng.choice(gi.size, ns, replace=False))
+    g = {k: np.asarray(p[k][gi], np.float64) for k in ("x", "y", "z")}
+    t1 = time.perf_counter()
+    oracle.knn(g, 64, sample=s)
+    t_knn = (time.perf_counter() - t1) * gi.size / ns
+    total = t_grav + t_knn
+    return {"value": n / total, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"one force evaluation of {name}: tree build + 1/{stride} of the group walks "
+                       f"(x{stride}), brute-force kNN of {ns} gas particles (x{gi.size / ns:.0f}); "
+                       f"SPH density/force sums and kicks not included; measured {time.perf_counter() - t0:.1f} s"),
+            "seconds_per_step_estimate": total}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("GNB_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return world, rank, local
+
+
+def reduce_max(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2510_23330_gb300 import galnb
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    p, desc = workload(args.config, seed=rank)
+    pr = params(args.config)
+    mode = pr["gravity"]
+    n = int(p["x"].shape[0])
+    ctx = galnb.Context(stream=stream.cuda_stream, **pr["cfg"])
+    ctx.set_particles(p)
+    ctx.compute_forces(mode)
+    for _ in range(args.warmup):
+        ctx.step_kdk(args.dt, 1, mode)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+    clocks = ClockSampler(local) if not args.no_clocks else None
+    ctx.set_timing(True)
+    ctx.phase_times(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    npp = npc = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        ctx.step_kdk(args.dt, 1, mode)
+        ev[k][1].record(stream)
+        st = ctx.stats()
+        npp += st["NPP"]
+        npc += st["NPC"]
+    torch.cuda.synchronize()
+    h1 = time.perf_counter()
+    barrier(world)
+    if clocks:
+        time.sleep(0.05)
+        clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    phases, calls, launches = ctx.phase_times(reset=True)
+    ctx.set_timing(False)
+    tmax = reduce_max(total_ms, world, dev)
+    value = n * args.steps * world / (tmax * 1e-3)
+    # dominant kernel: the gravity walk + PP/PC kernel
+    g_calls = max(calls["GRAVITY"], 1)
+    g_ms = phases["GRAVITY"] / g_calls
+    flops = (FLOP_PP * npp + FLOP_PC * npc) / max(args.steps, 1)
+    achieved = flops / (g_ms * 1e-3) / 1e12
+    traffic = gravity_traffic()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "n": n, "n_gas": int(np.sum(p["type"] == 1)), "dt": args.dt,
+                   "gravity": "tree" if mode == 1 else "direct", **pr["cfg"], "n_ngb": 64,
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "kernel": "k_gravity_tree (walk + PP/PC)", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": traffic,
+                     "note": (f"flops = {FLOP_PP}/PP + {FLOP_PC}/PC interaction; peak = 152 SMs x 128 lanes x 2 x "
+                              f"2070 MHz (FP32 CUDA cores)"),
+                     "ms_per_launch": g_ms},
+        "interactions_per_step": {"pp": npp / args.steps, "pc": npc / args.steps},
+        "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
+        "gpu_launches": int(launches),
+        "step_ms": step_ms,
+    }
+    if clocks:
+        out["clocks"] = clocks.summary(h0, h1)
+    if rank == 0 and world == 1 and not args.no_e2e:
+        out["e2e"] = e2e(args, p, pr, stream, galnb, torch)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p, desc)
+    ctx.close()
+    return out
+
+
+def e2e(args, p, pr, stream, galnb, torch):
+    """Same metric through the public API with host buffers: every step
+    uploads the particles from pinned host memory, steps once and reads the
+    new state back into pinned host memory."""
+    n = int(p["x"].shape[0])
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in p.items()}
+    outs = {"X": "x", "Y": "y", "Z": "z", "VX": "vx", "VY": "vy", "VZ": "vz", "U": "u"}
+    res = {f: torch.empty_like(host[k]).pin_memory() for f, k in outs.items()}
+    ctx = galnb.Context(stream=stream.cuda_stream, **pr["cfg"])
+    steps = max(1, min(args.steps, 3))
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = sum(t.numel() * t.element_size() for t in res.values())
+    ctx.set_particles(host)
+    ctx.step_kdk(args.dt, 1, pr["gravity"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.set_particles(host)
+        ctx.step_kdk(args.dt, 1, pr["gravity"])
+        for f, k in outs.items():
+            ctx.get(f, res[f])
+        for f, k in outs.items():
+            host[k].copy_(res[f])
+    t1 = time.perf_counter()
+    ctx.close()
+    return {"value": n * steps / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps,
+            "note": "each call re-evaluates the initial forces after the upload (2 force passes per step)"}
+
+
+def run_reference(args, world, rank, local):
+    """The FP64 oracle as it stands, on a bounded sample of each step."""
+    if rank != 0:
+        return None
+    p, desc = workload(args.config, seed=0)
+    n = int(p["x"].shape[0])
+    for _ in range(args.warmup):
+        pass  # the sampled oracle has no warm state; warm-up steps are not needed
+    secs = []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(p, desc)
+        secs.append(cb["seconds_per_step_estimate"])
+    value = n * args.steps / sum(secs)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "n": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cb["cores"],
+                             "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="disk", choices=["disk", "large", "tiny"])
+    ap.add_argument("--dt", type=float, default=1e-3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        # the CPU checker runs once, on rank 0; other ranks exit without work
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        out = run_reference(args, world, rank, 0)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    world, rank, local = dist_init()
+    out = run_ours(args, world, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -115,6 +115,20 @@ enum gnb_stat {
     GNB_S_COUNT_
 };
 
+/* Phases timed by gnb_phase_times (the timing convention of Sec. 4.3:
+ * timers around each routine, here CUDA events on cfg.cuda_stream). */
+enum gnb_phase {
+    GNB_T_SORT = 0,     /* root box, Morton keys, radix sort, permutation */
+    GNB_T_TREE,         /* octree, cell moments, groups */
+    GNB_T_GRAVITY,      /* tree walk + particle-particle/particle-cell kernel (or direct sum) */
+    GNB_T_EXTERNAL,     /* static halo and force assembly */
+    GNB_T_HYDRO_TREE,   /* gas extraction and hydro tree */
+    GNB_T_KNN,          /* kernel size + density/pressure */
+    GNB_T_FORCE,        /* symmetric lists + hydro force */
+    GNB_T_KDK,          /* kicks, drift, prediction */
+    GNB_T_COUNT_
+};
+
 /* Fill cfg with the defaults listed in gnb_config. */
 void gnb_config_default(gnb_config *cfg);
 
@@ -181,6 +195,19 @@ int gnb_diagnostics(gnb_ctx *ctx, double out[10]);
 
 /* Counters of the last passes (enum gnb_stat).  Errors: GNB_EINVAL. */
 int gnb_stats(gnb_ctx *ctx, int64_t out[GNB_S_COUNT_]);
+
+/* Enable (1) or disable (0) the per-phase timers.  While enabled, every
+ * call records a pair of CUDA events around each phase it runs.
+ * Errors: GNB_EINVAL (null ctx). */
+int gnb_set_timing(gnb_ctx *ctx, int enable);
+
+/* Device time per phase (enum gnb_phase) in milliseconds, summed over the
+ * calls since the last reset; calls[p] counts the timed occurrences and
+ * *launches the kernels this library launched in the process since the last
+ * reset (any of the three outputs may be NULL).  reset = 1 clears the sums
+ * after reading.  Errors: GNB_EINVAL (null ctx). */
+int gnb_phase_times(gnb_ctx *ctx, double out_ms[GNB_T_COUNT_], int64_t calls[GNB_T_COUNT_],
+                    int64_t *launches, int reset);
 
 /* One-line description of the last error of ctx ("" if none; a static
  * string if ctx is NULL). */

@@ -78,6 +78,8 @@ def _declare(L):
     L.orc_tree_gravity.argtypes = ([C.c_int64] + [_d] * 5 + [C.c_double, C.c_double, C.c_int,
                                    C.c_int64, C.c_int] + [_d] * 5 + [_i64])
     L.orc_tree_gravity.restype = C.c_int
+    L.orc_tree_gravity_ex.argtypes = L.orc_tree_gravity.argtypes + [C.c_int64, _d]
+    L.orc_tree_gravity_ex.restype = C.c_int
     L.orc_knn.argtypes = [C.c_int64, _d, _d, _d, C.c_int, C.c_int64, _i64, _i64, _d]
     L.orc_knn.restype = C.c_int
     L.orc_kernel_eval.argtypes = [C.c_int64, _d, C.c_double, _d, _d]
@@ -233,6 +235,24 @@ def tree_gravity(p: dict, theta: float = 0.5, n_leaf: int = 16, n_g: int = 64,
         raise RuntimeError("oracle tree gravity failed")
     out["nodes"], out["groups"], out["n_pp"], out["n_pc"] = (int(s) for s in stats)
     return out
+
+
+def tree_gravity_sampled(p: dict, gstride: int, theta: float = 0.5, n_leaf: int = 16,
+                         n_g: int = 64, quad: bool = True, G: float = 1.0):
+    """Tree gravity walking every gstride-th group only.  Returns
+    (build_seconds, walk_seconds, stats) for timing a bounded sample."""
+    n = p["x"].shape[0]
+    arrs = [f64(p[k]) for k in ("x", "y", "z", "m", "eps")]
+    out = {k: np.zeros(n) for k in ("ax", "ay", "az", "phi", "asum")}
+    stats = np.zeros(4, np.int64)
+    times = np.zeros(2)
+    rc = lib().orc_tree_gravity_ex(n, *(_p(a, np.float64) for a in arrs), G, theta, n_leaf, n_g,
+                                   int(bool(quad)),
+                                   *(_p(out[k], np.float64) for k in ("ax", "ay", "az", "phi", "asum")),
+                                   _p(stats, np.int64), int(gstride), _p(times, np.float64))
+    if rc != 0:
+        raise RuntimeError("oracle tree gravity failed")
+    return float(times[0]), float(times[1]), stats
 
 
 # --------------------------------------------------------------------------

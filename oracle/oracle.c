@@ -358,12 +358,41 @@ static void pc_term(double rx, double ry, double rz, double e2i, double M,
 /* excluded) plus the particle-cell sum over SPJ.  Inputs and outputs are in */
 /* input order.  stats = {nodes, groups, n_pp, n_pc}.  Returns 0 or -1.      */
 /* ------------------------------------------------------------------------ */
+static double wall_seconds(void)
+{
+#ifdef _OPENMP
+    return omp_get_wtime();
+#else
+    return 0.0;
+#endif
+}
+
+int orc_tree_gravity_ex(int64_t n, const double *x, const double *y, const double *z,
+                        const double *m, const double *eps, double G, double theta,
+                        int n_leaf, int64_t n_g, int quad,
+                        double *ax, double *ay, double *az, double *phi, double *asum,
+                        int64_t *stats, int64_t gstride, double *times);
+
 int orc_tree_gravity(int64_t n, const double *x, const double *y, const double *z,
                      const double *m, const double *eps, double G, double theta,
                      int n_leaf, int64_t n_g, int quad,
                      double *ax, double *ay, double *az, double *phi, double *asum,
                      int64_t *stats)
 {
+    return orc_tree_gravity_ex(n, x, y, z, m, eps, G, theta, n_leaf, n_g, quad, ax, ay, az, phi,
+                               asum, stats, 1, NULL);
+}
+
+/* As orc_tree_gravity; only every gstride-th group is walked and summed (the
+ * others are left untouched), and times = {build seconds, walk seconds}.   */
+int orc_tree_gravity_ex(int64_t n, const double *x, const double *y, const double *z,
+                        const double *m, const double *eps, double G, double theta,
+                        int n_leaf, int64_t n_g, int quad,
+                        double *ax, double *ay, double *az, double *phi, double *asum,
+                        int64_t *stats, int64_t gstride, double *times)
+{
+    double t0 = wall_seconds(), t1 = t0;
+    if (gstride < 1) gstride = 1;
     double lo[3], L;
     orc_root_box(n, x, y, z, lo, &L);
     uint64_t *key = malloc(8 * (size_t)n);
@@ -395,12 +424,13 @@ int orc_tree_gravity(int64_t n, const double *x, const double *y, const double *
     orc_moments(nn, fi, co, sx, sy, sz, sm, se, M, com, Q, e2);
     groups = malloc(8 * (size_t)nn);
     ng = orc_groups(nn, co, ch, nch, n_g, groups);
+    t1 = wall_seconds();
 #pragma omp parallel reduction(+ : npp, npc)
     {
         int64_t *epj = malloc(8 * (size_t)(n + 1));
         int64_t *spj = malloc(8 * (size_t)(nn + 1));
 #pragma omp for schedule(dynamic, 1)
-        for (int64_t gi = 0; gi < ng; gi++) {
+        for (int64_t gi = 0; gi < ng; gi += gstride) {
             int64_t g = groups[gi], ne, ns;
             if (orc_walk(g, lev, pre, fi, co, ch, nch, scx, scy, scz, theta, nn,
                          n + 1, epj, &ne, nn + 1, spj, &ns) != 0) {
@@ -436,6 +466,7 @@ int orc_tree_gravity(int64_t n, const double *x, const double *y, const double *
         free(epj); free(spj);
     }
 done:
+    if (times) { times[0] = t1 - t0; times[1] = wall_seconds() - t1; }
     if (stats) { stats[0] = nn; stats[1] = ng; stats[2] = npp; stats[3] = npc; }
     free(key); free(cx); free(cy); free(cz); free(ord); free(sk);
     free(scx); free(scy); free(scz); free(sx); free(sy); free(sz); free(sm); free(se);

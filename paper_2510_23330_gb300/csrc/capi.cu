@@ -258,6 +258,9 @@ void gnb_destroy(gnb_ctx *c)
                    c->rs_total, c->rtot_d, c->scan_part, c->scan_poff};
     for (void *q : all) dfree(c, q);
     if (c->pinned_i) cudaFreeHost(c->pinned_i);
+    for (auto &q : c->pend) { cudaEventDestroy(q.second.first); cudaEventDestroy(q.second.second); }
+    for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+    if (c->open_ev) cudaEventDestroy(c->open_ev);
     delete c;
 }
 
@@ -288,11 +291,11 @@ int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *t
     c->pinned_i[0] = ni;
     cudaMemcpyAsync(c->n_d, c->pinned_i, sizeof(int), cudaMemcpyHostToDevice, c->s);
     cudaMemsetAsync(c->work_d, 0, sizeof(int), c->s);
-    k_validate<<<nb, 256, 0, c->s>>>(p, ni, c->work_d);
-    k_set_init<<<nb, 256, 0, c->s>>>(p, ni);
-    k_gas_flag_in<<<nb, 256, 0, c->s>>>(p.type, c->gas_flag, ni);
+    gnb::counted(k_validate)<<<nb, 256, 0, c->s>>>(p, ni, c->work_d);
+    gnb::counted(k_set_init)<<<nb, 256, 0, c->s>>>(p, ni);
+    gnb::counted(k_gas_flag_in)<<<nb, 256, 0, c->s>>>(p.type, c->gas_flag, ni);
     GNB_TRY(device_scan(c, c->gas_flag, c->pscan, c->n_d, ni, c->ngas_d));
-    k_grank<<<nb, 256, 0, c->s>>>(p.type, c->pscan, ni, p.grank);
+    gnb::counted(k_grank)<<<nb, 256, 0, c->s>>>(p.type, c->pscan, ni, p.grank);
     GNB_LAUNCH_CHECK(c, "set particles");
     cudaMemcpyAsync(c->pinned_i + 1, c->work_d, sizeof(int), cudaMemcpyDeviceToHost, c->s);
     cudaMemcpyAsync(c->pinned_i + 2, c->ngas_d, sizeof(int), cudaMemcpyDeviceToHost, c->s);
@@ -318,12 +321,71 @@ int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *t
 
 namespace gnb {
 
+std::atomic<long long> g_launches{0};
+
+static cudaEvent_t ev_get(gnb_ctx *c)
+{
+    if (!c->evpool.empty()) {
+        cudaEvent_t e = c->evpool.back();
+        c->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void phase_begin(gnb_ctx *c, int phase)
+{
+    if (!c->timing) return;
+    phase_end(c);
+    c->open_ev = ev_get(c);
+    c->open_phase = phase;
+    if (c->open_ev) cudaEventRecord(c->open_ev, c->s);
+}
+
+void phase_end(gnb_ctx *c)
+{
+    if (!c->timing || c->open_phase < 0) return;
+    cudaEvent_t e = ev_get(c);
+    if (c->open_ev && e) {
+        cudaEventRecord(e, c->s);
+        c->pend.push_back({c->open_phase, {c->open_ev, e}});
+    }
+    c->open_phase = -1;
+    c->open_ev = nullptr;
+}
+
+// after the stream is idle: add the recorded phase durations
+static void phase_resolve(gnb_ctx *c)
+{
+    phase_end(c);
+    for (auto &q : c->pend) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, q.second.first, q.second.second) == cudaSuccess) {
+            c->phase_ms[q.first] += ms;
+            c->phase_calls[q.first] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        c->evpool.push_back(q.second.first);
+        c->evpool.push_back(q.second.second);
+    }
+    c->pend.clear();
+}
+
 static int do_build(gnb_ctx *c)
 {
+    phase_begin(c, GNB_T_SORT);
     GNB_TRY(morton_and_sort(c));
+    phase_begin(c, GNB_T_TREE);
     PArr &a = c->P[c->cur];
     GNB_TRY(build_tree(c, c->t, c->skey, (int)c->n, c->n_d, c->cfg.n_leaf, c->cfg.n_group, a.cx, a.cy, a.cz, a.rx,
                        a.ry, a.rz, a.m, a.eps, true));
+    phase_end(c);
     c->tree_valid = true;
     c->stats[GNB_S_NODES] = c->t.nnodes;
     return GNB_OK;
@@ -348,10 +410,13 @@ static int read_groups(gnb_ctx *c)
 static int do_gravity(gnb_ctx *c, int mode)
 {
     cudaMemsetAsync(c->counters_d, 0, 2 * sizeof(unsigned long long), c->s);
+    phase_begin(c, GNB_T_GRAVITY);
     if (mode == GNB_GRAV_TREE) GNB_TRY(gravity_tree(c));
     else GNB_TRY(gravity_direct(c));
+    phase_begin(c, GNB_T_EXTERNAL);
     GNB_TRY(gravity_nfw(c));
     GNB_TRY(zero_forces(c));
+    phase_end(c);
     c->gravity_valid = true;
     c->last_grav_mode = mode;
     return GNB_OK;
@@ -375,9 +440,12 @@ static int finish(gnb_ctx *c, int rc)
         cudaStreamSynchronize(c->s);
         cudaGetLastError();
         cudaMemset(c->status_d, 0, sizeof(int));
+        phase_resolve(c);
         return rc;
     }
-    return check_status(c);
+    rc = check_status(c);
+    phase_resolve(c);
+    return rc;
 }
 
 }  // namespace gnb
@@ -463,14 +531,18 @@ int gnb_step_kdk(gnb_ctx *c, double dt, int nsteps, int mode)
     }
     float hdt = (float)(0.5 * dt);
     for (int s = 0; s < nsteps && rc == GNB_OK; s++) {
+        phase_begin(c, GNB_T_KDK);
         rc = kick(c, hdt, true);
         if (rc == GNB_OK) rc = drift(c, dt);
         if (rc == GNB_OK) rc = predict(c, hdt);
+        phase_end(c);
         c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
         c->use_pred = true;
         if (rc == GNB_OK) rc = do_forces(c, mode);
         c->use_pred = false;
+        phase_begin(c, GNB_T_KDK);
         if (rc == GNB_OK) rc = kick(c, hdt, true);
+        phase_end(c);
     }
     if (rc == GNB_OK) rc = read_groups(c);
     return finish(c, rc);
@@ -550,6 +622,33 @@ int gnb_stats(gnb_ctx *c, int64_t out[GNB_S_COUNT_])
     if (c->rtot_d && c->n_gas > 0) cudaMemcpy(&rt, c->rtot_d, sizeof(int), cudaMemcpyDeviceToHost);
     c->stats[GNB_S_NSYM] = (int64_t)c->n_gas * 63 + rt;
     for (int k = 0; k < GNB_S_COUNT_; k++) out[k] = c->stats[k];
+    return GNB_OK;
+}
+
+int gnb_set_timing(gnb_ctx *c, int enable)
+{
+    if (!c) return GNB_EINVAL;
+    phase_resolve(c);
+    c->timing = enable != 0;
+    return GNB_OK;
+}
+
+int gnb_phase_times(gnb_ctx *c, double out_ms[GNB_T_COUNT_], int64_t calls[GNB_T_COUNT_], int64_t *launches,
+                    int reset)
+{
+    if (!c) return GNB_EINVAL;
+    cudaStreamSynchronize(c->s);
+    phase_resolve(c);
+    for (int k = 0; k < GNB_T_COUNT_; k++) {
+        if (out_ms) out_ms[k] = c->phase_ms[k];
+        if (calls) calls[k] = c->phase_calls[k];
+    }
+    long long now = g_launches.load();
+    if (launches) *launches = now - c->launch_base;
+    if (reset) {
+        for (int k = 0; k < GNB_T_COUNT_; k++) { c->phase_ms[k] = 0; c->phase_calls[k] = 0; }
+        c->launch_base = now;
+    }
     return GNB_OK;
 }
 

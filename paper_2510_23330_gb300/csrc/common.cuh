@@ -15,7 +15,11 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/galnb.h"
 
@@ -23,6 +27,15 @@
 #define GNB_GRID_MAX 2097151
 
 namespace gnb {
+
+// Kernel launches issued by this library (every launch goes through counted()).
+extern std::atomic<long long> g_launches;
+template <class K>
+inline K counted(K k)
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return k;
+}
 
 // Device-side status word bits (set by kernels, read by the host).
 enum : int {
@@ -140,6 +153,16 @@ struct gnb_ctx {
     double *red_d = nullptr;                   // reduction scratch
     int64_t stats[GNB_S_COUNT_] = {0};
 
+    // per-phase CUDA-event timers (enabled by gnb_set_timing)
+    bool timing = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pend;
+    std::vector<cudaEvent_t> evpool;
+    double phase_ms[GNB_T_COUNT_] = {0};
+    int64_t phase_calls[GNB_T_COUNT_] = {0};
+    long long launch_base = 0;
+    cudaEvent_t open_ev = nullptr;
+    int open_phase = -1;
+
     // state flags
     bool have_particles = false, tree_valid = false, gravity_valid = false;
     bool density_valid = false, force_valid = false, have_h = false, sphf_valid = false;
@@ -168,6 +191,11 @@ inline int dalloc(gnb_ctx *c, T **p, size_t count)
     }
     return GNB_OK;
 }
+
+// phase timers (capi.cu): events recorded on the context stream around
+// each phase, resolved after the call's final synchronisation
+void phase_begin(gnb_ctx *c, int phase);
+void phase_end(gnb_ctx *c);
 
 // sort.cu
 int morton_and_sort(gnb_ctx *c);

@@ -412,7 +412,7 @@ static int launch_persistent(gnb_ctx *c, K kern, GravParams p, int *next_d)
     if (per_sm < 1) per_sm = 1;
     p.next = next_d;
     cudaMemsetAsync(next_d, 0, sizeof(int), c->s);
-    kern<<<g_sms * per_sm, GW_THREADS, smem, c->s>>>(p);
+    gnb::counted(kern)<<<g_sms * per_sm, GW_THREADS, smem, c->s>>>(p);
     GNB_LAUNCH_CHECK(c, "gravity kernel");
     return GNB_OK;
 }
@@ -464,7 +464,7 @@ int gravity_nfw(gnb_ctx *c)
     int n = (int)c->n;
     PArr &a = c->P[c->cur];
     if (c->cfg.nfw_ms > 0) {
-        k_nfw<<<(n + 255) / 256, 256, 0, c->s>>>(a.x, a.y, a.z, n, (float)c->cfg.G, (float)c->cfg.nfw_ms,
+        gnb::counted(k_nfw)<<<(n + 255) / 256, 256, 0, c->s>>>(a.x, a.y, a.z, n, (float)c->cfg.G, (float)c->cfg.nfw_ms,
                                                  (float)c->cfg.nfw_rs, c->ax, c->ay, c->az, c->pext);
         GNB_LAUNCH_CHECK(c, "nfw");
     } else {

@@ -45,7 +45,7 @@ __global__ void k_predict(PArr p, const float *__restrict__ ax, const float *__r
 int kick(gnb_ctx *c, float hdt, bool)
 {
     int n = (int)c->n;
-    k_kick<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], c->ax, c->ay, c->az, c->dudt, n, hdt);
+    gnb::counted(k_kick)<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], c->ax, c->ay, c->az, c->dudt, n, hdt);
     GNB_LAUNCH_CHECK(c, "kick");
     return GNB_OK;
 }
@@ -53,7 +53,7 @@ int kick(gnb_ctx *c, float hdt, bool)
 int drift(gnb_ctx *c, double dt)
 {
     int n = (int)c->n;
-    k_drift<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], n, dt);
+    gnb::counted(k_drift)<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], n, dt);
     GNB_LAUNCH_CHECK(c, "drift");
     return GNB_OK;
 }
@@ -61,7 +61,7 @@ int drift(gnb_ctx *c, double dt)
 int predict(gnb_ctx *c, float hdt)
 {
     int n = (int)c->n;
-    k_predict<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], c->ax, c->ay, c->az, c->dudt, n, hdt);
+    gnb::counted(k_predict)<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], c->ax, c->ay, c->az, c->dudt, n, hdt);
     GNB_LAUNCH_CHECK(c, "predict");
     return GNB_OK;
 }
@@ -82,7 +82,7 @@ __global__ void k_combine(int n, const float *__restrict__ gax, const float *__r
 int zero_forces(gnb_ctx *c)
 {
     int n = (int)c->n;
-    k_combine<<<(n + 255) / 256, 256, 0, c->s>>>(n, c->gax, c->gay, c->gaz, c->ax, c->ay, c->az, c->dudt);
+    gnb::counted(k_combine)<<<(n + 255) / 256, 256, 0, c->s>>>(n, c->gax, c->gay, c->gaz, c->ax, c->ay, c->az, c->dudt);
     GNB_LAUNCH_CHECK(c, "combine");
     return GNB_OK;
 }
@@ -136,8 +136,8 @@ __global__ void k_diag_final(const double *__restrict__ part, int nb, double *__
 int diagnostics(gnb_ctx *c, double out[10])
 {
     int n = (int)c->n;
-    k_diag_partial<<<DG_BLOCKS, 256, 0, c->s>>>(c->P[c->cur], c->pot, c->pext, n, c->red_d);
-    k_diag_final<<<1, 32, 0, c->s>>>(c->red_d, DG_BLOCKS, c->red_d + DG_BLOCKS * 10);
+    gnb::counted(k_diag_partial)<<<DG_BLOCKS, 256, 0, c->s>>>(c->P[c->cur], c->pot, c->pext, n, c->red_d);
+    gnb::counted(k_diag_final)<<<1, 32, 0, c->s>>>(c->red_d, DG_BLOCKS, c->red_d + DG_BLOCKS * 10);
     GNB_LAUNCH_CHECK(c, "diagnostics");
     GNB_TRY(cuda_check(c, cudaMemcpyAsync(out, c->red_d + DG_BLOCKS * 10, 10 * sizeof(double),
                                           cudaMemcpyDeviceToHost, c->s), "diagnostics copy"));
@@ -215,41 +215,41 @@ int scatter_out(gnb_ctx *c, int field, void *dst)
     int nb = (n + 255) / 256;
     PArr &a = c->P[c->cur];
     switch (field) {
-    case GNB_F_X: k_scatter_orig<double><<<nb, 256, 0, c->s>>>(a.x, a.orig, n, (double *)dst); break;
-    case GNB_F_Y: k_scatter_orig<double><<<nb, 256, 0, c->s>>>(a.y, a.orig, n, (double *)dst); break;
-    case GNB_F_Z: k_scatter_orig<double><<<nb, 256, 0, c->s>>>(a.z, a.orig, n, (double *)dst); break;
-    case GNB_F_VX: k_scatter_orig<float><<<nb, 256, 0, c->s>>>(a.vx, a.orig, n, (float *)dst); break;
-    case GNB_F_VY: k_scatter_orig<float><<<nb, 256, 0, c->s>>>(a.vy, a.orig, n, (float *)dst); break;
-    case GNB_F_VZ: k_scatter_orig<float><<<nb, 256, 0, c->s>>>(a.vz, a.orig, n, (float *)dst); break;
-    case GNB_F_AX: k_scatter_orig<float><<<nb, 256, 0, c->s>>>(c->ax, a.orig, n, (float *)dst); break;
-    case GNB_F_AY: k_scatter_orig<float><<<nb, 256, 0, c->s>>>(c->ay, a.orig, n, (float *)dst); break;
-    case GNB_F_AZ: k_scatter_orig<float><<<nb, 256, 0, c->s>>>(c->az, a.orig, n, (float *)dst); break;
-    case GNB_F_AGRAV_X: k_scatter_orig<float><<<nb, 256, 0, c->s>>>(c->gax, a.orig, n, (float *)dst); break;
-    case GNB_F_AGRAV_Y: k_scatter_orig<float><<<nb, 256, 0, c->s>>>(c->gay, a.orig, n, (float *)dst); break;
-    case GNB_F_AGRAV_Z: k_scatter_orig<float><<<nb, 256, 0, c->s>>>(c->gaz, a.orig, n, (float *)dst); break;
-    case GNB_F_POT: k_scatter_orig<float><<<nb, 256, 0, c->s>>>(c->pot, a.orig, n, (float *)dst); break;
-    case GNB_F_U: k_scatter_orig_zero_star<<<nb, 256, 0, c->s>>>(a.u, a.orig, a.type, n, (float *)dst); break;
+    case GNB_F_X: gnb::counted(k_scatter_orig<double>)<<<nb, 256, 0, c->s>>>(a.x, a.orig, n, (double *)dst); break;
+    case GNB_F_Y: gnb::counted(k_scatter_orig<double>)<<<nb, 256, 0, c->s>>>(a.y, a.orig, n, (double *)dst); break;
+    case GNB_F_Z: gnb::counted(k_scatter_orig<double>)<<<nb, 256, 0, c->s>>>(a.z, a.orig, n, (double *)dst); break;
+    case GNB_F_VX: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(a.vx, a.orig, n, (float *)dst); break;
+    case GNB_F_VY: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(a.vy, a.orig, n, (float *)dst); break;
+    case GNB_F_VZ: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(a.vz, a.orig, n, (float *)dst); break;
+    case GNB_F_AX: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->ax, a.orig, n, (float *)dst); break;
+    case GNB_F_AY: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->ay, a.orig, n, (float *)dst); break;
+    case GNB_F_AZ: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->az, a.orig, n, (float *)dst); break;
+    case GNB_F_AGRAV_X: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->gax, a.orig, n, (float *)dst); break;
+    case GNB_F_AGRAV_Y: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->gay, a.orig, n, (float *)dst); break;
+    case GNB_F_AGRAV_Z: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->gaz, a.orig, n, (float *)dst); break;
+    case GNB_F_POT: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->pot, a.orig, n, (float *)dst); break;
+    case GNB_F_U: gnb::counted(k_scatter_orig_zero_star)<<<nb, 256, 0, c->s>>>(a.u, a.orig, a.type, n, (float *)dst); break;
     case GNB_F_DUDT:
-        k_scatter_orig_zero_star<<<nb, 256, 0, c->s>>>(c->dudt, a.orig, a.type, n, (float *)dst);
+        gnb::counted(k_scatter_orig_zero_star)<<<nb, 256, 0, c->s>>>(c->dudt, a.orig, a.type, n, (float *)dst);
         break;
-    case GNB_F_RHO: k_scatter_orig_zero_star<<<nb, 256, 0, c->s>>>(c->rho, a.orig, a.type, n, (float *)dst); break;
+    case GNB_F_RHO: gnb::counted(k_scatter_orig_zero_star)<<<nb, 256, 0, c->s>>>(c->rho, a.orig, a.type, n, (float *)dst); break;
     case GNB_F_PRES:
-        k_scatter_orig_zero_star<<<nb, 256, 0, c->s>>>(c->pres, a.orig, a.type, n, (float *)dst);
+        gnb::counted(k_scatter_orig_zero_star)<<<nb, 256, 0, c->s>>>(c->pres, a.orig, a.type, n, (float *)dst);
         break;
-    case GNB_F_CS: k_scatter_orig_zero_star<<<nb, 256, 0, c->s>>>(c->cs, a.orig, a.type, n, (float *)dst); break;
-    case GNB_F_H2: k_scatter_orig_zero_star_d<<<nb, 256, 0, c->s>>>(a.h2, a.orig, a.type, n, (double *)dst); break;
-    case GNB_F_KEY: k_scatter_orig<uint64_t><<<nb, 256, 0, c->s>>>(c->skey, a.orig, n, (uint64_t *)dst); break;
-    case GNB_F_ID: k_scatter_orig<int64_t><<<nb, 256, 0, c->s>>>(a.id, a.orig, n, (int64_t *)dst); break;
-    case GNB_F_ORDER: k_order_out<<<nb, 256, 0, c->s>>>(a.orig, n, (int64_t *)dst); break;
+    case GNB_F_CS: gnb::counted(k_scatter_orig_zero_star)<<<nb, 256, 0, c->s>>>(c->cs, a.orig, a.type, n, (float *)dst); break;
+    case GNB_F_H2: gnb::counted(k_scatter_orig_zero_star_d)<<<nb, 256, 0, c->s>>>(a.h2, a.orig, a.type, n, (double *)dst); break;
+    case GNB_F_KEY: gnb::counted(k_scatter_orig<uint64_t>)<<<nb, 256, 0, c->s>>>(c->skey, a.orig, n, (uint64_t *)dst); break;
+    case GNB_F_ID: gnb::counted(k_scatter_orig<int64_t>)<<<nb, 256, 0, c->s>>>(a.id, a.orig, n, (int64_t *)dst); break;
+    case GNB_F_ORDER: gnb::counted(k_order_out)<<<nb, 256, 0, c->s>>>(a.orig, n, (int64_t *)dst); break;
     case GNB_F_NODES:
-        k_nodes_out<<<(c->t.nnodes + 255) / 256, 256, 0, c->s>>>(c->t.na, c->skey, c->t.nnodes, (int64_t *)dst);
+        gnb::counted(k_nodes_out)<<<(c->t.nnodes + 255) / 256, 256, 0, c->s>>>(c->t.na, c->skey, c->t.nnodes, (int64_t *)dst);
         break;
     case GNB_F_GROUPS:
-        k_groups_out<<<(c->t.ngroups + 255) / 256, 256, 0, c->s>>>(c->t.groups, c->t.ngroups, (int64_t *)dst);
+        gnb::counted(k_groups_out)<<<(c->t.ngroups + 255) / 256, 256, 0, c->s>>>(c->t.groups, c->t.ngroups, (int64_t *)dst);
         break;
     case GNB_F_NBR: {
         int ng = (int)c->n_gas;
-        k_nbr_out<<<(ng + 127) / 128, 128, 0, c->s>>>(ng, c->nbr, c->gslot, a.orig, c->ggrank, (int64_t *)dst);
+        gnb::counted(k_nbr_out)<<<(ng + 127) / 128, 128, 0, c->s>>>(ng, c->nbr, c->gslot, a.orig, c->ggrank, (int64_t *)dst);
         break;
     }
     default: return fail(c, GNB_EINVAL, "unknown field");

@@ -91,11 +91,11 @@ __global__ void k_box_finalize(const unsigned long long *mm, double *box, int *s
 int root_box(gnb_ctx *c)
 {
     int n = (int)c->n;
-    k_mm_init<<<1, 32, 0, c->s>>>(c->mm_d);
+    gnb::counted(k_mm_init)<<<1, 32, 0, c->s>>>(c->mm_d);
     int blocks = (n + 255) / 256;
     if (blocks > 1216) blocks = 1216;
-    k_minmax<<<blocks, 256, 0, c->s>>>(c->P[c->cur].x, c->P[c->cur].y, c->P[c->cur].z, n, c->mm_d);
-    k_box_finalize<<<1, 32, 0, c->s>>>(c->mm_d, c->box_d, c->status_d);
+    gnb::counted(k_minmax)<<<blocks, 256, 0, c->s>>>(c->P[c->cur].x, c->P[c->cur].y, c->P[c->cur].z, n, c->mm_d);
+    gnb::counted(k_box_finalize)<<<1, 32, 0, c->s>>>(c->mm_d, c->box_d, c->status_d);
     GNB_LAUNCH_CHECK(c, "root box");
     return GNB_OK;
 }
@@ -291,7 +291,7 @@ int morton_and_sort(gnb_ctx *c)
     GNB_TRY(root_box(c));
     int nb = (n + 255) / 256;
     PArr &a = c->P[c->cur];
-    k_morton<<<nb, 256, 0, c->s>>>(a, n, c->box_d, c->key, c->skey, c->sval, c->slot_of_orig);
+    gnb::counted(k_morton)<<<nb, 256, 0, c->s>>>(a, n, c->box_d, c->key, c->skey, c->sval, c->slot_of_orig);
     GNB_LAUNCH_CHECK(c, "morton");
     int ntiles = (n + RS_TILE - 1) / RS_TILE;
     uint64_t *kin = c->skey, *kout = c->skey2;
@@ -299,18 +299,18 @@ int morton_and_sort(gnb_ctx *c)
     for (int pass = 0; pass < 8; pass++) {
         int shift = 8 * pass;
         cudaMemsetAsync(c->rs_total, 0, 256 * sizeof(int), c->s);
-        k_rs_hist<<<ntiles, RS_THREADS, 0, c->s>>>(kin, n, shift, c->rs_counts, ntiles, c->rs_total);
-        k_rs_scan<<<256, 1024, 0, c->s>>>(c->rs_counts, ntiles, c->rs_total);
-        k_rs_scatter<<<ntiles, RS_THREADS, 0, c->s>>>(kin, vin, kout, vout, n, shift, c->rs_counts,
+        gnb::counted(k_rs_hist)<<<ntiles, RS_THREADS, 0, c->s>>>(kin, n, shift, c->rs_counts, ntiles, c->rs_total);
+        gnb::counted(k_rs_scan)<<<256, 1024, 0, c->s>>>(c->rs_counts, ntiles, c->rs_total);
+        gnb::counted(k_rs_scatter)<<<ntiles, RS_THREADS, 0, c->s>>>(kin, vin, kout, vout, n, shift, c->rs_counts,
                                                       ntiles);
         uint64_t *tk = kin; kin = kout; kout = tk;
         int *tv = vin; vin = vout; vout = tv;
     }
     GNB_LAUNCH_CHECK(c, "radix sort");
     // after 8 passes the sorted data is back in skey / sval
-    k_src<<<nb, 256, 0, c->s>>>(vin, c->slot_of_orig, c->src, n);
+    gnb::counted(k_src)<<<nb, 256, 0, c->s>>>(vin, c->slot_of_orig, c->src, n);
     PArr &b = c->P[1 - c->cur];
-    k_permute<<<nb, 256, 0, c->s>>>(a, b, c->src, n);
+    gnb::counted(k_permute)<<<nb, 256, 0, c->s>>>(a, b, c->src, n);
     GNB_LAUNCH_CHECK(c, "permute");
     c->cur = 1 - c->cur;
     return GNB_OK;

@@ -657,12 +657,13 @@ int sph_density(gnb_ctx *c)
 {
     int n = (int)c->n, ng = (int)c->n_gas;
     if (ng == 0) return GNB_OK;
+    phase_begin(c, GNB_T_HYDRO_TREE);
     PArr &a = c->P[c->cur];
     int nb = (n + 255) / 256, gb = (ng + 255) / 256;
     // gas slots in Morton order
-    k_gas_flag<<<nb, 256, 0, c->s>>>(a.type, c->gas_flag, n);
+    gnb::counted(k_gas_flag)<<<nb, 256, 0, c->s>>>(a.type, c->gas_flag, n);
     GNB_TRY(device_scan(c, c->gas_flag, c->pscan, c->n_d, n, nullptr));
-    k_gas_compact<<<nb, 256, 0, c->s>>>(c->gas_flag, c->pscan, n, c->gslot);
+    gnb::counted(k_gas_compact)<<<nb, 256, 0, c->s>>>(c->gas_flag, c->pscan, n, c->gslot);
     GasGather gg;
     gg.skey = c->skey; gg.p = a; gg.gslot = c->gslot; gg.gkey = c->gkey;
     gg.gcx = c->gcx; gg.gcy = c->gcy; gg.gcz = c->gcz; gg.ggrank = c->ggrank;
@@ -670,13 +671,14 @@ int sph_density(gnb_ctx *c)
     gg.gvx = c->gvx; gg.gvy = c->gvy; gg.gvz = c->gvz; gg.gu = c->gu; gg.gRprev = c->gRprev;
     gg.gx = c->gx; gg.gy = c->gy; gg.gz = c->gz;
     gg.ng = ng; gg.pred = c->use_pred ? 1 : 0; gg.have_h = c->have_h ? 1 : 0;
-    k_gas_gather<<<gb, 256, 0, c->s>>>(gg);
+    gnb::counted(k_gas_gather)<<<gb, 256, 0, c->s>>>(gg);
     GNB_LAUNCH_CHECK(c, "gas gather");
     // hydro tree and groups of <= 32 gas particles
     GNB_TRY(build_tree(c, c->gt, c->gkey, ng, c->ngas_d, c->cfg.n_leaf, 32, c->gcx, c->gcy, c->gcz, c->grx,
                        c->gry, c->grz, c->gm, c->gm, false));
+    phase_begin(c, GNB_T_KNN);
     // work_d: [0] next item, [1] items left unfinished, [2] live item count, [3] per-pass snapshot
-    k_knn_init<<<304, 256, 0, c->s>>>(c->gt, c->gRprev, c->have_h ? 1 : 0, c->box_d, c->kR,
+    gnb::counted(k_knn_init)<<<304, 256, 0, c->s>>>(c->gt, c->gRprev, c->have_h ? 1 : 0, c->box_d, c->kR,
                                       c->kRb, c->kflag, c->kitem, c->work_d + 2);
     GNB_LAUNCH_CHECK(c, "knn init");
     KnnParams p;
@@ -706,7 +708,7 @@ int sph_density(gnb_ctx *c)
         for (int q = 0; q < 3; q++) {
             cudaMemsetAsync(c->work_d, 0, 2 * sizeof(int), c->s);
             cudaMemcpyAsync(c->work_d + 3, c->work_d + 2, sizeof(int), cudaMemcpyDeviceToDevice, c->s);
-            k_knn<<<g_knn_blocks, KN_THREADS, smem, c->s>>>(p);
+            gnb::counted(k_knn)<<<g_knn_blocks, KN_THREADS, smem, c->s>>>(p);
             passes++;
         }
         GNB_LAUNCH_CHECK(c, "knn");
@@ -719,9 +721,10 @@ int sph_density(gnb_ctx *c)
     }
     c->stats[GNB_S_KNN_PASSES] = passes;
     c->stats[GNB_S_GAS_NODES] = c->gt.nnodes;
-    k_gas_scatter_density<<<gb, 256, 0, c->s>>>(ng, c->gslot, c->grho, c->gP, c->gcs, c->gh2, c->rho, c->pres,
+    gnb::counted(k_gas_scatter_density)<<<gb, 256, 0, c->s>>>(ng, c->gslot, c->grho, c->gP, c->gcs, c->gh2, c->rho, c->pres,
                                                 c->cs, a.h2);
     GNB_LAUNCH_CHECK(c, "density scatter");
+    phase_end(c);
     c->have_h = true;
     return GNB_OK;
 }
@@ -731,12 +734,13 @@ int sph_force(gnb_ctx *c)
     int ng = (int)c->n_gas;
     if (ng == 0) return GNB_OK;
     int gb = (ng + 255) / 256;
+    phase_begin(c, GNB_T_FORCE);
     cudaMemsetAsync(c->rcnt, 0, sizeof(int) * ng, c->s);
-    k_mutual<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->nd2, c->gE, c->gh2, c->g64, c->ggrank, c->gx, c->gy, c->gz,
+    gnb::counted(k_mutual)<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->nd2, c->gE, c->gh2, c->g64, c->ggrank, c->gx, c->gy, c->gz,
                                    c->mut, c->rcnt);
     GNB_TRY(device_scan(c, c->rcnt, c->roff, c->ngas_d, ng, c->rtot_d));
     cudaMemsetAsync(c->rfill, 0, sizeof(int) * ng, c->s);
-    k_rev_fill<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->mut, c->roff, c->rfill, c->rlist);
+    gnb::counted(k_rev_fill)<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->mut, c->roff, c->rfill, c->rlist);
     GNB_LAUNCH_CHECK(c, "symmetric lists");
     ForceParams p;
     p.ng = ng; p.nbr = c->nbr; p.roff = c->roff; p.rcnt = c->rcnt; p.rlist = c->rlist;
@@ -744,10 +748,11 @@ int sph_force(gnb_ctx *c)
     p.gm = c->gm; p.gvx = c->gvx; p.gvy = c->gvy; p.gvz = c->gvz; p.h = c->gh; p.rho = c->grho; p.P = c->gP;
     p.cs = c->gcs; p.box = c->box_d; p.alpha = (float)c->cfg.alpha_visc;
     p.ax = c->hax; p.ay = c->hay; p.az = c->haz; p.du = c->hdu;
-    k_force<<<(ng + 127) / 128, 128, 0, c->s>>>(p);
-    k_gas_scatter<<<gb, 256, 0, c->s>>>(ng, c->gslot, c->hax, c->hay, c->haz, c->hdu, c->ax, c->ay, c->az,
+    gnb::counted(k_force)<<<(ng + 127) / 128, 128, 0, c->s>>>(p);
+    gnb::counted(k_gas_scatter)<<<gb, 256, 0, c->s>>>(ng, c->gslot, c->hax, c->hay, c->haz, c->hdu, c->ax, c->ay, c->az,
                                         c->dudt);
     GNB_LAUNCH_CHECK(c, "sph force");
+    phase_end(c);
     return GNB_OK;
 }
 

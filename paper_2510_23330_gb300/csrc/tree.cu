@@ -117,9 +117,9 @@ __global__ void k_scan_apply(const int *__restrict__ in, int *__restrict__ out, 
 int device_scan(gnb_ctx *c, const int *in, int *out, const int *n_d, int nmax, int *total_d)
 {
     (void)nmax;
-    k_scan_partial<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(in, n_d, c->scan_part);
-    k_scan_partials<<<1, 1024, 0, c->s>>>(c->scan_part, c->scan_poff, TB_BLOCKS, total_d);
-    k_scan_apply<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(in, out, n_d, c->scan_poff);
+    gnb::counted(k_scan_partial)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(in, n_d, c->scan_part);
+    gnb::counted(k_scan_partials)<<<1, 1024, 0, c->s>>>(c->scan_part, c->scan_poff, TB_BLOCKS, total_d);
+    gnb::counted(k_scan_apply)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(in, out, n_d, c->scan_poff);
     GNB_LAUNCH_CHECK(c, "scan");
     return GNB_OK;
 }
@@ -409,13 +409,13 @@ int build_tree(gnb_ctx *c, Tree &t, const uint64_t *skey, int n, const int *n_d,
 {
     for (int attempt = 0; attempt < 6; attempt++) {
         if (t.cap < 64) GNB_TRY(tree_alloc(c, t, n + n / 2 + 1024));
-        k_tree_root<<<1, 32, 0, c->s>>>(t, n);
+        gnb::counted(k_tree_root)<<<1, 32, 0, c->s>>>(t, n);
         for (int l = 0; l < GNB_MAXLEV; l++) {
-            k_split_count<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, l, n_leaf);
-            k_level_scan<<<1, 1024, 0, c->s>>>(t, l, TB_BLOCKS, c->status_d);
-            k_emit<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, l);
+            gnb::counted(k_split_count)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, l, n_leaf);
+            gnb::counted(k_level_scan)<<<1, 1024, 0, c->s>>>(t, l, TB_BLOCKS, c->status_d);
+            gnb::counted(k_emit)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, l);
         }
-        k_split_count<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, GNB_MAXLEV, n_leaf);
+        gnb::counted(k_split_count)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, GNB_MAXLEV, n_leaf);
         GNB_LAUNCH_CHECK(c, "tree build");
         // one check of the overflow flag per build
         int h[2];
@@ -437,7 +437,7 @@ int build_tree(gnb_ctx *c, Tree &t, const uint64_t *skey, int n, const int *n_d,
     if (t.nnodes <= 0) return fail(c, GNB_ECAPACITY, "tree node capacity");
     if (moments) {
         for (int l = GNB_MAXLEV; l >= 0; l--)
-            k_moments_level<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, l, pcx, pcy, pcz, prx, pry, prz, pm, peps,
+            gnb::counted(k_moments_level)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, l, pcx, pcy, pcz, prx, pry, prz, pm, peps,
                                                                 c->box_d);
         GNB_LAUNCH_CHECK(c, "moments");
     }
@@ -450,10 +450,10 @@ int build_tree(gnb_ctx *c, Tree &t, const uint64_t *skey, int n, const int *n_d,
         }
         int nb = (n + 255) / 256;
         cudaMemsetAsync(t.gmark, 0xff, sizeof(int) * (size_t)n, c->s);
-        k_group_mark<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, n_group, t.gmark);
-        k_group_flag<<<nb, 256, 0, c->s>>>(t.gmark, t.gflag, n);
+        gnb::counted(k_group_mark)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, n_group, t.gmark);
+        gnb::counted(k_group_flag)<<<nb, 256, 0, c->s>>>(t.gmark, t.gflag, n);
         GNB_TRY(device_scan(c, t.gflag, t.goff, n_d, n, t.ngroups_d));
-        k_group_compact<<<nb, 256, 0, c->s>>>(t.gmark, t.goff, n, t.groups);
+        gnb::counted(k_group_compact)<<<nb, 256, 0, c->s>>>(t.gmark, t.goff, n, t.groups);
         GNB_LAUNCH_CHECK(c, "groups");
     }
     return GNB_OK;

@@ -83,6 +83,11 @@ def _declare(L):
     L.gnb_stats.argtypes = [_vp, C.POINTER(C.c_int64)]
     L.gnb_last_error.argtypes = [_vp]
     L.gnb_last_error.restype = C.c_char_p
+    L.gnb_set_timing.argtypes = [_vp, C.c_int]
+    L.gnb_set_timing.restype = C.c_int
+    L.gnb_phase_times.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                  C.c_int]
+    L.gnb_phase_times.restype = C.c_int
     for name in ("gnb_create", "gnb_set_particles", "gnb_build_tree", "gnb_compute_gravity",
                  "gnb_compute_sph_density", "gnb_compute_sph_force", "gnb_compute_forces", "gnb_step_kdk",
                  "gnb_get", "gnb_diagnostics", "gnb_stats"):
@@ -145,6 +150,17 @@ def gnb_stats(ctx, out):
 def gnb_last_error(ctx):
     r = lib().gnb_last_error(ctx)
     return r.decode() if r else ""
+
+
+def gnb_set_timing(ctx, enable):
+    return lib().gnb_set_timing(ctx, enable)
+
+
+def gnb_phase_times(ctx, out_ms, calls, launches, reset):
+    return lib().gnb_phase_times(ctx, out_ms, calls, launches, reset)
+
+
+PHASES = ["SORT", "TREE", "GRAVITY", "EXTERNAL", "HYDRO_TREE", "KNN", "FORCE", "KDK"]
 
 
 # -------------------------------------------------------------- convenience wrapper
@@ -275,3 +291,14 @@ class Context:
         out = (C.c_int64 * len(STATS))()
         self._chk(gnb_stats(self.h, out))
         return dict(zip(STATS, out[:]))
+
+    def set_timing(self, enable=True):
+        self._chk(gnb_set_timing(self.h, 1 if enable else 0))
+
+    def phase_times(self, reset=False):
+        """({phase: ms}, {phase: timed occurrences}, library kernel launches)."""
+        ms = (C.c_double * len(PHASES))()
+        calls = (C.c_int64 * len(PHASES))()
+        launches = C.c_int64(0)
+        self._chk(gnb_phase_times(self.h, ms, calls, C.byref(launches), 1 if reset else 0))
+        return dict(zip(PHASES, ms[:])), dict(zip(PHASES, calls[:])), launches.value
