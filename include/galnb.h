@@ -209,6 +209,38 @@ int gnb_set_timing(gnb_ctx *ctx, int enable);
 int gnb_phase_times(gnb_ctx *ctx, double out_ms[GNB_T_COUNT_], int64_t calls[GNB_T_COUNT_],
                     int64_t *launches, int reset);
 
+/* Largest particle count accepted by gnb_morton_order_noalloc. */
+#define GNB_NOALLOC_MAX_N 262144
+
+/* Morton keys and space-filling-curve order of n particles without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory -- an application whose
+ * device memory is owned by another allocator (a framework's caching pool
+ * or a fixed arena), or a latency-sensitive loop in which cudaMalloc and
+ * cudaFree would synchronise the device or could fail under memory
+ * pressure.  It computes exactly what gnb_build_tree computes for the keys
+ * (GNB_F_KEY) and the order (GNB_F_ORDER): root box, 63-bit keys, order by
+ * (key, caller index).
+ *
+ * Scratch: one static device array of 6,424,320 bytes (6.13 MiB) inside
+ * libgalnb.so; every GPU that loads the library holds it until the process
+ * exits.  The first call on a device looks up the array's device address
+ * (with that device current), so make that first call before any stream
+ * capture.  Every call reuses the same array and clears what must start at
+ * zero itself; calls that overlap on the GPU (different streams or host
+ * threads, same device) race and give wrong results.  The call uses no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * x, y, z: device FP64 positions, n each, caller order.  keys: device
+ * uint64[n], written with each particle's key in caller order.  order:
+ * device int64[n], written with the caller index of the particle at each
+ * sorted slot.  stream: cudaStream_t (NULL = default stream); the call
+ * returns after its work on stream has finished.
+ * Errors: GNB_EINVAL (n < 1 or n > GNB_NOALLOC_MAX_N, null pointer, or a
+ * non-finite position -- keys and order are then not valid), GNB_ECUDA. */
+int gnb_morton_order_noalloc(int64_t n, const double *x, const double *y, const double *z,
+                             uint64_t *keys, int64_t *order, void *stream);
+
 /* One-line description of the last error of ctx ("" if none; a static
  * string if ctx is NULL). */
 const char *gnb_last_error(const gnb_ctx *ctx);

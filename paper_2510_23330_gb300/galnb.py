@@ -88,6 +88,8 @@ def _declare(L):
     L.gnb_phase_times.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                   C.c_int]
     L.gnb_phase_times.restype = C.c_int
+    L.gnb_morton_order_noalloc.argtypes = [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.gnb_morton_order_noalloc.restype = C.c_int
     for name in ("gnb_create", "gnb_set_particles", "gnb_build_tree", "gnb_compute_gravity",
                  "gnb_compute_sph_density", "gnb_compute_sph_force", "gnb_compute_forces", "gnb_step_kdk",
                  "gnb_get", "gnb_diagnostics", "gnb_stats"):
@@ -161,6 +163,14 @@ def gnb_phase_times(ctx, out_ms, calls, launches, reset):
 
 
 PHASES = ["SORT", "TREE", "GRAVITY", "EXTERNAL", "HYDRO_TREE", "KNN", "FORCE", "KDK"]
+
+GNB_NOALLOC_MAX_N = 262144
+
+
+def gnb_morton_order_noalloc(n, x, y, z, keys, order, stream):
+    """Keys and curve order of device positions with no device allocation
+    (for callers that cannot allocate); all pointers are device pointers."""
+    return lib().gnb_morton_order_noalloc(n, x, y, z, keys, order, stream)
 
 
 # -------------------------------------------------------------- convenience wrapper
