@@ -202,6 +202,12 @@ def run_ours(args, world, rank, local):
     n = int(p["x"].shape[0])
     ctx = galnb.Context(stream=stream.cuda_stream, **pr["cfg"])
     ctx.set_particles(p)
+    tuning = None
+    if mode == 1 and not args.no_autotune:
+        from paper_2510_23330_gb300 import autotune
+        best, table = autotune.tune_group_size(ctx, mode)
+        pr["cfg"]["n_group"] = best
+        tuning = {str(k): round(v, 4) for k, v in table.items()}
     ctx.compute_forces(mode)
     for _ in range(args.warmup):
         ctx.step_kdk(args.dt, 1, mode)
@@ -255,6 +261,7 @@ def run_ours(args, world, rank, local):
                               f"2070 MHz (FP32 CUDA cores)"),
                      "ms_per_launch": g_ms},
         "interactions_per_step": {"pp": npp / args.steps, "pc": npc / args.steps},
+        "n_group_tuning_ms": tuning,
         "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
         "gpu_launches": int(launches),
         "step_ms": step_ms,
@@ -333,6 +340,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         # the CPU checker runs once, on rank 0; other ranks exit without work

@@ -136,6 +136,12 @@ void gnb_config_default(gnb_config *cfg);
  * Errors: GNB_EINVAL (null or invalid cfg), GNB_ECUDA. */
 int gnb_create(gnb_ctx **out, const gnb_config *cfg);
 
+/* Replace the parameters of a context (same rules as gnb_create).  The
+ * particles are kept; the tree and all forces must be recomputed.  Used to
+ * choose n_group on the data (Sec. 5.2.4: the best n_g depends on the
+ * hardware).  Errors: GNB_EINVAL. */
+int gnb_set_config(gnb_ctx *ctx, const gnb_config *cfg);
+
 /* Free a context and all its device memory (NULL is ignored). */
 void gnb_destroy(gnb_ctx *ctx);
 

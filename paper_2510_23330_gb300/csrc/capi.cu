@@ -216,14 +216,29 @@ void gnb_config_default(gnb_config *cfg)
     cfg->cuda_stream = nullptr;
 }
 
+static bool config_ok(const gnb_config *cfg)
+{
+    return cfg->theta >= 0.0 && cfg->G > 0.0 && cfg->n_leaf >= 1 && cfg->n_leaf <= 255 && cfg->n_group >= 1 &&
+           cfg->n_ngb == 64 && cfg->gamma > 1.0 && cfg->alpha_visc >= 0.0 && cfg->nfw_ms >= 0.0 &&
+           !(cfg->nfw_ms > 0.0 && !(cfg->nfw_rs > 0.0));
+}
+
+int gnb_set_config(gnb_ctx *c, const gnb_config *cfg)
+{
+    if (!c || !cfg) return GNB_EINVAL;
+    if (!config_ok(cfg)) return fail(c, GNB_EINVAL, "invalid configuration");
+    cudaStreamSynchronize(c->s);
+    c->cfg = *cfg;
+    c->s = (cudaStream_t)cfg->cuda_stream;
+    c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    return GNB_OK;
+}
+
 int gnb_create(gnb_ctx **out, const gnb_config *cfg)
 {
     if (!out || !cfg) return GNB_EINVAL;
     *out = nullptr;
-    if (!(cfg->theta >= 0.0) || !(cfg->G > 0.0) || cfg->n_leaf < 1 || cfg->n_leaf > 255 || cfg->n_group < 1 ||
-        cfg->n_ngb != 64 || !(cfg->gamma > 1.0) || !(cfg->alpha_visc >= 0.0) || !(cfg->nfw_ms >= 0.0) ||
-        (cfg->nfw_ms > 0.0 && !(cfg->nfw_rs > 0.0)))
-        return GNB_EINVAL;
+    if (!config_ok(cfg)) return GNB_EINVAL;
     gnb_ctx *c = new (std::nothrow) gnb_ctx();
     if (!c) return GNB_ENOMEM;
     c->cfg = *cfg;

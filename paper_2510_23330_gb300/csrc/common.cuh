@@ -57,6 +57,7 @@ struct Tree {
     float4 *mo1 = nullptr; // {Qxx, Qyy, Qzz, Qxy}
     float4 *mo2 = nullptr; // {Qxz, Qyz, eps2, 0}
     int *lvl = nullptr;    // device: level begin offsets [GNB_MAXLEV + 2]
+    int *cb = nullptr;     // first slot of each child digit of split nodes [8 per node]
     int *partial = nullptr;
     int *poff = nullptr;
     int *gmark = nullptr;  // per particle: node starting a group there, else -1

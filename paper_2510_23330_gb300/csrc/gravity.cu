@@ -191,11 +191,13 @@ __global__ void __launch_bounds__(GW_THREADS, 4) k_gravity_tree(GravParams p)
         for (int i0 = 0; i0 < gcount; i0 += GW_THREADS) {
             const int icnt = min(GW_THREADS, gcount - i0);
             // j-splits: warps share i-particles and split the j loop
-            const int ilanes = ((icnt + 31) >> 5) << 5;
+            // j-splits: each of the js = floor(128 / icnt) thread sets holds all
+            // icnt i-particles and takes every js-th j entry
+            const int ilanes = icnt;
             const int js = GW_THREADS / ilanes;
             const int islot = tid % ilanes, split = tid / ilanes;
-            const bool ivalid = islot < icnt;
-            const int ip = gfirst + i0 + (ivalid ? islot : 0);
+            const bool ivalid = split < js;
+            const int ip = gfirst + i0 + islot;
             const int ci[3] = {p.cx[ip], p.cy[ip], p.cz[ip]};
             const float xi = grid_off(ci[0], gref[0], p.rx[ip], unit);
             const float yi = grid_off(ci[1], gref[1], p.ry[ip], unit);
@@ -330,11 +332,11 @@ __global__ void __launch_bounds__(GW_THREADS, 4) k_gravity_direct(GravParams p)
         const int4 ga = p.na[p.groups[gi]];
         for (int i0 = 0; i0 < ga.y; i0 += GW_THREADS) {
             const int icnt = min(GW_THREADS, ga.y - i0);
-            const int ilanes = ((icnt + 31) >> 5) << 5;
+            const int ilanes = icnt;
             const int js = GW_THREADS / ilanes;
             const int islot = tid % ilanes, split = tid / ilanes;
-            const bool ivalid = islot < icnt;
-            const int ip = ga.x + i0 + (ivalid ? islot : 0);
+            const bool ivalid = split < js;
+            const int ip = ga.x + i0 + islot;
             const int gref[3] = {p.cx[ga.x + i0], p.cy[ga.x + i0], p.cz[ga.x + i0]};
             const float xi = grid_off(p.cx[ip], gref[0], p.rx[ip], unit);
             const float yi = grid_off(p.cy[ip], gref[1], p.ry[ip], unit);

@@ -166,18 +166,30 @@ __global__ void __launch_bounds__(TB_THREADS) k_split_count(Tree t, const uint64
     int nl = le - lb, G = gridDim.x;
     int chunk = (nl + G - 1) / G;
     int beg = lb + blockIdx.x * chunk, end = min(le, beg + chunk);
+    // eight lanes per node, lane d finds the first slot of child digit d, so
+    // the seven binary searches of a node run side by side
+    const int d = threadIdx.x & 7;
+    const int sh = 3 * (GNB_MAXLEV - (l + 1));
     int s = 0;
-    for (int node = beg + threadIdx.x; node < end; node += blockDim.x) {
-        int4 a = t.na[node];
-        int nch = 0;
-        if (a.y > n_leaf && l < GNB_MAXLEV) {
-            int pos[9];
-            child_bounds(k, a.x, a.y, l, pos);
-#pragma unroll
-            for (int d = 0; d < 8; d++) nch += pos[d + 1] > pos[d];
+    for (int b0 = beg; b0 < end; b0 += blockDim.x >> 3) {
+        int node = b0 + (threadIdx.x >> 3);
+        bool live = node < end;
+        int4 a = live ? t.na[node] : make_int4(0, 0, 0, 0);
+        bool split = live && a.y > n_leaf && l < GNB_MAXLEV;
+        int pos = a.x;
+        if (split && d > 0) {
+            uint64_t base = (k[a.x] >> (sh + 3)) << (sh + 3);
+            pos = lower_bound_key(k, a.x, a.x + a.y, base | ((uint64_t)d << sh));
         }
-        t.na[node].w = (nch << 8) | l;
-        s += nch;
+        int nxt = __shfl_down_sync(0xffffffffu, pos, 1, 8);
+        if (d == 7) nxt = a.x + a.y;
+        unsigned ne = __ballot_sync(0xffffffffu, split && nxt > pos);
+        int nch = __popc((ne >> (threadIdx.x & 24)) & 0xffu);
+        if (split) t.cb[(size_t)node * 8 + d] = pos;
+        if (live && d == 0) {
+            t.na[node].w = (nch << 8) | l;
+            s += nch;
+        }
     }
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
@@ -234,34 +246,44 @@ __global__ void __launch_bounds__(TB_THREADS) k_emit(Tree t, const uint64_t *__r
     int beg = lb + blockIdx.x * chunk, end = min(le, beg + chunk);
     int carry = le + t.poff[blockIdx.x];
     int side = 1 << (GNB_MAXLEV - (l + 1));
-    for (int b0 = beg; b0 < end; b0 += blockDim.x) {
-        int node = b0 + threadIdx.x;
-        int nch = 0;
-        int4 a = make_int4(0, 0, 0, 0);
-        if (node < end) {
-            a = t.na[node];
-            nch = a.w >> 8;
-        }
-        int tot;
-        int e = block_excl_scan(nch, ws, &tot);
-        if (nch > 0) {
-            int base = carry + e;
-            t.na[node].z = base;
-            int4 cb = t.nb[node];
-            int pos[9];
-            child_bounds(k, a.x, a.y, l, pos);
-            int q = 0;
-#pragma unroll
-            for (int d = 0; d < 8; d++) {
-                if (pos[d + 1] > pos[d]) {
-                    t.na[base + q] = make_int4(pos[d], pos[d + 1] - pos[d], -1, l + 1);
-                    t.nb[base + q] = make_int4(cb.x + ((d >> 2) & 1) * side, cb.y + ((d >> 1) & 1) * side,
-                                               cb.z + (d & 1) * side, node);
-                    q++;
-                }
+    // eight lanes per node (lane d = child digit d), 32 nodes per iteration
+    __shared__ int s_n[32], s_ex[33];
+    const int d = threadIdx.x & 7, j = threadIdx.x >> 3;
+    (void)ws;
+    for (int b0 = beg; b0 < end; b0 += blockDim.x >> 3) {
+        int node = b0 + j;
+        bool live = node < end;
+        int4 a = live ? t.na[node] : make_int4(0, 0, 0, 0);
+        int nch = live ? (a.w >> 8) : 0;
+        int pos = nch > 0 ? t.cb[(size_t)node * 8 + d] : 0;
+        int nxt = __shfl_down_sync(0xffffffffu, pos, 1, 8);
+        if (d == 7) nxt = a.x + a.y;
+        bool ne = nch > 0 && nxt > pos;
+        unsigned bal = __ballot_sync(0xffffffffu, ne);
+        unsigned mine = (bal >> (threadIdx.x & 24)) & 0xffu;
+        if (d == 0) s_n[j] = nch;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int v = s_n[threadIdx.x], x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (threadIdx.x >= o) x += y;
             }
+            s_ex[threadIdx.x] = x - v;
+            if (threadIdx.x == 31) s_ex[32] = x;
         }
-        carry += tot;
+        __syncthreads();
+        int base = carry + s_ex[j];
+        if (nch > 0 && d == 0) t.na[node].z = base;
+        if (ne) {
+            int q = __popc(mine & ((1u << d) - 1u));
+            int4 cbn = t.nb[node];
+            t.na[base + q] = make_int4(pos, nxt - pos, -1, l + 1);
+            t.nb[base + q] = make_int4(cbn.x + ((d >> 2) & 1) * side, cbn.y + ((d >> 1) & 1) * side,
+                                       cbn.z + (d & 1) * side, node);
+        }
+        carry += s_ex[32];
+        __syncthreads();
     }
 }
 
@@ -378,7 +400,7 @@ __global__ void k_group_compact(const int *__restrict__ mark, const int *__restr
 int tree_alloc(gnb_ctx *c, Tree &t, int cap)
 {
     // node arrays only; the per-particle group scratch survives a regrow
-    dfree(c, t.na); dfree(c, t.nb); dfree(c, t.mo0); dfree(c, t.mo1); dfree(c, t.mo2);
+    dfree(c, t.na); dfree(c, t.nb); dfree(c, t.mo0); dfree(c, t.mo1); dfree(c, t.mo2); dfree(c, t.cb);
     dfree(c, t.lvl); dfree(c, t.partial); dfree(c, t.poff); dfree(c, t.ngroups_d);
     t.cap = cap;
     GNB_TRY(dalloc(c, &t.na, cap));
@@ -386,6 +408,7 @@ int tree_alloc(gnb_ctx *c, Tree &t, int cap)
     GNB_TRY(dalloc(c, &t.mo0, cap));
     GNB_TRY(dalloc(c, &t.mo1, cap));
     GNB_TRY(dalloc(c, &t.mo2, cap));
+    GNB_TRY(dalloc(c, &t.cb, (size_t)cap * 8));
     GNB_TRY(dalloc(c, &t.lvl, GNB_MAXLEV + 4));
     GNB_TRY(dalloc(c, &t.partial, 1100));
     GNB_TRY(dalloc(c, &t.poff, 1100));
@@ -395,7 +418,7 @@ int tree_alloc(gnb_ctx *c, Tree &t, int cap)
 
 void tree_free(gnb_ctx *c, Tree &t)
 {
-    dfree(c, t.na); dfree(c, t.nb); dfree(c, t.mo0); dfree(c, t.mo1); dfree(c, t.mo2);
+    dfree(c, t.na); dfree(c, t.nb); dfree(c, t.mo0); dfree(c, t.mo1); dfree(c, t.mo2); dfree(c, t.cb);
     dfree(c, t.lvl); dfree(c, t.partial); dfree(c, t.poff); dfree(c, t.gmark); dfree(c, t.gflag);
     dfree(c, t.goff); dfree(c, t.groups); dfree(c, t.ngroups_d);
     t = Tree();

@@ -90,6 +90,8 @@ def _declare(L):
     L.gnb_phase_times.restype = C.c_int
     L.gnb_morton_order_noalloc.argtypes = [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gnb_morton_order_noalloc.restype = C.c_int
+    L.gnb_set_config.argtypes = [_vp, C.POINTER(gnb_config)]
+    L.gnb_set_config.restype = C.c_int
     for name in ("gnb_create", "gnb_set_particles", "gnb_build_tree", "gnb_compute_gravity",
                  "gnb_compute_sph_density", "gnb_compute_sph_force", "gnb_compute_forces", "gnb_step_kdk",
                  "gnb_get", "gnb_diagnostics", "gnb_stats"):
@@ -107,6 +109,10 @@ def gnb_create(out, cfg):
 
 def gnb_destroy(ctx):
     lib().gnb_destroy(ctx)
+
+
+def gnb_set_config(ctx, cfg):
+    return lib().gnb_set_config(ctx, C.byref(cfg))
 
 
 def gnb_set_particles(ctx, n, id, type, x, y, z, vx, vy, vz, m, eps, u, on_device):
@@ -301,6 +307,14 @@ class Context:
         out = (C.c_int64 * len(STATS))()
         self._chk(gnb_stats(self.h, out))
         return dict(zip(STATS, out[:]))
+
+    def set_params(self, **params):
+        """Change configuration fields (tree and forces are recomputed later)."""
+        for k, v in params.items():
+            if not hasattr(self.cfg, k):
+                raise KeyError(k)
+            setattr(self.cfg, k, v)
+        self._chk(gnb_set_config(self.h, self.cfg))
 
     def set_timing(self, enable=True):
         self._chk(gnb_set_timing(self.h, 1 if enable else 0))
