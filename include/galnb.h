@@ -55,6 +55,7 @@ extern "C" {
 /* Gravity modes of gnb_compute_gravity / gnb_step_kdk. */
 #define GNB_GRAV_DIRECT 0  /* O(N^2) sum of Eq. 1 over all particles */
 #define GNB_GRAV_TREE 1    /* Barnes-Hut group walk, particle-particle + particle-cell */
+#define GNB_GRAV_NONE 2    /* no self-gravity (e.g. a supernova region evolved for 0.1 Myr) */
 
 typedef struct gnb_ctx gnb_ctx;
 
@@ -188,6 +189,31 @@ int gnb_compute_forces(gnb_ctx *ctx, int gravity_mode);
  * first if they are not current.  Errors: GNB_EINVAL (dt not finite,
  * nsteps < 0, mode), GNB_ESTATE, GNB_ECAPACITY, GNB_ECUDA. */
 int gnb_step_kdk(gnb_ctx *ctx, double dt, int nsteps, int gravity_mode);
+
+/* Supernova energy injection (Sec. 1: 10^51 erg per explosion; the injection
+ * rule is a reading): thermal energy `energy` is added to the n_ngb gas
+ * particles nearest to pos (ordered by FP64 d^2, then gas rank) with cubic
+ * spline weights whose support is the distance to the n_ngb-th of them:
+ * du_j = energy W_j / (m_j sum_k W_k).  info (may be NULL) receives
+ * {sum of weights, energy actually added (FP64 sum of m du after rounding u
+ * to FP32), support h, particles heated}.  Errors: GNB_EINVAL, GNB_ESTATE
+ * (no particles or fewer gas particles than n_ngb), GNB_ECUDA. */
+int gnb_inject_energy(gnb_ctx *ctx, const double pos[3], double energy, double info[4]);
+
+/* Shared CFL timestep of the last SPH force pass (Sec. 1: the CFL condition
+ * limits the hydro timestep): dt = courant * min_i h_i / vsig_i, vsig_i =
+ * max_j (c_i + c_j - 3 min(w_ij, 0)).  Errors: GNB_EINVAL, GNB_ESTATE (no SPH
+ * force at the current positions). */
+int gnb_cfl_timestep(gnb_ctx *ctx, double courant, double *dt);
+
+/* Plain small-timestep integration (the conventional integration of Sec. 3.2
+ * and 5.3 that the surrogate replaces): kick-drift-kick steps of the CFL
+ * timestep above, the last one shortened to end exactly at t_span, at most
+ * max_steps steps.  t_done and steps_done (may be NULL) receive the time
+ * covered and the steps taken.  Errors: GNB_EINVAL, GNB_ESTATE (no gas),
+ * GNB_ECAPACITY, GNB_ECUDA. */
+int gnb_integrate_cfl(gnb_ctx *ctx, double t_span, double courant, int max_steps, int gravity_mode,
+                      double *t_done, int64_t *steps_done);
 
 /* Copy one field into dst, which holds cap elements of the field's type.
  * Errors: GNB_EINVAL (field, cap too small, null dst), GNB_ESTATE (field

@@ -89,6 +89,7 @@ def _declare(L):
                                 + [_d] * 5)
     L.orc_sph_force.restype = C.c_int
     L.orc_num_threads.restype = C.c_int
+    L.orc_sph_vsig.argtypes = [C.c_int64] + [_d] * 7 + [C.c_int, _i64, _d]
 
 
 def _p(a, dtype):
@@ -323,12 +324,25 @@ def sph_force(g: dict, nbr, h2, rho, P, c, alpha: float = 1.0, v=None):
     return out
 
 
+def sph_vsig(g: dict, nbr, c, v=None):
+    """Largest pair signal velocity c_i + c_j - 3 min(w_ij, 0) per particle."""
+    n, k = nbr.shape
+    x, y, z = (f64(g[a]) for a in ("x", "y", "z"))
+    if v is None:
+        v = (g["vx"], g["vy"], g["vz"])
+    vx, vy, vz = (f64(a) for a in v)
+    out = np.zeros(n)
+    lib().orc_sph_vsig(n, *(_p(a, np.float64) for a in (x, y, z, vx, vy, vz, f64(c))), k,
+                       _p(np.ascontiguousarray(nbr, dtype=np.int64), np.int64), _p(out, np.float64))
+    return out
+
+
 def sph(g: dict, k: int = 64, gamma: float = 5.0 / 3.0, alpha: float = 1.0, u=None, v=None):
     """kNN + density + force for a gas-only particle set."""
     nbr, h2 = knn(g, k)
     rho, P, c = density(g, nbr, h2, gamma, u=u)
     f = sph_force(g, nbr, h2, rho, P, c, alpha, v=v)
-    f.update(nbr=nbr, h2=h2, rho=rho, P=P, c=c)
+    f.update(nbr=nbr, h2=h2, rho=rho, P=P, c=c, vsig=sph_vsig(g, nbr, c, v=v))
     return f
 
 
@@ -365,6 +379,8 @@ def forces(s: dict, cfg: Config, u=None, v=None) -> dict:
     n = s["x"].shape[0]
     if cfg.gravity == "direct":
         g = direct_gravity(s, cfg.G)
+    elif cfg.gravity == "none":
+        g = {k: np.zeros(n) for k in ("ax", "ay", "az", "phi", "asum")}
     else:
         g = tree_gravity(s, cfg.theta, cfg.n_leaf, cfg.n_g, cfg.quad, cfg.G)
     ax, ay, az = g["ax"].copy(), g["ay"].copy(), g["az"].copy()
@@ -435,3 +451,49 @@ def diagnostics(s: dict, f: dict) -> np.ndarray:
     L = [np.sum(m * (y * vz - z * vy)), np.sum(m * (z * vx - x * vz)),
          np.sum(m * (x * vy - y * vx))]
     return np.array([ek, ep, ee, eth, *P, *L])
+
+
+# --------------------------------------------------------------------------
+# Supernova region: injection and plain CFL-limited integration
+# --------------------------------------------------------------------------
+def inject_energy(s: dict, pos, E: float, k: int = 64):
+    """Thermal energy E into the k gas particles nearest to pos (ordered by
+    FP64 d^2 = (dx*dx + dy*dy) + dz*dz, then gas rank), weighted by the cubic
+    spline with support h = distance to the k-th: du_j = E W_j/(m_j sum W).
+    Returns the new state and {h, members, energy_added}."""
+    gi = np.nonzero(s["type"] == GAS)[0]
+    dx, dy, dz = (s[a][gi] - float(pos[i]) for i, a in enumerate(("x", "y", "z")))
+    d2 = (dx * dx + dy * dy) + dz * dz
+    order = np.lexsort((np.arange(gi.size), d2))[:k]
+    h = float(np.sqrt(d2[order[-1]]))
+    r = np.sqrt(d2[order])
+    if h > 0:
+        w, _ = kernel(r, h)
+    else:
+        w = np.ones(k)
+    ns = dict(s)
+    ns["u"] = s["u"].copy()
+    members = gi[order]
+    du = E * w / (s["m"][members] * w.sum())
+    ns["u"][members] += du
+    return ns, {"h": h, "members": members, "energy_added": float(np.sum(s["m"][members] * du)),
+                "weights_sum": float(w.sum())}
+
+
+def cfl_dt(f: dict, courant: float = 0.3) -> float:
+    """dt = courant * min_i h_i / vsig_i over the gas of a force evaluation."""
+    h = np.sqrt(f["sph"]["h2"])
+    return float(courant * np.min(h / f["sph"]["vsig"]))
+
+
+def integrate_cfl(s: dict, t_span: float, courant: float, cfg: Config, max_steps: int = 1 << 30):
+    """Plain small-timestep integration: KDK steps of the CFL timestep, the
+    last one shortened to end at t_span.  Returns (state, forces, t, steps)."""
+    f = forces(s, cfg)
+    t, n = 0.0, 0
+    while t < t_span and n < max_steps:
+        dt = min(cfl_dt(f, courant), t_span - t)
+        s, f = kdk_step(s, f, dt, cfg)
+        t += dt
+        n += 1
+    return s, f, t, n

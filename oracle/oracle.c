@@ -682,3 +682,29 @@ void orc_direct_gravity_sample(int64_t n, const double *x, const double *y, cons
         ax[s] = sx; ay[s] = sy; az[s] = sz; phi[s] = sp; asum[s] = sa;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Largest signal velocity of each gas particle over its symmetric pairs    */
+/* S_i (the CFL condition of Sec. 1; the signal velocity is a reading):      */
+/*   vsig_i = max(2 c_i, max_j c_i + c_j - 3 min(w_ij, 0)).                  */
+/* ------------------------------------------------------------------------ */
+void orc_sph_vsig(int64_t n, const double *x, const double *y, const double *z,
+                  const double *vx, const double *vy, const double *vz, const double *c,
+                  int k, const int64_t *nbr, double *vsig)
+{
+    for (int64_t i = 0; i < n; i++) vsig[i] = 2.0 * c[i];
+    for (int64_t i = 0; i < n; i++) {
+        for (int t = 0; t < k; t++) {
+            int64_t j = nbr[i * k + t];
+            if (j == i) continue;
+            double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double w = 0.0;
+            if (r > 0) w = ((vx[i] - vx[j]) * dx + (vy[i] - vy[j]) * dy + (vz[i] - vz[j]) * dz) / r;
+            double v = c[i] + c[j] - 3.0 * (w < 0.0 ? w : 0.0);
+            /* the pair belongs to S_i and to S_j */
+            if (v > vsig[i]) vsig[i] = v;
+            if (v > vsig[j]) vsig[j] = v;
+        }
+    }
+}

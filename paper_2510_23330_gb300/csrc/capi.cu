@@ -79,14 +79,14 @@ static void free_gas(gnb_ctx *c)
     void *all[] = {c->gslot, c->gkey, c->gcx, c->gcy, c->gcz, c->ggrank, c->grx, c->gry, c->grz, c->gx, c->gy,
                    c->gz, c->gm, c->gvx, c->gvy, c->gvz, c->gu, c->gh2, c->gh, c->g64, c->grho, c->gP, c->gcs,
                    c->gRprev, c->gE, c->nbr, c->nd2, c->mut, c->rcnt, c->roff, c->rfill, c->rlist, c->hax,
-                   c->hay, c->haz, c->hdu, c->kflag, c->kR, c->kRb, c->kitem};
+                   c->hay, c->haz, c->hdu, c->kflag, c->kR, c->kRb, c->kitem, c->gvsig};
     for (void *q : all) dfree(c, q);
     c->gslot = nullptr; c->gkey = nullptr; c->gcx = c->gcy = c->gcz = c->ggrank = nullptr;
     c->grx = c->gry = c->grz = nullptr; c->gx = c->gy = c->gz = nullptr;
     c->gm = c->gvx = c->gvy = c->gvz = c->gu = nullptr; c->gh2 = nullptr; c->gh = nullptr; c->g64 = nullptr;
     c->grho = c->gP = c->gcs = c->gRprev = c->gE = nullptr; c->nbr = nullptr; c->nd2 = nullptr; c->mut = nullptr;
     c->rcnt = c->roff = c->rfill = c->rlist = nullptr; c->hax = c->hay = c->haz = c->hdu = nullptr;
-    c->kflag = nullptr; c->kR = nullptr; c->kRb = nullptr; c->kitem = nullptr;
+    c->kflag = nullptr; c->kR = nullptr; c->kRb = nullptr; c->kitem = nullptr; c->gvsig = nullptr;
     tree_free(c, c->gt);
     c->gcap = 0;
 }
@@ -128,7 +128,7 @@ static int alloc_gas(gnb_ctx *c, int64_t ng)
     GNB_TRY(dalloc(c, &c->gvz, G)); GNB_TRY(dalloc(c, &c->gu, G));
     GNB_TRY(dalloc(c, &c->gh2, G)); GNB_TRY(dalloc(c, &c->gh, G)); GNB_TRY(dalloc(c, &c->g64, G));
     GNB_TRY(dalloc(c, &c->grho, G)); GNB_TRY(dalloc(c, &c->gP, G)); GNB_TRY(dalloc(c, &c->gcs, G));
-    GNB_TRY(dalloc(c, &c->gRprev, G)); GNB_TRY(dalloc(c, &c->gE, G));
+    GNB_TRY(dalloc(c, &c->gRprev, G)); GNB_TRY(dalloc(c, &c->gE, G)); GNB_TRY(dalloc(c, &c->gvsig, G));
     GNB_TRY(dalloc(c, &c->nbr, G * 64)); GNB_TRY(dalloc(c, &c->nd2, G * 64)); GNB_TRY(dalloc(c, &c->mut, G));
     GNB_TRY(dalloc(c, &c->rcnt, G + 1)); GNB_TRY(dalloc(c, &c->roff, G + 1)); GNB_TRY(dalloc(c, &c->rfill, G + 1));
     GNB_TRY(dalloc(c, &c->rlist, G * 64));
@@ -338,6 +338,11 @@ namespace gnb {
 
 std::atomic<long long> g_launches{0};
 
+static bool mode_ok(int mode)
+{
+    return mode == GNB_GRAV_DIRECT || mode == GNB_GRAV_TREE || mode == GNB_GRAV_NONE;
+}
+
 static cudaEvent_t ev_get(gnb_ctx *c)
 {
     if (!c->evpool.empty()) {
@@ -426,8 +431,15 @@ static int do_gravity(gnb_ctx *c, int mode)
 {
     cudaMemsetAsync(c->counters_d, 0, 2 * sizeof(unsigned long long), c->s);
     phase_begin(c, GNB_T_GRAVITY);
-    if (mode == GNB_GRAV_TREE) GNB_TRY(gravity_tree(c));
-    else GNB_TRY(gravity_direct(c));
+    if (mode == GNB_GRAV_TREE) {
+        GNB_TRY(gravity_tree(c));
+    } else if (mode == GNB_GRAV_DIRECT) {
+        GNB_TRY(gravity_direct(c));
+    } else {  // GNB_GRAV_NONE: no self-gravity
+        size_t b = sizeof(float) * (size_t)c->n;
+        cudaMemsetAsync(c->gax, 0, b, c->s); cudaMemsetAsync(c->gay, 0, b, c->s);
+        cudaMemsetAsync(c->gaz, 0, b, c->s); cudaMemsetAsync(c->pot, 0, b, c->s);
+    }
     phase_begin(c, GNB_T_EXTERNAL);
     GNB_TRY(gravity_nfw(c));
     GNB_TRY(zero_forces(c));
@@ -447,6 +459,25 @@ static int do_forces(gnb_ctx *c, int mode)
     c->force_valid = true;
     c->sphf_valid = true;
     return GNB_OK;
+}
+
+// One kick-drift-kick step; forces at the start of the step must be current.
+static int kdk_one(gnb_ctx *c, double dt, int mode)
+{
+    float hdt = (float)(0.5 * dt);
+    phase_begin(c, GNB_T_KDK);
+    int rc = kick(c, hdt, true);
+    if (rc == GNB_OK) rc = drift(c, dt);
+    if (rc == GNB_OK) rc = predict(c, hdt);
+    phase_end(c);
+    c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    c->use_pred = true;
+    if (rc == GNB_OK) rc = do_forces(c, mode);
+    c->use_pred = false;
+    phase_begin(c, GNB_T_KDK);
+    if (rc == GNB_OK) rc = kick(c, hdt, true);
+    phase_end(c);
+    return rc;
 }
 
 static int finish(gnb_ctx *c, int rc)
@@ -482,7 +513,7 @@ int gnb_compute_gravity(gnb_ctx *c, int mode)
 {
     if (!c) return GNB_EINVAL;
     c->err.clear();
-    if (mode != GNB_GRAV_DIRECT && mode != GNB_GRAV_TREE) return fail(c, GNB_EINVAL, "gravity mode");
+    if (!mode_ok(mode)) return fail(c, GNB_EINVAL, "gravity mode");
     if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
     int rc = GNB_OK;
     if (!c->tree_valid) rc = do_build(c);
@@ -525,7 +556,7 @@ int gnb_compute_forces(gnb_ctx *c, int mode)
 {
     if (!c) return GNB_EINVAL;
     c->err.clear();
-    if (mode != GNB_GRAV_DIRECT && mode != GNB_GRAV_TREE) return fail(c, GNB_EINVAL, "gravity mode");
+    if (!mode_ok(mode)) return fail(c, GNB_EINVAL, "gravity mode");
     if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
     int rc = do_forces(c, mode);
     if (rc == GNB_OK) rc = read_groups(c);
@@ -537,28 +568,77 @@ int gnb_step_kdk(gnb_ctx *c, double dt, int nsteps, int mode)
     if (!c) return GNB_EINVAL;
     c->err.clear();
     if (!std::isfinite(dt) || nsteps < 0) return fail(c, GNB_EINVAL, "dt or nsteps");
-    if (mode != GNB_GRAV_DIRECT && mode != GNB_GRAV_TREE) return fail(c, GNB_EINVAL, "gravity mode");
+    if (!mode_ok(mode)) return fail(c, GNB_EINVAL, "gravity mode");
     if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
     int rc = GNB_OK;
     if (!c->force_valid || c->last_grav_mode != mode) {
         rc = do_forces(c, mode);
         if (rc != GNB_OK) return finish(c, rc);
     }
-    float hdt = (float)(0.5 * dt);
-    for (int s = 0; s < nsteps && rc == GNB_OK; s++) {
-        phase_begin(c, GNB_T_KDK);
-        rc = kick(c, hdt, true);
-        if (rc == GNB_OK) rc = drift(c, dt);
-        if (rc == GNB_OK) rc = predict(c, hdt);
-        phase_end(c);
-        c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
-        c->use_pred = true;
-        if (rc == GNB_OK) rc = do_forces(c, mode);
-        c->use_pred = false;
-        phase_begin(c, GNB_T_KDK);
-        if (rc == GNB_OK) rc = kick(c, hdt, true);
-        phase_end(c);
+    for (int s = 0; s < nsteps && rc == GNB_OK; s++) rc = kdk_one(c, dt, mode);
+    if (rc == GNB_OK) rc = read_groups(c);
+    return finish(c, rc);
+}
+
+int gnb_inject_energy(gnb_ctx *c, const double pos[3], double energy, double info[4])
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!pos || !std::isfinite(pos[0]) || !std::isfinite(pos[1]) || !std::isfinite(pos[2]) ||
+        !std::isfinite(energy) || energy < 0.0)
+        return fail(c, GNB_EINVAL, "position or energy");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    if (c->n_gas < c->cfg.n_ngb) return fail(c, GNB_ESTATE, "fewer gas particles than neighbours");
+    double out[4] = {0, 0, 0, 0};
+    int rc = inject_energy(c, pos, energy, out);
+    if (info) for (int k = 0; k < 4; k++) info[k] = out[k];
+    // pressure and forces depend on u
+    c->density_valid = c->force_valid = c->sphf_valid = false;
+    return finish(c, rc);
+}
+
+int gnb_cfl_timestep(gnb_ctx *c, double courant, double *dt)
+{
+    if (!c || !dt) return GNB_EINVAL;
+    c->err.clear();
+    if (!(courant > 0.0)) return fail(c, GNB_EINVAL, "courant factor");
+    if (!c->sphf_valid) return fail(c, GNB_ESTATE, "SPH force not computed");
+    double m = 0.0;
+    int rc = cfl_min_h_over_vsig(c, &m);
+    *dt = courant * m;
+    return finish(c, rc);
+}
+
+int gnb_integrate_cfl(gnb_ctx *c, double t_span, double courant, int max_steps, int mode, double *t_done,
+                      int64_t *steps_done)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!(t_span >= 0.0) || !std::isfinite(t_span) || !(courant > 0.0) || max_steps < 0)
+        return fail(c, GNB_EINVAL, "t_span, courant or max_steps");
+    if (!mode_ok(mode)) return fail(c, GNB_EINVAL, "gravity mode");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    if (c->n_gas == 0) return fail(c, GNB_ESTATE, "no gas: the CFL timestep is undefined");
+    int rc = GNB_OK;
+    if (!c->force_valid || c->last_grav_mode != mode) rc = do_forces(c, mode);
+    double t = 0.0;
+    int64_t steps = 0;
+    while (rc == GNB_OK && t < t_span && steps < max_steps) {
+        double m = 0.0;
+        rc = cfl_min_h_over_vsig(c, &m);
+        if (rc != GNB_OK) break;
+        double dt = courant * m;
+        if (!(dt > 0.0) || !std::isfinite(dt)) {
+            rc = fail(c, GNB_EINVAL, "CFL timestep is not positive");
+            break;
+        }
+        if (dt > t_span - t) dt = t_span - t;
+        rc = kdk_one(c, dt, mode);
+        t += dt;
+        steps++;
     }
+    if (t_done) *t_done = t;
+    if (steps_done) *steps_done = steps;
     if (rc == GNB_OK) rc = read_groups(c);
     return finish(c, rc);
 }

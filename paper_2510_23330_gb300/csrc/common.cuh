@@ -131,6 +131,7 @@ struct gnb_ctx {
     float *grho = nullptr, *gP = nullptr, *gcs = nullptr;
     float *gRprev = nullptr;      // search radius hint per gas particle
     float *gE = nullptr;          // FP32 distance error bound used for the particle's list
+    float *gvsig = nullptr;       // largest pair signal velocity of the last force pass
     unsigned long long *mut = nullptr;  // per gas particle: mutual-neighbour bits
     int *nbr = nullptr;           // n_gas * 64 gas indices
     float *nd2 = nullptr;         // n_gas * 64 FP32 d^2
@@ -216,6 +217,9 @@ int gravity_nfw(gnb_ctx *c);
 // sph.cu
 int sph_density(gnb_ctx *c);
 int sph_force(gnb_ctx *c);
+// sn.cu
+int inject_energy(gnb_ctx *c, const double pos[3], double E, double out[4]);
+int cfl_min_h_over_vsig(gnb_ctx *c, double *out);
 // integrate.cu
 int kick(gnb_ctx *c, float hdt, bool gas_u);
 int drift(gnb_ctx *c, double dt);

@@ -561,12 +561,13 @@ struct ForceParams {
     const double *box;
     float alpha;
     float *ax, *ay, *az, *du;
+    float *vsig;  // largest signal velocity c_i + c_j - 3 min(w_ij, 0) over the pairs of i
 };
 
 __device__ __forceinline__ void pair_force(const ForceParams &p, int i, int j, float unit, int ci0, int ci1, int ci2,
                                            float ri0, float ri1, float ri2, float vi0, float vi1, float vi2,
                                            float hinv_i, float pi_, float rhoi, float csi, float &a0, float &a1,
-                                           float &a2, float &du)
+                                           float &a2, float &du, float &vs)
 {
     float dx = __fmaf_rn((float)(ci0 - p.gcx[j]), unit, ri0 - p.grx[j]);
     float dy = __fmaf_rn((float)(ci1 - p.gcy[j]), unit, ri1 - p.gry[j]);
@@ -581,10 +582,9 @@ __device__ __forceinline__ void pair_force(const ForceParams &p, int i, int j, f
     float vx = vi0 - p.gvx[j], vy = vi1 - p.gvy[j], vz = vi2 - p.gvz[j];
     float w = (vx * dx + vy * dy + vz * dz) * rinv;
     float visc = 0.f;
-    if (w < 0.f) {
-        float vsig = csi + p.cs[j] - 3.f * w;
-        visc = -0.5f * p.alpha * vsig * w / (0.5f * (rhoi + rhoj));
-    }
+    float vsig = csi + p.cs[j] - 3.f * fminf(w, 0.f);
+    vs = fmaxf(vs, vsig);
+    if (w < 0.f) visc = -0.5f * p.alpha * vsig * w / (0.5f * (rhoi + rhoj));
     float dwbar = 0.5f * (dwi + dwj);
     float mj = p.gm[j];
     float f = mj * (pi_ * dwi + pj_ * dwj + visc * dwbar) * rinv;
@@ -604,21 +604,23 @@ __global__ void k_force(ForceParams p)
     float vi0 = p.gvx[i], vi1 = p.gvy[i], vi2 = p.gvz[i];
     float hinv = 1.f / p.h[i], rhoi = p.rho[i], csi = p.cs[i];
     float pi_ = p.P[i] / (rhoi * rhoi);
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, du = 0.f;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, du = 0.f, vs = 2.f * csi;
     const int *nb = p.nbr + (size_t)i * NGB;
     for (int k = 0; k < NGB; k++) {
         int j = nb[k];
         if (j == i) continue;
-        pair_force(p, i, j, unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1, a2, du);
+        pair_force(p, i, j, unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1, a2, du,
+                   vs);
     }
     int b = p.roff[i], e = b + p.rcnt[i];
     for (int k = b; k < e; k++)
         pair_force(p, i, p.rlist[k], unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1,
-                   a2, du);
+                   a2, du, vs);
     p.ax[i] = a0;
     p.ay[i] = a1;
     p.az[i] = a2;
     p.du[i] = du;
+    p.vsig[i] = vs;
 }
 
 // hydro results back to particle slots
@@ -747,7 +749,7 @@ int sph_force(gnb_ctx *c)
     p.gcx = c->gcx; p.gcy = c->gcy; p.gcz = c->gcz; p.grx = c->grx; p.gry = c->gry; p.grz = c->grz;
     p.gm = c->gm; p.gvx = c->gvx; p.gvy = c->gvy; p.gvz = c->gvz; p.h = c->gh; p.rho = c->grho; p.P = c->gP;
     p.cs = c->gcs; p.box = c->box_d; p.alpha = (float)c->cfg.alpha_visc;
-    p.ax = c->hax; p.ay = c->hay; p.az = c->haz; p.du = c->hdu;
+    p.ax = c->hax; p.ay = c->hay; p.az = c->haz; p.du = c->hdu; p.vsig = c->gvsig;
     gnb::counted(k_force)<<<(ng + 127) / 128, 128, 0, c->s>>>(p);
     gnb::counted(k_gas_scatter)<<<gb, 256, 0, c->s>>>(ng, c->gslot, c->hax, c->hay, c->haz, c->hdu, c->ax, c->ay, c->az,
                                         c->dudt);

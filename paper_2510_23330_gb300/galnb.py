@@ -29,6 +29,7 @@ GNB_STAR = 0
 GNB_GAS = 1
 GNB_GRAV_DIRECT = 0
 GNB_GRAV_TREE = 1
+GNB_GRAV_NONE = 2
 
 FIELDS = ["X", "Y", "Z", "VX", "VY", "VZ", "AX", "AY", "AZ", "POT", "U", "DUDT", "RHO", "PRES", "CS", "H2",
           "KEY", "ORDER", "NBR", "NODES", "GROUPS", "ID", "AGRAV_X", "AGRAV_Y", "AGRAV_Z"]
@@ -92,6 +93,13 @@ def _declare(L):
     L.gnb_morton_order_noalloc.restype = C.c_int
     L.gnb_set_config.argtypes = [_vp, C.POINTER(gnb_config)]
     L.gnb_set_config.restype = C.c_int
+    L.gnb_inject_energy.argtypes = [_vp, C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_double)]
+    L.gnb_inject_energy.restype = C.c_int
+    L.gnb_cfl_timestep.argtypes = [_vp, C.c_double, C.POINTER(C.c_double)]
+    L.gnb_cfl_timestep.restype = C.c_int
+    L.gnb_integrate_cfl.argtypes = [_vp, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int64)]
+    L.gnb_integrate_cfl.restype = C.c_int
     for name in ("gnb_create", "gnb_set_particles", "gnb_build_tree", "gnb_compute_gravity",
                  "gnb_compute_sph_density", "gnb_compute_sph_force", "gnb_compute_forces", "gnb_step_kdk",
                  "gnb_get", "gnb_diagnostics", "gnb_stats"):
@@ -158,6 +166,18 @@ def gnb_stats(ctx, out):
 def gnb_last_error(ctx):
     r = lib().gnb_last_error(ctx)
     return r.decode() if r else ""
+
+
+def gnb_inject_energy(ctx, pos, energy, info):
+    return lib().gnb_inject_energy(ctx, pos, energy, info)
+
+
+def gnb_cfl_timestep(ctx, courant, dt):
+    return lib().gnb_cfl_timestep(ctx, courant, dt)
+
+
+def gnb_integrate_cfl(ctx, t_span, courant, max_steps, gravity_mode, t_done, steps_done):
+    return lib().gnb_integrate_cfl(ctx, t_span, courant, max_steps, gravity_mode, t_done, steps_done)
 
 
 def gnb_set_timing(ctx, enable):
@@ -307,6 +327,27 @@ class Context:
         out = (C.c_int64 * len(STATS))()
         self._chk(gnb_stats(self.h, out))
         return dict(zip(STATS, out[:]))
+
+    def inject_energy(self, pos, energy):
+        """Thermal energy into the n_ngb nearest gas particles; returns
+        {weights_sum, energy_added, h, heated}."""
+        p = (C.c_double * 3)(*[float(v) for v in pos])
+        info = (C.c_double * 4)()
+        self._chk(gnb_inject_energy(self.h, p, float(energy), info))
+        return dict(zip(("weights_sum", "energy_added", "h", "heated"), info[:]))
+
+    def cfl_timestep(self, courant=0.3):
+        dt = C.c_double(0.0)
+        self._chk(gnb_cfl_timestep(self.h, float(courant), C.byref(dt)))
+        return dt.value
+
+    def integrate_cfl(self, t_span, courant=0.3, max_steps=1 << 30, mode=GNB_GRAV_NONE):
+        """Plain CFL-limited KDK integration over t_span; returns (t, steps)."""
+        t = C.c_double(0.0)
+        n = C.c_int64(0)
+        self._chk(gnb_integrate_cfl(self.h, float(t_span), float(courant), int(min(max_steps, 2**31 - 1)), mode,
+                                    C.byref(t), C.byref(n)))
+        return t.value, n.value
 
     def set_params(self, **params):
         """Change configuration fields (tree and forces are recomputed later)."""

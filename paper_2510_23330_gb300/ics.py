@@ -208,3 +208,74 @@ def config_tiny(seed: int = 0) -> dict:
 def config_disk(n: int = 1 << 20, gas_frac: float = 0.2, seed: int = 0) -> dict:
     """Disk model: 80 % stars (R_d = 1, z_d = 0.1) and 20 % gas (R_d = 2)."""
     return exp_disk(n, gas_frac=gas_frac, seed=seed)
+
+
+# ---------------------------------------------------------------- SN regions
+# Units of supernova regions: pc, solar mass, km/s (time unit pc/(km/s) =
+# 0.97779 Myr).  u in (km/s)^2; T = (gamma - 1) mu m_H u / k_B with mu = 0.6.
+PC_KMS_MYR = 0.977792221
+E_SN_CODE = 1.0e51 / 1.98847e43          # 10^51 erg in Msun (km/s)^2
+T_PER_U = (2.0 / 3.0) * 0.6 * 1.67262e-24 * 1.0e10 / 1.380649e-16   # K per (km/s)^2
+T_SN_END = 0.1 / PC_KMS_MYR              # 0.1 Myr in code time
+
+
+def _grf(rng, ng: int, slope: float, ncomp: int = 1, solenoidal: bool = False):
+    """Gaussian random field(s) on an ng^3 periodic grid with power spectrum
+    P(k) ~ k^slope, zero mean, unit variance per component."""
+    k = np.fft.fftfreq(ng) * ng
+    kz = np.fft.rfftfreq(ng) * ng
+    KX, KY, KZ = np.meshgrid(k, k, kz, indexing="ij")
+    k2 = KX * KX + KY * KY + KZ * KZ
+    amp = np.zeros_like(k2)
+    nz = k2 > 0
+    amp[nz] = k2[nz] ** (slope / 4.0)
+    comps = []
+    for _ in range(ncomp):
+        ph = rng.normal(size=k2.shape) + 1j * rng.normal(size=k2.shape)
+        comps.append(ph * amp)
+    if solenoidal and ncomp == 3:
+        kv = (KX, KY, KZ)
+        dot = sum(kv[a] * comps[a] for a in range(3))
+        with np.errstate(invalid="ignore", divide="ignore"):
+            for a in range(3):
+                comps[a] = np.where(nz, comps[a] - kv[a] * dot / np.where(nz, k2, 1.0), 0.0)
+    out = []
+    for c in comps:
+        f = np.fft.irfftn(c, s=(ng, ng, ng), axes=(0, 1, 2))
+        f = (f - f.mean()) / (f.std() + 1e-300)
+        out.append(f)
+    return out
+
+
+def sn_region(n: int = 100000, seed: int = 0, side: float = 60.0, sigma: float = 1.0,
+              slope: float = -11.0 / 3.0, v_rms: float = 10.0, T: float = 100.0,
+              grid: int = 64, m: float = 1.0) -> dict:
+    """Turbulent star-forming gas around a supernova (the training setup of
+    Sec. 3.3: turbulent density fields, gas particles of 1 Msun): n gas
+    particles of mass m in a cube of side `side` pc centred on the origin,
+    log-normal density (sigma of ln rho) from a Gaussian random field with
+    P(k) ~ k^slope (Kolmogorov by default), a solenoidal velocity field with
+    the same spectrum and rms v_rms km/s, uniform temperature T."""
+    rng = np.random.default_rng(seed)
+    (g,) = _grf(rng, grid, slope)
+    rho = np.exp(sigma * g - 0.5 * sigma * sigma).ravel()
+    cell = rng.choice(rho.size, size=n, p=rho / rho.sum())
+    ix, iy, iz = np.unravel_index(cell, (grid, grid, grid))
+    dxv = side / grid
+    pos = np.stack([ix, iy, iz], axis=1) + rng.uniform(0.0, 1.0, (n, 3))
+    pos = pos * dxv - 0.5 * side
+    vf = _grf(rng, grid, slope, ncomp=3, solenoidal=True)
+    v = np.stack([f.ravel()[cell] for f in vf], axis=1)
+    v *= v_rms / np.sqrt(np.mean(np.sum(v * v, axis=1)))
+    u = np.full(n, T / T_PER_U)
+    return _pack(pos, v, np.full(n, m), np.full(n, 0.1), u, np.full(n, GAS, np.uint8))
+
+
+def uniform_box(n_side: int, seed: int = 0, jitter: float = 0.1, rho: float = 1.0, u: float = 1e-6) -> dict:
+    """Gas on a jittered cubic lattice filling [-1/2, 1/2]^3 at density rho
+    (for the Sedov-Taylor blast test)."""
+    n = n_side ** 3
+    d = 1.0 / n_side
+    p = lattice(n_side, spacing=d, mass=rho / n, u=u, eps=0.01 * d, jitter=jitter, seed=seed,
+                origin=(-0.5 + 0.5 * d,) * 3)
+    return p
