@@ -241,6 +241,46 @@ int gnb_set_timing(gnb_ctx *ctx, int enable);
 int gnb_phase_times(gnb_ctx *ctx, double out_ms[GNB_T_COUNT_], int64_t calls[GNB_T_COUNT_],
                     int64_t *launches, int reset);
 
+/* ------------------------------------------------------------------------
+ * Supernova surrogate: 3D U-Net (Sec. 3.3: a U-Net of 3D convolutions that
+ * maps the gas around a supernova, voxelised on a 64^3 grid, to its state
+ * 0.1 Myr later; MSE loss and Adam; trained at batch size 1).  The layer list
+ * is a reading: `levels` levels of widths base, 2 base, ...; two 3^3
+ * convolutions with zero padding and ReLU per level; 2^3 max-pool; 2^3
+ * stride-2 transposed convolution; skip concatenated before the up-sampled
+ * tensor; a 1^3 linear head.  Computation: BF16 operands on the tensor cores
+ * with FP32 accumulation; FP32 master weights and Adam state.
+ * Tensors are FP32 [batch][z][y][x][channel] (channels innermost).
+ * Parameters are one FP32 array, layer by layer in the order enc0a, enc0b,
+ * enc1a, ..., up(levels-2), dec(levels-2)a, dec(levels-2)b, ..., up0, dec0a,
+ * dec0b, head; per layer W[taps][cin][cout] then b[cout], with the 27 taps of
+ * a 3^3 convolution ordered (dz, dy, dx) over {-1,0,1}^3 with dx fastest and
+ * the 8 taps of the transposed convolution t = 4 tz + 2 ty + tx. */
+typedef struct gnb_unet gnb_unet;
+
+/* Create a U-Net on the current device with zero parameters.  Supported:
+ * 1 <= cin <= 16, 1 <= cout <= 8, base in {8, 16, 24, 32}, 2 <= levels <= 5,
+ * grid divisible by 2^(levels-1) with at least 2 voxels at the coarsest level.
+ * stream: cudaStream_t (NULL = default).  Errors: GNB_EINVAL, GNB_ENOMEM. */
+int gnb_unet_create(gnb_unet **out, int cin, int cout, int base, int levels, int grid, void *stream);
+void gnb_unet_destroy(gnb_unet *net);
+/* Number of FP32 parameters (-1 for NULL). */
+int64_t gnb_unet_num_params(const gnb_unet *net);
+/* Copy the parameters out / in (set also resets the Adam state).
+ * Errors: GNB_EINVAL, GNB_ECUDA. */
+int gnb_unet_get_params(gnb_unet *net, float *dst, int on_device);
+int gnb_unet_set_params(gnb_unet *net, const float *src, int on_device);
+/* Gradients of the last gnb_unet_train_step (before its Adam update). */
+int gnb_unet_get_grads(gnb_unet *net, float *dst, int on_device);
+/* Inference: x [batch][grid^3][cin] -> y [batch][grid^3][cout] (FP32).
+ * Errors: GNB_EINVAL, GNB_ENOMEM, GNB_ECUDA. */
+int gnb_unet_forward(gnb_unet *net, int batch, const float *x, float *y, int on_device);
+/* One training step: forward, MSE against target, back-propagation and, if
+ * lr > 0, one Adam step (beta1 0.9, beta2 0.999, eps 1e-8).  *loss (may be
+ * NULL) receives the mean squared error before the update. */
+int gnb_unet_train_step(gnb_unet *net, int batch, const float *x, const float *target, double lr,
+                        double *loss, int on_device);
+
 /* Largest particle count accepted by gnb_morton_order_noalloc. */
 #define GNB_NOALLOC_MAX_N 262144
 

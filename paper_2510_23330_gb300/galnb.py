@@ -100,6 +100,19 @@ def _declare(L):
     L.gnb_integrate_cfl.argtypes = [_vp, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int64)]
     L.gnb_integrate_cfl.restype = C.c_int
+    L.gnb_unet_create.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp]
+    L.gnb_unet_create.restype = C.c_int
+    L.gnb_unet_destroy.argtypes = [_vp]
+    L.gnb_unet_destroy.restype = None
+    L.gnb_unet_num_params.argtypes = [_vp]
+    L.gnb_unet_num_params.restype = C.c_int64
+    for name in ("gnb_unet_get_params", "gnb_unet_set_params", "gnb_unet_get_grads"):
+        getattr(L, name).argtypes = [_vp, _vp, C.c_int]
+        getattr(L, name).restype = C.c_int
+    L.gnb_unet_forward.argtypes = [_vp, C.c_int, _vp, _vp, C.c_int]
+    L.gnb_unet_forward.restype = C.c_int
+    L.gnb_unet_train_step.argtypes = [_vp, C.c_int, _vp, _vp, C.c_double, C.POINTER(C.c_double), C.c_int]
+    L.gnb_unet_train_step.restype = C.c_int
     for name in ("gnb_create", "gnb_set_particles", "gnb_build_tree", "gnb_compute_gravity",
                  "gnb_compute_sph_density", "gnb_compute_sph_force", "gnb_compute_forces", "gnb_step_kdk",
                  "gnb_get", "gnb_diagnostics", "gnb_stats"):
@@ -178,6 +191,106 @@ def gnb_cfl_timestep(ctx, courant, dt):
 
 def gnb_integrate_cfl(ctx, t_span, courant, max_steps, gravity_mode, t_done, steps_done):
     return lib().gnb_integrate_cfl(ctx, t_span, courant, max_steps, gravity_mode, t_done, steps_done)
+
+
+def gnb_unet_create(out, cin, cout, base, levels, grid, stream):
+    return lib().gnb_unet_create(out, cin, cout, base, levels, grid, stream)
+
+
+def gnb_unet_destroy(net):
+    lib().gnb_unet_destroy(net)
+
+
+def gnb_unet_num_params(net):
+    return lib().gnb_unet_num_params(net)
+
+
+def gnb_unet_get_params(net, dst, on_device):
+    return lib().gnb_unet_get_params(net, dst, on_device)
+
+
+def gnb_unet_set_params(net, src, on_device):
+    return lib().gnb_unet_set_params(net, src, on_device)
+
+
+def gnb_unet_get_grads(net, dst, on_device):
+    return lib().gnb_unet_get_grads(net, dst, on_device)
+
+
+def gnb_unet_forward(net, batch, x, y, on_device):
+    return lib().gnb_unet_forward(net, batch, x, y, on_device)
+
+
+def gnb_unet_train_step(net, batch, x, target, lr, loss, on_device):
+    return lib().gnb_unet_train_step(net, batch, x, target, lr, loss, on_device)
+
+
+class UNet:
+    """Owner of one gnb_unet (marshalling only)."""
+
+    def __init__(self, cin=5, cout=5, base=16, levels=4, grid=64, stream=None):
+        h = _vp()
+        rc = gnb_unet_create(C.byref(h), cin, cout, base, levels, grid, stream)
+        if rc != GNB_OK:
+            raise GalnbError(rc, "gnb_unet_create failed")
+        self.h, self.cin, self.cout, self.grid = h, cin, cout, grid
+
+    def close(self):
+        if getattr(self, "h", None):
+            gnb_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _chk(rc, what):
+        if rc != GNB_OK:
+            raise GalnbError(rc, what)
+
+    def num_params(self):
+        return int(gnb_unet_num_params(self.h))
+
+    def get_params(self):
+        out = np.empty(self.num_params(), np.float32)
+        self._chk(gnb_unet_get_params(self.h, out.ctypes.data, 0), "get_params")
+        return out
+
+    def get_grads(self):
+        out = np.empty(self.num_params(), np.float32)
+        self._chk(gnb_unet_get_grads(self.h, out.ctypes.data, 0), "get_grads")
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.num_params()
+        self._chk(gnb_unet_set_params(self.h, flat.ctypes.data, 0), "set_params")
+
+    def forward(self, x, out=None):
+        """x: [B, G, G, G, cin] (numpy float32 or a CUDA tensor)."""
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float32)
+            y = np.empty(x.shape[:4] + (self.cout,), np.float32) if out is None else out
+            self._chk(gnb_unet_forward(self.h, x.shape[0], x.ctypes.data, y.ctypes.data, 0), "forward")
+            return y
+        y = out
+        self._chk(gnb_unet_forward(self.h, x.shape[0], x.data_ptr(), y.data_ptr(), 1), "forward")
+        return y
+
+    def train_step(self, x, target, lr):
+        loss = C.c_double(0.0)
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float32)
+            target = np.ascontiguousarray(target, dtype=np.float32)
+            self._chk(gnb_unet_train_step(self.h, x.shape[0], x.ctypes.data, target.ctypes.data, float(lr),
+                                          C.byref(loss), 0), "train_step")
+        else:
+            self._chk(gnb_unet_train_step(self.h, x.shape[0], x.data_ptr(), target.data_ptr(), float(lr),
+                                          C.byref(loss), 1), "train_step")
+        return loss.value
 
 
 def gnb_set_timing(ctx, enable):

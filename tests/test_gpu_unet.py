@@ -1,0 +1,85 @@
+"""GPU parity of the BF16 tensor-core U-Net against the FP64 oracle run on the
+same BF16-rounded inputs, weights and stored activations: forward output and
+all parameter gradients within a relative L2 error of 1e-2; training lowers
+the loss."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_23330_gb300 import galnb
+    return galnb
+
+
+def flat(p, spec):
+    return np.concatenate([np.concatenate([p[n + ".w"].ravel(), p[n + ".b"]]) for n, *_ in spec])
+
+
+def unflat(v, spec, like):
+    out, o = {}, 0
+    for n, *_ in spec:
+        for k in (n + ".w", n + ".b"):
+            sz = like[k].size
+            out[k] = v[o:o + sz].reshape(like[k].shape).astype(np.float64)
+            o += sz
+    return out
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-30))
+
+
+def _setup(G, grid, batch, seed=0, base=16, levels=4):
+    spec = U.layer_spec(5, 5, base, levels)
+    p = U.init_params(seed, 5, 5, base, levels)
+    rng = np.random.default_rng(seed + 1)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = rng.normal(0, 0.1, p[k].shape)
+    x = U.bf16(rng.normal(size=(batch, grid, grid, grid, 5)))
+    net = G.UNet(5, 5, base, levels, grid)
+    net.set_params(flat(p, spec).astype(np.float32))
+    # the GPU keeps FP32 master weights; the oracle sees the FP32 values
+    p = unflat(net.get_params(), spec, p)
+    return spec, p, x, net
+
+
+@pytest.mark.parametrize("grid,batch", [(16, 2), (64, 1)])
+def test_forward_matches_oracle(G, grid, batch):
+    spec, p, x, net = _setup(G, grid, batch)
+    y = net.forward(x.astype(np.float32))
+    ref, _ = U.forward(p, x, bf=True)
+    assert rel_l2(y, ref) < 1e-2
+    assert np.max(np.abs(y - ref)) < 0.05 * np.max(np.abs(ref))
+
+
+def test_gradients_match_oracle(G):
+    spec, p, x, net = _setup(G, 16, 2, seed=3)
+    rng = np.random.default_rng(9)
+    t = rng.normal(size=x.shape)
+    loss = net.train_step(x.astype(np.float32), t.astype(np.float32), 0.0)
+    y, cache = U.forward(p, x, bf=True)
+    ref_loss, dy = U.mse(y, t)
+    assert abs(loss / ref_loss - 1.0) < 1e-2
+    g = unflat(net.get_grads(), spec, p)
+    rg = U.backward(p, cache, dy, bf=True)
+    errs = {k: rel_l2(g[k], rg[k]) for k in rg}
+    assert max(errs.values()) < 1e-2, errs
+
+
+def test_training_lowers_loss(G):
+    spec, p, x, net = _setup(G, 16, 1, seed=5)
+    rng = np.random.default_rng(11)
+    t = np.tanh(x[..., ::-1].copy()) * 0.5 + 0.1 * rng.normal(size=x.shape)
+    l0 = net.train_step(x.astype(np.float32), t.astype(np.float32), 1e-3)
+    for _ in range(60):
+        l1 = net.train_step(x.astype(np.float32), t.astype(np.float32), 1e-3)
+    assert l1 < 0.5 * l0
