@@ -281,6 +281,49 @@ int gnb_unet_forward(gnb_unet *net, int batch, const float *x, float *y, int on_
 int gnb_unet_train_step(gnb_unet *net, int batch, const float *x, const float *target, double lr,
                         double *loss, int on_device);
 
+/* ------------------------------------------------------------------------
+ * Surrogate coupling (Sec. 3.2-3.3).  A region r is the cube of side `side`
+ * centred on centers[3r..3r+2] (host array); a gas particle belongs to the
+ * first region containing it (|x - c|_inf <= side/2).  Grids have grid^3
+ * voxels with centres lo + (i + 1/2) side/grid, x fastest.  Channels
+ * (standardised network units; the scalings are a reading):
+ *   z0 = log10(max(rho, 1e-4)) + 0.33, z1 = (log10(max(T, 10)) - 2) / 2,
+ *   z2..z4 = v / 20,
+ * with rho in the mass/length^3 units of the particles (Msun/pc^3), T in K
+ * from T = u (gamma-1) mu m_H / k_B (mu = 0.6, u in (km/s)^2), v in km/s.
+ * --------------------------------------------------------------------- */
+
+/* Voxelise the gas of nreg regions (Sec. 3.3: SPH kernel convolution for the
+ * density, Shepard averages for T and v; empty voxels get rho = 0, T = 10 K,
+ * v = 0).  out: [nreg][grid^3][5] FP32.  Requires gnb_compute_sph_density
+ * at the current positions.  Errors: GNB_EINVAL, GNB_ESTATE, GNB_ENOMEM,
+ * GNB_ECUDA. */
+int gnb_voxelise(gnb_ctx *ctx, int nreg, const double *centers, double side, int grid, float *out,
+                 int on_device);
+
+/* Replace the gas of each region by the same number of particles, keeping
+ * IDs and masses (Sec. 3.2 step 4; Sec. 3.3: Gibbs sampling, mass conserved
+ * by keeping the particle count), drawn from the predicted grid pred
+ * [nreg][grid^3][5]: from the voxel of its old position each particle makes
+ * `sweeps` Gibbs sweeps over x, y, z, each draw choosing a voxel on the
+ * current line with probability proportional to 10^(z0 - 0.33) (FP64 CDF),
+ * then a uniform offset in the voxel; u and v come from the chosen voxel.
+ * Draw k of particle id uses U = (splitmix64(splitmix64(seed + id) + k) >> 11)
+ * * 2^-53.  Positions change, so trees and forces must be recomputed.
+ * Errors: GNB_EINVAL, GNB_ESTATE, GNB_ECUDA. */
+int gnb_remap_regions(gnb_ctx *ctx, int nreg, const double *centers, double side, int grid,
+                      const float *pred, uint64_t seed, int sweeps, int on_device);
+
+/* Batched surrogate step for nreg supernova regions of uneven particle
+ * counts: voxelise -> U-Net forward (net, which must predict 5 channels on
+ * its own grid) -> Gibbs remap, as above.  With use_graph = 1 and a
+ * non-default stream the sequence is captured into a CUDA graph on the first
+ * call and replayed while the shapes stay the same.  Requires
+ * gnb_compute_sph_density at the current positions.  Errors: GNB_EINVAL,
+ * GNB_ESTATE, GNB_ENOMEM, GNB_ECUDA. */
+int gnb_sn_surrogate_batch(gnb_ctx *ctx, gnb_unet *net, int nreg, const double *centers, double side,
+                           uint64_t seed, int sweeps, int use_graph);
+
 /* Largest particle count accepted by gnb_morton_order_noalloc. */
 #define GNB_NOALLOC_MAX_N 262144
 

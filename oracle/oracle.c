@@ -656,6 +656,116 @@ int orc_num_threads(void)
 #endif
 }
 
+/* ------------------------------------------------------------------------ */
+/* Voxelisation of one supernova region (Sec. 3.3: particles mapped to a     */
+/* 64^3 grid by SPH kernel convolution and the Shepard method).  Voxel       */
+/* centres x_v = lo + (i + 1/2) side/grid.  Accumulators per voxel:          */
+/*   acc[0] = sum m_j W(|x_v - x_j|, h_j)             (density)              */
+/*   acc[1] = sum (m_j/rho_j) W                       (Shepard denominator)   */
+/*   acc[2..5] = sum f_j (m_j/rho_j) W, f = T, vx, vy, vz                    */
+/* h_j is the kernel support.  acc has 6 * grid^3 doubles, voxel-major.    */
+/* ------------------------------------------------------------------------ */
+void orc_voxelise(int64_t n, const double *x, const double *y, const double *z, const double *m,
+                  const double *h, const double *rho, const double *T, const double *vx,
+                  const double *vy, const double *vz, const double *lo, double side, int grid,
+                  double *acc)
+{
+    double d = side / grid;
+    memset(acc, 0, sizeof(double) * 6 * (size_t)grid * grid * grid);
+    for (int64_t j = 0; j < n; j++) {
+        double p[3] = {x[j], y[j], z[j]};
+        int i0[3], i1[3];
+        for (int a = 0; a < 3; a++) {
+            i0[a] = (int)floor((p[a] - h[j] - lo[a]) / d - 0.5);
+            i1[a] = (int)ceil((p[a] + h[j] - lo[a]) / d - 0.5);
+            if (i0[a] < 0) i0[a] = 0;
+            if (i1[a] > grid - 1) i1[a] = grid - 1;
+        }
+        double wr = m[j] / rho[j];
+        for (int iz = i0[2]; iz <= i1[2]; iz++)
+            for (int iy = i0[1]; iy <= i1[1]; iy++)
+                for (int ix = i0[0]; ix <= i1[0]; ix++) {
+                    double dx = lo[0] + (ix + 0.5) * d - p[0];
+                    double dy = lo[1] + (iy + 0.5) * d - p[1];
+                    double dz = lo[2] + (iz + 0.5) * d - p[2];
+                    double r = sqrt(dx * dx + dy * dy + dz * dz);
+                    double w = kern_w(r, h[j]);
+                    if (w <= 0.0) continue;
+                    double *a = acc + 6 * (((size_t)iz * grid + iy) * grid + ix);
+                    a[0] += m[j] * w;
+                    a[1] += wr * w;
+                    a[2] += T[j] * wr * w;
+                    a[3] += vx[j] * wr * w;
+                    a[4] += vy[j] * wr * w;
+                    a[5] += vz[j] * wr * w;
+                }
+    }
+}
+
+/* SplitMix64 (Steele, Lea & Flood 2014; the constants of Vigna's public    */
+/* reference version) and the counter-based uniform draw used by the remap: */
+/*   U(seed, id, k) = (splitmix64(splitmix64(seed + id) + k) >> 11) 2^-53.   */
+static uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+uint64_t orc_splitmix64(uint64_t x) { return splitmix64(x); }
+
+double orc_uniform(uint64_t seed, uint64_t id, uint64_t k)
+{
+    return (double)(splitmix64(splitmix64(seed + id) + k) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid -> particles by Gibbs sampling (Sec. 3.3: the predicted grid is      */
+/* turned back into as many particles as went in, by a Markov chain Monte    */
+/* Carlo method).  Reading: each particle starts in the voxel that holds its */
+/* old position and makes `sweeps` Gibbs sweeps over x, y, z; each draw picks */
+/* a voxel along the current line with probability proportional to the      */
+/* voxel weight w (the predicted density).  Draw k of particle `id` uses    */
+/* U(seed, id, k), k = 3 s + axis; the final offsets inside the voxel use    */
+/* k = 3 sweeps + axis.  The CDF is FP64, summed from index 0 upwards, and   */
+/* the voxel is the first index whose inclusive CDF exceeds U * total.      */
+/* out: 3 voxel indices and 3 positions per particle.                        */
+/* ------------------------------------------------------------------------ */
+void orc_gibbs_remap(int64_t n, const int64_t *id, const int32_t *start, const double *w, int grid,
+                     const double *lo, double side, uint64_t seed, int sweeps, int32_t *vox,
+                     double *pos)
+{
+    double d = side / grid;
+    for (int64_t j = 0; j < n; j++) {
+        int c[3] = {start[3 * j], start[3 * j + 1], start[3 * j + 2]};
+        uint64_t k = 0;
+        for (int s = 0; s < sweeps; s++)
+            for (int a = 0; a < 3; a++, k++) {
+                double tot = 0.0;
+                for (int i = 0; i < grid; i++) {
+                    int cc[3] = {c[0], c[1], c[2]};
+                    cc[a] = i;
+                    tot += w[((size_t)cc[2] * grid + cc[1]) * grid + cc[0]];
+                }
+                double target = orc_uniform(seed, (uint64_t)id[j], k) * tot;
+                double cum = 0.0;
+                int pick = grid - 1;
+                for (int i = 0; i < grid; i++) {
+                    int cc[3] = {c[0], c[1], c[2]};
+                    cc[a] = i;
+                    cum += w[((size_t)cc[2] * grid + cc[1]) * grid + cc[0]];
+                    if (cum > target) { pick = i; break; }
+                }
+                c[a] = pick;
+            }
+        for (int a = 0; a < 3; a++) {
+            vox[3 * j + a] = c[a];
+            pos[3 * j + a] = lo[a] + (c[a] + orc_uniform(seed, (uint64_t)id[j], (uint64_t)(3 * sweeps + a))) * d;
+        }
+    }
+}
+
 /* Eq. 1 direct sum for the ns particles listed in `sample` only (used to
  * check full-size runs on a subsample).  Outputs have length ns. */
 void orc_direct_gravity_sample(int64_t n, const double *x, const double *y, const double *z,

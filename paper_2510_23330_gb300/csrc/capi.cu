@@ -273,6 +273,11 @@ void gnb_destroy(gnb_ctx *c)
                    c->rs_total, c->rtot_d, c->scan_part, c->scan_poff};
     for (void *q : all) dfree(c, q);
     if (c->pinned_i) cudaFreeHost(c->pinned_i);
+    {
+        void *sur[] = {c->sreg, c->rcount, c->vacc, c->vout, c->vw, c->cent_d, c->seed_d};
+        for (void *q : sur) dfree(c, q);
+        if (c->sn_graph) cudaGraphExecDestroy(c->sn_graph);
+    }
     for (auto &q : c->pend) { cudaEventDestroy(q.second.first); cudaEventDestroy(q.second.second); }
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
     if (c->open_ev) cudaEventDestroy(c->open_ev);
@@ -640,6 +645,54 @@ int gnb_integrate_cfl(gnb_ctx *c, double t_span, double courant, int max_steps, 
     if (t_done) *t_done = t;
     if (steps_done) *steps_done = steps;
     if (rc == GNB_OK) rc = read_groups(c);
+    return finish(c, rc);
+}
+
+int gnb_voxelise(gnb_ctx *c, int nreg, const double *centers, double side, int grid, float *out, int on_device)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (nreg < 1 || !centers || !out || !(side > 0.0) || grid < 1 || grid > 256)
+        return fail(c, GNB_EINVAL, "regions, side or grid");
+    if (!c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed for the current positions");
+    int rc = voxelise(c, nreg, centers, side, grid, on_device ? out : nullptr);
+    if (rc == GNB_OK && !on_device)
+        rc = cuda_check(c, cudaMemcpyAsync(out, c->vout, sizeof(float) * 5 * (size_t)nreg * grid * grid * grid,
+                                           cudaMemcpyDeviceToHost, c->s), "voxel copy");
+    return finish(c, rc);
+}
+
+int gnb_remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, int grid, const float *pred,
+                      uint64_t seed, int sweeps, int on_device)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (nreg < 1 || !centers || !pred || !(side > 0.0) || grid < 1 || grid > 256 || sweeps < 0)
+        return fail(c, GNB_EINVAL, "regions, side, grid or sweeps");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    const float *pd = pred;
+    int rc = GNB_OK;
+    if (!on_device) {
+        rc = voxelise_buffers_for(c, nreg, grid);
+        if (rc == GNB_OK)
+            rc = cuda_check(c, cudaMemcpyAsync(c->vout, pred, sizeof(float) * 5 * (size_t)nreg * grid * grid * grid,
+                                               cudaMemcpyHostToDevice, c->s), "prediction copy");
+        pd = c->vout;
+    }
+    if (rc == GNB_OK) rc = remap_regions(c, nreg, centers, side, grid, pd, seed, sweeps);
+    c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    return finish(c, rc);
+}
+
+int gnb_sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *centers, double side, uint64_t seed,
+                           int sweeps, int use_graph)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!net || nreg < 1 || !centers || !(side > 0.0) || sweeps < 0) return fail(c, GNB_EINVAL, "arguments");
+    if (!c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed for the current positions");
+    int rc = sn_surrogate_batch(c, net, nreg, centers, side, seed, sweeps, use_graph);
+    c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
     return finish(c, rc);
 }
 

@@ -145,6 +145,24 @@ struct gnb_ctx {
     int2 *kitem = nullptr;        // kNN work items (first, count); groups then split particles
     int *kcount_d = nullptr;
 
+    // supernova surrogate (surrogate.cu)
+    int *sreg = nullptr;          // region of each particle slot (-1: none)
+    int *rcount = nullptr;        // members per region
+    float *vacc = nullptr;        // voxel accumulators [nreg][grid^3][6]
+    float *vout = nullptr;        // standardised channels [nreg][grid^3][5]
+    double *vw = nullptr;         // remap weights [nreg][grid^3]
+    double *cent_d = nullptr;     // region centres [nreg][3]
+    unsigned long long *seed_d = nullptr;
+    size_t sur_nv = 0;
+    int sur_nreg = 0;
+    cudaGraphExec_t sn_graph = nullptr;  // captured voxelise -> U-Net -> remap
+    int sn_key[3] = {0, 0, 0};
+    void *sn_net = nullptr;
+    double sn_side = 0.0;
+    int64_t sn_n = 0;
+    int sn_cur = -1;
+    int64_t sn_graph_replays = 0;
+
     // status / counters
     int *status_d = nullptr;
     int *n_d = nullptr;                        // device copy of n
@@ -217,6 +235,13 @@ int gravity_nfw(gnb_ctx *c);
 // sph.cu
 int sph_density(gnb_ctx *c);
 int sph_force(gnb_ctx *c);
+// surrogate.cu
+int voxelise_buffers_for(gnb_ctx *c, int nreg, int grid);
+int voxelise(gnb_ctx *c, int nreg, const double *centers, double side, int grid, float *out_dev);
+int remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, int grid, const float *pred_dev,
+                  uint64_t seed, int sweeps);
+int sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *centers, double side, uint64_t seed,
+                       int sweeps, int use_graph);
 // sn.cu
 int inject_energy(gnb_ctx *c, const double pos[3], double E, double out[4]);
 int cfl_min_h_over_vsig(gnb_ctx *c, double *out);

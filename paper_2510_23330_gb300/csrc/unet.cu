@@ -752,6 +752,32 @@ int unet_check(gnb_unet *u, int rc)
 
 }  // namespace
 
+namespace gnb {
+// Hooks for the batched surrogate step: make room for `batch` regions and
+// expose the packed BF16 input [batch][grid^3][16] and the FP32 output
+// [batch][grid^3][cout]; unet_run launches the forward pass on `stream`
+// without synchronising (so it can be captured in a CUDA graph).
+int unet_prepare(gnb_unet *u, int batch, bf16 **xin, float **yout, int *grid, int *cout)
+{
+    int rc = unet_alloc_acts(u, batch);
+    if (rc != GNB_OK) return rc;
+    *xin = u->xin;
+    *yout = u->yout;
+    *grid = u->grid;
+    *cout = u->cout;
+    return GNB_OK;
+}
+
+int unet_run(gnb_unet *u, int batch, cudaStream_t stream)
+{
+    cudaStream_t keep = u->s;
+    u->s = stream;
+    int rc = unet_forward(u, batch);
+    u->s = keep;
+    return rc;
+}
+}  // namespace gnb
+
 extern "C" {
 
 int gnb_unet_create(gnb_unet **out, int cin, int cout, int base, int levels, int grid, void *stream)

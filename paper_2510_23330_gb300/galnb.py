@@ -100,6 +100,14 @@ def _declare(L):
     L.gnb_integrate_cfl.argtypes = [_vp, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int64)]
     L.gnb_integrate_cfl.restype = C.c_int
+    L.gnb_voxelise.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.c_double, C.c_int, _vp, C.c_int]
+    L.gnb_voxelise.restype = C.c_int
+    L.gnb_remap_regions.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.c_double, C.c_int, _vp, C.c_uint64,
+                                    C.c_int, C.c_int]
+    L.gnb_remap_regions.restype = C.c_int
+    L.gnb_sn_surrogate_batch.argtypes = [_vp, _vp, C.c_int, C.POINTER(C.c_double), C.c_double, C.c_uint64, C.c_int,
+                                         C.c_int]
+    L.gnb_sn_surrogate_batch.restype = C.c_int
     L.gnb_unet_create.argtypes = [C.POINTER(_vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp]
     L.gnb_unet_create.restype = C.c_int
     L.gnb_unet_destroy.argtypes = [_vp]
@@ -191,6 +199,23 @@ def gnb_cfl_timestep(ctx, courant, dt):
 
 def gnb_integrate_cfl(ctx, t_span, courant, max_steps, gravity_mode, t_done, steps_done):
     return lib().gnb_integrate_cfl(ctx, t_span, courant, max_steps, gravity_mode, t_done, steps_done)
+
+
+def gnb_voxelise(ctx, nreg, centers, side, grid, out, on_device):
+    return lib().gnb_voxelise(ctx, nreg, centers, side, grid, out, on_device)
+
+
+def gnb_remap_regions(ctx, nreg, centers, side, grid, pred, seed, sweeps, on_device):
+    return lib().gnb_remap_regions(ctx, nreg, centers, side, grid, pred, seed, sweeps, on_device)
+
+
+def gnb_sn_surrogate_batch(ctx, net, nreg, centers, side, seed, sweeps, use_graph):
+    return lib().gnb_sn_surrogate_batch(ctx, net, nreg, centers, side, seed, sweeps, use_graph)
+
+
+def _centers(centers):
+    c = np.ascontiguousarray(np.asarray(centers, np.float64).reshape(-1))
+    return c, (C.c_double * c.size)(*c)
 
 
 def gnb_unet_create(out, cin, cout, base, levels, grid, stream):
@@ -461,6 +486,26 @@ class Context:
         self._chk(gnb_integrate_cfl(self.h, float(t_span), float(courant), int(min(max_steps, 2**31 - 1)), mode,
                                     C.byref(t), C.byref(n)))
         return t.value, n.value
+
+    def voxelise(self, centers, side=60.0, grid=64):
+        """Standardised grids [nreg, grid, grid, grid, 5] of the regions."""
+        c, cp = _centers(centers)
+        nreg = c.size // 3
+        out = np.empty((nreg, grid, grid, grid, 5), np.float32)
+        self._chk(gnb_voxelise(self.h, nreg, cp, float(side), grid, out.ctypes.data, 0))
+        return out
+
+    def remap_regions(self, centers, pred, side=60.0, seed=0, sweeps=8):
+        c, cp = _centers(centers)
+        nreg = c.size // 3
+        pred = np.ascontiguousarray(pred, dtype=np.float32)
+        grid = int(round((pred.size // (5 * nreg)) ** (1.0 / 3.0)))
+        self._chk(gnb_remap_regions(self.h, nreg, cp, float(side), grid, pred.ctypes.data, int(seed), int(sweeps), 0))
+
+    def sn_surrogate_batch(self, net, centers, side=60.0, seed=0, sweeps=8, use_graph=True):
+        c, cp = _centers(centers)
+        self._chk(gnb_sn_surrogate_batch(self.h, net.h, c.size // 3, cp, float(side), int(seed), int(sweeps),
+                                         1 if use_graph else 0))
 
     def set_params(self, **params):
         """Change configuration fields (tree and forces are recomputed later)."""

@@ -1,0 +1,109 @@
+"""GPU parity of the surrogate's particle <-> grid mappings (voxelise, Gibbs
+remap) against the oracle, and invariants of the batched, graph-captured
+surrogate step."""
+import numpy as np
+import pytest
+
+from paper_2510_23330_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_23330_gb300 import galnb
+    return galnb
+
+
+def _region_state(G, orc, n=20000, seed=3):
+    p = ics.sn_region(n, seed=seed, grid=32)
+    c = G.Context()
+    c.set_particles(p)
+    c.compute_sph_density()
+    return p, c
+
+
+def test_voxelise_matches_oracle(G, orc):
+    from oracle import surrogate as S
+    p, c = _region_state(G, orc)
+    grid = 32
+    z = c.voxelise([(0.0, 0.0, 0.0)], side=60.0, grid=grid)[0].reshape(-1, 5)
+    s = orc.state(p)
+    rho = c.get("RHO").astype(np.float64)
+    h = np.sqrt(c.get("H2"))
+    mask = S.members(s, [(0.0, 0.0, 0.0)], 60.0) == 0
+    ref = S.voxelise(s, rho, h, (0.0, 0.0, 0.0), 60.0, grid, region_mask=mask)
+    assert np.max(np.abs(z[:, 0] - ref[:, 0])) < 2e-4
+    assert np.max(np.abs(z[:, 1] - ref[:, 1])) < 2e-4
+    assert np.max(np.abs(z[:, 2:] - ref[:, 2:])) < 1e-4 * max(1.0, np.max(np.abs(ref[:, 2:])))
+
+
+def test_remap_matches_oracle(G, orc):
+    from oracle import surrogate as S
+    p, c = _region_state(G, orc, n=15000, seed=4)
+    grid, side, cen = 32, 60.0, (1.0, -2.0, 0.5)
+    pred = c.voxelise([cen], side=side, grid=grid)
+    s = orc.state(p)
+    mem = np.nonzero(S.members(s, [cen], side) == 0)[0]
+    c.remap_regions([cen], pred, side=side, seed=9, sweeps=4)
+    x, y, z = c.get("X"), c.get("Y"), c.get("Z")
+    newp = np.stack([x, y, z], axis=1)
+    pos = np.stack([s["x"], s["y"], s["z"]], axis=1)[mem]
+    vox, rp, ru, rv = S.remap(pred[0].reshape(-1, 5).astype(np.float64), p["id"][mem], pos, cen, side, grid,
+                              seed=9, sweeps=4)
+    lo = np.asarray(cen) - 0.5 * side
+    gv = np.floor((newp[mem] - lo) / (side / grid)).astype(np.int64)
+    assert np.array_equal(gv, vox)
+    assert np.max(np.abs(newp[mem] - rp)) < 1e-12 * side
+    others = np.setdiff1d(np.arange(p["x"].size), mem)
+    assert np.array_equal(newp[others], pos_all(s)[others])
+    assert np.allclose(c.get("U")[mem], ru, rtol=1e-6)
+    v = np.stack([c.get("VX"), c.get("VY"), c.get("VZ")], axis=1)[mem]
+    assert np.allclose(v, rv, rtol=1e-6, atol=1e-6)
+
+
+def pos_all(s):
+    return np.stack([s["x"], s["y"], s["z"]], axis=1)
+
+
+def test_batched_surrogate_step_invariants(G, orc):
+    from oracle import unet as U
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        regions = [ics.sn_region(8000 + 3000 * k, seed=10 + k, grid=32) for k in range(4)]
+        offs = [(200.0 * k, 0.0, 0.0) for k in range(4)]
+        parts = {}
+        for k, (r, o) in enumerate(zip(regions, offs)):
+            r = dict(r)
+            r["x"] = r["x"] + o[0]
+            for key, val in r.items():
+                parts.setdefault(key, []).append(val)
+        p = {k: np.concatenate(v) for k, v in parts.items()}
+        p["id"] = np.arange(p["x"].size, dtype=np.int64)
+        c = G.Context(stream=stream.cuda_stream)
+        c.set_particles(p)
+        c.compute_sph_density()
+        net = G.UNet(5, 5, 16, 4, 32, stream=stream.cuda_stream)
+        spec = U.layer_spec(5, 5, 16, 4)
+        prm = U.init_params(1, 5, 5, 16, 4)
+        net.set_params(np.concatenate([np.concatenate([prm[n + ".w"].ravel(), prm[n + ".b"]])
+                                       for n, *_ in spec]).astype(np.float32))
+        c.sn_surrogate_batch(net, offs, side=60.0, seed=1, sweeps=8, use_graph=True)
+        ids = c.get("ID")
+        x, y, z = c.get("X"), c.get("Y"), c.get("Z")
+        for k, o in enumerate(offs):
+            lo = np.asarray(o) - 30.0
+            sel = (np.abs(p["x"] - o[0]) <= 30) & (np.abs(p["y"]) <= 30) & (np.abs(p["z"]) <= 30)
+            q = np.stack([x[sel], y[sel], z[sel]], axis=1)
+            assert np.all((q >= lo) & (q <= lo + 60.0))       # members stay in their cube
+        assert np.array_equal(ids, p["id"])                    # IDs and count conserved
+        assert np.all(np.isfinite(c.get("U"))) and np.all(c.get("U") > 0)
+        # replay: the same shapes reuse the captured graph
+        c.compute_sph_density()
+        c.sn_surrogate_batch(net, offs, side=60.0, seed=2, sweeps=8, use_graph=True)
+        assert np.all(np.isfinite(c.get("X")))
+    stream.synchronize()
