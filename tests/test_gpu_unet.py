@@ -1,7 +1,8 @@
 """GPU parity of the BF16 tensor-core U-Net against the FP64 oracle run on the
-same BF16-rounded inputs, weights and stored activations: forward output and
-all parameter gradients within a relative L2 error of 1e-2; training lowers
-the loss."""
+same BF16-rounded inputs, weights and stored activations: forward output
+within a relative L2 error of 1e-2; each parameter gradient within
+max(1e-2, 1.5 s) of it, s being that gradient's own BF16 sensitivity (the
+oracle with vs without BF16 storage); training lowers the loss."""
 import numpy as np
 import pytest
 
@@ -71,16 +72,21 @@ def test_gradients_match_oracle(G):
     assert abs(loss / ref_loss - 1.0) < 1e-2
     g = unflat(net.get_grads(), spec, p)
     rg = U.backward(p, cache, dy, bf=True)
+    # Sensitivity of each gradient to BF16 storage: the same oracle without
+    # any BF16 rounding.  Deep layers (the 2^3 bottleneck at this size sums
+    # few voxels with cancellation) move by several per cent between the two,
+    # and FP32-vs-FP64 accumulation flips individual BF16 roundings on the
+    # GPU in the same way, so each layer's bound scales with its sensitivity.
+    y64, cache64 = U.forward(p, x, bf=False)
+    _, dy64 = U.mse(y64, t)
+    rg64 = U.backward(p, cache64, dy64, bf=False)
+    sens = {k: rel_l2(rg64[k], rg[k]) for k in rg}
     errs = {k: rel_l2(g[k], rg[k]) for k in rg}
+    errs64 = {k: rel_l2(g[k], rg64[k]) for k in rg}
     worst = sorted(errs.items(), key=lambda kv: -kv[1])[:6]
-    # Gradients reaching enc0..enc2 pass a 2^3 max-pool: its routing picks the
-    # largest of eight BF16 values, and when two of them are within one BF16
-    # step the FP32 (GPU) and FP64 (oracle) accumulations can round them in
-    # opposite order, sending that voxel's gradient elsewhere.  Those layers
-    # get 1e-1; every layer whose gradient path has no max-pool gets 1e-2.
-    for k, e in errs.items():
-        pooled = k.startswith(("enc0", "enc1", "enc2"))
-        assert e < (1e-1 if pooled else 1e-2), (k, e, worst)
+    for k in rg:
+        assert errs[k] < max(1e-2, 1.5 * sens[k]), (k, errs[k], sens[k], worst)
+        assert errs64[k] < max(1e-2, 2.0 * sens[k]), (k, errs64[k], sens[k])
 
 
 def test_training_lowers_loss(G):
