@@ -272,8 +272,18 @@ int gnb_unet_get_params(gnb_unet *net, float *dst, int on_device);
 int gnb_unet_set_params(gnb_unet *net, const float *src, int on_device);
 /* Gradients of the last gnb_unet_train_step (before its Adam update). */
 int gnb_unet_get_grads(gnb_unet *net, float *dst, int on_device);
+/* Convolution kernels of the 3^3 layers.  GNB_CONV_AUTO (the default): the
+ * tcgen05 tensor-core kernel (TMA halo tiles, TMEM accumulators) wherever the
+ * channel counts are multiples of 16 and its weights fit in shared memory,
+ * the mma.sync implicit GEMM elsewhere; GNB_CONV_MMA_SYNC: the mma.sync
+ * implicit GEMM for every layer.  Both compute the same products with FP32
+ * accumulation.  A bounded device wait of the tensor-core kernel that runs out
+ * makes the call return GNB_ETIMEOUT.  Errors: GNB_EINVAL. */
+#define GNB_CONV_AUTO 0
+#define GNB_CONV_MMA_SYNC 2
+int gnb_unet_set_conv_impl(gnb_unet *net, int impl);
 /* Inference: x [batch][grid^3][cin] -> y [batch][grid^3][cout] (FP32).
- * Errors: GNB_EINVAL, GNB_ENOMEM, GNB_ECUDA. */
+ * Errors: GNB_EINVAL, GNB_ENOMEM, GNB_ECUDA, GNB_ETIMEOUT. */
 int gnb_unet_forward(gnb_unet *net, int batch, const float *x, float *y, int on_device);
 /* One training step: forward, MSE against target, back-propagation and, if
  * lr > 0, one Adam step (beta1 0.9, beta2 0.999, eps 1e-8).  *loss (may be

@@ -693,7 +693,10 @@ int gnb_sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *ce
     if (!c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed for the current positions");
     int rc = sn_surrogate_batch(c, net, nreg, centers, side, seed, sweeps, use_graph);
     c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
-    return finish(c, rc);
+    rc = finish(c, rc);
+    if (rc == GNB_OK && unet_poll_error(net) != GNB_OK)
+        return fail(c, GNB_ETIMEOUT, "a bounded wait in the U-Net's tensor-core convolution ran out");
+    return rc;
 }
 
 static int64_t field_count(gnb_ctx *c, int f, size_t *esz)

@@ -240,6 +240,9 @@ int voxelise_buffers_for(gnb_ctx *c, int nreg, int grid);
 int voxelise(gnb_ctx *c, int nreg, const double *centers, double side, int grid, float *out_dev);
 int remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, int grid, const float *pred_dev,
                   uint64_t seed, int sweeps);
+// GNB_ETIMEOUT (and clears it) when a tensor-core convolution of the network
+// recorded a bounded wait that ran out; the caller has synchronised.
+int unet_poll_error(gnb_unet *u);
 int sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *centers, double side, uint64_t seed,
                        int sweeps, int use_graph);
 // sn.cu

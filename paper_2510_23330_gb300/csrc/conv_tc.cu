@@ -1,0 +1,526 @@
+// conv_tc.cu -- 3^3 "same" convolution of BF16 NDHWC activations on the
+// 5th-generation tensor cores (tcgen05 + TMEM), used for the forward pass and
+// the input gradient of the surrogate U-Net's 3^3 convolutions (Sec. 3.3 of
+// Hirashima et al., SC'25).
+//
+// One output tile is 8 (x) x 16 (y) voxels x Zt z-planes; each z-plane is one
+// M = 128 MMA row block (row r = 8 y + x).  The tile's input halo,
+// (Zt + 2) x 18 x 10 voxels, is brought into shared memory once by TMA (one
+// 5-D box per group of 8 channels; out-of-range voxels are zero-filled by the
+// TMA unit, which is exactly the zero padding of the convolution) and stored
+// as [channel group][z][y][x][8 channels]: eight consecutive x voxels of one
+// channel group form one 8 x 16-byte core matrix of the canonical K-major
+// no-swizzle layout, so every one of the 27 taps is the same descriptor with
+// its start address shifted by the tap's (z, y, x) offset -- no im2col copy.
+// The weights of all taps stay resident in shared memory for the whole
+// persistent CTA, packed [tap][channel group][N][8].
+//
+// Roles (192 threads): warp 4 lane 0 issues the TMA loads, warp 5 lane 0
+// issues tcgen05.mma (FP32 accumulators in TMEM), warps 0..3 read TMEM with
+// tcgen05.ld and apply bias, ReLU and the BF16 store.  Halo buffers and TMEM
+// accumulators are double buffered so the loads of tile i + 1, the MMAs of
+// tile i and the epilogue of tile i - 1 overlap.  Every mbarrier wait is
+// bounded (1 s of %globaltimer); a wait that runs out sets the error word,
+// all roles leave their loops, in-flight copies and MMAs are drained (again
+// bounded) and TMEM is freed before the CTA exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "conv_tc.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+namespace gnb {
+
+namespace {
+
+constexpr int TC_THREADS = 192;
+constexpr int HX = 10, HY = 18;          // halo extent in x and y
+constexpr unsigned ROW_BYTES = 16;       // one voxel of one 8-channel group
+constexpr unsigned YSTRIDE = HX * ROW_BYTES;
+constexpr unsigned ZSTRIDE = HY * YSTRIDE;
+constexpr unsigned HDR = 128;            // barriers, TMEM slot, abort word
+constexpr unsigned ALIGN_SLACK = 1024;
+constexpr unsigned long long WAIT_NS = 1000000000ull;
+
+enum { B_W = 0, B_HF = 1, B_HE = 3, B_AF = 5, B_AE = 7, B_DR = 9, NBARS = 10 };
+
+struct TcArgs {
+    const bf16 *w;
+    const float *bias;
+    bf16 *out1, *out2;
+    int N, K, C1, O1, relu;
+    int B, D, H, W;
+    int Zt, nbuf, tx, ty, tz;
+    long long ntiles;
+    unsigned wbytes, plane, halo, off_w, off_h, tx_bytes, tmem_cols, idesc;
+    int *err;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mb_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mb_try(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase of `parity`.  Returns false when another role
+// has aborted (honour_abort) or after WAIT_NS, in which case it aborts the
+// CTA and records `code` in the error word.
+__device__ bool mb_wait(unsigned bar, unsigned parity, volatile int *abort_flag, int *err, int code,
+                        bool honour_abort = true)
+{
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; it++) {
+        if (mb_try(bar, parity)) return true;
+        if (honour_abort && *abort_flag) return false;
+        if ((it & 31u) == 0) {
+            unsigned long long t = gtimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > WAIT_NS) {
+                *abort_flag = 1;
+                atomicExch(err, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_5d(unsigned dst, const CUtensorMap *m, int c0, int c1, int c2, int c3, int c4,
+                                            unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];\n" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(unsigned dst, const void *src, unsigned bytes, unsigned bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
+// start address, leading-dimension byte offset (between core matrices along
+// K), stride-dimension byte offset (between 8-row groups along M or N), and
+// the descriptor version bit 46.
+__device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)(lbo >> 4) << 16) |
+           ((unsigned long long)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                       unsigned acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane; the wait is in the
+// same statement so no use of the registers can be scheduled before it.
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float *v)
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void decode_tile(const TcArgs &p, long long t, int &bb, int &z0, int &y0, int &x0)
+{
+    int xt = (int)(t % p.tx);
+    t /= p.tx;
+    int yt = (int)(t % p.ty);
+    t /= p.ty;
+    int zt = (int)(t % p.tz);
+    bb = (int)(t / p.tz);
+    x0 = 8 * xt;
+    y0 = 16 * yt;
+    z0 = p.Zt * zt;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_conv3_tc(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2, const TcArgs p)
+{
+    extern __shared__ unsigned char dsm[];
+    const unsigned raw = smem_u32(dsm);
+    const unsigned sb = (raw + (ALIGN_SLACK - 1)) & ~(ALIGN_SLACK - 1);
+    unsigned char *gb = dsm + (sb - raw);
+    unsigned *slot = reinterpret_cast<unsigned *>(gb + 8 * NBARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gb + 8 * NBARS + 4);
+    const unsigned sW = sb + p.off_w, sH = sb + p.off_h;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    auto bar = [&](int i) { return sb + 8u * (unsigned)i; };
+
+    if (threadIdx.x == 0) {
+        mb_init(bar(B_W), 1);
+        for (int b = 0; b < 2; b++) {
+            mb_init(bar(B_HF + b), 1);
+            mb_init(bar(B_HE + b), 1);
+            mb_init(bar(B_AF + b), 1);
+            mb_init(bar(B_AE + b), 128);
+        }
+        mb_init(bar(B_DR), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slot)),
+                     "r"(p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *slot;
+    const int kc8 = p.K >> 3;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // ---------------------------------------------------------- producer
+            mb_expect_tx(bar(B_W), p.wbytes);
+            for (unsigned o = 0; o < p.wbytes; o += 32768u) {
+                unsigned n = p.wbytes - o < 32768u ? p.wbytes - o : 32768u;
+                bulk_load(sW + o, reinterpret_cast<const unsigned char *>(p.w) + o, n, bar(B_W));
+            }
+            int uses[2] = {0, 0};
+            int i = 0;
+            for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, i++) {
+                const int b = i % p.nbuf;
+                const unsigned k = (unsigned)(i / p.nbuf);
+                if (k > 0 && !mb_wait(bar(B_HE + b), (k - 1) & 1u, abort_flag, p.err, 1)) break;
+                int bb, z0, y0, x0;
+                decode_tile(p, t, bb, z0, y0, x0);
+                mb_expect_tx(bar(B_HF + b), p.tx_bytes);
+                const unsigned dst = sH + (unsigned)b * p.halo;
+                for (int kc = 0; kc < kc8; kc++) {
+                    const int c = 8 * kc;
+                    if (c < p.C1) tma_load_5d(dst + kc * p.plane, &m1, c, x0 - 1, y0 - 1, z0 - 1, bb, bar(B_HF + b));
+                    else tma_load_5d(dst + kc * p.plane, &m2, c - p.C1, x0 - 1, y0 - 1, z0 - 1, bb, bar(B_HF + b));
+                }
+                uses[b]++;
+            }
+            // drain: every copy this CTA issued has landed before it exits
+            mb_wait(bar(B_W), 0, abort_flag, p.err, 2, false);
+            for (int b = 0; b < 2; b++)
+                if (uses[b] > 0) mb_wait(bar(B_HF + b), (unsigned)(uses[b] - 1) & 1u, abort_flag, p.err, 2, false);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // -------------------------------------------------------------- MMA
+            if (mb_wait(bar(B_W), 0, abort_flag, p.err, 3)) {
+                const unsigned wtap = (unsigned)kc8 * (unsigned)p.N * 16u;  // bytes of one tap's weights
+                const unsigned nbytes16 = (unsigned)p.N * 16u;              // one channel group of weights
+                int i = 0;
+                for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, i++) {
+                    const int b = i % p.nbuf;
+                    const unsigned k = (unsigned)(i / p.nbuf);
+                    if (!mb_wait(bar(B_HF + b), k & 1u, abort_flag, p.err, 4)) break;
+                    if (k > 0 && !mb_wait(bar(B_AE + b), (k - 1) & 1u, abort_flag, p.err, 5)) break;
+                    tc_fence_after();
+                    const unsigned hb = sH + (unsigned)b * p.halo;
+                    for (int zz = 0; zz < p.Zt; zz++) {
+                        const unsigned d = tmem + (unsigned)((b * p.Zt + zz) * p.N);
+                        unsigned acc = 0;
+                        for (int tz = 0; tz < 3; tz++)
+                            for (int ty = 0; ty < 3; ty++)
+                                for (int tx = 0; tx < 3; tx++) {
+                                    const int tap = 9 * tz + 3 * ty + tx;
+                                    const unsigned a0 = hb + (unsigned)(zz + tz) * ZSTRIDE + (unsigned)ty * YSTRIDE +
+                                                        (unsigned)tx * ROW_BYTES;
+                                    const unsigned w0 = sW + (unsigned)tap * wtap;
+                                    for (int ks = 0; ks < (p.K >> 4); ks++) {
+                                        const unsigned long long ad = sdesc(a0 + 2u * ks * p.plane, p.plane, YSTRIDE);
+                                        const unsigned long long bd = sdesc(w0 + 2u * ks * nbytes16, nbytes16, 128u);
+                                        tc_mma(d, ad, bd, p.idesc, acc);
+                                        acc = 1;
+                                    }
+                                }
+                    }
+                    tc_commit(bar(B_HE + b));
+                    tc_commit(bar(B_AF + b));
+                }
+            }
+            // drain: all MMAs issued by this thread are complete
+            tc_commit(bar(B_DR));
+            mb_wait(bar(B_DR), 0, abort_flag, p.err, 6, false);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int r = 32 * warp + lane;  // TMEM lane = row of the M = 128 block
+        const unsigned lane_addr = (unsigned)(32 * warp) << 16;
+        int i = 0;
+        for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, i++) {
+            const int b = i % p.nbuf;
+            const unsigned k = (unsigned)(i / p.nbuf);
+            int ok = mb_wait(bar(B_AF + b), k & 1u, abort_flag, p.err, 7);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            tc_fence_after();
+            int bb, z0, y0, x0;
+            decode_tile(p, t, bb, z0, y0, x0);
+            const int x = x0 + (r & 7), y = y0 + (r >> 3);
+            for (int zz = 0; zz < p.Zt; zz++) {
+                const int z = z0 + zz;
+                const bool valid = x < p.W && y < p.H && z < p.D;
+                const long long v = (((long long)bb * p.D + z) * p.H + y) * p.W + x;
+                for (int c0 = 0; c0 < p.N; c0 += 16) {
+                    float f[16];
+                    __syncwarp();
+                    tc_ld16(tmem + lane_addr + (unsigned)((b * p.Zt + zz) * p.N + c0), f);
+                    if (!valid) continue;
+                    if (p.bias) {
+#pragma unroll
+                        for (int q = 0; q < 16; q++) f[q] += __ldg(p.bias + c0 + q);
+                    }
+                    if (p.relu) {
+#pragma unroll
+                        for (int q = 0; q < 16; q++) f[q] = fmaxf(f[q], 0.f);
+                    }
+                    uint4 o[2];
+                    unsigned *ou = reinterpret_cast<unsigned *>(o);
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
+                        ou[q] = *reinterpret_cast<unsigned *>(&h2);
+                    }
+                    bf16 *dst = c0 < p.O1 ? p.out1 + v * p.O1 + c0 : p.out2 + v * (p.N - p.O1) + (c0 - p.O1);
+                    reinterpret_cast<uint4 *>(dst)[0] = o[0];
+                    reinterpret_cast<uint4 *>(dst)[1] = o[1];
+                }
+            }
+            tc_fence_before();
+            mb_arrive(bar(B_AE + b));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(p.tmem_cols)
+                     : "memory");
+    }
+}
+
+typedef CUresult (*encode_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+encode_fn get_encode()
+{
+    static encode_fn fn = []() -> encode_fn {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<encode_fn>(f);
+    }();
+    return fn;
+}
+
+// Tensor map of a BF16 (B, D, H, W, C) tensor read in halo boxes of
+// 8 channels x 10 x 18 x zh voxels.
+bool make_map(CUtensorMap *m, const bf16 *ptr, int C, int B, int D, int H, int W, int zh)
+{
+    encode_fn enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
+    cuuint64_t strides[4] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2,
+                             (cuuint64_t)D * H * W * C * 2};
+    cuuint32_t box[5] = {8, (cuuint32_t)HX, (cuuint32_t)HY, (cuuint32_t)zh, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(ptr), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int device_sms()
+{
+    static int n = []() {
+        int d = 0, v = 0;
+        cudaGetDevice(&d);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+        return v > 0 ? v : 1;
+    }();
+    return n;
+}
+
+unsigned pow2_at_least(unsigned v)
+{
+    unsigned c = 32;
+    while (c < v) c <<= 1;
+    return c;
+}
+
+}  // namespace
+
+bool conv3_tc_plan(int N, int K, int D, TcPlan *pl)
+{
+    if (N < 16 || N > 256 || (N % 16) || K < 16 || (K % 16)) return false;
+    const unsigned wbytes = 27u * (unsigned)N * (unsigned)K * 2u;
+    static const int zts[] = {4, 2, 1};
+    for (int nbuf = 2; nbuf >= 1; nbuf--) {
+        for (int zt : zts) {
+            if (zt > 1 && zt > D) continue;
+            const unsigned plane = ((unsigned)(zt + 2) * ZSTRIDE + 127u) & ~127u;
+            const unsigned halo = (unsigned)(K / 8) * plane;
+            const unsigned off_w = HDR;
+            const unsigned off_h = (off_w + wbytes + 127u) & ~127u;
+            const unsigned smem = ALIGN_SLACK + off_h + (unsigned)nbuf * halo;
+            const unsigned cols = pow2_at_least((unsigned)(nbuf * zt * N));
+            if (smem > TC_SMEM_MAX || cols > 512) continue;
+            pl->Zt = zt;
+            pl->nbuf = nbuf;
+            pl->plane = plane;
+            pl->halo = halo;
+            pl->off_w = off_w;
+            pl->off_h = off_h;
+            pl->wbytes = wbytes;
+            pl->smem = smem;
+            pl->tmem_cols = cols;
+            return true;
+        }
+    }
+    return false;
+}
+
+int conv3_tc(const TcConv &c, int *err, cudaStream_t s)
+{
+    const int K = c.C1 + c.C2, N = c.N;
+    TcPlan pl;
+    if ((c.C1 % 8) || (c.C2 % 8) || (c.O1 % 16) || c.O1 > N || !conv3_tc_plan(N, K, c.D, &pl)) return 0;
+    if ((reinterpret_cast<uintptr_t>(c.w) & 15) || (reinterpret_cast<uintptr_t>(c.in1) & 15) ||
+        (c.C2 && (reinterpret_cast<uintptr_t>(c.in2) & 15)))
+        return 0;
+    // from here on the shape is supported: a failure is an error, not a fallback
+    CUtensorMap m1, m2;
+    const int zh = pl.Zt + 2;
+    if (!make_map(&m1, c.in1, c.C1, c.B, c.D, c.H, c.W, zh)) return -1;
+    if (c.C2 > 0) {
+        if (!make_map(&m2, c.in2, c.C2, c.B, c.D, c.H, c.W, zh)) return -1;
+    } else {
+        m2 = m1;
+    }
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, []() {
+        attr_err = cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+    });
+    if (attr_err != cudaSuccess) return -1;
+    TcArgs a;
+    a.w = c.w;
+    a.bias = c.bias;
+    a.out1 = c.out1;
+    a.out2 = c.out2 ? c.out2 : c.out1;
+    a.N = N;
+    a.K = K;
+    a.C1 = c.C1;
+    a.O1 = c.O1;
+    a.relu = c.relu;
+    a.B = c.B; a.D = c.D; a.H = c.H; a.W = c.W;
+    a.Zt = pl.Zt;
+    a.nbuf = pl.nbuf;
+    a.tx = (c.W + 7) / 8;
+    a.ty = (c.H + 15) / 16;
+    a.tz = (c.D + pl.Zt - 1) / pl.Zt;
+    a.ntiles = (long long)a.tx * a.ty * a.tz * c.B;
+    a.wbytes = pl.wbytes;
+    a.plane = pl.plane;
+    a.halo = pl.halo;
+    a.off_w = pl.off_w;
+    a.off_h = pl.off_h;
+    a.tx_bytes = (unsigned)(K / 8) * (unsigned)zh * ZSTRIDE;
+    a.tmem_cols = pl.tmem_cols;
+    // kind::f16 instruction descriptor: FP32 accumulator (bit 4), BF16 A
+    // (bits 7-9 = 1) and B (bits 10-12 = 1), both K-major, N >> 3 at bit 17,
+    // M >> 4 at bit 24 (M = 128).
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((128u >> 4) << 24);
+    a.err = err;
+    const int per_sm_smem = (int)(TC_SMEM_SM / (pl.smem + 1024u));
+    const int per_sm_tmem = (int)(512u / pl.tmem_cols);
+    int per_sm = per_sm_smem < per_sm_tmem ? per_sm_smem : per_sm_tmem;
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)device_sms() * per_sm;
+    if (grid > a.ntiles) grid = a.ntiles;
+    if (grid < 1) return 1;
+    counted(k_conv3_tc)<<<(unsigned)grid, TC_THREADS, pl.smem, s>>>(m1, m2, a);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+// [taps][Npad][Kpad] (K innermost) -> [taps][Kpad / 8][Npad][8]
+__global__ void k_pack_w_tc(const bf16 *__restrict__ src, int taps, int Npad, int Kpad, bf16 *__restrict__ dst)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tot = (long long)taps * Npad * Kpad;
+    if (e >= tot) return;
+    int j = (int)(e & 7);
+    long long q = e >> 3;
+    int n = (int)(q % Npad);
+    q /= Npad;
+    int kc = (int)(q % (Kpad / 8));
+    int t = (int)(q / (Kpad / 8));
+    dst[e] = src[((long long)t * Npad + n) * Kpad + 8 * kc + j];
+}
+
+int pack_w_tc(const bf16 *src, int taps, int Npad, int Kpad, bf16 *dst, cudaStream_t s)
+{
+    long long tot = (long long)taps * Npad * Kpad;
+    counted(k_pack_w_tc)<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, taps, Npad, Kpad, dst);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace gnb

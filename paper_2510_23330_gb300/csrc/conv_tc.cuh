@@ -1,0 +1,50 @@
+// conv_tc.cuh -- host interface of the tcgen05 3^3 convolution (conv_tc.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace gnb {
+
+constexpr unsigned TC_SMEM_MAX = 232448;  // opt-in dynamic shared memory per CTA (227 KB)
+constexpr unsigned TC_SMEM_SM = 233472;   // shared memory per SM (228 KB)
+
+// out[v][n] = act(bias[n] + sum_{tap, k} in[v + tap][k] * w[tap][k][n]) over the
+// 27 taps of a zero-padded 3^3 neighbourhood; the input is the channel
+// concatenation of in1 (C1 channels) and in2 (C2 channels), the output is
+// split into out1 (channels [0, O1)) and out2 (channels [O1, N)).  All
+// tensors are BF16 with channels innermost on a (B, D, H, W) grid.
+struct TcConv {
+    const __nv_bfloat16 *in1, *in2;
+    int C1, C2;
+    const __nv_bfloat16 *w;  // packed [27][(C1 + C2) / 8][N][8]
+    const float *bias;       // [N] or null
+    int N;
+    __nv_bfloat16 *out1, *out2;
+    int O1;
+    int relu;
+    int B, D, H, W;
+};
+
+struct TcPlan {
+    int Zt, nbuf;
+    unsigned plane, halo, off_w, off_h, wbytes, smem, tmem_cols;
+};
+
+// Tile depth, buffering and shared-memory layout for N output and K input
+// channels on a grid of depth D; false when the shape is not supported
+// (N or K not a multiple of 16, N > 256, or the resident weights too large).
+bool conv3_tc_plan(int N, int K, int D, TcPlan *pl);
+
+// Launches the convolution on s.  Returns 1 when launched, 0 when the shape
+// or alignment is not supported (nothing launched; the caller uses another
+// kernel), -1 when a supported shape cannot be launched (tensor-map encoding
+// or launch error).  A device-side wait that runs out writes a
+// non-zero code into *err (device memory).
+int conv3_tc(const TcConv &c, int *err, cudaStream_t s);
+
+// Re-layout of packed weights [taps][Npad][Kpad] into the tensor-core
+// layout [taps][Kpad / 8][Npad][8].
+int pack_w_tc(const __nv_bfloat16 *src, int taps, int Npad, int Kpad, __nv_bfloat16 *dst, cudaStream_t s);
+
+}  // namespace gnb

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "conv_tc.cuh"
 
 typedef __nv_bfloat16 bf16;
 
@@ -446,6 +447,7 @@ struct ULayer {
     long long woff, boff;       // offsets in the flat parameter array
     int Npad, Kpad, Nd, Kd;     // padded forward / input-gradient GEMM shapes
     bf16 *wf = nullptr, *wd = nullptr;
+    bf16 *wtc = nullptr, *wdtc = nullptr;  // tensor-core layouts of wf / wd (3^3 layers)
 };
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
@@ -468,6 +470,9 @@ struct gnb_unet {
     bf16 *dyb = nullptr;
     std::vector<bf16 *> tmp;     // backward scratch
     double *loss_d = nullptr;
+    int *err_d = nullptr;        // device error word of the tcgen05 convolutions
+    int conv_impl = GNB_CONV_AUTO;
+    bool launch_failed = false;
     std::string err;
 };
 
@@ -594,6 +599,8 @@ int unet_pack(gnb_unet *u)
         long long nd = (long long)l.taps * l.Nd * l.Kd;
         counted(k_pack_w_dgrad)<<<(unsigned)((nd + 255) / 256), 256, 0, u->s>>>(
             u->p + l.woff, l.taps, l.kind == L_CONV3 ? 1 : 0, l.cin, l.cout, l.Nd, l.Kd, l.wd);
+        if (l.wtc && pack_w_tc(l.wf, l.taps, l.Npad, l.Kpad, l.wtc, u->s) != 0) return GNB_ECUDA;
+        if (l.wdtc && pack_w_tc(l.wd, l.taps, l.Nd, l.Kd, l.wdtc, u->s) != 0) return GNB_ECUDA;
     }
     return cudaGetLastError() == cudaSuccess ? GNB_OK : GNB_ECUDA;
 }
@@ -606,9 +613,27 @@ int LI_DECA(const gnb_unet *u, int l) { return LI_UP(u, l) + 1; }
 int LI_DECB(const gnb_unet *u, int l) { return LI_UP(u, l) + 2; }
 int LI_HEAD(const gnb_unet *u) { return 2 * u->levels + 3 * (u->levels - 1); }
 
+// The tcgen05 path for a 3^3 convolution: 1 launched, 0 not applicable, -1 error.
+int conv3_try_tc(gnb_unet *u, const bf16 *wtc, int N, int B, int D, const bf16 *in1, int C1, const bf16 *in2, int C2,
+                 const float *bias, bf16 *out1, int O1, bf16 *out2, int relu)
+{
+    if (!wtc || u->conv_impl == GNB_CONV_MMA_SYNC) return 0;
+    TcConv c;
+    c.in1 = in1; c.in2 = in2 ? in2 : in1; c.C1 = C1; c.C2 = C2;
+    c.w = wtc; c.bias = bias; c.N = N;
+    c.out1 = out1; c.out2 = out2 ? out2 : out1; c.O1 = O1; c.relu = relu;
+    c.B = B; c.D = D; c.H = D; c.W = D;
+    return conv3_tc(c, u->err_d, u->s);
+}
+
 void conv_fwd(gnb_unet *u, const ULayer &ly, int mode, int B, int D, const bf16 *in1, int C1, const bf16 *in2, int C2,
               bf16 *out, float *outf, int relu)
 {
+    if (mode == IG_CONV3 && !outf) {
+        int rc = conv3_try_tc(u, ly.wtc, ly.Npad, B, D, in1, C1, in2, C2, u->p + ly.boff, out, ly.cout, nullptr,
+                              relu);
+        if (rc != 0) { if (rc < 0) u->launch_failed = true; return; }
+    }
     IgArgs a = ig_base(mode, B, D, D, D);
     a.in1 = in1; a.in2 = in2 ? in2 : in1; a.C1 = C1; a.C2 = C2;
     a.w = ly.wf; a.bias = u->p + ly.boff; a.N = ly.cout; a.Npad = ly.Npad;
@@ -620,6 +645,10 @@ void conv_fwd(gnb_unet *u, const ULayer &ly, int mode, int B, int D, const bf16 
 void conv_dgrad(gnb_unet *u, const ULayer &ly, int mode, int B, int D, const bf16 *dz, int Cz, bf16 *dx1, int O1,
                 bf16 *dx2)
 {
+    if (mode == IG_CONV3 && Cz == ly.Kd) {
+        int rc = conv3_try_tc(u, ly.wdtc, ly.Nd, B, D, dz, Cz, nullptr, 0, nullptr, dx1, O1, dx2, 0);
+        if (rc != 0) { if (rc < 0) u->launch_failed = true; return; }
+    }
     IgArgs a = ig_base(mode, B, D, D, D);
     a.in1 = dz; a.in2 = dz; a.C1 = Cz; a.C2 = 0;
     a.w = ly.wd; a.bias = nullptr; a.N = ly.cin; a.Npad = ly.Nd;
@@ -673,7 +702,7 @@ int unet_forward(gnb_unet *u, int B)
         h = u->act[S_DECB(u, l)];
     }
     conv_fwd(u, u->L[LI_HEAD(u)], IG_CONV1, B, G, h, u->base, nullptr, 0, nullptr, u->yout, 0);
-    return cudaGetLastError() == cudaSuccess ? GNB_OK : GNB_ECUDA;
+    return cudaGetLastError() == cudaSuccess && !u->launch_failed ? GNB_OK : GNB_ECUDA;
 }
 
 // Backward through the network for dy in u->dyb (16 channels); gradients
@@ -740,14 +769,25 @@ int unet_backward(gnb_unet *u, int B)
             dcur = T0;
         }
     }
-    return cudaGetLastError() == cudaSuccess ? GNB_OK : GNB_ECUDA;
+    return cudaGetLastError() == cudaSuccess && !u->launch_failed ? GNB_OK : GNB_ECUDA;
 }
 
+// Synchronise and collect errors: launch failures, CUDA errors and the
+// tcgen05 convolutions' device error word (a bounded wait that ran out).
 int unet_check(gnb_unet *u, int rc)
 {
-    if (rc != GNB_OK) return rc;
+    u->launch_failed = false;
     if (cudaStreamSynchronize(u->s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GNB_ECUDA;
-    return GNB_OK;
+    int e = 0;
+    if (u->err_d) {
+        if (cudaMemcpy(&e, u->err_d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GNB_ECUDA;
+        if (e != 0) {
+            cudaMemsetAsync(u->err_d, 0, sizeof(int), u->s);
+            cudaStreamSynchronize(u->s);
+            return GNB_ETIMEOUT;
+        }
+    }
+    return rc;
 }
 
 }  // namespace
@@ -766,6 +806,15 @@ int unet_prepare(gnb_unet *u, int batch, bf16 **xin, float **yout, int *grid, in
     *grid = u->grid;
     *cout = u->cout;
     return GNB_OK;
+}
+
+int unet_poll_error(gnb_unet *u)
+{
+    int e = 0;
+    if (!u || !u->err_d || cudaMemcpy(&e, u->err_d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GNB_OK;
+    if (e == 0) return GNB_OK;
+    cudaMemset(u->err_d, 0, sizeof(int));
+    return GNB_ETIMEOUT;
 }
 
 int unet_run(gnb_unet *u, int batch, cudaStream_t stream)
@@ -825,10 +874,16 @@ int gnb_unet_create(gnb_unet **out, int cin, int cout, int base, int levels, int
               cudaMalloc((void **)&u->g, u->nparam * 4) == cudaSuccess &&
               cudaMalloc((void **)&u->m, u->nparam * 4) == cudaSuccess &&
               cudaMalloc((void **)&u->v, u->nparam * 4) == cudaSuccess &&
-              cudaMalloc((void **)&u->loss_d, 16) == cudaSuccess;
+              cudaMalloc((void **)&u->loss_d, 16) == cudaSuccess &&
+              cudaMalloc((void **)&u->err_d, sizeof(int)) == cudaSuccess;
     for (auto &l : u->L) {
         ok = ok && cudaMalloc((void **)&l.wf, (size_t)l.taps * l.Npad * l.Kpad * 2) == cudaSuccess &&
              cudaMalloc((void **)&l.wd, (size_t)l.taps * l.Nd * l.Kd * 2) == cudaSuccess;
+        TcPlan pl;
+        if (ok && l.kind == L_CONV3 && conv3_tc_plan(l.Npad, l.Kpad, grid, &pl))
+            ok = cudaMalloc((void **)&l.wtc, (size_t)l.taps * l.Npad * l.Kpad * 2) == cudaSuccess;
+        if (ok && l.kind == L_CONV3 && conv3_tc_plan(l.Nd, l.Kd, grid, &pl))
+            ok = cudaMalloc((void **)&l.wdtc, (size_t)l.taps * l.Nd * l.Kd * 2) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();
@@ -839,6 +894,7 @@ int gnb_unet_create(gnb_unet **out, int cin, int cout, int base, int levels, int
     cudaMemsetAsync(u->g, 0, u->nparam * 4, u->s);
     cudaMemsetAsync(u->m, 0, u->nparam * 4, u->s);
     cudaMemsetAsync(u->v, 0, u->nparam * 4, u->s);
+    cudaMemsetAsync(u->err_d, 0, sizeof(int), u->s);
     *out = u;
     return unet_check(u, unet_pack(u));
 }
@@ -851,14 +907,24 @@ void gnb_unet_destroy(gnb_unet *u)
     for (auto &l : u->L) {
         if (l.wf) cudaFree(l.wf);
         if (l.wd) cudaFree(l.wd);
+        if (l.wtc) cudaFree(l.wtc);
+        if (l.wdtc) cudaFree(l.wdtc);
     }
     float *a[] = {u->p, u->g, u->m, u->v};
     for (float *q : a) if (q) cudaFree(q);
     if (u->loss_d) cudaFree(u->loss_d);
+    if (u->err_d) cudaFree(u->err_d);
     delete u;
 }
 
 int64_t gnb_unet_num_params(const gnb_unet *u) { return u ? u->nparam : -1; }
+
+int gnb_unet_set_conv_impl(gnb_unet *u, int impl)
+{
+    if (!u || (impl != GNB_CONV_AUTO && impl != GNB_CONV_MMA_SYNC)) return GNB_EINVAL;
+    u->conv_impl = impl;
+    return GNB_OK;
+}
 
 int gnb_unet_get_params(gnb_unet *u, float *dst, int on_device)
 {

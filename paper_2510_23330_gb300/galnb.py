@@ -30,6 +30,8 @@ GNB_GAS = 1
 GNB_GRAV_DIRECT = 0
 GNB_GRAV_TREE = 1
 GNB_GRAV_NONE = 2
+GNB_CONV_AUTO = 0
+GNB_CONV_MMA_SYNC = 2
 
 FIELDS = ["X", "Y", "Z", "VX", "VY", "VZ", "AX", "AY", "AZ", "POT", "U", "DUDT", "RHO", "PRES", "CS", "H2",
           "KEY", "ORDER", "NBR", "NODES", "GROUPS", "ID", "AGRAV_X", "AGRAV_Y", "AGRAV_Z"]
@@ -117,6 +119,8 @@ def _declare(L):
     for name in ("gnb_unet_get_params", "gnb_unet_set_params", "gnb_unet_get_grads"):
         getattr(L, name).argtypes = [_vp, _vp, C.c_int]
         getattr(L, name).restype = C.c_int
+    L.gnb_unet_set_conv_impl.argtypes = [_vp, C.c_int]
+    L.gnb_unet_set_conv_impl.restype = C.c_int
     L.gnb_unet_forward.argtypes = [_vp, C.c_int, _vp, _vp, C.c_int]
     L.gnb_unet_forward.restype = C.c_int
     L.gnb_unet_train_step.argtypes = [_vp, C.c_int, _vp, _vp, C.c_double, C.POINTER(C.c_double), C.c_int]
@@ -230,6 +234,10 @@ def gnb_unet_num_params(net):
     return lib().gnb_unet_num_params(net)
 
 
+def gnb_unet_set_conv_impl(net, impl):
+    return lib().gnb_unet_set_conv_impl(net, impl)
+
+
 def gnb_unet_get_params(net, dst, on_device):
     return lib().gnb_unet_get_params(net, dst, on_device)
 
@@ -275,6 +283,10 @@ class UNet:
     def _chk(rc, what):
         if rc != GNB_OK:
             raise GalnbError(rc, what)
+
+    def set_conv_impl(self, impl):
+        """GNB_CONV_AUTO (tcgen05 where supported) or GNB_CONV_MMA_SYNC."""
+        self._chk(gnb_unet_set_conv_impl(self.h, impl), "set_conv_impl")
 
     def num_params(self):
         return int(gnb_unet_num_params(self.h))

@@ -38,7 +38,10 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (np.linalg.norm(b) + 1e-30))
 
 
-def _setup(G, grid, batch, seed=0, base=16, levels=4):
+IMPLS = {"auto": 0, "mma_sync": 2}
+
+
+def _setup(G, grid, batch, seed=0, base=16, levels=4, impl="auto"):
     spec = U.layer_spec(5, 5, base, levels)
     p = U.init_params(seed, 5, 5, base, levels)
     rng = np.random.default_rng(seed + 1)
@@ -47,39 +50,44 @@ def _setup(G, grid, batch, seed=0, base=16, levels=4):
             p[k] = rng.normal(0, 0.1, p[k].shape)
     x = U.bf16(rng.normal(size=(batch, grid, grid, grid, 5)))
     net = G.UNet(5, 5, base, levels, grid)
+    net.set_conv_impl(IMPLS[impl])
     net.set_params(flat(p, spec).astype(np.float32))
     # the GPU keeps FP32 master weights; the oracle sees the FP32 values
     p = unflat(net.get_params(), spec, p)
     return spec, p, x, net
 
 
-@pytest.mark.parametrize("grid,batch", [(16, 2), (64, 1)])
-def test_forward_matches_oracle(G, grid, batch):
-    spec, p, x, net = _setup(G, grid, batch)
+# 20^3 with 3 levels leaves ragged tensor-core tiles in x (8 + 8 + 4), y
+# (16 + 4) and z (level 1: 10 = 4 + 4 + 2).
+@pytest.mark.parametrize("impl", ["auto", "mma_sync"])
+@pytest.mark.parametrize("grid,batch,levels", [(16, 2, 4), (20, 2, 3), (64, 1, 4)])
+def test_forward_matches_oracle(G, grid, batch, levels, impl):
+    spec, p, x, net = _setup(G, grid, batch, levels=levels, impl=impl)
     y = net.forward(x.astype(np.float32))
-    ref, _ = U.forward(p, x, bf=True)
+    ref, _ = U.forward(p, x, levels=levels, bf=True)
     assert rel_l2(y, ref) < 1e-2
     assert np.max(np.abs(y - ref)) < 0.05 * np.max(np.abs(ref))
 
 
-def test_gradients_match_oracle(G):
-    spec, p, x, net = _setup(G, 16, 2, seed=3)
+@pytest.mark.parametrize("grid,levels,impl", [(16, 4, "auto"), (16, 4, "mma_sync"), (20, 3, "auto")])
+def test_gradients_match_oracle(G, grid, levels, impl):
+    spec, p, x, net = _setup(G, grid, 2, seed=3, levels=levels, impl=impl)
     rng = np.random.default_rng(9)
     t = rng.normal(size=x.shape)
     loss = net.train_step(x.astype(np.float32), t.astype(np.float32), 0.0)
-    y, cache = U.forward(p, x, bf=True)
+    y, cache = U.forward(p, x, levels=levels, bf=True)
     ref_loss, dy = U.mse(y, t)
     assert abs(loss / ref_loss - 1.0) < 1e-2
     g = unflat(net.get_grads(), spec, p)
-    rg = U.backward(p, cache, dy, bf=True)
+    rg = U.backward(p, cache, dy, levels=levels, bf=True)
     # Sensitivity of each gradient to BF16 storage: the same oracle without
     # any BF16 rounding.  Deep layers (the 2^3 bottleneck at this size sums
     # few voxels with cancellation) move by several per cent between the two,
     # and FP32-vs-FP64 accumulation flips individual BF16 roundings on the
     # GPU in the same way, so each layer's bound scales with its sensitivity.
-    y64, cache64 = U.forward(p, x, bf=False)
+    y64, cache64 = U.forward(p, x, levels=levels, bf=False)
     _, dy64 = U.mse(y64, t)
-    rg64 = U.backward(p, cache64, dy64, bf=False)
+    rg64 = U.backward(p, cache64, dy64, levels=levels, bf=False)
     sens = {k: rel_l2(rg64[k], rg[k]) for k in rg}
     errs = {k: rel_l2(g[k], rg[k]) for k in rg}
     errs64 = {k: rel_l2(g[k], rg64[k]) for k in rg}
