@@ -3,20 +3,25 @@
 // the input gradient of the surrogate U-Net's 3^3 convolutions (Sec. 3.3 of
 // Hirashima et al., SC'25).
 //
+// Activations are blocked by 8 channels, [batch][channel / 8][z][y][x][8], so
+// 10 x voxels of one channel group are one contiguous 160-byte row.
+//
 // One output tile is 8 (x) x 16 (y) voxels x Zt z-planes; each z-plane is one
 // M = 128 MMA row block (row r = 8 y + x).  The tile's input halo,
 // (Zt + 2) x 18 x 10 voxels, is brought into shared memory once by TMA (one
-// 5-D box per group of 8 channels; out-of-range voxels are zero-filled by the
-// TMA unit, which is exactly the zero padding of the convolution) and stored
-// as [channel group][z][y][x][8 channels]: eight consecutive x voxels of one
-// channel group form one 8 x 16-byte core matrix of the canonical K-major
-// no-swizzle layout, so every one of the 27 taps is the same descriptor with
-// its start address shifted by the tap's (z, y, x) offset -- no im2col copy.
+// 4-D box of 18 (Zt + 2) rows of 160 bytes per channel group; out-of-range
+// voxels are zero-filled by the TMA unit, which is exactly the zero padding
+// of the convolution) and lands as [channel group][z][y][x][8 channels]:
+// eight consecutive x voxels of one channel group form one 8 x 16-byte core
+// matrix of the canonical K-major no-swizzle layout, so every one of the 27
+// taps is the same descriptor with its start address shifted by the tap's
+// (z, y, x) offset -- no im2col copy.
 // The weights of all taps stay resident in shared memory for the whole
 // persistent CTA, packed [tap][channel group][N][8].
 //
-// Roles (192 threads): warp 4 lane 0 issues the TMA loads, warp 5 lane 0
-// issues tcgen05.mma (FP32 accumulators in TMEM), warps 0..3 read TMEM with
+// Roles (192 threads): warp 4 lane 0 issues the TMA loads, warp 5 runs the
+// MMA loop warp-uniformly and one elected lane issues tcgen05.mma (FP32
+// accumulators in TMEM), warps 0..3 read TMEM with
 // tcgen05.ld and apply bias, ReLU and the BF16 store.  Halo buffers and TMEM
 // accumulators are double buffered so the loads of tile i + 1, the MMAs of
 // tile i and the epilogue of tile i - 1 overlap.  Every mbarrier wait is
@@ -114,13 +119,13 @@ __device__ bool mb_wait(unsigned bar, unsigned parity, volatile int *abort_flag,
     }
 }
 
-__device__ __forceinline__ void tma_load_5d(unsigned dst, const CUtensorMap *m, int c0, int c1, int c2, int c3, int c4,
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap *m, int c0, int c1, int c2, int c3,
                                             unsigned bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-        "%6}], [%7];\n" ::"r"(dst),
-        "l"(reinterpret_cast<unsigned long long>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
         : "memory");
 }
 __device__ __forceinline__ void bulk_load(unsigned dst, const void *src, unsigned bytes, unsigned bar)
@@ -143,18 +148,23 @@ __device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo,
            ((unsigned long long)(sbo >> 4) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
-                                       unsigned acc)
+// MMA and commit are executed by the whole warp in uniform control flow (so
+// the operands stay warp-uniform); elect.sync picks the one lane that issues.
+__device__ __forceinline__ void tc_mma_elect(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                             unsigned acc)
 {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d),
+        "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
-__device__ __forceinline__ void tc_commit(unsigned bar)
+__device__ __forceinline__ void tc_commit_elect(unsigned bar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+    asm volatile(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(bar)
+        : "memory");
 }
 
 // 16 consecutive FP32 columns of this thread's TMEM lane; the wait is in the
@@ -242,10 +252,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 decode_tile(p, t, bb, z0, y0, x0);
                 mb_expect_tx(bar(B_HF + b), p.tx_bytes);
                 const unsigned dst = sH + (unsigned)b * p.halo;
+                // x and the 8 channels of a group form the innermost TMA
+                // dimension: start 8 (x0 - 1) elements = 16 (x0 - 1) bytes
+                const int g1 = p.C1 >> 3, g2 = (p.K - p.C1) >> 3;
                 for (int kc = 0; kc < kc8; kc++) {
-                    const int c = 8 * kc;
-                    if (c < p.C1) tma_load_5d(dst + kc * p.plane, &m1, c, x0 - 1, y0 - 1, z0 - 1, bb, bar(B_HF + b));
-                    else tma_load_5d(dst + kc * p.plane, &m2, c - p.C1, x0 - 1, y0 - 1, z0 - 1, bb, bar(B_HF + b));
+                    if (kc < g1)
+                        tma_load_4d(dst + kc * p.plane, &m1, 8 * (x0 - 1), y0 - 1, z0 - 1, bb * g1 + kc, bar(B_HF + b));
+                    else
+                        tma_load_4d(dst + kc * p.plane, &m2, 8 * (x0 - 1), y0 - 1, z0 - 1, bb * g2 + (kc - g1),
+                                    bar(B_HF + b));
                 }
                 uses[b]++;
             }
@@ -255,49 +270,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (uses[b] > 0) mb_wait(bar(B_HF + b), (unsigned)(uses[b] - 1) & 1u, abort_flag, p.err, 2, false);
         }
     } else if (warp == 5) {
-        if (lane == 0) {
-            // -------------------------------------------------------------- MMA
-            if (mb_wait(bar(B_W), 0, abort_flag, p.err, 3)) {
-                const unsigned wtap = (unsigned)kc8 * (unsigned)p.N * 16u;  // bytes of one tap's weights
-                const unsigned nbytes16 = (unsigned)p.N * 16u;              // one channel group of weights
-                int i = 0;
-                for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, i++) {
-                    const int b = i % p.nbuf;
-                    const unsigned k = (unsigned)(i / p.nbuf);
-                    if (!mb_wait(bar(B_HF + b), k & 1u, abort_flag, p.err, 4)) break;
-                    if (k > 0 && !mb_wait(bar(B_AE + b), (k - 1) & 1u, abort_flag, p.err, 5)) break;
-                    tc_fence_after();
-                    const unsigned hb = sH + (unsigned)b * p.halo;
-                    for (int zz = 0; zz < p.Zt; zz++) {
-                        const unsigned d = tmem + (unsigned)((b * p.Zt + zz) * p.N);
-                        unsigned acc = 0;
-                        for (int tz = 0; tz < 3; tz++)
-                            for (int ty = 0; ty < 3; ty++)
-                                for (int tx = 0; tx < 3; tx++) {
-                                    const int tap = 9 * tz + 3 * ty + tx;
-                                    const unsigned a0 = hb + (unsigned)(zz + tz) * ZSTRIDE + (unsigned)ty * YSTRIDE +
-                                                        (unsigned)tx * ROW_BYTES;
-                                    const unsigned w0 = sW + (unsigned)tap * wtap;
-                                    for (int ks = 0; ks < (p.K >> 4); ks++) {
-                                        const unsigned long long ad = sdesc(a0 + 2u * ks * p.plane, p.plane, YSTRIDE);
-                                        const unsigned long long bd = sdesc(w0 + 2u * ks * nbytes16, nbytes16, 128u);
-                                        tc_mma(d, ad, bd, p.idesc, acc);
-                                        acc = 1;
-                                    }
-                                }
-                    }
-                    tc_commit(bar(B_HE + b));
-                    tc_commit(bar(B_AF + b));
+        // ------------------------------------------------------------------ MMA
+        // The Zt z-planes of a tile accumulate into Zt independent TMEM
+        // blocks; their MMAs are interleaved so consecutive MMAs never feed
+        // the same accumulator.
+        int ok = mb_wait(bar(B_W), 0, abort_flag, p.err, 3);
+        if (__all_sync(0xffffffffu, ok)) {
+            const unsigned wtap = (unsigned)kc8 * (unsigned)p.N * 16u;  // bytes of one tap's weights
+            const unsigned nbytes16 = (unsigned)p.N * 16u;              // one channel group of weights
+            int i = 0;
+            for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, i++) {
+                const int b = i % p.nbuf;
+                const unsigned k = (unsigned)(i / p.nbuf);
+                ok = mb_wait(bar(B_HF + b), k & 1u, abort_flag, p.err, 4);
+                if (!__all_sync(0xffffffffu, ok)) break;
+                if (k > 0) {
+                    ok = mb_wait(bar(B_AE + b), (k - 1) & 1u, abort_flag, p.err, 5);
+                    if (!__all_sync(0xffffffffu, ok)) break;
                 }
+                tc_fence_after();
+                const unsigned hb = sH + (unsigned)b * p.halo;
+                const unsigned d0 = tmem + (unsigned)(b * p.Zt * p.N);
+                for (int tap = 0; tap < 27; tap++) {
+                    const int tz = tap / 9, ty = (tap / 3) % 3, tx = tap % 3;
+                    const unsigned a0 = hb + (unsigned)tz * ZSTRIDE + (unsigned)ty * YSTRIDE + (unsigned)tx * ROW_BYTES;
+                    const unsigned w0 = sW + (unsigned)tap * wtap;
+                    for (int ks = 0; ks < (p.K >> 4); ks++) {
+                        const unsigned long long bd = sdesc(w0 + 2u * ks * nbytes16, nbytes16, 128u);
+                        const unsigned acc = (tap | ks) != 0;
+                        for (int zz = 0; zz < p.Zt; zz++) {
+                            const unsigned long long ad =
+                                sdesc(a0 + (unsigned)zz * ZSTRIDE + 2u * ks * p.plane, p.plane, YSTRIDE);
+                            tc_mma_elect(d0 + (unsigned)(zz * p.N), ad, bd, p.idesc, acc);
+                        }
+                    }
+                }
+                tc_commit_elect(bar(B_HE + b));
+                tc_commit_elect(bar(B_AF + b));
             }
-            // drain: all MMAs issued by this thread are complete
-            tc_commit(bar(B_DR));
-            mb_wait(bar(B_DR), 0, abort_flag, p.err, 6, false);
         }
+        // drain: all MMAs issued by this warp's elected lane are complete
+        tc_commit_elect(bar(B_DR));
+        mb_wait(bar(B_DR), 0, abort_flag, p.err, 6, false);
+        __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
         const int r = 32 * warp + lane;  // TMEM lane = row of the M = 128 block
         const unsigned lane_addr = (unsigned)(32 * warp) << 16;
+        const long long Vs = (long long)p.D * p.H * p.W;
         int i = 0;
         for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, i++) {
             const int b = i % p.nbuf;
@@ -312,7 +332,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int zz = 0; zz < p.Zt; zz++) {
                 const int z = z0 + zz;
                 const bool valid = x < p.W && y < p.H && z < p.D;
-                const long long v = (((long long)bb * p.D + z) * p.H + y) * p.W + x;
+                const long long sv = ((long long)z * p.H + y) * p.W + x;
                 for (int c0 = 0; c0 < p.N; c0 += 16) {
                     float f[16];
                     __syncwarp();
@@ -333,9 +353,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
                         ou[q] = *reinterpret_cast<unsigned *>(&h2);
                     }
-                    bf16 *dst = c0 < p.O1 ? p.out1 + v * p.O1 + c0 : p.out2 + v * (p.N - p.O1) + (c0 - p.O1);
-                    reinterpret_cast<uint4 *>(dst)[0] = o[0];
-                    reinterpret_cast<uint4 *>(dst)[1] = o[1];
+                    // two channel groups: two 16-byte pieces, Vs * 8 elements apart
+                    const bool lo = c0 < p.O1;
+                    const int Cx = lo ? p.O1 : p.N - p.O1, cc = lo ? c0 : c0 - p.O1;
+                    bf16 *dst = (lo ? p.out1 : p.out2) + (((long long)bb * (Cx >> 3) + (cc >> 3)) * Vs + sv) * 8;
+                    *reinterpret_cast<uint4 *>(dst) = o[0];
+                    *reinterpret_cast<uint4 *>(dst + Vs * 8) = o[1];
                 }
             }
             tc_fence_before();
@@ -372,18 +395,18 @@ encode_fn get_encode()
     return fn;
 }
 
-// Tensor map of a BF16 (B, D, H, W, C) tensor read in halo boxes of
-// 8 channels x 10 x 18 x zh voxels.
+// Tensor map of a blocked BF16 tensor [B][C / 8][D][H][W][8] viewed as 4-D
+// (8 W, H, D, B C / 8) and read in halo boxes of 8 x 10 elements (10 voxels
+// of one channel group) x 18 x zh.
 bool make_map(CUtensorMap *m, const bf16 *ptr, int C, int B, int D, int H, int W, int zh)
 {
     encode_fn enc = get_encode();
     if (!enc) return false;
-    cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
-    cuuint64_t strides[4] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2,
-                             (cuuint64_t)D * H * W * C * 2};
-    cuuint32_t box[5] = {8, (cuuint32_t)HX, (cuuint32_t)HY, (cuuint32_t)zh, 1};
-    cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(ptr), dims, strides, box, es,
+    cuuint64_t dims[4] = {(cuuint64_t)W * 8, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B * (C / 8)};
+    cuuint64_t strides[3] = {(cuuint64_t)W * 16, (cuuint64_t)H * W * 16, (cuuint64_t)D * H * W * 16};
+    cuuint32_t box[4] = {8 * HX, (cuuint32_t)HY, (cuuint32_t)zh, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(ptr), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }

@@ -13,7 +13,8 @@ constexpr unsigned TC_SMEM_SM = 233472;   // shared memory per SM (228 KB)
 // 27 taps of a zero-padded 3^3 neighbourhood; the input is the channel
 // concatenation of in1 (C1 channels) and in2 (C2 channels), the output is
 // split into out1 (channels [0, O1)) and out2 (channels [O1, N)).  All
-// tensors are BF16 with channels innermost on a (B, D, H, W) grid.
+// tensors are BF16 on a (B, D, H, W) grid, blocked by 8 channels:
+// [B][C / 8][D][H][W][8]; C1, C2, O1 and N are multiples of 16.
 struct TcConv {
     const __nv_bfloat16 *in1, *in2;
     int C1, C2;

@@ -120,8 +120,9 @@ __global__ void k_vox_scatter(PArr p, int n, const int *__restrict__ reg, const 
     }
 }
 
-// standardised channels; FP32 [r][v][5] and/or BF16 [r][v][16] (U-Net input)
-__global__ void k_vox_finalize(const float *__restrict__ acc, long long nv, float *__restrict__ out,
+// standardised channels; FP32 [r][v][5] and/or BF16 [r][2][v][8] (the U-Net's
+// input: 16 channels blocked by 8, vs voxels per region)
+__global__ void k_vox_finalize(const float *__restrict__ acc, long long nv, long long vs, float *__restrict__ out,
                                bf16 *__restrict__ outb)
 {
     long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -135,8 +136,11 @@ __global__ void k_vox_finalize(const float *__restrict__ acc, long long nv, floa
     for (int c = 0; c < 3; c++) z[2 + c] = den > 0.f ? a[3 + c] / den / 20.f : 0.f;
     if (out)
         for (int c = 0; c < 5; c++) out[v * 5 + c] = z[c];
-    if (outb)
-        for (int c = 0; c < 16; c++) outb[v * 16 + c] = __float2bfloat16_rn(c < 5 ? z[c] : 0.f);
+    if (outb) {
+        long long r = v / vs, sv = v - r * vs;
+        for (int c = 0; c < 16; c++)
+            outb[((r * 2 + (c >> 3)) * vs + sv) * 8 + (c & 7)] = __float2bfloat16_rn(c < 5 ? z[c] : 0.f);
+    }
 }
 
 __global__ void k_remap_weights(const float *__restrict__ pred, long long nv, int cout, double *__restrict__ w)
@@ -226,7 +230,8 @@ static int vox_launch(gnb_ctx *c, int nreg, double side, int grid, float *out, b
                                                                 c->rcount);
     cudaMemsetAsync(c->vacc, 0, sizeof(float) * nv * 6, c->s);
     counted(k_vox_scatter)<<<(n + 127) / 128, 128, 0, c->s>>>(a, n, c->sreg, c->rho, c->cent_d, side, grid, c->vacc);
-    counted(k_vox_finalize)<<<(unsigned)((nv + 255) / 256), 256, 0, c->s>>>(c->vacc, (long long)nv, out, outb);
+    counted(k_vox_finalize)<<<(unsigned)((nv + 255) / 256), 256, 0, c->s>>>(
+        c->vacc, (long long)nv, (long long)grid * grid * grid, out, outb);
     GNB_LAUNCH_CHECK(c, "voxelise");
     return GNB_OK;
 }

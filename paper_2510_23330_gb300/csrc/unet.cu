@@ -7,8 +7,11 @@
 // widths base, 2 base, 4 base, 8 base; two 3^3 convolutions (zero "same"
 // padding, ReLU) per level; 2^3 max-pool down; 2^3 stride-2 transposed
 // convolution up; skip tensor concatenated before the up-sampled tensor; 1^3
-// linear head.  Activations are BF16 in (batch, z, y, x, channel) order with
-// channels innermost; the network input is padded to 16 channels.
+// linear head.  Activations are BF16 and blocked by 8 channels:
+// [batch][channel / 8][z][y][x][channel % 8], so that 8 channels of one
+// voxel are one 16-byte piece and a run of x voxels of one channel group is
+// contiguous (the tensor-core convolution loads its halo rows by TMA); the
+// network input is padded to 16 channels.
 //
 // Every convolution-shaped product is one implicit GEMM (rows = output
 // voxels, columns = output channels, K = taps x input channels) on the
@@ -49,6 +52,14 @@ struct IgArgs {
     int relu;
     int B, D, H, W;         // grid of the GEMM rows
 };
+
+// Offset of element (voxel v = b * Vs + s, channel c) of a C-channel blocked
+// tensor whose grid has Vs voxels per batch entry.
+__device__ __forceinline__ long long blk(long long v, int c, int C, long long Vs)
+{
+    long long b = v / Vs, s = v - b * Vs;
+    return ((b * (C >> 3) + (c >> 3)) * Vs + s) * 8 + (c & 7);
+}
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *g, int bytes)
 {
@@ -116,6 +127,9 @@ __global__ void __launch_bounds__(128) k_igemm(IgArgs p)
     const int tapz = p.mode == IG_UP2 ? (int)blockIdx.z : 0;
     const int kch = K / 16;
     const int nsteps = ntap * kch;
+    const long long Vrow = (long long)p.D * p.H * p.W;
+    const long long VsA = p.mode == IG_DOWN2 ? 8 * Vrow : Vrow;  // voxels per batch entry of the source grid
+    const long long VsO = p.mode == IG_UP2 ? 8 * Vrow : Vrow;    // ... and of the output grid
     float acc[NB][4];
 #pragma unroll
     for (int j = 0; j < NB; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
@@ -131,7 +145,7 @@ __global__ void __launch_bounds__(128) k_igemm(IgArgs p)
             const bf16 *src = p.in1;
             int bytes = 0;
             if (v >= 0) {
-                src = c < p.C1 ? p.in1 + v * p.C1 + c : p.in2 + v * p.C2 + (c - p.C1);
+                src = c < p.C1 ? p.in1 + blk(v, c, p.C1, VsA) : p.in2 + blk(v, c - p.C1, p.C2, VsA);
                 bytes = 16;
             }
             cp_async16(&sA[buf][r][8 * half], src, bytes);
@@ -190,8 +204,8 @@ __global__ void __launch_bounds__(128) k_igemm(IgArgs p)
                 if (col + 1 < p.N) p.outf[ov * p.N + col + 1] = v1;
             } else if (col + 1 < p.N || (col < p.N && (p.N & 1) == 0)) {
                 __nv_bfloat162 pr = __floats2bfloat162_rn(v0, v1);
-                if (col < p.O1) *reinterpret_cast<__nv_bfloat162 *>(p.out1 + ov * p.O1 + col) = pr;
-                else *reinterpret_cast<__nv_bfloat162 *>(p.out2 + ov * (p.N - p.O1) + (col - p.O1)) = pr;
+                if (col < p.O1) *reinterpret_cast<__nv_bfloat162 *>(p.out1 + blk(ov, col, p.O1, VsO)) = pr;
+                else *reinterpret_cast<__nv_bfloat162 *>(p.out2 + blk(ov, col - p.O1, p.N - p.O1, VsO)) = pr;
             }
         }
     }
@@ -227,6 +241,8 @@ __global__ void __launch_bounds__(128) k_wgrad(WgArgs p)
     const long long r0 = (long long)blockIdx.x * p.chunk, r1 = min(M, r0 + p.chunk);
     IgArgs q;
     q.mode = p.mode; q.B = p.B; q.D = p.D; q.H = p.H; q.W = p.W;
+    const long long VsX = (long long)p.D * p.H * p.W;                    // X lives on the row grid
+    const long long VsG = p.mode == IG_UP2 ? 8 * VsX : VsX;              // G on the fine grid for IG_UP2
     float acc[NB][4];
 #pragma unroll
     for (int j = 0; j < NB; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
@@ -240,8 +256,8 @@ __global__ void __launch_bounds__(128) k_wgrad(WgArgs p)
             int c = ci0 + c8;
             uint4 val = make_uint4(0, 0, 0, 0);
             if (v >= 0 && c < Cin)
-                val = c < p.C1 ? *reinterpret_cast<const uint4 *>(p.x1 + v * p.C1 + c)
-                               : *reinterpret_cast<const uint4 *>(p.x2 + v * p.C2 + (c - p.C1));
+                val = c < p.C1 ? *reinterpret_cast<const uint4 *>(p.x1 + blk(v, c, p.C1, VsX))
+                               : *reinterpret_cast<const uint4 *>(p.x2 + blk(v, c - p.C1, p.C2, VsX));
             const bf16 *pv = reinterpret_cast<const bf16 *>(&val);
 #pragma unroll
             for (int k = 0; k < 8; k++) sX[c8 + k][rr] = pv[k];
@@ -253,7 +269,7 @@ __global__ void __launch_bounds__(128) k_wgrad(WgArgs p)
             uint4 val = make_uint4(0, 0, 0, 0);
             if (r < r1) {
                 long long v = p.mode == IG_UP2 ? ig_dst(q, r, t) : r;
-                if (c8 < p.Cg) val = *reinterpret_cast<const uint4 *>(p.g + v * p.Cg + c8);
+                if (c8 < p.Cg) val = *reinterpret_cast<const uint4 *>(p.g + blk(v, c8, p.Cg, VsG));
             }
             const bf16 *pv = reinterpret_cast<const bf16 *>(&val);
 #pragma unroll
@@ -290,32 +306,36 @@ __global__ void __launch_bounds__(128) k_wgrad(WgArgs p)
 }
 
 // ----------------------------------------------------------------- elementwise
-__global__ void k_pack_input(const float *__restrict__ x, int cin, long long V, bf16 *__restrict__ out)
+// FP32 [V][cin] -> blocked BF16 with 16 channels (zeros beyond cin); Vs
+// voxels per batch entry.
+__global__ void k_pack_input(const float *__restrict__ x, int cin, long long V, long long Vs, bf16 *__restrict__ out)
 {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= V * 16) return;
     long long v = e >> 4;
     int c = (int)(e & 15);
-    out[e] = __float2bfloat16_rn(c < cin ? x[v * cin + c] : 0.f);
+    out[blk(v, c, 16, Vs)] = __float2bfloat16_rn(c < cin ? x[v * cin + c] : 0.f);
 }
 
 __global__ void k_maxpool(const bf16 *__restrict__ in, bf16 *__restrict__ out, unsigned char *__restrict__ idx, int B,
                           int D, int H, int W, int C)
 {
-    // output grid (B, D, H, W); input grid twice as fine
+    // output grid (B, D, H, W); input grid twice as fine; e runs over the
+    // blocked output, (b, channel group, voxel, channel % 8)
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long tot = (long long)B * D * H * W * C;
     if (e >= tot) return;
-    int c = (int)(e % C);
-    long long v = e / C;
-    long long x = v % W, q = v / W, y = q % H;
-    q /= H;
-    long long z = q % D, b = q / D;
+    const long long Vs = (long long)D * H * W;
+    int j = (int)(e & 7);
+    long long q = e >> 3;
+    long long s = q % Vs, bg = q / Vs;  // bg = b * C / 8 + channel group
+    long long x = s % W, r = s / W, y = r % H, z = r / H;
+    const bf16 *src = in + bg * 8 * Vs * 8 + j;
     float best = -INFINITY;
     int bi = 0;
     for (int t = 0; t < 8; t++) {
         long long zz = 2 * z + ((t >> 2) & 1), yy = 2 * y + ((t >> 1) & 1), xx = 2 * x + (t & 1);
-        float f = __bfloat162float(in[(((b * 2 * D + zz) * 2 * H + yy) * 2 * W + xx) * C + c]);
+        float f = __bfloat162float(src[((zz * 2 * H + yy) * 2 * W + xx) * 8]);
         if (f > best) { best = f; bi = t; }
     }
     out[e] = __float2bfloat16_rn(best);
@@ -326,17 +346,17 @@ __global__ void k_maxpool(const bf16 *__restrict__ in, bf16 *__restrict__ out, u
 __global__ void k_maxpool_bwd(const bf16 *__restrict__ dout, const unsigned char *__restrict__ idx,
                               const bf16 *__restrict__ dskip, bf16 *__restrict__ din, int B, int D, int H, int W, int C)
 {
-    // fine grid (B, 2D, 2H, 2W)
+    // fine grid (B, 2D, 2H, 2W); e runs over the blocked fine tensor
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long tot = (long long)B * 8 * D * H * W * C;
     if (e >= tot) return;
-    int c = (int)(e % C);
-    long long v = e / C;
-    long long x = v % (2 * W), q = v / (2 * W), y = q % (2 * H);
-    q /= (2 * H);
-    long long z = q % (2 * D), b = q / (2 * D);
+    const long long Vc = (long long)D * H * W, Vf = 8 * Vc;
+    int j = (int)(e & 7);
+    long long q = e >> 3;
+    long long s = q % Vf, bg = q / Vf;
+    long long x = s % (2 * W), r = s / (2 * W), y = r % (2 * H), z = r / (2 * H);
     int t = (int)(((z & 1) << 2) | ((y & 1) << 1) | (x & 1));
-    long long cv = (((b * D + (z >> 1)) * H + (y >> 1)) * W + (x >> 1)) * C + c;
+    long long cv = (bg * Vc + ((z >> 1) * H + (y >> 1)) * W + (x >> 1)) * 8 + j;
     float g = idx[cv] == t ? __bfloat162float(dout[cv]) : 0.f;
     if (dskip) g += __bfloat162float(dskip[e]);
     din[e] = __float2bfloat16_rn(g);
@@ -350,7 +370,7 @@ __global__ void k_relu_mask(const bf16 *__restrict__ dy, const bf16 *__restrict_
 
 // MSE over (voxels, cout): loss partial sums in FP64 and dy = 2 (y - t) / count
 // as BF16 with 16 channels (zeros beyond cout).
-__global__ void k_mse(const float *__restrict__ y, const float *__restrict__ tgt, long long V, int cout,
+__global__ void k_mse(const float *__restrict__ y, const float *__restrict__ tgt, long long V, long long Vs, int cout,
                       bf16 *__restrict__ dy, double *__restrict__ loss)
 {
     __shared__ double sh[32];
@@ -365,7 +385,7 @@ __global__ void k_mse(const float *__restrict__ y, const float *__restrict__ tgt
             l = (double)d * d;
             g = 2.f * d / (float)(V * cout);
         }
-        dy[e] = __float2bfloat16_rn(g);
+        dy[blk(v, c, 16, Vs)] = __float2bfloat16_rn(g);
     }
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = l;
@@ -377,8 +397,9 @@ __global__ void k_mse(const float *__restrict__ y, const float *__restrict__ tgt
     }
 }
 
-// column sums of a BF16 tensor [V][Cs] into db[0..N)
-__global__ void k_colsum(const bf16 *__restrict__ g, long long V, int Cs, int N, float *__restrict__ db)
+// column sums of a blocked BF16 tensor with Cs channels (V voxels, Vs per
+// batch entry) into db[0..N)
+__global__ void k_colsum(const bf16 *__restrict__ g, long long V, long long Vs, int Cs, int N, float *__restrict__ db)
 {
     int c = threadIdx.x % Cs;
     int lanes = blockDim.x / Cs;
@@ -386,7 +407,7 @@ __global__ void k_colsum(const bf16 *__restrict__ g, long long V, int Cs, int N,
     if (sub >= lanes) return;
     float s = 0.f;
     for (long long v = (long long)blockIdx.x * lanes + sub; v < V; v += (long long)gridDim.x * lanes)
-        s += __bfloat162float(g[v * Cs + c]);
+        s += __bfloat162float(g[blk(v, c, Cs, Vs)]);
     if (c < N) atomicAdd(&db[c], s);
 }
 
@@ -666,10 +687,11 @@ void conv_wgrad(gnb_unet *u, const ULayer &ly, int mode, int B, int D, const bf1
     a.dw = u->g + ly.woff; a.B = B; a.D = D; a.H = D; a.W = D;
     launch_wg(a, ly.taps, u->s);
     // bias gradient: column sums of the output gradient
-    long long V = (long long)B * (mode == IG_UP2 ? 8LL * D * D * D : (long long)D * D * D);
+    long long Vs = mode == IG_UP2 ? 8LL * D * D * D : (long long)D * D * D;
+    long long V = (long long)B * Vs;
     int threads = 256 / Cg * Cg;
     if (threads < Cg) threads = Cg;
-    counted(k_colsum)<<<120, threads, 0, u->s>>>(g, V, Cg, ly.cout, u->g + ly.boff);
+    counted(k_colsum)<<<120, threads, 0, u->s>>>(g, V, Vs, Cg, ly.cout, u->g + ly.boff);
 }
 
 int unet_forward(gnb_unet *u, int B)
@@ -794,7 +816,7 @@ int unet_check(gnb_unet *u, int rc)
 
 namespace gnb {
 // Hooks for the batched surrogate step: make room for `batch` regions and
-// expose the packed BF16 input [batch][grid^3][16] and the FP32 output
+// expose the blocked BF16 input [batch][2][grid^3][8] and the FP32 output
 // [batch][grid^3][cout]; unet_run launches the forward pass on `stream`
 // without synchronising (so it can be captured in a CUDA graph).
 int unet_prepare(gnb_unet *u, int batch, bf16 **xin, float **yout, int *grid, int *cout)
@@ -963,7 +985,7 @@ int gnb_unet_forward(gnb_unet *u, int batch, const float *x, float *y, int on_de
         cudaMemcpyAsync(tmpx, x, V * u->cin * 4, cudaMemcpyHostToDevice, u->s);
         xd = tmpx;
     }
-    counted(k_pack_input)<<<(unsigned)((V * 16 + 255) / 256), 256, 0, u->s>>>(xd, u->cin, V, u->xin);
+    counted(k_pack_input)<<<(unsigned)((V * 16 + 255) / 256), 256, 0, u->s>>>(xd, u->cin, V, vox(u, 0, 1), u->xin);
     rc = unet_forward(u, batch);
     if (rc == GNB_OK)
         cudaMemcpyAsync(y, u->yout, V * u->cout * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -989,11 +1011,11 @@ int gnb_unet_train_step(gnb_unet *u, int batch, const float *x, const float *tar
     }
     cudaMemcpyAsync(u->tgt, target, V * u->cout * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                     u->s);
-    counted(k_pack_input)<<<(unsigned)((V * 16 + 255) / 256), 256, 0, u->s>>>(xd, u->cin, V, u->xin);
+    counted(k_pack_input)<<<(unsigned)((V * 16 + 255) / 256), 256, 0, u->s>>>(xd, u->cin, V, vox(u, 0, 1), u->xin);
     rc = unet_forward(u, batch);
     cudaMemsetAsync(u->loss_d, 0, 8, u->s);
-    counted(k_mse)<<<(unsigned)((V * 16 + 255) / 256), 256, 0, u->s>>>(u->yout, u->tgt, V, u->cout, u->dyb,
-                                                                     u->loss_d);
+    counted(k_mse)<<<(unsigned)((V * 16 + 255) / 256), 256, 0, u->s>>>(u->yout, u->tgt, V, vox(u, 0, 1), u->cout,
+                                                                     u->dyb, u->loss_d);
     cudaMemsetAsync(u->g, 0, u->nparam * 4, u->s);
     if (rc == GNB_OK) rc = unet_backward(u, batch);
     if (rc == GNB_OK && lr > 0.0) {
