@@ -10,7 +10,15 @@ through the C ABI (tree build, gravity, halo, kernel size, density, force,
 kicks, drift).  Inputs are resident in HBM when the timed region starts; L2 is
 flushed (256 MiB write on the same stream) before every timed step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+The same JSON line carries the supernova half of the metric under "sn"
+(rank 0, one GPU): SN regions per second of the surrogate path (256 ragged
+regions of 2e4 - 3e5 gas particles, log-uniform, voxelised to 64^3, BF16 U-Net
+forward, Gibbs remap, one CUDA-graph replay per batch) against the plain
+CFL-limited integration of a 1e5-particle region over 0.1 Myr on the same GPU,
+with the surrogate's field error from the committed training report and the
+U-Net forward's tensor throughput against the measured BF16 peak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sn]
 
 With N > 1 (torchrun) every rank runs an independent replica on its own GPU
 (the step has no exchange on one GPU; replicas only) and rank 0 prints the
@@ -44,6 +52,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # and this library's own count for the quadrupole particle-cell term
 FLOP_PP = 27
 FLOP_PC = 59
+# U-Net forward per 64^3 region: 3^3 convolutions, transposed convolutions
+# and the head with the network's own 5 input channels (algorithmic count)
+UNET_GFLOP_64 = 29.0497
+SN_REPORT = os.path.join(ROOT, "profiles", "surrogate_sn_region_1e5_grid64.txt")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
 def workload(name: str, seed: int):
@@ -163,6 +176,121 @@ def cpu_baseline(p, name):
             "seconds_per_step_estimate": total}
 
 
+def read_kv(path):
+    try:
+        text = open(path).read()
+    except OSError:
+        return {}
+    return {k.strip(): v.strip() for k, v in (line.split(":", 1) for line in text.splitlines()
+                                                if ":" in line and not line.startswith("#"))}
+
+
+def sn_regions(nreg, distinct, lo, hi, seed):
+    """nreg supernova regions with gas counts log-uniform in [lo, hi], built
+    from `distinct` generated regions, each placed nreg / distinct times on a
+    lattice of centres 180 pc apart (3 region sides, so the cubes never
+    overlap).  Returns (particles, centres, counts)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), distinct)).astype(int)
+    base = [ics.sn_region(int(m), seed=seed + k, grid=32) for k, m in enumerate(sizes)]
+    parts, centers, counts = {}, [], []
+    for r in range(nreg):
+        b = base[r % distinct]
+        o = (180.0 * (r % 16), 180.0 * (r // 16), 0.0)
+        centers.append(o)
+        counts.append(b["x"].size)
+        for key, val in b.items():
+            if key == "x":
+                val = val + o[0]
+            elif key == "y":
+                val = val + o[1]
+            parts.setdefault(key, []).append(val)
+    p = {k: np.concatenate(v) for k, v in parts.items()}
+    p["id"] = np.arange(p["x"].size, dtype=np.int64)
+    return p, centers, np.asarray(counts)
+
+
+def sn_bench(stream, galnb, torch, nreg=256, reps=3):
+    """SN regions/s: batched surrogate vs plain integration (see module doc)."""
+    from paper_2510_23330_gb300 import surrogate as S
+    sp = stream.cuda_stream
+    net = galnb.UNet(5, 5, 16, 4, 64, stream=sp)
+    net.set_params(S.he_init(seed=0))
+    # --- surrogate: one graph replay per batch of nreg ragged regions
+    p, centers, counts = sn_regions(nreg, 16, 20000, 300000, seed=7)
+    ctx = galnb.Context(stream=sp)
+    ctx.set_particles(p)
+    ctx.compute_sph_density()
+    ctx.sn_surrogate_batch(net, centers, seed=0)  # first call captures the graph
+    ms = []
+    for r in range(reps):
+        ctx.compute_sph_density()  # the coupled step has it from the global step
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.sn_surrogate_batch(net, centers, seed=r + 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    # stage split, eager with the phase timers
+    ctx.compute_sph_density()
+    ctx.set_timing(True)
+    ctx.phase_times(reset=True)
+    ctx.sn_surrogate_batch(net, centers, seed=99)
+    ph, _, _ = ctx.phase_times(reset=True)
+    ctx.set_timing(False)
+    ctx.close()
+    # --- U-Net forward alone, device tensors, batch 32
+    xb = torch.randn(32, 64, 64, 64, 5, device=stream.device)
+    yb = torch.empty_like(xb)
+    for _ in range(2):
+        net.forward(xb, out=yb)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        net.forward(xb, out=yb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 3
+    del xb, yb
+    net.close()
+    # --- plain: CFL-limited integration of a 1e5-particle region over 0.1 Myr
+    plain = []
+    for seed in (1900, 1901):
+        _, _, info = S.make_pair(seed, n=100000, grid=64, stream=sp)
+        plain.append(info)
+    plain_s = float(np.median([i["seconds"] for i in plain]))
+    sur_ms = float(np.median(ms))
+    kv = read_kv(SN_REPORT)
+    try:
+        peaks = json.load(open(PEAKS))
+        peak, peak_note = float(peaks["bf16_tflops"]), "of measured (cuBLAS bf16 burst, MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        peak, peak_note = 1900.0, "of fallback"
+    tflops = UNET_GFLOP_64 * 32 / fwd_ms / 1e3
+    return {
+        "metric": "SN regions/s: surrogate vs plain at fixed error",
+        "surrogate_regions_per_s": nreg / (sur_ms * 1e-3),
+        "plain_regions_per_s": 1.0 / plain_s,
+        "speedup": nreg / (sur_ms * 1e-3) * plain_s,
+        "surrogate": {"regions": nreg, "gas_particles": int(counts.sum()),
+                      "counts_min_max": [int(counts.min()), int(counts.max())], "grid": 64, "side_pc": 60.0,
+                      "ms_per_batch": sur_ms, "batch_ms": ms, "graph": True,
+                      "stage_ms": {k: ph[k] for k in ("VOXELISE", "UNET", "REMAP")},
+                      "note": "16 generated regions placed 16 times each; density from the global step not timed"},
+        "plain": {"particles": 100000, "t_end_myr": 0.1, "seconds_per_region": plain_s,
+                  "steps": [int(i["steps"]) for i in plain], "gravity": "none (SN region integrator)"},
+        "field_error": {"rmse_surrogate": float(kv["rmse_surrogate_all"]) if "rmse_surrogate_all" in kv else None,
+                        "rmse_no_feedback": float(kv["rmse_identity_all"]) if "rmse_identity_all" in kv else None,
+                        "units": "standardised channels, mean over 5 channels and 8 held-out seeds",
+                        "source": os.path.relpath(SN_REPORT, ROOT)},
+        "unet_roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                          "frac": tflops / peak, "note": f"whole forward, {UNET_GFLOP_64} GFLOP per 64^3 region, "
+                                                          f"batch 32, {peak_note}", "ms_per_region": fwd_ms / 32},
+    }
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -273,6 +401,8 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, desc)
     ctx.close()
+    if rank == 0 and world == 1 and not args.no_sn:
+        out["sn"] = sn_bench(stream, galnb, torch)
     return out
 
 
@@ -341,6 +471,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-sn", action="store_true", help="skip the supernova surrogate-vs-plain section")
     args = ap.parse_args()
     if args.impl == "reference":
         # the CPU checker runs once, on rank 0; other ranks exit without work

@@ -127,6 +127,9 @@ enum gnb_phase {
     GNB_T_KNN,          /* kernel size + density/pressure */
     GNB_T_FORCE,        /* symmetric lists + hydro force */
     GNB_T_KDK,          /* kicks, drift, prediction */
+    GNB_T_VOXELISE,     /* surrogate: region membership, voxelisation, standardisation */
+    GNB_T_UNET,         /* surrogate: U-Net forward */
+    GNB_T_REMAP,        /* surrogate: Gibbs remap and replacement */
     GNB_T_COUNT_
 };
 
@@ -326,8 +329,9 @@ int gnb_remap_regions(gnb_ctx *ctx, int nreg, const double *centers, double side
 
 /* Batched surrogate step for nreg supernova regions of uneven particle
  * counts: voxelise -> U-Net forward (net, which must predict 5 channels on
- * its own grid) -> Gibbs remap, as above.  With use_graph = 1 and a
- * non-default stream the sequence is captured into a CUDA graph on the first
+ * its own grid) -> Gibbs remap, as above.  With use_graph = 1, a
+ * non-default stream and the phase timers off, the sequence is captured into a
+ * CUDA graph on the first
  * call and replayed while the shapes stay the same.  Requires
  * gnb_compute_sph_density at the current positions.  Errors: GNB_EINVAL,
  * GNB_ESTATE, GNB_ENOMEM, GNB_ECUDA. */

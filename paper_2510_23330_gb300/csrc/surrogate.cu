@@ -252,7 +252,10 @@ int voxelise(gnb_ctx *c, int nreg, const double *centers, double side, int grid,
     GNB_TRY(voxelise_buffers_for(c, nreg, grid));
     GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->cent_d, centers, sizeof(double) * 3 * nreg, cudaMemcpyHostToDevice,
                                           c->s), "centres"));
-    return vox_launch(c, nreg, side, grid, out_dev ? out_dev : c->vout, nullptr);
+    phase_begin(c, GNB_T_VOXELISE);
+    int rc = vox_launch(c, nreg, side, grid, out_dev ? out_dev : c->vout, nullptr);
+    phase_end(c);
+    return rc;
 }
 
 int remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, int grid, const float *pred_dev,
@@ -267,7 +270,9 @@ int remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, int 
     cudaMemsetAsync(c->rcount, 0, sizeof(int) * nreg, c->s);
     counted(k_region_assign)<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], n, c->cent_d, nreg, 0.5 * side,
                                                                 c->sreg, c->rcount);
+    phase_begin(c, GNB_T_REMAP);
     GNB_TRY(remap_launch(c, nreg, side, grid, pred_dev, 5, sweeps));
+    phase_end(c);
     return cuda_check(c, cudaStreamSynchronize(c->s), "remap sync");
 }
 
@@ -293,11 +298,18 @@ int sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *center
         return cuda_check(c, cudaGraphLaunch(c->sn_graph, c->s), "surrogate graph launch");
     }
     auto issue = [&]() -> int {
+        phase_begin(c, GNB_T_VOXELISE);
         GNB_TRY(vox_launch(c, nreg, side, grid, nullptr, xin));
+        phase_begin(c, GNB_T_UNET);
         GNB_TRY(unet_run(net, nreg, c->s));
-        return remap_launch(c, nreg, side, grid, yout, cout, sweeps);
+        phase_begin(c, GNB_T_REMAP);
+        int rc = remap_launch(c, nreg, side, grid, yout, cout, sweeps);
+        phase_end(c);
+        return rc;
     };
-    if (!use_graph || c->s == nullptr) return issue();
+    // with the phase timers on, the batch runs eagerly (no graph) so that
+    // each stage's events are recorded
+    if (!use_graph || c->s == nullptr || c->timing) return issue();
     if (c->sn_graph) {
         cudaGraphExecDestroy(c->sn_graph);
         c->sn_graph = nullptr;

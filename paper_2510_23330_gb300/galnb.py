@@ -338,7 +338,7 @@ def gnb_phase_times(ctx, out_ms, calls, launches, reset):
     return lib().gnb_phase_times(ctx, out_ms, calls, launches, reset)
 
 
-PHASES = ["SORT", "TREE", "GRAVITY", "EXTERNAL", "HYDRO_TREE", "KNN", "FORCE", "KDK"]
+PHASES = ["SORT", "TREE", "GRAVITY", "EXTERNAL", "HYDRO_TREE", "KNN", "FORCE", "KDK", "VOXELISE", "UNET", "REMAP"]
 
 GNB_NOALLOC_MAX_N = 262144
 
