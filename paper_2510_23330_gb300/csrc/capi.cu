@@ -274,7 +274,9 @@ void gnb_destroy(gnb_ctx *c)
     for (void *q : all) dfree(c, q);
     if (c->pinned_i) cudaFreeHost(c->pinned_i);
     {
-        void *sur[] = {c->sreg, c->rcount, c->vacc, c->vout, c->vw, c->cent_d, c->seed_d};
+        void *sur[] = {c->sreg, c->rcount, c->vacc, c->vout, c->vw, c->vcdf, c->cent_d, c->seed_d, c->centf,
+                       c->vovf, c->vt_count, c->vt_off, c->vt_cur, c->vt_list, c->vt_total, c->vt_misc,
+                       c->vt_choff};
         for (void *q : sur) dfree(c, q);
         if (c->sn_graph) cudaGraphExecDestroy(c->sn_graph);
     }

@@ -151,7 +151,18 @@ struct gnb_ctx {
     float *vacc = nullptr;        // voxel accumulators [nreg][grid^3][6]
     float *vout = nullptr;        // standardised channels [nreg][grid^3][5]
     double *vw = nullptr;         // remap weights [nreg][grid^3]
+    double *vcdf = nullptr;       // remap line CDFs [nreg][axis][grid^2 lines][grid]
     double *cent_d = nullptr;     // region centres [nreg][3]
+    float *centf = nullptr;       // FP32 copy of the centres (membership pre-filter)
+    unsigned char *vovf = nullptr;  // per particle: voxelised by the direct scatter (tile lists full)
+    int *vt_count = nullptr, *vt_off = nullptr, *vt_cur = nullptr;  // per (region, 8^3-voxel tile)
+    int *vt_choff = nullptr;      // first chunk of each tile's list
+    int *vt_list = nullptr;       // particle indices grouped by tile
+    unsigned long long *vt_total = nullptr;  // list slots reserved
+    int *vt_misc = nullptr;       // [0] tile count (scan length), [1] some particle overflowed, [2] chunks
+    size_t vt_ntile = 0, vt_cap = 0;
+    int64_t sur_pcap = 0;         // particle capacity of sreg / vovf
+    uint64_t sur_gen = 0;         // bumped whenever a surrogate buffer is reallocated
     unsigned long long *seed_d = nullptr;
     size_t sur_nv = 0;
     int sur_nreg = 0;
@@ -161,6 +172,7 @@ struct gnb_ctx {
     double sn_side = 0.0;
     int64_t sn_n = 0;
     int sn_cur = -1;
+    uint64_t sn_gen = 0;          // sur_gen when the graph was captured
     int64_t sn_graph_replays = 0;
 
     // status / counters
