@@ -268,7 +268,7 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3):
         peak, peak_note = float(peaks["bf16_tflops"]), "of measured (cuBLAS bf16 burst, MEASURED_PEAKS.json)"
     except (OSError, KeyError, ValueError):
         peak, peak_note = 1900.0, "of fallback"
-    tflops = UNET_GFLOP_64 * 32 / fwd_ms / 1e3
+    tflops = UNET_GFLOP_64 * 32 / fwd_ms  # GFLOP per ms = TFLOP/s
     return {
         "metric": "SN regions/s: surrogate vs plain at fixed error",
         "surrogate_regions_per_s": nreg / (sur_ms * 1e-3),
