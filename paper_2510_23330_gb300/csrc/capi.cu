@@ -274,9 +274,8 @@ void gnb_destroy(gnb_ctx *c)
     for (void *q : all) dfree(c, q);
     if (c->pinned_i) cudaFreeHost(c->pinned_i);
     {
-        void *sur[] = {c->sreg, c->rcount, c->vacc, c->vout, c->vw, c->vcdf, c->cent_d, c->seed_d, c->centf,
-                       c->vovf, c->vt_count, c->vt_off, c->vt_cur, c->vt_list, c->vt_total, c->vt_misc,
-                       c->vt_choff};
+        void *sur[] = {c->sreg, c->rcount, c->vacc, c->vout, c->vw,  c->vcdf, c->cent_d, c->seed_d,
+                       c->rsx,  c->rsi,    c->centf, c->vpa, c->vpb, c->vpc,  c->vbox};
         for (void *q : sur) dfree(c, q);
         if (c->sn_graph) cudaGraphExecDestroy(c->sn_graph);
     }

@@ -148,20 +148,19 @@ struct gnb_ctx {
     // supernova surrogate (surrogate.cu)
     int *sreg = nullptr;          // region of each particle slot (-1: none)
     int *rcount = nullptr;        // members per region
-    float *vacc = nullptr;        // voxel accumulators [nreg][grid^3][6]
+    float *vacc = nullptr;        // voxel accumulators [nreg][grid^3][8] (six used)
     float *vout = nullptr;        // standardised channels [nreg][grid^3][5]
     double *vw = nullptr;         // remap weights [nreg][grid^3]
     double *vcdf = nullptr;       // remap line CDFs [nreg][axis][grid^2 lines][grid]
     double *cent_d = nullptr;     // region centres [nreg][3]
+    float *rsx = nullptr;         // region centre x (FP32), sorted ascending (membership search)
+    int *rsi = nullptr;           // region index of each sorted entry
     float *centf = nullptr;       // FP32 copy of the centres (membership pre-filter)
-    unsigned char *vovf = nullptr;  // per particle: voxelised by the direct scatter (tile lists full)
-    int *vt_count = nullptr, *vt_off = nullptr, *vt_cur = nullptr;  // per (region, 8^3-voxel tile)
-    int *vt_choff = nullptr;      // first chunk of each tile's list
-    int *vt_list = nullptr;       // particle indices grouped by tile
-    unsigned long long *vt_total = nullptr;  // list slots reserved
-    int *vt_misc = nullptr;       // [0] tile count (scan length), [1] some particle overflowed, [2] chunks
-    size_t vt_ntile = 0, vt_cap = 0;
-    int64_t sur_pcap = 0;         // particle capacity of sreg / vovf
+    std::vector<int> rs_order;    // host staging of rsi / rsx / centf
+    std::vector<float> rs_x, rs_cf;
+    float4 *vpa = nullptr, *vpb = nullptr, *vpc = nullptr;  // voxelisation: staged FP32 values per particle
+    int *vbox = nullptr;          // voxelisation: packed x and y footprint ranges per particle
+    int64_t sur_pcap = 0;         // particle capacity of sreg and the staged arrays
     uint64_t sur_gen = 0;         // bumped whenever a surrogate buffer is reallocated
     unsigned long long *seed_d = nullptr;
     size_t sur_nv = 0;

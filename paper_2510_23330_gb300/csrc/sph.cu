@@ -166,9 +166,20 @@ struct KnnSmem {
     int un[KN_WARPS];
     int ui[KN_WARPS][KN_U];
     double uD[KN_WARPS][KN_U];
-    int nc, sp, g, under, over, bmin[3], bmax[3];
+    int nc, sp, g, under, over, split, bmin[3], bmax[3];
     unsigned amax;
 };
+
+// A particle of a group could not be ranked within the buffers: the FP32
+// error band (2^-17 A^2, A the group's largest offset) is wide when a dense
+// clump sits inside a spread-out group.  The group is then split into
+// single-particle work items, whose band scales with their own search
+// radius; only a single particle that still fails is reported.
+__device__ __forceinline__ void knn_fail(KnnSmem &S, int count, int *status)
+{
+    if (count > 1) S.split = 1;
+    else atomicOr(status, ST_KNN_OVERFLOW);
+}
 
 __device__ __forceinline__ float d2f(float4 c, float xi, float yi, float zi)
 {
@@ -202,7 +213,7 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
         const int4 ga = make_int4(gitem.x, gitem.y, 0, 0);
         const float R = p.kR[gi];
         if (tid < 3) { S.bmin[tid] = 0x7fffffff; S.bmax[tid] = -1; }
-        if (tid == 0) { S.nc = 0; S.sp = 1; S.stack[0] = 0; S.under = 0; S.over = 0; S.amax = 0u; }
+        if (tid == 0) { S.nc = 0; S.sp = 1; S.stack[0] = 0; S.under = 0; S.over = 0; S.split = 0; S.amax = 0u; }
         __syncthreads();
         for (int i = ga.x + tid; i < ga.x + ga.y; i += KN_THREADS) {
             atomicMin(&S.bmin[0], p.gcx[i]); atomicMax(&S.bmax[0], p.gcx[i]);
@@ -343,7 +354,7 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                     R2i = R2i * (float)(bstar + 1) * (1.f / 64.f) * (1.f + 1e-6f);
                 }
                 if (!ok) {
-                    if (lane == 0) atomicOr(p.status, ST_KNN_OVERFLOW);
+                    if (lane == 0) knn_fail(S, ga.y, p.status);
                     continue;
                 }
                 for (int c = lane; c < nc; c += 32) {
@@ -356,7 +367,7 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                 __syncwarp();
                 const int nb = S.bn[w];
                 if (nb > KN_BKT) {
-                    if (lane == 0) atomicOr(p.status, ST_KNN_OVERFLOW);
+                    if (lane == 0) knn_fail(S, ga.y, p.status);
                     continue;
                 }
                 // t = kth smallest value in the bucket (ties by position)
@@ -373,7 +384,7 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                 }
                 unsigned fb = __ballot_sync(0xffffffffu, found);
                 if (fb == 0u) {  // cannot happen when the histogram is consistent
-                    if (lane == 0) atomicOr(p.status, ST_KNN_OVERFLOW);
+                    if (lane == 0) knn_fail(S, ga.y, p.status);
                     continue;
                 }
                 t = __shfl_sync(0xffffffffu, t, __ffs(fb) - 1);
@@ -406,7 +417,7 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                 __syncwarp();
                 const int nu = S.un[w];
                 if (nu > KN_U || nS >= NGB) {
-                    if (lane == 0) atomicOr(p.status, ST_KNN_OVERFLOW);
+                    if (lane == 0) knn_fail(S, ga.y, p.status);
                     continue;
                 }
                 for (int e = lane; e < nu; e += 32) S.uD[w][e] = exact_d2(p.gx, p.gy, p.gz, i, S.ui[w][e]);
@@ -433,7 +444,7 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                 }
                 unsigned hb = __ballot_sync(0xffffffffu, have);
                 if (hb == 0u) {  // error bound violated: fewer uncertain entries than needed
-                    if (lane == 0) atomicOr(p.status, ST_KNN_OVERFLOW);
+                    if (lane == 0) knn_fail(S, ga.y, p.status);
                     continue;
                 }
                 int hs = __ffs(hb) - 1;
@@ -463,7 +474,7 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
             }
         }
         __syncthreads();
-        if (S.over && ga.y > 1) {
+        if ((S.over || S.split) && ga.y > 1) {
             // the members need a radius whose candidates do not fit: hand
             // each particle to its own work item
             __syncthreads();

@@ -20,6 +20,8 @@
 //             u and v are the predicted voxel's T / T_PER_U and 20 z.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 typedef __nv_bfloat16 bf16;
@@ -44,46 +46,57 @@ __device__ __forceinline__ double uniform01(uint64_t seed, uint64_t id, uint64_t
     return (double)(sm64(sm64(seed + id) + k) >> 11) * (1.0 / 9007199254740992.0);
 }
 
-__device__ __forceinline__ float sur_w(float r, float hinv)
+// counter[key] += 1 for every active lane, one atomic per distinct key in
+// the warp (neighbouring particles in Morton order mostly share their
+// region and tiles); returns each lane's slot.
+__device__ __forceinline__ int warp_inc(int *counter, int key)
 {
-    float q = r * hinv;
-    float s = 2.546479089470325f * hinv * hinv * hinv;
-    if (q <= 0.5f) return s * (1.f - 6.f * q * q + 6.f * q * q * q);
-    if (q <= 1.f) { float t = 1.f - q; return s * 2.f * t * t * t; }
-    return 0.f;
+    const unsigned mask = __match_any_sync(__activemask(), key);
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter + key, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1));
 }
 
-// FP32 copy of the region centres for the membership pre-filter.
-__global__ void k_centres_f32(const double *__restrict__ cent, int nreg, float *__restrict__ cf)
-{
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < 3 * nreg) cf[k] = (float)cent[k];
-}
-
-// Region of every gas particle: the first region r with |x - c_r|_inf <=
-// side / 2, decided in FP64; an FP32 test with a margin far above its
-// rounding error skips the regions that cannot contain the particle.
-__global__ void k_region_assign(PArr p, int n, const double *__restrict__ cent, const float *__restrict__ cf, int nreg,
-                                double half, int *__restrict__ reg, int *__restrict__ rcount)
+// Region of every gas particle: the first region r (smallest index) with
+// |x - c_r|_inf <= side / 2, decided in FP64.  Candidates come from the
+// regions sorted by centre x: an FP32 binary search finds the slab
+// |c_x - x| <= half and an FP32 test on all three axes filters it, both with
+// a margin far above the FP32 rounding of the coordinates; only the
+// survivors get the exact FP64 test (GB300's FP64 rate is a small fraction
+// of its FP32 rate).
+__global__ void k_region_assign(PArr p, int n, const double *__restrict__ cent, const float *__restrict__ rsx,
+                                const int *__restrict__ rsi, const float *__restrict__ cf, int nreg, double half,
+                                int *__restrict__ reg, int *__restrict__ rcount)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int r = -1;
     if (p.type[i] == GNB_GAS) {
-        double x = p.x[i], y = p.y[i], z = p.z[i];
-        float xf = (float)x, yf = (float)y, zf = (float)z, hf = (float)half;
-        for (int k = 0; k < nreg; k++) {
-            float cx = cf[3 * k], cy = cf[3 * k + 1], cz = cf[3 * k + 2];
-            float tol = hf + 1e-5f * (fabsf(xf) + fabsf(cx) + fabsf(yf) + fabsf(cy) + fabsf(zf) + fabsf(cz) + hf);
-            if (fabsf(xf - cx) > tol || fabsf(yf - cy) > tol || fabsf(zf - cz) > tol) continue;
-            if (fabs(x - cent[3 * k]) <= half && fabs(y - cent[3 * k + 1]) <= half && fabs(z - cent[3 * k + 2]) <= half) {
-                r = k;
-                break;
-            }
+        const double x = p.x[i], y = p.y[i], z = p.z[i];
+        const float xf = (float)x, yf = (float)y, zf = (float)z, hf = (float)half;
+        const float tol = 1e-5f * (fabsf(xf) + fabsf(yf) + fabsf(zf) + hf) + 1e-30f;
+        const float xl = xf - hf - tol, xr = xf + hf + tol;
+        int a = 0, b = nreg;
+        while (a < b) {
+            int m = (a + b) >> 1;
+            if (rsx[m] < xl) a = m + 1;
+            else b = m;
         }
+        int best = nreg;
+        for (int k = a; k < nreg && rsx[k] <= xr; k++) {
+            const int q = rsi[k];
+            if (q >= best) continue;
+            const float tq = tol + 1e-5f * (fabsf(cf[3 * q]) + fabsf(cf[3 * q + 1]) + fabsf(cf[3 * q + 2]));
+            if (fabsf(yf - cf[3 * q + 1]) > hf + tq || fabsf(zf - cf[3 * q + 2]) > hf + tq) continue;
+            if (fabs(x - cent[3 * q]) <= half && fabs(y - cent[3 * q + 1]) <= half && fabs(z - cent[3 * q + 2]) <= half)
+                best = q;
+        }
+        if (best < nreg) r = best;
     }
     reg[i] = r;
-    if (r >= 0) atomicAdd(&rcount[r], 1);
+    if (r >= 0) warp_inc(rcount, r);
 }
 
 // Voxels whose centre can lie inside the kernel support of particle i
@@ -106,225 +119,96 @@ __device__ __forceinline__ void region_lo(const double *cent, int r, double side
     for (int a = 0; a < 3; a++) lo[a] = cent[3 * r + a] - 0.5 * side;
 }
 
-// Voxelisation is binned by tiles of 8^3 voxels.  Pass 1: every member
-// reserves one slot per tile its footprint touches (block-aggregated
-// reservation against the list capacity) and counts itself into those tiles;
-// a particle whose slots do not fit is flagged and goes through the direct
-// scatter below instead.
-__global__ void k_vox_bin_count(PArr p, int n, const int *__restrict__ reg, const double *__restrict__ cent,
-                                double side, int grid, int tpa, unsigned long long cap,
-                                unsigned long long *__restrict__ total, int *__restrict__ count,
-                                unsigned char *__restrict__ ovf, int *__restrict__ any_ovf)
-{
-    __shared__ unsigned long long s_base;
-    __shared__ unsigned s_sum;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int r = i < n ? reg[i] : -1;
-    int i0[3] = {0, 0, 0}, i1[3] = {-1, -1, -1};
-    unsigned np = 0;
-    if (r >= 0) {
-        double lo[3];
-        region_lo(cent, r, side, lo);
-        vox_footprint(p, i, lo, side / grid, grid, i0, i1);
-        np = (unsigned)(((i1[0] >> 3) - (i0[0] >> 3) + 1) * ((i1[1] >> 3) - (i0[1] >> 3) + 1) *
-                        ((i1[2] >> 3) - (i0[2] >> 3) + 1));
-    }
-    if (threadIdx.x == 0) s_sum = 0;
-    __syncthreads();
-    unsigned mine = np ? atomicAdd(&s_sum, np) : 0;
-    __syncthreads();
-    if (threadIdx.x == 0) s_base = s_sum ? atomicAdd(total, (unsigned long long)s_sum) : 0;
-    __syncthreads();
-    if (i >= n) return;
-    if (r < 0) { ovf[i] = 0; return; }
-    if (s_base + mine + np > cap) {
-        ovf[i] = 1;
-        *any_ovf = 1;
-        return;
-    }
-    ovf[i] = 0;
-    const int nt = tpa * tpa * tpa;
-    int *cr = count + (size_t)r * nt;
-    for (int tz = i0[2] >> 3; tz <= (i1[2] >> 3); tz++)
-        for (int ty = i0[1] >> 3; ty <= (i1[1] >> 3); ty++)
-            for (int tx = i0[0] >> 3; tx <= (i1[0] >> 3); tx++) atomicAdd(cr + (tz * tpa + ty) * tpa + tx, 1);
-}
-
-// Pass 2: write each member's index into the lists of its tiles.
-__global__ void k_vox_bin_fill(PArr p, int n, const int *__restrict__ reg, const double *__restrict__ cent,
-                               double side, int grid, int tpa, const unsigned char *__restrict__ ovf,
-                               const int *__restrict__ off, const int *__restrict__ count, int *__restrict__ cur,
-                               int *__restrict__ list)
+// Voxelisation, pass 1 (the only pass with FP64 arithmetic): every region
+// member's footprint and FP32 values are computed once and staged as three
+// float4 -- offset from the region corner and support^2; 1/h, m s,
+// (m/rho) s, T; velocity and the packed z range of the footprint (s = 8 /
+// (pi h^3), the kernel normalisation) -- plus the packed x and y ranges
+// (grids of at most 256 voxels per axis).
+__global__ void k_vox_stage(PArr p, int n, const int *__restrict__ reg, const float *__restrict__ rho,
+                            const double *__restrict__ cent, double side, int grid, float4 *__restrict__ vpa,
+                            float4 *__restrict__ vpb, float4 *__restrict__ vpc, int *__restrict__ vbox)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int r = reg[i];
-    if (r < 0 || ovf[i]) return;
+    if (r < 0) return;
     double lo[3];
     int i0[3], i1[3];
     region_lo(cent, r, side, lo);
     vox_footprint(p, i, lo, side / grid, grid, i0, i1);
-    const size_t t0 = (size_t)r * tpa * tpa * tpa;
-    for (int tz = i0[2] >> 3; tz <= (i1[2] >> 3); tz++)
-        for (int ty = i0[1] >> 3; ty <= (i1[1] >> 3); ty++)
-            for (int tx = i0[0] >> 3; tx <= (i1[0] >> 3); tx++) {
-                size_t t = t0 + (tz * tpa + ty) * tpa + tx;
-                int slot = atomicAdd(cur + t, 1);
-                if (slot < count[t]) list[off[t] + slot] = i;  // never past the tile's counted slots
-            }
+    const float hinv = (float)(1.0 / sqrt(p.h2[i]));
+    const float sn = 2.546479089470325f * hinv * hinv * hinv;  // 8 / (pi h^3)
+    const float m = p.m[i];
+    vpa[i] = make_float4((float)(p.x[i] - lo[0]), (float)(p.y[i] - lo[1]), (float)(p.z[i] - lo[2]), 1.f / (hinv * hinv));
+    vpb[i] = make_float4(hinv, m * sn, m / rho[i] * sn, p.u[i] * (float)SUR_T_PER_U);
+    vpc[i] = make_float4(p.vx[i], p.vy[i], p.vz[i], __int_as_float((i0[2] << 16) | i1[2]));
+    vbox[i] = i0[0] | (i1[0] << 8) | (i0[1] << 16) | (i1[1] << 24);
 }
 
-// Direct scatter with global atomics, only for the particles flagged in pass 1
-// acc[r][v][6] = {sum m W, sum (m/rho) W, sum T (m/rho) W, sum v (m/rho) W}
-__global__ void k_vox_scatter(PArr p, int n, const int *__restrict__ reg, const unsigned char *__restrict__ ovf,
-                              const float *__restrict__ rho, const double *__restrict__ cent, double side, int grid,
-                              float *__restrict__ acc)
+__device__ __forceinline__ float m4_shape(float q)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !ovf[i]) return;
-    int r = reg[i];
-    if (r < 0) return;
-    double d = side / grid, lo[3];
-    int i0[3], i1[3];
-    region_lo(cent, r, side, lo);
-    vox_footprint(p, i, lo, d, grid, i0, i1);
-    float off[3] = {(float)(p.x[i] - lo[0]), (float)(p.y[i] - lo[1]), (float)(p.z[i] - lo[2])};
-    float m = p.m[i], wr = m / rho[i];
-    float T = p.u[i] * (float)SUR_T_PER_U;
-    float vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
-    float hinv = (float)(1.0 / sqrt(p.h2[i])), df = (float)d;
-    float *base = acc + (size_t)r * grid * grid * grid * 6;
-    for (int iz = i0[2]; iz <= i1[2]; iz++) {
-        float dz = (iz + 0.5f) * df - off[2];
-        for (int iy = i0[1]; iy <= i1[1]; iy++) {
-            float dy = (iy + 0.5f) * df - off[1];
-            for (int ix = i0[0]; ix <= i1[0]; ix++) {
-                float dx = (ix + 0.5f) * df - off[0];
-                float w = sur_w(sqrtf(dx * dx + dy * dy + dz * dz), hinv);
-                if (w <= 0.f) continue;
-                float *q = base + (((size_t)iz * grid + iy) * grid + ix) * 6;
-                float ww = wr * w;
-                atomicAdd(q + 0, m * w);
-                atomicAdd(q + 1, ww);
-                atomicAdd(q + 2, T * ww);
-                atomicAdd(q + 3, vx * ww);
-                atomicAdd(q + 4, vy * ww);
-                atomicAdd(q + 5, vz * ww);
-            }
-        }
-    }
+    // cubic spline without its normalisation: 1 - 6q^2 + 6q^3 (q <= 1/2),
+    // 2 (1 - q)^3 (1/2 < q <= 1), 0 beyond
+    if (q <= 0.5f) return 1.f - 6.f * q * q + 6.f * q * q * q;
+    if (q <= 1.f) { float t = 1.f - q; return 2.f * t * t * t; }
+    return 0.f;
 }
 
-// Pass 3: the tile lists are cut into chunks of at most VOX_CHUNK pairs so
-// that a dense clump's tile is shared by many CTAs.  nchunk[t] chunks per
-// tile; their exclusive scan gives each tile's first chunk.
-#define VOX_CHUNK 1024
-__global__ void k_vox_chunks(const int *__restrict__ count, const int *__restrict__ ntile_d, int *__restrict__ nchunk)
+// Pass 2, one warp per member particle: the lanes sweep the voxels of the
+// particle's footprint box and add its six kernel-weighted terms
+// {m W, (m/rho) W, T (m/rho) W, v (m/rho) W} to acc[r][v][8] (six used,
+// padded to 32 bytes) with two vector reductions per voxel
+// (red.global.add.v4.f32 + .v2.f32, fire-and-forget at L2).  Consecutive
+// warps take neighbouring particles (Morton order), so their reductions hit
+// neighbouring voxels.  No FP64 arithmetic runs here.
+__device__ __forceinline__ void red_v4(float *a, float x, float y, float z, float w)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < *ntile_d) nchunk[t] = (count[t] + VOX_CHUNK - 1) / VOX_CHUNK;
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(a), "f"(x), "f"(y), "f"(z), "f"(w)
+                 : "memory");
+}
+__device__ __forceinline__ void red_v2(float *a, float x, float y)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};\n" ::"l"(a), "f"(x), "f"(y) : "memory");
 }
 
-// Persistent CTAs over chunks, gather form (no shared-memory atomics): the
-// 8 warps own the 8 z-slices of the tile and each lane owns two voxels of its
-// slice, (x, y) = (lane % 8, lane / 8) and (lane % 8, lane / 8 + 4), with
-// their six sums in registers.  The chunk's particles are staged in shared
-// memory 256 at a time; every warp reads each staged particle by broadcast,
-// skips it when its footprint misses the warp's slice, and otherwise adds
-// the kernel weight at its two voxel centres.  Sums are added to the global
-// accumulators acc[r][v][6] once per chunk.
-struct VoxP {
-    float ox, oy, oz, h2, hinv, m, wr, T, vx, vy, vz;
-    int zlo, zhi;
-};
-
-__global__ void __launch_bounds__(256) k_vox_tile(PArr p, const float *__restrict__ rho,
-                                                  const double *__restrict__ cent, double side, int grid, int tpa,
-                                                  const int *__restrict__ ntile_d, const int *__restrict__ off,
-                                                  const int *__restrict__ cnt, const int *__restrict__ choff,
-                                                  const int *__restrict__ nchunks_d, const int *__restrict__ list,
-                                                  float *__restrict__ vacc)
+__global__ void __launch_bounds__(256) k_vox_warp_scatter(int n, const int *__restrict__ reg,
+                                                          const float4 *__restrict__ vpa,
+                                                          const float4 *__restrict__ vpb,
+                                                          const float4 *__restrict__ vpc,
+                                                          const int *__restrict__ vbox, double side, int grid,
+                                                          float *__restrict__ acc8)
 {
-    __shared__ VoxP sp[256];
-    const int nt = tpa * tpa * tpa, ntile = *ntile_d, nchunks = *nchunks_d;
-    const double d = side / grid;
-    const float df = (float)d;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const float df = (float)(side / grid);
     const size_t G = (size_t)grid;
-    for (int cid = blockIdx.x; cid < nchunks; cid += gridDim.x) {
-        int lo_t = 0, hi_t = ntile;  // last tile whose first chunk is <= cid
-        while (lo_t < hi_t) {
-            int mid = (lo_t + hi_t) >> 1;
-            if (choff[mid] <= cid) lo_t = mid + 1;
-            else hi_t = mid;
-        }
-        const int tile = lo_t - 1;
-        const int r = tile / nt, t = tile % nt;
-        const int x0 = 8 * (t % tpa), y0 = 8 * ((t / tpa) % tpa), z0 = 8 * (t / (tpa * tpa));
-        const int k = cid - choff[tile];
-        const int beg = off[tile] + k * VOX_CHUNK, end = off[tile] + min(cnt[tile], (k + 1) * VOX_CHUNK);
-        double lo[3];
-        region_lo(cent, r, side, lo);
-        const int iz = z0 + warp, ix = x0 + (lane & 7), iy0 = y0 + (lane >> 3), iy1 = iy0 + 4;
-        const float cx = (ix + 0.5f) * df, cy0 = (iy0 + 0.5f) * df, cy1 = (iy1 + 0.5f) * df, cz = (iz + 0.5f) * df;
-        float a0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, a1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int b = beg; b < end; b += 256) {
-            __syncthreads();  // the previous batch has been read by every warp
-            const int q = b + threadIdx.x;
-            if (q < end) {
-                const int i = list[q];
-                int i0[3], i1[3];
-                vox_footprint(p, i, lo, d, grid, i0, i1);
-                VoxP v;
-                v.ox = (float)(p.x[i] - lo[0]);
-                v.oy = (float)(p.y[i] - lo[1]);
-                v.oz = (float)(p.z[i] - lo[2]);
-                const double h = sqrt(p.h2[i]);
-                v.hinv = (float)(1.0 / h);
-                v.h2 = 1.f / (v.hinv * v.hinv);
-                v.m = p.m[i];
-                v.wr = v.m / rho[i];
-                v.T = p.u[i] * (float)SUR_T_PER_U;
-                v.vx = p.vx[i]; v.vy = p.vy[i]; v.vz = p.vz[i];
-                v.zlo = i0[2];
-                v.zhi = i1[2];
-                sp[threadIdx.x] = v;
-            }
-            __syncthreads();
-            const int nb = min(256, end - b);
-            for (int j = 0; j < nb; j++) {
-                const VoxP &v = sp[j];
-                if (iz < v.zlo || iz > v.zhi) continue;  // warp-uniform
-                const float dz = cz - v.oz, dx = cx - v.ox;
-                const float dxz = dx * dx + dz * dz;
-                const float dy0 = cy0 - v.oy, dy1 = cy1 - v.oy;
-                const float r20 = dxz + dy0 * dy0, r21 = dxz + dy1 * dy1;
-                if (r20 < v.h2) {
-                    const float w = sur_w(sqrtf(r20), v.hinv);
-                    const float ww = v.wr * w;
-                    a0[0] += v.m * w; a0[1] += ww; a0[2] += v.T * ww;
-                    a0[3] += v.vx * ww; a0[4] += v.vy * ww; a0[5] += v.vz * ww;
-                }
-                if (r21 < v.h2) {
-                    const float w = sur_w(sqrtf(r21), v.hinv);
-                    const float ww = v.wr * w;
-                    a1[0] += v.m * w; a1[1] += ww; a1[2] += v.T * ww;
-                    a1[3] += v.vx * ww; a1[4] += v.vy * ww; a1[5] += v.vz * ww;
-                }
-            }
-        }
-        if (ix < grid && iz < grid) {
-            const size_t rb = (size_t)r * G * G * G;
-            if (iy0 < grid) {
-                float *g = vacc + (rb + ((size_t)iz * G + iy0) * G + ix) * 6;
-                for (int c = 0; c < 6; c++)
-                    if (a0[c] != 0.f) atomicAdd(g + c, a0[c]);
-            }
-            if (iy1 < grid) {
-                float *g = vacc + (rb + ((size_t)iz * G + iy1) * G + ix) * 6;
-                for (int c = 0; c < 6; c++)
-                    if (a1[c] != 0.f) atomicAdd(g + c, a1[c]);
-            }
+    for (long long i = wid; i < n; i += nwarps) {
+        const int r = reg[i];
+        if (r < 0) continue;  // warp-uniform
+        const float4 pa = vpa[i], pb = vpb[i], pc = vpc[i];
+        const int bx = vbox[i], bz = __float_as_int(pc.w);
+        const int x0 = bx & 0xff, x1 = (bx >> 8) & 0xff, y0 = (bx >> 16) & 0xff, y1 = (bx >> 24) & 0xff;
+        const int z0 = bz >> 16, z1 = bz & 0xffff;
+        const int nx = x1 - x0 + 1, ny = y1 - y0 + 1, nz = z1 - z0 + 1;
+        const int nxy = nx * ny, vol = nxy * nz;
+        const float inx = 1.f / (float)nx, inxy = 1.f / (float)nxy;
+        float *base = acc8 + (size_t)r * G * G * G * 8;
+        for (int j = lane; j < vol; j += 32) {
+            // j -> (x, y, z) by float multiplies: exact for these small ranges
+            const int jz = (int)(((float)j + 0.5f) * inxy), rem = j - jz * nxy;
+            const int jy = (int)(((float)rem + 0.5f) * inx), jx = rem - jy * nx;
+            const int ix = x0 + jx, iy = y0 + jy, iz = z0 + jz;
+            const float dx = (ix + 0.5f) * df - pa.x, dy = (iy + 0.5f) * df - pa.y, dz = (iz + 0.5f) * df - pa.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= pa.w) continue;
+            const float w = m4_shape(sqrtf(r2) * pb.x);
+            if (w <= 0.f) continue;
+            const float ww = pb.z * w;
+            float *q = base + (((size_t)iz * G + iy) * G + ix) * 8;
+            red_v4(q, pb.y * w, ww, pb.w * ww, pc.x * ww);
+            red_v2(q + 4, pc.y * ww, pc.z * ww);
         }
     }
 }
@@ -336,7 +220,7 @@ __global__ void k_vox_finalize(const float *__restrict__ acc, long long nv, long
 {
     long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
-    const float *a = acc + v * 6;
+    const float *a = acc + v * 8;
     float rho_v = a[0], den = a[1];
     float T = den > 0.f ? a[2] / den : 10.f;
     float z[5];
@@ -354,8 +238,6 @@ __global__ void k_vox_finalize(const float *__restrict__ acc, long long nv, long
     }
 }
 
-__global__ void k_set_int(int *p, int v) { *p = v; }
-
 static int vox_sms()
 {
     static int n = []() {
@@ -370,7 +252,7 @@ static int vox_sms()
 __global__ void k_remap_weights(const float *__restrict__ pred, long long nv, int cout, double *__restrict__ w)
 {
     long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < nv) w[v] = pow(10.0, (double)pred[v * cout] - 0.33);
+    if (v < nv) w[v] = exp10((double)pred[v * cout] - 0.33);
 }
 
 // Cumulative weights along every grid line of every region, one thread per
@@ -443,7 +325,7 @@ __global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float 
     p.y[i] = np[1];
     p.z[i] = np[2];
     const float *pv = pred + ((((size_t)r * grid + c[2]) * grid + c[1]) * grid + c[0]) * cout;
-    double T = pow(10.0, 2.0 * (double)pv[1] + 2.0);
+    double T = exp10(2.0 * (double)pv[1] + 2.0);
     p.u[i] = (float)(T / SUR_T_PER_U);
     p.vx[i] = 20.f * pv[2];
     p.vy[i] = 20.f * pv[3];
@@ -456,53 +338,58 @@ int voxelise_buffers_for(gnb_ctx *c, int nreg, int grid)
     size_t nv = (size_t)nreg * grid * grid * grid;
     if (c->sur_pcap < c->cap) {
         c->sur_gen++;
-        dfree(c, c->sreg); dfree(c, c->vovf);
-        c->sreg = nullptr; c->vovf = nullptr;
+        dfree(c, c->sreg); dfree(c, c->vpa); dfree(c, c->vpb); dfree(c, c->vpc); dfree(c, c->vbox);
+        c->sreg = nullptr; c->vpa = nullptr; c->vpb = nullptr; c->vpc = nullptr; c->vbox = nullptr;
         GNB_TRY(dalloc(c, &c->sreg, (size_t)c->cap + 1));
-        GNB_TRY(dalloc(c, &c->vovf, (size_t)c->cap + 1));
+        GNB_TRY(dalloc(c, &c->vpa, (size_t)c->cap + 1));
+        GNB_TRY(dalloc(c, &c->vpb, (size_t)c->cap + 1));
+        GNB_TRY(dalloc(c, &c->vpc, (size_t)c->cap + 1));
+        GNB_TRY(dalloc(c, &c->vbox, (size_t)c->cap + 1));
         c->sur_pcap = c->cap;
     }
     if (c->sur_nv < nv || c->sur_nreg < nreg) {
         c->sur_gen++;
         dfree(c, c->vacc); dfree(c, c->vw); dfree(c, c->vcdf); dfree(c, c->cent_d); dfree(c, c->rcount);
-        dfree(c, c->vout); dfree(c, c->centf);
+        dfree(c, c->vout); dfree(c, c->rsx); dfree(c, c->rsi); dfree(c, c->centf);
         c->vacc = nullptr; c->vw = nullptr; c->vcdf = nullptr; c->cent_d = nullptr; c->rcount = nullptr;
-        c->vout = nullptr; c->centf = nullptr;
-        GNB_TRY(dalloc(c, &c->vacc, nv * 6));
+        c->vout = nullptr; c->rsx = nullptr; c->rsi = nullptr; c->centf = nullptr;
+        GNB_TRY(dalloc(c, &c->vacc, nv * 8));
         GNB_TRY(dalloc(c, &c->vw, nv));
         GNB_TRY(dalloc(c, &c->vcdf, nv * 3));
         GNB_TRY(dalloc(c, &c->vout, nv * 5));
         GNB_TRY(dalloc(c, &c->cent_d, (size_t)nreg * 3));
+        GNB_TRY(dalloc(c, &c->rsx, (size_t)nreg));
+        GNB_TRY(dalloc(c, &c->rsi, (size_t)nreg));
         GNB_TRY(dalloc(c, &c->centf, (size_t)nreg * 3));
         GNB_TRY(dalloc(c, &c->rcount, (size_t)nreg));
         c->sur_nv = nv;
         c->sur_nreg = nreg;
     }
-    const size_t tpa = (size_t)(grid + 7) / 8, ntile = (size_t)nreg * tpa * tpa * tpa;
-    if (c->vt_ntile < ntile) {
-        c->sur_gen++;
-        dfree(c, c->vt_count); dfree(c, c->vt_off); dfree(c, c->vt_cur); dfree(c, c->vt_choff);
-        c->vt_count = nullptr; c->vt_off = nullptr; c->vt_cur = nullptr; c->vt_choff = nullptr;
-        GNB_TRY(dalloc(c, &c->vt_count, ntile));
-        GNB_TRY(dalloc(c, &c->vt_off, ntile + 1));
-        GNB_TRY(dalloc(c, &c->vt_cur, ntile));
-        GNB_TRY(dalloc(c, &c->vt_choff, ntile + 1));
-        c->vt_ntile = ntile;
-    }
-    // tile-list slots: a support of h reaches about 2 h / 8 voxels + 1 tiles per
-    // axis; six per particle covers the usual supports, the rest overflow to
-    // the direct scatter
-    const size_t lcap = 6 * (size_t)c->cap + ((size_t)1 << 20);
-    if (c->vt_cap < lcap) {
-        c->sur_gen++;
-        dfree(c, c->vt_list);
-        c->vt_list = nullptr;
-        GNB_TRY(dalloc(c, &c->vt_list, lcap));
-        c->vt_cap = lcap;
-    }
-    if (!c->vt_total) GNB_TRY(dalloc(c, &c->vt_total, 1));
-    if (!c->vt_misc) GNB_TRY(dalloc(c, &c->vt_misc, 4));
     if (!c->seed_d) GNB_TRY(dalloc(c, &c->seed_d, 1));
+    return GNB_OK;
+}
+
+// Centres to the device, with the regions sorted by centre x (ties by
+// index) for the membership search.
+static int upload_centres(gnb_ctx *c, int nreg, const double *centers)
+{
+    c->rs_order.resize(nreg);
+    for (int k = 0; k < nreg; k++) c->rs_order[k] = k;
+    std::sort(c->rs_order.begin(), c->rs_order.end(), [&](int a, int b) {
+        return centers[3 * a] < centers[3 * b] || (centers[3 * a] == centers[3 * b] && a < b);
+    });
+    c->rs_x.resize(nreg);
+    c->rs_cf.resize(3 * nreg);
+    for (int k = 0; k < nreg; k++) c->rs_x[k] = (float)centers[3 * c->rs_order[k]];
+    for (int k = 0; k < 3 * nreg; k++) c->rs_cf[k] = (float)centers[k];
+    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->cent_d, centers, sizeof(double) * 3 * nreg, cudaMemcpyHostToDevice,
+                                          c->s), "centres"));
+    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->rsx, c->rs_x.data(), sizeof(float) * nreg, cudaMemcpyHostToDevice, c->s),
+                       "sorted centres"));
+    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->centf, c->rs_cf.data(), sizeof(float) * 3 * nreg, cudaMemcpyHostToDevice,
+                                          c->s), "FP32 centres"));
+    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->rsi, c->rs_order.data(), sizeof(int) * nreg, cudaMemcpyHostToDevice,
+                                          c->s), "centre order"));
     return GNB_OK;
 }
 
@@ -513,31 +400,14 @@ static int vox_launch(gnb_ctx *c, int nreg, double side, int grid, float *out, b
     int n = (int)c->n;
     PArr &a = c->P[c->cur];
     size_t nv = (size_t)nreg * grid * grid * grid;
-    const int tpa = (grid + 7) / 8;
-    const long long ntile = (long long)nreg * tpa * tpa * tpa;
     cudaMemsetAsync(c->rcount, 0, sizeof(int) * nreg, c->s);
-    counted(k_centres_f32)<<<(3 * nreg + 255) / 256, 256, 0, c->s>>>(c->cent_d, nreg, c->centf);
-    counted(k_region_assign)<<<(n + 255) / 256, 256, 0, c->s>>>(a, n, c->cent_d, c->centf, nreg, 0.5 * side,
-                                                                c->sreg, c->rcount);
-    cudaMemsetAsync(c->vacc, 0, sizeof(float) * nv * 6, c->s);
-    cudaMemsetAsync(c->vt_count, 0, sizeof(int) * ntile, c->s);
-    cudaMemsetAsync(c->vt_cur, 0, sizeof(int) * ntile, c->s);
-    cudaMemsetAsync(c->vt_total, 0, sizeof(unsigned long long), c->s);
-    cudaMemsetAsync(c->vt_misc, 0, 4 * sizeof(int), c->s);
-    counted(k_set_int)<<<1, 1, 0, c->s>>>(c->vt_misc, (int)ntile);
-    counted(k_vox_bin_count)<<<(n + 255) / 256, 256, 0, c->s>>>(a, n, c->sreg, c->cent_d, side, grid, tpa,
-                                                                (unsigned long long)c->vt_cap, c->vt_total,
-                                                                c->vt_count, c->vovf, c->vt_misc + 1);
-    GNB_TRY(device_scan(c, c->vt_count, c->vt_off, c->vt_misc, (int)ntile, nullptr));
-    counted(k_vox_bin_fill)<<<(n + 255) / 256, 256, 0, c->s>>>(a, n, c->sreg, c->cent_d, side, grid, tpa, c->vovf,
-                                                               c->vt_off, c->vt_count, c->vt_cur, c->vt_list);
-    counted(k_vox_scatter)<<<(n + 127) / 128, 128, 0, c->s>>>(a, n, c->sreg, c->vovf, c->rho, c->cent_d, side, grid,
-                                                              c->vacc);
-    counted(k_vox_chunks)<<<(unsigned)((ntile + 255) / 256), 256, 0, c->s>>>(c->vt_count, c->vt_misc, c->vt_cur);
-    GNB_TRY(device_scan(c, c->vt_cur, c->vt_choff, c->vt_misc, (int)ntile, c->vt_misc + 2));
-    counted(k_vox_tile)<<<(unsigned)(vox_sms() * 8), 256, 0, c->s>>>(
-        a, c->rho, c->cent_d, side, grid, tpa, c->vt_misc, c->vt_off, c->vt_count, c->vt_choff, c->vt_misc + 2,
-        c->vt_list, c->vacc);
+    counted(k_region_assign)<<<(n + 255) / 256, 256, 0, c->s>>>(a, n, c->cent_d, c->rsx, c->rsi, c->centf, nreg,
+                                                                0.5 * side, c->sreg, c->rcount);
+    cudaMemsetAsync(c->vacc, 0, sizeof(float) * nv * 8, c->s);
+    counted(k_vox_stage)<<<(n + 255) / 256, 256, 0, c->s>>>(a, n, c->sreg, c->rho, c->cent_d, side, grid, c->vpa,
+                                                            c->vpb, c->vpc, c->vbox);
+    counted(k_vox_warp_scatter)<<<(unsigned)(vox_sms() * 16), 256, 0, c->s>>>(n, c->sreg, c->vpa, c->vpb, c->vpc,
+                                                                             c->vbox, side, grid, c->vacc);
     counted(k_vox_finalize)<<<(unsigned)((nv + 255) / 256), 256, 0, c->s>>>(
         c->vacc, (long long)nv, (long long)grid * grid * grid, out, outb);
     GNB_LAUNCH_CHECK(c, "voxelise");
@@ -560,8 +430,7 @@ static int remap_launch(gnb_ctx *c, int nreg, double side, int grid, const float
 int voxelise(gnb_ctx *c, int nreg, const double *centers, double side, int grid, float *out_dev)
 {
     GNB_TRY(voxelise_buffers_for(c, nreg, grid));
-    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->cent_d, centers, sizeof(double) * 3 * nreg, cudaMemcpyHostToDevice,
-                                          c->s), "centres"));
+    GNB_TRY(upload_centres(c, nreg, centers));
     phase_begin(c, GNB_T_VOXELISE);
     int rc = vox_launch(c, nreg, side, grid, out_dev ? out_dev : c->vout, nullptr);
     phase_end(c);
@@ -572,15 +441,13 @@ int remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, int 
                   uint64_t seed, int sweeps)
 {
     GNB_TRY(voxelise_buffers_for(c, nreg, grid));
-    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->cent_d, centers, sizeof(double) * 3 * nreg, cudaMemcpyHostToDevice,
-                                          c->s), "centres"));
+    GNB_TRY(upload_centres(c, nreg, centers));
     unsigned long long sd = seed;
     GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->seed_d, &sd, sizeof(sd), cudaMemcpyHostToDevice, c->s), "seed"));
     int n = (int)c->n;
     cudaMemsetAsync(c->rcount, 0, sizeof(int) * nreg, c->s);
-    counted(k_centres_f32)<<<(3 * nreg + 255) / 256, 256, 0, c->s>>>(c->cent_d, nreg, c->centf);
-    counted(k_region_assign)<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], n, c->cent_d, c->centf, nreg, 0.5 * side,
-                                                                c->sreg, c->rcount);
+    counted(k_region_assign)<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], n, c->cent_d, c->rsx, c->rsi, c->centf,
+                                                                nreg, 0.5 * side, c->sreg, c->rcount);
     phase_begin(c, GNB_T_REMAP);
     GNB_TRY(remap_launch(c, nreg, side, grid, pred_dev, 5, sweeps));
     phase_end(c);
@@ -597,9 +464,9 @@ int sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *center
     int grid = 0, cout = 0;
     GNB_TRY(unet_prepare(net, nreg, &xin, &yout, &grid, &cout));
     if (cout != 5) return fail(c, GNB_EINVAL, "the surrogate network must predict 5 channels");
+    if (grid > 256) return fail(c, GNB_EINVAL, "surrogate grids are limited to 256 voxels per axis");
     GNB_TRY(voxelise_buffers_for(c, nreg, grid));
-    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->cent_d, centers, sizeof(double) * 3 * nreg, cudaMemcpyHostToDevice,
-                                          c->s), "centres"));
+    GNB_TRY(upload_centres(c, nreg, centers));
     unsigned long long sd = seed;
     GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->seed_d, &sd, sizeof(sd), cudaMemcpyHostToDevice, c->s), "seed"));
     bool same = c->sn_graph && c->sn_key[0] == nreg && c->sn_key[1] == grid && c->sn_key[2] == sweeps &&
