@@ -48,11 +48,12 @@ constexpr int HX = 10, HY = 18;          // halo extent in x and y
 constexpr unsigned ROW_BYTES = 16;       // one voxel of one 8-channel group
 constexpr unsigned YSTRIDE = HX * ROW_BYTES;
 constexpr unsigned ZSTRIDE = HY * YSTRIDE;
-constexpr unsigned HDR = 128;            // barriers, TMEM slot, abort word
+constexpr unsigned HDR = 256;            // barriers, TMEM slot, abort word
+constexpr int MAX_WSTAGE = 4;            // weight ring stages when the weights are streamed
 constexpr unsigned ALIGN_SLACK = 1024;
 constexpr unsigned long long WAIT_NS = 1000000000ull;
 
-enum { B_W = 0, B_HF = 1, B_HE = 3, B_AF = 5, B_AE = 7, B_DR = 9, NBARS = 10 };
+enum { B_W = 0, B_HF = 1, B_HE = 3, B_AF = 5, B_AE = 7, B_DR = 9, B_WF = 10, B_WE = 14, NBARS = 18 };
 
 struct TcArgs {
     const bf16 *w;
@@ -61,6 +62,7 @@ struct TcArgs {
     int N, K, C1, O1, relu;
     int B, D, H, W;
     int Zt, nbuf, tx, ty, tz;
+    int wstages;  // 0: all 27 taps resident; else a ring of this many one-tap stages
     long long ntiles;
     unsigned wbytes, plane, halo, off_w, off_h, tx_bytes, tmem_cols, idesc;
     int *err;
@@ -219,6 +221,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mb_init(bar(B_AE + b), 128);
         }
         mb_init(bar(B_DR), 1);
+        for (int q = 0; q < MAX_WSTAGE; q++) {
+            mb_init(bar(B_WF + q), 1);
+            mb_init(bar(B_WE + q), 1);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -237,12 +243,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 4) {
         if (lane == 0) {
             // ---------------------------------------------------------- producer
-            mb_expect_tx(bar(B_W), p.wbytes);
-            for (unsigned o = 0; o < p.wbytes; o += 32768u) {
-                unsigned n = p.wbytes - o < 32768u ? p.wbytes - o : 32768u;
-                bulk_load(sW + o, reinterpret_cast<const unsigned char *>(p.w) + o, n, bar(B_W));
+            const unsigned wtap = (unsigned)kc8 * (unsigned)p.N * 16u;  // bytes of one tap's weights
+            if (!p.wstages) {
+                mb_expect_tx(bar(B_W), p.wbytes);
+                for (unsigned o = 0; o < p.wbytes; o += 32768u) {
+                    unsigned n = p.wbytes - o < 32768u ? p.wbytes - o : 32768u;
+                    bulk_load(sW + o, reinterpret_cast<const unsigned char *>(p.w) + o, n, bar(B_W));
+                }
             }
             int uses[2] = {0, 0};
+            long long wg = 0;  // weight-tap loads issued (streamed mode)
+            bool stop = false;
             int i = 0;
             for (long long t = blockIdx.x; t < p.ntiles; t += gridDim.x, i++) {
                 const int b = i % p.nbuf;
@@ -263,19 +274,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                     bar(B_HF + b));
                 }
                 uses[b]++;
+                // streamed weights: the 27 taps of this tile through the ring
+                for (int tap = 0; p.wstages && tap < 27; tap++, wg++) {
+                    const int st = (int)(wg % p.wstages);
+                    const unsigned kk = (unsigned)(wg / p.wstages);
+                    if (kk > 0 && !mb_wait(bar(B_WE + st), (kk - 1) & 1u, abort_flag, p.err, 8)) {
+                        stop = true;
+                        break;
+                    }
+                    mb_expect_tx(bar(B_WF + st), wtap);
+                    bulk_load(sW + (unsigned)st * wtap, reinterpret_cast<const unsigned char *>(p.w) + (size_t)tap * wtap,
+                              wtap, bar(B_WF + st));
+                }
+                if (stop) break;
             }
             // drain: every copy this CTA issued has landed before it exits
-            mb_wait(bar(B_W), 0, abort_flag, p.err, 2, false);
+            if (!p.wstages) mb_wait(bar(B_W), 0, abort_flag, p.err, 2, false);
             for (int b = 0; b < 2; b++)
                 if (uses[b] > 0) mb_wait(bar(B_HF + b), (unsigned)(uses[b] - 1) & 1u, abort_flag, p.err, 2, false);
+            for (int st = 0; p.wstages && st < p.wstages; st++) {
+                // the last load issued into stage st is number (wg - 1 - ((wg - 1 - st) mod S))
+                if (wg > st) {
+                    const long long last = st + ((wg - 1 - st) / p.wstages) * p.wstages;
+                    mb_wait(bar(B_WF + st), (unsigned)(last / p.wstages) & 1u, abort_flag, p.err, 2, false);
+                }
+            }
         }
     } else if (warp == 5) {
         // ------------------------------------------------------------------ MMA
         // The Zt z-planes of a tile accumulate into Zt independent TMEM
         // blocks; their MMAs are interleaved so consecutive MMAs never feed
         // the same accumulator.
-        int ok = mb_wait(bar(B_W), 0, abort_flag, p.err, 3);
+        int ok = p.wstages ? 1 : mb_wait(bar(B_W), 0, abort_flag, p.err, 3);
         if (__all_sync(0xffffffffu, ok)) {
+            long long wg = 0;  // weight taps consumed (streamed mode)
             const unsigned wtap = (unsigned)kc8 * (unsigned)p.N * 16u;  // bytes of one tap's weights
             const unsigned nbytes16 = (unsigned)p.N * 16u;              // one channel group of weights
             int i = 0;
@@ -291,10 +323,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 const unsigned hb = sH + (unsigned)b * p.halo;
                 const unsigned d0 = tmem + (unsigned)(b * p.Zt * p.N);
+                bool stop = false;
                 for (int tap = 0; tap < 27; tap++) {
                     const int tz = tap / 9, ty = (tap / 3) % 3, tx = tap % 3;
                     const unsigned a0 = hb + (unsigned)tz * ZSTRIDE + (unsigned)ty * YSTRIDE + (unsigned)tx * ROW_BYTES;
-                    const unsigned w0 = sW + (unsigned)tap * wtap;
+                    unsigned w0 = sW + (unsigned)tap * wtap;
+                    int st = 0;
+                    if (p.wstages) {
+                        st = (int)(wg % p.wstages);
+                        ok = mb_wait(bar(B_WF + st), (unsigned)(wg / p.wstages) & 1u, abort_flag, p.err, 9);
+                        if (!__all_sync(0xffffffffu, ok)) { stop = true; break; }
+                        tc_fence_after();
+                        w0 = sW + (unsigned)st * wtap;
+                    }
                     for (int ks = 0; ks < (p.K >> 4); ks++) {
                         const unsigned long long bd = sdesc(w0 + 2u * ks * nbytes16, nbytes16, 128u);
                         const unsigned acc = (tap | ks) != 0;
@@ -304,7 +345,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             tc_mma_elect(d0 + (unsigned)(zz * p.N), ad, bd, p.idesc, acc);
                         }
                     }
+                    if (p.wstages) {
+                        tc_commit_elect(bar(B_WE + st));  // the stage is free once these MMAs complete
+                        wg++;
+                    }
                 }
+                if (stop) break;
                 tc_commit_elect(bar(B_HE + b));
                 tc_commit_elect(bar(B_AF + b));
             }
@@ -434,28 +480,34 @@ unsigned pow2_at_least(unsigned v)
 bool conv3_tc_plan(int N, int K, int D, TcPlan *pl)
 {
     if (N < 16 || N > 256 || (N % 16) || K < 16 || (K % 16)) return false;
-    const unsigned wbytes = 27u * (unsigned)N * (unsigned)K * 2u;
+    const unsigned wtap = (unsigned)N * (unsigned)K * 2u;
     static const int zts[] = {4, 2, 1};
-    for (int nbuf = 2; nbuf >= 1; nbuf--) {
-        for (int zt : zts) {
-            if (zt > 1 && zt > D) continue;
-            const unsigned plane = ((unsigned)(zt + 2) * ZSTRIDE + 127u) & ~127u;
-            const unsigned halo = (unsigned)(K / 8) * plane;
-            const unsigned off_w = HDR;
-            const unsigned off_h = (off_w + wbytes + 127u) & ~127u;
-            const unsigned smem = ALIGN_SLACK + off_h + (unsigned)nbuf * halo;
-            const unsigned cols = pow2_at_least((unsigned)(nbuf * zt * N));
-            if (smem > TC_SMEM_MAX || cols > 512) continue;
-            pl->Zt = zt;
-            pl->nbuf = nbuf;
-            pl->plane = plane;
-            pl->halo = halo;
-            pl->off_w = off_w;
-            pl->off_h = off_h;
-            pl->wbytes = wbytes;
-            pl->smem = smem;
-            pl->tmem_cols = cols;
-            return true;
+    // resident weights first; then a ring of 4, 3, 2 one-tap stages
+    for (int stages = 0; stages <= MAX_WSTAGE; stages = stages ? stages - 1 : MAX_WSTAGE) {
+        if (stages == 1) break;
+        const unsigned wbytes = (stages ? (unsigned)stages : 27u) * wtap;
+        for (int nbuf = 2; nbuf >= 1; nbuf--) {
+            for (int zt : zts) {
+                if (zt > 1 && zt > D) continue;
+                const unsigned plane = ((unsigned)(zt + 2) * ZSTRIDE + 127u) & ~127u;
+                const unsigned halo = (unsigned)(K / 8) * plane;
+                const unsigned off_w = HDR;
+                const unsigned off_h = (off_w + wbytes + 127u) & ~127u;
+                const unsigned smem = ALIGN_SLACK + off_h + (unsigned)nbuf * halo;
+                const unsigned cols = pow2_at_least((unsigned)(nbuf * zt * N));
+                if (smem > TC_SMEM_MAX || cols > 512) continue;
+                pl->Zt = zt;
+                pl->nbuf = nbuf;
+                pl->wstages = stages;
+                pl->plane = plane;
+                pl->halo = halo;
+                pl->off_w = off_w;
+                pl->off_h = off_h;
+                pl->wbytes = wbytes;
+                pl->smem = smem;
+                pl->tmem_cols = cols;
+                return true;
+            }
         }
     }
     return false;
@@ -497,6 +549,7 @@ int conv3_tc(const TcConv &c, int *err, cudaStream_t s)
     a.B = c.B; a.D = c.D; a.H = c.H; a.W = c.W;
     a.Zt = pl.Zt;
     a.nbuf = pl.nbuf;
+    a.wstages = pl.wstages;
     a.tx = (c.W + 7) / 8;
     a.ty = (c.H + 15) / 16;
     a.tz = (c.D + pl.Zt - 1) / pl.Zt;

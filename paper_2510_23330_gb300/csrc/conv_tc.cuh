@@ -28,13 +28,15 @@ struct TcConv {
 };
 
 struct TcPlan {
-    int Zt, nbuf;
+    int Zt, nbuf, wstages;
     unsigned plane, halo, off_w, off_h, wbytes, smem, tmem_cols;
 };
 
 // Tile depth, buffering and shared-memory layout for N output and K input
-// channels on a grid of depth D; false when the shape is not supported
-// (N or K not a multiple of 16, N > 256, or the resident weights too large).
+// channels on a grid of depth D: all 27 taps' weights resident when they fit,
+// else a ring of 4 to 2 one-tap stages streamed per tile; false when the
+// shape is not supported (N or K not a multiple of 16, N > 256, or not even a
+// two-stage ring fits).
 bool conv3_tc_plan(int N, int K, int D, TcPlan *pl);
 
 // Launches the convolution on s.  Returns 1 when launched, 0 when the shape
