@@ -331,7 +331,10 @@ def run_ours(args, world, rank, local):
     ctx = galnb.Context(stream=stream.cuda_stream, **pr["cfg"])
     ctx.set_particles(p)
     tuning = None
-    if mode == 1 and not args.no_autotune:
+    if args.n_group:
+        pr["cfg"]["n_group"] = args.n_group
+        ctx.set_params(n_group=args.n_group)
+    elif mode == 1 and not args.no_autotune:
         from paper_2510_23330_gb300 import autotune
         best, table = autotune.tune_group_size(ctx, mode)
         pr["cfg"]["n_group"] = best
@@ -339,6 +342,7 @@ def run_ours(args, world, rank, local):
     ctx.compute_forces(mode)
     for _ in range(args.warmup):
         ctx.step_kdk(args.dt, 1, mode)
+    d0 = ctx.diagnostics()  # FP64 energies, momentum, angular momentum before the timed steps
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
     clocks = ClockSampler(local) if not args.no_clocks else None
     ctx.set_timing(True)
@@ -363,6 +367,9 @@ def run_ours(args, world, rank, local):
         time.sleep(0.05)
         clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    d1 = ctx.diagnostics()
+    e0, e1 = float(np.sum(d0[:4])), float(np.sum(d1[:4]))
+    psc = float(np.sum(np.abs(d0[:4])))
     total_ms = sum(step_ms)
     phases, calls, launches = ctx.phase_times(reset=True)
     ctx.set_timing(False)
@@ -393,6 +400,11 @@ def run_ours(args, world, rank, local):
         "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
         "gpu_launches": int(launches),
         "step_ms": step_ms,
+        "drift": {"steps": args.steps, "energy_rel": (e1 - e0) / abs(e0) if e0 else None,
+                  "momentum_rel": float(np.linalg.norm(d1[4:7] - d0[4:7])) / max(psc, 1e-300),
+                  "energy_before": e0, "energy_after": e1,
+                  "note": "E = E_kin + E_pot + E_ext + E_th (FP64 reductions); |dP| relative to sum |E| "
+                          "as the momentum scale is not defined separately"},
     }
     if clocks:
         out["clocks"] = clocks.summary(h0, h1)
@@ -471,6 +483,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--n-group", type=int, default=0, help="fixed group size n_g (skips the autotuner)")
     ap.add_argument("--no-sn", action="store_true", help="skip the supernova surrogate-vs-plain section")
     args = ap.parse_args()
     if args.impl == "reference":
