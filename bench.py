@@ -369,7 +369,8 @@ def run_ours(args, world, rank, local):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     d1 = ctx.diagnostics()
     e0, e1 = float(np.sum(d0[:4])), float(np.sum(d1[:4]))
-    psc = float(np.sum(np.abs(d0[:4])))
+    # momentum scale: sum m |v| of the initial state
+    psc = float(np.sum(p["m"] * np.sqrt(p["vx"].astype(np.float64) ** 2 + p["vy"] ** 2 + p["vz"] ** 2)))
     total_ms = sum(step_ms)
     phases, calls, launches = ctx.phase_times(reset=True)
     ctx.set_timing(False)
@@ -403,8 +404,8 @@ def run_ours(args, world, rank, local):
         "drift": {"steps": args.steps, "energy_rel": (e1 - e0) / abs(e0) if e0 else None,
                   "momentum_rel": float(np.linalg.norm(d1[4:7] - d0[4:7])) / max(psc, 1e-300),
                   "energy_before": e0, "energy_after": e1,
-                  "note": "E = E_kin + E_pot + E_ext + E_th (FP64 reductions); |dP| relative to sum |E| "
-                          "as the momentum scale is not defined separately"},
+                  "note": "E = E_kin + E_pot + E_ext + E_th (FP64 reductions, the static halo included); "
+                          "|dP| relative to sum m|v|; the NFW halo is external, so P is not conserved exactly"},
     }
     if clocks:
         out["clocks"] = clocks.summary(h0, h1)
