@@ -180,6 +180,10 @@ struct gnb_ctx {
     unsigned long long *counters_d = nullptr;  // [8]
     int *work_d = nullptr;                     // work counters of persistent kernels [8]
     int *scan_part = nullptr, *scan_poff = nullptr;  // device_scan scratch [1100]
+    // tree-gravity interaction lists (gravity.cu): chunk pool and per-group heads
+    int *gl_pool = nullptr, *gl_next = nullptr, *gl_cnt = nullptr, *gl_top = nullptr;
+    int4 *gl_head = nullptr, *gl_ref = nullptr;
+    int gl_cap = 0, gl_gcap = 0;
     int *pinned_i = nullptr;                   // pinned host scratch [64]
     double *red_d = nullptr;                   // reduction scratch
     int64_t stats[GNB_S_COUNT_] = {0};

@@ -2,24 +2,33 @@
 // by Barnes-Hut group walk (Sec. 3.4, 5.2.2, 5.2.4) or direct summation,
 // plus the static NFW halo of the disk model.
 //
-// Design (GB300): one CTA of GW_THREADS threads per group, scheduled
-// persistently from a device work counter.  The CTA walks the octree with a
-// shared-memory stack, testing up to GW_THREADS cells at a time with the
-// exact integer opening test, and stages accepted cells (monopole +
-// quadrupole) and the particles of opened leaves in shared memory as FP32
-// offsets from the group's reference grid point (Sec. 4.3 mixed precision).
-// When a staging buffer fills, every thread evaluates its i-particle against
-// the staged j entries, which are read as warp-wide broadcasts.  Small groups
-// split the j loop over warps ("j-splits") so that all warps stay busy.
+// Design (GB300), tree gravity in two kernels:
+//  * k_grav_walk: one warp per group walks the octree (Sec. 3.4) with a
+//    per-warp shared-memory stack, testing up to 32 nodes at a time with the
+//    exact integer opening test, and writes the group's interaction lists --
+//    accepted cells and opened leaves -- into chains of 256-entry chunks of a
+//    device pool.  No CTA barriers, high occupancy: the walk is latency bound
+//    and many warps hide the latency of the node loads.
+//  * k_grav_eval: one CTA of GW_THREADS threads per group, scheduled
+//    persistently; it streams the group's chains through shared memory,
+//    staging accepted cells (monopole + quadrupole) and the particles of
+//    opened leaves as FP32 offsets from the group's reference grid point
+//    (Sec. 4.3 mixed precision); every thread evaluates its i-particle
+//    against the staged j entries, read as warp-wide broadcasts.  Small
+//    groups split the j loop over warps ("j-splits") so all warps stay busy.
 // Pair arithmetic is FP32 on the CUDA cores (not a dense contraction).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gnb {
 
 #define GW_THREADS 128
-#define GW_STACK 4096
+#define GL_CH 256        // entries per list chunk
+#define GL_WARPS 8       // warps per walk CTA
+#define GL_STACK 1024    // walk stack entries per warp
 #define GW_LEAF 256
-#define GW_JP 1024
+#define GW_JP 512
 #define GW_JC 256
 
 struct GravParams {
@@ -37,18 +46,23 @@ struct GravParams {
     int *next;
     int *status;
     unsigned long long *counters;
+    // interaction-list pool (tree walk -> evaluation)
+    int *pool, *cnext, *ccnt, *top;
+    int4 *ghead;   // per group: {cell chain head, leaf chain head, particles in opened leaves, -}
+    int4 *gref;    // per group: reference grid cell {x, y, z, -}
+    int cap;       // pool chunks
 };
 
 struct GravSmem {
-    int stack[GW_STACK];
     int leaf[GW_LEAF];
     int leafoff[GW_LEAF + 1];
     float4 jp[GW_JP];
     float je[GW_JP];
-    float4 c0[GW_JC], c1[GW_JC], c2[GW_JC];
+    float4 c0[2][GW_JC], c1[2][GW_JC], c2[2][GW_JC];  // two buffers: one evaluated, one filling
+    int4 cnb[2][GW_JC];                                // raw cell corners of the buffer being filled
     float4 red[GW_THREADS];
     int ws[32];
-    int sp, nl, nc, g, bmin[3], bmax[3];
+    int g;
 };
 
 __device__ __forceinline__ bool must_open(int4 C, int level, const int *bmin, const int *bmax, double theta2)
@@ -99,14 +113,14 @@ __device__ __forceinline__ void pp_loop(const GravSmem &S, int np, int split, in
 //   a   += -M r/R^3 + Q r/R^5 - 5/2 (r.Q.r) r/R^7
 //   phi += -M/R - 1/2 r.Q.r/R^5         (accumulated with the sign flipped)
 template <bool QUAD>
-__device__ __forceinline__ void pc_loop(const GravSmem &S, int nc, int split, int js, float xi, float yi, float zi,
-                                        float e2i, float &ax, float &ay, float &az, float &ph)
+__device__ __forceinline__ void pc_loop(const GravSmem &S, int buf, int nc, int split, int js, float xi, float yi,
+                                        float zi, float e2i, float &ax, float &ay, float &az, float &ph)
 {
 #pragma unroll 2
     for (int c = split; c < nc; c += js) {
-        float4 a = S.c0[c];
-        float4 b = S.c1[c];
-        float4 d = S.c2[c];
+        float4 a = S.c0[buf][c];
+        float4 b = S.c1[buf][c];
+        float4 d = S.c2[buf][c];
         float rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
         float R2 = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, __fmaf_rn(rz, rz, e2i + d.z)));
         float Ri = rsqrtf(R2);
@@ -159,38 +173,206 @@ __device__ __forceinline__ int block_scan_excl(int v, int *ws, int *tot)
     return r;
 }
 
+// Appends the entries of the lanes with flag set to a chunk chain (cur: the
+// chain's current chunk, cnt: entries in it).  A full chunk is closed and a
+// new one taken from the pool; when the pool is exhausted the chain goes dead
+// (cur = -1), the pool counter exceeds its capacity and the host repeats the
+// walk with a larger pool.
+__device__ __forceinline__ void chain_append(bool flag, int val, int &cur, int &cnt, const GravParams &p, int lane)
+{
+    const unsigned b = __ballot_sync(0xffffffffu, flag);
+    if (!b) return;
+    const int n = __popc(b), pre = __popc(b & ((1u << lane) - 1u));
+    const bool spill = cnt + n > GL_CH;
+    int nxt = -1;
+    if (spill) {
+        if (lane == 0) {
+            if (cur >= 0) {
+                nxt = atomicAdd(p.top, 1);
+                if (nxt >= p.cap) nxt = -1;
+                p.cnext[cur] = nxt;
+                p.ccnt[cur] = GL_CH;
+            }
+        }
+        nxt = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+    const int pos = cnt + pre;
+    if (flag) {
+        if (pos < GL_CH) {
+            if (cur >= 0) p.pool[(size_t)cur * GL_CH + pos] = val;
+        } else if (nxt >= 0) {
+            p.pool[(size_t)nxt * GL_CH + pos - GL_CH] = val;
+        }
+    }
+    if (spill) { cur = nxt; cnt = cnt + n - GL_CH; }
+    else cnt += n;
+}
+
+__device__ __forceinline__ int chain_new(const GravParams &p, int lane)
+{
+    int c = 0;
+    if (lane == 0) {
+        c = atomicAdd(p.top, 1);
+        if (c >= p.cap) c = -1;
+    }
+    return __shfl_sync(0xffffffffu, c, 0);
+}
+
+// Closes a chain: records the last chunk's count and pads its unused slots
+// with node 0 (a valid index), so a whole chunk can always be copied.
+__device__ __forceinline__ void chain_close(const GravParams &p, int cur, int cnt, int lane)
+{
+    if (cur < 0) return;
+    for (int q = cnt + lane; q < GL_CH; q += 32) p.pool[(size_t)cur * GL_CH + q] = 0;
+    if (lane == 0) {
+        p.ccnt[cur] = cnt;
+        p.cnext[cur] = -1;
+    }
+}
+
+__device__ __forceinline__ void cp_async16_g(void *smem, const void *g)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_g() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_g() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Raw data of up to GW_JC accepted cells (two per thread, node indices in
+// idx) into buffer b: corner, centre of mass + mass, quadrupole.
+__device__ __forceinline__ void cells_issue(GravSmem &S, const GravParams &p, int b, const int *idx)
+{
+    for (int h = 0; h < 2; h++) {
+        const int s = threadIdx.x + h * GW_THREADS, node = idx[h];
+        cp_async16_g(&S.cnb[b][s], &p.nb[node]);
+        cp_async16_g(&S.c0[b][s], &p.mo0[node]);
+        cp_async16_g(&S.c1[b][s], &p.mo1[node]);
+        cp_async16_g(&S.c2[b][s], &p.mo2[node]);
+    }
+    cp_async_commit_g();
+}
+
+// Centre of mass as an FP32 offset from the group's reference grid cell.
+__device__ __forceinline__ void cells_convert(GravSmem &S, int b, const int *gref, float unit)
+{
+    for (int h = 0; h < 2; h++) {
+        const int s = threadIdx.x + h * GW_THREADS;
+        const int4 C = S.cnb[b][s];
+        const float4 m0 = S.c0[b][s];
+        S.c0[b][s] = make_float4(grid_off(C.x, gref[0], m0.x, unit), grid_off(C.y, gref[1], m0.y, unit),
+                                 grid_off(C.z, gref[2], m0.z, unit), m0.w);
+    }
+}
+
+// Tree walk of one group per warp (see the file comment).
+__global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
+{
+    __shared__ int stack[GL_WARPS][GL_STACK];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int *st = stack[w];
+    const int ngroups = *p.ngroups;
+    unsigned long long cnt_pp = 0, cnt_pc = 0;
+    for (;;) {
+        int gi = 0;
+        if (lane == 0) gi = atomicAdd(p.next, 1);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if (gi >= ngroups) break;
+        const int4 ga = __ldg(&p.na[p.groups[gi]]);
+        const int gfirst = ga.x, gcount = ga.y;
+        // bounding box of the group's particle cells
+        int bmin[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, bmax[3] = {-1, -1, -1};
+        for (int i = gfirst + lane; i < gfirst + gcount; i += 32) {
+            const int cc[3] = {p.cx[i], p.cy[i], p.cz[i]};
+#pragma unroll
+            for (int a = 0; a < 3; a++) { bmin[a] = min(bmin[a], cc[a]); bmax[a] = max(bmax[a], cc[a]); }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            for (int o = 16; o > 0; o >>= 1) {
+                bmin[a] = min(bmin[a], __shfl_xor_sync(0xffffffffu, bmin[a], o));
+                bmax[a] = max(bmax[a], __shfl_xor_sync(0xffffffffu, bmax[a], o));
+            }
+        int ccur = chain_new(p, lane), lcur = chain_new(p, lane);
+        const int chead = ccur, lhead = lcur;
+        int ccnt = 0, lcnt = 0, ncell = 0, npart = 0;
+        int sp = 1;
+        if (lane == 0) st[0] = 0;
+        __syncwarp();
+        while (sp > 0) {
+            // pop up to 32 nodes, keeping room for their children
+            int k = min(32, sp);
+            const int room = max(1, (GL_STACK - sp) / 7);
+            k = min(k, room);
+            const int node = lane < k ? st[sp - k + lane] : -1;
+            __syncwarp();
+            sp -= k;
+            bool is_cell = false, is_leaf = false;
+            int nch = 0, child0 = 0, lcount = 0;
+            if (node >= 0) {
+                const int4 a = __ldg(&p.na[node]);
+                const int lev = a.w & 255;
+                const bool open = node == 0 || must_open(__ldg(&p.nb[node]), lev, bmin, bmax, p.theta2);
+                if (!open) is_cell = true;
+                else if ((a.w >> 8) == 0) { is_leaf = true; lcount = a.y; }
+                else { nch = a.w >> 8; child0 = a.z; }
+            }
+            // push children (inclusive scan of the child counts over the warp)
+            int inc = nch;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const int tot = __shfl_sync(0xffffffffu, inc, 31);
+            const int base = sp + inc - nch;
+            for (int q = 0; q < nch; q++) {
+                if (base + q < GL_STACK) st[base + q] = child0 + q;
+                else atomicOr(p.status, ST_STACK_OVERFLOW);
+            }
+            sp = min(sp + tot, GL_STACK);
+            __syncwarp();
+            chain_append(is_cell, node, ccur, ccnt, p, lane);
+            chain_append(is_leaf, node, lcur, lcnt, p, lane);
+            ncell += __popc(__ballot_sync(0xffffffffu, is_cell));
+            int lp = lcount;
+            for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
+            npart += lp;
+        }
+        chain_close(p, ccur, ccnt, lane);
+        chain_close(p, lcur, lcnt, lane);
+        if (lane == 0) {
+            p.ghead[gi] = make_int4(chead, lhead, npart, 0);
+            p.gref[gi] = make_int4((bmin[0] + bmax[0]) >> 1, (bmin[1] + bmax[1]) >> 1, (bmin[2] + bmax[2]) >> 1, 0);
+        }
+        cnt_pc += (unsigned long long)ncell * gcount;
+        cnt_pp += (unsigned long long)npart * gcount;
+    }
+    if (lane == 0) {
+        atomicAdd(&p.counters[0], cnt_pp);
+        atomicAdd(&p.counters[1], cnt_pc);
+    }
+}
+
+// Evaluation of the walk's lists, one group per CTA (see the file comment).
 template <bool MASK, bool QUAD>
-__global__ void __launch_bounds__(GW_THREADS, 4) k_gravity_tree(GravParams p)
+__global__ void __launch_bounds__(GW_THREADS, 4) k_grav_eval(GravParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GravSmem &S = *reinterpret_cast<GravSmem *>(smem_raw);
     const int tid = threadIdx.x;
     const float unit = (float)p.box[4];
     const int ngroups = *p.ngroups;
-    unsigned long long cnt_pp = 0, cnt_pc = 0;
-
     for (;;) {
         if (tid == 0) S.g = atomicAdd(p.next, 1);
         __syncthreads();
         const int gi = S.g;
         if (gi >= ngroups) break;
-        const int gnode = p.groups[gi];
-        const int4 ga = p.na[gnode];
+        const int4 ga = p.na[p.groups[gi]];
         const int gfirst = ga.x, gcount = ga.y;
-        // bounding box of the whole group (its cells on the Morton grid)
-        if (tid < 3) { S.bmin[tid] = 0x7fffffff; S.bmax[tid] = -1; }
-        __syncthreads();
-        for (int i = gfirst + tid; i < gfirst + gcount; i += GW_THREADS) {
-            int cc[3] = {p.cx[i], p.cy[i], p.cz[i]};
-#pragma unroll
-            for (int a = 0; a < 3; a++) { atomicMin(&S.bmin[a], cc[a]); atomicMax(&S.bmax[a], cc[a]); }
-        }
-        __syncthreads();
-        const int bmin[3] = {S.bmin[0], S.bmin[1], S.bmin[2]}, bmax[3] = {S.bmax[0], S.bmax[1], S.bmax[2]};
-        const int gref[3] = {(bmin[0] + bmax[0]) >> 1, (bmin[1] + bmax[1]) >> 1, (bmin[2] + bmax[2]) >> 1};
+        const int4 gh = p.ghead[gi];
+        const int4 gr = p.gref[gi];
+        const int gref[3] = {gr.x, gr.y, gr.z};
         for (int i0 = 0; i0 < gcount; i0 += GW_THREADS) {
             const int icnt = min(GW_THREADS, gcount - i0);
-            // j-splits: warps share i-particles and split the j loop
             // j-splits: each of the js = floor(128 / icnt) thread sets holds all
             // icnt i-particles and takes every js-th j entry
             const int ilanes = icnt;
@@ -198,106 +380,104 @@ __global__ void __launch_bounds__(GW_THREADS, 4) k_gravity_tree(GravParams p)
             const int islot = tid % ilanes, split = tid / ilanes;
             const bool ivalid = split < js;
             const int ip = gfirst + i0 + islot;
-            const int ci[3] = {p.cx[ip], p.cy[ip], p.cz[ip]};
-            const float xi = grid_off(ci[0], gref[0], p.rx[ip], unit);
-            const float yi = grid_off(ci[1], gref[1], p.ry[ip], unit);
-            const float zi = grid_off(ci[2], gref[2], p.rz[ip], unit);
+            const float xi = grid_off(p.cx[ip], gref[0], p.rx[ip], unit);
+            const float yi = grid_off(p.cy[ip], gref[1], p.ry[ip], unit);
+            const float zi = grid_off(p.cz[ip], gref[2], p.rz[ip], unit);
             const float epi = p.eps[ip];
             const float e2i = epi * epi;
             float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
-            if (tid == 0) { S.sp = 1; S.stack[0] = 0; S.nl = 0; S.nc = 0; }
-            for (;;) {
-                __syncthreads();
-                const int sp = S.sp;
-                const int nl0 = S.nl, nc0 = S.nc;
-                // flush staged cells
-                if (nc0 > GW_JC - GW_THREADS || (sp == 0 && nc0 > 0)) {
-                    if (ivalid) pc_loop<QUAD>(S, nc0, split, js, xi, yi, zi, e2i, ax, ay, az, ph);
-                    cnt_pc += (unsigned long long)nc0 * icnt;
-                    __syncthreads();
-                    if (tid == 0) S.nc = 0;
-                }
-                // flush pending leaves: expand to particles in chunks of GW_JP
-                if (nl0 > GW_LEAF - GW_THREADS || (sp == 0 && nl0 > 0)) {
-                    int total = 0;
-                    for (int q0 = 0; q0 < nl0; q0 += GW_THREADS) {
-                        int q = q0 + tid;
-                        int v = q < nl0 ? p.na[S.leaf[q]].y : 0;
-                        int tot;
-                        int e = block_scan_excl(v, S.ws, &tot);
-                        if (q < nl0) S.leafoff[q] = total + e;
-                        total += tot;
+            // accepted cells, one chunk at a time, double buffered: while a
+            // chunk is evaluated, cp.async fills the other buffer with the
+            // next chunk (whose node indices were loaded one chunk earlier)
+            {
+                int ch = gh.x, b = 0;
+                int idx[2] = {0, 0}, nxt = -1;
+                if (ch >= 0) {
+                    idx[0] = p.pool[(size_t)ch * GL_CH + tid];
+                    idx[1] = p.pool[(size_t)ch * GL_CH + tid + GW_THREADS];
+                    cells_issue(S, p, 0, idx);
+                    nxt = p.cnext[ch];
+                    if (nxt >= 0) {
+                        idx[0] = p.pool[(size_t)nxt * GL_CH + tid];
+                        idx[1] = p.pool[(size_t)nxt * GL_CH + tid + GW_THREADS];
                     }
-                    if (tid == 0) S.leafoff[nl0] = total;
+                    cp_async_wait_all_g();
+                    cells_convert(S, 0, gref, unit);
                     __syncthreads();
-                    for (int c0 = 0; c0 < total; c0 += GW_JP) {
-                        int np = min(GW_JP, total - c0);
-                        for (int k = tid; k < np; k += GW_THREADS) {
-                            int pos = c0 + k;
-                            int lo = 0, hi = nl0 - 1;
-                            while (lo < hi) {
-                                int mid = (lo + hi + 1) >> 1;
-                                if (S.leafoff[mid] <= pos) lo = mid;
-                                else hi = mid - 1;
-                            }
-                            int j = p.na[S.leaf[lo]].x + (pos - S.leafoff[lo]);
-                            float ej = p.eps[j];
-                            S.jp[k] = make_float4(grid_off(p.cx[j], gref[0], p.rx[j], unit),
-                                                  grid_off(p.cy[j], gref[1], p.ry[j], unit),
-                                                  grid_off(p.cz[j], gref[2], p.rz[j], unit), p.m[j]);
-                            S.je[k] = ej * ej;
-                        }
-                        __syncthreads();
-                        if (ivalid) pp_loop<MASK>(S, np, split, js, xi, yi, zi, e2i, ax, ay, az, ph);
-                        __syncthreads();
-                    }
-                    cnt_pp += (unsigned long long)total * icnt;
-                    if (tid == 0) S.nl = 0;
                 }
-                __syncthreads();
-                if (sp == 0) break;
-                // pop k nodes; children pushed never exceed the stack
-                int k = min(GW_THREADS, sp);
-                int room = (GW_STACK - sp) / 7;
-                if (room < 1) room = 1;
-                k = min(k, room);
-                int node = tid < k ? S.stack[sp - k + tid] : -1;
-                __syncthreads();
-                if (tid == 0) S.sp = sp - k;
-                __syncthreads();
-                if (node >= 0) {
-                    int4 a = p.na[node];
-                    int nch = a.w >> 8, lev = a.w & 255;
-                    bool open = node == 0 || must_open(p.nb[node], lev, bmin, bmax, p.theta2);
-                    if (!open) {
-                        int slot = atomicAdd(&S.nc, 1);
-                        int4 C = p.nb[node];
-                        float4 m0 = p.mo0[node];
-                        S.c0[slot] = make_float4(grid_off(C.x, gref[0], m0.x, unit), grid_off(C.y, gref[1], m0.y, unit),
-                                                 grid_off(C.z, gref[2], m0.z, unit), m0.w);
-                        S.c1[slot] = p.mo1[node];
-                        S.c2[slot] = p.mo2[node];
-                    } else if (nch == 0) {
-                        int slot = atomicAdd(&S.nl, 1);
-                        S.leaf[slot] = node;
-                    } else {
-                        int b = atomicAdd(&S.sp, nch);
-                        if (b + nch <= GW_STACK) {
-                            for (int q = 0; q < nch; q++) S.stack[b + q] = a.z + q;
-                        } else {
-                            atomicOr(p.status, ST_STACK_OVERFLOW);
-                            atomicSub(&S.sp, nch);
+                while (ch >= 0) {
+                    const int nc = p.ccnt[ch];
+                    int nxt2 = -1, idx2[2] = {0, 0};
+                    if (nxt >= 0) {
+                        cells_issue(S, p, b ^ 1, idx);
+                        nxt2 = p.cnext[nxt];
+                        if (nxt2 >= 0) {
+                            idx2[0] = p.pool[(size_t)nxt2 * GL_CH + tid];
+                            idx2[1] = p.pool[(size_t)nxt2 * GL_CH + tid + GW_THREADS];
                         }
                     }
+                    if (ivalid) pc_loop<QUAD>(S, b, nc, split, js, xi, yi, zi, e2i, ax, ay, az, ph);
+                    if (nxt >= 0) {
+                        cp_async_wait_all_g();
+                        cells_convert(S, b ^ 1, gref, unit);
+                    }
+                    __syncthreads();  // buffer b evaluated by all; buffer b ^ 1 converted by all
+                    ch = nxt;
+                    nxt = nxt2;
+                    idx[0] = idx2[0];
+                    idx[1] = idx2[1];
+                    b ^= 1;
                 }
             }
+            // opened leaves, one chunk at a time: particle offsets by a scan of
+            // the leaf counts, then sub-chunks of GW_JP particles
+            for (int ch = gh.y; ch >= 0;) {
+                const int nl = p.ccnt[ch];
+                int total = 0;
+                for (int q0 = 0; q0 < nl; q0 += GW_THREADS) {
+                    const int q = q0 + tid;
+                    int leaf = -1, v = 0;
+                    if (q < nl) {
+                        leaf = p.pool[(size_t)ch * GL_CH + q];
+                        v = p.na[leaf].y;
+                        S.leaf[q] = leaf;
+                    }
+                    int tot;
+                    const int e = block_scan_excl(v, S.ws, &tot);
+                    if (q < nl) S.leafoff[q] = total + e;
+                    total += tot;
+                }
+                if (tid == 0) S.leafoff[nl] = total;
+                __syncthreads();
+                for (int c0 = 0; c0 < total; c0 += GW_JP) {
+                    const int np = min(GW_JP, total - c0);
+                    for (int k = tid; k < np; k += GW_THREADS) {
+                        const int pos = c0 + k;
+                        int lo = 0, hi = nl - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (S.leafoff[mid] <= pos) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        const int j = p.na[S.leaf[lo]].x + (pos - S.leafoff[lo]);
+                        const float ej = p.eps[j];
+                        S.jp[k] = make_float4(grid_off(p.cx[j], gref[0], p.rx[j], unit),
+                                              grid_off(p.cy[j], gref[1], p.ry[j], unit),
+                                              grid_off(p.cz[j], gref[2], p.rz[j], unit), p.m[j]);
+                        S.je[k] = ej * ej;
+                    }
+                    __syncthreads();
+                    if (ivalid) pp_loop<MASK>(S, np, split, js, xi, yi, zi, e2i, ax, ay, az, ph);
+                    __syncthreads();
+                }
+                ch = p.cnext[ch];
+            }
             // reduce j-splits
-            __syncthreads();
             S.red[tid] = make_float4(ax, ay, az, ph);
             __syncthreads();
             if (split == 0 && ivalid) {
                 for (int s2 = 1; s2 < js; s2++) {
-                    float4 r = S.red[tid + s2 * ilanes];
+                    const float4 r = S.red[tid + s2 * ilanes];
                     ax += r.x; ay += r.y; az += r.z; ph += r.w;
                 }
                 if (!MASK) ph -= p.m[ip] * rsqrtf(2.f * e2i);  // remove the j == i term
@@ -308,10 +488,6 @@ __global__ void __launch_bounds__(GW_THREADS, 4) k_gravity_tree(GravParams p)
             }
             __syncthreads();
         }
-    }
-    if (tid == 0) {
-        atomicAdd(&p.counters[0], cnt_pp);
-        atomicAdd(&p.counters[1], cnt_pc);
     }
 }
 
@@ -419,17 +595,73 @@ static int launch_persistent(gnb_ctx *c, K kern, GravParams p, int *next_d)
     return GNB_OK;
 }
 
+// Interaction-list pool: group arrays for the current tree, chunks for `chunks`.
+// The group count itself stays on the device (reading it would synchronise);
+// the tree's node count, known on the host after every build, bounds it.
+static int lists_alloc(gnb_ctx *c, int chunks)
+{
+    const int ng = std::max(c->t.nnodes, 1);
+    if (c->gl_gcap < ng) {
+        dfree(c, c->gl_head); dfree(c, c->gl_ref);
+        c->gl_head = nullptr; c->gl_ref = nullptr;
+        const int cap = ng + ng / 4 + 64;
+        GNB_TRY(dalloc(c, &c->gl_head, (size_t)cap));
+        GNB_TRY(dalloc(c, &c->gl_ref, (size_t)cap));
+        c->gl_gcap = cap;
+    }
+    if (c->gl_cap < chunks) {
+        dfree(c, c->gl_pool); dfree(c, c->gl_next); dfree(c, c->gl_cnt);
+        c->gl_pool = nullptr; c->gl_next = nullptr; c->gl_cnt = nullptr;
+        GNB_TRY(dalloc(c, &c->gl_pool, (size_t)chunks * GL_CH));
+        GNB_TRY(dalloc(c, &c->gl_next, (size_t)chunks));
+        GNB_TRY(dalloc(c, &c->gl_cnt, (size_t)chunks));
+        c->gl_cap = chunks;
+    }
+    if (!c->gl_top) GNB_TRY(dalloc(c, &c->gl_top, 1));
+    return GNB_OK;
+}
+
 int gravity_tree(gnb_ctx *c)
 {
-    GravParams p = make_params(c);
-    int *next_d = c->counters_d ? (int *)(c->counters_d + 6) : nullptr;
-    bool q = c->cfg.multipole != 0;
-    if (c->min_eps_zero) {
-        if (q) return launch_persistent(c, k_gravity_tree<true, true>, p, next_d);
-        return launch_persistent(c, k_gravity_tree<true, false>, p, next_d);
+    // first guess: two chunks per possible group (cells, leaves) plus 16 list
+    // entries per particle
+    const int want = 2 * c->t.nnodes + (int)((16 * (long long)c->n) / GL_CH) + 1024;
+    GNB_TRY(lists_alloc(c, std::max(c->gl_cap, want)));
+    int *next_d = (int *)(c->counters_d + 6);
+    for (int attempt = 0;; attempt++) {
+        GravParams p = make_params(c);
+        p.pool = c->gl_pool; p.cnext = c->gl_next; p.ccnt = c->gl_cnt; p.top = c->gl_top;
+        p.ghead = c->gl_head; p.gref = c->gl_ref; p.cap = c->gl_cap;
+        p.next = next_d;
+        cudaMemsetAsync(c->counters_d, 0, 2 * sizeof(unsigned long long), c->s);
+        cudaMemsetAsync(c->gl_top, 0, sizeof(int), c->s);
+        cudaMemsetAsync(next_d, 0, sizeof(int), c->s);
+        if (g_sms == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grav_walk, GL_WARPS * 32, 0);
+        gnb::counted(k_grav_walk)<<<g_sms * std::max(per_sm, 1), GL_WARPS * 32, 0, c->s>>>(p);
+        GNB_LAUNCH_CHECK(c, "tree walk");
+        // the pool must have held every list; otherwise grow it and walk again
+        GNB_TRY(cuda_check(c, cudaMemcpyAsync(&c->pinned_i[40], c->gl_top, sizeof(int), cudaMemcpyDeviceToHost, c->s),
+                           "list pool read"));
+        GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "list pool sync"));
+        const int used = c->pinned_i[40];
+        if (used <= c->gl_cap) {
+            const bool q = c->cfg.multipole != 0;
+            if (c->min_eps_zero) {
+                if (q) return launch_persistent(c, k_grav_eval<true, true>, p, next_d);
+                return launch_persistent(c, k_grav_eval<true, false>, p, next_d);
+            }
+            if (q) return launch_persistent(c, k_grav_eval<false, true>, p, next_d);
+            return launch_persistent(c, k_grav_eval<false, false>, p, next_d);
+        }
+        if (attempt >= 4) return fail(c, GNB_ECAPACITY, "interaction-list pool");
+        GNB_TRY(lists_alloc(c, used + used / 2 + 1024));
     }
-    if (q) return launch_persistent(c, k_gravity_tree<false, true>, p, next_d);
-    return launch_persistent(c, k_gravity_tree<false, false>, p, next_d);
 }
 
 int gravity_direct(gnb_ctx *c)
