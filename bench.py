@@ -311,6 +311,12 @@ def reduce_max(x, world, device=None):
     return float(t.item())
 
 
+def whole_job_value(units_per_rank, steps, world, tmax_ms):
+    """Units processed by all ranks per second, timed by the slowest rank
+    (weak scaling: every rank steps its own replica)."""
+    return units_per_rank * steps * world / (tmax_ms * 1e-3)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -375,7 +381,7 @@ def run_ours(args, world, rank, local):
     phases, calls, launches = ctx.phase_times(reset=True)
     ctx.set_timing(False)
     tmax = reduce_max(total_ms, world, dev)
-    value = n * args.steps * world / (tmax * 1e-3)
+    value = whole_job_value(n, args.steps, world, tmax)
     # dominant kernel: the gravity walk + PP/PC kernel
     g_calls = max(calls["GRAVITY"], 1)
     g_ms = phases["GRAVITY"] / g_calls

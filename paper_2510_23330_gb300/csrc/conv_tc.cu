@@ -559,7 +559,7 @@ int conv3_tc(const TcConv &c, int *err, cudaStream_t s)
     a.halo = pl.halo;
     a.off_w = pl.off_w;
     a.off_h = pl.off_h;
-    a.tx_bytes = (unsigned)(K / 8) * (unsigned)zh * ZSTRIDE;
+    a.tx_bytes = (unsigned)(K / 8) * (unsigned)zh * ZSTRIDE + c.tx_extra;
     a.tmem_cols = pl.tmem_cols;
     // kind::f16 instruction descriptor: FP32 accumulator (bit 4), BF16 A
     // (bits 7-9 = 1) and B (bits 10-12 = 1), both K-major, N >> 3 at bit 17,

@@ -25,6 +25,7 @@ struct TcConv {
     int O1;
     int relu;
     int B, D, H, W;
+    unsigned tx_extra;  // 0; > 0 only in the wait-timeout test (bytes the halo barrier expects beyond the loads)
 };
 
 struct TcPlan {

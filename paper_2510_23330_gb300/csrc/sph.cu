@@ -8,8 +8,12 @@
 // iterates a search until it converges; here one CTA per hydro-tree group
 // gathers every gas particle within a search radius R of the group into
 // shared memory, and each warp selects the neighbours of one particle:
-//   1. FP32 distances d (exact grid offsets, error |d - D| <= E, proven
-//      bound E = 2^-17 A^2 with A the largest offset in the group),
+//   1. FP32 distances d from FP32 offsets to the group's reference cell,
+//      with |d - D| <= E(D) = 2^-23 (4 sqrt(3) A' sqrt(D) + 5 D), A' = the
+//      largest offset in the group plus two grid units: each offset carries
+//      one rounding (<= 2^-24 A') plus the residual's (<= 2^-24 unit), the
+//      difference and the three fused multiply-adds one rounding each, and
+//      the factor 2 over the first-order bound covers the second-order terms,
 //   2. a 64-bin histogram and an in-bucket rank give the exact 64th smallest
 //      FP32 value t,
 //   3. entries with d < t - 2E are certainly neighbours, entries with
@@ -302,10 +306,10 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                 atomicMax(&S.amax, __float_as_uint(ox * ox + oy * oy + oz * oz));
             }
             __syncthreads();
-            const float A2 = __uint_as_float(S.amax) + 4.f * unit * unit;
-            const float E = A2 * 7.62939453125e-06f;  // 2^-17 A^2
+            // error bound of an FP32 d^2 near D (see the file comment)
+            const float EA = 6.92820323f * (sqrtf(__uint_as_float(S.amax)) + 2.f * unit);  // 4 sqrt(3) A'
             const float R2 = R * R;
-            const float thrR = R2 - E;
+            const float thrR = R2 - 1.1920929e-07f * (EA * sqrtf(R2) + 5.f * R2);
             for (int i = ga.x + w; i < ga.x + ga.y; i += KN_WARPS) {
                 const float xi = grid_off(p.gcx[i], gref[0], p.grx[i], unit);
                 const float yi = grid_off(p.gcy[i], gref[1], p.gry[i], unit);
@@ -388,6 +392,9 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                     continue;
                 }
                 t = __shfl_sync(0xffffffffu, t, __ffs(fb) - 1);
+                // the bound at a point just above the band's upper end (E << t)
+                const float tb = t * 1.0009765625f;
+                const float E = 1.1920929e-07f * (EA * sqrtf(tb) + 5.f * tb);
                 const float lo = t - 2.f * E, hi = t + 2.f * E;
                 // classify: sure members written directly, uncertain ones collected
                 int nS = 0;

@@ -493,6 +493,7 @@ struct gnb_unet {
     double *loss_d = nullptr;
     int *err_d = nullptr;        // device error word of the tcgen05 convolutions
     int conv_impl = GNB_CONV_AUTO;
+    unsigned tx_extra = 0;       // wait-timeout test only
     bool launch_failed = false;
     std::string err;
 };
@@ -644,6 +645,8 @@ int conv3_try_tc(gnb_unet *u, const bf16 *wtc, int N, int B, int D, const bf16 *
     c.w = wtc; c.bias = bias; c.N = N;
     c.out1 = out1; c.out2 = out2 ? out2 : out1; c.O1 = O1; c.relu = relu;
     c.B = B; c.D = D; c.H = D; c.W = D;
+    c.tx_extra = u->tx_extra;
+    u->tx_extra = 0;  // the wait-timeout test affects the first tensor-core launch only
     return conv3_tc(c, u->err_d, u->s);
 }
 
@@ -940,6 +943,18 @@ void gnb_unet_destroy(gnb_unet *u)
 }
 
 int64_t gnb_unet_num_params(const gnb_unet *u) { return u ? u->nparam : -1; }
+
+int gnb_unet_test_wait_timeout(gnb_unet *u)
+{
+    if (!u || u->conv_impl == GNB_CONV_MMA_SYNC) return GNB_EINVAL;
+    int rc = unet_alloc_acts(u, 1);
+    if (rc != GNB_OK) return rc;
+    cudaMemsetAsync(u->xin, 0, (size_t)vox(u, 0, 1) * 16 * 2, u->s);
+    u->tx_extra = 16;
+    rc = unet_forward(u, 1);
+    u->tx_extra = 0;
+    return unet_check(u, rc);
+}
 
 int gnb_unet_set_conv_impl(gnb_unet *u, int impl)
 {

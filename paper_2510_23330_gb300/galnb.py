@@ -121,6 +121,8 @@ def _declare(L):
         getattr(L, name).restype = C.c_int
     L.gnb_unet_set_conv_impl.argtypes = [_vp, C.c_int]
     L.gnb_unet_set_conv_impl.restype = C.c_int
+    L.gnb_unet_test_wait_timeout.argtypes = [_vp]
+    L.gnb_unet_test_wait_timeout.restype = C.c_int
     L.gnb_unet_forward.argtypes = [_vp, C.c_int, _vp, _vp, C.c_int]
     L.gnb_unet_forward.restype = C.c_int
     L.gnb_unet_train_step.argtypes = [_vp, C.c_int, _vp, _vp, C.c_double, C.POINTER(C.c_double), C.c_int]
@@ -236,6 +238,10 @@ def gnb_unet_num_params(net):
 
 def gnb_unet_set_conv_impl(net, impl):
     return lib().gnb_unet_set_conv_impl(net, impl)
+
+
+def gnb_unet_test_wait_timeout(net):
+    return lib().gnb_unet_test_wait_timeout(net)
 
 
 def gnb_unet_get_params(net, dst, on_device):

@@ -105,3 +105,14 @@ def test_training_lowers_loss(G):
     for _ in range(60):
         l1 = net.train_step(x.astype(np.float32), t.astype(np.float32), 1e-3)
     assert l1 < 0.5 * l0
+
+
+def test_bounded_wait_timeout_reports_and_recovers(G):
+    """The tensor-core convolution's bounded waits: a forward pass whose halo
+    barriers can never complete returns GNB_ETIMEOUT after the 1 s limits,
+    and the same network then computes the oracle's result again."""
+    spec, p, x, net = _setup(G, 16, 1)
+    assert G.gnb_unet_test_wait_timeout(net.h) == G.GNB_ETIMEOUT
+    y = net.forward(x.astype(np.float32))
+    ref, _ = U.forward(p, x, bf=True)
+    assert rel_l2(y, ref) < 1e-2
