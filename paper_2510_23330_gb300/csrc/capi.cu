@@ -271,7 +271,7 @@ void gnb_destroy(gnb_ctx *c)
     free_gas(c);
     void *all[] = {c->status_d, c->n_d, c->ngas_d, c->counters_d, c->work_d, c->box_d, c->mm_d, c->red_d,
                    c->rs_total, c->rtot_d, c->scan_part, c->scan_poff, c->gl_pool, c->gl_next, c->gl_cnt,
-                   c->gl_top, c->gl_head, c->gl_ref};
+                   c->gl_top, c->gl_head, c->gl_ref, c->gl_lcum};
     for (void *q : all) dfree(c, q);
     if (c->pinned_i) cudaFreeHost(c->pinned_i);
     {

@@ -181,7 +181,7 @@ struct gnb_ctx {
     int *work_d = nullptr;                     // work counters of persistent kernels [8]
     int *scan_part = nullptr, *scan_poff = nullptr;  // device_scan scratch [1100]
     // tree-gravity interaction lists (gravity.cu): chunk pool and per-group heads
-    int *gl_pool = nullptr, *gl_next = nullptr, *gl_cnt = nullptr, *gl_top = nullptr;
+    int *gl_pool = nullptr, *gl_next = nullptr, *gl_cnt = nullptr, *gl_top = nullptr, *gl_lcum = nullptr;
     int4 *gl_head = nullptr, *gl_ref = nullptr;
     int gl_cap = 0, gl_gcap = 0;
     int *pinned_i = nullptr;                   // pinned host scratch [64]

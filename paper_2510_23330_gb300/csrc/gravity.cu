@@ -48,6 +48,7 @@ struct GravParams {
     unsigned long long *counters;
     // interaction-list pool (tree walk -> evaluation)
     int *pool, *cnext, *ccnt, *top;
+    int *lcum;     // leaf chains: offset of each leaf's first particle in the group's leaf-particle list
     int4 *ghead;   // per group: {cell chain head, leaf chain head, particles in opened leaves, -}
     int4 *gref;    // per group: reference grid cell {x, y, z, -}
     int cap;       // pool chunks
@@ -264,6 +265,51 @@ __device__ __forceinline__ void cells_convert(GravSmem &S, int b, const int *gre
     }
 }
 
+// Leaf variant of chain_append: the entry is the leaf's first particle and
+// lcum receives the leaf's offset in the group's concatenated leaf particles.
+__device__ __forceinline__ void chain_append_leaf(bool flag, int first, int count, int &npart, int &cur, int &cnt,
+                                                  const GravParams &p, int lane)
+{
+    const unsigned b = __ballot_sync(0xffffffffu, flag);
+    if (!b) return;
+    int inc = flag ? count : 0;  // inclusive scan of the counts over the appending lanes
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const int off = npart + inc - (flag ? count : 0);
+    npart += __shfl_sync(0xffffffffu, inc, 31);
+    const int n = __popc(b), pre = __popc(b & ((1u << lane) - 1u));
+    const bool spill = cnt + n > GL_CH;
+    int nxt = -1;
+    if (spill) {
+        if (lane == 0) {
+            if (cur >= 0) {
+                nxt = atomicAdd(p.top, 1);
+                if (nxt >= p.cap) nxt = -1;
+                p.cnext[cur] = nxt;
+                p.ccnt[cur] = GL_CH;
+            }
+        }
+        nxt = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+    const int pos = cnt + pre;
+    if (flag) {
+        size_t slot = (size_t)-1;
+        if (pos < GL_CH) {
+            if (cur >= 0) slot = (size_t)cur * GL_CH + pos;
+        } else if (nxt >= 0) {
+            slot = (size_t)nxt * GL_CH + pos - GL_CH;
+        }
+        if (slot != (size_t)-1) {
+            p.pool[slot] = first;
+            p.lcum[slot] = off;
+        }
+    }
+    if (spill) { cur = nxt; cnt = cnt + n - GL_CH; }
+    else cnt += n;
+}
+
 // Tree walk of one group per warp (see the file comment).
 __global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
 {
@@ -307,13 +353,13 @@ __global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
             __syncwarp();
             sp -= k;
             bool is_cell = false, is_leaf = false;
-            int nch = 0, child0 = 0, lcount = 0;
+            int nch = 0, child0 = 0, lcount = 0, lfirst = 0;
             if (node >= 0) {
                 const int4 a = __ldg(&p.na[node]);
                 const int lev = a.w & 255;
                 const bool open = node == 0 || must_open(__ldg(&p.nb[node]), lev, bmin, bmax, p.theta2);
                 if (!open) is_cell = true;
-                else if ((a.w >> 8) == 0) { is_leaf = true; lcount = a.y; }
+                else if ((a.w >> 8) == 0) { is_leaf = true; lcount = a.y; lfirst = a.x; }
                 else { nch = a.w >> 8; child0 = a.z; }
             }
             // push children (inclusive scan of the child counts over the warp)
@@ -331,11 +377,8 @@ __global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
             sp = min(sp + tot, GL_STACK);
             __syncwarp();
             chain_append(is_cell, node, ccur, ccnt, p, lane);
-            chain_append(is_leaf, node, lcur, lcnt, p, lane);
+            chain_append_leaf(is_leaf, lfirst, lcount, npart, lcur, lcnt, p, lane);
             ncell += __popc(__ballot_sync(0xffffffffu, is_cell));
-            int lp = lcount;
-            for (int o = 16; o > 0; o >>= 1) lp += __shfl_xor_sync(0xffffffffu, lp, o);
-            npart += lp;
         }
         chain_close(p, ccur, ccnt, lane);
         chain_close(p, lcur, lcnt, lane);
@@ -388,64 +431,35 @@ __global__ void __launch_bounds__(GW_THREADS, 4) k_grav_eval(GravParams p)
             float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
             // accepted cells, one chunk at a time, double buffered: while a
             // chunk is evaluated, cp.async fills the other buffer with the
-            // next chunk (whose node indices were loaded one chunk earlier)
-            {
-                int ch = gh.x, b = 0;
-                int idx[2] = {0, 0}, nxt = -1;
-                if (ch >= 0) {
-                    idx[0] = p.pool[(size_t)ch * GL_CH + tid];
-                    idx[1] = p.pool[(size_t)ch * GL_CH + tid + GW_THREADS];
-                    cells_issue(S, p, 0, idx);
-                    nxt = p.cnext[ch];
-                    if (nxt >= 0) {
-                        idx[0] = p.pool[(size_t)nxt * GL_CH + tid];
-                        idx[1] = p.pool[(size_t)nxt * GL_CH + tid + GW_THREADS];
-                    }
-                    cp_async_wait_all_g();
-                    cells_convert(S, 0, gref, unit);
-                    __syncthreads();
-                }
-                while (ch >= 0) {
-                    const int nc = p.ccnt[ch];
-                    int nxt2 = -1, idx2[2] = {0, 0};
-                    if (nxt >= 0) {
-                        cells_issue(S, p, b ^ 1, idx);
-                        nxt2 = p.cnext[nxt];
-                        if (nxt2 >= 0) {
-                            idx2[0] = p.pool[(size_t)nxt2 * GL_CH + tid];
-                            idx2[1] = p.pool[(size_t)nxt2 * GL_CH + tid + GW_THREADS];
-                        }
-                    }
-                    if (ivalid) pc_loop<QUAD>(S, b, nc, split, js, xi, yi, zi, e2i, ax, ay, az, ph);
-                    if (nxt >= 0) {
-                        cp_async_wait_all_g();
-                        cells_convert(S, b ^ 1, gref, unit);
-                    }
-                    __syncthreads();  // buffer b evaluated by all; buffer b ^ 1 converted by all
-                    ch = nxt;
-                    nxt = nxt2;
-                    idx[0] = idx2[0];
-                    idx[1] = idx2[1];
-                    b ^= 1;
+            // next chunk (whose node indices were loaded one chunk earlier).
+            // The first chunk's copy is issued here and lands while the
+            // opened leaves below are evaluated.
+            int ch = gh.x, cb = 0;
+            int idx[2] = {0, 0}, cnx = -1;
+            if (ch >= 0) {
+                idx[0] = p.pool[(size_t)ch * GL_CH + tid];
+                idx[1] = p.pool[(size_t)ch * GL_CH + tid + GW_THREADS];
+                cells_issue(S, p, 0, idx);
+                cnx = p.cnext[ch];
+                if (cnx >= 0) {
+                    idx[0] = p.pool[(size_t)cnx * GL_CH + tid];
+                    idx[1] = p.pool[(size_t)cnx * GL_CH + tid + GW_THREADS];
                 }
             }
-            // opened leaves, one chunk at a time: particle offsets by a scan of
-            // the leaf counts, then sub-chunks of GW_JP particles
-            for (int ch = gh.y; ch >= 0;) {
-                const int nl = p.ccnt[ch];
-                int total = 0;
-                for (int q0 = 0; q0 < nl; q0 += GW_THREADS) {
-                    const int q = q0 + tid;
-                    int leaf = -1, v = 0;
-                    if (q < nl) {
-                        leaf = p.pool[(size_t)ch * GL_CH + q];
-                        v = p.na[leaf].y;
-                        S.leaf[q] = leaf;
-                    }
-                    int tot;
-                    const int e = block_scan_excl(v, S.ws, &tot);
-                    if (q < nl) S.leafoff[q] = total + e;
-                    total += tot;
+            // opened leaves, one chunk at a time: each entry holds the leaf's
+            // first particle and its offset in the group's leaf particles (from
+            // the walk), so particles are staged in batches of GW_JP without a
+            // scan or a node lookup
+            for (int lch = gh.y; lch >= 0;) {
+                const int nl = p.ccnt[lch];
+                const int lnx = p.cnext[lch];
+                // only a chain's head chunk can be empty (a group with no opened leaf)
+                const int base = nl > 0 ? p.lcum[(size_t)lch * GL_CH] : 0;
+                const int end = lnx >= 0 ? p.lcum[(size_t)lnx * GL_CH] : gh.z;
+                const int total = nl > 0 ? end - base : 0;
+                for (int q = tid; q < nl; q += GW_THREADS) {
+                    S.leaf[q] = p.pool[(size_t)lch * GL_CH + q];
+                    S.leafoff[q] = p.lcum[(size_t)lch * GL_CH + q] - base;
                 }
                 if (tid == 0) S.leafoff[nl] = total;
                 __syncthreads();
@@ -453,13 +467,13 @@ __global__ void __launch_bounds__(GW_THREADS, 4) k_grav_eval(GravParams p)
                     const int np = min(GW_JP, total - c0);
                     for (int k = tid; k < np; k += GW_THREADS) {
                         const int pos = c0 + k;
-                        int lo = 0, hi = nl - 1;
+                        int lo = 0, hi = nl - 1;  // the leaf holding position pos
                         while (lo < hi) {
                             const int mid = (lo + hi + 1) >> 1;
                             if (S.leafoff[mid] <= pos) lo = mid;
                             else hi = mid - 1;
                         }
-                        const int j = p.na[S.leaf[lo]].x + (pos - S.leafoff[lo]);
+                        const int j = S.leaf[lo] + (pos - S.leafoff[lo]);
                         const float ej = p.eps[j];
                         S.jp[k] = make_float4(grid_off(p.cx[j], gref[0], p.rx[j], unit),
                                               grid_off(p.cy[j], gref[1], p.ry[j], unit),
@@ -470,7 +484,35 @@ __global__ void __launch_bounds__(GW_THREADS, 4) k_grav_eval(GravParams p)
                     if (ivalid) pp_loop<MASK>(S, np, split, js, xi, yi, zi, e2i, ax, ay, az, ph);
                     __syncthreads();
                 }
-                ch = p.cnext[ch];
+                lch = lnx;
+            }
+            if (ch >= 0) {
+                cp_async_wait_all_g();
+                cells_convert(S, 0, gref, unit);
+                __syncthreads();
+            }
+            while (ch >= 0) {
+                const int nc = p.ccnt[ch];
+                int nxt2 = -1, idx2[2] = {0, 0};
+                if (cnx >= 0) {
+                    cells_issue(S, p, cb ^ 1, idx);
+                    nxt2 = p.cnext[cnx];
+                    if (nxt2 >= 0) {
+                        idx2[0] = p.pool[(size_t)nxt2 * GL_CH + tid];
+                        idx2[1] = p.pool[(size_t)nxt2 * GL_CH + tid + GW_THREADS];
+                    }
+                }
+                if (ivalid) pc_loop<QUAD>(S, cb, nc, split, js, xi, yi, zi, e2i, ax, ay, az, ph);
+                if (cnx >= 0) {
+                    cp_async_wait_all_g();
+                    cells_convert(S, cb ^ 1, gref, unit);
+                }
+                __syncthreads();  // buffer cb evaluated by all; buffer cb ^ 1 converted by all
+                ch = cnx;
+                cnx = nxt2;
+                idx[0] = idx2[0];
+                idx[1] = idx2[1];
+                cb ^= 1;
             }
             // reduce j-splits
             S.red[tid] = make_float4(ax, ay, az, ph);
@@ -610,9 +652,10 @@ static int lists_alloc(gnb_ctx *c, int chunks)
         c->gl_gcap = cap;
     }
     if (c->gl_cap < chunks) {
-        dfree(c, c->gl_pool); dfree(c, c->gl_next); dfree(c, c->gl_cnt);
-        c->gl_pool = nullptr; c->gl_next = nullptr; c->gl_cnt = nullptr;
+        dfree(c, c->gl_pool); dfree(c, c->gl_next); dfree(c, c->gl_cnt); dfree(c, c->gl_lcum);
+        c->gl_pool = nullptr; c->gl_next = nullptr; c->gl_cnt = nullptr; c->gl_lcum = nullptr;
         GNB_TRY(dalloc(c, &c->gl_pool, (size_t)chunks * GL_CH));
+        GNB_TRY(dalloc(c, &c->gl_lcum, (size_t)chunks * GL_CH));
         GNB_TRY(dalloc(c, &c->gl_next, (size_t)chunks));
         GNB_TRY(dalloc(c, &c->gl_cnt, (size_t)chunks));
         c->gl_cap = chunks;
@@ -630,7 +673,7 @@ int gravity_tree(gnb_ctx *c)
     int *next_d = (int *)(c->counters_d + 6);
     for (int attempt = 0;; attempt++) {
         GravParams p = make_params(c);
-        p.pool = c->gl_pool; p.cnext = c->gl_next; p.ccnt = c->gl_cnt; p.top = c->gl_top;
+        p.pool = c->gl_pool; p.cnext = c->gl_next; p.ccnt = c->gl_cnt; p.top = c->gl_top; p.lcum = c->gl_lcum;
         p.ghead = c->gl_head; p.gref = c->gl_ref; p.cap = c->gl_cap;
         p.next = next_d;
         cudaMemsetAsync(c->counters_d, 0, 2 * sizeof(unsigned long long), c->s);
