@@ -63,6 +63,8 @@ struct TcArgs {
     int B, D, H, W;
     int Zt, nbuf, tx, ty, tz;
     int wstages;  // 0: all 27 taps resident; else a ring of this many one-tap stages
+    int dzn;      // 1: the three z-taps share one MMA (N = 3 N_out, sliding TMEM windows)
+    unsigned acc_cols;  // TMEM columns of one accumulator buffer
     long long ntiles;
     unsigned wbytes, plane, halo, off_w, off_h, tx_bytes, tmem_cols, idesc;
     int *err;
@@ -140,14 +142,21 @@ __device__ __forceinline__ void bulk_load(unsigned dst, const void *src, unsigne
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
+// Shared-memory matrix descriptors, canonical K-major layout without swizzle:
 // start address, leading-dimension byte offset (between core matrices along
 // K), stride-dimension byte offset (between 8-row groups along M or N), and
-// the descriptor version bit 46.
-__device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo, unsigned sbo)
+// the descriptor version bit 46.  The low 32-bit word holds the start address
+// in 16-byte units (bits 0-13) and the leading offset (bits 16-29), so moving
+// the start by a multiple of 16 bytes is one add on the low word; the high
+// word holds the stride offset and the version bit.
+__device__ __forceinline__ unsigned sdesc_lo(unsigned addr, unsigned lbo)
 {
-    return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)(lbo >> 4) << 16) |
-           ((unsigned long long)(sbo >> 4) << 32) | (1ull << 46);
+    return ((addr & 0x3FFFFu) >> 4) | ((lbo >> 4) << 16);
+}
+__device__ __forceinline__ unsigned sdesc_hi(unsigned sbo) { return (sbo >> 4) | (1u << 14); }
+__device__ __forceinline__ unsigned long long dpair(unsigned lo, unsigned hi)
+{
+    return ((unsigned long long)hi << 32) | lo;
 }
 
 // MMA and commit are executed by the whole warp in uniform control flow (so
@@ -186,7 +195,19 @@ __device__ __forceinline__ void tc_ld16(unsigned taddr, float *v)
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void decode_tile(const TcArgs &p, long long t, int &bb, int &z0, int &y0, int &x0)
+// Zeros 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tc_st16_zero(unsigned taddr)
+{
+    const unsigned z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1};\n" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+__device__ __forceinline__ void decode_tile(const TcArgs &p, int Zt, long long t, int &bb, int &z0, int &y0, int &x0)
 {
     int xt = (int)(t % p.tx);
     t /= p.tx;
@@ -196,12 +217,51 @@ __device__ __forceinline__ void decode_tile(const TcArgs &p, long long t, int &b
     bb = (int)(t / p.tz);
     x0 = 8 * xt;
     y0 = 16 * yt;
-    z0 = p.Zt * zt;
+    z0 = Zt * zt;
 }
 
+// The MMAs of one dz-in-N tile.  Input plane j, in-plane tap (ty, tx): one
+// MMA of N = 3 N_out whose column window [j N, (j + 3) N) holds output planes
+// j - 2, j - 1, j (z-taps 2, 1, 0); every MMA accumulates.  Windows of planes
+// j = r, r + 3, ... are disjoint, so issuing them back to back keeps several
+// accumulations in flight instead of a chain of dependent MMAs.  With the
+// tile depth and K / 16 known at compile time the loop nest is straight-line
+// code: a small-N MMA takes only ~40 cycles of the tensor core, and a loop
+// with run-time bounds spends about twice that per MMA on issue.
+template <int ZT, int NKS>
+__device__ __forceinline__ void issue_dzn(const TcArgs &p, unsigned alo0, unsigned sW, unsigned d0)
+{
+    const int Zt = ZT ? ZT : p.Zt, nks = NKS ? NKS : (p.K >> 4);
+    const unsigned ahi = sdesc_hi(YSTRIDE), bhi = sdesc_hi(128u);
+    const unsigned zs4 = ZSTRIDE >> 4, pl4 = (2u * p.plane) >> 4;
+    const unsigned n3 = 3u * (unsigned)p.N;
+    const unsigned wyx4 = ((unsigned)nks * 2u * n3 * 16u) >> 4;  // one (ty, tx) slice of weights
+    const unsigned bk4 = (2u * n3 * 16u) >> 4;
+    const unsigned blo0 = sdesc_lo(sW, n3 * 16u);
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int yx = 0; yx < 9; yx++) {
+            const unsigned aoff = ((unsigned)(yx / 3) * YSTRIDE + (unsigned)(yx % 3) * ROW_BYTES) >> 4;
+#pragma unroll
+            for (int ks = 0; ks < nks; ks++) {
+                const unsigned long long bd = dpair(blo0 + (unsigned)yx * wyx4 + (unsigned)ks * bk4, bhi);
+#pragma unroll
+                for (int j = r; j < Zt + 2; j += 3)
+                    tc_mma_elect(d0 + (unsigned)(j * p.N), dpair(alo0 + aoff + (unsigned)ks * pl4 + (unsigned)j * zs4, ahi),
+                                 bd, p.idesc, 1u);
+            }
+        }
+}
+
+// DZ: 1 dz-in-N, 0 plain, -1 read from p; ZT: tile depth (0: read from p);
+// NKS: K / 16 (0: read from p).
+template <int DZ, int ZT, int NKS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_conv3_tc(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2, const TcArgs p)
 {
+    const int Zt = ZT ? ZT : p.Zt;
+    const bool dzn = DZ >= 0 ? DZ != 0 : p.dzn != 0;
     extern __shared__ unsigned char dsm[];
     const unsigned raw = smem_u32(dsm);
     const unsigned sb = (raw + (ALIGN_SLACK - 1)) & ~(ALIGN_SLACK - 1);
@@ -239,6 +299,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const unsigned tmem = *slot;
     const int kc8 = p.K >> 3;
+    if (dzn) {
+        // the sliding accumulator windows start from zero: the epilogue warps
+        // clear both buffers here and each buffer again after reading it
+        if (warp < 4) {
+            for (unsigned c = 0; c < (unsigned)p.nbuf * p.acc_cols; c += 16)
+                tc_st16_zero(tmem + ((unsigned)(32 * warp) << 16) + c);
+            tc_wait_st();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
 
     if (warp == 4) {
         if (lane == 0) {
@@ -260,7 +332,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const unsigned k = (unsigned)(i / p.nbuf);
                 if (k > 0 && !mb_wait(bar(B_HE + b), (k - 1) & 1u, abort_flag, p.err, 1)) break;
                 int bb, z0, y0, x0;
-                decode_tile(p, t, bb, z0, y0, x0);
+                decode_tile(p, Zt, t, bb, z0, y0, x0);
                 mb_expect_tx(bar(B_HF + b), p.tx_bytes);
                 const unsigned dst = sH + (unsigned)b * p.halo;
                 // x and the 8 channels of a group form the innermost TMA
@@ -322,11 +394,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
                 const unsigned hb = sH + (unsigned)b * p.halo;
-                const unsigned d0 = tmem + (unsigned)(b * p.Zt * p.N);
+                const unsigned d0 = tmem + (unsigned)b * p.acc_cols;
                 bool stop = false;
-                for (int tap = 0; tap < 27; tap++) {
+                // descriptors are stepped as 32-bit low words (start address in
+                // 16-byte units): a few adds per MMA
+                const unsigned ahi = sdesc_hi(YSTRIDE), bhi = sdesc_hi(128u);
+                const unsigned alo0 = sdesc_lo(hb, p.plane);
+                const unsigned zs4 = ZSTRIDE >> 4, pl4 = (2u * p.plane) >> 4;
+                if (dzn) issue_dzn<ZT, NKS>(p, alo0, sW, d0);
+                const unsigned nb4 = (2u * (unsigned)p.N * 16u) >> 4;  // two channel groups of weights
+                for (int tap = 0; !dzn && tap < 27; tap++) {
                     const int tz = tap / 9, ty = (tap / 3) % 3, tx = tap % 3;
-                    const unsigned a0 = hb + (unsigned)tz * ZSTRIDE + (unsigned)ty * YSTRIDE + (unsigned)tx * ROW_BYTES;
+                    unsigned alo = alo0 + (((unsigned)tz * ZSTRIDE + (unsigned)ty * YSTRIDE + (unsigned)tx * ROW_BYTES) >> 4);
                     unsigned w0 = sW + (unsigned)tap * wtap;
                     int st = 0;
                     if (p.wstages) {
@@ -336,14 +415,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         tc_fence_after();
                         w0 = sW + (unsigned)st * wtap;
                     }
-                    for (int ks = 0; ks < (p.K >> 4); ks++) {
-                        const unsigned long long bd = sdesc(w0 + 2u * ks * nbytes16, nbytes16, 128u);
+                    unsigned blo = sdesc_lo(w0, nbytes16);
+                    for (int ks = 0; ks < (p.K >> 4); ks++, alo += pl4, blo += nb4) {
+                        const unsigned long long bd = dpair(blo, bhi);
                         const unsigned acc = (tap | ks) != 0;
-                        for (int zz = 0; zz < p.Zt; zz++) {
-                            const unsigned long long ad =
-                                sdesc(a0 + (unsigned)zz * ZSTRIDE + 2u * ks * p.plane, p.plane, YSTRIDE);
-                            tc_mma_elect(d0 + (unsigned)(zz * p.N), ad, bd, p.idesc, acc);
-                        }
+#pragma unroll
+                        for (int zz = 0; zz < Zt; zz++)
+                            tc_mma_elect(d0 + (unsigned)(zz * p.N), dpair(alo + (unsigned)zz * zs4, ahi), bd, p.idesc, acc);
                     }
                     if (p.wstages) {
                         tc_commit_elect(bar(B_WE + st));  // the stage is free once these MMAs complete
@@ -373,16 +451,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (!ok) break;
             tc_fence_after();
             int bb, z0, y0, x0;
-            decode_tile(p, t, bb, z0, y0, x0);
+            decode_tile(p, Zt, t, bb, z0, y0, x0);
             const int x = x0 + (r & 7), y = y0 + (r >> 3);
-            for (int zz = 0; zz < p.Zt; zz++) {
+            for (int zz = 0; zz < Zt; zz++) {
                 const int z = z0 + zz;
                 const bool valid = x < p.W && y < p.H && z < p.D;
                 const long long sv = ((long long)z * p.H + y) * p.W + x;
                 for (int c0 = 0; c0 < p.N; c0 += 16) {
                     float f[16];
                     __syncwarp();
-                    tc_ld16(tmem + lane_addr + (unsigned)((b * p.Zt + zz) * p.N + c0), f);
+                    tc_ld16(tmem + lane_addr + (unsigned)b * p.acc_cols + (unsigned)((zz + (dzn ? 2 : 0)) * p.N + c0),
+                            f);
                     if (!valid) continue;
                     if (p.bias) {
 #pragma unroll
@@ -406,6 +485,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     *reinterpret_cast<uint4 *>(dst) = o[0];
                     *reinterpret_cast<uint4 *>(dst + Vs * 8) = o[1];
                 }
+            }
+            if (dzn) {
+                __syncwarp();
+                for (unsigned c = 0; c < p.acc_cols; c += 16) tc_st16_zero(tmem + lane_addr + (unsigned)b * p.acc_cols + c);
+                tc_wait_st();
             }
             tc_fence_before();
             mb_arrive(bar(B_AE + b));
@@ -477,9 +561,52 @@ unsigned pow2_at_least(unsigned v)
 
 }  // namespace
 
+// z-taps in N for the thin layers, which are otherwise bound by the
+// shared-memory reads of A: when N <= 32 and the resident weights fit beside
+// two halo buffers of two-plane tiles.
+static bool dzn_fits(int N, int K, int zt, int nbuf, unsigned *smem, unsigned *cols, unsigned *plane,
+                     unsigned *halo, unsigned *off_h)
+{
+    const unsigned wbytes = 27u * (unsigned)N * (unsigned)K * 2u;
+    *plane = ((unsigned)(zt + 2) * ZSTRIDE + 127u) & ~127u;
+    *halo = (unsigned)(K / 8) * *plane;
+    *off_h = (HDR + wbytes + 127u) & ~127u;
+    *smem = ALIGN_SLACK + *off_h + (unsigned)nbuf * *halo;
+    const unsigned acc = (unsigned)((zt + 4) * N);
+    *cols = pow2_at_least((unsigned)nbuf * acc);
+    return *smem <= TC_SMEM_MAX && *cols <= 512;
+}
+
+bool conv3_tc_dzn(int N, int K)
+{
+    unsigned a, b, c, d, e;
+    return N >= 16 && N <= 32 && (N % 16) == 0 && K >= 16 && (K % 16) == 0 && dzn_fits(N, K, 2, 2, &a, &b, &c, &d, &e);
+}
+
 bool conv3_tc_plan(int N, int K, int D, TcPlan *pl)
 {
     if (N < 16 || N > 256 || (N % 16) || K < 16 || (K % 16)) return false;
+    if (conv3_tc_dzn(N, K)) {
+        static const int zd[] = {8, 4, 2};
+        const int nbuf = 2;
+        for (int zt : zd) {
+            if (zt > 2 && zt > D) continue;
+            unsigned smem, cols, plane, halo, off_h;
+            if (!dzn_fits(N, K, zt, nbuf, &smem, &cols, &plane, &halo, &off_h)) continue;
+            pl->Zt = zt;
+            pl->nbuf = nbuf;
+            pl->wstages = 0;
+            pl->dzn = 1;
+            pl->plane = plane;
+            pl->halo = halo;
+            pl->off_w = HDR;
+            pl->off_h = off_h;
+            pl->wbytes = 27u * (unsigned)N * (unsigned)K * 2u;
+            pl->smem = smem;
+            pl->tmem_cols = cols;
+            return true;
+        }
+    }
     const unsigned wtap = (unsigned)N * (unsigned)K * 2u;
     static const int zts[] = {4, 2, 1};
     // resident weights first; then a ring of 4, 3, 2 one-tap stages
@@ -499,6 +626,7 @@ bool conv3_tc_plan(int N, int K, int D, TcPlan *pl)
                 pl->Zt = zt;
                 pl->nbuf = nbuf;
                 pl->wstages = stages;
+                pl->dzn = 0;
                 pl->plane = plane;
                 pl->halo = halo;
                 pl->off_w = off_w;
@@ -511,6 +639,28 @@ bool conv3_tc_plan(int N, int K, int D, TcPlan *pl)
         }
     }
     return false;
+}
+
+using TcKernel = void (*)(const CUtensorMap, const CUtensorMap, const TcArgs);
+
+// The instantiations: the hot tile shapes with compile-time loop bounds, and
+// one run-time variant per mode for the rest.
+const TcKernel TC_KERNELS[] = {k_conv3_tc<1, 8, 1>, k_conv3_tc<1, 4, 1>, k_conv3_tc<1, 4, 2>, k_conv3_tc<1, 0, 0>,
+                               k_conv3_tc<0, 4, 0>, k_conv3_tc<0, 2, 0>, k_conv3_tc<0, 1, 0>, k_conv3_tc<0, 0, 0>};
+
+TcKernel pick_kernel(const TcPlan &pl, int K)
+{
+    const int nks = K >> 4;
+    if (pl.dzn) {
+        if (pl.Zt == 8 && nks == 1) return TC_KERNELS[0];
+        if (pl.Zt == 4 && nks == 1) return TC_KERNELS[1];
+        if (pl.Zt == 4 && nks == 2) return TC_KERNELS[2];
+        return TC_KERNELS[3];
+    }
+    if (pl.Zt == 4) return TC_KERNELS[4];
+    if (pl.Zt == 2) return TC_KERNELS[5];
+    if (pl.Zt == 1) return TC_KERNELS[6];
+    return TC_KERNELS[7];
 }
 
 int conv3_tc(const TcConv &c, int *err, cudaStream_t s)
@@ -533,7 +683,10 @@ int conv3_tc(const TcConv &c, int *err, cudaStream_t s)
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, []() {
-        attr_err = cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+        for (TcKernel k : TC_KERNELS) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+            if (e != cudaSuccess) attr_err = e;
+        }
     });
     if (attr_err != cudaSuccess) return -1;
     TcArgs a;
@@ -550,6 +703,8 @@ int conv3_tc(const TcConv &c, int *err, cudaStream_t s)
     a.Zt = pl.Zt;
     a.nbuf = pl.nbuf;
     a.wstages = pl.wstages;
+    a.dzn = pl.dzn;
+    a.acc_cols = (unsigned)((pl.dzn ? pl.Zt + 4 : pl.Zt) * N);
     a.tx = (c.W + 7) / 8;
     a.ty = (c.H + 15) / 16;
     a.tz = (c.D + pl.Zt - 1) / pl.Zt;
@@ -564,7 +719,8 @@ int conv3_tc(const TcConv &c, int *err, cudaStream_t s)
     // kind::f16 instruction descriptor: FP32 accumulator (bit 4), BF16 A
     // (bits 7-9 = 1) and B (bits 10-12 = 1), both K-major, N >> 3 at bit 17,
     // M >> 4 at bit 24 (M = 128).
-    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((128u >> 4) << 24);
+    const int nmma = pl.dzn ? 3 * N : N;
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(nmma >> 3) << 17) | ((128u >> 4) << 24);
     a.err = err;
     const int per_sm_smem = (int)(TC_SMEM_SM / (pl.smem + 1024u));
     const int per_sm_tmem = (int)(512u / pl.tmem_cols);
@@ -573,7 +729,7 @@ int conv3_tc(const TcConv &c, int *err, cudaStream_t s)
     long long grid = (long long)device_sms() * per_sm;
     if (grid > a.ntiles) grid = a.ntiles;
     if (grid < 1) return 1;
-    counted(k_conv3_tc)<<<(unsigned)grid, TC_THREADS, pl.smem, s>>>(m1, m2, a);
+    counted(pick_kernel(pl, K))<<<(unsigned)grid, TC_THREADS, pl.smem, s>>>(m1, m2, a);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -592,8 +748,31 @@ __global__ void k_pack_w_tc(const bf16 *__restrict__ src, int taps, int Npad, in
     dst[e] = src[((long long)t * Npad + n) * Kpad + 8 * kc + j];
 }
 
+// [27][Npad][Kpad] -> [9 (ty, tx)][Kpad / 8][3 Npad (z-taps 2, 1, 0)][8]
+__global__ void k_pack_w_tc_dzn(const bf16 *__restrict__ src, int Npad, int Kpad, bf16 *__restrict__ dst)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n3n = 3 * Npad;
+    long long tot = 27LL * Npad * Kpad;
+    if (e >= tot) return;
+    int j = (int)(e & 7);
+    long long q = e >> 3;
+    int n3 = (int)(q % n3n);
+    q /= n3n;
+    int kc = (int)(q % (Kpad / 8));
+    int yx = (int)(q / (Kpad / 8));
+    int tz = 2 - n3 / Npad, n = n3 % Npad;
+    int tap = 9 * tz + yx;
+    dst[e] = src[((long long)tap * Npad + n) * Kpad + 8 * kc + j];
+}
+
 int pack_w_tc(const bf16 *src, int taps, int Npad, int Kpad, bf16 *dst, cudaStream_t s)
 {
+    if (taps == 27 && conv3_tc_dzn(Npad, Kpad)) {
+        long long tot = 27LL * Npad * Kpad;
+        counted(k_pack_w_tc_dzn)<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, Npad, Kpad, dst);
+        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
     long long tot = (long long)taps * Npad * Kpad;
     counted(k_pack_w_tc)<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, taps, Npad, Kpad, dst);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -29,7 +29,7 @@ struct TcConv {
 };
 
 struct TcPlan {
-    int Zt, nbuf, wstages;
+    int Zt, nbuf, wstages, dzn;
     unsigned plane, halo, off_w, off_h, wbytes, smem, tmem_cols;
 };
 
@@ -47,8 +47,13 @@ bool conv3_tc_plan(int N, int K, int D, TcPlan *pl);
 // non-zero code into *err (device memory).
 int conv3_tc(const TcConv &c, int *err, cudaStream_t s);
 
+// Whether a 3^3 layer with N output and K input channels runs with its
+// three z-taps in one MMA (N <= 32; see conv_tc.cu).
+bool conv3_tc_dzn(int N, int K);
+
 // Re-layout of packed weights [taps][Npad][Kpad] into the tensor-core
-// layout [taps][Kpad / 8][Npad][8].
+// layout [taps][Kpad / 8][Npad][8], or, for the layers of conv3_tc_dzn,
+// [9 (y, x)-taps][Kpad / 8][3 Npad (z-taps 2, 1, 0)][8].
 int pack_w_tc(const __nv_bfloat16 *src, int taps, int Npad, int Kpad, __nv_bfloat16 *dst, cudaStream_t s);
 
 }  // namespace gnb
