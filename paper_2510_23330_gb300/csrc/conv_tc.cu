@@ -195,6 +195,20 @@ __device__ __forceinline__ void tc_ld16(unsigned taddr, float *v)
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// 8 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld8(unsigned taddr, float *v)
+{
+    unsigned r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+
 // Zeros 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
 __device__ __forceinline__ void tc_st16_zero(unsigned taddr)
 {
@@ -559,6 +573,131 @@ unsigned pow2_at_least(unsigned v)
     return c;
 }
 
+
+// ------------------------------------------------------------------ UP2
+// 2x2x2 transposed convolution with stride 2 on the tensor cores: one tile is
+// 128 consecutive coarse voxels of one batch entry (M = 128) and all eight
+// taps' output channels form N = 8 N_out, so a tile is K / 16 MMAs (split in
+// two when 8 N_out > 256).  In the blocked layout the 128 voxels of one
+// channel group are 2 KB of contiguous memory, i.e. exactly a column of
+// K-major core matrices; the tile and the weights arrive by bulk copies.
+struct Up2Args {
+    const bf16 *in;      // coarse [B][K / 8][Vc][8]
+    const bf16 *w;       // [K / 8][8 N][8], row t N + n = tap t, output channel n
+    const float *bias;   // [N] or null
+    bf16 *out;           // fine [B][N / 8][8 Vc][8]
+    int K, N, Dc;        // input channels, output channels, coarse grid edge
+    long long Vc, ntiles;
+    unsigned abytes, wbytes, tmem_cols, idesc, nsplit, ncols_split;
+    int *err;
+};
+constexpr unsigned UP_HDR = 256;
+
+__global__ void __launch_bounds__(128) k_up2_tc(const Up2Args p)
+{
+    extern __shared__ unsigned char dsm[];
+    const unsigned raw = smem_u32(dsm);
+    const unsigned sb = (raw + (ALIGN_SLACK - 1)) & ~(ALIGN_SLACK - 1);
+    unsigned char *gb = dsm + (sb - raw);
+    unsigned *slot = reinterpret_cast<unsigned *>(gb + 16);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gb + 20);
+    const unsigned bar_ld = sb, bar_mma = sb + 8;
+    const unsigned sA = sb + UP_HDR, sB = sA + p.abytes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long r0 = (long long)blockIdx.x * 128;
+    const long long bb = r0 / p.Vc, v0 = r0 - bb * p.Vc;
+    const int kc8 = p.K >> 3;
+    if (threadIdx.x == 0) {
+        mb_init(bar_ld, 1);
+        mb_init(bar_mma, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slot)),
+                     "r"(p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *slot;
+    if (threadIdx.x == 0) {
+        mb_expect_tx(bar_ld, p.abytes + p.wbytes);
+        for (int kc = 0; kc < kc8; kc++)
+            bulk_load(sA + (unsigned)kc * 2048u, p.in + ((bb * kc8 + kc) * p.Vc + v0) * 8, 2048u, bar_ld);
+        for (unsigned o = 0; o < p.wbytes; o += 32768u) {
+            unsigned n = p.wbytes - o < 32768u ? p.wbytes - o : 32768u;
+            bulk_load(sB + o, reinterpret_cast<const unsigned char *>(p.w) + o, n, bar_ld);
+        }
+    }
+    bool ok = true;
+    if (warp == 1) {
+        ok = __all_sync(0xffffffffu, mb_wait(bar_ld, 0, abort_flag, p.err, 11));
+        if (ok) {
+            tc_fence_after();
+            const unsigned ahi = sdesc_hi(128u), bhi = sdesc_hi(128u);
+            const unsigned nrow16 = (unsigned)(8 * p.N) * 16u;  // one channel group of all weight rows
+            for (int ks = 0; ks < (p.K >> 4); ks++)
+                for (unsigned h = 0; h < p.nsplit; h++)
+                    tc_mma_elect(tmem + h * p.ncols_split,
+                                 dpair(sdesc_lo(sA + (unsigned)ks * 4096u, 2048u), ahi),
+                                 dpair(sdesc_lo(sB + (unsigned)ks * 2u * nrow16 + h * p.ncols_split * 16u, nrow16), bhi),
+                                 p.idesc, ks != 0);
+            tc_commit_elect(bar_mma);
+        }
+    }
+    // every thread: the accumulators are ready (or the CTA gave up)
+    ok = mb_wait(bar_mma, 0, abort_flag, p.err, 12);
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) {
+        tc_fence_after();
+        const int r = 32 * warp + lane;
+        const unsigned lane_addr = (unsigned)(32 * warp) << 16;
+        const long long v = v0 + r;
+        const int D = p.Dc, x = (int)(v % D), y = (int)((v / D) % D), z = (int)(v / ((long long)D * D));
+        const long long Vf = 8 * p.Vc;
+        const int F = 2 * D;
+        // taps in pairs (dx = 0, 1): the two fine voxels are adjacent in x,
+        // so each channel group is one 32-byte store
+        for (int tp = 0; tp < 4; tp++) {
+            const int dz = tp >> 1, dy = tp & 1;
+            const long long fv = ((long long)(2 * z + dz) * F + (2 * y + dy)) * F + 2 * x;
+            for (int g = 0; g < (p.N >> 3); g++) {
+                float f0[16], f1[16];
+                // columns of tap (dz, dy, 0) and (dz, dy, 1): t N + 8 g + j
+                const unsigned c0 = (unsigned)((2 * tp) * p.N + 8 * g), c1 = c0 + (unsigned)p.N;
+                __syncwarp();
+                tc_ld8(tmem + lane_addr + c0, f0);
+                tc_ld8(tmem + lane_addr + c1, f1);
+                uint4 o[2];
+                unsigned *ou = reinterpret_cast<unsigned *>(o);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const float b0 = p.bias ? __ldg(p.bias + 8 * g + 2 * q) : 0.f;
+                    const float b1 = p.bias ? __ldg(p.bias + 8 * g + 2 * q + 1) : 0.f;
+                    __nv_bfloat162 h0 = __floats2bfloat162_rn(f0[2 * q] + b0, f0[2 * q + 1] + b1);
+                    __nv_bfloat162 h1 = __floats2bfloat162_rn(f1[2 * q] + b0, f1[2 * q + 1] + b1);
+                    ou[q] = *reinterpret_cast<unsigned *>(&h0);
+                    ou[4 + q] = *reinterpret_cast<unsigned *>(&h1);
+                }
+                bf16 *dst = p.out + ((bb * (p.N >> 3) + g) * Vf + fv) * 8;
+                reinterpret_cast<uint4 *>(dst)[0] = o[0];
+                reinterpret_cast<uint4 *>(dst)[1] = o[1];
+            }
+        }
+    }
+    if (threadIdx.x == 0) mb_wait(bar_ld, 0, abort_flag, p.err, 13, false);  // no copy outlives the CTA
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(p.tmem_cols)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 // z-taps in N for the thin layers, which are otherwise bound by the
@@ -609,7 +748,8 @@ bool conv3_tc_plan(int N, int K, int D, TcPlan *pl)
     }
     const unsigned wtap = (unsigned)N * (unsigned)K * 2u;
     static const int zts[] = {4, 2, 1};
-    // resident weights first; then a ring of 4, 3, 2 one-tap stages
+    // resident weights first (even single-buffered: streaming the weights
+    // costs more than the lost overlap); then a ring of 4, 3, 2 one-tap stages
     for (int stages = 0; stages <= MAX_WSTAGE; stages = stages ? stages - 1 : MAX_WSTAGE) {
         if (stages == 1) break;
         const unsigned wbytes = (stages ? (unsigned)stages : 27u) * wtap;
@@ -730,6 +870,49 @@ int conv3_tc(const TcConv &c, int *err, cudaStream_t s)
     if (grid > a.ntiles) grid = a.ntiles;
     if (grid < 1) return 1;
     counted(pick_kernel(pl, K))<<<(unsigned)grid, TC_THREADS, pl.smem, s>>>(m1, m2, a);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+bool up2_tc_ok(int N, int K, long long Vc)
+{
+    return N >= 8 && N % 8 == 0 && 8 * N <= 512 && K >= 16 && K % 16 == 0 && Vc % 128 == 0 &&
+           UP_HDR + ALIGN_SLACK + (unsigned)K / 8u * 2048u + (unsigned)K * 16u * (unsigned)N <= TC_SMEM_MAX;
+}
+
+int up2_tc(const bf16 *in, const bf16 *w, const float *bias, bf16 *out, int B, int Dc, int K, int N, int *err,
+           cudaStream_t s)
+{
+    const long long Vc = (long long)Dc * Dc * Dc;
+    if (!up2_tc_ok(N, K, Vc) || (reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(w) & 15) ||
+        (reinterpret_cast<uintptr_t>(out) & 15))
+        return 0;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, []() {
+        attr_err = cudaFuncSetAttribute(k_up2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+    });
+    if (attr_err != cudaSuccess) return -1;
+    Up2Args a;
+    a.in = in; a.w = w; a.bias = bias; a.out = out;
+    a.K = K; a.N = N; a.Dc = Dc; a.Vc = Vc;
+    a.ntiles = (long long)B * Vc / 128;
+    a.abytes = (unsigned)K / 8u * 2048u;
+    a.wbytes = (unsigned)K * 16u * (unsigned)N;  // 8 N rows x K x 2 bytes
+    const unsigned ncols = 8u * (unsigned)N;
+    a.nsplit = ncols > 256u ? 2u : 1u;
+    a.ncols_split = ncols / a.nsplit;
+    a.tmem_cols = pow2_at_least(ncols);
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((a.ncols_split >> 3) << 17) | ((128u >> 4) << 24);
+    a.err = err;
+    // at most as many CTAs per SM as their TMEM allocations fit: size the
+    // shared-memory request so that no allocation has to wait
+    const unsigned need = ALIGN_SLACK + UP_HDR + a.abytes + a.wbytes;
+    const unsigned per_sm = 512u / a.tmem_cols;
+    unsigned smem = TC_SMEM_SM / per_sm - 1024u;
+    if (smem > TC_SMEM_MAX) smem = TC_SMEM_MAX;
+    if (smem < need) smem = need;
+    if (a.ntiles < 1) return 1;
+    counted(k_up2_tc)<<<(unsigned)a.ntiles, 128, smem, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -47,6 +47,17 @@ bool conv3_tc_plan(int N, int K, int D, TcPlan *pl);
 // non-zero code into *err (device memory).
 int conv3_tc(const TcConv &c, int *err, cudaStream_t s);
 
+// 2x2x2 transposed convolution with stride 2 (the U-Net's up-sampling) on
+// the tensor cores: out(fine voxel 2 v + (dz, dy, dx))[n] = bias[n] +
+// sum_k in(v)[k] w[t][k][n], t = 4 dz + 2 dy + dx, blocked BF16 tensors on a
+// (B, Dc^3) coarse and (B, (2 Dc)^3) fine grid; w in the layout of pack_w_tc
+// with taps = 1 and 8 N rows (row t N + n).  Returns 1 when launched, 0 when
+// the shape is not supported (Dc^3 not a multiple of 128, N > 64, ...),
+// -1 on a launch error.
+bool up2_tc_ok(int N, int K, long long Vc);
+int up2_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out, int B, int Dc,
+           int K, int N, int *err, cudaStream_t s);
+
 // Whether a 3^3 layer with N output and K input channels runs with its
 // three z-taps in one MMA (N <= 32; see conv_tc.cu).
 bool conv3_tc_dzn(int N, int K);

@@ -310,36 +310,115 @@ __global__ void __launch_bounds__(128) k_wgrad(WgArgs p)
 // voxels per batch entry.
 __global__ void k_pack_input(const float *__restrict__ x, int cin, long long V, long long Vs, bf16 *__restrict__ out)
 {
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= V * 16) return;
-    long long v = e >> 4;
-    int c = (int)(e & 15);
-    out[blk(v, c, 16, Vs)] = __float2bfloat16_rn(c < cin ? x[v * cin + c] : 0.f);
+    // one voxel per thread: its cin values, two 16-byte channel groups out
+    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    float f[16];
+#pragma unroll
+    for (int c = 0; c < 16; c++) f[c] = c < cin ? x[v * cin + c] : 0.f;
+    const long long b = v / Vs, sv = v - b * Vs;
+#pragma unroll
+    for (int g = 0; g < 2; g++) {
+        uint4 o;
+        unsigned *ou = reinterpret_cast<unsigned *>(&o);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(f[8 * g + 2 * q], f[8 * g + 2 * q + 1]);
+            ou[q] = *reinterpret_cast<unsigned *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(out + ((b * 2 + g) * Vs + sv) * 8) = o;
+    }
+}
+
+// 1x1x1 head: FP32 out[v][n] = bias[n] + sum_k in(v)[k] w[n][k] for n < cout
+// (<= 8) and k < C (<= 32, a multiple of 8); w is the packed BF16 [Npad][Kpad]
+// forward weight.  One voxel per thread; a block's outputs are staged in
+// shared memory and leave as contiguous 16-byte stores.
+constexpr int HEAD_T = 256;
+__global__ void __launch_bounds__(HEAD_T) k_head(const bf16 *__restrict__ in, int C, const bf16 *__restrict__ w,
+                                                 int Kpad, const float *__restrict__ bias, int cout, long long V,
+                                                 long long Vs, float *__restrict__ out)
+{
+    __shared__ float sw[8][32], sbias[8];
+    __shared__ __align__(16) float so[HEAD_T * 8];
+    for (int i = threadIdx.x; i < 8 * 32; i += blockDim.x) {
+        const int n = i >> 5, k = i & 31;
+        sw[n][k] = n < cout && k < C ? __bfloat162float(w[n * Kpad + k]) : 0.f;
+    }
+    if (threadIdx.x < 8) sbias[threadIdx.x] = threadIdx.x < cout && bias ? bias[threadIdx.x] : 0.f;
+    __syncthreads();
+    const long long v0 = (long long)blockIdx.x * HEAD_T;
+    const long long v = v0 + threadIdx.x;
+    if (v < V) {
+        const long long b = v / Vs, sv = v - b * Vs;
+        float acc[8];
+#pragma unroll
+        for (int n = 0; n < 8; n++) acc[n] = sbias[n];
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+            if (g >= (C >> 3)) break;
+            const uint4 u = *reinterpret_cast<const uint4 *>(in + ((b * (C >> 3) + g) * Vs + sv) * 8);
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const float2 f = __bfloat1622float2(h[q]);
+#pragma unroll
+                for (int n = 0; n < 8; n++) acc[n] += f.x * sw[n][8 * g + 2 * q] + f.y * sw[n][8 * g + 2 * q + 1];
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < 8; n++)
+            if (n < cout) so[threadIdx.x * cout + n] = acc[n];
+    }
+    __syncthreads();
+    const long long nv = V - v0 < HEAD_T ? V - v0 : HEAD_T;
+    const long long nf = nv * cout;  // floats of this block, contiguous from out + v0 cout
+    float *dst = out + v0 * cout;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        for (long long i = threadIdx.x; i < nf / 4; i += HEAD_T)
+            reinterpret_cast<float4 *>(dst)[i] = reinterpret_cast<const float4 *>(so)[i];
+        for (long long i = (nf / 4) * 4 + threadIdx.x; i < nf; i += HEAD_T) dst[i] = so[i];
+    } else {
+        for (long long i = threadIdx.x; i < nf; i += HEAD_T) dst[i] = so[i];
+    }
 }
 
 __global__ void k_maxpool(const bf16 *__restrict__ in, bf16 *__restrict__ out, unsigned char *__restrict__ idx, int B,
                           int D, int H, int W, int C)
 {
-    // output grid (B, D, H, W); input grid twice as fine; e runs over the
-    // blocked output, (b, channel group, voxel, channel % 8)
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long tot = (long long)B * D * H * W * C;
-    if (e >= tot) return;
+    // output grid (B, D, H, W); input grid twice as fine; q runs over the
+    // blocked output's (b, channel group, voxel): 8 channels per thread, the
+    // 2x2x2 inputs as 16-byte loads; the first maximum of the 8 taps wins
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long Vs = (long long)D * H * W;
-    int j = (int)(e & 7);
-    long long q = e >> 3;
+    if (q >= (long long)B * (C >> 3) * Vs) return;
     long long s = q % Vs, bg = q / Vs;  // bg = b * C / 8 + channel group
     long long x = s % W, r = s / W, y = r % H, z = r / H;
-    const bf16 *src = in + bg * 8 * Vs * 8 + j;
-    float best = -INFINITY;
-    int bi = 0;
+    const bf16 *src = in + bg * 8 * Vs * 8;
+    float best[8];
+    unsigned bi[8];
+#pragma unroll
     for (int t = 0; t < 8; t++) {
         long long zz = 2 * z + ((t >> 2) & 1), yy = 2 * y + ((t >> 1) & 1), xx = 2 * x + (t & 1);
-        float f = __bfloat162float(src[((zz * 2 * H + yy) * 2 * W + xx) * 8]);
-        if (f > best) { best = f; bi = t; }
+        const uint4 u = *reinterpret_cast<const uint4 *>(src + ((zz * 2 * H + yy) * 2 * W + xx) * 8);
+        const bf16 *h = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const float f = __bfloat162float(h[j]);
+            if (t == 0 || f > best[j]) { best[j] = f; bi[j] = (unsigned)t; }
+        }
     }
-    out[e] = __float2bfloat16_rn(best);
-    idx[e] = (unsigned char)bi;
+    uint4 o;
+    bf16 *ob = reinterpret_cast<bf16 *>(&o);
+    unsigned lo = 0, hi = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        ob[j] = __float2bfloat16_rn(best[j]);
+        if (j < 4) lo |= bi[j] << (8 * j);
+        else hi |= bi[j] << (8 * (j - 4));
+    }
+    *reinterpret_cast<uint4 *>(out + q * 8) = o;
+    *reinterpret_cast<uint2 *>(idx + q * 8) = make_uint2(lo, hi);
 }
 
 // dIn (fine grid) = routed pool gradient + skip gradient
@@ -468,7 +547,7 @@ struct ULayer {
     long long woff, boff;       // offsets in the flat parameter array
     int Npad, Kpad, Nd, Kd;     // padded forward / input-gradient GEMM shapes
     bf16 *wf = nullptr, *wd = nullptr;
-    bf16 *wtc = nullptr, *wdtc = nullptr;  // tensor-core layouts of wf / wd (3^3 layers)
+    bf16 *wtc = nullptr, *wdtc = nullptr;  // tensor-core layouts of wf / wd (3^3 and up-sampling layers)
 };
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
@@ -621,7 +700,9 @@ int unet_pack(gnb_unet *u)
         long long nd = (long long)l.taps * l.Nd * l.Kd;
         counted(k_pack_w_dgrad)<<<(unsigned)((nd + 255) / 256), 256, 0, u->s>>>(
             u->p + l.woff, l.taps, l.kind == L_CONV3 ? 1 : 0, l.cin, l.cout, l.Nd, l.Kd, l.wd);
-        if (l.wtc && pack_w_tc(l.wf, l.taps, l.Npad, l.Kpad, l.wtc, u->s) != 0) return GNB_ECUDA;
+        // up-sampling: the 8 taps' output channels are the rows of one matrix
+        if (l.wtc && l.kind == L_UP2 && pack_w_tc(l.wf, 1, 8 * l.Npad, l.Kpad, l.wtc, u->s) != 0) return GNB_ECUDA;
+        if (l.wtc && l.kind == L_CONV3 && pack_w_tc(l.wf, l.taps, l.Npad, l.Kpad, l.wtc, u->s) != 0) return GNB_ECUDA;
         if (l.wdtc && pack_w_tc(l.wd, l.taps, l.Nd, l.Kd, l.wdtc, u->s) != 0) return GNB_ECUDA;
     }
     return cudaGetLastError() == cudaSuccess ? GNB_OK : GNB_ECUDA;
@@ -657,6 +738,17 @@ void conv_fwd(gnb_unet *u, const ULayer &ly, int mode, int B, int D, const bf16 
         int rc = conv3_try_tc(u, ly.wtc, ly.Npad, B, D, in1, C1, in2, C2, u->p + ly.boff, out, ly.cout, nullptr,
                               relu);
         if (rc != 0) { if (rc < 0) u->launch_failed = true; return; }
+    }
+    if (mode == IG_UP2 && !outf && !in2 && !relu && ly.wtc && C1 == ly.Kpad && ly.cout == ly.Npad &&
+        u->conv_impl != GNB_CONV_MMA_SYNC) {
+        int rc = up2_tc(in1, ly.wtc, u->p + ly.boff, out, B, D, C1, ly.Npad, u->err_d, u->s);
+        if (rc != 0) { if (rc < 0) u->launch_failed = true; return; }
+    }
+    if (mode == IG_CONV1 && outf && !in2 && ly.Npad <= 8 && C1 % 8 == 0 && C1 <= 32 && ly.Kpad <= 32) {
+        const long long V = (long long)B * D * D * D;
+        counted(k_head)<<<(unsigned)((V + HEAD_T - 1) / HEAD_T), HEAD_T, 0, u->s>>>(in1, C1, ly.wf, ly.Kpad, u->p + ly.boff, ly.cout,
+                                                                      V, (long long)D * D * D, outf);
+        return;
     }
     IgArgs a = ig_base(mode, B, D, D, D);
     a.in1 = in1; a.in2 = in2 ? in2 : in1; a.C1 = C1; a.C2 = C2;
@@ -708,8 +800,8 @@ int unet_forward(gnb_unet *u, int B)
         conv_fwd(u, u->L[LI_ENCB(l)], IG_CONV3, B, D, u->act[S_ENCA(l)], w, nullptr, 0, u->act[S_ENCB(l)], nullptr, 1);
         if (l + 1 < u->levels) {
             long long n = vox(u, l + 1, B) * w;
-            counted(k_maxpool)<<<(unsigned)((n + 255) / 256), 256, 0, u->s>>>(u->act[S_ENCB(l)], u->act[S_POOL(l)],
-                                                                             u->pidx[l], B, D / 2, D / 2, D / 2, w);
+            counted(k_maxpool)<<<(unsigned)((n / 8 + 255) / 256), 256, 0, u->s>>>(u->act[S_ENCB(l)], u->act[S_POOL(l)],
+                                                                                 u->pidx[l], B, D / 2, D / 2, D / 2, w);
             h = u->act[S_POOL(l)];
         } else {
             h = u->act[S_ENCB(l)];
@@ -907,6 +999,8 @@ int gnb_unet_create(gnb_unet **out, int cin, int cout, int base, int levels, int
         TcPlan pl;
         if (ok && l.kind == L_CONV3 && conv3_tc_plan(l.Npad, l.Kpad, grid, &pl))
             ok = cudaMalloc((void **)&l.wtc, (size_t)l.taps * l.Npad * l.Kpad * 2) == cudaSuccess;
+        if (ok && l.kind == L_UP2 && l.cin == l.Kpad && up2_tc_ok(l.Npad, l.Kpad, 128))
+            ok = cudaMalloc((void **)&l.wtc, (size_t)l.taps * l.Npad * l.Kpad * 2) == cudaSuccess;
         if (ok && l.kind == L_CONV3 && conv3_tc_plan(l.Nd, l.Kd, grid, &pl))
             ok = cudaMalloc((void **)&l.wdtc, (size_t)l.taps * l.Nd * l.Kd * 2) == cudaSuccess;
     }
@@ -1000,7 +1094,7 @@ int gnb_unet_forward(gnb_unet *u, int batch, const float *x, float *y, int on_de
         cudaMemcpyAsync(tmpx, x, V * u->cin * 4, cudaMemcpyHostToDevice, u->s);
         xd = tmpx;
     }
-    counted(k_pack_input)<<<(unsigned)((V * 16 + 255) / 256), 256, 0, u->s>>>(xd, u->cin, V, vox(u, 0, 1), u->xin);
+    counted(k_pack_input)<<<(unsigned)((V + 255) / 256), 256, 0, u->s>>>(xd, u->cin, V, vox(u, 0, 1), u->xin);
     rc = unet_forward(u, batch);
     if (rc == GNB_OK)
         cudaMemcpyAsync(y, u->yout, V * u->cout * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -1026,7 +1120,7 @@ int gnb_unet_train_step(gnb_unet *u, int batch, const float *x, const float *tar
     }
     cudaMemcpyAsync(u->tgt, target, V * u->cout * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                     u->s);
-    counted(k_pack_input)<<<(unsigned)((V * 16 + 255) / 256), 256, 0, u->s>>>(xd, u->cin, V, vox(u, 0, 1), u->xin);
+    counted(k_pack_input)<<<(unsigned)((V + 255) / 256), 256, 0, u->s>>>(xd, u->cin, V, vox(u, 0, 1), u->xin);
     rc = unet_forward(u, batch);
     cudaMemsetAsync(u->loss_d, 0, 8, u->s);
     counted(k_mse)<<<(unsigned)((V * 16 + 255) / 256), 256, 0, u->s>>>(u->yout, u->tgt, V, vox(u, 0, 1), u->cout,
