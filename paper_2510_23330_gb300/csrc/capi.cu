@@ -276,7 +276,7 @@ void gnb_destroy(gnb_ctx *c)
     if (c->pinned_i) cudaFreeHost(c->pinned_i);
     {
         void *sur[] = {c->sreg, c->rcount, c->vacc, c->vout, c->vw,  c->vcdf, c->cent_d, c->seed_d,
-                       c->rsx,  c->rsi,    c->centf, c->vpa, c->vpb, c->vpc,  c->vbox};
+                       c->rsx,  c->rsi,    c->centf, c->vpa, c->vpb, c->vpc,  c->vbox, c->vcdf32, c->vcdfc};
         for (void *q : sur) dfree(c, q);
         if (c->sn_graph) cudaGraphExecDestroy(c->sn_graph);
     }

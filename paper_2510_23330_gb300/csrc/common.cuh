@@ -152,6 +152,8 @@ struct gnb_ctx {
     float *vout = nullptr;        // standardised channels [nreg][grid^3][5]
     double *vw = nullptr;         // remap weights [nreg][grid^3]
     double *vcdf = nullptr;       // remap line CDFs [nreg][axis][grid^2 lines][grid]
+    float *vcdf32 = nullptr;      // the same, rounded to FP32 (decides the comparisons it can)
+    float *vcdfc = nullptr;       // every 8th FP32 sum of each line (its last entry = the line total)
     double *cent_d = nullptr;     // region centres [nreg][3]
     float *rsx = nullptr;         // region centre x (FP32), sorted ascending (membership search)
     int *rsi = nullptr;           // region index of each sorted entry

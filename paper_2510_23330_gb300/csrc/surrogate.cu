@@ -99,32 +99,19 @@ __global__ void k_region_assign(PArr p, int n, const double *__restrict__ cent, 
     if (r >= 0) warp_inc(rcount, r);
 }
 
-// Voxels whose centre can lie inside the kernel support of particle i
-// (clipped to the grid): [i0, i1] per axis.
-__device__ __forceinline__ void vox_footprint(const PArr &p, int i, const double *lo, double d, int grid, int *i0,
-                                              int *i1)
-{
-    // explicit round-to-nearest operations: the counting and the filling pass
-    // must derive the same tiles for a particle
-    const double pp[3] = {p.x[i], p.y[i], p.z[i]};
-    const double h = __dsqrt_rn(p.h2[i]);
-    for (int a = 0; a < 3; a++) {
-        i0[a] = max((int)floor(__dsub_rn(__ddiv_rn(__dsub_rn(__dsub_rn(pp[a], h), lo[a]), d), 0.5)), 0);
-        i1[a] = min((int)ceil(__dsub_rn(__ddiv_rn(__dsub_rn(__dadd_rn(pp[a], h), lo[a]), d), 0.5)), grid - 1);
-    }
-}
-
 __device__ __forceinline__ void region_lo(const double *cent, int r, double side, double *lo)
 {
     for (int a = 0; a < 3; a++) lo[a] = cent[3 * r + a] - 0.5 * side;
 }
 
-// Voxelisation, pass 1 (the only pass with FP64 arithmetic): every region
-// member's footprint and FP32 values are computed once and staged as three
-// float4 -- offset from the region corner and support^2; 1/h, m s,
-// (m/rho) s, T; velocity and the packed z range of the footprint (s = 8 /
-// (pi h^3), the kernel normalisation) -- plus the packed x and y ranges
-// (grids of at most 256 voxels per axis).
+// Voxelisation, pass 1: every region member's FP32 values are computed once
+// and staged as three float4 -- offset from the region corner (the one FP64
+// step: the difference of two FP64 positions) and h^2; 1/h, m s, (m/rho) s,
+// T; velocity and the packed z range of the footprint (s = 8 / (pi h^3), the
+// kernel normalisation) -- plus the packed x and y ranges (grids of at most
+// 256 voxels per axis).  The footprint box only bounds the walk of pass 2,
+// which tests every voxel exactly, so it is taken in FP32 and widened by one
+// voxel on each side.
 __global__ void k_vox_stage(PArr p, int n, const int *__restrict__ reg, const float *__restrict__ rho,
                             const double *__restrict__ cent, double side, int grid, float4 *__restrict__ vpa,
                             float4 *__restrict__ vpb, float4 *__restrict__ vpc, int *__restrict__ vbox)
@@ -134,13 +121,18 @@ __global__ void k_vox_stage(PArr p, int n, const int *__restrict__ reg, const fl
     int r = reg[i];
     if (r < 0) return;
     double lo[3];
-    int i0[3], i1[3];
     region_lo(cent, r, side, lo);
-    vox_footprint(p, i, lo, side / grid, grid, i0, i1);
-    const float hinv = (float)(1.0 / sqrt(p.h2[i]));
+    const float rel[3] = {(float)(p.x[i] - lo[0]), (float)(p.y[i] - lo[1]), (float)(p.z[i] - lo[2])};
+    const float h2 = (float)p.h2[i], h = sqrtf(h2), hinv = 1.f / h;
+    const float idf = (float)grid / (float)side;
+    int i0[3], i1[3];
+    for (int a = 0; a < 3; a++) {
+        i0[a] = max((int)floorf((rel[a] - h) * idf - 0.5f) - 1, 0);
+        i1[a] = min((int)ceilf((rel[a] + h) * idf - 0.5f) + 1, grid - 1);
+    }
     const float sn = 2.546479089470325f * hinv * hinv * hinv;  // 8 / (pi h^3)
     const float m = p.m[i];
-    vpa[i] = make_float4((float)(p.x[i] - lo[0]), (float)(p.y[i] - lo[1]), (float)(p.z[i] - lo[2]), 1.f / (hinv * hinv));
+    vpa[i] = make_float4(rel[0], rel[1], rel[2], h2);
     vpb[i] = make_float4(hinv, m * sn, m / rho[i] * sn, p.u[i] * (float)SUR_T_PER_U);
     vpc[i] = make_float4(p.vx[i], p.vy[i], p.vz[i], __int_as_float((i0[2] << 16) | i1[2]));
     vbox[i] = i0[0] | (i1[0] << 8) | (i0[1] << 16) | (i1[1] << 24);
@@ -155,13 +147,18 @@ __device__ __forceinline__ float m4_shape(float q)
     return 0.f;
 }
 
-// Pass 2, one warp per member particle: the lanes sweep the voxels of the
-// particle's footprint box and add its six kernel-weighted terms
-// {m W, (m/rho) W, T (m/rho) W, v (m/rho) W} to acc[r][v][8] (six used,
-// padded to 32 bytes) with two vector reductions per voxel
-// (red.global.add.v4.f32 + .v2.f32, fire-and-forget at L2).  Consecutive
-// warps take neighbouring particles (Morton order), so their reductions hit
-// neighbouring voxels.  No FP64 arithmetic runs here.
+// Pass 2, one thread per member particle: the six kernel-weighted terms
+// {m W, (m/rho) W, T (m/rho) W, v (m/rho) W} of every voxel inside the
+// particle's support are added to acc[r][v][8] (six used, padded to 32 bytes)
+// with two vector reductions (red.global.add.v4.f32 + .v2.f32, resolved at
+// L2).  The thread walks the (y, z) rows of the footprint box and, in each
+// row, only the x-range that can lie inside the support (conservatively
+// wide; the exact r^2 test decides), so only voxels near the support sphere
+// are visited.  Neighbouring threads take neighbouring particles (Morton
+// order): their smoothing lengths and footprints are alike, so the lanes of
+// a warp run loops of similar length, and their reductions hit voxels that
+// are close in memory.  The L2 reduction rate bounds this pass (one atomic
+// operation per vector reduction); no FP64 arithmetic runs here.
 __device__ __forceinline__ void red_v4(float *a, float x, float y, float z, float w)
 {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(a), "f"(x), "f"(y), "f"(z), "f"(w)
@@ -172,43 +169,43 @@ __device__ __forceinline__ void red_v2(float *a, float x, float y)
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};\n" ::"l"(a), "f"(x), "f"(y) : "memory");
 }
 
-__global__ void __launch_bounds__(256) k_vox_warp_scatter(int n, const int *__restrict__ reg,
-                                                          const float4 *__restrict__ vpa,
-                                                          const float4 *__restrict__ vpb,
-                                                          const float4 *__restrict__ vpc,
-                                                          const int *__restrict__ vbox, double side, int grid,
-                                                          float *__restrict__ acc8)
+__global__ void __launch_bounds__(256) k_vox_scatter(int n, const int *__restrict__ reg,
+                                                     const float4 *__restrict__ vpa, const float4 *__restrict__ vpb,
+                                                     const float4 *__restrict__ vpc, const int *__restrict__ vbox,
+                                                     double side, int grid, float *__restrict__ acc8)
 {
-    const int lane = threadIdx.x & 31;
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const float df = (float)(side / grid);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = reg[i];
+    if (r < 0) return;
+    const float df = (float)(side / grid), idf = 1.f / df;
     const size_t G = (size_t)grid;
-    for (long long i = wid; i < n; i += nwarps) {
-        const int r = reg[i];
-        if (r < 0) continue;  // warp-uniform
-        const float4 pa = vpa[i], pb = vpb[i], pc = vpc[i];
-        const int bx = vbox[i], bz = __float_as_int(pc.w);
-        const int x0 = bx & 0xff, x1 = (bx >> 8) & 0xff, y0 = (bx >> 16) & 0xff, y1 = (bx >> 24) & 0xff;
-        const int z0 = bz >> 16, z1 = bz & 0xffff;
-        const int nx = x1 - x0 + 1, ny = y1 - y0 + 1, nz = z1 - z0 + 1;
-        const int nxy = nx * ny, vol = nxy * nz;
-        const float inx = 1.f / (float)nx, inxy = 1.f / (float)nxy;
-        float *base = acc8 + (size_t)r * G * G * G * 8;
-        for (int j = lane; j < vol; j += 32) {
-            // j -> (x, y, z) by float multiplies: exact for these small ranges
-            const int jz = (int)(((float)j + 0.5f) * inxy), rem = j - jz * nxy;
-            const int jy = (int)(((float)rem + 0.5f) * inx), jx = rem - jy * nx;
-            const int ix = x0 + jx, iy = y0 + jy, iz = z0 + jz;
-            const float dx = (ix + 0.5f) * df - pa.x, dy = (iy + 0.5f) * df - pa.y, dz = (iz + 0.5f) * df - pa.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 >= pa.w) continue;
-            const float w = m4_shape(sqrtf(r2) * pb.x);
-            if (w <= 0.f) continue;
-            const float ww = pb.z * w;
-            float *q = base + (((size_t)iz * G + iy) * G + ix) * 8;
-            red_v4(q, pb.y * w, ww, pb.w * ww, pc.x * ww);
-            red_v2(q + 4, pc.y * ww, pc.z * ww);
+    const float4 pa = vpa[i], pb = vpb[i], pc = vpc[i];
+    const int bx = vbox[i], bz = __float_as_int(pc.w);
+    const int x0 = bx & 0xff, x1 = (bx >> 8) & 0xff, y0 = (bx >> 16) & 0xff, y1 = (bx >> 24) & 0xff;
+    const int z0 = bz >> 16, z1 = bz & 0xffff;
+    float *base = acc8 + (size_t)r * G * G * G * 8;
+    for (int iz = z0; iz <= z1; iz++) {
+        const float dz = (iz + 0.5f) * df - pa.z;
+        for (int iy = y0; iy <= y1; iy++) {
+            const float dy = (iy + 0.5f) * df - pa.y;
+            const float dyz2 = dy * dy + dz * dz;
+            const float rem = pa.w - dyz2;
+            if (rem <= 0.f) continue;
+            const float sx = sqrtf(rem);
+            const int lo = max(x0, (int)floorf((pa.x - sx) * idf - 0.5f));
+            const int hi = min(x1, (int)ceilf((pa.x + sx) * idf - 0.5f));
+            float *q = base + (((size_t)iz * G + iy) * G + lo) * 8;
+            for (int ix = lo; ix <= hi; ix++, q += 8) {
+                const float dx = (ix + 0.5f) * df - pa.x;
+                const float r2 = dx * dx + dyz2;
+                if (r2 >= pa.w) continue;
+                const float w = m4_shape(sqrtf(r2) * pb.x);
+                if (w <= 0.f) continue;
+                const float ww = pb.z * w;
+                red_v4(q, pb.y * w, ww, pb.w * ww, pc.x * ww);
+                red_v2(q + 4, pc.y * ww, pc.z * ww);
+            }
         }
     }
 }
@@ -238,16 +235,6 @@ __global__ void k_vox_finalize(const float *__restrict__ acc, long long nv, long
     }
 }
 
-static int vox_sms()
-{
-    static int n = []() {
-        int d = 0, v = 0;
-        cudaGetDevice(&d);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
-        return v > 0 ? v : 1;
-    }();
-    return n;
-}
 
 __global__ void k_remap_weights(const float *__restrict__ pred, long long nv, int cout, double *__restrict__ w)
 {
@@ -258,9 +245,11 @@ __global__ void k_remap_weights(const float *__restrict__ pred, long long nv, in
 // Cumulative weights along every grid line of every region, one thread per
 // (region, axis, line), summed left to right in FP64 -- the same additions in
 // the same order as a running sum taken at draw time, so each draw below sees
-// bit-identical partial sums.  Line of axis a through voxel (x, y, z):
+// bit-identical partial sums -- and each sum also rounded to nearest FP32;
+// every 8th FP32 sum also goes to a coarse table (grids of a multiple of 8).  Line of axis a through voxel (x, y, z):
 // a = 0 -> z G + y, a = 1 -> z G + x, a = 2 -> y G + x.
-__global__ void k_line_cdf(const double *__restrict__ w, int nreg, int grid, double *__restrict__ cdf)
+__global__ void k_line_cdf(const double *__restrict__ w, int nreg, int grid, double *__restrict__ cdf,
+                           float *__restrict__ cdf32, float *__restrict__ cdfc)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long G = grid, lines = G * G;
@@ -275,15 +264,19 @@ __global__ void k_line_cdf(const double *__restrict__ w, int nreg, int grid, dou
     else { b0 = u * G + v; stride = G * G; }                   // y = u, x = v
     const double *wr = w + r * G * G * G + b0;
     double *out = cdf + t * G;
+    float *out32 = cdf32 + t * G;
     double cum = 0.0;
     for (int q = 0; q < grid; q++) {
         cum = __dadd_rn(cum, wr[q * stride]);
         out[q] = cum;
+        out32[q] = __double2float_rn(cum);
+        if ((grid & 7) == 0 && (q & 7) == 7) cdfc[t * (G >> 3) + (q >> 3)] = out32[q];
     }
 }
 
 __global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float *__restrict__ pred, int cout,
-                        const double *__restrict__ cdf, const double *__restrict__ cent, double side, int grid,
+                        const double *__restrict__ cdf, const float *__restrict__ cdf32,
+                        const float *__restrict__ cdfc, const double *__restrict__ cent, double side, int grid,
                         const unsigned long long *__restrict__ seedp, int sweeps)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -301,20 +294,81 @@ __global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float 
     }
     const size_t G = (size_t)grid;
     uint64_t id = (uint64_t)p.id[i];
+    const uint64_t sid = sm64(seed + id);  // the particle's stream: draw k is sm64(sid + k)
+    const bool coarse8 = (grid & 31) == 0 && grid <= 64;  // lines of 8 or fewer coarse sums, float4-aligned
     uint64_t k = 0;
     for (int s = 0; s < sweeps; s++) {
         for (int a = 0; a < 3; a++, k++) {
             // the line through the current voxel along axis a; pick the first
-            // q whose running sum exceeds U * total (binary search of the
-            // non-decreasing running sums = the first crossing of a scan)
+            // q whose running sum exceeds target = U * total (the first
+            // crossing of a scan of the non-decreasing running sums).  The
+            // comparisons run on FP32 images: t32 approximates target from
+            // the top 32 bits of U's 53-bit integer m and the FP32 total
+            // within a relative 2^-21 (m >= 2^45: truncation 2^-24, three
+            // roundings 2^-24 each, FP64 rounding of target 2^-53; the total
+            // kept in FP32's normal range), and the FP32 sums are within 2^-24
+            // of the FP64 ones, so a sum outside t32 (1 -+ 2^-20) orders
+            // against target as its image does; inside that band (and for
+            // m < 2^45) the FP64 values decide.  With 8 | grid the search is
+            // two scans of 8: the coarse sums (every 8th) pick the block, the
+            // block's 8 sums the voxel -- two dependent 32-byte loads.
             size_t line = a == 0 ? (size_t)c[2] * G + c[1] : (a == 1 ? (size_t)c[2] * G + c[0] : (size_t)c[1] * G + c[0]);
-            const double *L = cdf + (((size_t)r * 3 + a) * G * G + line) * G;
-            double target = __dmul_rn(uniform01(seed, id, k), L[grid - 1]);
-            int qa = 0, qb = grid;
-            while (qa < qb) {
-                int mid = (qa + qb) >> 1;
-                if (L[mid] > target) qb = mid;
-                else qa = mid + 1;
+            const size_t lid = ((size_t)r * 3 + a) * G * G + line;
+            const double *L = cdf + lid * G;
+            const float *L32 = cdf32 + lid * G;
+            const uint64_t m = sm64(sid + k) >> 11;
+            double target = 0.0;
+            bool have = false;
+            float lo32 = 0.f, hi32 = 0.f;
+            bool fast = false;
+            // true when running sum q (FP32 image l32) exceeds target
+            auto above = [&](float l32, int q) -> bool {
+                if (fast && l32 > hi32) return true;
+                if (fast && l32 < lo32) return false;
+                if (!have) {
+                    target = __dmul_rn((double)m * (1.0 / 9007199254740992.0), L[grid - 1]);
+                    have = true;
+                }
+                return L[q] > target;
+            };
+            auto setup = [&](float tot32) {
+                fast = m >= (1ull << 45) && tot32 >= 0x1p-90f && tot32 <= 0x1p100f;
+                const float t32 = __fmul_rn(__uint2float_rn((unsigned)(m >> 21)), tot32 * 0x1p-32f);
+                lo32 = __fmul_rn(t32, 1.f - 0x1p-20f);
+                hi32 = __fmul_rn(t32, 1.f + 0x1p-20f);
+            };
+            int qa;
+            if (coarse8) {
+                const int nc = grid >> 3;
+                const float4 *C4 = reinterpret_cast<const float4 *>(cdfc + lid * nc);
+                const float4 v0 = C4[0];
+                const float4 v1 = nc == 8 ? C4[1] : v0;
+                const float cv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                setup(nc == 8 ? v1.w : v0.w);
+                int jb = nc;
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (j < nc && above(cv[j], 8 * j + 7)) { jb = j; break; }
+                if (jb == nc) {
+                    qa = grid;
+                } else {
+                    const float4 *F4 = reinterpret_cast<const float4 *>(L32 + 8 * jb);
+                    const float4 f0 = F4[0], f1 = F4[1];
+                    const float fv[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+                    qa = 8 * jb + 7;  // block jb's last sum is above target
+#pragma unroll
+                    for (int q = 0; q < 7; q++)
+                        if (above(fv[q], 8 * jb + q)) { qa = 8 * jb + q; break; }
+                }
+            } else {
+                setup(L32[grid - 1]);
+                int qb = grid;
+                qa = 0;
+                while (qa < qb) {
+                    int mid = (qa + qb) >> 1;
+                    if (above(L32[mid], mid)) qb = mid;
+                    else qa = mid + 1;
+                }
             }
             c[a] = qa < grid ? qa : grid - 1;
         }
@@ -349,13 +403,19 @@ int voxelise_buffers_for(gnb_ctx *c, int nreg, int grid)
     }
     if (c->sur_nv < nv || c->sur_nreg < nreg) {
         c->sur_gen++;
-        dfree(c, c->vacc); dfree(c, c->vw); dfree(c, c->vcdf); dfree(c, c->cent_d); dfree(c, c->rcount);
+        dfree(c, c->vacc); dfree(c, c->vw); dfree(c, c->vcdf); dfree(c, c->vcdf32); dfree(c, c->vcdfc);
+        dfree(c, c->cent_d);
+        dfree(c, c->rcount);
         dfree(c, c->vout); dfree(c, c->rsx); dfree(c, c->rsi); dfree(c, c->centf);
-        c->vacc = nullptr; c->vw = nullptr; c->vcdf = nullptr; c->cent_d = nullptr; c->rcount = nullptr;
+        c->vacc = nullptr; c->vw = nullptr; c->vcdf = nullptr; c->vcdf32 = nullptr; c->vcdfc = nullptr;
+        c->cent_d = nullptr;
+        c->rcount = nullptr;
         c->vout = nullptr; c->rsx = nullptr; c->rsi = nullptr; c->centf = nullptr;
         GNB_TRY(dalloc(c, &c->vacc, nv * 8));
         GNB_TRY(dalloc(c, &c->vw, nv));
         GNB_TRY(dalloc(c, &c->vcdf, nv * 3));
+        GNB_TRY(dalloc(c, &c->vcdf32, nv * 3));
+        GNB_TRY(dalloc(c, &c->vcdfc, nv * 3 / 8 + 1));
         GNB_TRY(dalloc(c, &c->vout, nv * 5));
         GNB_TRY(dalloc(c, &c->cent_d, (size_t)nreg * 3));
         GNB_TRY(dalloc(c, &c->rsx, (size_t)nreg));
@@ -406,8 +466,8 @@ static int vox_launch(gnb_ctx *c, int nreg, double side, int grid, float *out, b
     cudaMemsetAsync(c->vacc, 0, sizeof(float) * nv * 8, c->s);
     counted(k_vox_stage)<<<(n + 255) / 256, 256, 0, c->s>>>(a, n, c->sreg, c->rho, c->cent_d, side, grid, c->vpa,
                                                             c->vpb, c->vpc, c->vbox);
-    counted(k_vox_warp_scatter)<<<(unsigned)(vox_sms() * 16), 256, 0, c->s>>>(n, c->sreg, c->vpa, c->vpb, c->vpc,
-                                                                             c->vbox, side, grid, c->vacc);
+    counted(k_vox_scatter)<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(n, c->sreg, c->vpa, c->vpb, c->vpc, c->vbox,
+                                                                         side, grid, c->vacc);
     counted(k_vox_finalize)<<<(unsigned)((nv + 255) / 256), 256, 0, c->s>>>(
         c->vacc, (long long)nv, (long long)grid * grid * grid, out, outb);
     GNB_LAUNCH_CHECK(c, "voxelise");
@@ -420,9 +480,10 @@ static int remap_launch(gnb_ctx *c, int nreg, double side, int grid, const float
     size_t nv = (size_t)nreg * grid * grid * grid;
     counted(k_remap_weights)<<<(unsigned)((nv + 255) / 256), 256, 0, c->s>>>(pred, (long long)nv, cout, c->vw);
     long long nl = (long long)nreg * 3 * grid * grid;
-    counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, c->s>>>(c->vw, nreg, grid, c->vcdf);
-    counted(k_remap)<<<(n + 127) / 128, 128, 0, c->s>>>(c->P[c->cur], n, c->sreg, pred, cout, c->vcdf, c->cent_d,
-                                                        side, grid, c->seed_d, sweeps);
+    counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, c->s>>>(c->vw, nreg, grid, c->vcdf, c->vcdf32,
+                                                                        c->vcdfc);
+    counted(k_remap)<<<(n + 127) / 128, 128, 0, c->s>>>(c->P[c->cur], n, c->sreg, pred, cout, c->vcdf, c->vcdf32,
+                                                        c->vcdfc, c->cent_d, side, grid, c->seed_d, sweeps);
     GNB_LAUNCH_CHECK(c, "remap");
     return GNB_OK;
 }

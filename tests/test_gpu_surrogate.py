@@ -41,10 +41,13 @@ def test_voxelise_matches_oracle(G, orc):
     assert np.max(np.abs(z[:, 2:] - ref[:, 2:])) < 1e-4 * max(1.0, np.max(np.abs(ref[:, 2:])))
 
 
-def test_remap_matches_oracle(G, orc):
+# grid 64 and 32: the two-level (coarse block, then voxel) search over the
+# line sums; grid 20: the binary search
+@pytest.mark.parametrize("grid", [32, 64, 20])
+def test_remap_matches_oracle(G, orc, grid):
     from oracle import surrogate as S
     p, c = _region_state(G, orc, n=15000, seed=4)
-    grid, side, cen = 32, 60.0, (1.0, -2.0, 0.5)
+    side, cen = 60.0, (1.0, -2.0, 0.5)
     pred = c.voxelise([cen], side=side, grid=grid)
     s = orc.state(p)
     mem = np.nonzero(S.members(s, [cen], side) == 0)[0]
