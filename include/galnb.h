@@ -338,14 +338,22 @@ int gnb_remap_regions(gnb_ctx *ctx, int nreg, const double *centers, double side
 
 /* Batched surrogate step for nreg supernova regions of uneven particle
  * counts: voxelise -> U-Net forward (net, which must predict 5 channels on
- * its own grid) -> Gibbs remap, as above.  With use_graph = 1, a
- * non-default stream and the phase timers off, the sequence is captured into a
- * CUDA graph on the first
- * call and replayed while the shapes stay the same.  Requires
+ * its own grid) -> Gibbs remap, as above, pipelined over region chunks (see
+ * gnb_set_sn_chunks).  With use_graph = 1, a non-default stream and the
+ * phase timers off, the whole batch (all streams) is captured into one CUDA
+ * graph on the first call and replayed while the shapes stay the same.  Requires
  * gnb_compute_sph_density at the current positions.  Errors: GNB_EINVAL,
  * GNB_ESTATE, GNB_ENOMEM, GNB_ECUDA. */
 int gnb_sn_surrogate_batch(gnb_ctx *ctx, gnb_unet *net, int nreg, const double *centers, double side,
                            uint64_t seed, int sweeps, int use_graph);
+
+/* Number of region chunks the batched surrogate step pipelines (1 to 16;
+ * default 1, the stages in sequence): with k > 1 chunks, chunk i is
+ * voxelised on the context's stream, goes through the U-Net on a second
+ * stream and is remapped on a third, so the stages of different chunks can
+ * overlap.  With the phase timers on, the step always runs its stages in
+ * sequence.  Errors: GNB_EINVAL (chunks outside 1..16). */
+int gnb_set_sn_chunks(gnb_ctx *ctx, int chunks);
 
 /* Largest particle count accepted by gnb_morton_order_noalloc. */
 #define GNB_NOALLOC_MAX_N 262144

@@ -279,6 +279,11 @@ void gnb_destroy(gnb_ctx *c)
                        c->rsx,  c->rsi,    c->centf, c->vpa, c->vpb, c->vpc,  c->vbox, c->vcdf32, c->vcdfc};
         for (void *q : sur) dfree(c, q);
         if (c->sn_graph) cudaGraphExecDestroy(c->sn_graph);
+        for (cudaStream_t st : c->sn_st)
+            if (st) cudaStreamDestroy(st);
+        for (auto &row : c->sn_ev)
+            for (cudaEvent_t e : row)
+                if (e) cudaEventDestroy(e);
     }
     for (auto &q : c->pend) { cudaEventDestroy(q.second.first); cudaEventDestroy(q.second.second); }
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
@@ -783,6 +788,13 @@ int gnb_set_timing(gnb_ctx *c, int enable)
     if (!c) return GNB_EINVAL;
     phase_resolve(c);
     c->timing = enable != 0;
+    return GNB_OK;
+}
+
+int gnb_set_sn_chunks(gnb_ctx *c, int chunks)
+{
+    if (!c || chunks < 1 || chunks > gnb_ctx::SN_MAXCH) return GNB_EINVAL;
+    c->sn_chunks = chunks;
     return GNB_OK;
 }
 

@@ -168,7 +168,13 @@ struct gnb_ctx {
     size_t sur_nv = 0;
     int sur_nreg = 0;
     cudaGraphExec_t sn_graph = nullptr;  // captured voxelise -> U-Net -> remap
-    int sn_key[3] = {0, 0, 0};
+    // pipelined batch: the U-Net and the remap of region chunks run on their
+    // own streams, chunk k's stages ordered by events
+    static constexpr int SN_MAXCH = 16;
+    cudaStream_t sn_st[2] = {nullptr, nullptr};
+    cudaEvent_t sn_ev[3][SN_MAXCH] = {};
+    int sn_chunks = 1;                // region chunks of the pipelined batch (1: stages in sequence)
+    int sn_key[4] = {0, 0, 0, 0};
     void *sn_net = nullptr;
     double sn_side = 0.0;
     int64_t sn_n = 0;

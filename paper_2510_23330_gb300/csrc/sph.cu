@@ -198,6 +198,57 @@ __device__ __forceinline__ double exact_d2(const double *x, const double *y, con
     return __dadd_rn(a, __dmul_rn(dz, dz));
 }
 
+// Exact k-th smallest FP32 d^2 (1-based k) among the candidates of this
+// warp's particle that fall in histogram bucket bstar of [0, R2sel] (the
+// same bin rule as the histogram): a radix select on the bit patterns, which
+// order non-negative floats like their values, 8 bits per pass.  Used when
+// the bucket holds more candidates than the bucket buffer -- a particle whose
+// nearest neighbours all lie in a thin shell, e.g. a compact clump seen from
+// outside, where shrinking the radius does not thin the bucket.
+__device__ __noinline__ float knn_radix_kth(KnnSmem &S, int w, int lane, int nc, float xi, float yi, float zi, float R2sel,
+                               float inv64, int bstar, int k, bool *ok)
+{
+    int *hb = reinterpret_cast<int *>(S.bkt[w]);  // 256 bins (the bucket buffer is free here)
+    unsigned prefix = 0u, pmask = 0u;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        __syncwarp();
+        for (int b = lane; b < 256; b += 32) hb[b] = 0;
+        __syncwarp();
+        for (int c = lane; c < nc; c += 32) {
+            const float d = d2f(S.cand[c], xi, yi, zi);
+            if (d <= R2sel && min(63, (int)(d * inv64)) == bstar) {
+                const unsigned u = __float_as_uint(d);
+                if ((u & pmask) == prefix) atomicAdd(&hb[(u >> shift) & 255u], 1);
+            }
+        }
+        __syncwarp();
+        int loc[8], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) { loc[q] = hb[8 * lane + q]; sum += loc[q]; }
+        int inc = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int exc = inc - sum;
+        int myb = -1, mybefore = 0, run = exc;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if (myb < 0 && run < k && k <= run + loc[q]) { myb = 8 * lane + q; mybefore = run; }
+            run += loc[q];
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, myb >= 0);
+        if (bal == 0u) { *ok = false; return 0.f; }
+        const int src = __ffs(bal) - 1;
+        const int b = __shfl_sync(0xffffffffu, myb, src);
+        k -= __shfl_sync(0xffffffffu, mybefore, src);
+        prefix |= (unsigned)b << shift;
+        pmask |= 255u << shift;
+    }
+    *ok = true;
+    return __uint_as_float(prefix);
+}
+
 __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -325,11 +376,12 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                 }
                 // bucket holding the 64th smallest; shrink this particle's
                 // radius to that bucket while the bucket is too full to rank
-                float R2i = R2, inv64 = 64.f / R2;
+                float R2i = R2, inv64 = 64.f / R2, R2sel = R2;
                 int bstar = -1, kth = 0;
                 bool ok = false;
                 for (int it = 0; it < 16; it++) {
                     __syncwarp();
+                    R2sel = R2i;  // the radius of this histogram (bstar, kth refer to it)
                     S.hist[w][lane] = 0;
                     S.hist[w][lane + 32] = 0;
                     __syncwarp();
@@ -357,41 +409,49 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                     if (S.hist[w][bstar] <= KN_BKT) { ok = true; break; }
                     R2i = R2i * (float)(bstar + 1) * (1.f / 64.f) * (1.f + 1e-6f);
                 }
-                if (!ok) {
-                    if (lane == 0) knn_fail(S, ga.y, p.status);
-                    continue;
-                }
-                for (int c = lane; c < nc; c += 32) {
-                    float d = d2f(S.cand[c], xi, yi, zi);
-                    if (d <= R2i && min(63, (int)(d * inv64)) == bstar) {
-                        int slot = atomicAdd(&S.bn[w], 1);
-                        if (slot < KN_BKT) S.bkt[w][slot] = d;
-                    }
-                }
-                __syncwarp();
-                const int nb = S.bn[w];
-                if (nb > KN_BKT) {
-                    if (lane == 0) knn_fail(S, ga.y, p.status);
-                    continue;
-                }
-                // t = kth smallest value in the bucket (ties by position)
                 float t = 0.f;
-                bool found = false;
-                for (int e = lane; e < nb; e += 32) {
-                    float de = S.bkt[w][e];
-                    int r = 0;
-                    for (int f = 0; f < nb; f++) {
-                        float df = S.bkt[w][f];
-                        r += (df < de) || (df == de && f < e);
+                bool have_t = false;
+                if (ok) {
+                    for (int c = lane; c < nc; c += 32) {
+                        float d = d2f(S.cand[c], xi, yi, zi);
+                        if (d <= R2i && min(63, (int)(d * inv64)) == bstar) {
+                            int slot = atomicAdd(&S.bn[w], 1);
+                            if (slot < KN_BKT) S.bkt[w][slot] = d;
+                        }
                     }
-                    if (r == kth - 1) { t = de; found = true; }
+                    __syncwarp();
+                    const int nb = S.bn[w];
+                    if (nb <= KN_BKT) {
+                        // t = kth smallest value in the bucket (ties by position)
+                        bool found = false;
+                        for (int e = lane; e < nb; e += 32) {
+                            float de = S.bkt[w][e];
+                            int r = 0;
+                            for (int f = 0; f < nb; f++) {
+                                float df = S.bkt[w][f];
+                                r += (df < de) || (df == de && f < e);
+                            }
+                            if (r == kth - 1) { t = de; found = true; }
+                        }
+                        unsigned fb = __ballot_sync(0xffffffffu, found);
+                        if (fb != 0u) {
+                            t = __shfl_sync(0xffffffffu, t, __ffs(fb) - 1);
+                            have_t = true;
+                        }
+                    }
                 }
-                unsigned fb = __ballot_sync(0xffffffffu, found);
-                if (fb == 0u) {  // cannot happen when the histogram is consistent
+                if (!have_t && bstar >= 0 && ga.y == 1) {
+                    // a single particle whose bucket stays too full: exact
+                    // selection over the candidates themselves (groups split
+                    // first, which is cheaper for a clump inside a spread group)
+                    bool okr = false;
+                    t = knn_radix_kth(S, w, lane, nc, xi, yi, zi, R2sel, 64.f / R2sel, bstar, kth, &okr);
+                    have_t = okr;
+                }
+                if (!have_t) {
                     if (lane == 0) knn_fail(S, ga.y, p.status);
                     continue;
                 }
-                t = __shfl_sync(0xffffffffu, t, __ffs(fb) - 1);
                 // the bound at a point just above the band's upper end (E << t)
                 const float tb = t * 1.0009765625f;
                 const float E = 1.1920929e-07f * (EA * sqrtf(tb) + 5.f * tb);

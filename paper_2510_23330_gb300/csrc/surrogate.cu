@@ -29,7 +29,7 @@ typedef __nv_bfloat16 bf16;
 namespace gnb {
 
 int unet_prepare(gnb_unet *u, int batch, bf16 **xin, float **yout, int *grid, int *cout);
-int unet_run(gnb_unet *u, int batch, cudaStream_t stream);
+int unet_run(gnb_unet *u, int batch, cudaStream_t stream, const bf16 *xin, float *yout);
 
 #define SUR_T_PER_U 48.45894937815476  // (gamma - 1) mu m_H / k_B, K per (km/s)^2, mu = 0.6
 
@@ -112,14 +112,14 @@ __device__ __forceinline__ void region_lo(const double *cent, int r, double side
 // 256 voxels per axis).  The footprint box only bounds the walk of pass 2,
 // which tests every voxel exactly, so it is taken in FP32 and widened by one
 // voxel on each side.
-__global__ void k_vox_stage(PArr p, int n, const int *__restrict__ reg, const float *__restrict__ rho,
+__global__ void k_vox_stage(PArr p, int n, const int *__restrict__ reg, int r0, int r1, const float *__restrict__ rho,
                             const double *__restrict__ cent, double side, int grid, float4 *__restrict__ vpa,
                             float4 *__restrict__ vpb, float4 *__restrict__ vpc, int *__restrict__ vbox)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int r = reg[i];
-    if (r < 0) return;
+    if (r < r0 || r >= r1) return;  // not a member of regions [r0, r1)
     double lo[3];
     region_lo(cent, r, side, lo);
     const float rel[3] = {(float)(p.x[i] - lo[0]), (float)(p.y[i] - lo[1]), (float)(p.z[i] - lo[2])};
@@ -169,22 +169,23 @@ __device__ __forceinline__ void red_v2(float *a, float x, float y)
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};\n" ::"l"(a), "f"(x), "f"(y) : "memory");
 }
 
-__global__ void __launch_bounds__(256) k_vox_scatter(int n, const int *__restrict__ reg,
+__global__ void __launch_bounds__(256) k_vox_scatter(int n, const int *__restrict__ reg, int r0, int r1,
                                                      const float4 *__restrict__ vpa, const float4 *__restrict__ vpb,
                                                      const float4 *__restrict__ vpc, const int *__restrict__ vbox,
                                                      double side, int grid, float *__restrict__ acc8)
 {
+    // members of regions [r0, r1); acc8 holds those regions
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int r = reg[i];
-    if (r < 0) return;
+    if (r < r0 || r >= r1) return;
     const float df = (float)(side / grid), idf = 1.f / df;
     const size_t G = (size_t)grid;
     const float4 pa = vpa[i], pb = vpb[i], pc = vpc[i];
     const int bx = vbox[i], bz = __float_as_int(pc.w);
     const int x0 = bx & 0xff, x1 = (bx >> 8) & 0xff, y0 = (bx >> 16) & 0xff, y1 = (bx >> 24) & 0xff;
     const int z0 = bz >> 16, z1 = bz & 0xffff;
-    float *base = acc8 + (size_t)r * G * G * G * 8;
+    float *base = acc8 + (size_t)(r - r0) * G * G * G * 8;
     for (int iz = z0; iz <= z1; iz++) {
         const float dz = (iz + 0.5f) * df - pa.z;
         for (int iy = y0; iy <= y1; iy++) {
@@ -277,12 +278,13 @@ __global__ void k_line_cdf(const double *__restrict__ w, int nreg, int grid, dou
 __global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float *__restrict__ pred, int cout,
                         const double *__restrict__ cdf, const float *__restrict__ cdf32,
                         const float *__restrict__ cdfc, const double *__restrict__ cent, double side, int grid,
-                        const unsigned long long *__restrict__ seedp, int sweeps)
+                        const unsigned long long *__restrict__ seedp, int sweeps, int r0, int r1)
 {
+    // members of regions [r0, r1); the line sums hold those regions
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int r = reg[i];
-    if (r < 0) return;
+    if (r < r0 || r >= r1) return;
     uint64_t seed = *seedp;
     double d = side / grid;
     double lo[3] = {cent[3 * r] - 0.5 * side, cent[3 * r + 1] - 0.5 * side, cent[3 * r + 2] - 0.5 * side};
@@ -313,7 +315,7 @@ __global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float 
             // two scans of 8: the coarse sums (every 8th) pick the block, the
             // block's 8 sums the voxel -- two dependent 32-byte loads.
             size_t line = a == 0 ? (size_t)c[2] * G + c[1] : (a == 1 ? (size_t)c[2] * G + c[0] : (size_t)c[1] * G + c[0]);
-            const size_t lid = ((size_t)r * 3 + a) * G * G + line;
+            const size_t lid = ((size_t)(r - r0) * 3 + a) * G * G + line;
             const double *L = cdf + lid * G;
             const float *L32 = cdf32 + lid * G;
             const uint64_t m = sm64(sid + k) >> 11;
@@ -453,39 +455,63 @@ static int upload_centres(gnb_ctx *c, int nreg, const double *centers)
     return GNB_OK;
 }
 
-// Region membership and accumulators; the finalised channels go to `out`
-// (FP32 [nreg][grid^3][5]) and/or `outb` (BF16 U-Net input).
-static int vox_launch(gnb_ctx *c, int nreg, double side, int grid, float *out, bf16 *outb)
+// Region membership of every gas particle (all nreg regions).
+static void assign_launch(gnb_ctx *c, int nreg, double side, cudaStream_t st)
+{
+    int n = (int)c->n;
+    cudaMemsetAsync(c->rcount, 0, sizeof(int) * nreg, st);
+    counted(k_region_assign)<<<(n + 255) / 256, 256, 0, st>>>(c->P[c->cur], n, c->cent_d, c->rsx, c->rsi, c->centf,
+                                                              nreg, 0.5 * side, c->sreg, c->rcount);
+}
+
+// Accumulators of regions [r0, r1) (membership already assigned); their
+// finalised channels go to `out` (FP32 [nreg][grid^3][5]) and/or `outb`
+// (BF16 U-Net input), both indexed from region 0.
+static int vox_regions(gnb_ctx *c, int r0, int r1, double side, int grid, float *out, bf16 *outb, cudaStream_t st)
 {
     int n = (int)c->n;
     PArr &a = c->P[c->cur];
-    size_t nv = (size_t)nreg * grid * grid * grid;
-    cudaMemsetAsync(c->rcount, 0, sizeof(int) * nreg, c->s);
-    counted(k_region_assign)<<<(n + 255) / 256, 256, 0, c->s>>>(a, n, c->cent_d, c->rsx, c->rsi, c->centf, nreg,
-                                                                0.5 * side, c->sreg, c->rcount);
-    cudaMemsetAsync(c->vacc, 0, sizeof(float) * nv * 8, c->s);
-    counted(k_vox_stage)<<<(n + 255) / 256, 256, 0, c->s>>>(a, n, c->sreg, c->rho, c->cent_d, side, grid, c->vpa,
-                                                            c->vpb, c->vpc, c->vbox);
-    counted(k_vox_scatter)<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(n, c->sreg, c->vpa, c->vpb, c->vpc, c->vbox,
-                                                                         side, grid, c->vacc);
-    counted(k_vox_finalize)<<<(unsigned)((nv + 255) / 256), 256, 0, c->s>>>(
-        c->vacc, (long long)nv, (long long)grid * grid * grid, out, outb);
+    const long long V = (long long)grid * grid * grid;
+    size_t nv = (size_t)(r1 - r0) * V;
+    cudaMemsetAsync(c->vacc, 0, sizeof(float) * nv * 8, st);
+    counted(k_vox_stage)<<<(n + 255) / 256, 256, 0, st>>>(a, n, c->sreg, r0, r1, c->rho, c->cent_d, side, grid,
+                                                          c->vpa, c->vpb, c->vpc, c->vbox);
+    counted(k_vox_scatter)<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, c->sreg, r0, r1, c->vpa, c->vpb, c->vpc,
+                                                                       c->vbox, side, grid, c->vacc);
+    counted(k_vox_finalize)<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(
+        c->vacc, (long long)nv, V, out ? out + (size_t)r0 * V * 5 : nullptr, outb ? outb + (size_t)r0 * V * 16 : nullptr);
     GNB_LAUNCH_CHECK(c, "voxelise");
+    return GNB_OK;
+}
+
+static int vox_launch(gnb_ctx *c, int nreg, double side, int grid, float *out, bf16 *outb)
+{
+    assign_launch(c, nreg, side, c->s);
+    return vox_regions(c, 0, nreg, side, grid, out, outb, c->s);
+}
+
+// Remap of the members of regions [r0, r1) from the predictions `pred`
+// (FP32 [nreg][grid^3][cout], indexed from region 0).
+static int remap_regions_launch(gnb_ctx *c, int r0, int r1, double side, int grid, const float *pred, int cout,
+                                int sweeps, cudaStream_t st)
+{
+    int n = (int)c->n;
+    const long long V = (long long)grid * grid * grid;
+    size_t nv = (size_t)(r1 - r0) * V;
+    counted(k_remap_weights)<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(pred + (size_t)r0 * V * cout,
+                                                                           (long long)nv, cout, c->vw);
+    long long nl = (long long)(r1 - r0) * 3 * grid * grid;
+    counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(c->vw, r1 - r0, grid, c->vcdf, c->vcdf32,
+                                                                      c->vcdfc);
+    counted(k_remap)<<<(n + 127) / 128, 128, 0, st>>>(c->P[c->cur], n, c->sreg, pred, cout, c->vcdf, c->vcdf32,
+                                                      c->vcdfc, c->cent_d, side, grid, c->seed_d, sweeps, r0, r1);
+    GNB_LAUNCH_CHECK(c, "remap");
     return GNB_OK;
 }
 
 static int remap_launch(gnb_ctx *c, int nreg, double side, int grid, const float *pred, int cout, int sweeps)
 {
-    int n = (int)c->n;
-    size_t nv = (size_t)nreg * grid * grid * grid;
-    counted(k_remap_weights)<<<(unsigned)((nv + 255) / 256), 256, 0, c->s>>>(pred, (long long)nv, cout, c->vw);
-    long long nl = (long long)nreg * 3 * grid * grid;
-    counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, c->s>>>(c->vw, nreg, grid, c->vcdf, c->vcdf32,
-                                                                        c->vcdfc);
-    counted(k_remap)<<<(n + 127) / 128, 128, 0, c->s>>>(c->P[c->cur], n, c->sreg, pred, cout, c->vcdf, c->vcdf32,
-                                                        c->vcdfc, c->cent_d, side, grid, c->seed_d, sweeps);
-    GNB_LAUNCH_CHECK(c, "remap");
-    return GNB_OK;
+    return remap_regions_launch(c, 0, nreg, side, grid, pred, cout, sweeps, c->s);
 }
 
 int voxelise(gnb_ctx *c, int nreg, const double *centers, double side, int grid, float *out_dev)
@@ -517,6 +543,23 @@ int remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, int 
 
 // voxelise -> U-Net -> remap for nreg regions; after the first call with a
 // given shape the whole sequence is replayed as one CUDA graph.
+// The pipelined batch's two extra streams and its events, made once.
+static int sn_streams(gnb_ctx *c)
+{
+    // the U-Net stream gets the highest priority and the remap stream the
+    // next, so that their blocks are placed first as SMs free up
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    for (int k = 0; k < 2; k++)
+        if (!c->sn_st[k])
+            GNB_TRY(cuda_check(c, cudaStreamCreateWithPriority(&c->sn_st[k], cudaStreamNonBlocking,
+                                                               k == 0 ? hi : (hi < lo ? hi + 1 : hi)), "stream"));
+    for (auto &row : c->sn_ev)
+        for (auto &e : row)
+            if (!e) GNB_TRY(cuda_check(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event"));
+    return GNB_OK;
+}
+
 int sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *centers, double side, uint64_t seed,
                        int sweeps, int use_graph)
 {
@@ -530,7 +573,9 @@ int sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *center
     GNB_TRY(upload_centres(c, nreg, centers));
     unsigned long long sd = seed;
     GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->seed_d, &sd, sizeof(sd), cudaMemcpyHostToDevice, c->s), "seed"));
+    const int nch = std::max(1, std::min(std::min(c->sn_chunks, nreg), (int)gnb_ctx::SN_MAXCH));
     bool same = c->sn_graph && c->sn_key[0] == nreg && c->sn_key[1] == grid && c->sn_key[2] == sweeps &&
+                c->sn_key[3] == nch &&
                 c->sn_net == (void *)net && c->sn_side == side && c->sn_n == c->n && c->sn_cur == c->cur &&
                 c->sn_gen == c->sur_gen;
     if (use_graph && same) {
@@ -541,29 +586,58 @@ int sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *center
         phase_begin(c, GNB_T_VOXELISE);
         GNB_TRY(vox_launch(c, nreg, side, grid, nullptr, xin));
         phase_begin(c, GNB_T_UNET);
-        GNB_TRY(unet_run(net, nreg, c->s));
+        GNB_TRY(unet_run(net, nreg, c->s, nullptr, nullptr));
         phase_begin(c, GNB_T_REMAP);
         int rc = remap_launch(c, nreg, side, grid, yout, cout, sweeps);
         phase_end(c);
         return rc;
     };
-    // with the phase timers on, the batch runs eagerly (no graph) so that
-    // each stage's events are recorded
-    if (!use_graph || c->s == nullptr || c->timing) return issue();
+    // Pipelined (nch > 1): the regions go through in nch chunks; chunk k is
+    // voxelised on the context's stream, runs through the U-Net on a second
+    // stream and is remapped on a third, so the stages of different chunks
+    // may overlap.  (On GB300 they gain nothing: the voxel scatter's L2
+    // reductions and the remap's dependent L2 loads contend, and each stage
+    // alone fills the GPU; the default is one chunk.)  The chunks' members are disjoint particles, every buffer is
+    // used by one stream only (accumulators: voxelise; activations: U-Net;
+    // line sums: remap) apart from the network's input and output, which
+    // are indexed by region, and events order each chunk's three stages.
+    const long long V = (long long)grid * grid * grid;
+    auto issue_pipelined = [&]() -> int {
+        GNB_TRY(sn_streams(c));
+        cudaStream_t sa = c->s, sb = c->sn_st[0], sc = c->sn_st[1];
+        assign_launch(c, nreg, side, sa);
+        for (int k = 0; k < nch; k++) {
+            const int r0 = (int)((long long)k * nreg / nch), r1 = (int)((long long)(k + 1) * nreg / nch);
+            GNB_TRY(vox_regions(c, r0, r1, side, grid, nullptr, xin, sa));
+            GNB_TRY(cuda_check(c, cudaEventRecord(c->sn_ev[0][k], sa), "event"));
+            GNB_TRY(cuda_check(c, cudaStreamWaitEvent(sb, c->sn_ev[0][k], 0), "event wait"));
+            GNB_TRY(unet_run(net, r1 - r0, sb, xin + (size_t)r0 * V * 16, yout + (size_t)r0 * V * cout));
+            GNB_TRY(cuda_check(c, cudaEventRecord(c->sn_ev[1][k], sb), "event"));
+            GNB_TRY(cuda_check(c, cudaStreamWaitEvent(sc, c->sn_ev[1][k], 0), "event wait"));
+            GNB_TRY(remap_regions_launch(c, r0, r1, side, grid, yout, cout, sweeps, sc));
+        }
+        // join: the context's stream continues after the last remap
+        GNB_TRY(cuda_check(c, cudaEventRecord(c->sn_ev[2][0], sc), "event"));
+        return cuda_check(c, cudaStreamWaitEvent(sa, c->sn_ev[2][0], 0), "event wait");
+    };
+    // with the phase timers on, the batch runs eagerly and in sequence (no
+    // graph, one chunk) so that each stage's events are recorded
+    if (c->timing || c->s == nullptr) return issue();
+    if (!use_graph) return nch > 1 ? issue_pipelined() : issue();
     if (c->sn_graph) {
         cudaGraphExecDestroy(c->sn_graph);
         c->sn_graph = nullptr;
     }
     cudaGraph_t g = nullptr;
     GNB_TRY(cuda_check(c, cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal), "begin capture"));
-    int rc = issue();
+    int rc = nch > 1 ? issue_pipelined() : issue();
     cudaError_t e = cudaStreamEndCapture(c->s, &g);
     if (rc != GNB_OK) { if (g) cudaGraphDestroy(g); return rc; }
     GNB_TRY(cuda_check(c, e, "end capture"));
     e = cudaGraphInstantiate(&c->sn_graph, g, 0);
     cudaGraphDestroy(g);
     GNB_TRY(cuda_check(c, e, "graph instantiate"));
-    c->sn_key[0] = nreg; c->sn_key[1] = grid; c->sn_key[2] = sweeps;
+    c->sn_key[0] = nreg; c->sn_key[1] = grid; c->sn_key[2] = sweeps; c->sn_key[3] = nch;
     c->sn_net = net; c->sn_side = side; c->sn_n = c->n; c->sn_cur = c->cur; c->sn_gen = c->sur_gen;
     return cuda_check(c, cudaGraphLaunch(c->sn_graph, c->s), "surrogate graph launch");
 }

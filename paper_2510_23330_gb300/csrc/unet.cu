@@ -789,10 +789,12 @@ void conv_wgrad(gnb_unet *u, const ULayer &ly, int mode, int B, int D, const bf1
     counted(k_colsum)<<<120, threads, 0, u->s>>>(g, V, Vs, Cg, ly.cout, u->g + ly.boff);
 }
 
-int unet_forward(gnb_unet *u, int B)
+// Forward pass of B regions from the blocked BF16 input xin to the FP32
+// output yout (defaults: the network's own buffers).
+int unet_forward(gnb_unet *u, int B, const bf16 *xin = nullptr, float *yout = nullptr)
 {
     int G = u->grid;
-    const bf16 *h = u->xin;
+    const bf16 *h = xin ? xin : u->xin;
     int ch = 16;
     for (int l = 0; l < u->levels; l++) {
         int D = G >> l, w = width(u, l);
@@ -818,7 +820,7 @@ int unet_forward(gnb_unet *u, int B)
                  nullptr, 1);
         h = u->act[S_DECB(u, l)];
     }
-    conv_fwd(u, u->L[LI_HEAD(u)], IG_CONV1, B, G, h, u->base, nullptr, 0, nullptr, u->yout, 0);
+    conv_fwd(u, u->L[LI_HEAD(u)], IG_CONV1, B, G, h, u->base, nullptr, 0, nullptr, yout ? yout : u->yout, 0);
     return cudaGetLastError() == cudaSuccess && !u->launch_failed ? GNB_OK : GNB_ECUDA;
 }
 
@@ -912,8 +914,9 @@ int unet_check(gnb_unet *u, int rc)
 namespace gnb {
 // Hooks for the batched surrogate step: make room for `batch` regions and
 // expose the blocked BF16 input [batch][2][grid^3][8] and the FP32 output
-// [batch][grid^3][cout]; unet_run launches the forward pass on `stream`
-// without synchronising (so it can be captured in a CUDA graph).
+// [batch][grid^3][cout]; unet_run launches the forward pass of `batch`
+// regions on `stream` without synchronising (so it can be captured in a CUDA
+// graph), from xin to yout (null: those buffers' starts).
 int unet_prepare(gnb_unet *u, int batch, bf16 **xin, float **yout, int *grid, int *cout)
 {
     int rc = unet_alloc_acts(u, batch);
@@ -934,11 +937,11 @@ int unet_poll_error(gnb_unet *u)
     return GNB_ETIMEOUT;
 }
 
-int unet_run(gnb_unet *u, int batch, cudaStream_t stream)
+int unet_run(gnb_unet *u, int batch, cudaStream_t stream, const bf16 *xin, float *yout)
 {
     cudaStream_t keep = u->s;
     u->s = stream;
-    int rc = unet_forward(u, batch);
+    int rc = unet_forward(u, batch, xin, yout);
     u->s = keep;
     return rc;
 }

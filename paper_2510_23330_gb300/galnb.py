@@ -88,6 +88,8 @@ def _declare(L):
     L.gnb_last_error.restype = C.c_char_p
     L.gnb_set_timing.argtypes = [_vp, C.c_int]
     L.gnb_set_timing.restype = C.c_int
+    L.gnb_set_sn_chunks.argtypes = [_vp, C.c_int]
+    L.gnb_set_sn_chunks.restype = C.c_int
     L.gnb_phase_times.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                   C.c_int]
     L.gnb_phase_times.restype = C.c_int
@@ -340,6 +342,10 @@ def gnb_set_timing(ctx, enable):
     return lib().gnb_set_timing(ctx, enable)
 
 
+def gnb_set_sn_chunks(ctx, chunks):
+    return lib().gnb_set_sn_chunks(ctx, chunks)
+
+
 def gnb_phase_times(ctx, out_ms, calls, launches, reset):
     return lib().gnb_phase_times(ctx, out_ms, calls, launches, reset)
 
@@ -535,6 +541,9 @@ class Context:
 
     def set_timing(self, enable=True):
         self._chk(gnb_set_timing(self.h, 1 if enable else 0))
+
+    def set_sn_chunks(self, chunks):
+        self._chk(gnb_set_sn_chunks(self.h, int(chunks)))
 
     def phase_times(self, reset=False):
         """({phase: ms}, {phase: timed occurrences}, library kernel launches)."""

@@ -110,3 +110,59 @@ def test_batched_surrogate_step_invariants(G, orc):
         c.sn_surrogate_batch(net, offs, side=60.0, seed=2, sweeps=8, use_graph=True)
         assert np.all(np.isfinite(c.get("X")))
     stream.synchronize()
+
+
+def test_pipelined_batch_matches_sequential(G, orc):
+    """The batch pipelined over region chunks (voxelise / U-Net / remap of
+    different chunks on three streams, one captured graph) against the same
+    batch with its stages in sequence.  Without Gibbs sweeps each member
+    keeps its voxel and draws a new offset inside it, so positions must be
+    bit-identical; u and v come from that voxel's prediction.  The voxel sums
+    are FP32 reductions in no fixed order, and the last-bit differences reach
+    the network's BF16 input, so two sequential runs already differ: the
+    pipelined run must differ from a sequential one no more than two
+    sequential runs do (a chunk that read another chunk's grid or
+    predictions would differ by far more)."""
+    from oracle import unet as U
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        regions = [ics.sn_region(6000 + 2000 * k, seed=30 + k, grid=32) for k in range(5)]
+        offs = [(150.0 * k, 40.0 * k, 0.0) for k in range(5)]
+        parts = {}
+        for r, o in zip(regions, offs):
+            r = dict(r)
+            r["x"] = r["x"] + o[0]
+            r["y"] = r["y"] + o[1]
+            for key, val in r.items():
+                parts.setdefault(key, []).append(val)
+        p = {k: np.concatenate(v) for k, v in parts.items()}
+        p["id"] = np.arange(p["x"].size, dtype=np.int64)
+        net = G.UNet(5, 5, 16, 4, 32, stream=stream.cuda_stream)
+        spec = U.layer_spec(5, 5, 16, 4)
+        prm = U.init_params(3, 5, 5, 16, 4)
+        net.set_params(np.concatenate([np.concatenate([prm[n + ".w"].ravel(), prm[n + ".b"]])
+                                       for n, *_ in spec]).astype(np.float32))
+        out = []
+        for chunks in (1, 1, 3):
+            c = G.Context(stream=stream.cuda_stream)
+            c.set_particles(p)
+            c.set_sn_chunks(chunks)
+            c.compute_sph_density()
+            c.sn_surrogate_batch(net, offs, side=60.0, seed=5, sweeps=0, use_graph=True)
+            out.append({k: c.get(k) for k in ("X", "Y", "Z", "U", "VX", "VY", "VZ", "ID")})
+            c.close()
+    stream.synchronize()
+    s1, s2, pp = out
+    assert np.array_equal(pp["ID"], p["id"])
+    assert (pp["X"] != p["x"]).mean() > 0.9  # the members were remapped
+    for k in ("X", "Y", "Z"):
+        assert np.array_equal(s1[k], pp[k]) and np.array_equal(s1[k], s2[k])
+
+    def spread(a, b):
+        d = [np.abs(a["U"] / b["U"] - 1.0)] + [np.abs(a[k] - b[k]) / 20.0 for k in ("VX", "VY", "VZ")]
+        return np.median(np.concatenate(d)), max(float(np.max(x)) for x in d)
+
+    med_ss, max_ss = spread(s1, s2)
+    med_sp, max_sp = spread(s1, pp)
+    assert med_sp <= 2.0 * med_ss + 2e-3 and max_sp <= 2.0 * max_ss + 0.05, (med_sp, med_ss, max_sp, max_ss)
