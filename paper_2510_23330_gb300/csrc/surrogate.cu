@@ -41,9 +41,11 @@ __device__ __forceinline__ uint64_t sm64(uint64_t x)
     return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ double uniform01(uint64_t seed, uint64_t id, uint64_t k)
+// Draw k of a particle whose stream is sid = splitmix64(seed + id): a uniform
+// double in [0, 1) from the top 53 bits of splitmix64(sid + k).
+__device__ __forceinline__ double uniform_draw(uint64_t sid, uint64_t k)
 {
-    return (double)(sm64(sm64(seed + id) + k) >> 11) * (1.0 / 9007199254740992.0);
+    return (double)(sm64(sid + k) >> 11) * (1.0 / 9007199254740992.0);
 }
 
 // counter[key] += 1 for every active lane, one atomic per distinct key in
@@ -277,8 +279,9 @@ __global__ void k_line_cdf(const double *__restrict__ w, int nreg, int grid, dou
 
 __global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float *__restrict__ pred, int cout,
                         const double *__restrict__ cdf, const float *__restrict__ cdf32,
-                        const float *__restrict__ cdfc, const double *__restrict__ cent, double side, int grid,
-                        const unsigned long long *__restrict__ seedp, int sweeps, int r0, int r1)
+                        const float *__restrict__ cdfc, const double *__restrict__ cent, double side, double d,
+                        double inv_d, int grid, const unsigned long long *__restrict__ seedp, int sweeps, int r0,
+                        int r1)
 {
     // members of regions [r0, r1); the line sums hold those regions
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -286,12 +289,19 @@ __global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float 
     int r = reg[i];
     if (r < r0 || r >= r1) return;
     uint64_t seed = *seedp;
-    double d = side / grid;
+    // d = side / grid and inv_d = 1 / d come from the host (two FP64
+    // divides per thread would cost more than the rest of the FP64 work)
     double lo[3] = {cent[3 * r] - 0.5 * side, cent[3 * r + 1] - 0.5 * side, cent[3 * r + 2] - 0.5 * side};
     double pp[3] = {p.x[i], p.y[i], p.z[i]};
     int c[3];
     for (int a = 0; a < 3; a++) {
-        double f = floor(__ddiv_rn(__dsub_rn(pp[a], lo[a]), d));
+        // floor of the rounded quotient (q / d): q inv_d is within ~1e-14 of
+        // it, so its floor is the same unless it lies within 1e-9 of an
+        // integer, where the divide decides
+        const double q = __dsub_rn(pp[a], lo[a]);
+        const double g = q * inv_d;
+        double f = floor(g);
+        if (g - f < 1e-9 || f + 1.0 - g < 1e-9) f = floor(__ddiv_rn(q, d));
         c[a] = f < 0.0 ? 0 : (f > (double)(grid - 1) ? grid - 1 : (int)f);
     }
     const size_t G = (size_t)grid;
@@ -376,13 +386,16 @@ __global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float 
         }
     }
     double np[3];
-    for (int a = 0; a < 3; a++) np[a] = lo[a] + (c[a] + uniform01(seed, id, (uint64_t)(3 * sweeps + a))) * d;
+    for (int a = 0; a < 3; a++) {
+        np[a] = lo[a] + (c[a] + uniform_draw(sid, (uint64_t)(3 * sweeps + a))) * d;
+    }
     p.x[i] = np[0];
     p.y[i] = np[1];
     p.z[i] = np[2];
     const float *pv = pred + ((((size_t)r * grid + c[2]) * grid + c[1]) * grid + c[0]) * cout;
-    double T = exp10(2.0 * (double)pv[1] + 2.0);
-    p.u[i] = (float)(T / SUR_T_PER_U);
+    // u = 10^(2 z1 + 2) / T_PER_U in FP32: 2 z1 is exact, exp10f is within
+    // 2 ulp, and the product with 100 / T_PER_U adds one rounding
+    p.u[i] = exp10f(2.f * pv[1]) * (float)(100.0 / SUR_T_PER_U);
     p.vx[i] = 20.f * pv[2];
     p.vy[i] = 20.f * pv[3];
     p.vz[i] = 20.f * pv[4];
@@ -504,7 +517,8 @@ static int remap_regions_launch(gnb_ctx *c, int r0, int r1, double side, int gri
     counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(c->vw, r1 - r0, grid, c->vcdf, c->vcdf32,
                                                                       c->vcdfc);
     counted(k_remap)<<<(n + 127) / 128, 128, 0, st>>>(c->P[c->cur], n, c->sreg, pred, cout, c->vcdf, c->vcdf32,
-                                                      c->vcdfc, c->cent_d, side, grid, c->seed_d, sweeps, r0, r1);
+                                                      c->vcdfc, c->cent_d, side, side / grid, 1.0 / (side / grid), grid,
+                                                      c->seed_d, sweeps, r0, r1);
     GNB_LAUNCH_CHECK(c, "remap");
     return GNB_OK;
 }
