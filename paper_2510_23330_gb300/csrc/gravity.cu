@@ -40,6 +40,7 @@ struct GravParams {
     float *ax, *ay, *az, *pot;
     const double *box;
     double theta2;
+    long long open_d2max[GNB_MAXLEV + 1];  // per level: largest d2 that opens a cell (see must_open)
     float G;
     int quad;
     int n;
@@ -66,7 +67,14 @@ struct GravSmem {
     int g;
 };
 
-__device__ __forceinline__ bool must_open(int4 C, int level, const int *bmin, const int *bmax, double theta2)
+// A cell of `level` must be opened for a group when their boxes overlap or
+// when (2 s)^2 > theta^2 d2 in FP64 (s the cell side and d2 the squared
+// distance between the cell centre and the group box, both in doubled grid
+// units).  That FP64 test is monotone in the integer d2, so the host finds,
+// with the same FP64 arithmetic, the largest d2 that passes it for each
+// level; the walk then compares integers (no FP64 per visited cell).
+__device__ __forceinline__ bool must_open(int4 C, int level, const int *bmin, const int *bmax,
+                                          const long long *d2max)
 {
     long long s = 1ll << (GNB_MAXLEV - level);
     bool overlap = true;
@@ -82,9 +90,7 @@ __device__ __forceinline__ bool must_open(int4 C, int level, const int *bmin, co
         else if (cen > 2 * b1) d = cen - 2 * b1;
         d2 += d * d;
     }
-    if (overlap) return true;
-    double lhs = (double)(2 * s) * (double)(2 * s);
-    return lhs > theta2 * (double)d2;
+    return overlap || d2 <= d2max[level];
 }
 
 // Particle-particle: accumulate sum m_j (x_j - x_i)/R^3 and sum m_j/R, with
@@ -314,8 +320,11 @@ __device__ __forceinline__ void chain_append_leaf(bool flag, int first, int coun
 __global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
 {
     __shared__ int stack[GL_WARPS][GL_STACK];
+    __shared__ long long d2max[GNB_MAXLEV + 1];  // lanes index it by level: shared, not the parameter bank
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int *st = stack[w];
+    for (int l = threadIdx.x; l <= GNB_MAXLEV; l += blockDim.x) d2max[l] = p.open_d2max[l];
+    __syncthreads();
     const int ngroups = *p.ngroups;
     unsigned long long cnt_pp = 0, cnt_pc = 0;
     for (;;) {
@@ -357,7 +366,7 @@ __global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
             if (node >= 0) {
                 const int4 a = __ldg(&p.na[node]);
                 const int lev = a.w & 255;
-                const bool open = node == 0 || must_open(__ldg(&p.nb[node]), lev, bmin, bmax, p.theta2);
+                const bool open = node == 0 || must_open(__ldg(&p.nb[node]), lev, bmin, bmax, d2max);
                 if (!open) is_cell = true;
                 else if ((a.w >> 8) == 0) { is_leaf = true; lcount = a.y; lfirst = a.x; }
                 else { nch = a.w >> 8; child0 = a.z; }
@@ -607,6 +616,23 @@ static GravParams make_params(gnb_ctx *c)
     p.ax = c->gax; p.ay = c->gay; p.az = c->gaz; p.pot = c->pot;
     p.box = c->box_d;
     p.theta2 = c->cfg.theta * c->cfg.theta;
+    for (int l = 0; l <= GNB_MAXLEV; l++) {
+        // largest d2 with (2 s)^2 > theta2 * (double)d2 (the test is monotone
+        // in d2; (double)d2 rounds the same way here and on the device)
+        const long long sz = 1ll << (GNB_MAXLEV - l);
+        const double lhs = (double)(2 * sz) * (double)(2 * sz);
+        long long lo = 0, hi = (1ll << 62);
+        if (!(lhs > p.theta2 * (double)hi)) {
+            while (hi - lo > 1) {  // invariant: lo passes, hi fails
+                const long long mid = lo + (hi - lo) / 2;
+                if (lhs > p.theta2 * (double)mid) lo = mid;
+                else hi = mid;
+            }
+            p.open_d2max[l] = lo;
+        } else {
+            p.open_d2max[l] = hi;  // theta = 0: every cell opens
+        }
+    }
     p.G = (float)c->cfg.G;
     p.quad = c->cfg.multipole;
     p.n = (int)c->n;

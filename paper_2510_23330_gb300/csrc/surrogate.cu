@@ -345,7 +345,13 @@ __global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float 
             };
             auto setup = [&](float tot32) {
                 fast = m >= (1ull << 45) && tot32 >= 0x1p-90f && tot32 <= 0x1p100f;
-                const float t32 = __fmul_rn(__uint2float_rn((unsigned)(m >> 21)), tot32 * 0x1p-32f);
+                // float(M), M = m >> 21 < 2^32, rounded to nearest, on the FP32
+                // pipes: its two 16-bit halves are exact as 2^23 + x - 2^23, and
+                // one FMA joins them with a single rounding
+                const unsigned M = (unsigned)(m >> 21);
+                const float mh = __int_as_float(0x4B000000 | (int)(M >> 16)) - 8388608.f;
+                const float ml = __int_as_float(0x4B000000 | (int)(M & 0xFFFFu)) - 8388608.f;
+                const float t32 = __fmul_rn(__fmaf_rn(mh, 65536.f, ml), tot32 * 0x1p-32f);
                 lo32 = __fmul_rn(t32, 1.f - 0x1p-20f);
                 hi32 = __fmul_rn(t32, 1.f + 0x1p-20f);
             };
