@@ -210,8 +210,9 @@ def sn_regions(nreg, distinct, lo, hi, seed):
     return p, centers, np.asarray(counts)
 
 
-def sn_bench(stream, galnb, torch, nreg=256, reps=3):
-    """SN regions/s: batched surrogate vs plain integration (see module doc)."""
+def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True):
+    """SN regions/s: batched surrogate vs plain integration (see module doc).
+    nreg and plain_runs=False only serve profiling (--sn-only --sn-regions)."""
     from paper_2510_23330_gb300 import surrogate as S
     sp = stream.cuda_stream
     net = galnb.UNet(5, 5, 16, 4, 64, stream=sp)
@@ -257,10 +258,10 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3):
     net.close()
     # --- plain: CFL-limited integration of a 1e5-particle region over 0.1 Myr
     plain = []
-    for seed in (1900, 1901):
+    for seed in ((1900, 1901) if plain_runs else ()):
         _, _, info = S.make_pair(seed, n=100000, grid=64, stream=sp)
         plain.append(info)
-    plain_s = float(np.median([i["seconds"] for i in plain]))
+    plain_s = float(np.median([i["seconds"] for i in plain])) if plain else float("nan")
     sur_ms = float(np.median(ms))
     kv = read_kv(SN_REPORT)
     try:
@@ -396,7 +397,7 @@ def run_ours(args, world, rank, local):
                    "gravity": "tree" if mode == 1 else "direct", **pr["cfg"], "n_ngb": 64,
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": "k_gravity_tree (walk + PP/PC)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_grav_walk + k_grav_eval (walk, PP/PC)", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": traffic,
                      "note": (f"flops = {FLOP_PP}/PP + {FLOP_PC}/PC interaction; peak = 152 SMs x 128 lanes x 2 x "
@@ -492,6 +493,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--n-group", type=int, default=0, help="fixed group size n_g (skips the autotuner)")
     ap.add_argument("--no-sn", action="store_true", help="skip the supernova surrogate-vs-plain section")
+    ap.add_argument("--sn-only", action="store_true",
+                    help="profiling: only the supernova section, printed alone (not the bench line)")
+    ap.add_argument("--sn-regions", type=int, default=256, help="regions of the --sn-only batch")
+    ap.add_argument("--sn-no-plain", action="store_true", help="--sn-only without the plain integrations")
     args = ap.parse_args()
     if args.impl == "reference":
         # the CPU checker runs once, on rank 0; other ranks exit without work
@@ -500,6 +505,13 @@ def main():
         out = run_reference(args, world, rank, 0)
         if out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.sn_only:
+        import torch
+        from paper_2510_23330_gb300 import galnb
+        stream = torch.cuda.current_stream(torch.device("cuda", 0))
+        out = sn_bench(stream, galnb, torch, nreg=args.sn_regions, plain_runs=not args.sn_no_plain)
+        print(json.dumps(out), flush=True)
         return
     world, rank, local = dist_init()
     out = run_ours(args, world, rank, local)
