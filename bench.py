@@ -149,22 +149,28 @@ def gravity_traffic():
         return None
 
 
-def cpu_baseline(p, name):
-    """The FP64 oracle on a bounded sample of one force evaluation: the full
-    tree build plus every 16th group's walk (scaled by 16) and brute-force kNN
-    for 64 sampled gas particles (scaled to all gas)."""
+def cpu_baseline(p, name, knn_seconds=6.0):
+    """The FP64 oracle on a bounded sample of one force evaluation (about
+    10 s of CPU work at 2^20): the full tree build plus every 4th group's walk
+    (scaled by 4) and brute-force kNN of as many sampled gas particles as
+    take about knn_seconds (scaled to all gas)."""
     import oracle
     oracle.build()
     n = p["x"].shape[0]
     gi = np.nonzero(p["type"] == 1)[0]
-    stride = 16 if n > 100000 else 1
+    stride = 4 if n > 100000 else 1
     t0 = time.perf_counter()
     tb, tw, st = oracle.tree_gravity_sampled(p, stride, theta=0.5, n_leaf=16, n_g=64, quad=True)
     t_grav = tb + tw * stride
-    ns = min(64, gi.size)
-    rng = np.random.default_rng(0)
-    s = np.sort(rng.choice(gi.size, ns, replace=False))
     g = {k: np.asarray(p[k][gi], np.float64) for k in ("x", "y", "z")}
+    rng = np.random.default_rng(0)
+    # calibrate on 64 particles, then time a sample sized to about knn_seconds
+    ns = min(64, gi.size)
+    t1 = time.perf_counter()
+    oracle.knn(g, 64, sample=np.sort(rng.choice(gi.size, ns, replace=False)))
+    t64 = max(time.perf_counter() - t1, 1e-4)
+    ns = int(min(gi.size, max(ns, ns * knn_seconds / t64)))
+    s = np.sort(rng.choice(gi.size, ns, replace=False))
     t1 = time.perf_counter()
     oracle.knn(g, 64, sample=s)
     t_knn = (time.perf_counter() - t1) * gi.size / ns
