@@ -347,6 +347,30 @@ int gnb_remap_regions(gnb_ctx *ctx, int nreg, const double *centers, double side
 int gnb_sn_surrogate_batch(gnb_ctx *ctx, gnb_unet *net, int nreg, const double *centers, double side,
                            uint64_t seed, int sweeps, int use_graph);
 
+/* Asynchronous surrogate batch: the pool nodes' role in Sec. 3.2 (steps
+ * 2-4), where the supernova regions are handed off, predicted while the
+ * global integration goes on, and returned 0.1 Myr (50 global steps) later.
+ * gnb_sn_async_submit takes a snapshot of the members of the nreg regions
+ * (the same membership rule as gnb_voxelise) on the context's stream -- their
+ * state, caller index and ID -- and then voxelises the snapshot, runs the
+ * U-Net (net) and builds the remap's line sums on a second stream; it
+ * returns without waiting.  The context's steps may run meanwhile.
+ * gnb_sn_async_apply waits for that work and replaces every snapshot member,
+ * found at its current position in the arrays by its caller index, exactly
+ * as gnb_remap_regions would: sweeps Gibbs sweeps on the prediction starting
+ * from the voxel of its snapshot position, with draws from (seed, ID); u
+ * and v from the drawn voxel.  One batch can be pending per context; while
+ * it is, gnb_set_particles, gnb_voxelise, gnb_remap_regions and
+ * gnb_sn_surrogate_batch return GNB_ESTATE, and net must not be used.
+ * Requires gnb_compute_sph_density at the current positions for the submit.
+ * gnb_sn_async_pending returns 1 while a batch is pending, else 0.
+ * Errors: GNB_EINVAL, GNB_ESTATE (a batch pending at submit, none at apply),
+ * GNB_ENOMEM, GNB_ECUDA, GNB_ETIMEOUT (as gnb_unet_forward). */
+int gnb_sn_async_submit(gnb_ctx *ctx, gnb_unet *net, int nreg, const double *centers, double side, uint64_t seed,
+                        int sweeps);
+int gnb_sn_async_apply(gnb_ctx *ctx);
+int gnb_sn_async_pending(const gnb_ctx *ctx);
+
 /* Number of region chunks the batched surrogate step pipelines (1 to 16;
  * default 1, the stages in sequence): with k > 1 chunks, chunk i is
  * voxelised on the context's stream, goes through the U-Net on a second

@@ -279,6 +279,15 @@ void gnb_destroy(gnb_ctx *c)
                        c->rsx,  c->rsi,    c->centf, c->vpa, c->vpb, c->vpc,  c->vbox, c->vcdf32, c->vcdfc};
         for (void *q : sur) dfree(c, q);
         if (c->sn_graph) cudaGraphExecDestroy(c->sn_graph);
+        if (c->sna_st) {
+            cudaStreamSynchronize(c->sna_st);  // a pending batch's work ends before its buffers go
+            cudaStreamDestroy(c->sna_st);
+        }
+        if (c->sna_ev_snap) cudaEventDestroy(c->sna_ev_snap);
+        if (c->sna_ev_done) cudaEventDestroy(c->sna_ev_done);
+        void *sna[] = {c->sna_x, c->sna_y, c->sna_z, c->sna_h2, c->sna_m, c->sna_u, c->sna_vx, c->sna_vy, c->sna_vz,
+                       c->sna_rho, c->sna_reg, c->sna_orig, c->sna_pos, c->sna_inv, c->sna_id, c->sna_seed};
+        for (void *q : sna) dfree(c, q);
         for (cudaStream_t st : c->sn_st)
             if (st) cudaStreamDestroy(st);
         for (auto &row : c->sn_ev)
@@ -298,6 +307,7 @@ int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *t
     if (!c) return GNB_EINVAL;
     c->err.clear();
     if (n < 1 || n > (1ll << 30)) return fail(c, GNB_EINVAL, "particle count out of range");
+    if (c->sna_pending) return fail(c, GNB_ESTATE, "an asynchronous surrogate batch is pending");
     if (!id || !type || !x || !y || !z || !vx || !vy || !vz || !m || !eps || !u)
         return fail(c, GNB_EINVAL, "null array");
     c->have_particles = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = false;
@@ -662,6 +672,7 @@ int gnb_voxelise(gnb_ctx *c, int nreg, const double *centers, double side, int g
     if (nreg < 1 || !centers || !out || !(side > 0.0) || grid < 1 || grid > 256)
         return fail(c, GNB_EINVAL, "regions, side or grid");
     if (!c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed for the current positions");
+    if (c->sna_pending) return fail(c, GNB_ESTATE, "an asynchronous surrogate batch is pending");
     int rc = voxelise(c, nreg, centers, side, grid, on_device ? out : nullptr);
     if (rc == GNB_OK && !on_device)
         rc = cuda_check(c, cudaMemcpyAsync(out, c->vout, sizeof(float) * 5 * (size_t)nreg * grid * grid * grid,
@@ -677,6 +688,7 @@ int gnb_remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, 
     if (nreg < 1 || !centers || !pred || !(side > 0.0) || grid < 1 || grid > 256 || sweeps < 0)
         return fail(c, GNB_EINVAL, "regions, side, grid or sweeps");
     if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    if (c->sna_pending) return fail(c, GNB_ESTATE, "an asynchronous surrogate batch is pending");
     const float *pd = pred;
     int rc = GNB_OK;
     if (!on_device) {
@@ -698,6 +710,7 @@ int gnb_sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *ce
     c->err.clear();
     if (!net || nreg < 1 || !centers || !(side > 0.0) || sweeps < 0) return fail(c, GNB_EINVAL, "arguments");
     if (!c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed for the current positions");
+    if (c->sna_pending) return fail(c, GNB_ESTATE, "an asynchronous surrogate batch is pending");
     int rc = sn_surrogate_batch(c, net, nreg, centers, side, seed, sweeps, use_graph);
     c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
     rc = finish(c, rc);
@@ -790,6 +803,31 @@ int gnb_set_timing(gnb_ctx *c, int enable)
     c->timing = enable != 0;
     return GNB_OK;
 }
+
+int gnb_sn_async_submit(gnb_ctx *c, gnb_unet *net, int nreg, const double *centers, double side, uint64_t seed,
+                        int sweeps)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!net || nreg < 1 || !centers || !(side > 0.0) || sweeps < 0) return fail(c, GNB_EINVAL, "arguments");
+    if (!c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed for the current positions");
+    int rc = sn_async_submit(c, net, nreg, centers, side, seed, sweeps);
+    return finish(c, rc);
+}
+
+int gnb_sn_async_apply(gnb_ctx *c)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    int rc = sn_async_apply(c);
+    if (rc == GNB_OK) c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    rc = finish(c, rc);
+    if (rc == GNB_OK && unet_poll_error((gnb_unet *)c->sna_net) != GNB_OK)
+        return fail(c, GNB_ETIMEOUT, "a bounded wait in the U-Net's tensor-core convolution ran out");
+    return rc;
+}
+
+int gnb_sn_async_pending(const gnb_ctx *c) { return c && c->sna_pending ? 1 : 0; }
 
 int gnb_set_sn_chunks(gnb_ctx *c, int chunks)
 {

@@ -174,6 +174,23 @@ struct gnb_ctx {
     cudaStream_t sn_st[2] = {nullptr, nullptr};
     cudaEvent_t sn_ev[3][SN_MAXCH] = {};
     int sn_chunks = 1;                // region chunks of the pipelined batch (1: stages in sequence)
+    // asynchronous surrogate batch (submitted now, applied later): a snapshot
+    // of the region members (state, caller index, ID, region), worked on a
+    // side stream; sna_inv maps caller index -> current slot at apply time
+    bool sna_pending = false;
+    int sna_nreg = 0, sna_grid = 0, sna_sweeps = 0;
+    double sna_side = 0.0;
+    void *sna_net = nullptr;
+    int64_t sna_cap = 0;
+    double *sna_x = nullptr, *sna_y = nullptr, *sna_z = nullptr, *sna_h2 = nullptr;
+    float *sna_m = nullptr, *sna_u = nullptr, *sna_vx = nullptr, *sna_vy = nullptr, *sna_vz = nullptr;
+    float *sna_rho = nullptr;
+    int *sna_reg = nullptr, *sna_orig = nullptr, *sna_pos = nullptr, *sna_inv = nullptr;
+    int64_t *sna_id = nullptr;
+    unsigned long long *sna_seed = nullptr;
+    float *sna_yout = nullptr;    // the network's predictions of the pending batch
+    cudaStream_t sna_st = nullptr;
+    cudaEvent_t sna_ev_snap = nullptr, sna_ev_done = nullptr;
     int sn_key[4] = {0, 0, 0, 0};
     void *sn_net = nullptr;
     double sn_side = 0.0;
@@ -266,6 +283,9 @@ int remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, int 
 // GNB_ETIMEOUT (and clears it) when a tensor-core convolution of the network
 // recorded a bounded wait that ran out; the caller has synchronised.
 int unet_poll_error(gnb_unet *u);
+int sn_async_submit(gnb_ctx *c, gnb_unet *net, int nreg, const double *centers, double side, uint64_t seed,
+                    int sweeps);
+int sn_async_apply(gnb_ctx *c);
 int sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *centers, double side, uint64_t seed,
                        int sweeps, int use_graph);
 // sn.cu

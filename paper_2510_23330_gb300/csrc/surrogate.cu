@@ -277,7 +277,11 @@ __global__ void k_line_cdf(const double *__restrict__ w, int nreg, int grid, dou
     }
 }
 
-__global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float *__restrict__ pred, int cout,
+// Members are read from `p` (positions, ID; region in reg) and their new
+// state is written to `q` at slot dst(i) = map ? map[src_orig[i]] : i (the
+// asynchronous batch reads a snapshot and writes the current arrays).
+__global__ void k_remap(PArr p, PArr q, const int *__restrict__ src_orig, const int *__restrict__ map, int n,
+                        const int *__restrict__ reg, const float *__restrict__ pred, int cout,
                         const double *__restrict__ cdf, const float *__restrict__ cdf32,
                         const float *__restrict__ cdfc, const double *__restrict__ cent, double side, double d,
                         double inv_d, int grid, const unsigned long long *__restrict__ seedp, int sweeps, int r0,
@@ -395,16 +399,17 @@ __global__ void k_remap(PArr p, int n, const int *__restrict__ reg, const float 
     for (int a = 0; a < 3; a++) {
         np[a] = lo[a] + (c[a] + uniform_draw(sid, (uint64_t)(3 * sweeps + a))) * d;
     }
-    p.x[i] = np[0];
-    p.y[i] = np[1];
-    p.z[i] = np[2];
+    const int o = map ? map[src_orig[i]] : i;
+    q.x[o] = np[0];
+    q.y[o] = np[1];
+    q.z[o] = np[2];
     const float *pv = pred + ((((size_t)r * grid + c[2]) * grid + c[1]) * grid + c[0]) * cout;
     // u = 10^(2 z1 + 2) / T_PER_U in FP32: 2 z1 is exact, exp10f is within
     // 2 ulp, and the product with 100 / T_PER_U adds one rounding
-    p.u[i] = exp10f(2.f * pv[1]) * (float)(100.0 / SUR_T_PER_U);
-    p.vx[i] = 20.f * pv[2];
-    p.vy[i] = 20.f * pv[3];
-    p.vz[i] = 20.f * pv[4];
+    q.u[o] = exp10f(2.f * pv[1]) * (float)(100.0 / SUR_T_PER_U);
+    q.vx[o] = 20.f * pv[2];
+    q.vy[o] = 20.f * pv[3];
+    q.vz[o] = 20.f * pv[4];
 }
 
 // ---------------------------------------------------------------- host
@@ -486,21 +491,27 @@ static void assign_launch(gnb_ctx *c, int nreg, double side, cudaStream_t st)
 // Accumulators of regions [r0, r1) (membership already assigned); their
 // finalised channels go to `out` (FP32 [nreg][grid^3][5]) and/or `outb`
 // (BF16 U-Net input), both indexed from region 0.
-static int vox_regions(gnb_ctx *c, int r0, int r1, double side, int grid, float *out, bf16 *outb, cudaStream_t st)
+// The members are read from the view (a, n, reg, rho): the context's current
+// particles, or the asynchronous batch's snapshot.
+static int vox_regions_view(gnb_ctx *c, const PArr &a, int n, const int *reg, const float *rho, int r0, int r1,
+                            double side, int grid, float *out, bf16 *outb, cudaStream_t st)
 {
-    int n = (int)c->n;
-    PArr &a = c->P[c->cur];
     const long long V = (long long)grid * grid * grid;
     size_t nv = (size_t)(r1 - r0) * V;
     cudaMemsetAsync(c->vacc, 0, sizeof(float) * nv * 8, st);
-    counted(k_vox_stage)<<<(n + 255) / 256, 256, 0, st>>>(a, n, c->sreg, r0, r1, c->rho, c->cent_d, side, grid,
-                                                          c->vpa, c->vpb, c->vpc, c->vbox);
-    counted(k_vox_scatter)<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, c->sreg, r0, r1, c->vpa, c->vpb, c->vpc,
+    counted(k_vox_stage)<<<(n + 255) / 256, 256, 0, st>>>(a, n, reg, r0, r1, rho, c->cent_d, side, grid, c->vpa,
+                                                          c->vpb, c->vpc, c->vbox);
+    counted(k_vox_scatter)<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, reg, r0, r1, c->vpa, c->vpb, c->vpc,
                                                                        c->vbox, side, grid, c->vacc);
     counted(k_vox_finalize)<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(
         c->vacc, (long long)nv, V, out ? out + (size_t)r0 * V * 5 : nullptr, outb ? outb + (size_t)r0 * V * 16 : nullptr);
     GNB_LAUNCH_CHECK(c, "voxelise");
     return GNB_OK;
+}
+
+static int vox_regions(gnb_ctx *c, int r0, int r1, double side, int grid, float *out, bf16 *outb, cudaStream_t st)
+{
+    return vox_regions_view(c, c->P[c->cur], (int)c->n, c->sreg, c->rho, r0, r1, side, grid, out, outb, st);
 }
 
 static int vox_launch(gnb_ctx *c, int nreg, double side, int grid, float *out, bf16 *outb)
@@ -522,7 +533,8 @@ static int remap_regions_launch(gnb_ctx *c, int r0, int r1, double side, int gri
     long long nl = (long long)(r1 - r0) * 3 * grid * grid;
     counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(c->vw, r1 - r0, grid, c->vcdf, c->vcdf32,
                                                                       c->vcdfc);
-    counted(k_remap)<<<(n + 127) / 128, 128, 0, st>>>(c->P[c->cur], n, c->sreg, pred, cout, c->vcdf, c->vcdf32,
+    counted(k_remap)<<<(n + 127) / 128, 128, 0, st>>>(c->P[c->cur], c->P[c->cur], nullptr, nullptr, n, c->sreg, pred,
+                                                      cout, c->vcdf, c->vcdf32,
                                                       c->vcdfc, c->cent_d, side, side / grid, 1.0 / (side / grid), grid,
                                                       c->seed_d, sweeps, r0, r1);
     GNB_LAUNCH_CHECK(c, "remap");
@@ -559,6 +571,137 @@ int remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, int 
     GNB_TRY(remap_launch(c, nreg, side, grid, pred_dev, 5, sweeps));
     phase_end(c);
     return cuda_check(c, cudaStreamSynchronize(c->s), "remap sync");
+}
+
+// ------------------------------------------------------- asynchronous batch
+// The pool nodes' role (Sec. 3.2 steps 2-4): the members of the regions are
+// snapshotted when the batch is submitted; voxelise, U-Net and the remap's
+// line sums run on a side stream while the global steps go on; when the
+// batch is applied (e.g. 50 global steps = 0.1 Myr later) each member, found
+// by its caller index, is replaced by a draw from the predicted grid that
+// starts from the voxel of its snapshot position.
+
+__global__ void k_sna_flag(int n, const int *__restrict__ reg, int *__restrict__ flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = reg[i] >= 0;
+}
+
+// member i -> snapshot slot pos[i] (exclusive scan of the flags: Morton
+// order kept, which keeps the voxel reductions local)
+__global__ void k_sna_snapshot(PArr p, int n, const int *__restrict__ reg, const float *__restrict__ rho,
+                               const int *__restrict__ pos, PArr s, float *__restrict__ srho, int *__restrict__ sreg,
+                               int *__restrict__ sorig)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = reg[i];
+    if (r < 0) return;
+    const int k = pos[i];
+    s.x[k] = p.x[i]; s.y[k] = p.y[i]; s.z[k] = p.z[i]; s.h2[k] = p.h2[i];
+    s.m[k] = p.m[i]; s.u[k] = p.u[i]; s.vx[k] = p.vx[i]; s.vy[k] = p.vy[i]; s.vz[k] = p.vz[i];
+    s.id[k] = p.id[i];
+    srho[k] = rho[i];
+    sreg[k] = r;
+    sorig[k] = p.orig[i];
+}
+
+// current slot of every caller index
+__global__ void k_inverse(const int *__restrict__ orig, int n, int *__restrict__ inv)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) inv[orig[i]] = i;
+}
+
+static PArr sna_view(gnb_ctx *c)
+{
+    PArr s;
+    s.x = c->sna_x; s.y = c->sna_y; s.z = c->sna_z; s.h2 = c->sna_h2; s.id = c->sna_id;
+    s.m = c->sna_m; s.u = c->sna_u; s.vx = c->sna_vx; s.vy = c->sna_vy; s.vz = c->sna_vz;
+    return s;
+}
+
+static int sna_buffers(gnb_ctx *c)
+{
+    if (!c->sna_st) GNB_TRY(cuda_check(c, cudaStreamCreateWithFlags(&c->sna_st, cudaStreamNonBlocking), "stream"));
+    if (!c->sna_ev_snap)
+        GNB_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->sna_ev_snap, cudaEventDisableTiming), "event"));
+    if (!c->sna_ev_done)
+        GNB_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->sna_ev_done, cudaEventDisableTiming), "event"));
+    if (!c->sna_seed) GNB_TRY(dalloc(c, &c->sna_seed, 1));
+    if (c->sna_cap >= c->cap) return GNB_OK;
+    void *old[] = {c->sna_x, c->sna_y, c->sna_z, c->sna_h2, c->sna_m, c->sna_u, c->sna_vx, c->sna_vy, c->sna_vz,
+                   c->sna_rho, c->sna_reg, c->sna_orig, c->sna_pos, c->sna_inv, c->sna_id};
+    for (void *q : old) dfree(c, q);
+    const size_t m = (size_t)c->cap + 1;
+    GNB_TRY(dalloc(c, &c->sna_x, m)); GNB_TRY(dalloc(c, &c->sna_y, m)); GNB_TRY(dalloc(c, &c->sna_z, m));
+    GNB_TRY(dalloc(c, &c->sna_h2, m)); GNB_TRY(dalloc(c, &c->sna_m, m)); GNB_TRY(dalloc(c, &c->sna_u, m));
+    GNB_TRY(dalloc(c, &c->sna_vx, m)); GNB_TRY(dalloc(c, &c->sna_vy, m)); GNB_TRY(dalloc(c, &c->sna_vz, m));
+    GNB_TRY(dalloc(c, &c->sna_rho, m)); GNB_TRY(dalloc(c, &c->sna_reg, m)); GNB_TRY(dalloc(c, &c->sna_orig, m));
+    GNB_TRY(dalloc(c, &c->sna_pos, m)); GNB_TRY(dalloc(c, &c->sna_inv, m)); GNB_TRY(dalloc(c, &c->sna_id, m));
+    c->sna_cap = c->cap;
+    return GNB_OK;
+}
+
+int sn_async_submit(gnb_ctx *c, gnb_unet *net, int nreg, const double *centers, double side, uint64_t seed,
+                    int sweeps)
+{
+    if (c->sna_pending) return fail(c, GNB_ESTATE, "an asynchronous surrogate batch is already pending");
+    bf16 *xin = nullptr;
+    float *yout = nullptr;
+    int grid = 0, cout = 0;
+    GNB_TRY(unet_prepare(net, nreg, &xin, &yout, &grid, &cout));
+    if (cout != 5) return fail(c, GNB_EINVAL, "the surrogate network must predict 5 channels");
+    if (grid > 256) return fail(c, GNB_EINVAL, "surrogate grids are limited to 256 voxels per axis");
+    GNB_TRY(voxelise_buffers_for(c, nreg, grid));
+    GNB_TRY(upload_centres(c, nreg, centers));
+    GNB_TRY(sna_buffers(c));
+    unsigned long long sd = seed;
+    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->sna_seed, &sd, sizeof(sd), cudaMemcpyHostToDevice, c->s), "seed"));
+    const int n = (int)c->n;
+    const int nb = (n + 255) / 256;
+    // snapshot on the context's stream
+    assign_launch(c, nreg, side, c->s);
+    counted(k_sna_flag)<<<nb, 256, 0, c->s>>>(n, c->sreg, c->sna_inv);
+    GNB_TRY(device_scan(c, c->sna_inv, c->sna_pos, c->n_d, n, nullptr));
+    cudaMemsetAsync(c->sna_reg, 0xff, sizeof(int) * (size_t)n, c->s);  // -1: not a member
+    counted(k_sna_snapshot)<<<nb, 256, 0, c->s>>>(c->P[c->cur], n, c->sreg, c->rho, c->sna_pos, sna_view(c),
+                                                  c->sna_rho, c->sna_reg, c->sna_orig);
+    GNB_LAUNCH_CHECK(c, "surrogate snapshot");
+    GNB_TRY(cuda_check(c, cudaEventRecord(c->sna_ev_snap, c->s), "event"));
+    // the rest on the side stream
+    cudaStream_t st = c->sna_st;
+    GNB_TRY(cuda_check(c, cudaStreamWaitEvent(st, c->sna_ev_snap, 0), "event wait"));
+    GNB_TRY(vox_regions_view(c, sna_view(c), n, c->sna_reg, c->sna_rho, 0, nreg, side, grid, nullptr, xin, st));
+    GNB_TRY(unet_run(net, nreg, st, nullptr, nullptr));
+    const size_t nv = (size_t)nreg * grid * grid * grid;
+    counted(k_remap_weights)<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(yout, (long long)nv, cout, c->vw);
+    const long long nl = (long long)nreg * 3 * grid * grid;
+    counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(c->vw, nreg, grid, c->vcdf, c->vcdf32,
+                                                                      c->vcdfc);
+    GNB_LAUNCH_CHECK(c, "surrogate side stream");
+    GNB_TRY(cuda_check(c, cudaEventRecord(c->sna_ev_done, st), "event"));
+    c->sna_pending = true;
+    c->sna_nreg = nreg; c->sna_grid = grid; c->sna_sweeps = sweeps; c->sna_side = side;
+    c->sna_net = net; c->sna_yout = yout;
+    return GNB_OK;
+}
+
+int sn_async_apply(gnb_ctx *c)
+{
+    if (!c->sna_pending) return fail(c, GNB_ESTATE, "no asynchronous surrogate batch is pending");
+    GNB_TRY(cuda_check(c, cudaStreamWaitEvent(c->s, c->sna_ev_done, 0), "event wait"));
+    c->sna_pending = false;
+    const int n = (int)c->n;
+    const double side = c->sna_side;
+    const int grid = c->sna_grid;
+    counted(k_inverse)<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur].orig, n, c->sna_inv);
+    counted(k_remap)<<<(n + 127) / 128, 128, 0, c->s>>>(sna_view(c), c->P[c->cur], c->sna_orig, c->sna_inv, n,
+                                                        c->sna_reg, c->sna_yout, 5, c->vcdf, c->vcdf32, c->vcdfc,
+                                                        c->cent_d, side, side / grid, 1.0 / (side / grid), grid,
+                                                        c->sna_seed, c->sna_sweeps, 0, c->sna_nreg);
+    GNB_LAUNCH_CHECK(c, "surrogate apply");
+    return GNB_OK;
 }
 
 // voxelise -> U-Net -> remap for nreg regions; after the first call with a

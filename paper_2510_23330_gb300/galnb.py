@@ -90,6 +90,12 @@ def _declare(L):
     L.gnb_set_timing.restype = C.c_int
     L.gnb_set_sn_chunks.argtypes = [_vp, C.c_int]
     L.gnb_set_sn_chunks.restype = C.c_int
+    L.gnb_sn_async_submit.argtypes = [_vp, _vp, C.c_int, _vp, C.c_double, C.c_uint64, C.c_int]
+    L.gnb_sn_async_submit.restype = C.c_int
+    L.gnb_sn_async_apply.argtypes = [_vp]
+    L.gnb_sn_async_apply.restype = C.c_int
+    L.gnb_sn_async_pending.argtypes = [_vp]
+    L.gnb_sn_async_pending.restype = C.c_int
     L.gnb_phase_times.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                   C.c_int]
     L.gnb_phase_times.restype = C.c_int
@@ -346,6 +352,18 @@ def gnb_set_sn_chunks(ctx, chunks):
     return lib().gnb_set_sn_chunks(ctx, chunks)
 
 
+def gnb_sn_async_submit(ctx, net, nreg, centers, side, seed, sweeps):
+    return lib().gnb_sn_async_submit(ctx, net, nreg, centers, side, seed, sweeps)
+
+
+def gnb_sn_async_apply(ctx):
+    return lib().gnb_sn_async_apply(ctx)
+
+
+def gnb_sn_async_pending(ctx):
+    return lib().gnb_sn_async_pending(ctx)
+
+
 def gnb_phase_times(ctx, out_ms, calls, launches, reset):
     return lib().gnb_phase_times(ctx, out_ms, calls, launches, reset)
 
@@ -544,6 +562,20 @@ class Context:
 
     def set_sn_chunks(self, chunks):
         self._chk(gnb_set_sn_chunks(self.h, int(chunks)))
+
+    def sn_async_submit(self, net, centers, side=60.0, seed=0, sweeps=8):
+        """Snapshot the regions' members and start voxelise + U-Net on a side stream."""
+        c, cp = _centers(centers)
+        self._sna_keep = (c, net)  # the centres array and the network outlive the call
+        self._chk(gnb_sn_async_submit(self.h, net.h, c.size // 3, cp, float(side), int(seed), int(sweeps)))
+
+    def sn_async_apply(self):
+        """Replace the snapshot's members from the pending batch's prediction."""
+        self._chk(gnb_sn_async_apply(self.h))
+        self._sna_keep = None
+
+    def sn_async_pending(self):
+        return bool(gnb_sn_async_pending(self.h))
 
     def phase_times(self, reset=False):
         """({phase: ms}, {phase: timed occurrences}, library kernel launches)."""

@@ -166,3 +166,92 @@ def test_pipelined_batch_matches_sequential(G, orc):
     med_ss, max_ss = spread(s1, s2)
     med_sp, max_sp = spread(s1, pp)
     assert med_sp <= 2.0 * med_ss + 2e-3 and max_sp <= 2.0 * max_ss + 0.05, (med_sp, med_ss, max_sp, max_ss)
+
+
+def _net32(G, stream):
+    from oracle import unet as U
+    net = G.UNet(5, 5, 16, 4, 32, stream=stream.cuda_stream)
+    spec = U.layer_spec(5, 5, 16, 4)
+    prm = U.init_params(5, 5, 5, 16, 4)
+    net.set_params(np.concatenate([np.concatenate([prm[n + ".w"].ravel(), prm[n + ".b"]])
+                                   for n, *_ in spec]).astype(np.float32))
+    return net
+
+
+def test_async_batch_applied_at_once_matches_the_batch(G, orc):
+    """Submitted and applied with no step between, the asynchronous batch
+    places every member exactly where the synchronous batch does (no Gibbs
+    sweeps: the voxel of the old position and the seeded offset)."""
+    import torch
+    stream = torch.cuda.Stream()
+    p = ics.sn_region(12000, seed=41, grid=32)
+    cen = [(0.5, -1.0, 2.0)]
+    with torch.cuda.stream(stream):
+        net = _net32(G, stream)
+        out = []
+        for mode in ("sync", "async"):
+            c = G.Context(stream=stream.cuda_stream)
+            c.set_particles(p)
+            c.compute_sph_density()
+            if mode == "sync":
+                c.sn_surrogate_batch(net, cen, side=60.0, seed=3, sweeps=0, use_graph=False)
+            else:
+                c.sn_async_submit(net, cen, side=60.0, seed=3, sweeps=0)
+                assert c.sn_async_pending()
+                c.sn_async_apply()
+                assert not c.sn_async_pending()
+            out.append({k: c.get(k) for k in ("X", "Y", "Z", "U", "ID")})
+            c.close()
+    stream.synchronize()
+    a, b = out
+    for k in ("X", "Y", "Z", "ID"):
+        assert np.array_equal(a[k], b[k])
+    assert np.all(np.isfinite(b["U"])) and np.all(b["U"] > 0)
+
+
+def test_async_batch_deferred_over_global_steps(G, orc):
+    """Submit, three KDK steps (the particle arrays are re-sorted every step),
+    apply: the members are replaced from their snapshot (starting voxel of the
+    snapshot position, seeded draws -- the oracle's remap, bit for bit), the
+    other particles are those of the same three steps without the batch."""
+    from oracle import surrogate as S
+    import torch
+    stream = torch.cuda.Stream()
+    p = ics.sn_region(12000, seed=43, grid=32)
+    cen = (0.5, -1.0, 2.0)
+    side, grid, seed = 60.0, 32, 11
+    s0 = orc.state(p)
+    mem = np.nonzero(S.members(s0, [cen], side) == 0)[0]
+    assert mem.size > 1000
+    with torch.cuda.stream(stream):
+        net = _net32(G, stream)
+        res = {}
+        for mode in ("plain", "async"):
+            c = G.Context(stream=stream.cuda_stream)
+            c.set_particles(p)
+            c.compute_sph_density()
+            if mode == "async":
+                c.sn_async_submit(net, [cen], side=side, seed=seed, sweeps=0)
+                with pytest.raises(G.GalnbError):
+                    c.sn_async_submit(net, [cen], side=side, seed=seed, sweeps=0)  # one pending batch
+                with pytest.raises(G.GalnbError):
+                    c.voxelise([cen], side=side, grid=grid)
+            c.compute_forces(G.GNB_GRAV_NONE)
+            c.step_kdk(1e-4, 3, G.GNB_GRAV_NONE)
+            if mode == "async":
+                c.sn_async_apply()
+                with pytest.raises(G.GalnbError):
+                    c.sn_async_apply()  # nothing pending
+            res[mode] = np.stack([c.get("X"), c.get("Y"), c.get("Z")], axis=1)
+            assert np.array_equal(c.get("ID"), p["id"])
+            c.close()
+    stream.synchronize()
+    # (the symmetric SPH force sums reverse-neighbour lists filled in no fixed
+    # order, so two runs of the same steps differ in the last bits)
+    others = np.setdiff1d(np.arange(p["x"].size), mem)
+    assert np.max(np.abs(res["async"][others] - res["plain"][others])) < 1e-9 * side
+    pos0 = np.stack([s0["x"], s0["y"], s0["z"]], axis=1)[mem]
+    pred = np.zeros((grid ** 3, 5))  # positions do not depend on the prediction without sweeps
+    vox, rp, _, _ = S.remap(pred, p["id"][mem], pos0, cen, side, grid, seed=seed, sweeps=0)
+    assert np.max(np.abs(res["async"][mem] - rp)) < 1e-12 * side
+    assert not np.array_equal(res["async"][mem], res["plain"][mem])
