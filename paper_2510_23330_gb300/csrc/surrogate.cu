@@ -277,6 +277,54 @@ __global__ void k_line_cdf(const double *__restrict__ w, int nreg, int grid, dou
     }
 }
 
+// The same sums for grids of 32 or 64 voxels per axis, one warp per 32
+// consecutive lines (same region and axis) staged through shared memory:
+// the weights are read and the sums written as contiguous blocks (a line of
+// axis 0 is contiguous; lines of axes 1 and 2 are read across the warp),
+// and each lane sums its own line left to right as above (bit-identical).
+constexpr int LC_W = 2;  // warps per block
+__global__ void __launch_bounds__(32 * LC_W) k_line_cdf_tiled(const double *__restrict__ w, int nreg, int grid,
+                                                              double *__restrict__ cdf, float *__restrict__ cdf32,
+                                                              float *__restrict__ cdfc)
+{
+    __shared__ double tile[LC_W][32][65];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const long long G = grid, lines = G * G;
+    const long long t0 = ((long long)blockIdx.x * LC_W + wq) * 32;  // first line of this warp
+    if (t0 >= (long long)nreg * 3 * lines) return;                  // (warp-uniform)
+    const long long line0 = t0 % lines, ra = t0 / lines;
+    const int a = (int)(ra % 3);
+    const long long r = ra / 3;
+    const long long u = line0 / G, v0 = line0 % G;
+    const double *wr = w + r * G * G * G;
+    double(*T)[65] = tile[wq];
+    if (a == 0) {
+        // lines (z = u, y = v0 .. v0 + 31) along x: one contiguous block of 32 G weights
+        const double *blk = wr + (u * G + v0) * G;
+        for (int k = lane; k < 32 * grid; k += 32) T[k / grid][k % grid] = blk[k];
+    } else {
+        const long long stride = a == 1 ? G : G * G;
+        const long long b0 = a == 1 ? u * G * G + v0 : u * G + v0;  // line l adds l (inner x)
+        for (int q = 0; q < grid; q++) T[lane][q] = wr[b0 + lane + q * stride];
+    }
+    __syncwarp();
+    double cum = 0.0;
+    for (int q = 0; q < grid; q++) {
+        cum = __dadd_rn(cum, T[lane][q]);
+        T[lane][q] = cum;
+    }
+    __syncwarp();
+    double *out = cdf + t0 * G;
+    float *out32 = cdf32 + t0 * G;
+    for (int k = lane; k < 32 * grid; k += 32) {
+        const double c = T[k / grid][k % grid];
+        out[k] = c;
+        out32[k] = __double2float_rn(c);
+    }
+    const int nc = grid >> 3;
+    for (int k = lane; k < 32 * nc; k += 32) cdfc[t0 * nc + k] = __double2float_rn(T[k / nc][8 * (k % nc) + 7]);
+}
+
 // Members are read from `p` (positions, ID; region in reg) and their new
 // state is written to `q` at slot dst(i) = map ? map[src_orig[i]] : i (the
 // asynchronous batch reads a snapshot and writes the current arrays).
@@ -531,8 +579,12 @@ static int remap_regions_launch(gnb_ctx *c, int r0, int r1, double side, int gri
     counted(k_remap_weights)<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(pred + (size_t)r0 * V * cout,
                                                                            (long long)nv, cout, c->vw);
     long long nl = (long long)(r1 - r0) * 3 * grid * grid;
-    counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(c->vw, r1 - r0, grid, c->vcdf, c->vcdf32,
-                                                                      c->vcdfc);
+    if (grid == 32 || grid == 64)
+        counted(k_line_cdf_tiled)<<<(unsigned)((nl / 32 + LC_W - 1) / LC_W), 32 * LC_W, 0, st>>>(
+            c->vw, r1 - r0, grid, c->vcdf, c->vcdf32, c->vcdfc);
+    else
+        counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(c->vw, r1 - r0, grid, c->vcdf, c->vcdf32,
+                                                                          c->vcdfc);
     counted(k_remap)<<<(n + 127) / 128, 128, 0, st>>>(c->P[c->cur], c->P[c->cur], nullptr, nullptr, n, c->sreg, pred,
                                                       cout, c->vcdf, c->vcdf32,
                                                       c->vcdfc, c->cent_d, side, side / grid, 1.0 / (side / grid), grid,
@@ -677,8 +729,12 @@ int sn_async_submit(gnb_ctx *c, gnb_unet *net, int nreg, const double *centers, 
     const size_t nv = (size_t)nreg * grid * grid * grid;
     counted(k_remap_weights)<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(yout, (long long)nv, cout, c->vw);
     const long long nl = (long long)nreg * 3 * grid * grid;
-    counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(c->vw, nreg, grid, c->vcdf, c->vcdf32,
-                                                                      c->vcdfc);
+    if (grid == 32 || grid == 64)
+        counted(k_line_cdf_tiled)<<<(unsigned)((nl / 32 + LC_W - 1) / LC_W), 32 * LC_W, 0, st>>>(
+            c->vw, nreg, grid, c->vcdf, c->vcdf32, c->vcdfc);
+    else
+        counted(k_line_cdf)<<<(unsigned)((nl + 127) / 128), 128, 0, st>>>(c->vw, nreg, grid, c->vcdf, c->vcdf32,
+                                                                          c->vcdfc);
     GNB_LAUNCH_CHECK(c, "surrogate side stream");
     GNB_TRY(cuda_check(c, cudaEventRecord(c->sna_ev_done, st), "event"));
     c->sna_pending = true;
