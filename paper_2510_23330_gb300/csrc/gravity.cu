@@ -141,11 +141,12 @@ __device__ __forceinline__ void pc_loop(const GravSmem &S, int buf, int nc, int 
             float rqr = __fmaf_rn(rx, qx, __fmaf_rn(ry, qy, rz * qz));
             float Ri5 = Ri2 * Ri2 * Ri;
             float Ri7 = Ri5 * Ri2;
-            float t = 2.5f * rqr * Ri7 + mR3;
-            ax += __fmaf_rn(qx, Ri5, -t * rx);
-            ay += __fmaf_rn(qy, Ri5, -t * ry);
-            az += __fmaf_rn(qz, Ri5, -t * rz);
-            ph += __fmaf_rn(0.5f * rqr, Ri5, mR);
+            float t = __fmaf_rn(2.5f * rqr, Ri7, mR3);
+            // two chained FMAs per component (Q r/R^5, then -t r)
+            ax = __fmaf_rn(-t, rx, __fmaf_rn(qx, Ri5, ax));
+            ay = __fmaf_rn(-t, ry, __fmaf_rn(qy, Ri5, ay));
+            az = __fmaf_rn(-t, rz, __fmaf_rn(qz, Ri5, az));
+            ph = __fmaf_rn(0.5f * rqr, Ri5, ph) + mR;
         } else {
             ax = __fmaf_rn(-mR3, rx, ax);
             ay = __fmaf_rn(-mR3, ry, ay);
@@ -678,6 +679,10 @@ static int lists_alloc(gnb_ctx *c, int chunks)
         c->gl_gcap = cap;
     }
     if (c->gl_cap < chunks) {
+        // grow geometrically with headroom: the estimate follows the node
+        // count, which drifts from step to step, and a reallocation (cudaFree
+        // synchronises the device) must not recur every step
+        chunks = std::max(chunks + chunks / 4, c->gl_cap + c->gl_cap / 2);
         dfree(c, c->gl_pool); dfree(c, c->gl_next); dfree(c, c->gl_cnt); dfree(c, c->gl_lcum);
         c->gl_pool = nullptr; c->gl_next = nullptr; c->gl_cnt = nullptr; c->gl_lcum = nullptr;
         GNB_TRY(dalloc(c, &c->gl_pool, (size_t)chunks * GL_CH));
