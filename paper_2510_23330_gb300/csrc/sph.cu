@@ -287,6 +287,9 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
         }
         const double Rg = (double)R / (double)unit;  // radius in grid units
         const double Rg2m = Rg * Rg * (1.0 + 1e-5) + 4.0;
+        // the node test compares integers: gap2 is an integer, so gap2 <= Rg2m
+        // exactly when gap2 <= floor(Rg2m) (no FP64 per visited node)
+        const long long Rg2i = Rg2m >= 4.0e18 ? 0x7fffffffffffffffll : (long long)Rg2m;
         const float R2stage = R * R * (1.f + 1e-4f) + 4.f * unit * unit;
         // gather candidates within R of the group box
         for (;;) {
@@ -306,15 +309,15 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                 int lev = a.w & 255, nch = a.w >> 8;
                 long long s = 1ll << (GNB_MAXLEV - lev);
                 int cc[3] = {C.x, C.y, C.z};
-                double gap2 = 0.0;
+                long long gap2 = 0;  // < 3 * 2^44: exact in 64-bit integers
 #pragma unroll
                 for (int q = 0; q < 3; q++) {
                     long long gp = 0;
                     if ((long long)cc[q] > (long long)b1[q] + 1) gp = cc[q] - ((long long)b1[q] + 1);
                     else if ((long long)b0[q] > cc[q] + s) gp = b0[q] - (cc[q] + s);
-                    gap2 += (double)gp * (double)gp;
+                    gap2 += gp * gp;
                 }
-                if (gap2 <= Rg2m) {
+                if (gap2 <= Rg2i) {
                     if (nch > 0) {
                         int b = atomicAdd(&S.sp, nch);
                         if (b + nch <= KN_STACK) {
