@@ -497,3 +497,162 @@ def integrate_cfl(s: dict, t_span: float, courant: float, cfg: Config, max_steps
         t += dt
         n += 1
     return s, f, t, n
+
+
+# --------------------------------------------------------------------------
+# Plain integration with hierarchical (block) individual timesteps
+# --------------------------------------------------------------------------
+# Sec. 1 describes the conventional scheme the surrogate competes with: every
+# particle carries its own timestep and is integrated only when its step
+# ends, while at each such step the positions and other quantities of all
+# particles are predicted and the octree is rebuilt for the force
+# calculation.  The paper gives no formulas; the reading written out here is
+# the usual power-of-two block scheme on an integer time grid:
+#   * ticks: the span is 2^(K+1) ticks of length t_span 2^-(K+1); level k has
+#     the step dt_k = t_span 2^-k = 2^(K+1-k) ticks (k = 0 .. K);
+#   * the CFL level of a gas particle is the coarsest k with dt_k <= its CFL
+#     step C h_i / vsig_i (other particles: level 0); a step starting at tick
+#     T takes the coarser of the finest of that level and the coarsest level
+#     whose step divides T, so steps start and end on their own grid;
+#   * a block step goes to the next tick T at which some step ends, drifts
+#     every particle there with its half-step velocity, predicts the velocity
+#     and energy of every particle from the force of its last evaluation
+#     (v + a (t - t_mid), t_mid the middle of its current step), and
+#     evaluates all forces at that predicted state;
+#   * a particle whose step ends at T, or whose CFL level at T is finer than
+#     its current level (a wake-up: the step is cut short at T, its opening
+#     kick and the drift since its start are corrected to the shorter step),
+#     gets the closing half kick with the new force and -- unless the span
+#     is done -- a new level and the opening half kick of its next step.
+def hier_cfl_level(dtc, K: int, t_span: float) -> np.ndarray:
+    """The coarsest k <= K with dt_k = t_span 2^-k <= dtc; -1 where even
+    dt_K exceeds dtc (the finest level does not resolve the particle)."""
+    dtc = np.asarray(dtc, dtype=np.float64)
+    k = np.zeros(dtc.shape, dtype=np.int64)
+    for j in range(K):
+        k += np.ldexp(t_span, -j) > dtc  # dt_j longer than the CFL step: one level finer
+    return np.where(np.ldexp(t_span, -K) > dtc, -1, k)
+
+
+def hier_align_level(T: int, K: int) -> int:
+    """The coarsest level whose step 2^(K+1-k) ticks divides tick T."""
+    if T == 0:
+        return 0
+    a = (T & -T).bit_length() - 1  # T = 2^a * odd
+    return max(0, K + 1 - a)
+
+
+def cfl_steps(f: dict, n: int, courant: float) -> np.ndarray:
+    """Individual CFL steps: courant h_i / vsig_i for gas, infinite for the
+    other particles and for gas with vsig = 0."""
+    out = np.full(n, np.inf)
+    if "sph" in f:
+        gi = f["gas_index"]
+        h = np.sqrt(f["sph"]["h2"])
+        vs = f["sph"]["vsig"]
+        with np.errstate(divide="ignore"):
+            out[gi] = np.where(vs > 0, courant * h / np.where(vs > 0, vs, 1.0), np.inf)
+    return out
+
+
+def level_margin(dtc, kc, t_span: float) -> float:
+    """Smallest relative distance of a CFL step to the level boundaries that
+    decided its level (dt_kc <= dtc < dt_(kc-1)): how far a rounding error
+    of the step would have to go to change the decision."""
+    dtc = np.asarray(dtc, dtype=np.float64)
+    ok = np.isfinite(dtc) & (kc >= 0)
+    if not np.any(ok):
+        return np.inf
+    d, k = dtc[ok], kc[ok]
+    lo = np.abs(d / np.ldexp(t_span, -k) - 1.0)
+    hi = np.where(k > 0, np.abs(d / np.ldexp(t_span, -(k - 1)) - 1.0), np.inf)
+    return float(min(lo.min(), hi.min()))
+
+
+def integrate_hier(s: dict, t_span: float, courant: float, cfg: Config, max_level: int = 20,
+                   max_steps: int = 1 << 30, force_fn=None, step_fn=None):
+    """Plain integration over t_span with hierarchical individual timesteps
+    (Sec. 1; the reading above).  force_fn(s, u, v) -> {ax, ay, az, dudt, ...}
+    defaults to forces(s, cfg, u, v); step_fn(f, n) -> individual steps
+    defaults to the CFL steps.  Returns (state, forces, info) with info =
+    {t, steps (block steps), updates (particle updates after the start),
+    wakeups, level (the last step's), margin (smallest level_margin)}."""
+    if force_fn is None:
+        def force_fn(st, u=None, v=None):
+            return forces(st, cfg, u=u, v=v)
+    if step_fn is None:
+        def step_fn(ff, nn):
+            return cfl_steps(ff, nn, courant)
+    K = int(max_level)
+    NT = 1 << (K + 1)
+    tick = float(np.ldexp(t_span, -(K + 1)))
+    s = dict(s)
+    for k in ("x", "y", "z", "vx", "vy", "vz", "u"):
+        s[k] = np.array(s[k], dtype=np.float64, copy=True)
+    n = s["x"].shape[0]
+    gas = s["type"] == GAS
+    V = ("vx", "vy", "vz")
+
+    def cfl_level(ff):
+        dtc = step_fn(ff, n)
+        kc = hier_cfl_level(dtc, K, t_span)
+        return kc, level_margin(dtc, kc, t_span)
+
+    def kick(mask, acc, half):
+        for a, k in enumerate(V):
+            s[k][mask] = s[k][mask] + acc[a][mask] * half[mask]
+        g = mask & gas
+        s["u"][g] = s["u"][g] + acc[3][g] * half[g]
+
+    f = force_fn(s)
+    acc = [np.array(f[k], dtype=np.float64, copy=True) for k in ("ax", "ay", "az", "dudt")]
+    kc, margin = cfl_level(f)
+    if np.any(kc < 0):
+        raise ValueError("a CFL step is shorter than the finest level")
+    lev = kc.copy()
+    T0 = np.zeros(n, dtype=np.int64)
+    T1 = np.left_shift(np.int64(1), K + 1 - lev).astype(np.int64)
+    kick(np.ones(n, dtype=bool), acc, ((T1 - T0) // 2).astype(np.float64) * tick)  # opening half kicks
+    T, steps, updates, wakeups = 0, 0, 0, 0
+    while T < NT and steps < max_steps:
+        Tn = int(T1.min())
+        dd = float(Tn) * tick - float(T) * tick
+        for k in ("x", "y", "z"):
+            s[k] = s[k] + s["v" + k] * dd
+        T = Tn
+        tau = (T - (T0 + T1) // 2).astype(np.float64) * tick
+        vp = [s[k] + acc[a] * tau for a, k in enumerate(V)]
+        up = np.where(gas, s["u"] + acc[3] * tau, 0.0)
+        f = force_fn(s, u=up, v=vp)
+        kc, mg = cfl_level(f)
+        margin = min(margin, mg)
+        due = T1 == T
+        wake = ~due & (kc > lev)
+        if np.any(wake):
+            # the step [T0, T1] becomes [T0, T]: opening kick and drift redone
+            cut = (T - T1).astype(np.float64) * (0.5 * tick)  # <= 0
+            el = (T - T0).astype(np.float64) * tick
+            for a, k in enumerate(V):
+                dv = acc[a] * cut
+                s[k[1]][wake] = s[k[1]][wake] + (dv * el)[wake]
+                s[k][wake] = s[k][wake] + dv[wake]
+            g = wake & gas
+            s["u"][g] = s["u"][g] + (acc[3] * cut)[g]
+        active = due | wake
+        new = [np.asarray(f[k], dtype=np.float64) for k in ("ax", "ay", "az", "dudt")]
+        for a in range(4):
+            acc[a] = np.where(active, new[a], acc[a])
+        kick(active, acc, ((T - T0) // 2).astype(np.float64) * tick)  # closing half kicks
+        if T < NT:
+            if np.any(kc[active] < 0):
+                raise ValueError("a CFL step is shorter than the finest level")
+            lev = np.where(active, np.maximum(kc, hier_align_level(T, K)), lev)
+            T0 = np.where(active, T, T0)
+            T1 = np.where(active, T + np.left_shift(np.int64(1), K + 1 - lev), T1)
+            kick(active, acc, ((T1 - T0) // 2).astype(np.float64) * tick)  # opening half kicks
+        steps += 1
+        updates += int(np.count_nonzero(active))
+        wakeups += int(np.count_nonzero(wake))
+    info = {"t": float(T) * tick, "steps": steps, "updates": updates, "wakeups": wakeups,
+            "level": lev, "margin": margin}
+    return s, f, info
