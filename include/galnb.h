@@ -98,6 +98,8 @@ enum gnb_field {
                                        particle [int64, groups] */
     GNB_F_ID,                       /* particle IDs [int64, n] */
     GNB_F_AGRAV_X, GNB_F_AGRAV_Y, GNB_F_AGRAV_Z, /* self-gravity part of a [float, n] */
+    GNB_F_LEVEL,                    /* timestep level k (step t_span 2^-k) of each particle's last step
+                                       in gnb_integrate_hier [int32, n] */
     GNB_F_COUNT_
 };
 
@@ -217,6 +219,32 @@ int gnb_cfl_timestep(gnb_ctx *ctx, double courant, double *dt);
  * GNB_ECAPACITY, GNB_ECUDA. */
 int gnb_integrate_cfl(gnb_ctx *ctx, double t_span, double courant, int max_steps, int gravity_mode,
                       double *t_done, int64_t *steps_done);
+
+/* Plain integration with hierarchical (block) individual timesteps (Sec. 1:
+ * every particle has its own timestep and is updated only when it ends, while
+ * all particles are predicted and the tree is rebuilt at each step; the rules
+ * are a reading).  The span is 2^(max_level+1) integer ticks; level k steps
+ * t_span 2^-k.  A step starting at tick T takes the coarser of the gas
+ * particle's CFL level (the coarsest k with t_span 2^-k <= courant h / vsig;
+ * level 0 for other particles) and the coarsest level whose step divides T.
+ * Each block step goes to the next tick at which a step ends, drifts all
+ * particles there, predicts v and u of every particle from the force of its
+ * last update (v + a (t - t_mid), t_mid the middle of its step), evaluates
+ * all forces (gravity_mode as in gnb_compute_forces) at the predicted state
+ * and kicks the particles whose step ends there; a particle whose CFL level
+ * there is finer than its own is woken: its step is cut to end there (its
+ * opening kick and drift are corrected) and it is kicked too.  All particles
+ * end synchronised at t_span unless max_steps block steps come first (then
+ * velocities are those of the particles' current half steps).
+ * t_done (may be NULL) receives the time reached; info (may be NULL) {block
+ * steps, particle updates after the start, wake-ups}.  The levels are read
+ * with GNB_F_LEVEL.  Errors: GNB_EINVAL (t_span, courant, max_level outside
+ * 1..40, max_steps < 0, mode), GNB_ESTATE (no particles or no gas, a pending
+ * asynchronous surrogate batch), GNB_ECAPACITY (a gas particle's CFL step
+ * at some block step is shorter than the finest level's: that block step
+ * kicks nobody, so the particles stay within their steps), GNB_ECUDA. */
+int gnb_integrate_hier(gnb_ctx *ctx, double t_span, double courant, int max_level, int max_steps, int gravity_mode,
+                       double *t_done, int64_t info[3]);
 
 /* Copy one field into dst, which holds cap elements of the field's type.
  * Errors: GNB_EINVAL (field, cap too small, null dst), GNB_ESTATE (field

@@ -269,6 +269,7 @@ void gnb_destroy(gnb_ctx *c)
     else cudaDeviceSynchronize();
     free_particles(c);
     free_gas(c);
+    hier_free(c);
     void *all[] = {c->status_d, c->n_d, c->ngas_d, c->counters_d, c->work_d, c->box_d, c->mm_d, c->red_d,
                    c->rs_total, c->rtot_d, c->scan_part, c->scan_poff, c->gl_pool, c->gl_next, c->gl_cnt,
                    c->gl_top, c->gl_head, c->gl_ref, c->gl_lcum};
@@ -313,6 +314,7 @@ int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *t
     c->have_particles = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = false;
     c->sphf_valid = false;
     c->have_h = false;
+    c->hier_on = c->hier_valid = false;
     GNB_TRY(alloc_particles(c, n));
     c->cur = 0;
     PArr &p = c->P[0];
@@ -665,6 +667,64 @@ int gnb_integrate_cfl(gnb_ctx *c, double t_span, double courant, int max_steps, 
     return finish(c, rc);
 }
 
+int gnb_integrate_hier(gnb_ctx *c, double t_span, double courant, int max_level, int max_steps, int mode,
+                       double *t_done, int64_t info[3])
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!(t_span > 0.0) || !std::isfinite(t_span) || !(courant > 0.0) || !std::isfinite(courant) || max_level < 1 ||
+        max_level > 40 || max_steps < 0)
+        return fail(c, GNB_EINVAL, "t_span, courant, max_level or max_steps");
+    if (!mode_ok(mode)) return fail(c, GNB_EINVAL, "gravity mode");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    if (c->n_gas == 0) return fail(c, GNB_ESTATE, "no gas: the CFL timestep is undefined");
+    if (c->sna_pending) return fail(c, GNB_ESTATE, "an asynchronous surrogate batch is pending");
+    c->hier_on = c->hier_valid = false;
+    int rc = hier_buffers(c);
+    if (rc == GNB_OK && (!c->force_valid || c->last_grav_mode != mode)) rc = do_forces(c, mode);
+    const int K = max_level;
+    const long long NT = 1ll << (K + 1);
+    const double tick = std::ldexp(t_span, -(K + 1));
+    long long T = 0;
+    int64_t steps = 0, updates = 0, wakes = 0;
+    const char *coarse = "a CFL step is shorter than the finest level's (raise max_level)";
+    if (rc == GNB_OK) {
+        c->hier_on = true;  // from here every sort permutes the step state
+        rc = hier_start(c, K, tick, courant, t_span);
+    }
+    if (rc == GNB_OK && c->hred_h[3]) rc = fail(c, GNB_ECAPACITY, coarse);
+    while (rc == GNB_OK && T < NT && steps < max_steps) {
+        const long long Tn = (long long)c->hred_h[0];
+        const double dd = (double)Tn * tick - (double)T * tick;
+        T = Tn;
+        phase_begin(c, GNB_T_KDK);
+        rc = drift(c, dd);
+        if (rc == GNB_OK) rc = hier_predict(c, T, tick);
+        phase_end(c);
+        c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+        c->use_pred = true;
+        if (rc == GNB_OK) rc = do_forces(c, mode);
+        c->use_pred = false;
+        phase_begin(c, GNB_T_KDK);
+        if (rc == GNB_OK) rc = hier_update(c, T, K, tick, courant, t_span);
+        phase_end(c);
+        if (rc == GNB_OK && c->hred_h[3]) rc = fail(c, GNB_ECAPACITY, coarse);
+        if (rc != GNB_OK) break;
+        steps++;
+        updates += (int64_t)c->hred_h[1];
+        wakes += (int64_t)c->hred_h[2];
+    }
+    c->hier_valid = rc == GNB_OK;
+    if (t_done) *t_done = (double)T * tick;
+    if (info) {
+        info[0] = steps;
+        info[1] = updates;
+        info[2] = wakes;
+    }
+    if (rc == GNB_OK) rc = read_groups(c);
+    return finish(c, rc);
+}
+
 int gnb_voxelise(gnb_ctx *c, int nreg, const double *centers, double side, int grid, float *out, int on_device)
 {
     if (!c) return GNB_EINVAL;
@@ -748,6 +808,7 @@ int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
         return fail(c, GNB_ESTATE, "forces not computed");
     if (need_den && !c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed");
     if (field == GNB_F_DUDT && !c->sphf_valid) return fail(c, GNB_ESTATE, "SPH force not computed");
+    if (field == GNB_F_LEVEL && !c->hier_valid) return fail(c, GNB_ESTATE, "no hierarchical integration");
     size_t esz;
     int64_t cnt = field_count(c, field, &esz);
     if (cap < cnt) return fail(c, GNB_EINVAL, "destination too small");

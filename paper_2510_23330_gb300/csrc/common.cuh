@@ -210,6 +210,16 @@ struct gnb_ctx {
     int4 *gl_head = nullptr, *gl_ref = nullptr;
     int gl_cap = 0, gl_gcap = 0;
     int *pinned_i = nullptr;                   // pinned host scratch [64]
+    // hierarchical timesteps (integrate.cu): per particle slot, permuted with
+    // the particles by every sort while hier_on; [2] = current and scratch
+    bool hier_on = false, hier_valid = false;
+    int64_t hier_cap = 0;
+    long long *hT0[2] = {nullptr, nullptr}, *hT1[2] = {nullptr, nullptr};  // step start, end (ticks)
+    int *hlev[2] = {nullptr, nullptr};
+    float4 *hacc[2] = {nullptr, nullptr};  // a_x, a_y, a_z, du/dt of the particle's last update
+    int *hkc = nullptr;                    // CFL level per slot (gas) of the last force pass
+    unsigned long long *hred = nullptr;    // {next tick (min), updates, wake-ups, status}
+    unsigned long long *hred_h = nullptr;  // pinned copy
     double *red_d = nullptr;                   // reduction scratch
     int64_t stats[GNB_S_COUNT_] = {0};
 
@@ -259,6 +269,14 @@ void phase_end(gnb_ctx *c);
 
 // sort.cu
 int morton_and_sort(gnb_ctx *c);
+
+// integrate.cu: hierarchical timesteps
+int hier_buffers(gnb_ctx *c);
+int hier_permute(gnb_ctx *c);
+int hier_start(gnb_ctx *c, int K, double tick, double courant, double t_span);
+int hier_predict(gnb_ctx *c, long long T, double tick);
+int hier_update(gnb_ctx *c, long long T, int K, double tick, double courant, double t_span);
+void hier_free(gnb_ctx *c);
 int root_box(gnb_ctx *c);
 // tree.cu
 int build_tree(gnb_ctx *c, Tree &t, const uint64_t *skey, int n, const int *n_d, int n_leaf,

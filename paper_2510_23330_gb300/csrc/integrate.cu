@@ -5,6 +5,8 @@
 // (Sec. 4.3).  The energy, momentum and angular momentum totals are FP64
 // two-level reductions (block partials, then one block), so they do not
 // depend on scheduling.
+#include <utility>
+
 #include "common.cuh"
 
 namespace gnb {
@@ -239,6 +241,7 @@ int scatter_out(gnb_ctx *c, int field, void *dst)
     case GNB_F_CS: gnb::counted(k_scatter_orig_zero_star)<<<nb, 256, 0, c->s>>>(c->cs, a.orig, a.type, n, (float *)dst); break;
     case GNB_F_H2: gnb::counted(k_scatter_orig_zero_star_d)<<<nb, 256, 0, c->s>>>(a.h2, a.orig, a.type, n, (double *)dst); break;
     case GNB_F_KEY: gnb::counted(k_scatter_orig<uint64_t>)<<<nb, 256, 0, c->s>>>(c->skey, a.orig, n, (uint64_t *)dst); break;
+    case GNB_F_LEVEL: gnb::counted(k_scatter_orig<int>)<<<nb, 256, 0, c->s>>>(c->hlev[0], a.orig, n, (int *)dst); break;
     case GNB_F_ID: gnb::counted(k_scatter_orig<int64_t>)<<<nb, 256, 0, c->s>>>(a.id, a.orig, n, (int64_t *)dst); break;
     case GNB_F_ORDER: gnb::counted(k_order_out)<<<nb, 256, 0, c->s>>>(a.orig, n, (int64_t *)dst); break;
     case GNB_F_NODES:
@@ -256,6 +259,296 @@ int scatter_out(gnb_ctx *c, int field, void *dst)
     }
     GNB_LAUNCH_CHECK(c, "export");
     return GNB_OK;
+}
+
+// ---------------------------------------------------------------- hierarchical timesteps
+// Plain integration with individual power-of-two timesteps on an integer
+// tick grid (Sec. 1 describes the scheme; the rules are a reading): the span
+// is 2^(K+1) ticks and level k steps 2^(K+1-k) ticks.  Per particle slot:
+// the current step [T0, T1], its level and the force (a, du/dt) of the
+// particle's last update, permuted with the particles by every sort.  Kicks
+// are FP32 FMAs like the shared-step leapfrog; tick arithmetic is integer
+// and times are FP64 (tick count x tick length).
+
+// The coarsest level whose step divides tick T.
+__device__ __forceinline__ int hier_align(long long T, int K)
+{
+    if (T == 0) return 0;
+    const int a = __ffsll(T) - 1;  // T = 2^a * odd
+    return max(0, K + 1 - a);
+}
+
+// CFL level of every gas particle: the coarsest k <= K with t_span 2^-k <=
+// courant h / vsig (h from the FP64 h^2 of the kernel-size search, the same
+// FP64 operations as a scalar reference), written to the particle's slot.
+// When even the finest step is too long the status word red[3] is set and
+// the kernel that follows on the stream changes nothing.
+__global__ void k_hier_kc(int ng, const int *__restrict__ gslot, const double *__restrict__ h2,
+                          const float *__restrict__ vsig, double courant, double t_span, int K, int *__restrict__ kc,
+                          unsigned long long *__restrict__ red)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    const double v = (double)vsig[g];
+    const double dtc = v > 0.0 ? __ddiv_rn(__dmul_rn(courant, __dsqrt_rn(h2[g])), v)
+                               : __longlong_as_double(0x7ff0000000000000ll);
+    int k = 0;
+    for (int j = 0; j < K; j++) k += ldexp(t_span, -j) > dtc;
+    if (ldexp(t_span, -K) > dtc) {
+        k = K;
+        atomicOr(&red[3], 1ull);
+    }
+    kc[gslot[g]] = k;
+}
+
+struct HierArgs {
+    PArr p;
+    const float *ax, *ay, *az, *dudt;  // forces of the pass just made, per slot
+    const int *kc;
+    long long *T0, *T1;
+    int *lev;
+    float4 *acc;
+    unsigned long long *red;  // {min next tick, updates, wake-ups, status}
+    long long T, NT;
+    double tick;
+    int K, n;
+};
+
+__device__ __forceinline__ void hier_kick(const PArr &p, int i, float4 f, float h, bool gas)
+{
+    p.vx[i] = __fmaf_rn(f.x, h, p.vx[i]);
+    p.vy[i] = __fmaf_rn(f.y, h, p.vy[i]);
+    p.vz[i] = __fmaf_rn(f.z, h, p.vz[i]);
+    if (gas) p.u[i] = __fmaf_rn(f.w, h, p.u[i]);
+}
+
+// half of a tick count, as a time
+__device__ __forceinline__ float hier_half(long long ticks, double tick)
+{
+    return (float)((double)(ticks / 2) * tick);
+}
+
+// Warp-level min of the next tick and sums of the counts, one atomic each per warp.
+__device__ __forceinline__ void hier_reduce(unsigned long long next, unsigned upd, unsigned wake,
+                                            unsigned long long *red)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long q = __shfl_xor_sync(0xffffffffu, next, o);
+        next = q < next ? q : next;
+        upd += __shfl_xor_sync(0xffffffffu, upd, o);
+        wake += __shfl_xor_sync(0xffffffffu, wake, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&red[0], next);
+        if (upd) atomicAdd(&red[1], (unsigned long long)upd);
+        if (wake) atomicAdd(&red[2], (unsigned long long)wake);
+    }
+}
+
+// Tick 0: every particle starts a step of its CFL level with the opening half kick.
+__global__ void k_hier_start(HierArgs a)
+{
+    if (*(volatile unsigned long long *)&a.red[3]) return;  // a level was unresolved: nothing changes
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long next = ~0ull;
+    if (i < a.n) {
+        const bool gas = a.p.type[i] == GNB_GAS;
+        const int k = gas ? a.kc[i] : 0;
+        const long long S = 1ll << (a.K + 1 - k);
+        const float4 f = make_float4(a.ax[i], a.ay[i], a.az[i], gas ? a.dudt[i] : 0.f);
+        a.lev[i] = k;
+        a.T0[i] = 0;
+        a.T1[i] = S;
+        a.acc[i] = f;
+        hier_kick(a.p, i, f, hier_half(S, a.tick), gas);
+        next = (unsigned long long)S;
+    }
+    hier_reduce(next, 0u, 0u, a.red);
+}
+
+// Predicted v and u of every particle at tick T from its last update's
+// force: v + a (t - t_mid), t_mid the middle of its current step.
+__global__ void k_hier_predict(PArr p, const long long *__restrict__ T0, const long long *__restrict__ T1,
+                               const float4 *__restrict__ acc, int n, long long T, double tick)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float tau = (float)((double)(T - (T0[i] + T1[i]) / 2) * tick);  // T0 + T1 is even
+    const float4 f = acc[i];
+    p.vpx[i] = __fmaf_rn(f.x, tau, p.vx[i]);
+    p.vpy[i] = __fmaf_rn(f.y, tau, p.vy[i]);
+    p.vpz[i] = __fmaf_rn(f.z, tau, p.vz[i]);
+    p.up[i] = p.type[i] == GNB_GAS ? __fmaf_rn(f.w, tau, p.u[i]) : 0.f;
+}
+
+// After the force pass at tick T: particles whose step ends at T, or whose
+// CFL level is finer than their own (woken: the step is cut to end at T,
+// the opening kick and the drift since T0 are corrected with the old
+// force), get the closing half kick with the new force and, before the end
+// of the span, a new level and the opening half kick of the next step.
+__global__ void k_hier_update(HierArgs a)
+{
+    if (*(volatile unsigned long long *)&a.red[3]) return;  // a level was unresolved: nothing changes
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long next = ~0ull;
+    unsigned upd = 0, wk = 0;
+    if (i < a.n) {
+        const bool gas = a.p.type[i] == GNB_GAS;
+        const int kc = gas ? a.kc[i] : 0;
+        long long T0 = a.T0[i], T1 = a.T1[i];
+        const bool due = T1 == a.T;
+        const bool wake = !due && kc > a.lev[i];
+        if (due || wake) {
+            if (wake) {
+                const float4 f0 = a.acc[i];
+                const double cut = (double)((a.T - T1) / 2) * a.tick;  // <= 0
+                const double el = (double)(a.T - T0) * a.tick;
+                a.p.x[i] = __dadd_rn(a.p.x[i], __dmul_rn(__dmul_rn((double)f0.x, cut), el));
+                a.p.y[i] = __dadd_rn(a.p.y[i], __dmul_rn(__dmul_rn((double)f0.y, cut), el));
+                a.p.z[i] = __dadd_rn(a.p.z[i], __dmul_rn(__dmul_rn((double)f0.z, cut), el));
+                hier_kick(a.p, i, f0, (float)cut, gas);
+            }
+            const float4 f = make_float4(a.ax[i], a.ay[i], a.az[i], gas ? a.dudt[i] : 0.f);
+            hier_kick(a.p, i, f, hier_half(a.T - T0, a.tick), gas);
+            if (a.T < a.NT) {
+                const int k = max(kc, hier_align(a.T, a.K));
+                T0 = a.T;
+                T1 = a.T + (1ll << (a.K + 1 - k));
+                hier_kick(a.p, i, f, hier_half(T1 - T0, a.tick), gas);
+                a.lev[i] = k;
+                a.T0[i] = T0;
+                a.T1[i] = T1;
+            }
+            a.acc[i] = f;
+            upd = 1;
+            wk = wake ? 1u : 0u;
+        }
+        next = (unsigned long long)T1;
+    }
+    hier_reduce(next, upd, wk, a.red);
+}
+
+__global__ void k_hier_permute(const int *__restrict__ src, int n, const long long *__restrict__ T0,
+                               const long long *__restrict__ T1, const int *__restrict__ lev,
+                               const float4 *__restrict__ acc, long long *__restrict__ T0b, long long *__restrict__ T1b,
+                               int *__restrict__ levb, float4 *__restrict__ accb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = src[i];
+    T0b[i] = T0[s];
+    T1b[i] = T1[s];
+    levb[i] = lev[s];
+    accb[i] = acc[s];
+}
+
+void hier_free(gnb_ctx *c)
+{
+    for (int b = 0; b < 2; b++) {
+        dfree(c, c->hT0[b]);
+        dfree(c, c->hT1[b]);
+        dfree(c, c->hlev[b]);
+        dfree(c, c->hacc[b]);
+        c->hT0[b] = c->hT1[b] = nullptr;
+        c->hlev[b] = nullptr;
+        c->hacc[b] = nullptr;
+    }
+    dfree(c, c->hkc);
+    dfree(c, c->hred);
+    c->hkc = nullptr;
+    c->hred = nullptr;
+    if (c->hred_h) cudaFreeHost(c->hred_h);
+    c->hred_h = nullptr;
+    c->hier_cap = 0;
+}
+
+int hier_buffers(gnb_ctx *c)
+{
+    if (c->hier_cap >= c->cap && c->hred_h) return GNB_OK;
+    hier_free(c);
+    const size_t N = (size_t)c->cap;
+    for (int b = 0; b < 2; b++) {
+        GNB_TRY(dalloc(c, &c->hT0[b], N));
+        GNB_TRY(dalloc(c, &c->hT1[b], N));
+        GNB_TRY(dalloc(c, &c->hlev[b], N));
+        GNB_TRY(dalloc(c, &c->hacc[b], N));
+    }
+    GNB_TRY(dalloc(c, &c->hkc, N));
+    GNB_TRY(dalloc(c, &c->hred, 4));
+    if (cudaMallocHost((void **)&c->hred_h, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        c->hred_h = nullptr;
+        return fail(c, GNB_ENOMEM, "pinned host allocation");
+    }
+    c->hier_cap = c->cap;
+    return GNB_OK;
+}
+
+int hier_permute(gnb_ctx *c)
+{
+    const int n = (int)c->n;
+    gnb::counted(k_hier_permute)<<<(n + 255) / 256, 256, 0, c->s>>>(c->src, n, c->hT0[0], c->hT1[0], c->hlev[0],
+                                                                   c->hacc[0], c->hT0[1], c->hT1[1], c->hlev[1],
+                                                                   c->hacc[1]);
+    GNB_LAUNCH_CHECK(c, "hier permute");
+    std::swap(c->hT0[0], c->hT0[1]);
+    std::swap(c->hT1[0], c->hT1[1]);
+    std::swap(c->hlev[0], c->hlev[1]);
+    std::swap(c->hacc[0], c->hacc[1]);
+    return GNB_OK;
+}
+
+static HierArgs hier_args(gnb_ctx *c, long long T, int K, double tick)
+{
+    HierArgs a;
+    a.p = c->P[c->cur];
+    a.ax = c->ax; a.ay = c->ay; a.az = c->az; a.dudt = c->dudt;
+    a.kc = c->hkc;
+    a.T0 = c->hT0[0]; a.T1 = c->hT1[0]; a.lev = c->hlev[0]; a.acc = c->hacc[0];
+    a.red = c->hred;
+    a.T = T;
+    a.NT = 1ll << (K + 1);
+    a.tick = tick;
+    a.K = K;
+    a.n = (int)c->n;
+    return a;
+}
+
+// red = {~0, 0, 0, 0}; the CFL levels of the force pass just made, then the
+// start or update kernel; read back (one synchronisation per block step)
+template <class Kern>
+static int hier_run(gnb_ctx *c, Kern kern, const HierArgs &a, double courant, double t_span, const char *what)
+{
+    cudaMemsetAsync(c->hred, 0xff, sizeof(unsigned long long), c->s);
+    cudaMemsetAsync(c->hred + 1, 0, 3 * sizeof(unsigned long long), c->s);
+    const int ng = (int)c->n_gas;
+    if (ng > 0)
+        gnb::counted(k_hier_kc)<<<(ng + 255) / 256, 256, 0, c->s>>>(ng, c->gslot, c->gh2, c->gvsig, courant, t_span,
+                                                                   a.K, c->hkc, c->hred);
+    gnb::counted(kern)<<<(a.n + 255) / 256, 256, 0, c->s>>>(a);
+    GNB_LAUNCH_CHECK(c, what);
+    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->hred_h, c->hred, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                          c->s), "hier copy"));
+    return cuda_check(c, cudaStreamSynchronize(c->s), "hier sync");
+}
+
+int hier_start(gnb_ctx *c, int K, double tick, double courant, double t_span)
+{
+    return hier_run(c, k_hier_start, hier_args(c, 0, K, tick), courant, t_span, "hier start");
+}
+
+int hier_predict(gnb_ctx *c, long long T, double tick)
+{
+    const int n = (int)c->n;
+    gnb::counted(k_hier_predict)<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], c->hT0[0], c->hT1[0], c->hacc[0], n,
+                                                                    T, tick);
+    GNB_LAUNCH_CHECK(c, "hier predict");
+    return GNB_OK;
+}
+
+int hier_update(gnb_ctx *c, long long T, int K, double tick, double courant, double t_span)
+{
+    return hier_run(c, k_hier_update, hier_args(c, T, K, tick), courant, t_span, "hier update");
 }
 
 }  // namespace gnb

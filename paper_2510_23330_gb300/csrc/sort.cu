@@ -313,6 +313,7 @@ int morton_and_sort(gnb_ctx *c)
     gnb::counted(k_permute)<<<nb, 256, 0, c->s>>>(a, b, c->src, n);
     GNB_LAUNCH_CHECK(c, "permute");
     c->cur = 1 - c->cur;
+    if (c->hier_on) GNB_TRY(hier_permute(c));  // per-particle step state follows the particles
     return GNB_OK;
 }
 

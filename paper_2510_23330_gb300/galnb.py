@@ -34,10 +34,11 @@ GNB_CONV_AUTO = 0
 GNB_CONV_MMA_SYNC = 2
 
 FIELDS = ["X", "Y", "Z", "VX", "VY", "VZ", "AX", "AY", "AZ", "POT", "U", "DUDT", "RHO", "PRES", "CS", "H2",
-          "KEY", "ORDER", "NBR", "NODES", "GROUPS", "ID", "AGRAV_X", "AGRAV_Y", "AGRAV_Z"]
+          "KEY", "ORDER", "NBR", "NODES", "GROUPS", "ID", "AGRAV_X", "AGRAV_Y", "AGRAV_Z", "LEVEL"]
 F = {name: i for i, name in enumerate(FIELDS)}
 FIELD_DTYPE = {"X": np.float64, "Y": np.float64, "Z": np.float64, "H2": np.float64, "KEY": np.uint64,
-               "ORDER": np.int64, "NBR": np.int64, "NODES": np.int64, "GROUPS": np.int64, "ID": np.int64}
+               "ORDER": np.int64, "NBR": np.int64, "NODES": np.int64, "GROUPS": np.int64, "ID": np.int64,
+               "LEVEL": np.int32}
 STATS = ["N", "NGAS", "NODES", "GROUPS", "NPP", "NPC", "GAS_NODES", "KNN_PASSES", "NSYM", "MAXLEVEL"]
 
 
@@ -110,6 +111,9 @@ def _declare(L):
     L.gnb_integrate_cfl.argtypes = [_vp, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int64)]
     L.gnb_integrate_cfl.restype = C.c_int
+    L.gnb_integrate_hier.argtypes = [_vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_int64)]
+    L.gnb_integrate_hier.restype = C.c_int
     L.gnb_voxelise.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.c_double, C.c_int, _vp, C.c_int]
     L.gnb_voxelise.restype = C.c_int
     L.gnb_remap_regions.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.c_double, C.c_int, _vp, C.c_uint64,
@@ -213,6 +217,10 @@ def gnb_cfl_timestep(ctx, courant, dt):
 
 def gnb_integrate_cfl(ctx, t_span, courant, max_steps, gravity_mode, t_done, steps_done):
     return lib().gnb_integrate_cfl(ctx, t_span, courant, max_steps, gravity_mode, t_done, steps_done)
+
+
+def gnb_integrate_hier(ctx, t_span, courant, max_level, max_steps, gravity_mode, t_done, info):
+    return lib().gnb_integrate_hier(ctx, t_span, courant, max_level, max_steps, gravity_mode, t_done, info)
 
 
 def gnb_voxelise(ctx, nreg, centers, side, grid, out, on_device):
@@ -528,6 +536,15 @@ class Context:
         self._chk(gnb_integrate_cfl(self.h, float(t_span), float(courant), int(min(max_steps, 2**31 - 1)), mode,
                                     C.byref(t), C.byref(n)))
         return t.value, n.value
+
+    def integrate_hier(self, t_span, courant=0.3, max_level=20, max_steps=1 << 30, mode=GNB_GRAV_NONE):
+        """Plain integration over t_span with hierarchical individual
+        timesteps; returns (t, block steps, particle updates, wake-ups)."""
+        t = C.c_double(0.0)
+        info = (C.c_int64 * 3)()
+        self._chk(gnb_integrate_hier(self.h, float(t_span), float(courant), int(max_level),
+                                     int(min(max_steps, 2**31 - 1)), mode, C.byref(t), info))
+        return t.value, int(info[0]), int(info[1]), int(info[2])
 
     def voxelise(self, centers, side=60.0, grid=64):
         """Standardised grids [nreg, grid, grid, grid, 5] of the regions."""

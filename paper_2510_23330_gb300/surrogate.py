@@ -23,8 +23,9 @@ from . import galnb, ics
 
 
 def make_pair(seed: int, n: int = 100000, grid: int = 64, side: float = 60.0, courant: float = 0.3,
-              stream=None):
-    """(input grid, target grid, info) of one supernova region."""
+              stream=None, integrator: str = "cfl", max_level: int = 20):
+    """(input grid, target grid, info) of one supernova region, integrated
+    with the shared CFL step ("cfl") or individual timesteps ("hier")."""
     p = ics.sn_region(n, seed=seed, side=side)
     c = galnb.Context(stream=stream)
     c.set_particles(p)
@@ -32,12 +33,18 @@ def make_pair(seed: int, n: int = 100000, grid: int = 64, side: float = 60.0, co
     x = c.voxelise([(0.0, 0.0, 0.0)], side, grid)[0]
     c.inject_energy((0.0, 0.0, 0.0), ics.E_SN_CODE)
     t0 = time.perf_counter()
-    t, steps = c.integrate_cfl(ics.T_SN_END, courant, mode=galnb.GNB_GRAV_NONE)
+    if integrator == "hier":
+        t, steps, updates, wakes = c.integrate_hier(ics.T_SN_END, courant, max_level=max_level,
+                                                    mode=galnb.GNB_GRAV_NONE)
+        extra = {"updates": updates, "wakeups": wakes}
+    else:
+        t, steps = c.integrate_cfl(ics.T_SN_END, courant, mode=galnb.GNB_GRAV_NONE)
+        extra = {"updates": int(steps) * n}
     dt_wall = time.perf_counter() - t0
     c.compute_sph_density()
     y = c.voxelise([(0.0, 0.0, 0.0)], side, grid)[0]
     c.close()
-    return x, y, {"seed": seed, "steps": int(steps), "t": t, "seconds": dt_wall, "n": n}
+    return x, y, {"seed": seed, "steps": int(steps), "t": t, "seconds": dt_wall, "n": n, **extra}
 
 
 def rmse(a, b):
