@@ -61,7 +61,7 @@ struct GravSmem {
     float4 jp[GW_JP];
     float je[GW_JP];
     float4 c0[2][GW_JC], c1[2][GW_JC], c2[2][GW_JC];  // two buffers: one evaluated, one filling
-    int4 cnb[2][GW_JC];                                // raw cell corners of the buffer being filled
+    int4 cnb[GW_JC];  // raw cell corners of the buffer being filled (each thread converts its own slots)
     float4 red[GW_THREADS];
     int ws[32];
     int g;
@@ -252,7 +252,7 @@ __device__ __forceinline__ void cells_issue(GravSmem &S, const GravParams &p, in
 {
     for (int h = 0; h < 2; h++) {
         const int s = threadIdx.x + h * GW_THREADS, node = idx[h];
-        cp_async16_g(&S.cnb[b][s], &p.nb[node]);
+        cp_async16_g(&S.cnb[s], &p.nb[node]);
         cp_async16_g(&S.c0[b][s], &p.mo0[node]);
         cp_async16_g(&S.c1[b][s], &p.mo1[node]);
         cp_async16_g(&S.c2[b][s], &p.mo2[node]);
@@ -265,7 +265,7 @@ __device__ __forceinline__ void cells_convert(GravSmem &S, int b, const int *gre
 {
     for (int h = 0; h < 2; h++) {
         const int s = threadIdx.x + h * GW_THREADS;
-        const int4 C = S.cnb[b][s];
+        const int4 C = S.cnb[s];
         const float4 m0 = S.c0[b][s];
         S.c0[b][s] = make_float4(grid_off(C.x, gref[0], m0.x, unit), grid_off(C.y, gref[1], m0.y, unit),
                                  grid_off(C.z, gref[2], m0.z, unit), m0.w);
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
 
 // Evaluation of the walk's lists, one group per CTA (see the file comment).
 template <bool MASK, bool QUAD>
-__global__ void __launch_bounds__(GW_THREADS, 4) k_grav_eval(GravParams p)
+__global__ void __launch_bounds__(GW_THREADS, 5) k_grav_eval(GravParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GravSmem &S = *reinterpret_cast<GravSmem *>(smem_raw);
