@@ -79,7 +79,7 @@ static void free_gas(gnb_ctx *c)
     void *all[] = {c->gslot, c->gkey, c->gcx, c->gcy, c->gcz, c->ggrank, c->grx, c->gry, c->grz, c->gx, c->gy,
                    c->gz, c->gm, c->gvx, c->gvy, c->gvz, c->gu, c->gh2, c->gh, c->g64, c->grho, c->gP, c->gcs,
                    c->gRprev, c->gE, c->nbr, c->nd2, c->mut, c->rcnt, c->roff, c->rfill, c->rlist, c->hax,
-                   c->hay, c->haz, c->hdu, c->kflag, c->kR, c->kRb, c->kitem, c->gvsig};
+                   c->hay, c->haz, c->hdu, c->kflag, c->kR, c->kRb, c->kitem, c->gvsig, c->kwl[0], c->kwl[1]};
     for (void *q : all) dfree(c, q);
     c->gslot = nullptr; c->gkey = nullptr; c->gcx = c->gcy = c->gcz = c->ggrank = nullptr;
     c->grx = c->gry = c->grz = nullptr; c->gx = c->gy = c->gz = nullptr;
@@ -87,6 +87,7 @@ static void free_gas(gnb_ctx *c)
     c->grho = c->gP = c->gcs = c->gRprev = c->gE = nullptr; c->nbr = nullptr; c->nd2 = nullptr; c->mut = nullptr;
     c->rcnt = c->roff = c->rfill = c->rlist = nullptr; c->hax = c->hay = c->haz = c->hdu = nullptr;
     c->kflag = nullptr; c->kR = nullptr; c->kRb = nullptr; c->kitem = nullptr; c->gvsig = nullptr;
+    c->kwl[0] = c->kwl[1] = nullptr;
     tree_free(c, c->gt);
     c->gcap = 0;
 }
@@ -137,6 +138,7 @@ static int alloc_gas(gnb_ctx *c, int64_t ng)
     GNB_TRY(dalloc(c, &c->hdu, G));
     GNB_TRY(dalloc(c, &c->kflag, 2 * G + 1)); GNB_TRY(dalloc(c, &c->kR, 2 * G + 1));
     GNB_TRY(dalloc(c, &c->kRb, 2 * G + 1)); GNB_TRY(dalloc(c, &c->kitem, 2 * G + 1));
+    GNB_TRY(dalloc(c, &c->kwl[0], 2 * G + 1)); GNB_TRY(dalloc(c, &c->kwl[1], 2 * G + 1));
     c->gcap = ng;
     return GNB_OK;
 }

@@ -143,6 +143,7 @@ struct gnb_ctx {
     float *kR = nullptr;          // per hydro group search radius
     float2 *kRb = nullptr;        // per hydro group radius bracket (too small, too large)
     int2 *kitem = nullptr;        // kNN work items (first, count); groups then split particles
+    int *kwl[2] = {nullptr, nullptr};  // kNN worklists: items a pass hands to the next (ping-pong)
     int *kcount_d = nullptr;
 
     // supernova surrogate (surrogate.cu)

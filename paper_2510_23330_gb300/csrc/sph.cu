@@ -141,7 +141,10 @@ struct KnnParams {
     int4 *na, *nb;
     int2 *item;
     int *nitems;       // live count (splits append here)
-    const int *nsnap;  // count at the start of this pass (only these are processed)
+    const int *nsnap;  // entries of this pass's worklist
+    const int *wl_in;  // this pass's items (null: items 0 .. *nsnap - 1)
+    int *wl_out;       // items left for the next pass: retried radii and new single-particle items
+    int *nwl_out;
     int item_cap;
     const int *gcx, *gcy, *gcz, *ggrank;
     const float *grx, *gry, *grz, *gm, *gu;
@@ -170,7 +173,7 @@ struct KnnSmem {
     int un[KN_WARPS];
     int ui[KN_WARPS][KN_U];
     double uD[KN_WARPS][KN_U];
-    int nc, sp, g, under, over, split, bmin[3], bmax[3];
+    int nc, sp, g, wb, under, over, split, bmin[3], bmax[3];
     unsigned amax;
 };
 
@@ -255,14 +258,14 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
     KnnSmem &S = *reinterpret_cast<KnnSmem *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const float unit = (float)p.box[4];
-    const int ngroups = *p.nsnap;
+    const int ngroups = min(*p.nsnap, p.item_cap);
     const unsigned ltmask = (1u << lane) - 1u;
     for (;;) {
         __syncthreads();  // every thread has read the previous S.g
         if (tid == 0) S.g = atomicAdd(p.next, 1);
         __syncthreads();
-        const int gi = S.g;
-        if (gi >= ngroups) break;
+        if (S.g >= ngroups) break;
+        const int gi = p.wl_in ? p.wl_in[S.g] : S.g;
         if (p.kflag[gi] == 0) continue;  // uniform
         const int2 gitem = p.item[gi];
         const int4 ga = make_int4(gitem.x, gitem.y, 0, 0);
@@ -550,13 +553,15 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
             __syncthreads();
             if (tid == 0) {
                 S.g = atomicAdd(p.nitems, ga.y);
+                S.wb = atomicAdd(p.nwl_out, ga.y);
                 p.kflag[gi] = 0;
                 atomicAdd(p.remaining, 1);
             }
             __syncthreads();
             const int base = S.g;
             for (int k = tid; k < ga.y; k += KN_THREADS) {
-                if (base + k < p.item_cap) {
+                const bool fits = base + k < p.item_cap;
+                if (fits) {
                     p.item[base + k] = make_int2(ga.x + k, 1);
                     p.kR[base + k] = R;
                     p.kRb[base + k] = make_float2(0.f, 0.f);
@@ -564,6 +569,8 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
                 } else {
                     atomicOr(p.status, ST_KNN_OVERFLOW);
                 }
+                // an item that did not fit is replaced by the finished parent
+                if (S.wb + k < p.item_cap) p.wl_out[S.wb + k] = fits ? base + k : gi;
             }
             continue;
         }
@@ -581,7 +588,11 @@ __global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
             }
             p.kRb[gi] = rb;
             p.kflag[gi] = done ? 0 : 1;
-            if (!done) atomicAdd(p.remaining, 1);
+            if (!done) {
+                atomicAdd(p.remaining, 1);
+                const int w = atomicAdd(p.nwl_out, 1);
+                if (w < p.item_cap) p.wl_out[w] = gi;
+            }
         }
     }
 }
@@ -787,10 +798,22 @@ int sph_density(gnb_ctx *c)
     int passes = 0;
     const int rounds = 12;
     for (int round = 0; round < rounds; round++) {
-        // three device passes per host check; converged items are skipped
+        // three device passes per host check; each pass takes the worklist
+        // the previous one wrote (the first takes every item)
         for (int q = 0; q < 3; q++) {
+            const int o = passes & 1;
             cudaMemsetAsync(c->work_d, 0, 2 * sizeof(int), c->s);
-            cudaMemcpyAsync(c->work_d + 3, c->work_d + 2, sizeof(int), cudaMemcpyDeviceToDevice, c->s);
+            cudaMemsetAsync(c->work_d + 4 + o, 0, sizeof(int), c->s);
+            if (passes == 0) {
+                cudaMemcpyAsync(c->work_d + 3, c->work_d + 2, sizeof(int), cudaMemcpyDeviceToDevice, c->s);
+                p.nsnap = c->work_d + 3;
+                p.wl_in = nullptr;
+            } else {
+                p.nsnap = c->work_d + 4 + (o ^ 1);
+                p.wl_in = c->kwl[o ^ 1];
+            }
+            p.wl_out = c->kwl[o];
+            p.nwl_out = c->work_d + 4 + o;
             gnb::counted(k_knn)<<<g_knn_blocks, KN_THREADS, smem, c->s>>>(p);
             passes++;
         }
