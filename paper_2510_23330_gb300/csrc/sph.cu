@@ -31,7 +31,7 @@ namespace gnb {
 
 #define KN_THREADS 128
 #define KN_WARPS (KN_THREADS / 32)
-#define KN_CAP 1536
+#define KN_CAP 1024
 #define KN_STACK 768
 #define KN_BKT 256
 #define KN_U 64
