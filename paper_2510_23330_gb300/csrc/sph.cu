@@ -31,7 +31,7 @@ namespace gnb {
 
 #define KN_THREADS 128
 #define KN_WARPS (KN_THREADS / 32)
-#define KN_CAP 1024
+#define KN_CAP 768
 #define KN_STACK 768
 #define KN_BKT 256
 #define KN_U 64
@@ -252,7 +252,7 @@ __device__ __noinline__ float knn_radix_kth(KnnSmem &S, int w, int lane, int nc,
     return __uint_as_float(prefix);
 }
 
-__global__ void __launch_bounds__(KN_THREADS) k_knn(KnnParams p)
+__global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     KnnSmem &S = *reinterpret_cast<KnnSmem *>(smem_raw);
