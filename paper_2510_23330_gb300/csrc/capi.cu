@@ -79,7 +79,8 @@ static void free_gas(gnb_ctx *c)
     void *all[] = {c->gslot, c->gkey, c->gcx, c->gcy, c->gcz, c->ggrank, c->grx, c->gry, c->grz, c->gx, c->gy,
                    c->gz, c->gm, c->gvx, c->gvy, c->gvz, c->gu, c->gh2, c->gh, c->g64, c->grho, c->gP, c->gcs,
                    c->gRprev, c->gE, c->nbr, c->nd2, c->mut, c->rcnt, c->roff, c->rfill, c->rlist, c->hax,
-                   c->hay, c->haz, c->hdu, c->kflag, c->kR, c->kRb, c->kitem, c->gvsig, c->kwl[0], c->kwl[1]};
+                   c->hay, c->haz, c->hdu, c->kflag, c->kR, c->kRb, c->kitem, c->gvsig, c->kwl[0], c->kwl[1],
+                   c->gh2lo, c->gh2hi};
     for (void *q : all) dfree(c, q);
     c->gslot = nullptr; c->gkey = nullptr; c->gcx = c->gcy = c->gcz = c->ggrank = nullptr;
     c->grx = c->gry = c->grz = nullptr; c->gx = c->gy = c->gz = nullptr;
@@ -88,6 +89,7 @@ static void free_gas(gnb_ctx *c)
     c->rcnt = c->roff = c->rfill = c->rlist = nullptr; c->hax = c->hay = c->haz = c->hdu = nullptr;
     c->kflag = nullptr; c->kR = nullptr; c->kRb = nullptr; c->kitem = nullptr; c->gvsig = nullptr;
     c->kwl[0] = c->kwl[1] = nullptr;
+    c->gh2lo = c->gh2hi = nullptr;
     tree_free(c, c->gt);
     c->gcap = 0;
 }
@@ -139,6 +141,7 @@ static int alloc_gas(gnb_ctx *c, int64_t ng)
     GNB_TRY(dalloc(c, &c->kflag, 2 * G + 1)); GNB_TRY(dalloc(c, &c->kR, 2 * G + 1));
     GNB_TRY(dalloc(c, &c->kRb, 2 * G + 1)); GNB_TRY(dalloc(c, &c->kitem, 2 * G + 1));
     GNB_TRY(dalloc(c, &c->kwl[0], 2 * G + 1)); GNB_TRY(dalloc(c, &c->kwl[1], 2 * G + 1));
+    GNB_TRY(dalloc(c, &c->gh2lo, G)); GNB_TRY(dalloc(c, &c->gh2hi, G));
     c->gcap = ng;
     return GNB_OK;
 }

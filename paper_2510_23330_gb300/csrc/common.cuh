@@ -144,6 +144,7 @@ struct gnb_ctx {
     float2 *kRb = nullptr;        // per hydro group radius bracket (too small, too large)
     int2 *kitem = nullptr;        // kNN work items (first, count); groups then split particles
     int *kwl[2] = {nullptr, nullptr};  // kNN worklists: items a pass hands to the next (ping-pong)
+    float *gh2lo = nullptr, *gh2hi = nullptr;  // h^2 rounded down / up to FP32 (per gas)
     int *kcount_d = nullptr;
 
     // supernova surrogate (surrogate.cu)

@@ -159,6 +159,7 @@ struct KnnParams {
     int *nbr;
     float *nd2;
     double *h2;
+    float *h2lo, *h2hi;
     float *h, *E, *rho, *P, *cs;
     int *g64;
     float gamma;
@@ -537,6 +538,8 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
                     float u = p.gu[i];
                     float P = (p.gamma - 1.f) * rs * u;
                     p.h2[i] = hsq;
+                    p.h2lo[i] = __double2float_rd(hsq);
+                    p.h2hi[i] = __double2float_ru(hsq);
                     p.h[i] = hh;
                     p.g64[i] = h64;
                     p.E[i] = E;
@@ -599,30 +602,42 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
 
 // ---------------------------------------------------------------- symmetric lists
 // Bit k of mut[i] is set when entry k of N_i is mutual (i in N_j too), using
-// (d^2, gas rank) <= (h_j^2, rank of j's n_ngb-th neighbour); FP32 decides
-// unless d lies within the error bound of h_j^2, then FP64 decides.
+// (d^2, gas rank) <= (h_j^2, rank of j's n_ngb-th neighbour).  The FP32 d^2
+// lies within 2 E_i of the FP64 one; the interval [d - 2E, d + 2E], widened
+// by directed rounding, is first compared with h_j^2 rounded down and up to
+// FP32 (no FP64 work: GB300 issues FP64 at a small fraction of the FP32
+// rate).  Only a pair that test leaves open takes the FP64 test and, within
+// its band, the exact FP64 d^2.  Every decision the FP32 test takes is the
+// one the FP64 test would take.
 __global__ void k_mutual(int ng, const int *__restrict__ nbr, const float *__restrict__ nd2,
-                         const float *__restrict__ E, const double *__restrict__ h2, const int *__restrict__ g64,
-                         const int *__restrict__ grank, const double *__restrict__ x, const double *__restrict__ y,
-                         const double *__restrict__ z, unsigned long long *__restrict__ mut, int *__restrict__ rcnt)
+                         const float *__restrict__ E, const double *__restrict__ h2, const float *__restrict__ h2lo,
+                         const float *__restrict__ h2hi, const int *__restrict__ g64, const int *__restrict__ grank,
+                         const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                         unsigned long long *__restrict__ mut, int *__restrict__ rcnt)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ng) return;
     unsigned long long mask = 0ull;
-    float Ei = E[i];
+    const float Ei = E[i];
+    const float e2 = 2.f * Ei;  // exact
     int gi = grank[i];
     for (int k = 0; k < NGB; k++) {
         int j = nbr[(size_t)i * NGB + k];
         if (j == i) { mask |= 1ull << k; continue; }
-        double d = (double)nd2[(size_t)i * NGB + k];
-        double hj = h2[j];
-        double e = 2.0 * (double)Ei;
+        const float df = nd2[(size_t)i * NGB + k];
         bool m;
-        if (d + e < hj) m = true;
-        else if (d - e > hj) m = false;
+        if (__fadd_ru(df, e2) < h2lo[j]) m = true;
+        else if (__fsub_rd(df, e2) > h2hi[j]) m = false;
         else {
-            double D = exact_d2(x, y, z, i, j);
-            m = (D < hj) || (D == hj && gi <= g64[j]);
+            double d = (double)df;
+            double hj = h2[j];
+            double e = 2.0 * (double)Ei;
+            if (d + e < hj) m = true;
+            else if (d - e > hj) m = false;
+            else {
+                double D = exact_d2(x, y, z, i, j);
+                m = (D < hj) || (D == hj && gi <= g64[j]);
+            }
         }
         if (m) mask |= 1ull << k;
         else atomicAdd(&rcnt[j], 1);
@@ -783,7 +798,7 @@ int sph_density(gnb_ctx *c)
     p.gx = c->gx; p.gy = c->gy; p.gz = c->gz; p.box = c->box_d;
     p.kR = c->kR; p.kRb = c->kRb; p.kflag = c->kflag;
     p.next = c->work_d; p.remaining = c->work_d + 1; p.status = c->status_d;
-    p.nbr = c->nbr; p.nd2 = c->nd2; p.h2 = c->gh2; p.h = c->gh; p.E = c->gE; p.rho = c->grho; p.P = c->gP;
+    p.nbr = c->nbr; p.nd2 = c->nd2; p.h2 = c->gh2; p.h2lo = c->gh2lo; p.h2hi = c->gh2hi; p.h = c->gh; p.E = c->gE; p.rho = c->grho; p.P = c->gP;
     p.cs = c->gcs; p.g64 = c->g64; p.gamma = (float)c->cfg.gamma;
     size_t smem = sizeof(KnnSmem);
     cudaError_t e = cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -842,8 +857,8 @@ int sph_force(gnb_ctx *c)
     int gb = (ng + 255) / 256;
     phase_begin(c, GNB_T_FORCE);
     cudaMemsetAsync(c->rcnt, 0, sizeof(int) * ng, c->s);
-    gnb::counted(k_mutual)<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->nd2, c->gE, c->gh2, c->g64, c->ggrank, c->gx, c->gy, c->gz,
-                                   c->mut, c->rcnt);
+    gnb::counted(k_mutual)<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->nd2, c->gE, c->gh2, c->gh2lo, c->gh2hi, c->g64,
+                                                 c->ggrank, c->gx, c->gy, c->gz, c->mut, c->rcnt);
     GNB_TRY(device_scan(c, c->rcnt, c->roff, c->ngas_d, ng, c->rtot_d));
     cudaMemsetAsync(c->rfill, 0, sizeof(int) * ng, c->s);
     gnb::counted(k_rev_fill)<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->mut, c->roff, c->rfill, c->rlist);
