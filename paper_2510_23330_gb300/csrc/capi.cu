@@ -80,7 +80,7 @@ static void free_gas(gnb_ctx *c)
                    c->gz, c->gm, c->gvx, c->gvy, c->gvz, c->gu, c->gh2, c->gh, c->g64, c->grho, c->gP, c->gcs,
                    c->gRprev, c->gE, c->nbr, c->nd2, c->mut, c->rcnt, c->roff, c->rfill, c->rlist, c->hax,
                    c->hay, c->haz, c->hdu, c->kflag, c->kR, c->kRb, c->kitem, c->gvsig, c->kwl[0], c->kwl[1],
-                   c->gh2lo, c->gh2hi};
+                   c->gh2lo, c->gh2hi, c->fC, c->fR, c->fV, c->fQ};
     for (void *q : all) dfree(c, q);
     c->gslot = nullptr; c->gkey = nullptr; c->gcx = c->gcy = c->gcz = c->ggrank = nullptr;
     c->grx = c->gry = c->grz = nullptr; c->gx = c->gy = c->gz = nullptr;
@@ -90,6 +90,7 @@ static void free_gas(gnb_ctx *c)
     c->kflag = nullptr; c->kR = nullptr; c->kRb = nullptr; c->kitem = nullptr; c->gvsig = nullptr;
     c->kwl[0] = c->kwl[1] = nullptr;
     c->gh2lo = c->gh2hi = nullptr;
+    c->fC = nullptr; c->fR = nullptr; c->fV = nullptr; c->fQ = nullptr;
     tree_free(c, c->gt);
     c->gcap = 0;
 }
@@ -142,6 +143,8 @@ static int alloc_gas(gnb_ctx *c, int64_t ng)
     GNB_TRY(dalloc(c, &c->kRb, 2 * G + 1)); GNB_TRY(dalloc(c, &c->kitem, 2 * G + 1));
     GNB_TRY(dalloc(c, &c->kwl[0], 2 * G + 1)); GNB_TRY(dalloc(c, &c->kwl[1], 2 * G + 1));
     GNB_TRY(dalloc(c, &c->gh2lo, G)); GNB_TRY(dalloc(c, &c->gh2hi, G));
+    GNB_TRY(dalloc(c, &c->fC, G)); GNB_TRY(dalloc(c, &c->fR, G)); GNB_TRY(dalloc(c, &c->fV, G));
+    GNB_TRY(dalloc(c, &c->fQ, G));
     c->gcap = ng;
     return GNB_OK;
 }

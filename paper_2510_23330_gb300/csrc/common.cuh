@@ -145,6 +145,11 @@ struct gnb_ctx {
     int2 *kitem = nullptr;        // kNN work items (first, count); groups then split particles
     int *kwl[2] = {nullptr, nullptr};  // kNN worklists: items a pass hands to the next (ping-pong)
     float *gh2lo = nullptr, *gh2hi = nullptr;  // h^2 rounded down / up to FP32 (per gas)
+    // per-gas records the hydro force gathers for neighbour j (one pass packs them)
+    int4 *fC = nullptr;           // cell x, y, z, mass bits
+    float4 *fR = nullptr;         // residual x, y, z, 1/h
+    float4 *fV = nullptr;         // v x, y, z, sound speed
+    float2 *fQ = nullptr;         // rho, P / rho^2
     int *kcount_d = nullptr;
 
     // supernova surrogate (surrogate.cu)

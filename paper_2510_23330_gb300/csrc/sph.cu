@@ -663,37 +663,59 @@ __global__ void k_rev_fill(int ng, const int *__restrict__ nbr, const unsigned l
 struct ForceParams {
     int ng;
     const int *nbr, *roff, *rcnt, *rlist;
-    const int *gcx, *gcy, *gcz;
-    const float *grx, *gry, *grz, *gm, *gvx, *gvy, *gvz, *h, *rho, *P, *cs;
+    const int4 *C;    // neighbour records (k_force_pack)
+    const float4 *R, *V;
+    const float2 *Q;
     const double *box;
     float alpha;
     float *ax, *ay, *az, *du;
     float *vsig;  // largest signal velocity c_i + c_j - 3 min(w_ij, 0) over the pairs of i
 };
 
-__device__ __forceinline__ void pair_force(const ForceParams &p, int i, int j, float unit, int ci0, int ci1, int ci2,
+// One record set per gas particle so a pair gathers four records instead of
+// fourteen fields: {cell, mass}, {residual, 1/h}, {v, c}, {rho, P/rho^2}.
+__global__ void k_force_pack(int ng, const int *__restrict__ gcx, const int *__restrict__ gcy,
+                             const int *__restrict__ gcz, const float *__restrict__ grx, const float *__restrict__ gry,
+                             const float *__restrict__ grz, const float *__restrict__ gm, const float *__restrict__ gvx,
+                             const float *__restrict__ gvy, const float *__restrict__ gvz, const float *__restrict__ h,
+                             const float *__restrict__ rho, const float *__restrict__ P, const float *__restrict__ cs,
+                             int4 *__restrict__ C, float4 *__restrict__ R, float4 *__restrict__ V, float2 *__restrict__ Q)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ng) return;
+    const float rj = rho[j];
+    C[j] = make_int4(gcx[j], gcy[j], gcz[j], __float_as_int(gm[j]));
+    R[j] = make_float4(grx[j], gry[j], grz[j], 1.f / h[j]);
+    V[j] = make_float4(gvx[j], gvy[j], gvz[j], cs[j]);
+    Q[j] = make_float2(rj, P[j] / (rj * rj));
+}
+
+__device__ __forceinline__ void pair_force(const ForceParams &p, int j, float unit, int ci0, int ci1, int ci2,
                                            float ri0, float ri1, float ri2, float vi0, float vi1, float vi2,
                                            float hinv_i, float pi_, float rhoi, float csi, float &a0, float &a1,
                                            float &a2, float &du, float &vs)
 {
-    float dx = __fmaf_rn((float)(ci0 - p.gcx[j]), unit, ri0 - p.grx[j]);
-    float dy = __fmaf_rn((float)(ci1 - p.gcy[j]), unit, ri1 - p.gry[j]);
-    float dz = __fmaf_rn((float)(ci2 - p.gcz[j]), unit, ri2 - p.grz[j]);
+    const int4 Cj = p.C[j];
+    const float4 Rj = p.R[j];
+    const float4 Vj = p.V[j];
+    const float2 Qj = p.Q[j];
+    float dx = __fmaf_rn((float)(ci0 - Cj.x), unit, ri0 - Rj.x);
+    float dy = __fmaf_rn((float)(ci1 - Cj.y), unit, ri1 - Rj.y);
+    float dz = __fmaf_rn((float)(ci2 - Cj.z), unit, ri2 - Rj.z);
     float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz));
     float r = sqrtf(r2);
     float rinv = r > 0.f ? 1.f / r : 0.f;
-    float hj = p.h[j];
-    float dwi = kern_dw(r, hinv_i), dwj = kern_dw(r, 1.f / hj);
-    float rhoj = p.rho[j];
-    float pj_ = p.P[j] / (rhoj * rhoj);
-    float vx = vi0 - p.gvx[j], vy = vi1 - p.gvy[j], vz = vi2 - p.gvz[j];
+    float dwi = kern_dw(r, hinv_i), dwj = kern_dw(r, Rj.w);
+    float rhoj = Qj.x;
+    float pj_ = Qj.y;
+    float vx = vi0 - Vj.x, vy = vi1 - Vj.y, vz = vi2 - Vj.z;
     float w = (vx * dx + vy * dy + vz * dz) * rinv;
     float visc = 0.f;
-    float vsig = csi + p.cs[j] - 3.f * fminf(w, 0.f);
+    float vsig = csi + Vj.w - 3.f * fminf(w, 0.f);
     vs = fmaxf(vs, vsig);
     if (w < 0.f) visc = -0.5f * p.alpha * vsig * w / (0.5f * (rhoi + rhoj));
     float dwbar = 0.5f * (dwi + dwj);
-    float mj = p.gm[j];
+    float mj = __int_as_float(Cj.w);
     float f = mj * (pi_ * dwi + pj_ * dwj + visc * dwbar) * rinv;
     a0 -= f * dx;
     a1 -= f * dy;
@@ -706,22 +728,25 @@ __global__ void k_force(ForceParams p)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.ng) return;
     const float unit = (float)p.box[4];
-    int ci0 = p.gcx[i], ci1 = p.gcy[i], ci2 = p.gcz[i];
-    float ri0 = p.grx[i], ri1 = p.gry[i], ri2 = p.grz[i];
-    float vi0 = p.gvx[i], vi1 = p.gvy[i], vi2 = p.gvz[i];
-    float hinv = 1.f / p.h[i], rhoi = p.rho[i], csi = p.cs[i];
-    float pi_ = p.P[i] / (rhoi * rhoi);
+    const int4 Ci = p.C[i];
+    const float4 Ri = p.R[i];
+    const float4 Vi = p.V[i];
+    const float2 Qi = p.Q[i];
+    const int ci0 = Ci.x, ci1 = Ci.y, ci2 = Ci.z;
+    const float ri0 = Ri.x, ri1 = Ri.y, ri2 = Ri.z;
+    const float vi0 = Vi.x, vi1 = Vi.y, vi2 = Vi.z;
+    const float hinv = Ri.w, rhoi = Qi.x, csi = Vi.w;
+    const float pi_ = Qi.y;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, du = 0.f, vs = 2.f * csi;
     const int *nb = p.nbr + (size_t)i * NGB;
     for (int k = 0; k < NGB; k++) {
         int j = nb[k];
         if (j == i) continue;
-        pair_force(p, i, j, unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1, a2, du,
-                   vs);
+        pair_force(p, j, unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1, a2, du, vs);
     }
     int b = p.roff[i], e = b + p.rcnt[i];
     for (int k = b; k < e; k++)
-        pair_force(p, i, p.rlist[k], unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1,
+        pair_force(p, p.rlist[k], unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1,
                    a2, du, vs);
     p.ax[i] = a0;
     p.ay[i] = a1;
@@ -863,11 +888,13 @@ int sph_force(gnb_ctx *c)
     cudaMemsetAsync(c->rfill, 0, sizeof(int) * ng, c->s);
     gnb::counted(k_rev_fill)<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->mut, c->roff, c->rfill, c->rlist);
     GNB_LAUNCH_CHECK(c, "symmetric lists");
+    gnb::counted(k_force_pack)<<<gb, 256, 0, c->s>>>(ng, c->gcx, c->gcy, c->gcz, c->grx, c->gry, c->grz, c->gm, c->gvx,
+                                                     c->gvy, c->gvz, c->gh, c->grho, c->gP, c->gcs, c->fC, c->fR,
+                                                     c->fV, c->fQ);
     ForceParams p;
     p.ng = ng; p.nbr = c->nbr; p.roff = c->roff; p.rcnt = c->rcnt; p.rlist = c->rlist;
-    p.gcx = c->gcx; p.gcy = c->gcy; p.gcz = c->gcz; p.grx = c->grx; p.gry = c->gry; p.grz = c->grz;
-    p.gm = c->gm; p.gvx = c->gvx; p.gvy = c->gvy; p.gvz = c->gvz; p.h = c->gh; p.rho = c->grho; p.P = c->gP;
-    p.cs = c->gcs; p.box = c->box_d; p.alpha = (float)c->cfg.alpha_visc;
+    p.C = c->fC; p.R = c->fR; p.V = c->fV; p.Q = c->fQ;
+    p.box = c->box_d; p.alpha = (float)c->cfg.alpha_visc;
     p.ax = c->hax; p.ay = c->hay; p.az = c->haz; p.du = c->hdu; p.vsig = c->gvsig;
     gnb::counted(k_force)<<<(ng + 127) / 128, 128, 0, c->s>>>(p);
     gnb::counted(k_gas_scatter)<<<gb, 256, 0, c->s>>>(ng, c->gslot, c->hax, c->hay, c->haz, c->hdu, c->ax, c->ay, c->az,
