@@ -50,6 +50,7 @@ struct Tree {
     int cap = 0;       // node capacity
     int nnodes = 0;    // nodes of the last build (host copy)
     int maxlev = 0;
+    int depth = GNB_MAXLEV;  // deepest non-empty level of the last build (host; bounds the next one's launches)
     // node arrays
     int4 *na = nullptr;   // {first, count, child, (nchild << 8) | level}
     int4 *nb = nullptr;   // {corner x, corner y, corner z, parent}

@@ -433,33 +433,47 @@ int build_tree(gnb_ctx *c, Tree &t, const uint64_t *skey, int n, const int *n_d,
     for (int attempt = 0; attempt < 6; attempt++) {
         if (t.cap < 64) GNB_TRY(tree_alloc(c, t, n + n / 2 + 1024));
         gnb::counted(k_tree_root)<<<1, 32, 0, c->s>>>(t, n);
-        for (int l = 0; l < GNB_MAXLEV; l++) {
-            gnb::counted(k_split_count)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, l, n_leaf);
-            gnb::counted(k_level_scan)<<<1, 1024, 0, c->s>>>(t, l, TB_BLOCKS, c->status_d);
-            gnb::counted(k_emit)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, l);
+        // Levels down to two below the last build's depth, then one check of
+        // the overflow flag and the level table; the remaining levels run only
+        // if the last level built still holds nodes (the tree got deeper).
+        int from = 0, L = std::min(GNB_MAXLEV, t.depth + 2);
+        bool over = false;
+        const int *lv = c->pinned_i + 1;  // level table copy [GNB_MAXLEV + 2]
+        for (;;) {
+            for (int l = from; l < L; l++) {
+                gnb::counted(k_split_count)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, l, n_leaf);
+                gnb::counted(k_level_scan)<<<1, 1024, 0, c->s>>>(t, l, TB_BLOCKS, c->status_d);
+                gnb::counted(k_emit)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, l);
+            }
+            if (L == GNB_MAXLEV) gnb::counted(k_split_count)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, GNB_MAXLEV, n_leaf);
+            GNB_LAUNCH_CHECK(c, "tree build");
+            cudaMemcpyAsync(c->pinned_i, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+            cudaMemcpyAsync(c->pinned_i + 1, t.lvl, sizeof(int) * (GNB_MAXLEV + 2), cudaMemcpyDeviceToHost, c->s);
+            GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "tree build sync"));
+            if (c->pinned_i[0] & ST_TREE_OVERFLOW) {
+                over = true;
+                break;
+            }
+            if (L == GNB_MAXLEV || lv[L + 1] == lv[L]) break;  // level L is empty: the tree is complete
+            from = L;
+            L = GNB_MAXLEV;
         }
-        gnb::counted(k_split_count)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, skey, GNB_MAXLEV, n_leaf);
-        GNB_LAUNCH_CHECK(c, "tree build");
-        // one check of the overflow flag per build
-        int h[2];
-        cudaMemcpyAsync(c->pinned_i, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->s);
-        cudaMemcpyAsync(c->pinned_i + 1, t.lvl + GNB_MAXLEV + 1, sizeof(int), cudaMemcpyDeviceToHost, c->s);
-        GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "tree build sync"));
-        h[0] = c->pinned_i[0];
-        h[1] = c->pinned_i[1];
-        if (h[0] & ST_TREE_OVERFLOW) {
+        if (over) {
             int zero = 0;
             cudaMemcpyAsync(c->status_d, &zero, sizeof(int), cudaMemcpyHostToDevice, c->s);
             cudaStreamSynchronize(c->s);
             GNB_TRY(tree_alloc(c, t, t.cap * 2));
             continue;
         }
-        t.nnodes = h[1];
+        t.nnodes = lv[GNB_MAXLEV + 1];
+        t.depth = 0;
+        for (int l = 0; l <= GNB_MAXLEV; l++)
+            if (lv[l + 1] > lv[l]) t.depth = l;
         break;
     }
     if (t.nnodes <= 0) return fail(c, GNB_ECAPACITY, "tree node capacity");
     if (moments) {
-        for (int l = GNB_MAXLEV; l >= 0; l--)
+        for (int l = t.depth; l >= 0; l--)  // deeper levels are empty
             gnb::counted(k_moments_level)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(t, l, pcx, pcy, pcz, prx, pry, prz, pm, peps,
                                                                 c->box_d);
         GNB_LAUNCH_CHECK(c, "moments");
