@@ -625,6 +625,8 @@ def integrate_hier(s: dict, t_span: float, courant: float, cfg: Config, max_leve
         up = np.where(gas, s["u"] + acc[3] * tau, 0.0)
         f = force_fn(s, u=up, v=vp)
         kc, mg = cfl_level(f)
+        if np.any(kc < 0):
+            raise ValueError("a CFL step is shorter than the finest level")
         margin = min(margin, mg)
         due = T1 == T
         wake = ~due & (kc > lev)
@@ -644,8 +646,6 @@ def integrate_hier(s: dict, t_span: float, courant: float, cfg: Config, max_leve
             acc[a] = np.where(active, new[a], acc[a])
         kick(active, acc, ((T - T0) // 2).astype(np.float64) * tick)  # closing half kicks
         if T < NT:
-            if np.any(kc[active] < 0):
-                raise ValueError("a CFL step is shorter than the finest level")
             lev = np.where(active, np.maximum(kc, hier_align_level(T, K)), lev)
             T0 = np.where(active, T, T0)
             T1 = np.where(active, T + np.left_shift(np.int64(1), K + 1 - lev), T1)
