@@ -838,9 +838,9 @@ int sph_density(gnb_ctx *c)
     int passes = 0;
     const int rounds = 12;
     for (int round = 0; round < rounds; round++) {
-        // three device passes per host check; each pass takes the worklist
+        // four device passes per host check; each pass takes the worklist
         // the previous one wrote (the first takes every item)
-        for (int q = 0; q < 3; q++) {
+        for (int q = 0; q < 4; q++) {
             const int o = passes & 1;
             cudaMemsetAsync(c->work_d, 0, 2 * sizeof(int), c->s);
             cudaMemsetAsync(c->work_d + 4 + o, 0, sizeof(int), c->s);
