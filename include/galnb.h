@@ -88,7 +88,7 @@ enum gnb_field {
     GNB_F_PRES,                     /* pressure, 0 for stars [float, n] */
     GNB_F_CS,                       /* sound speed, 0 for stars [float, n] */
     GNB_F_H2,                       /* squared kernel support h^2, 0 for stars [double, n] */
-    GNB_F_KEY,                      /* Morton key of the last tree build [uint64, n] */
+    GNB_F_KEY,                      /* Morton key of the last sort [uint64, n] */
     GNB_F_ORDER,                    /* original index of the particle at each sorted slot [int64, n] */
     GNB_F_NBR,                      /* neighbour lists: n_ngb original indices per gas particle,
                                        ascending [int64, n_gas * n_ngb] */
@@ -184,8 +184,11 @@ int gnb_compute_sph_density(gnb_ctx *ctx);
  * change of positions.  Errors: GNB_ESTATE, GNB_ECUDA. */
 int gnb_compute_sph_force(gnb_ctx *ctx);
 
-/* Total force evaluation: tree build, gravity (mode), NFW, SPH density and
- * force.  Errors: as the calls above. */
+/* Total force evaluation: sort and tree build, gravity (mode), NFW, SPH
+ * density and force.  With GNB_GRAV_NONE (and in the integrators below with
+ * that mode) the particles are sorted but the gravity tree is not built:
+ * GNB_F_NODES and GNB_F_GROUPS then return GNB_ESTATE.  Errors: as the calls
+ * above. */
 int gnb_compute_forces(gnb_ctx *ctx, int gravity_mode);
 
 /* nsteps kick-drift-kick leapfrog steps with shared timestep dt (Sec. 3.2):

@@ -238,7 +238,7 @@ int gnb_set_config(gnb_ctx *c, const gnb_config *cfg)
     cudaStreamSynchronize(c->s);
     c->cfg = *cfg;
     c->s = (cudaStream_t)cfg->cuda_stream;
-    c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    c->sorted_valid = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
     return GNB_OK;
 }
 
@@ -319,7 +319,7 @@ int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *t
     if (c->sna_pending) return fail(c, GNB_ESTATE, "an asynchronous surrogate batch is pending");
     if (!id || !type || !x || !y || !z || !vx || !vy || !vz || !m || !eps || !u)
         return fail(c, GNB_EINVAL, "null array");
-    c->have_particles = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = false;
+    c->have_particles = c->sorted_valid = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = false;
     c->sphf_valid = false;
     c->have_h = false;
     c->hier_on = c->hier_valid = false;
@@ -429,10 +429,20 @@ static void phase_resolve(gnb_ctx *c)
     c->pend.clear();
 }
 
-static int do_build(gnb_ctx *c)
+// Root box, keys and the Morton-order permutation of all particle arrays.
+static int do_sort(gnb_ctx *c)
 {
     phase_begin(c, GNB_T_SORT);
     GNB_TRY(morton_and_sort(c));
+    phase_end(c);
+    c->sorted_valid = true;
+    c->tree_valid = false;
+    return GNB_OK;
+}
+
+static int do_build(gnb_ctx *c)
+{
+    GNB_TRY(do_sort(c));
     phase_begin(c, GNB_T_TREE);
     PArr &a = c->P[c->cur];
     GNB_TRY(build_tree(c, c->t, c->skey, (int)c->n, c->n_d, c->cfg.n_leaf, c->cfg.n_group, a.cx, a.cy, a.cz, a.rx,
@@ -445,6 +455,7 @@ static int do_build(gnb_ctx *c)
 
 static int read_groups(gnb_ctx *c)
 {
+    if (!c->tree_valid) return GNB_OK;  // no gravity tree for the current positions (gravity off)
     GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->pinned_i + 8, c->t.ngroups_d, sizeof(int), cudaMemcpyDeviceToHost, c->s),
                        "groups count"));
     GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->pinned_i + 9, c->t.lvl, sizeof(int) * (GNB_MAXLEV + 2),
@@ -483,7 +494,9 @@ static int do_gravity(gnb_ctx *c, int mode)
 
 static int do_forces(gnb_ctx *c, int mode)
 {
-    GNB_TRY(do_build(c));
+    // without self-gravity only the hydro tree is needed, which the sorted
+    // gas particles give
+    GNB_TRY(mode == GNB_GRAV_NONE ? do_sort(c) : do_build(c));
     GNB_TRY(do_gravity(c, mode));
     GNB_TRY(sph_density(c));
     c->density_valid = true;
@@ -502,7 +515,7 @@ static int kdk_one(gnb_ctx *c, double dt, int mode)
     if (rc == GNB_OK) rc = drift(c, dt);
     if (rc == GNB_OK) rc = predict(c, hdt);
     phase_end(c);
-    c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    c->sorted_valid = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
     c->use_pred = true;
     if (rc == GNB_OK) rc = do_forces(c, mode);
     c->use_pred = false;
@@ -709,7 +722,7 @@ int gnb_integrate_hier(gnb_ctx *c, double t_span, double courant, int max_level,
         rc = drift(c, dd);
         if (rc == GNB_OK) rc = hier_predict(c, T, tick);
         phase_end(c);
-        c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+        c->sorted_valid = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
         c->use_pred = true;
         if (rc == GNB_OK) rc = do_forces(c, mode);
         c->use_pred = false;
@@ -767,7 +780,7 @@ int gnb_remap_regions(gnb_ctx *c, int nreg, const double *centers, double side, 
         pd = c->vout;
     }
     if (rc == GNB_OK) rc = remap_regions(c, nreg, centers, side, grid, pd, seed, sweeps);
-    c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    c->sorted_valid = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
     return finish(c, rc);
 }
 
@@ -780,7 +793,7 @@ int gnb_sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *ce
     if (!c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed for the current positions");
     if (c->sna_pending) return fail(c, GNB_ESTATE, "an asynchronous surrogate batch is pending");
     int rc = sn_surrogate_batch(c, net, nreg, centers, side, seed, sweeps, use_graph);
-    c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    c->sorted_valid = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
     rc = finish(c, rc);
     if (rc == GNB_OK && unet_poll_error(net) != GNB_OK)
         return fail(c, GNB_ETIMEOUT, "a bounded wait in the U-Net's tensor-core convolution ran out");
@@ -805,11 +818,13 @@ int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
     c->err.clear();
     if (!dst || field < 0 || field >= GNB_F_COUNT_) return fail(c, GNB_EINVAL, "field or destination");
     if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
-    bool need_tree = field == GNB_F_KEY || field == GNB_F_ORDER || field == GNB_F_NODES || field == GNB_F_GROUPS;
+    bool need_sort = field == GNB_F_KEY || field == GNB_F_ORDER;
+    bool need_tree = field == GNB_F_NODES || field == GNB_F_GROUPS;
     bool need_grav = field == GNB_F_AX || field == GNB_F_AY || field == GNB_F_AZ || field == GNB_F_POT ||
                      field == GNB_F_AGRAV_X || field == GNB_F_AGRAV_Y || field == GNB_F_AGRAV_Z;
     bool need_den = field == GNB_F_RHO || field == GNB_F_PRES || field == GNB_F_CS || field == GNB_F_H2 ||
                     field == GNB_F_NBR;
+    if (need_sort && !c->sorted_valid) return fail(c, GNB_ESTATE, "particles not sorted for the current positions");
     if (need_tree && !c->tree_valid) return fail(c, GNB_ESTATE, "tree not built");
     bool total_acc = field == GNB_F_AX || field == GNB_F_AY || field == GNB_F_AZ;
     if (need_grav && !c->gravity_valid && !(total_acc && c->sphf_valid))
@@ -889,7 +904,7 @@ int gnb_sn_async_apply(gnb_ctx *c)
     if (!c) return GNB_EINVAL;
     c->err.clear();
     int rc = sn_async_apply(c);
-    if (rc == GNB_OK) c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    if (rc == GNB_OK) c->sorted_valid = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
     rc = finish(c, rc);
     if (rc == GNB_OK && unet_poll_error((gnb_unet *)c->sna_net) != GNB_OK)
         return fail(c, GNB_ETIMEOUT, "a bounded wait in the U-Net's tensor-core convolution ran out");

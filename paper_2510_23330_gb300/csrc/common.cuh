@@ -243,6 +243,7 @@ struct gnb_ctx {
 
     // state flags
     bool have_particles = false, tree_valid = false, gravity_valid = false;
+    bool sorted_valid = false;  // particles in Morton order for the current positions (keys, order)
     bool density_valid = false, force_valid = false, have_h = false, sphf_valid = false;
     bool use_pred = false;      // SPH uses predicted v, u (inside a KDK step)
     int last_grav_mode = -1;
