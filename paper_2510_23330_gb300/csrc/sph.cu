@@ -173,7 +173,8 @@ struct KnnSmem {
     int bn[KN_WARPS];
     int un[KN_WARPS];
     int ui[KN_WARPS][KN_U];
-    double uD[KN_WARPS][KN_U];
+    long long uD[KN_WARPS][KN_U];  // exact FP64 d^2 as bit patterns (non-negative: they order like the values)
+    int ug[KN_WARPS][KN_U];        // gas ranks of the uncertain entries
     int nc, sp, g, wb, under, over, split, bmin[3], bmax[3];
     unsigned amax;
 };
@@ -494,27 +495,30 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
                     if (lane == 0) knn_fail(S, ga.y, p.status);
                     continue;
                 }
-                for (int e = lane; e < nu; e += 32) S.uD[w][e] = exact_d2(p.gx, p.gy, p.gz, i, S.ui[w][e]);
+                for (int e = lane; e < nu; e += 32) {
+                    const int je = S.ui[w][e];
+                    S.uD[w][e] = __double_as_longlong(exact_d2(p.gx, p.gy, p.gz, i, je));
+                    S.ug[w][e] = p.ggrank[je];
+                }
                 __syncwarp();
                 const int need = NGB - nS;
                 double hsq = 0.0;
                 int h64 = -1;
                 bool have = false;
                 for (int e = lane; e < nu; e += 32) {
-                    double De = S.uD[w][e];
-                    int je = S.ui[w][e];
-                    int ge = p.ggrank[je];
+                    const long long De = S.uD[w][e];
+                    const int je = S.ui[w][e];
+                    const int ge = S.ug[w][e];
                     int r = 0;
-                    for (int f = 0; f < nu; f++) {
-                        double Df = S.uD[w][f];
-                        int gf = p.ggrank[S.ui[w][f]];
-                        r += (Df < De) || (Df == De && gf < ge);
+                    for (int f = 0; f < nu; f++) {  // integer compares: no FP64 work
+                        const long long Df = S.uD[w][f];
+                        r += (Df < De) || (Df == De && S.ug[w][f] < ge);
                     }
                     if (r < need) {
                         outn[nS + r] = je;
-                        outd[nS + r] = (float)De;
+                        outd[nS + r] = (float)__longlong_as_double(De);
                     }
-                    if (r == need - 1) { hsq = De; h64 = ge; have = true; }
+                    if (r == need - 1) { hsq = __longlong_as_double(De); h64 = ge; have = true; }
                 }
                 unsigned hb = __ballot_sync(0xffffffffu, have);
                 if (hb == 0u) {  // error bound violated: fewer uncertain entries than needed
