@@ -95,3 +95,35 @@ def test_hier_errors_leave_the_context_usable(G):
     t, steps, updates, wakes = c.integrate_hier(1e-4, 0.3, max_level=20)
     assert t == 1e-4 and steps >= 1 and updates >= len(p["m"])
     assert np.all(np.isfinite(c.get("X"))) and c.get("LEVEL").min() >= 0
+
+
+@pytest.mark.parametrize("max_steps", [3, 1 << 20])
+def test_hier_with_direct_gravity_matches_oracle(G, orc, max_steps):
+    """Stars and gas under direct self-gravity (stars on level 0, gas on its
+    CFL levels; the force passes sort and build the gravity tree, so the step
+    state must follow the particles through every sort).  Stopping after
+    max_steps block steps leaves the same unsynchronised state as the
+    oracle's."""
+    p = ics.plummer(3000, seed=3, n_gas=1000, u_gas=0.05)
+    cfg = orc.Config(gravity="direct")
+    s = orc.state(p)
+    f = orc.forces(s, cfg)
+    span = 7.3 * float(np.min(orc.cfl_steps(f, len(s["x"]), 0.3)))
+    ref, _, info = orc.integrate_hier(s, span, 0.3, cfg, max_level=10, max_steps=max_steps)
+    assert info["margin"] > 1e-4 and len(set(info["level"])) >= 3
+    c = G.Context()
+    c.set_particles(p)
+    t, steps, updates, wakes = c.integrate_hier(span, 0.3, max_level=10, max_steps=max_steps,
+                                                mode=G.GNB_GRAV_DIRECT)
+    assert t == info["t"] and (steps, updates, wakes) == (info["steps"], info["updates"], info["wakeups"])
+    assert (t < span) == (max_steps == 3)
+    assert np.array_equal(c.get("LEVEL"), info["level"])
+    r = np.sqrt(ref["x"] ** 2 + ref["y"] ** 2 + ref["z"] ** 2)
+    for k in ("X", "Y", "Z"):
+        assert np.max(np.abs(c.get(k) - ref[k.lower()])) < 1e-5 * np.percentile(r, 90)
+    vmax = np.max(np.abs(ref["vx"]))
+    for k in ("VX", "VY", "VZ"):
+        assert np.max(np.abs(c.get(k) - ref[k.lower()])) < 1e-4 * vmax
+    gas = p["type"] == 1
+    u = c.get("U")
+    assert np.max(np.abs(u[gas] - ref["u"][gas]) / np.abs(ref["u"][gas])) < 1e-3
