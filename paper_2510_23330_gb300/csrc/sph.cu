@@ -19,9 +19,12 @@
 //   3. entries with d < t - 2E are certainly neighbours, entries with
 //      d > t + 2E certainly not; only the few in between get the exact FP64
 //      d^2 and are ranked by (d^2, gas rank).
-// A group whose radius holds fewer than n_ngb particles for some member, or
-// more candidates than fit, retries with a bisected radius (the paper's
-// "usually twice").  Density and the ideal-gas EOS are fused in.
+// A group whose radius holds fewer than n_ngb particles for some member
+// retries with a larger radius (bisected once both bounds are known: the
+// paper's "usually twice"); a group whose candidates do not fit is split into
+// single-particle items, and a single particle whose candidates do not fit
+// retries with a smaller radius.  Each pass hands the next only its
+// unfinished items.  Density and the ideal-gas EOS are fused in.
 //
 // Force: symmetric SPH over S_i = N_i u {j : i in N_j}.  The reverse part is
 // built from the non-mutual pairs only, so N_i and R_i are disjoint.
@@ -31,6 +34,8 @@ namespace gnb {
 
 #define KN_THREADS 128
 #define KN_WARPS (KN_THREADS / 32)
+// Candidate buffer and node stack size the shared memory of a CTA (24.7 KB),
+// and with it the CTAs per SM (9, as the 56 registers allow).
 #define KN_CAP 768
 #define KN_STACK 768
 #define KN_BKT 256
