@@ -96,23 +96,40 @@ __device__ __forceinline__ bool must_open(int4 C, int level, const int *bmin, co
 // Particle-particle: accumulate sum m_j (x_j - x_i)/R^3 and sum m_j/R, with
 // R^2 = |x_j - x_i|^2 + eps_i^2 + eps_j^2.
 template <bool MASK>
+__device__ __forceinline__ void pp_one(float4 q, float e, float xi, float yi, float zi, float e2i, float &ax,
+                                       float &ay, float &az, float &ph)
+{
+    float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
+    float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, e + e2i)));
+    float ri = rsqrtf(r2);
+    if (MASK) ri = r2 > 0.f ? ri : 0.f;
+    float mr = q.w * ri;
+    float mr3 = mr * ri * ri;
+    ax = __fmaf_rn(mr3, dx, ax);
+    ay = __fmaf_rn(mr3, dy, ay);
+    az = __fmaf_rn(mr3, dz, az);
+    ph += mr;
+}
+
+template <bool MASK>
 __device__ __forceinline__ void pp_loop(const GravSmem &S, int np, int split, int js, float xi, float yi, float zi,
                                         float e2i, float &ax, float &ay, float &az, float &ph)
 {
 #pragma unroll 4
+    for (int j = split; j < np; j += js) pp_one<MASK>(S.jp[j], S.je[j], xi, yi, zi, e2i, ax, ay, az, ph);
+}
+
+// Two i-particles per thread: each staged j entry is read once for both.
+template <bool MASK>
+__device__ __forceinline__ void pp_loop2(const GravSmem &S, int np, int split, int js, const float4 &i0,
+                                         const float4 &i1, float4 &a0, float4 &a1)
+{
+#pragma unroll 2
     for (int j = split; j < np; j += js) {
-        float4 q = S.jp[j];
-        float e = S.je[j];
-        float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
-        float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, e + e2i)));
-        float ri = rsqrtf(r2);
-        if (MASK) ri = r2 > 0.f ? ri : 0.f;
-        float mr = q.w * ri;
-        float mr3 = mr * ri * ri;
-        ax = __fmaf_rn(mr3, dx, ax);
-        ay = __fmaf_rn(mr3, dy, ay);
-        az = __fmaf_rn(mr3, dz, az);
-        ph += mr;
+        const float4 q = S.jp[j];
+        const float e = S.je[j];
+        pp_one<MASK>(q, e, i0.x, i0.y, i0.z, i0.w, a0.x, a0.y, a0.z, a0.w);
+        pp_one<MASK>(q, e, i1.x, i1.y, i1.z, i1.w, a1.x, a1.y, a1.z, a1.w);
     }
 }
 
@@ -120,39 +137,53 @@ __device__ __forceinline__ void pp_loop(const GravSmem &S, int np, int split, in
 //   a   += -M r/R^3 + Q r/R^5 - 5/2 (r.Q.r) r/R^7
 //   phi += -M/R - 1/2 r.Q.r/R^5         (accumulated with the sign flipped)
 template <bool QUAD>
+__device__ __forceinline__ void pc_one(float4 a, float4 b, float4 d, float xi, float yi, float zi, float e2i,
+                                       float &ax, float &ay, float &az, float &ph)
+{
+    float rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
+    float R2 = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, __fmaf_rn(rz, rz, e2i + d.z)));
+    float Ri = rsqrtf(R2);
+    float Ri2 = Ri * Ri;
+    float mR = a.w * Ri;
+    float mR3 = mR * Ri2;
+    if (QUAD) {
+        float qx = __fmaf_rn(b.x, rx, __fmaf_rn(b.w, ry, d.x * rz));
+        float qy = __fmaf_rn(b.w, rx, __fmaf_rn(b.y, ry, d.y * rz));
+        float qz = __fmaf_rn(d.x, rx, __fmaf_rn(d.y, ry, b.z * rz));
+        float rqr = __fmaf_rn(rx, qx, __fmaf_rn(ry, qy, rz * qz));
+        float Ri5 = Ri2 * Ri2 * Ri;
+        float Ri7 = Ri5 * Ri2;
+        float t = __fmaf_rn(2.5f * rqr, Ri7, mR3);
+        // two chained FMAs per component (Q r/R^5, then -t r)
+        ax = __fmaf_rn(-t, rx, __fmaf_rn(qx, Ri5, ax));
+        ay = __fmaf_rn(-t, ry, __fmaf_rn(qy, Ri5, ay));
+        az = __fmaf_rn(-t, rz, __fmaf_rn(qz, Ri5, az));
+        ph = __fmaf_rn(0.5f * rqr, Ri5, ph) + mR;
+    } else {
+        ax = __fmaf_rn(-mR3, rx, ax);
+        ay = __fmaf_rn(-mR3, ry, ay);
+        az = __fmaf_rn(-mR3, rz, az);
+        ph += mR;
+    }
+}
+
+template <bool QUAD>
 __device__ __forceinline__ void pc_loop(const GravSmem &S, int buf, int nc, int split, int js, float xi, float yi,
                                         float zi, float e2i, float &ax, float &ay, float &az, float &ph)
 {
 #pragma unroll 2
+    for (int c = split; c < nc; c += js)
+        pc_one<QUAD>(S.c0[buf][c], S.c1[buf][c], S.c2[buf][c], xi, yi, zi, e2i, ax, ay, az, ph);
+}
+
+template <bool QUAD>
+__device__ __forceinline__ void pc_loop2(const GravSmem &S, int buf, int nc, int split, int js, const float4 &i0,
+                                         const float4 &i1, float4 &a0, float4 &a1)
+{
     for (int c = split; c < nc; c += js) {
-        float4 a = S.c0[buf][c];
-        float4 b = S.c1[buf][c];
-        float4 d = S.c2[buf][c];
-        float rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
-        float R2 = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, __fmaf_rn(rz, rz, e2i + d.z)));
-        float Ri = rsqrtf(R2);
-        float Ri2 = Ri * Ri;
-        float mR = a.w * Ri;
-        float mR3 = mR * Ri2;
-        if (QUAD) {
-            float qx = __fmaf_rn(b.x, rx, __fmaf_rn(b.w, ry, d.x * rz));
-            float qy = __fmaf_rn(b.w, rx, __fmaf_rn(b.y, ry, d.y * rz));
-            float qz = __fmaf_rn(d.x, rx, __fmaf_rn(d.y, ry, b.z * rz));
-            float rqr = __fmaf_rn(rx, qx, __fmaf_rn(ry, qy, rz * qz));
-            float Ri5 = Ri2 * Ri2 * Ri;
-            float Ri7 = Ri5 * Ri2;
-            float t = __fmaf_rn(2.5f * rqr, Ri7, mR3);
-            // two chained FMAs per component (Q r/R^5, then -t r)
-            ax = __fmaf_rn(-t, rx, __fmaf_rn(qx, Ri5, ax));
-            ay = __fmaf_rn(-t, ry, __fmaf_rn(qy, Ri5, ay));
-            az = __fmaf_rn(-t, rz, __fmaf_rn(qz, Ri5, az));
-            ph = __fmaf_rn(0.5f * rqr, Ri5, ph) + mR;
-        } else {
-            ax = __fmaf_rn(-mR3, rx, ax);
-            ay = __fmaf_rn(-mR3, ry, ay);
-            az = __fmaf_rn(-mR3, rz, az);
-            ph += mR;
-        }
+        const float4 a = S.c0[buf][c], b = S.c1[buf][c], d = S.c2[buf][c];
+        pc_one<QUAD>(a, b, d, i0.x, i0.y, i0.z, i0.w, a0.x, a0.y, a0.z, a0.w);
+        pc_one<QUAD>(a, b, d, i1.x, i1.y, i1.z, i1.w, a1.x, a1.y, a1.z, a1.w);
     }
 }
 
@@ -426,19 +457,30 @@ __global__ void __launch_bounds__(GW_THREADS, 5) k_grav_eval(GravParams p)
         const int gref[3] = {gr.x, gr.y, gr.z};
         for (int i0 = 0; i0 < gcount; i0 += GW_THREADS) {
             const int icnt = min(GW_THREADS, gcount - i0);
-            // j-splits: each of the js = floor(128 / icnt) thread sets holds all
-            // icnt i-particles and takes every js-th j entry
-            const int ilanes = icnt;
+            // j-splits: each of the js thread sets holds all icnt i-particles
+            // and takes every js-th j entry.  Above 32 i-particles a thread
+            // holds two (slot s and s + ilanes), which halves the threads a
+            // set needs, so more sets fit in the CTA and each staged j entry
+            // is read once for both.
+            const bool two = icnt > 32;
+            const int ilanes = two ? (icnt + 1) >> 1 : icnt;
             const int js = GW_THREADS / ilanes;
             const int islot = tid % ilanes, split = tid / ilanes;
             const bool ivalid = split < js;
             const int ip = gfirst + i0 + islot;
+            const bool has2 = two && islot + ilanes < icnt;
+            const int ip2 = has2 ? ip + ilanes : ip;  // a duplicate of ip when there is no second particle
             const float xi = grid_off(p.cx[ip], gref[0], p.rx[ip], unit);
             const float yi = grid_off(p.cy[ip], gref[1], p.ry[ip], unit);
             const float zi = grid_off(p.cz[ip], gref[2], p.rz[ip], unit);
             const float epi = p.eps[ip];
             const float e2i = epi * epi;
-            float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+            const float ep2 = p.eps[ip2];
+            const float4 pi0 = make_float4(xi, yi, zi, e2i);
+            const float4 pi1 = make_float4(grid_off(p.cx[ip2], gref[0], p.rx[ip2], unit),
+                                           grid_off(p.cy[ip2], gref[1], p.ry[ip2], unit),
+                                           grid_off(p.cz[ip2], gref[2], p.rz[ip2], unit), ep2 * ep2);
+            float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
             // accepted cells, one chunk at a time, double buffered: while a
             // chunk is evaluated, cp.async fills the other buffer with the
             // next chunk (whose node indices were loaded one chunk earlier).
@@ -491,7 +533,10 @@ __global__ void __launch_bounds__(GW_THREADS, 5) k_grav_eval(GravParams p)
                         S.je[k] = ej * ej;
                     }
                     __syncthreads();
-                    if (ivalid) pp_loop<MASK>(S, np, split, js, xi, yi, zi, e2i, ax, ay, az, ph);
+                    if (ivalid) {
+                        if (two) pp_loop2<MASK>(S, np, split, js, pi0, pi1, acc0, acc1);
+                        else pp_loop<MASK>(S, np, split, js, xi, yi, zi, e2i, acc0.x, acc0.y, acc0.z, acc0.w);
+                    }
                     __syncthreads();
                 }
                 lch = lnx;
@@ -512,7 +557,10 @@ __global__ void __launch_bounds__(GW_THREADS, 5) k_grav_eval(GravParams p)
                         idx2[1] = p.pool[(size_t)nxt2 * GL_CH + tid + GW_THREADS];
                     }
                 }
-                if (ivalid) pc_loop<QUAD>(S, cb, nc, split, js, xi, yi, zi, e2i, ax, ay, az, ph);
+                if (ivalid) {
+                    if (two) pc_loop2<QUAD>(S, cb, nc, split, js, pi0, pi1, acc0, acc1);
+                    else pc_loop<QUAD>(S, cb, nc, split, js, xi, yi, zi, e2i, acc0.x, acc0.y, acc0.z, acc0.w);
+                }
                 if (cnx >= 0) {
                     cp_async_wait_all_g();
                     cells_convert(S, cb ^ 1, gref, unit);
@@ -524,19 +572,32 @@ __global__ void __launch_bounds__(GW_THREADS, 5) k_grav_eval(GravParams p)
                 idx[1] = idx2[1];
                 cb ^= 1;
             }
-            // reduce j-splits
-            S.red[tid] = make_float4(ax, ay, az, ph);
+            // reduce j-splits (the second particles' partial sums go through
+            // the PP staging buffer, idle here)
+            S.red[tid] = acc0;
+            if (two) S.jp[tid] = acc1;
             __syncthreads();
             if (split == 0 && ivalid) {
                 for (int s2 = 1; s2 < js; s2++) {
                     const float4 r = S.red[tid + s2 * ilanes];
-                    ax += r.x; ay += r.y; az += r.z; ph += r.w;
+                    acc0.x += r.x; acc0.y += r.y; acc0.z += r.z; acc0.w += r.w;
                 }
-                if (!MASK) ph -= p.m[ip] * rsqrtf(2.f * e2i);  // remove the j == i term
-                p.ax[ip] = p.G * ax;
-                p.ay[ip] = p.G * ay;
-                p.az[ip] = p.G * az;
-                p.pot[ip] = -p.G * ph;
+                if (!MASK) acc0.w -= p.m[ip] * rsqrtf(2.f * e2i);  // remove the j == i term
+                p.ax[ip] = p.G * acc0.x;
+                p.ay[ip] = p.G * acc0.y;
+                p.az[ip] = p.G * acc0.z;
+                p.pot[ip] = -p.G * acc0.w;
+                if (has2) {
+                    for (int s2 = 1; s2 < js; s2++) {
+                        const float4 r = S.jp[tid + s2 * ilanes];
+                        acc1.x += r.x; acc1.y += r.y; acc1.z += r.z; acc1.w += r.w;
+                    }
+                    if (!MASK) acc1.w -= p.m[ip2] * rsqrtf(2.f * pi1.w);
+                    p.ax[ip2] = p.G * acc1.x;
+                    p.ay[ip2] = p.G * acc1.y;
+                    p.az[ip2] = p.G * acc1.z;
+                    p.pot[ip2] = -p.G * acc1.w;
+                }
             }
             __syncthreads();
         }
