@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(GW_THREADS, 5) k_grav_eval(GravParams p)
             // holds two (slot s and s + ilanes), which halves the threads a
             // set needs, so more sets fit in the CTA and each staged j entry
             // is read once for both.
-            const bool two = icnt > 32;
+            const bool two = icnt > 16;
             const int ilanes = two ? (icnt + 1) >> 1 : icnt;
             const int js = GW_THREADS / ilanes;
             const int islot = tid % ilanes, split = tid / ilanes;
