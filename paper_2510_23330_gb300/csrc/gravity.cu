@@ -180,6 +180,7 @@ template <bool QUAD>
 __device__ __forceinline__ void pc_loop2(const GravSmem &S, int buf, int nc, int split, int js, const float4 &i0,
                                          const float4 &i1, float4 &a0, float4 &a1)
 {
+#pragma unroll 2
     for (int c = split; c < nc; c += js) {
         const float4 a = S.c0[buf][c], b = S.c1[buf][c], d = S.c2[buf][c];
         pc_one<QUAD>(a, b, d, i0.x, i0.y, i0.z, i0.w, a0.x, a0.y, a0.z, a0.w);
