@@ -124,7 +124,7 @@ template <bool MASK>
 __device__ __forceinline__ void pp_loop2(const GravSmem &S, int np, int split, int js, const float4 &i0,
                                          const float4 &i1, float4 &a0, float4 &a1)
 {
-#pragma unroll 2
+#pragma unroll 4
     for (int j = split; j < np; j += js) {
         const float4 q = S.jp[j];
         const float e = S.je[j];
