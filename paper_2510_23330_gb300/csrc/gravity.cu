@@ -456,10 +456,12 @@ __global__ void __launch_bounds__(GW_THREADS, 5) k_grav_eval(GravParams p)
         const int4 gh = p.ghead[gi];
         const int4 gr = p.gref[gi];
         const int gref[3] = {gr.x, gr.y, gr.z};
-        for (int i0 = 0; i0 < gcount; i0 += GW_THREADS) {
-            const int icnt = min(GW_THREADS, gcount - i0);
+        // up to two i-particles per thread: a group of up to 2 GW_THREADS
+        // particles streams its lists once
+        for (int i0 = 0; i0 < gcount; i0 += 2 * GW_THREADS) {
+            const int icnt = min(2 * GW_THREADS, gcount - i0);
             // j-splits: each of the js thread sets holds all icnt i-particles
-            // and takes every js-th j entry.  Above 32 i-particles a thread
+            // and takes every js-th j entry.  Above 16 i-particles a thread
             // holds two (slot s and s + ilanes), which halves the threads a
             // set needs, so more sets fit in the CTA and each staged j entry
             // is read once for both.
