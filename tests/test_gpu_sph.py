@@ -117,3 +117,25 @@ def test_disk_full_size_knn_sampled(G, orc):
     c, gi, g, ref_nbr, ref_h2 = _check_knn(G, orc, p, sample=s)
     rho, _, _ = orc.density(g, ref_nbr, ref_h2, sample=s)
     assert np.max(np.abs(c.get("RHO")[gi[s]] - rho) / rho) < TOL
+
+
+def test_knn_unrankable_clump_reports_ecapacity(G, orc):
+    """200 gas particles at one point: their 64 nearest neighbours are
+    exact ties at d = 0, more than the buffer of entries ranked in FP64 (64)
+    holds, so the search reports GNB_ECAPACITY after its bounded retries; the
+    context then works on a regular set."""
+    p = ics.uniform_random(3000, seed=11, gas_frac=1.0)
+    for k in ("x", "y", "z"):
+        p[k] = np.array(p[k], copy=True)
+        p[k][:200] = p[k][0]
+    c = G.Context()
+    c.set_particles(p)
+    with pytest.raises(G.GalnbError) as e:
+        c.compute_sph_density()
+    assert e.value.code == G.GNB_ECAPACITY
+    q = ics.uniform_random(3000, seed=12, gas_frac=1.0)
+    c.set_particles(q)
+    c.compute_sph_density()
+    gi, g = _gas(q)
+    ref_nbr, ref_h2 = orc.knn(g, 64)
+    assert np.array_equal(c.get("NBR"), np.sort(gi[ref_nbr], axis=1))
