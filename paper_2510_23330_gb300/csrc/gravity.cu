@@ -14,8 +14,9 @@
 //    staging accepted cells (monopole + quadrupole) and the particles of
 //    opened leaves as FP32 offsets from the group's reference grid point
 //    (Sec. 4.3 mixed precision); every thread evaluates its i-particle
-//    against the staged j entries, read as warp-wide broadcasts.  Small
-//    groups split the j loop over warps ("j-splits") so all warps stay busy.
+//    (two above 16 particles per group chunk) against the staged j
+//    entries, read as warp-wide broadcasts, and the j loop is split over as
+//    many thread sets as fit ("j-splits") so all warps stay busy.
 // Pair arithmetic is FP32 on the CUDA cores (not a dense contraction).
 #include <algorithm>
 
