@@ -84,9 +84,9 @@ def _declare(L):
     L.orc_knn.restype = C.c_int
     L.orc_kernel_eval.argtypes = [C.c_int64, _d, C.c_double, _d, _d]
     L.orc_density.argtypes = [C.c_int64, _i64, _d, _d, _d, _d, _d, C.c_int, _i64, _d,
-                              C.c_double, _d, _d, _d]
+                              C.c_double, _d, _d, _d, C.c_int]
     L.orc_sph_force.argtypes = ([C.c_int64] + [_d] * 6 + [_d] * 4 + [_d, C.c_int, _i64, C.c_double]
-                                + [_d] * 5)
+                                + [_d] * 5 + [_d, C.c_double, C.c_int])
     L.orc_sph_force.restype = C.c_int
     L.orc_num_threads.restype = C.c_int
     L.orc_sph_vsig.argtypes = [C.c_int64] + [_d] * 7 + [C.c_int, _i64, _d]
@@ -286,8 +286,10 @@ def kernel(r, h):
     return w, dw
 
 
-def density(g: dict, nbr, h2, gamma: float = 5.0 / 3.0, sample=None, u=None):
-    """rho, P, c of the sampled gas particles (Table 3 "density and pressure")."""
+def density(g: dict, nbr, h2, gamma: float = 5.0 / 3.0, sample=None, u=None, pressure: bool = False):
+    """rho, P, c of the sampled gas particles (Table 3 "density and pressure").
+    pressure=True: P is the smoothed pressure (gamma-1) sum_j m_j u_j W_ij(h_i)
+    of pressure-energy SPH instead of (gamma-1) rho_i u_i."""
     n = g["x"].shape[0]
     if sample is None:
         sample = np.arange(n, dtype=np.int64)
@@ -301,13 +303,15 @@ def density(g: dict, nbr, h2, gamma: float = 5.0 / 3.0, sample=None, u=None):
     lib().orc_density(ns, _p(sample, np.int64), _p(x, np.float64), _p(y, np.float64),
                       _p(z, np.float64), _p(m, np.float64), _p(uu, np.float64), k,
                       _p(nbr, np.int64), _p(h2, np.float64), gamma, _p(rho, np.float64),
-                      _p(P, np.float64), _p(c, np.float64))
+                      _p(P, np.float64), _p(c, np.float64), int(pressure))
     return rho, P, c
 
 
-def sph_force(g: dict, nbr, h2, rho, P, c, alpha: float = 1.0, v=None):
+def sph_force(g: dict, nbr, h2, rho, P, c, alpha: float = 1.0, v=None, u=None,
+              gamma: float = 5.0 / 3.0, pressure: bool = False):
     """Symmetric SPH pressure force + artificial viscosity and du/dt over the
-    union neighbour sets (Table 3 "hydro force")."""
+    union neighbour sets (Table 3 "hydro force"); pressure=True: the
+    pressure-energy form with the smoothed pressure P (see oracle.c)."""
     n, k = nbr.shape
     x, y, z, m = (f64(g[a]) for a in ("x", "y", "z", "m"))
     if v is None:
@@ -318,7 +322,8 @@ def sph_force(g: dict, nbr, h2, rho, P, c, alpha: float = 1.0, v=None):
     rc = lib().orc_sph_force(n, *(_p(a, np.float64) for a in (x, y, z, vx, vy, vz, m)),
                              *(_p(f64(a), np.float64) for a in (rho, P, c, h2)), k,
                              _p(nbr, np.int64), alpha,
-                             *(_p(out[a], np.float64) for a in ("ax", "ay", "az", "dudt", "asum")))
+                             *(_p(out[a], np.float64) for a in ("ax", "ay", "az", "dudt", "asum")),
+                             _p(f64(g["u"] if u is None else u), np.float64), gamma, int(pressure))
     if rc != 0:
         raise RuntimeError("oracle sph force failed")
     return out
@@ -337,11 +342,13 @@ def sph_vsig(g: dict, nbr, c, v=None):
     return out
 
 
-def sph(g: dict, k: int = 64, gamma: float = 5.0 / 3.0, alpha: float = 1.0, u=None, v=None):
-    """kNN + density + force for a gas-only particle set."""
+def sph(g: dict, k: int = 64, gamma: float = 5.0 / 3.0, alpha: float = 1.0, u=None, v=None,
+        pressure: bool = False):
+    """kNN + density + force for a gas-only particle set (pressure=True:
+    pressure-energy SPH)."""
     nbr, h2 = knn(g, k)
-    rho, P, c = density(g, nbr, h2, gamma, u=u)
-    f = sph_force(g, nbr, h2, rho, P, c, alpha, v=v)
+    rho, P, c = density(g, nbr, h2, gamma, u=u, pressure=pressure)
+    f = sph_force(g, nbr, h2, rho, P, c, alpha, v=v, u=u, gamma=gamma, pressure=pressure)
     f.update(nbr=nbr, h2=h2, rho=rho, P=P, c=c, vsig=sph_vsig(g, nbr, c, v=v))
     return f
 
@@ -366,10 +373,11 @@ class Config:
     """Parameters of one force evaluation (defaults of the disk model)."""
 
     def __init__(self, G=1.0, theta=0.5, n_leaf=16, n_g=64, quad=True, gravity="tree",
-                 n_ngb=64, gamma=5.0 / 3.0, alpha=1.0, nfw_ms=0.0, nfw_rs=8.0):
+                 n_ngb=64, gamma=5.0 / 3.0, alpha=1.0, nfw_ms=0.0, nfw_rs=8.0, sph="density"):
         self.G, self.theta, self.n_leaf, self.n_g, self.quad = G, theta, n_leaf, n_g, quad
         self.gravity, self.n_ngb, self.gamma, self.alpha = gravity, n_ngb, gamma, alpha
         self.nfw_ms, self.nfw_rs = nfw_ms, nfw_rs
+        self.sph = sph  # "density": density-energy SPH; "pressure": pressure-energy SPH
 
 
 def forces(s: dict, cfg: Config, u=None, v=None) -> dict:
@@ -396,7 +404,7 @@ def forces(s: dict, cfg: Config, u=None, v=None) -> dict:
         uu = (s["u"] if u is None else u)[gi]
         vv = [(s[k] if v is None else v[a])[gi] for a, k in enumerate(("vx", "vy", "vz"))]
         gs["u"] = uu
-        h = sph(gs, cfg.n_ngb, cfg.gamma, cfg.alpha, u=uu, v=vv)
+        h = sph(gs, cfg.n_ngb, cfg.gamma, cfg.alpha, u=uu, v=vv, pressure=cfg.sph == "pressure")
         ax[gi] += h["ax"]; ay[gi] += h["ay"]; az[gi] += h["az"]
         dudt[gi] = h["dudt"]
         res["sph"] = h

@@ -547,22 +547,28 @@ void orc_kernel_eval(int64_t n, const double *r, double h, double *w, double *dw
 /* P_i = (gamma-1) rho_i u_i, c_i = sqrt(gamma P_i / rho_i).                 */
 /* nbr holds k indices per sampled particle; h2 the squared support radius.  */
 /* ------------------------------------------------------------------------ */
+/* pressure: 0 = P_i = (gamma - 1) rho_i u_i (density-energy SPH);
+ * 1 = the smoothed pressure P_i = (gamma - 1) sum_j m_j u_j W_ij(h_i) of
+ * pressure-energy SPH (Table 3 names a "density and pressure" interaction).
+ * c_i = sqrt(gamma P_i / rho_i) in both. */
 void orc_density(int64_t ns, const int64_t *sample, const double *x, const double *y,
                  const double *z, const double *m, const double *u, int k,
                  const int64_t *nbr, const double *h2, double gamma,
-                 double *rho, double *P, double *c)
+                 double *rho, double *P, double *c, int pressure)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < ns; s++) {
         int64_t i = sample[s];
-        double h = sqrt(h2[s]), r = 0.0;
+        double h = sqrt(h2[s]), r = 0.0, q = 0.0;
         for (int t = 0; t < k; t++) {
             int64_t j = nbr[s * k + t];
             double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
-            r += m[j] * kern_w(sqrt(dx * dx + dy * dy + dz * dz), h);
+            double w = kern_w(sqrt(dx * dx + dy * dy + dz * dz), h);
+            r += m[j] * w;
+            q += m[j] * u[j] * w;
         }
         rho[s] = r;
-        P[s] = (gamma - 1.0) * r * u[i];
+        P[s] = pressure ? (gamma - 1.0) * q : (gamma - 1.0) * r * u[i];
         c[s] = sqrt(gamma * P[s] / r);
     }
 }
@@ -579,12 +585,19 @@ void orc_density(int64_t ns, const int64_t *sample, const double *x, const doubl
 /* w = v_ij.x_ij/r_ij, Pi_ij = -(alpha/2)(c_i + c_j - 3w) w / rhobar if      */
 /* w < 0 else 0, rhobar = (rho_i + rho_j)/2.  All arrays are full (n gas);   */
 /* nbr is n*k.  asum_i = sum |acc term| (condition number).                  */
+/* pressure = 1: pressure-energy SPH with the smoothed pressure P (see       */
+/* orc_density) in place of the two pressure terms:                         */
+/*   a_i  = -sum m_j [(g-1)^2 u_i u_j (gW_ij(h_i)/P_i + gW_ij(h_j)/P_j)      */
+/*                    + Pi_ij gWbar_ij]                                      */
+/*   du_i = sum m_j [(g-1)^2 u_i u_j / P_i v_ij.gW_ij(h_i)                   */
+/*                   + 1/2 Pi_ij v_ij.gWbar_ij],  g = gamma.                 */
 /* ------------------------------------------------------------------------ */
 int orc_sph_force(int64_t n, const double *x, const double *y, const double *z,
                   const double *vx, const double *vy, const double *vz,
                   const double *m, const double *rho, const double *P, const double *c,
                   const double *h2, int k, const int64_t *nbr, double alpha,
-                  double *ax, double *ay, double *az, double *dudt, double *asum)
+                  double *ax, double *ay, double *az, double *dudt, double *asum,
+                  const double *u, double gamma, int pressure)
 {
     /* reverse lists: R_j = {i : j in N_i} */
     int64_t *cnt = calloc((size_t)n + 1, 8);
@@ -632,12 +645,18 @@ int orc_sph_force(int64_t n, const double *x, const double *y, const double *z,
                     visc = -0.5 * alpha * vsig * w / (0.5 * (rho[i] + rho[j]));
                 }
                 double dwbar = 0.5 * (dwi + dwj);
-                double f = pi_ * dwi + pj_ * dwj + visc * dwbar;
+                double ci = pi_, cj = pj_;  /* coefficients of gW(h_i) and gW(h_j) */
+                if (pressure) {
+                    double uu = (gamma - 1.0) * (gamma - 1.0) * u[i] * u[j];
+                    ci = uu / P[i];
+                    cj = uu / P[j];
+                }
+                double f = ci * dwi + cj * dwj + visc * dwbar;
                 double tx = m[j] * f * ex, ty = m[j] * f * ey, tz = m[j] * f * ez;
                 a0 -= tx; a1 -= ty; a2 -= tz;
                 am += sqrt(tx * tx + ty * ty + tz * tz);
                 double vdotg = dvx * ex + dvy * ey + dvz * ez;
-                du += m[j] * (pi_ * dwi * vdotg + 0.5 * visc * dwbar * vdotg);
+                du += m[j] * (ci * dwi * vdotg + 0.5 * visc * dwbar * vdotg);
             }
             ax[i] = a0; ay[i] = a1; az[i] = a2; dudt[i] = du; asum[i] = am;
         }

@@ -135,3 +135,56 @@ def test_viscosity_heats_converging_flow_only(orc):
     # expanding flow: only the (tiny) pressure work, which cools
     assert h_out["dudt"][c] < 0 and abs(h_out["dudt"][c]) < 1e-3 * h_in["dudt"][c]
     assert abs(h_off["dudt"][c]) < 1e-3 * h_in["dudt"][c]
+
+
+# ---- pressure-energy SPH (the smoothed-pressure "density and pressure" form)
+def test_pressure_form_equals_density_form_for_uniform_u(orc):
+    """With one u for all particles the smoothed pressure is (gamma-1) u rho
+    and the pair coefficients (gamma-1)^2 u^2 / P equal P / rho^2: the two
+    formulations give the same forces and du/dt."""
+    g = _random_gas(1500, 21)
+    g["u"] = np.full(1500, 0.7)
+    a = orc.sph(g, 64, alpha=1.0)
+    b = orc.sph(g, 64, alpha=1.0, pressure=True)
+    assert np.allclose(b["P"], a["P"], rtol=1e-13, atol=0)
+    for k in ("ax", "ay", "az"):
+        assert np.max(np.abs(b[k] - a[k])) < 1e-12 * np.max(a["asum"])
+    assert np.max(np.abs(b["dudt"] - a["dudt"])) < 1e-12 * np.max(np.abs(a["dudt"]))
+
+
+def test_pressure_form_conserves_momentum_and_energy(orc):
+    g = _random_gas(2000, 22)
+    g["u"] = g["u"] * (1.0 + 3.0 * np.random.default_rng(1).uniform(size=2000))
+    h = orc.sph(g, 64, alpha=1.0, pressure=True)
+    m = g["m"]
+    scale = np.sum(m * h["asum"])
+    for k in ("ax", "ay", "az"):
+        assert abs(np.sum(m * h[k])) < 1e-13 * scale
+    de = np.sum(m * (g["vx"] * h["ax"] + g["vy"] * h["ay"] + g["vz"] * h["az"] + h["dudt"]))
+    de_scale = np.sum(m * (np.abs(g["vx"] * h["ax"]) + np.abs(g["vy"] * h["ay"])
+                           + np.abs(g["vz"] * h["az"]) + np.abs(h["dudt"])))
+    assert abs(de) < 1e-12 * de_scale
+
+
+def test_pressure_form_has_no_force_at_a_contact(orc):
+    """A lattice with masses 1 | 4 and u 4 | 1 across x = 6.5 is in pressure
+    equilibrium (rho u = 4 on both sides).  Density-energy SPH smooths rho
+    across the contact and pushes the particles next to it (the pressure
+    blip); with the smoothed pressure m u = 4 everywhere, so the interior
+    force vanishes to rounding."""
+    n = 14
+    p = ics.lattice(n)
+    left = p["x"] < 6.5
+    g = {k: np.asarray(p[k], np.float64) for k in ("x", "y", "z")}
+    g["m"] = np.where(left, 1.0, 4.0)
+    g["u"] = np.where(left, 4.0, 1.0)
+    zero = (np.zeros(n ** 3),) * 3
+    a = orc.sph(g, 64, u=g["u"], v=zero)
+    b = orc.sph(g, 64, u=g["u"], v=zero, pressure=True)
+    x, y, z = p["x"], p["y"], p["z"]
+    interior = (x > 3) & (x < n - 4) & (y > 3) & (y < n - 4) & (z > 3) & (z < n - 4)
+    contact = interior & (np.abs(x - 6.5) < 1.0)
+    blip = np.max(np.abs(a["ax"][contact]))
+    assert blip > 1e-2 * np.max(a["asum"][contact])  # density-energy SPH: a real spurious force
+    ab = np.sqrt(b["ax"] ** 2 + b["ay"] ** 2 + b["az"] ** 2)
+    assert np.max(ab[interior]) < 1e-12 * np.max(b["asum"][interior])
