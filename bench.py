@@ -352,6 +352,8 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     p, desc = workload(args.config, seed=rank)
     pr = params(args.config)
+    if args.sph == "pressure":
+        pr["cfg"]["sph_variant"] = 1  # pressure-energy SPH (smoothed pressure)
     mode = pr["gravity"]
     n = int(p["x"].shape[0])
     ctx = galnb.Context(stream=stream.cuda_stream, **pr["cfg"])
@@ -508,6 +510,8 @@ def main():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--n-group", type=int, default=0, help="fixed group size n_g (skips the autotuner)")
+    ap.add_argument("--sph", default="density", choices=["density", "pressure"],
+                    help="SPH formulation: density-energy (default) or pressure-energy")
     ap.add_argument("--no-sn", action="store_true", help="skip the supernova surrogate-vs-plain section")
     ap.add_argument("--sn-only", action="store_true",
                     help="profiling: only the supernova section, printed alone (not the bench line)")

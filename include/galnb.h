@@ -72,6 +72,11 @@ typedef struct gnb_config {
     double nfw_ms;     /* static NFW halo mass scale 4 pi rho_s r_s^3; 0 disables [0] */
     double nfw_rs;     /* NFW scale radius [8] */
     void *cuda_stream; /* cudaStream_t for all work; NULL = default stream [NULL] */
+    int sph_variant;   /* SPH formulation [0]: 0 = density-energy, P_i = (gamma-1) rho_i u_i;
+                          1 = pressure-energy: the density and pressure pass (Table 3) also
+                          smooths P_i = (gamma-1) sum_j m_j u_j W_ij(h_i), and the pair force
+                          uses (gamma-1)^2 u_i u_j / P_i and / P_j in place of P_i / rho_i^2
+                          and P_j / rho_j^2 (a reading) */
 } gnb_config;
 
 /* Fields readable with gnb_get.  Element type and count in brackets; n is

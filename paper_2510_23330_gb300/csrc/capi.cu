@@ -222,13 +222,14 @@ void gnb_config_default(gnb_config *cfg)
     cfg->nfw_ms = 0.0;
     cfg->nfw_rs = 8.0;
     cfg->cuda_stream = nullptr;
+    cfg->sph_variant = 0;
 }
 
 static bool config_ok(const gnb_config *cfg)
 {
     return cfg->theta >= 0.0 && cfg->G > 0.0 && cfg->n_leaf >= 1 && cfg->n_leaf <= 255 && cfg->n_group >= 1 &&
            cfg->n_ngb == 64 && cfg->gamma > 1.0 && cfg->alpha_visc >= 0.0 && cfg->nfw_ms >= 0.0 &&
-           !(cfg->nfw_ms > 0.0 && !(cfg->nfw_rs > 0.0));
+           !(cfg->nfw_ms > 0.0 && !(cfg->nfw_rs > 0.0)) && (cfg->sph_variant == 0 || cfg->sph_variant == 1);
 }
 
 int gnb_set_config(gnb_ctx *c, const gnb_config *cfg)

@@ -150,7 +150,7 @@ struct gnb_ctx {
     int4 *fC = nullptr;           // cell x, y, z, mass bits
     float4 *fR = nullptr;         // residual x, y, z, 1/h
     float4 *fV = nullptr;         // v x, y, z, sound speed
-    float2 *fQ = nullptr;         // rho, P / rho^2
+    float4 *fQ = nullptr;         // rho, Y, U, - (pair coefficient U_j Y_i of gW(h_i); see sph.cu)
     int *kcount_d = nullptr;
 
     // supernova surrogate (surrogate.cu)

@@ -168,6 +168,7 @@ struct KnnParams {
     float *h, *E, *rho, *P, *cs;
     int *g64;
     float gamma;
+    int pressure;  // 1: also smooth P = (gamma - 1) sum_j m_j u_j W_ij (pressure-energy SPH)
 };
 
 struct KnnSmem {
@@ -537,15 +538,18 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
                 // density and EOS over the 64 neighbours
                 const float hh = (float)sqrt(hsq);
                 const float hinv = 1.f / hh;
-                float rs = 0.f;
+                float rs = 0.f, qs = 0.f;
                 for (int e = lane; e < NGB; e += 32) {
                     int j = outn[e];
-                    rs += p.gm[j] * kern_w(sqrtf(outd[e]), hinv);
+                    const float mw = p.gm[j] * kern_w(sqrtf(outd[e]), hinv);
+                    rs += mw;
+                    if (p.pressure) qs = __fmaf_rn(mw, p.gu[j], qs);
                 }
                 rs = warp_sum(rs);
+                if (p.pressure) qs = warp_sum(qs);
                 if (lane == 0) {
                     float u = p.gu[i];
-                    float P = (p.gamma - 1.f) * rs * u;
+                    float P = p.pressure ? (p.gamma - 1.f) * qs : (p.gamma - 1.f) * rs * u;
                     p.h2[i] = hsq;
                     p.h2lo[i] = __double2float_rd(hsq);
                     p.h2hi[i] = __double2float_ru(hsq);
@@ -673,8 +677,7 @@ struct ForceParams {
     int ng;
     const int *nbr, *roff, *rcnt, *rlist;
     const int4 *C;    // neighbour records (k_force_pack)
-    const float4 *R, *V;
-    const float2 *Q;
+    const float4 *R, *V, *Q;
     const double *box;
     float alpha;
     float *ax, *ay, *az, *du;
@@ -682,13 +685,18 @@ struct ForceParams {
 };
 
 // One record set per gas particle so a pair gathers four records instead of
-// fourteen fields: {cell, mass}, {residual, 1/h}, {v, c}, {rho, P/rho^2}.
+// fourteen fields: {cell, mass}, {residual, 1/h}, {v, c}, {rho, Y, U}.  The
+// pressure terms of a pair are U_j Y_i gW(h_i) + U_i Y_j gW(h_j): Y = P/rho^2,
+// U = 1 for density-energy SPH; Y = (gamma-1) u / P, U = (gamma-1) u for
+// pressure-energy SPH with the smoothed P, whose pair coefficients are
+// (gamma-1)^2 u_i u_j / P_i and / P_j.
 __global__ void k_force_pack(int ng, const int *__restrict__ gcx, const int *__restrict__ gcy,
                              const int *__restrict__ gcz, const float *__restrict__ grx, const float *__restrict__ gry,
                              const float *__restrict__ grz, const float *__restrict__ gm, const float *__restrict__ gvx,
                              const float *__restrict__ gvy, const float *__restrict__ gvz, const float *__restrict__ h,
                              const float *__restrict__ rho, const float *__restrict__ P, const float *__restrict__ cs,
-                             int4 *__restrict__ C, float4 *__restrict__ R, float4 *__restrict__ V, float2 *__restrict__ Q)
+                             const float *__restrict__ gu, float gamma, int pressure, int4 *__restrict__ C,
+                             float4 *__restrict__ R, float4 *__restrict__ V, float4 *__restrict__ Q)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ng) return;
@@ -696,18 +704,23 @@ __global__ void k_force_pack(int ng, const int *__restrict__ gcx, const int *__r
     C[j] = make_int4(gcx[j], gcy[j], gcz[j], __float_as_int(gm[j]));
     R[j] = make_float4(grx[j], gry[j], grz[j], 1.f / h[j]);
     V[j] = make_float4(gvx[j], gvy[j], gvz[j], cs[j]);
-    Q[j] = make_float2(rj, P[j] / (rj * rj));
+    if (pressure) {
+        const float U = (gamma - 1.f) * gu[j];
+        Q[j] = make_float4(rj, U / P[j], U, 0.f);
+    } else {
+        Q[j] = make_float4(rj, P[j] / (rj * rj), 1.f, 0.f);
+    }
 }
 
 __device__ __forceinline__ void pair_force(const ForceParams &p, int j, float unit, int ci0, int ci1, int ci2,
                                            float ri0, float ri1, float ri2, float vi0, float vi1, float vi2,
-                                           float hinv_i, float pi_, float rhoi, float csi, float &a0, float &a1,
-                                           float &a2, float &du, float &vs)
+                                           float hinv_i, float pi_, float ui_, float rhoi, float csi, float &a0,
+                                           float &a1, float &a2, float &du, float &vs)
 {
     const int4 Cj = p.C[j];
     const float4 Rj = p.R[j];
     const float4 Vj = p.V[j];
-    const float2 Qj = p.Q[j];
+    const float4 Qj = p.Q[j];
     float dx = __fmaf_rn((float)(ci0 - Cj.x), unit, ri0 - Rj.x);
     float dy = __fmaf_rn((float)(ci1 - Cj.y), unit, ri1 - Rj.y);
     float dz = __fmaf_rn((float)(ci2 - Cj.z), unit, ri2 - Rj.z);
@@ -725,11 +738,12 @@ __device__ __forceinline__ void pair_force(const ForceParams &p, int j, float un
     if (w < 0.f) visc = -0.5f * p.alpha * vsig * w / (0.5f * (rhoi + rhoj));
     float dwbar = 0.5f * (dwi + dwj);
     float mj = __int_as_float(Cj.w);
-    float f = mj * (pi_ * dwi + pj_ * dwj + visc * dwbar) * rinv;
+    const float ci = Qj.z * pi_, cj = ui_ * pj_;  // U_j Y_i, U_i Y_j
+    float f = mj * (ci * dwi + cj * dwj + visc * dwbar) * rinv;
     a0 -= f * dx;
     a1 -= f * dy;
     a2 -= f * dz;
-    du += mj * (pi_ * dwi + 0.5f * visc * dwbar) * w;
+    du += mj * (ci * dwi + 0.5f * visc * dwbar) * w;
 }
 
 __global__ void k_force(ForceParams p)
@@ -740,23 +754,24 @@ __global__ void k_force(ForceParams p)
     const int4 Ci = p.C[i];
     const float4 Ri = p.R[i];
     const float4 Vi = p.V[i];
-    const float2 Qi = p.Q[i];
+    const float4 Qi = p.Q[i];
     const int ci0 = Ci.x, ci1 = Ci.y, ci2 = Ci.z;
     const float ri0 = Ri.x, ri1 = Ri.y, ri2 = Ri.z;
     const float vi0 = Vi.x, vi1 = Vi.y, vi2 = Vi.z;
     const float hinv = Ri.w, rhoi = Qi.x, csi = Vi.w;
-    const float pi_ = Qi.y;
+    const float pi_ = Qi.y, ui_ = Qi.z;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, du = 0.f, vs = 2.f * csi;
     const int *nb = p.nbr + (size_t)i * NGB;
     for (int k = 0; k < NGB; k++) {
         int j = nb[k];
         if (j == i) continue;
-        pair_force(p, j, unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1, a2, du, vs);
+        pair_force(p, j, unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, ui_, rhoi, csi, a0, a1, a2, du,
+                   vs);
     }
     int b = p.roff[i], e = b + p.rcnt[i];
     for (int k = b; k < e; k++)
-        pair_force(p, p.rlist[k], unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, rhoi, csi, a0, a1,
-                   a2, du, vs);
+        pair_force(p, p.rlist[k], unit, ci0, ci1, ci2, ri0, ri1, ri2, vi0, vi1, vi2, hinv, pi_, ui_, rhoi, csi, a0,
+                   a1, a2, du, vs);
     p.ax[i] = a0;
     p.ay[i] = a1;
     p.az[i] = a2;
@@ -833,7 +848,7 @@ int sph_density(gnb_ctx *c)
     p.kR = c->kR; p.kRb = c->kRb; p.kflag = c->kflag;
     p.next = c->work_d; p.remaining = c->work_d + 1; p.status = c->status_d;
     p.nbr = c->nbr; p.nd2 = c->nd2; p.h2 = c->gh2; p.h2lo = c->gh2lo; p.h2hi = c->gh2hi; p.h = c->gh; p.E = c->gE; p.rho = c->grho; p.P = c->gP;
-    p.cs = c->gcs; p.g64 = c->g64; p.gamma = (float)c->cfg.gamma;
+    p.cs = c->gcs; p.g64 = c->g64; p.gamma = (float)c->cfg.gamma; p.pressure = c->cfg.sph_variant;
     size_t smem = sizeof(KnnSmem);
     cudaError_t e = cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(c, e, "knn smem attribute");
@@ -898,8 +913,9 @@ int sph_force(gnb_ctx *c)
     gnb::counted(k_rev_fill)<<<gb, 256, 0, c->s>>>(ng, c->nbr, c->mut, c->roff, c->rfill, c->rlist);
     GNB_LAUNCH_CHECK(c, "symmetric lists");
     gnb::counted(k_force_pack)<<<gb, 256, 0, c->s>>>(ng, c->gcx, c->gcy, c->gcz, c->grx, c->gry, c->grz, c->gm, c->gvx,
-                                                     c->gvy, c->gvz, c->gh, c->grho, c->gP, c->gcs, c->fC, c->fR,
-                                                     c->fV, c->fQ);
+                                                     c->gvy, c->gvz, c->gh, c->grho, c->gP, c->gcs, c->gu,
+                                                     (float)c->cfg.gamma, c->cfg.sph_variant, c->fC, c->fR, c->fV,
+                                                     c->fQ);
     ForceParams p;
     p.ng = ng; p.nbr = c->nbr; p.roff = c->roff; p.rcnt = c->rcnt; p.rlist = c->rlist;
     p.C = c->fC; p.R = c->fR; p.V = c->fV; p.Q = c->fQ;

@@ -45,7 +45,8 @@ STATS = ["N", "NGAS", "NODES", "GROUPS", "NPP", "NPC", "GAS_NODES", "KNN_PASSES"
 class gnb_config(C.Structure):
     _fields_ = [("G", C.c_double), ("theta", C.c_double), ("gamma", C.c_double), ("alpha_visc", C.c_double),
                 ("n_leaf", C.c_int), ("n_group", C.c_int), ("n_ngb", C.c_int), ("multipole", C.c_int),
-                ("nfw_ms", C.c_double), ("nfw_rs", C.c_double), ("cuda_stream", C.c_void_p)]
+                ("nfw_ms", C.c_double), ("nfw_rs", C.c_double), ("cuda_stream", C.c_void_p),
+                ("sph_variant", C.c_int)]
 
 
 _lock = threading.Lock()

@@ -139,3 +139,59 @@ def test_knn_unrankable_clump_reports_ecapacity(G, orc):
     gi, g = _gas(q)
     ref_nbr, ref_h2 = orc.knn(g, 64)
     assert np.array_equal(c.get("NBR"), np.sort(gi[ref_nbr], axis=1))
+
+
+def _exploded(orc, n, seed):
+    p = ics.sn_region(n, seed=seed, grid=32)
+    s, _ = orc.inject_energy(orc.state(p), (0.0, 0.0, 0.0), ics.E_SN_CODE)
+    return p, s
+
+
+def test_pressure_energy_density_and_force(G, orc):
+    """Pressure-energy SPH (sph_variant = 1) on an exploded region, where u
+    spans orders of magnitude: smoothed pressure, sound speed, accelerations
+    and du/dt against the oracle's pressure form."""
+    p, s = _exploded(orc, 4000, 31)
+    c = G.Context(sph_variant=1)
+    c.set_particles(p)
+    c.inject_energy((0.0, 0.0, 0.0), ics.E_SN_CODE)
+    c.compute_sph_density()
+    c.compute_sph_force()
+    g = {k: np.asarray(s[k], np.float64) for k in ("x", "y", "z", "m", "u", "vx", "vy", "vz")}
+    h = orc.sph(g, 64, alpha=1.0, pressure=True)
+    u_gpu = c.get("U").astype(np.float64)
+    assert np.max(np.abs(u_gpu - g["u"]) / g["u"]) < 2e-7  # same injected energies (FP32 storage)
+    assert np.max(np.abs(c.get("RHO") - h["rho"]) / h["rho"]) < TOL
+    assert np.max(np.abs(c.get("PRES") - h["P"]) / h["P"]) < TOL
+    assert np.max(np.abs(c.get("CS") - h["c"]) / h["c"]) < TOL
+    ax, ay, az = (c.get(k) for k in ("AX", "AY", "AZ"))
+    err = np.sqrt((ax - h["ax"]) ** 2 + (ay - h["ay"]) ** 2 + (az - h["az"]) ** 2) / h["asum"]
+    assert err.max() < TOL
+    du = c.get("DUDT")
+    assert np.max(np.abs(du - h["dudt"])) / np.max(np.abs(h["dudt"])) < 10 * TOL
+    # the two formulations do differ here
+    d = orc.sph(g, 64, alpha=1.0)
+    assert np.max(np.abs(d["P"] - h["P"]) / h["P"]) > 1e-2
+
+
+def test_pressure_energy_cfl_integration_matches_oracle(G, orc):
+    p, s = _exploded(orc, 5000, 32)
+    cfg = orc.Config(gravity="none", sph="pressure")
+    f = orc.forces(s, cfg)
+    span = 0.0
+    for _ in range(5):
+        dt = orc.cfl_dt(f, 0.3)
+        s, f = orc.kdk_step(s, f, dt, cfg)
+        span += dt
+    c = G.Context(sph_variant=1)
+    c.set_particles(p)
+    c.inject_energy((0.0, 0.0, 0.0), ics.E_SN_CODE)
+    t, n = c.integrate_cfl(span, 0.3, mode=G.GNB_GRAV_NONE)
+    assert abs(t - span) < 1e-12 * span and n in (5, 6)
+    for k in ("X", "Y", "Z"):
+        assert np.max(np.abs(c.get(k) - s[k.lower()])) < 1e-5 * 60.0
+    vmax = np.max(np.abs(s["vx"]))
+    for k in ("VX", "VY", "VZ"):
+        assert np.max(np.abs(c.get(k) - s[k.lower()])) < 2e-3 * vmax
+    u = c.get("U")
+    assert np.max(np.abs(u - s["u"]) / (np.abs(s["u"]) + 1e-3 * np.max(s["u"]))) < 2e-3
