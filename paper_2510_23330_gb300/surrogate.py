@@ -5,8 +5,8 @@ Pairs: a turbulent region of gas (ics.sn_region) is voxelised just before the
 explosion (input) and again after the plain CFL-limited integration of the
 injected 10^51 erg over 0.1 Myr (target).  The network is the library's BF16
 U-Net trained with MSE and Adam at batch size 1 (Sec. 3.3).  The plain
-integration is both the training signal and the judge of the surrogate's
-error; "identity" (the input grid taken as the prediction, i.e. the region
+integration is both the training signal and the reference the surrogate's
+error is measured against; "identity" (the input grid taken as the prediction, i.e. the region
 without the supernova's feedback) is the baseline the surrogate must beat.
 
     python -m paper_2510_23330_gb300.surrogate --train 48 --test 8 --out report.json
