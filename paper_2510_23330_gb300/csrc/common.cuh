@@ -46,6 +46,10 @@ enum : int {
     ST_BAD_INPUT = 16,
 };
 
+// The octree's top levels find their child boundaries in a table of the first
+// slot of every key prefix at this level (one parallel search per build).
+constexpr int GNB_PTAB_LEVEL = 6;
+
 struct Tree {
     int cap = 0;       // node capacity
     int nnodes = 0;    // nodes of the last build (host copy)
@@ -66,6 +70,7 @@ struct Tree {
     int *groups = nullptr; // group node ids, ascending first particle
     int *ngroups_d = nullptr;
     int ngroups = 0;
+    int *ptab = nullptr;   // first slot of every level-GNB_PTAB_LEVEL key prefix (8^L + 1 entries)
 };
 
 struct Buf {

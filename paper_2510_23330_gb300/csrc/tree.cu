@@ -158,6 +158,16 @@ __device__ __forceinline__ void child_bounds(const uint64_t *__restrict__ k, int
     for (int d = 1; d < 8; d++) pos[d] = lower_bound_key(k, pos[d - 1], first + count, base | ((uint64_t)d << sh));
 }
 
+// ptab[c] = first slot whose key is >= prefix c at level GNB_PTAB_LEVEL
+// (c < 8^L), ptab[8^L] = n: independent binary searches, all in parallel.
+__global__ void k_prefix_table(const uint64_t *__restrict__ k, int n, int *__restrict__ ptab)
+{
+    const int ncell = 1 << (3 * GNB_PTAB_LEVEL);
+    const int sh = 3 * (GNB_MAXLEV - GNB_PTAB_LEVEL);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= ncell; c += gridDim.x * blockDim.x)
+        ptab[c] = c == ncell ? n : lower_bound_key(k, 0, n, (uint64_t)c << sh);
+}
+
 __global__ void __launch_bounds__(TB_THREADS) k_split_count(Tree t, const uint64_t *__restrict__ k, int l,
                                                             int n_leaf)
 {
@@ -179,7 +189,11 @@ __global__ void __launch_bounds__(TB_THREADS) k_split_count(Tree t, const uint64
         int pos = a.x;
         if (split && d > 0) {
             uint64_t base = (k[a.x] >> (sh + 3)) << (sh + 3);
-            pos = lower_bound_key(k, a.x, a.x + a.y, base | ((uint64_t)d << sh));
+            const uint64_t target = base | ((uint64_t)d << sh);
+            // a node's keys share its prefix, so the first slot >= target in
+            // the whole array lies in [a.x, a.x + a.y]: the table's entry
+            if (l < GNB_PTAB_LEVEL) pos = t.ptab[target >> (3 * (GNB_MAXLEV - GNB_PTAB_LEVEL))];
+            else pos = lower_bound_key(k, a.x, a.x + a.y, target);
         }
         int nxt = __shfl_down_sync(0xffffffffu, pos, 1, 8);
         if (d == 7) nxt = a.x + a.y;
@@ -401,7 +415,7 @@ int tree_alloc(gnb_ctx *c, Tree &t, int cap)
 {
     // node arrays only; the per-particle group scratch survives a regrow
     dfree(c, t.na); dfree(c, t.nb); dfree(c, t.mo0); dfree(c, t.mo1); dfree(c, t.mo2); dfree(c, t.cb);
-    dfree(c, t.lvl); dfree(c, t.partial); dfree(c, t.poff); dfree(c, t.ngroups_d);
+    dfree(c, t.lvl); dfree(c, t.partial); dfree(c, t.poff); dfree(c, t.ngroups_d); dfree(c, t.ptab);
     t.cap = cap;
     GNB_TRY(dalloc(c, &t.na, cap));
     GNB_TRY(dalloc(c, &t.nb, cap));
@@ -413,6 +427,7 @@ int tree_alloc(gnb_ctx *c, Tree &t, int cap)
     GNB_TRY(dalloc(c, &t.partial, 1100));
     GNB_TRY(dalloc(c, &t.poff, 1100));
     GNB_TRY(dalloc(c, &t.ngroups_d, 4));
+    GNB_TRY(dalloc(c, &t.ptab, ((size_t)1 << (3 * GNB_PTAB_LEVEL)) + 1));
     return GNB_OK;
 }
 
@@ -420,7 +435,7 @@ void tree_free(gnb_ctx *c, Tree &t)
 {
     dfree(c, t.na); dfree(c, t.nb); dfree(c, t.mo0); dfree(c, t.mo1); dfree(c, t.mo2); dfree(c, t.cb);
     dfree(c, t.lvl); dfree(c, t.partial); dfree(c, t.poff); dfree(c, t.gmark); dfree(c, t.gflag);
-    dfree(c, t.goff); dfree(c, t.groups); dfree(c, t.ngroups_d);
+    dfree(c, t.goff); dfree(c, t.groups); dfree(c, t.ngroups_d); dfree(c, t.ptab);
     t = Tree();
 }
 
@@ -433,6 +448,8 @@ int build_tree(gnb_ctx *c, Tree &t, const uint64_t *skey, int n, const int *n_d,
     for (int attempt = 0; attempt < 6; attempt++) {
         if (t.cap < 64) GNB_TRY(tree_alloc(c, t, n + n / 2 + 1024));
         gnb::counted(k_tree_root)<<<1, 32, 0, c->s>>>(t, n);
+        gnb::counted(k_prefix_table)<<<((1 << (3 * GNB_PTAB_LEVEL)) + TB_THREADS) / TB_THREADS, TB_THREADS, 0,
+                                        c->s>>>(skey, n, t.ptab);  // one search per thread
         // Levels down to two below the last build's depth, then one check of
         // the overflow flag and the level table; the remaining levels run only
         // if the last level built still holds nodes (the tree got deeper).
