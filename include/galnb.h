@@ -90,7 +90,8 @@ enum gnb_field {
     GNB_F_U,                        /* internal energy, 0 for stars [float, n] */
     GNB_F_DUDT,                     /* du/dt, 0 for stars [float, n] */
     GNB_F_RHO,                      /* SPH density, 0 for stars [float, n] */
-    GNB_F_PRES,                     /* pressure, 0 for stars [float, n] */
+    GNB_F_PRES,                     /* pressure ((gamma-1) rho u, or the smoothed pressure when
+                                       sph_variant = 1), 0 for stars [float, n] */
     GNB_F_CS,                       /* sound speed, 0 for stars [float, n] */
     GNB_F_H2,                       /* squared kernel support h^2, 0 for stars [double, n] */
     GNB_F_KEY,                      /* Morton key of the last sort [uint64, n] */
@@ -179,8 +180,10 @@ int gnb_build_tree(gnb_ctx *ctx);
 int gnb_compute_gravity(gnb_ctx *ctx, int mode);
 
 /* SPH kernel size (exact n_ngb nearest gas neighbours, Sec. 5.2.5), density
- * and pressure (Table 3 "density and pressure").  Builds the tree first if
- * needed.  Errors: GNB_ESTATE, GNB_ECAPACITY, GNB_ECUDA. */
+ * and pressure (Table 3 "density and pressure"; with sph_variant = 1 the
+ * pressure is smoothed over the neighbours, see gnb_config).  Builds the tree
+ * first if needed.  Errors: GNB_ESTATE, GNB_ECAPACITY (e.g. more than 64
+ * particles tied at one neighbour distance), GNB_ECUDA. */
 int gnb_compute_sph_density(gnb_ctx *ctx);
 
 /* SPH pressure force, artificial viscosity and du/dt over the symmetric
