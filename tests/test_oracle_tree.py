@@ -167,6 +167,41 @@ def test_groups_partition_particles(orc):
         assert np.all((c <= n_g) | (t["nchild"][g] == 0))
 
 
+def _parents(t):
+    par = np.full(t["level"].shape[0], -1, np.int64)
+    for k in range(t["level"].shape[0]):
+        if t["nchild"][k]:
+            par[t["child"][k]:t["child"][k] + t["nchild"][k]] = k
+    return par
+
+
+def test_groups_are_the_highest_cells_within_n_g(orc):
+    """Groups are the highest cells with count <= n_g (or leaves): every
+    group's parent holds more than n_g particles, so no group could be
+    merged one level up; the root is a group iff N <= n_g.  A walk that
+    stopped one level too deep, or too high, fails this."""
+    p = ics.exp_disk(5000, seed=4)
+    key, _, _, _ = orc.morton(p)
+    t = orc.octree(np.sort(key), 16)
+    par = _parents(t)
+    for n_g in (16, 64, 300, 4999, 5000, 6000):
+        g = orc.groups(t, n_g)
+        if n_g >= 5000:
+            assert list(g) == [0]
+            continue
+        assert 0 not in set(g)
+        assert np.all(t["count"][par[g]] > n_g)
+        # every cell not inside a group has count > n_g and is not a leaf
+        inside = np.zeros(t["level"].shape[0], bool)
+        stack = list(g)
+        while stack:
+            k = stack.pop()
+            inside[k] = True
+            stack += list(range(t["child"][k], t["child"][k] + t["nchild"][k])) if t["nchild"][k] else []
+        outside = ~inside
+        assert np.all(t["count"][outside] > n_g) and np.all(t["nchild"][outside] > 0)
+
+
 def _tree_err(orc, p, **kw):
     d = orc.direct_gravity(p)
     t = orc.tree_gravity(p, **kw)
