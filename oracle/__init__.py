@@ -86,7 +86,7 @@ def _declare(L):
     L.orc_density.argtypes = [C.c_int64, _i64, _d, _d, _d, _d, _d, C.c_int, _i64, _d,
                               C.c_double, _d, _d, _d, C.c_int]
     L.orc_sph_force.argtypes = ([C.c_int64] + [_d] * 6 + [_d] * 4 + [_d, C.c_int, _i64, C.c_double]
-                                + [_d] * 5 + [_d, C.c_double, C.c_int])
+                                + [_d] * 5 + [_d, C.c_double, C.c_int, _d])
     L.orc_sph_force.restype = C.c_int
     L.orc_num_threads.restype = C.c_int
     L.orc_sph_vsig.argtypes = [C.c_int64] + [_d] * 7 + [C.c_int, _i64, _d]
@@ -311,19 +311,22 @@ def sph_force(g: dict, nbr, h2, rho, P, c, alpha: float = 1.0, v=None, u=None,
               gamma: float = 5.0 / 3.0, pressure: bool = False):
     """Symmetric SPH pressure force + artificial viscosity and du/dt over the
     union neighbour sets (Table 3 "hydro force"); pressure=True: the
-    pressure-energy form with the smoothed pressure P (see oracle.c)."""
+    pressure-energy form with the smoothed pressure P (see oracle.c).
+    Also returns the sums' scales: asum = sum_j |a_ij| and dusum = sum_j of
+    the magnitudes of du/dt's pressure and viscosity terms."""
     n, k = nbr.shape
     x, y, z, m = (f64(g[a]) for a in ("x", "y", "z", "m"))
     if v is None:
         v = (g["vx"], g["vy"], g["vz"])
     vx, vy, vz = (f64(a) for a in v)
-    out = {a: np.zeros(n) for a in ("ax", "ay", "az", "dudt", "asum")}
+    out = {a: np.zeros(n) for a in ("ax", "ay", "az", "dudt", "asum", "dusum")}
     nbr = np.ascontiguousarray(nbr, dtype=np.int64)
     rc = lib().orc_sph_force(n, *(_p(a, np.float64) for a in (x, y, z, vx, vy, vz, m)),
                              *(_p(f64(a), np.float64) for a in (rho, P, c, h2)), k,
                              _p(nbr, np.int64), alpha,
                              *(_p(out[a], np.float64) for a in ("ax", "ay", "az", "dudt", "asum")),
-                             _p(f64(g["u"] if u is None else u), np.float64), gamma, int(pressure))
+                             _p(f64(g["u"] if u is None else u), np.float64), gamma, int(pressure),
+                             _p(out["dusum"], np.float64))
     if rc != 0:
         raise RuntimeError("oracle sph force failed")
     return out

@@ -597,7 +597,7 @@ int orc_sph_force(int64_t n, const double *x, const double *y, const double *z,
                   const double *m, const double *rho, const double *P, const double *c,
                   const double *h2, int k, const int64_t *nbr, double alpha,
                   double *ax, double *ay, double *az, double *dudt, double *asum,
-                  const double *u, double gamma, int pressure)
+                  const double *u, double gamma, int pressure, double *dusum)
 {
     /* reverse lists: R_j = {i : j in N_i} */
     int64_t *cnt = calloc((size_t)n + 1, 8);
@@ -626,7 +626,7 @@ int orc_sph_force(int64_t n, const double *x, const double *y, const double *z,
                 if (j != i && !mark[j]) { mark[j] = 1; lst[nl++] = j; }
             }
             double hi = sqrt(h2[i]);
-            double a0 = 0, a1 = 0, a2 = 0, du = 0, am = 0;
+            double a0 = 0, a1 = 0, a2 = 0, du = 0, am = 0, dm = 0;
             double pi_ = P[i] / (rho[i] * rho[i]);
             for (int64_t t = 0; t < nl; t++) {
                 int64_t j = lst[t];
@@ -657,8 +657,11 @@ int orc_sph_force(int64_t n, const double *x, const double *y, const double *z,
                 am += sqrt(tx * tx + ty * ty + tz * tz);
                 double vdotg = dvx * ex + dvy * ey + dvz * ez;
                 du += m[j] * (ci * dwi * vdotg + 0.5 * visc * dwbar * vdotg);
+                /* the scale of the du/dt sum: its pressure and viscosity terms in magnitude */
+                dm += fabs(m[j] * ci * dwi * vdotg) + fabs(m[j] * 0.5 * visc * dwbar * vdotg);
             }
             ax[i] = a0; ay[i] = a1; az[i] = a2; dudt[i] = du; asum[i] = am;
+            if (dusum) dusum[i] = dm;
         }
         free(mark); free(lst);
     }

@@ -188,3 +188,17 @@ def test_pressure_form_has_no_force_at_a_contact(orc):
     assert blip > 1e-2 * np.max(a["asum"][contact])  # density-energy SPH: a real spurious force
     ab = np.sqrt(b["ax"] ** 2 + b["ay"] ** 2 + b["az"] ** 2)
     assert np.max(ab[interior]) < 1e-12 * np.max(b["asum"][interior])
+
+
+def test_force_sum_scales_bound_the_sums(orc):
+    """asum and dusum are sums of term magnitudes: they bound |a| and |du/dt|
+    (triangle inequality); with all velocities zero, du/dt and its scale
+    vanish."""
+    p = ics.uniform_random(1500, seed=8, gas_frac=1.0)
+    g = {k: np.asarray(p[k], np.float64) for k in ("x", "y", "z", "m", "u", "vx", "vy", "vz")}
+    h = orc.sph(g, 64)
+    a = np.sqrt(h["ax"] ** 2 + h["ay"] ** 2 + h["az"] ** 2)
+    assert np.all(a <= h["asum"] * (1 + 1e-12))
+    assert np.all(np.abs(h["dudt"]) <= h["dusum"] * (1 + 1e-12)) and np.all(h["dusum"] > 0)
+    z = orc.sph(g, 64, v=(np.zeros(1500), np.zeros(1500), np.zeros(1500)))
+    assert np.all(z["dudt"] == 0) and np.all(z["dusum"] == 0)
