@@ -15,6 +15,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "morton.cuh"
 
 namespace gnb {
 namespace {
@@ -40,104 +41,27 @@ constexpr size_t SCRATCH_BYTES = OFF_FLAG + al256(sizeof(int) * 4);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
-__device__ __forceinline__ unsigned long long na_ord(double v)
-{
-    long long b = __double_as_longlong(v);
-    return b >= 0 ? ((unsigned long long)b ^ 0x8000000000000000ull) : ~(unsigned long long)b;
-}
-__device__ __forceinline__ double na_unord(unsigned long long o)
-{
-    long long b = (o & 0x8000000000000000ull) ? (long long)(o ^ 0x8000000000000000ull) : (long long)~o;
-    return __longlong_as_double(b);
-}
-
 // Clears what must start at zero (or at the min/max sentinels) every call.
 __global__ void k_na_init(unsigned char *scr)
 {
-    unsigned long long *mm = (unsigned long long *)(scr + OFF_MM);
-    int *flag = (int *)(scr + OFF_FLAG);
-    int t = threadIdx.x;
-    if (t < 3) mm[t] = ~0ull;
-    else if (t < 6) mm[t] = 0ull;
-    else if (t == 6) mm[t] = 0ull;
-    if (t == 0) flag[0] = 0;
+    minmax_init((unsigned long long *)(scr + OFF_MM), threadIdx.x);
+    if (threadIdx.x == 0) ((int *)(scr + OFF_FLAG))[0] = 0;
 }
 
+// The root box and the keys come from the same device functions as the
+// context path (morton.cuh), so both paths give the same bits.
 __global__ void k_na_minmax(const double *__restrict__ x, const double *__restrict__ y,
                             const double *__restrict__ z, int n, unsigned char *scr)
 {
-    unsigned long long *mm = (unsigned long long *)(scr + OFF_MM);
-    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
-    bool bad = false;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double v[3] = {x[i], y[i], z[i]};
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            bad |= !isfinite(v[a]);
-            unsigned long long o = na_ord(v[a]);
-            mn[a] = o < mn[a] ? o : mn[a];
-            mx[a] = o > mx[a] ? o : mx[a];
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long p = __shfl_xor_sync(0xffffffffu, mn[a], o);
-            unsigned long long q = __shfl_xor_sync(0xffffffffu, mx[a], o);
-            mn[a] = p < mn[a] ? p : mn[a];
-            mx[a] = q > mx[a] ? q : mx[a];
-        }
-    }
-    bad = __any_sync(0xffffffffu, bad);
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            atomicMin(&mm[a], mn[a]);
-            atomicMax(&mm[3 + a], mx[a]);
-        }
-        if (bad) atomicExch(&mm[6], 1ull);
-    }
+    minmax_accumulate(x, y, z, n, (unsigned long long *)(scr + OFF_MM));
 }
 
 // box = {lo x, lo y, lo z, L, unit}: lo = minimum, L = power of two >= extent
 __global__ void k_na_box(unsigned char *scr)
 {
     if (threadIdx.x != 0) return;
-    const unsigned long long *mm = (const unsigned long long *)(scr + OFF_MM);
-    double *box = (double *)(scr + OFF_BOX);
-    int *flag = (int *)(scr + OFF_FLAG);
-    if (mm[6]) flag[0] = 1;
-    double ext = 0.0;
-    for (int a = 0; a < 3; a++) {
-        double lo = na_unord(mm[a]), hi = na_unord(mm[3 + a]);
-        box[a] = lo;
-        double e = __dsub_rn(hi, lo);
-        ext = e > ext ? e : ext;
-    }
-    double L = 1.0;
-    if (ext > 0.0) {
-        while (L < ext) L *= 2.0;
-        while (L / 2.0 >= ext) L /= 2.0;
-    }
-    box[3] = L;
-    box[4] = L / 2097152.0;
-}
-
-__device__ __forceinline__ uint64_t na_spread3(uint32_t v)
-{
-    uint64_t x = v & 0x1fffffu;
-    x = (x | x << 32) & 0x1f00000000ffffull;
-    x = (x | x << 16) & 0x1f0000ff0000ffull;
-    x = (x | x << 8) & 0x100f00f00f00f00full;
-    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
-    x = (x | x << 2) & 0x1249249249249249ull;
-    return x;
-}
-
-__device__ __forceinline__ uint32_t na_cell(double x, double lo, double scale)
-{
-    double f = floor(__dmul_rn(__dsub_rn(x, lo), scale));
-    return f < 0.0 ? 0u : (f > (double)GNB_GRID_MAX ? (uint32_t)GNB_GRID_MAX : (uint32_t)f);
+    if (box_from_minmax((const unsigned long long *)(scr + OFF_MM), (double *)(scr + OFF_BOX)))
+        ((int *)(scr + OFF_FLAG))[0] = 1;
 }
 
 __global__ void k_na_keys(const double *__restrict__ x, const double *__restrict__ y,
@@ -148,8 +72,8 @@ __global__ void k_na_keys(const double *__restrict__ x, const double *__restrict
     if (i >= n) return;
     const double *box = (const double *)(scr + OFF_BOX);
     double scale = 2097152.0 / box[3];
-    uint32_t c0 = na_cell(x[i], box[0], scale), c1 = na_cell(y[i], box[1], scale), c2 = na_cell(z[i], box[2], scale);
-    keys[i] = (na_spread3(c0) << 2) | (na_spread3(c1) << 1) | na_spread3(c2);
+    keys[i] = morton_key(grid_cell(x[i], box[0], scale), grid_cell(y[i], box[1], scale),
+                         grid_cell(z[i], box[2], scale));
 }
 
 __global__ void __launch_bounds__(NA_THREADS) k_na_hist(const uint64_t *__restrict__ k, int n, int shift,

@@ -8,84 +8,24 @@
 // index): the keys are scattered to caller order and sorted by a stable LSD
 // radix sort, so equal keys keep caller order.
 #include "common.cuh"
+#include "morton.cuh"
 
 namespace gnb {
 
 // ---------------------------------------------------------------- root box
-__device__ __forceinline__ unsigned long long dbl_to_ord(double v)
-{
-    long long b = __double_as_longlong(v);
-    return b >= 0 ? ((unsigned long long)b ^ 0x8000000000000000ull) : ~(unsigned long long)b;
-}
-__device__ __forceinline__ double ord_to_dbl(unsigned long long o)
-{
-    long long b = (o & 0x8000000000000000ull) ? (long long)(o ^ 0x8000000000000000ull)
-                                              : (long long)~o;
-    return __longlong_as_double(b);
-}
-
-__global__ void k_mm_init(unsigned long long *mm)
-{
-    int t = threadIdx.x;
-    if (t < 3) mm[t] = ~0ull;        // min
-    else if (t < 6) mm[t] = 0ull;    // max
-    else if (t == 6) mm[t] = 0ull;   // non-finite flag
-}
+__global__ void k_mm_init(unsigned long long *mm) { minmax_init(mm, threadIdx.x); }
 
 __global__ void k_minmax(const double *__restrict__ x, const double *__restrict__ y,
                          const double *__restrict__ z, int n, unsigned long long *mm)
 {
-    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
-    bool bad = false;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double v[3] = {x[i], y[i], z[i]};
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            bad |= !isfinite(v[a]);
-            unsigned long long o = dbl_to_ord(v[a]);
-            mn[a] = o < mn[a] ? o : mn[a];
-            mx[a] = o > mx[a] ? o : mx[a];
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long p = __shfl_xor_sync(0xffffffffu, mn[a], o);
-            unsigned long long q = __shfl_xor_sync(0xffffffffu, mx[a], o);
-            mn[a] = p < mn[a] ? p : mn[a];
-            mx[a] = q > mx[a] ? q : mx[a];
-        }
-    }
-    bad = __any_sync(0xffffffffu, bad);
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            atomicMin(&mm[a], mn[a]);
-            atomicMax(&mm[3 + a], mx[a]);
-        }
-        if (bad) atomicExch(&mm[6], 1ull);
-    }
+    minmax_accumulate(x, y, z, n, mm);
 }
 
 // box = {lo_x, lo_y, lo_z, L, unit}
 __global__ void k_box_finalize(const unsigned long long *mm, double *box, int *status)
 {
     if (threadIdx.x != 0) return;
-    if (mm[6]) atomicOr(status, ST_BAD_INPUT);
-    double ext = 0.0;
-    for (int a = 0; a < 3; a++) {
-        double lo = ord_to_dbl(mm[a]), hi = ord_to_dbl(mm[3 + a]);
-        box[a] = lo;
-        double e = __dsub_rn(hi, lo);
-        ext = e > ext ? e : ext;
-    }
-    double L = 1.0;
-    if (ext > 0.0) {
-        while (L < ext) L *= 2.0;
-        while (L / 2.0 >= ext) L /= 2.0;
-    }
-    box[3] = L;
-    box[4] = L / 2097152.0;
+    if (box_from_minmax(mm, box)) atomicOr(status, ST_BAD_INPUT);
 }
 
 int root_box(gnb_ctx *c)
@@ -101,23 +41,10 @@ int root_box(gnb_ctx *c)
 }
 
 // ---------------------------------------------------------------- Morton
-__host__ __device__ __forceinline__ uint64_t spread3(uint32_t v)
-{
-    uint64_t x = v & 0x1fffffu;
-    x = (x | x << 32) & 0x1f00000000ffffull;
-    x = (x | x << 16) & 0x1f0000ff0000ffull;
-    x = (x | x << 8) & 0x100f00f00f00f00full;
-    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
-    x = (x | x << 2) & 0x1249249249249249ull;
-    return x;
-}
-
 __device__ __forceinline__ int cell_of(double x, double lo, double scale, double unit, float *r)
 {
-    double d = __dsub_rn(x, lo);
-    double f = floor(__dmul_rn(d, scale));
-    int c = f < 0.0 ? 0 : (f > (double)GNB_GRID_MAX ? GNB_GRID_MAX : (int)f);
-    *r = (float)__dsub_rn(d, __dmul_rn((double)c, unit));
+    int c = grid_cell(x, lo, scale);
+    *r = (float)__dsub_rn(__dsub_rn(x, lo), __dmul_rn((double)c, unit));
     return c;
 }
 
@@ -137,7 +64,7 @@ __global__ void k_morton(PArr p, int n, const double *__restrict__ box, uint64_t
     int c2 = cell_of(p.z[i], lo2, scale, unit, &r2);
     p.cx[i] = c0; p.cy[i] = c1; p.cz[i] = c2;
     p.rx[i] = r0; p.ry[i] = r1; p.rz[i] = r2;
-    uint64_t k = (spread3(c0) << 2) | (spread3(c1) << 1) | spread3(c2);
+    uint64_t k = morton_key(c0, c1, c2);
     key[i] = k;
     int o = p.orig[i];
     keyo[o] = k;
@@ -259,6 +186,27 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
         }
         __syncthreads();
     }
+}
+
+// Stable sort of n (64-bit key, 32-bit value) pairs held in (k0, v0), with
+// (k1, v1) as the ping-pong buffers; the sorted pairs end in (k0, v0).
+int radix_sort_pairs(gnb_ctx *c, uint64_t *k0, int *v0, uint64_t *k1, int *v1, int n)
+{
+    int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    uint64_t *kin = k0, *kout = k1;
+    int *vin = v0, *vout = v1;
+    for (int pass = 0; pass < 8; pass++) {
+        int shift = 8 * pass;
+        cudaMemsetAsync(c->rs_total, 0, 256 * sizeof(int), c->s);
+        gnb::counted(k_rs_hist)<<<ntiles, RS_THREADS, 0, c->s>>>(kin, n, shift, c->rs_counts, ntiles, c->rs_total);
+        gnb::counted(k_rs_scan)<<<256, 1024, 0, c->s>>>(c->rs_counts, ntiles, c->rs_total);
+        gnb::counted(k_rs_scatter)<<<ntiles, RS_THREADS, 0, c->s>>>(kin, vin, kout, vout, n, shift, c->rs_counts,
+                                                                    ntiles);
+        uint64_t *tk = kin; kin = kout; kout = tk;
+        int *tv = vin; vin = vout; vout = tv;
+    }
+    GNB_LAUNCH_CHECK(c, "radix sort");
+    return GNB_OK;
 }
 
 // ---------------------------------------------------------------- permute
