@@ -106,6 +106,7 @@ enum gnb_field {
     GNB_F_AGRAV_X, GNB_F_AGRAV_Y, GNB_F_AGRAV_Z, /* self-gravity part of a [float, n] */
     GNB_F_LEVEL,                    /* timestep level k (step t_span 2^-k) of each particle's last step
                                        in gnb_integrate_hier [int32, n] */
+    GNB_F_POT_EXT,                  /* potential of the static NFW halo, 0 when it is off [float, n] */
     GNB_F_COUNT_
 };
 
@@ -257,6 +258,26 @@ int gnb_integrate_cfl(gnb_ctx *ctx, double t_span, double courant, int max_steps
 int gnb_integrate_hier(gnb_ctx *ctx, double t_span, double courant, int max_level, int max_steps, int gravity_mode,
                        double *t_done, int64_t info[3]);
 
+/* Replace particles by ID (Sec. 3.2, step 4: the particles of a supernova
+ * region, integrated elsewhere -- by the surrogate, by the plain small-step
+ * integration, on another device or from a checkpoint -- are handed back and
+ * overwrite the particles with the same IDs).  n particles in SoA arrays:
+ * id, FP64 position, FP32 velocity and internal energy (u is read for gas
+ * particles only; a particle keeps its type, mass and softening).  Every ID
+ * must be held by exactly one particle of the context and appear once in
+ * the input; the particles are checked first and written only if all pass,
+ * so a rejected call changes nothing.  A region is the set of particles its
+ * IDs name: membership is not re-tested against a cube, since particles
+ * drift between hand-off and return.  Positions change, so trees and forces
+ * must be recomputed.  on_device as in gnb_set_particles.
+ * Errors: GNB_EINVAL (n < 1, null pointer, non-finite position),
+ * GNB_ESTATE (no particles, a pending asynchronous surrogate batch),
+ * GNB_EMISMATCH (an ID not held, held twice, or repeated in the input;
+ * more particles than the context holds), GNB_ENOMEM, GNB_ECUDA. */
+int gnb_replace_region(gnb_ctx *ctx, int64_t n, const int64_t *id, const double *x, const double *y,
+                       const double *z, const float *vx, const float *vy, const float *vz, const float *u,
+                       int on_device);
+
 /* Copy one field into dst, which holds cap elements of the field's type.
  * Errors: GNB_EINVAL (field, cap too small, null dst), GNB_ESTATE (field
  * not computed yet), GNB_ECUDA. */
@@ -314,6 +335,12 @@ int gnb_unet_get_params(gnb_unet *net, float *dst, int on_device);
 int gnb_unet_set_params(gnb_unet *net, const float *src, int on_device);
 /* Gradients of the last gnb_unet_train_step (before its Adam update). */
 int gnb_unet_get_grads(gnb_unet *net, float *dst, int on_device);
+/* The FP32 output [batch][grid^3][cout] of the network's last forward pass,
+ * first `batch` samples: gnb_unet_forward, gnb_unet_train_step, or the
+ * prediction gnb_sn_surrogate_batch remapped from (its regions in the order
+ * of `centers`).  Errors: GNB_EINVAL (batch < 1 or above the batch of the
+ * largest pass so far, NULL), GNB_ECUDA. */
+int gnb_unet_get_output(gnb_unet *net, int batch, float *dst, int on_device);
 /* Convolution kernels of the 3^3 layers.  GNB_CONV_AUTO (the default): the
  * tcgen05 tensor-core kernel (TMA halo tiles, TMEM accumulators) wherever the
  * channel counts are multiples of 16 and its weights fit in shared memory,
@@ -434,11 +461,16 @@ int gnb_set_sn_chunks(gnb_ctx *ctx, int chunks);
  * Scratch: one static device array of 6,424,320 bytes (6.13 MiB) inside
  * libgalnb.so; every GPU that loads the library holds it until the process
  * exits.  The first call on a device looks up the array's device address
- * (with that device current), so make that first call before any stream
- * capture.  Every call reuses the same array and clears what must start at
- * zero itself; calls that overlap on the GPU (different streams or host
- * threads, same device) race and give wrong results.  The call uses no
- * cudaMalloc, cudaFree or allocating library routine.
+ * (with that device current) and keeps it for the life of the process, so
+ * make that first call before any stream capture, and do not call this
+ * entry point on a device after cudaDeviceReset there (the array went away
+ * with the context).  Every call reuses the same array and clears what must
+ * start at zero itself; calls that overlap on the GPU (different streams or
+ * host threads, same device) race and give wrong results, so the caller
+ * must serialise them.  Every call waits for its own work on `stream` to
+ * finish before it returns: it reads back a flag that marks a non-finite
+ * position.  The call uses no cudaMalloc, cudaFree or allocating library
+ * routine.
  *
  * x, y, z: device FP64 positions, n each, caller order.  keys: device
  * uint64[n], written with each particle's key in caller order.  order:

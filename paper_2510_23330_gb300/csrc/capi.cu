@@ -136,7 +136,7 @@ static int alloc_gas(gnb_ctx *c, int64_t ng)
     GNB_TRY(dalloc(c, &c->nbr, G * 64)); GNB_TRY(dalloc(c, &c->nd2, G * 64)); GNB_TRY(dalloc(c, &c->mut, G));
     GNB_TRY(dalloc(c, &c->rcnt, G + 1)); GNB_TRY(dalloc(c, &c->roff, G + 1)); GNB_TRY(dalloc(c, &c->rfill, G + 1));
     GNB_TRY(dalloc(c, &c->rlist, G * 64));
-    cudaMemset(c->nbr, 0, sizeof(int) * G * 64);  // list entries are always valid indices
+    cudaMemsetAsync(c->nbr, 0, sizeof(int) * G * 64, c->s);  // list entries are always valid indices
     GNB_TRY(dalloc(c, &c->hax, G)); GNB_TRY(dalloc(c, &c->hay, G)); GNB_TRY(dalloc(c, &c->haz, G));
     GNB_TRY(dalloc(c, &c->hdu, G));
     GNB_TRY(dalloc(c, &c->kflag, 2 * G + 1)); GNB_TRY(dalloc(c, &c->kR, 2 * G + 1));
@@ -157,7 +157,7 @@ static int check_status(gnb_ctx *c)
     int st = 0;
     GNB_TRY(cuda_check(c, cudaMemcpy(&st, c->status_d, sizeof(int), cudaMemcpyDeviceToHost), "status read"));
     if (st == 0) return GNB_OK;
-    cudaMemset(c->status_d, 0, sizeof(int));
+    cudaMemsetAsync(c->status_d, 0, sizeof(int), c->s);
     if (st & ST_BAD_INPUT) return fail(c, GNB_EINVAL, "non-finite particle position");
     if (st & ST_TREE_OVERFLOW) return fail(c, GNB_ECAPACITY, "tree node capacity exceeded");
     if (st & ST_STACK_OVERFLOW) return fail(c, GNB_ECAPACITY, "tree walk stack overflow");
@@ -265,8 +265,14 @@ int gnb_create(gnb_ctx **out, const gnb_config *cfg)
         gnb_destroy(c);
         return GNB_ENOMEM;
     }
-    cudaMemset(c->status_d, 0, 4 * sizeof(int));
-    cudaMemset(c->counters_d, 0, 8 * sizeof(unsigned long long));
+    // cleared on the context's stream, which may be a non-blocking one
+    if (cudaMemsetAsync(c->status_d, 0, 4 * sizeof(int), c->s) != cudaSuccess ||
+        cudaMemsetAsync(c->counters_d, 0, 8 * sizeof(unsigned long long), c->s) != cudaSuccess ||
+        cudaStreamSynchronize(c->s) != cudaSuccess) {
+        cudaGetLastError();
+        gnb_destroy(c);
+        return GNB_ECUDA;
+    }
     *out = c;
     return GNB_OK;
 }
@@ -279,6 +285,7 @@ void gnb_destroy(gnb_ctx *c)
     free_particles(c);
     free_gas(c);
     hier_free(c);
+    replace_free(c);
     void *all[] = {c->status_d, c->n_d, c->ngas_d, c->counters_d, c->work_d, c->box_d, c->mm_d, c->red_d,
                    c->rs_total, c->rtot_d, c->scan_part, c->scan_poff, c->gl_pool, c->gl_next, c->gl_cnt,
                    c->gl_top, c->gl_head, c->gl_ref, c->gl_lcum};
@@ -324,6 +331,7 @@ int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *t
     c->sphf_valid = false;
     c->have_h = false;
     c->hier_on = c->hier_valid = false;
+    c->rid_valid = false;
     GNB_TRY(alloc_particles(c, n));
     c->cur = 0;
     PArr &p = c->P[0];
@@ -531,7 +539,7 @@ static int finish(gnb_ctx *c, int rc)
     if (rc != GNB_OK) {
         cudaStreamSynchronize(c->s);
         cudaGetLastError();
-        cudaMemset(c->status_d, 0, sizeof(int));
+        cudaMemsetAsync(c->status_d, 0, sizeof(int), c->s);
         phase_resolve(c);
         return rc;
     }
@@ -801,6 +809,22 @@ int gnb_sn_surrogate_batch(gnb_ctx *c, gnb_unet *net, int nreg, const double *ce
     return rc;
 }
 
+int gnb_replace_region(gnb_ctx *c, int64_t n, const int64_t *id, const double *x, const double *y, const double *z,
+                       const float *vx, const float *vy, const float *vz, const float *u, int on_device)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (n < 1) return fail(c, GNB_EINVAL, "particle count out of range");
+    if (!id || !x || !y || !z || !vx || !vy || !vz || !u) return fail(c, GNB_EINVAL, "null array");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    if (c->sna_pending) return fail(c, GNB_ESTATE, "an asynchronous surrogate batch is pending");
+    if (n > c->n) return fail(c, GNB_EMISMATCH, "more particles than the context holds");
+    int rc = replace_particles(c, n, id, x, y, z, vx, vy, vz, u, on_device);
+    if (rc == GNB_OK)
+        c->sorted_valid = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
+    return finish(c, rc);
+}
+
 static int64_t field_count(gnb_ctx *c, int f, size_t *esz)
 {
     switch (f) {
@@ -822,6 +846,7 @@ int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
     bool need_sort = field == GNB_F_KEY || field == GNB_F_ORDER;
     bool need_tree = field == GNB_F_NODES || field == GNB_F_GROUPS;
     bool need_grav = field == GNB_F_AX || field == GNB_F_AY || field == GNB_F_AZ || field == GNB_F_POT ||
+                     field == GNB_F_POT_EXT ||
                      field == GNB_F_AGRAV_X || field == GNB_F_AGRAV_Y || field == GNB_F_AGRAV_Z;
     bool need_den = field == GNB_F_RHO || field == GNB_F_PRES || field == GNB_F_CS || field == GNB_F_H2 ||
                     field == GNB_F_NBR;

@@ -235,6 +235,15 @@ struct gnb_ctx {
     unsigned long long *hred_h = nullptr;  // pinned copy
     double *red_d = nullptr;                   // reduction scratch
     int64_t stats[GNB_S_COUNT_] = {0};
+    // replacement by ID (replace.cu): the held IDs sorted with their caller
+    // indices (built on the first replacement after gnb_set_particles), and
+    // per-call staging of the incoming particles
+    bool rid_valid = false;
+    int64_t rid_cap = 0, rep_cap = 0, rep_scap = 0;
+    uint64_t *rid_key = nullptr, *rid_key2 = nullptr;
+    int *rid_orig = nullptr, *rid_orig2 = nullptr, *rid_inv = nullptr, *rid_mark = nullptr;
+    unsigned char *rep_buf = nullptr;   // incoming id, x, y, z, vx, vy, vz, u (48 B per particle)
+    int *rep_slot = nullptr;            // slot of each incoming particle
 
     // per-phase CUDA-event timers (enabled by gnb_set_timing)
     bool timing = false;
@@ -283,6 +292,11 @@ void phase_end(gnb_ctx *c);
 
 // sort.cu
 int morton_and_sort(gnb_ctx *c);
+int radix_sort_pairs(gnb_ctx *c, uint64_t *k0, int *v0, uint64_t *k1, int *v1, int n);
+// replace.cu
+int replace_particles(gnb_ctx *c, int64_t n, const int64_t *id, const double *x, const double *y, const double *z,
+                      const float *vx, const float *vy, const float *vz, const float *u, int on_device);
+void replace_free(gnb_ctx *c);
 
 // integrate.cu: hierarchical timesteps
 int hier_buffers(gnb_ctx *c);

@@ -230,6 +230,7 @@ int scatter_out(gnb_ctx *c, int field, void *dst)
     case GNB_F_AGRAV_Y: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->gay, a.orig, n, (float *)dst); break;
     case GNB_F_AGRAV_Z: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->gaz, a.orig, n, (float *)dst); break;
     case GNB_F_POT: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->pot, a.orig, n, (float *)dst); break;
+    case GNB_F_POT_EXT: gnb::counted(k_scatter_orig<float>)<<<nb, 256, 0, c->s>>>(c->pext, a.orig, n, (float *)dst); break;
     case GNB_F_U: gnb::counted(k_scatter_orig_zero_star)<<<nb, 256, 0, c->s>>>(a.u, a.orig, a.type, n, (float *)dst); break;
     case GNB_F_DUDT:
         gnb::counted(k_scatter_orig_zero_star)<<<nb, 256, 0, c->s>>>(c->dudt, a.orig, a.type, n, (float *)dst);

@@ -933,7 +933,7 @@ int unet_poll_error(gnb_unet *u)
     int e = 0;
     if (!u || !u->err_d || cudaMemcpy(&e, u->err_d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GNB_OK;
     if (e == 0) return GNB_OK;
-    cudaMemset(u->err_d, 0, sizeof(int));
+    cudaMemsetAsync(u->err_d, 0, sizeof(int), u->s);
     return GNB_ETIMEOUT;
 }
 
@@ -1071,6 +1071,14 @@ int gnb_unet_get_grads(gnb_unet *u, float *dst, int on_device)
 {
     if (!u || !dst) return GNB_EINVAL;
     cudaMemcpyAsync(dst, u->g, u->nparam * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, u->s);
+    return unet_check(u, GNB_OK);
+}
+
+int gnb_unet_get_output(gnb_unet *u, int batch, float *dst, int on_device)
+{
+    if (!u || !dst || batch < 1 || batch > u->bcap || !u->yout) return GNB_EINVAL;
+    size_t bytes = (size_t)vox(u, 0, batch) * u->cout * 4;
+    cudaMemcpyAsync(dst, u->yout, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, u->s);
     return unet_check(u, GNB_OK);
 }
 

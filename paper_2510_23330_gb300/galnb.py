@@ -34,7 +34,8 @@ GNB_CONV_AUTO = 0
 GNB_CONV_MMA_SYNC = 2
 
 FIELDS = ["X", "Y", "Z", "VX", "VY", "VZ", "AX", "AY", "AZ", "POT", "U", "DUDT", "RHO", "PRES", "CS", "H2",
-          "KEY", "ORDER", "NBR", "NODES", "GROUPS", "ID", "AGRAV_X", "AGRAV_Y", "AGRAV_Z", "LEVEL"]
+          "KEY", "ORDER", "NBR", "NODES", "GROUPS", "ID", "AGRAV_X", "AGRAV_Y", "AGRAV_Z", "LEVEL",
+          "POT_EXT"]
 F = {name: i for i, name in enumerate(FIELDS)}
 FIELD_DTYPE = {"X": np.float64, "Y": np.float64, "Z": np.float64, "H2": np.float64, "KEY": np.uint64,
                "ORDER": np.int64, "NBR": np.int64, "NODES": np.int64, "GROUPS": np.int64, "ID": np.int64,
@@ -101,6 +102,8 @@ def _declare(L):
     L.gnb_phase_times.argtypes = [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                   C.c_int]
     L.gnb_phase_times.restype = C.c_int
+    L.gnb_replace_region.argtypes = [_vp, C.c_int64] + [_vp] * 8 + [C.c_int]
+    L.gnb_replace_region.restype = C.c_int
     L.gnb_morton_order_noalloc.argtypes = [C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gnb_morton_order_noalloc.restype = C.c_int
     L.gnb_set_config.argtypes = [_vp, C.POINTER(gnb_config)]
@@ -132,6 +135,8 @@ def _declare(L):
     for name in ("gnb_unet_get_params", "gnb_unet_set_params", "gnb_unet_get_grads"):
         getattr(L, name).argtypes = [_vp, _vp, C.c_int]
         getattr(L, name).restype = C.c_int
+    L.gnb_unet_get_output.argtypes = [_vp, C.c_int, _vp, C.c_int]
+    L.gnb_unet_get_output.restype = C.c_int
     L.gnb_unet_set_conv_impl.argtypes = [_vp, C.c_int]
     L.gnb_unet_set_conv_impl.restype = C.c_int
     L.gnb_unet_test_wait_timeout.argtypes = [_vp]
@@ -189,6 +194,10 @@ def gnb_compute_forces(ctx, mode):
 
 def gnb_step_kdk(ctx, dt, nsteps, mode):
     return lib().gnb_step_kdk(ctx, dt, nsteps, mode)
+
+
+def gnb_replace_region(ctx, n, id, x, y, z, vx, vy, vz, u, on_device):
+    return lib().gnb_replace_region(ctx, n, id, x, y, z, vx, vy, vz, u, on_device)
 
 
 def gnb_get(ctx, field, dst, cap, on_device):
@@ -273,6 +282,10 @@ def gnb_unet_get_grads(net, dst, on_device):
     return lib().gnb_unet_get_grads(net, dst, on_device)
 
 
+def gnb_unet_get_output(net, batch, dst, on_device):
+    return lib().gnb_unet_get_output(net, batch, dst, on_device)
+
+
 def gnb_unet_forward(net, batch, x, y, on_device):
     return lib().gnb_unet_forward(net, batch, x, y, on_device)
 
@@ -322,6 +335,13 @@ class UNet:
     def get_grads(self):
         out = np.empty(self.num_params(), np.float32)
         self._chk(gnb_unet_get_grads(self.h, out.ctypes.data, 0), "get_grads")
+        return out
+
+    def get_output(self, batch):
+        """FP32 output [batch, G, G, G, cout] of the last forward pass."""
+        g = self.grid
+        out = np.empty((batch, g, g, g, self.cout), np.float32)
+        self._chk(gnb_unet_get_output(self.h, batch, out.ctypes.data, 0), "get_output")
         return out
 
     def set_params(self, flat):
@@ -506,6 +526,23 @@ class Context:
         if field == "NODES" and isinstance(out, np.ndarray):
             return out.reshape(-1, 4)
         return out
+
+    def replace_region(self, p: dict):
+        """Overwrite the particles with IDs p["id"] by p's position, velocity
+        and internal energy (numpy arrays or tensors, all on one side)."""
+        keys = ("id", "x", "y", "z", "vx", "vy", "vz", "u")
+        arrs = []
+        for k in keys:
+            a = p[k]
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=self._DT[k])
+            arrs.append(a)
+        ptrs = [_ptr(a) for a in arrs]
+        on_dev = {d for _, d in ptrs}
+        if len(on_dev) != 1:
+            raise ValueError("all arrays must be on the same side (host or device)")
+        n = int(arrs[0].shape[0])
+        self._chk(gnb_replace_region(self.h, n, *[q for q, _ in ptrs], on_dev.pop()))
 
     def diagnostics(self):
         out = (C.c_double * 10)()

@@ -112,6 +112,56 @@ def test_batched_surrogate_step_invariants(G, orc):
     stream.synchronize()
 
 
+def test_batched_surrogate_step_matches_oracle_remap(G, orc):
+    """Eight Gibbs sweeps inside the graph-captured batch of four regions:
+    every member of region r ends where the oracle's remap of r puts it, given
+    the prediction the batch itself computed (read back from the network):
+    voxel choices bit for bit, positions within 1e-12 of the side, u and v
+    within 1e-6 relative; particles outside the regions do not move."""
+    import torch
+    from oracle import surrogate as S
+    stream = torch.cuda.Stream()
+    side, grid, seed = 60.0, 32, 21
+    with torch.cuda.stream(stream):
+        regions = [ics.sn_region(7000 + 2500 * k, seed=60 + k, grid=32) for k in range(4)]
+        offs = [(150.0 * k, -30.0 * k, 10.0 * k) for k in range(4)]
+        parts = {}
+        for r, o in zip(regions, offs):
+            r = dict(r)
+            for a, key in enumerate(("x", "y", "z")):
+                r[key] = r[key] + o[a]
+            for key, val in r.items():
+                parts.setdefault(key, []).append(val)
+        p = {k: np.concatenate(v) for k, v in parts.items()}
+        p["id"] = np.arange(p["x"].size, dtype=np.int64) * 5 + 17
+        c = G.Context(stream=stream.cuda_stream)
+        c.set_particles(p)
+        c.compute_sph_density()
+        net = _net32(G, stream)
+        c.sn_surrogate_batch(net, offs, side=side, seed=seed, sweeps=8, use_graph=True)
+        pred = net.get_output(len(offs))
+        got = {k: c.get(k) for k in ("X", "Y", "Z", "U", "VX", "VY", "VZ", "ID")}
+    stream.synchronize()
+    s = orc.state(p)
+    reg = S.members(s, offs, side)
+    newp = np.stack([got["X"], got["Y"], got["Z"]], axis=1)
+    pos0 = np.stack([s["x"], s["y"], s["z"]], axis=1)
+    assert np.array_equal(got["ID"], p["id"])
+    assert np.array_equal(newp[reg < 0], pos0[reg < 0])
+    for r, cen in enumerate(offs):
+        mem = np.nonzero(reg == r)[0]
+        assert mem.size > 1000
+        vox, rp, ru, rv = S.remap(pred[r].reshape(-1, 5).astype(np.float64), p["id"][mem], pos0[mem], cen, side,
+                                  grid, seed=seed, sweeps=8)
+        lo = np.asarray(cen) - 0.5 * side
+        gv = np.floor((newp[mem] - lo) / (side / grid)).astype(np.int64)
+        assert np.array_equal(gv, vox), r
+        assert np.max(np.abs(newp[mem] - rp)) < 1e-12 * side
+        assert np.allclose(got["U"][mem], ru, rtol=1e-6)
+        v = np.stack([got["VX"], got["VY"], got["VZ"]], axis=1)[mem]
+        assert np.allclose(v, rv, rtol=1e-6, atol=1e-6)
+
+
 def test_pipelined_batch_matches_sequential(G, orc):
     """The batch pipelined over region chunks (voxelise / U-Net / remap of
     different chunks on three streams, one captured graph) against the same

@@ -1,8 +1,7 @@
 """GPU parity of the BF16 tensor-core U-Net against the FP64 oracle run on the
-same BF16-rounded inputs, weights and stored activations: forward output
-within a relative L2 error of 1e-2; each parameter gradient within
-max(1e-2, 1.5 s) of it, s being that gradient's own BF16 sensitivity (the
-oracle with vs without BF16 storage); training lowers the loss."""
+same BF16-rounded inputs, weights and stored activations: forward output and
+every parameter gradient within a relative L2 error of 1e-2; Adam's FP32
+master weights element by element; training lowers the loss."""
 import numpy as np
 import pytest
 
@@ -69,9 +68,18 @@ def test_forward_matches_oracle(G, grid, batch, levels, impl):
     assert np.max(np.abs(y - ref)) < 0.05 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("grid,levels,impl", [(16, 4, "auto"), (16, 4, "mma_sync"), (20, 3, "auto")])
-def test_gradients_match_oracle(G, grid, levels, impl):
-    spec, p, x, net = _setup(G, grid, 2, seed=3, levels=levels, impl=impl)
+# Sizes whose coarsest level keeps at least 4^3 voxels per sample: at a 2^3
+# bottleneck a deep layer's weight gradient sums a handful of voxels with
+# cancellation, and FP32 (GPU) against FP64 (oracle) accumulation rounds a
+# stored activation to a different BF16 neighbour often enough to move it by
+# several per cent; with more voxels per sum such flips average out.  20^3
+# with 3 levels (bottleneck 5^3) leaves ragged tensor-core tiles.
+@pytest.mark.parametrize("grid,batch,levels,impl", [(32, 2, 4, "auto"), (32, 1, 4, "mma_sync"),
+                                                    (64, 1, 4, "auto"), (20, 2, 3, "auto")])
+def test_gradients_match_oracle(G, grid, batch, levels, impl):
+    """Every parameter gradient within relative L2 1e-2 of the FP64 oracle run
+    on the same BF16-rounded inputs, weights and stored activations."""
+    spec, p, x, net = _setup(G, grid, batch, seed=3, levels=levels, impl=impl)
     rng = np.random.default_rng(9)
     t = rng.normal(size=x.shape)
     loss = net.train_step(x.astype(np.float32), t.astype(np.float32), 0.0)
@@ -80,21 +88,31 @@ def test_gradients_match_oracle(G, grid, levels, impl):
     assert abs(loss / ref_loss - 1.0) < 1e-2
     g = unflat(net.get_grads(), spec, p)
     rg = U.backward(p, cache, dy, levels=levels, bf=True)
-    # Sensitivity of each gradient to BF16 storage: the same oracle without
-    # any BF16 rounding.  Deep layers (the 2^3 bottleneck at this size sums
-    # few voxels with cancellation) move by several per cent between the two,
-    # and FP32-vs-FP64 accumulation flips individual BF16 roundings on the
-    # GPU in the same way, so each layer's bound scales with its sensitivity.
-    y64, cache64 = U.forward(p, x, levels=levels, bf=False)
-    _, dy64 = U.mse(y64, t)
-    rg64 = U.backward(p, cache64, dy64, levels=levels, bf=False)
-    sens = {k: rel_l2(rg64[k], rg[k]) for k in rg}
     errs = {k: rel_l2(g[k], rg[k]) for k in rg}
-    errs64 = {k: rel_l2(g[k], rg64[k]) for k in rg}
     worst = sorted(errs.items(), key=lambda kv: -kv[1])[:6]
     for k in rg:
-        assert errs[k] < max(1e-2, 1.5 * sens[k]), (k, errs[k], sens[k], worst)
-        assert errs64[k] < max(1e-2, 2.0 * sens[k]), (k, errs64[k], sens[k])
+        assert errs[k] < 1e-2, (k, errs[k], worst)
+
+
+def test_adam_matches_oracle(G):
+    """Three training steps: the GPU's FP32 master weights after each Adam
+    update equal the oracle's Adam (Kingma and Ba; beta 0.9, 0.999, eps
+    1e-8) applied to the GPU's own gradients of that step, element by
+    element within 1e-6 relative (plus 1e-6 of the step size lr)."""
+    spec, p, x, net = _setup(G, 16, 1, seed=7)
+    rng = np.random.default_rng(13)
+    t = rng.normal(size=x.shape).astype(np.float32)
+    lr = 1e-3
+    ref = {k: v.copy() for k, v in p.items()}
+    st = U.adam_init(ref)
+    for step in range(3):
+        net.train_step(x.astype(np.float32), t, lr)
+        g = unflat(net.get_grads(), spec, p)
+        ref = U.adam_step(ref, g, st, lr=lr)
+        got = unflat(net.get_params(), spec, p)
+        for k in ref:
+            d = np.abs(got[k] - ref[k])
+            assert np.all(d <= 1e-6 * np.abs(ref[k]) + 1e-6 * lr), (step, k, float(d.max()))
 
 
 def test_training_lowers_loss(G):
