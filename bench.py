@@ -1,14 +1,19 @@
 #!/usr/bin/env python3
 """Benchmark of the N-body/SPH step: particle-steps/s (gravity + SPH).
 
-Workload (default): the 2^20-particle disk model -- 80 % stars in an
-exponential disk (R_d = 1, z_d = 0.1), 20 % gas (R_d = 2, u log-uniform in
-[1e-3, 1e-1]) in a static NFW halo (r_s = 8, M_s = 30), G = 1, eps = 0.01,
-Barnes-Hut tree gravity with theta = 0.5 and monopole + quadrupole, 64 SPH
-neighbours, kick-drift-kick steps of dt = 1e-3.  A step is one full KDK step
+Workload (default, the largest single-GPU configuration): the 2^24-particle
+disk model -- 90 % stars in an exponential disk (R_d = 1, z_d = 0.1), 10 % gas
+(R_d = 2, u log-uniform in [1e-3, 1e-1]) in a static NFW halo (r_s = 8,
+M_s = 30), G = 1, eps = 0.01, Barnes-Hut tree gravity with theta = 0.5 and
+monopole + quadrupole, 64 SPH neighbours, kick-drift-kick steps of
+dt = 1e-3, with the energy and momentum drift over the timed steps
+(--config disk: the 2^20 disk with 20 % gas).  A step is one full KDK step
 through the C ABI (tree build, gravity, halo, kernel size, density, force,
 kicks, drift).  Inputs are resident in HBM when the timed region starts; L2 is
-flushed (256 MiB write on the same stream) before every timed step.
+flushed (256 MiB write on the same stream) before every timed step.  Besides
+the gravity kernel's FP32 roofline, the line reports the HBM fraction of the
+tree build (sort + octree + moments + hydro tree) and of the two SPH passes
+against their algorithmic bytes.
 
 The same JSON line carries the supernova half of the metric under "sn"
 (rank 0, one GPU): SN regions per second of the surrogate path (256 ragged
@@ -57,6 +62,17 @@ FLOP_PC = 59
 UNET_GFLOP_64 = 29.0497
 SN_REPORT = os.path.join(ROOT, "profiles", "surrogate_sn_region_1e5_grid64.txt")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Algorithmic bytes per unit of the HBM-bound phases:
+#  tree build, per particle: positions read 24 + key write 8 + 4 radix passes
+#    of (key, index) read and written 4 x 24 + the permutation of ~48 B of
+#    state read and written 96 + node build 8 + moments 28 = 260 B;
+#  kNN + density, per gas particle: state read 28 + neighbour list written
+#    256 + h^2 8, then state 40 + list read 256 + rho/P/c written 12 = 600 B;
+#  hydro force, per gas particle: state 56 + symmetric list ~4 x 66 +
+#    results 16 = ~390 B (neighbour state re-reads hit L2 in Morton order).
+BYTES_TREE_PER_PARTICLE = 260
+BYTES_KNN_DENSITY_PER_GAS = 600
+BYTES_FORCE_PER_GAS = 390
 
 
 def workload(name: str, seed: int):
@@ -130,10 +146,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(win)}
 
 
-def gravity_traffic():
-    """DRAM bytes per gravity launch from the committed ncu summary, if the
-    kernel source is unchanged since the capture."""
-    path = os.path.join(ROOT, "profiles", "gravity_tree_disk2p20.txt")
+def gravity_traffic(config):
+    """DRAM bytes per gravity launch of the full workload, from the committed
+    ncu summary of that workload's gravity kernels, if the kernel source is
+    unchanged since the capture (else None)."""
+    name = {"disk": "gravity_tree_disk2p20.txt", "large": "gravity_tree_disk2p24.txt"}.get(config)
+    if name is None:
+        return None
+    path = os.path.join(ROOT, "profiles", name)
     src = os.path.join(ROOT, "paper_2510_23330_gb300", "csrc", "gravity.cu")
     try:
         text = open(path).read()
@@ -149,18 +169,36 @@ def gravity_traffic():
         return None
 
 
-def cpu_baseline(p, name, knn_seconds=6.0):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(p, name, knn_seconds=6.0, n_g=64):
     """The FP64 oracle on a bounded sample of one force evaluation (about
-    10 s of CPU work at 2^20): the full tree build plus every 4th group's walk
-    (scaled by 4) and brute-force kNN of as many sampled gas particles as
-    take about knn_seconds (scaled to all gas)."""
+    15-25 s of CPU work): the full tree build plus every k-th group's walk
+    (k = N / 2^18, scaled by k) and brute-force kNN of as many sampled gas
+    particles as take about knn_seconds (scaled to all gas)."""
     import oracle
     oracle.build()
     n = p["x"].shape[0]
     gi = np.nonzero(p["type"] == 1)[0]
-    stride = 4 if n > 100000 else 1
+    stride = max(1, n >> 18)
     t0 = time.perf_counter()
-    tb, tw, st = oracle.tree_gravity_sampled(p, stride, theta=0.5, n_leaf=16, n_g=64, quad=True)
+    tb, tw, st = oracle.tree_gravity_sampled(p, stride, theta=0.5, n_leaf=16, n_g=n_g, quad=True)
     t_grav = tb + tw * stride
     g = {k: np.asarray(p[k][gi], np.float64) for k in ("x", "y", "z")}
     rng = np.random.default_rng(0)
@@ -175,7 +213,8 @@ def cpu_baseline(p, name, knn_seconds=6.0):
     oracle.knn(g, 64, sample=s)
     t_knn = (time.perf_counter() - t1) * gi.size / ns
     total = t_grav + t_knn
-    return {"value": n / total, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    return {"value": n / total, "unit": UNIT, "cores": oracle.num_threads(), "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": (f"one force evaluation of {name}: tree build + 1/{stride} of the group walks "
                        f"(x{stride}), brute-force kNN of {ns} gas particles (x{gi.size / ns:.0f}); "
                        f"SPH density/force sums and kicks not included; measured {time.perf_counter() - t0:.1f} s"),
@@ -409,7 +448,27 @@ def run_ours(args, world, rank, local):
     g_ms = phases["GRAVITY"] / g_calls
     flops = (FLOP_PP * npp + FLOP_PC * npc) / max(args.steps, 1)
     achieved = flops / (g_ms * 1e-3) / 1e12
-    traffic = gravity_traffic() if args.config == "disk" else None  # the profile is of the 2^20 disk
+    traffic = gravity_traffic(args.config)
+    try:
+        hbm_peak, hbm_note = float(json.load(open(PEAKS))["hbm_gbs"]), "of measured (copy, MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        hbm_peak, hbm_note = 6800.0, "of fallback"
+    n_gas = int(np.sum(p["type"] == 1))
+
+    def hbm_entry(phase_names, bytes_total, what):
+        ms = sum(phases[k] for k in phase_names) / max(args.steps, 1)
+        gbs = bytes_total / (ms * 1e-3) / 1e9 if ms > 0 else None
+        return {"bound": "hbm", "phases": list(phase_names), "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak if gbs else None, "ms_per_step": ms, "algorithmic_bytes": bytes_total,
+                "note": f"{what}; {hbm_note}"}
+
+    rooflines = {
+        "tree_build": hbm_entry(("SORT", "TREE", "HYDRO_TREE"), BYTES_TREE_PER_PARTICLE * n,
+                                f"{BYTES_TREE_PER_PARTICLE} B per particle"),
+        "knn_density": hbm_entry(("KNN",), BYTES_KNN_DENSITY_PER_GAS * n_gas,
+                                 f"{BYTES_KNN_DENSITY_PER_GAS} B per gas particle"),
+        "hydro_force": hbm_entry(("FORCE",), BYTES_FORCE_PER_GAS * n_gas, f"{BYTES_FORCE_PER_GAS} B per gas particle"),
+    }
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -424,6 +483,7 @@ def run_ours(args, world, rank, local):
                      "note": (f"flops = {FLOP_PP}/PP + {FLOP_PC}/PC interaction; peak = 152 SMs x 128 lanes x 2 x "
                               f"2070 MHz (FP32 CUDA cores)"),
                      "ms_per_launch": g_ms},
+        "rooflines_hbm": rooflines,
         "interactions_per_step": {"pp": npp / args.steps, "pc": npc / args.steps},
         "n_group_tuning_ms": tuning,
         "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
@@ -440,7 +500,7 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_e2e:
         out["e2e"] = e2e(args, p, pr, stream, galnb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(p, desc)
+        out["cpu_baseline"] = cpu_baseline(p, desc, n_g=int(pr["cfg"].get("n_group", 64)))
     ctx.close()
     if rank == 0 and world == 1 and not args.no_sn:
         out["sn"] = sn_bench(stream, galnb, torch)
@@ -485,7 +545,7 @@ def run_reference(args, world, rank, local):
     secs = []
     cb = None
     for _ in range(args.steps):
-        cb = cpu_baseline(p, desc)
+        cb = cpu_baseline(p, desc, knn_seconds=2.0, n_g=128)
         secs.append(cb["seconds_per_step_estimate"])
     value = n * args.steps / sum(secs)
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -493,7 +553,7 @@ def run_reference(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": desc, "n": n},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cb["cores"],
-                             "sample": cb["sample"]},
+                             "cpu_model": cb["cpu_model"], "sample": cb["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -503,7 +563,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="disk", choices=["disk", "large", "tiny"])
+    ap.add_argument("--config", default="large", choices=["disk", "large", "tiny"])
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
