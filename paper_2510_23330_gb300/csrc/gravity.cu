@@ -13,10 +13,11 @@
 //    persistently; it streams the group's chains through shared memory,
 //    staging accepted cells (monopole + quadrupole) and the particles of
 //    opened leaves as FP32 offsets from the group's reference grid point
-//    (Sec. 4.3 mixed precision); every thread evaluates its i-particle
-//    (two above 16 particles per group chunk) against the staged j
-//    entries, read as warp-wide broadcasts, and the j loop is split over as
-//    many thread sets as fit ("j-splits") so all warps stay busy.
+//    (Sec. 4.3 mixed precision); every thread evaluates its i-particles
+//    (one, two above 16 and four above 64 particles per group chunk)
+//    against the staged j entries, read as warp-wide broadcasts, and the j
+//    loop is split over as many thread sets as fit ("j-splits") so all
+//    warps stay busy.
 // Pair arithmetic is FP32 on the CUDA cores (not a dense contraction).
 #include <algorithm>
 
@@ -31,6 +32,8 @@ namespace gnb {
 #define GW_LEAF 256
 #define GW_JP 512
 #define GW_JC 256
+#define GW_NI_MAX 4     // i-particles per thread at most
+#define GW_EVAL_CTAS 5  // evaluation CTAs per SM the registers are sized for (96 per thread)
 
 struct GravParams {
     int4 *na, *nb;
@@ -94,16 +97,28 @@ __device__ __forceinline__ bool must_open(int4 C, int level, const int *bmin, co
     return overlap || d2 <= d2max[level];
 }
 
+// FP32 1/sqrt(x) of a squared distance plus softening (a positive normal
+// number when no softening is zero): the hardware approximation with
+// denormals flushed, a single instruction (relative error below 2^-22).
+__device__ __forceinline__ float rsqrt_pos(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Particle-particle: accumulate sum m_j (x_j - x_i)/R^3 and sum m_j/R, with
-// R^2 = |x_j - x_i|^2 + eps_i^2 + eps_j^2.
+// R^2 = |x_j - x_i|^2 + eps_i^2 + eps_j^2.  MASK (some softening is zero): a
+// pair at R = 0 (the particle itself) contributes nothing.
 template <bool MASK>
 __device__ __forceinline__ void pp_one(float4 q, float e, float xi, float yi, float zi, float e2i, float &ax,
                                        float &ay, float &az, float &ph)
 {
     float dx = q.x - xi, dy = q.y - yi, dz = q.z - zi;
     float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmaf_rn(dz, dz, e + e2i)));
-    float ri = rsqrtf(r2);
-    if (MASK) ri = r2 > 0.f ? ri : 0.f;
+    float ri;
+    if (MASK) ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    else ri = rsqrt_pos(r2);
     float mr = q.w * ri;
     float mr3 = mr * ri * ri;
     ax = __fmaf_rn(mr3, dx, ax);
@@ -120,72 +135,69 @@ __device__ __forceinline__ void pp_loop(const GravSmem &S, int np, int split, in
     for (int j = split; j < np; j += js) pp_one<MASK>(S.jp[j], S.je[j], xi, yi, zi, e2i, ax, ay, az, ph);
 }
 
-// Two i-particles per thread: each staged j entry is read once for both.
-template <bool MASK>
-__device__ __forceinline__ void pp_loop2(const GravSmem &S, int np, int split, int js, const float4 &i0,
-                                         const float4 &i1, float4 &a0, float4 &a1)
+// NI i-particles per thread: each staged j entry is read from shared memory
+// once for all of them.
+template <int NI, bool MASK>
+__device__ __forceinline__ void pp_loopN(const GravSmem &S, int np, int split, int js, const float4 (&pi)[NI],
+                                         float4 (&acc)[NI])
 {
-#pragma unroll 4
+    constexpr int UNR = NI >= 4 ? 2 : (NI == 2 ? 2 : 4);
+#pragma unroll UNR
     for (int j = split; j < np; j += js) {
         const float4 q = S.jp[j];
         const float e = S.je[j];
-        pp_one<MASK>(q, e, i0.x, i0.y, i0.z, i0.w, a0.x, a0.y, a0.z, a0.w);
-        pp_one<MASK>(q, e, i1.x, i1.y, i1.z, i1.w, a1.x, a1.y, a1.z, a1.w);
+#pragma unroll
+        for (int k = 0; k < NI; k++)
+            pp_one<MASK>(q, e, pi[k].x, pi[k].y, pi[k].z, pi[k].w, acc[k].x, acc[k].y, acc[k].z, acc[k].w);
     }
 }
 
 // Particle-cell with monopole (+ traceless quadrupole), r = x_i - com:
 //   a   += -M r/R^3 + Q r/R^5 - 5/2 (r.Q.r) r/R^7
 //   phi += -M/R - 1/2 r.Q.r/R^5         (accumulated with the sign flipped)
+// evaluated as t = M/R^3 + 5/2 (r.Q.r/R^5)/R^2, a += (Q r)/R^5 - t r.
 template <bool QUAD>
 __device__ __forceinline__ void pc_one(float4 a, float4 b, float4 d, float xi, float yi, float zi, float e2i,
                                        float &ax, float &ay, float &az, float &ph)
 {
     float rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
     float R2 = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, __fmaf_rn(rz, rz, e2i + d.z)));
-    float Ri = rsqrtf(R2);
+    float Ri = rsqrt_pos(R2);
     float Ri2 = Ri * Ri;
-    float mR = a.w * Ri;
-    float mR3 = mR * Ri2;
+    float Ri3 = Ri * Ri2;
     if (QUAD) {
         float qx = __fmaf_rn(b.x, rx, __fmaf_rn(b.w, ry, d.x * rz));
         float qy = __fmaf_rn(b.w, rx, __fmaf_rn(b.y, ry, d.y * rz));
         float qz = __fmaf_rn(d.x, rx, __fmaf_rn(d.y, ry, b.z * rz));
         float rqr = __fmaf_rn(rx, qx, __fmaf_rn(ry, qy, rz * qz));
-        float Ri5 = Ri2 * Ri2 * Ri;
-        float Ri7 = Ri5 * Ri2;
-        float t = __fmaf_rn(2.5f * rqr, Ri7, mR3);
+        float Ri5 = Ri3 * Ri2;
+        float rqr5 = rqr * Ri5;
+        float t = __fmaf_rn(rqr5, 2.5f * Ri2, a.w * Ri3);
         // two chained FMAs per component (Q r/R^5, then -t r)
         ax = __fmaf_rn(-t, rx, __fmaf_rn(qx, Ri5, ax));
         ay = __fmaf_rn(-t, ry, __fmaf_rn(qy, Ri5, ay));
         az = __fmaf_rn(-t, rz, __fmaf_rn(qz, Ri5, az));
-        ph = __fmaf_rn(0.5f * rqr, Ri5, ph) + mR;
+        ph = __fmaf_rn(0.5f, rqr5, __fmaf_rn(a.w, Ri, ph));
     } else {
+        float mR3 = a.w * Ri3;
         ax = __fmaf_rn(-mR3, rx, ax);
         ay = __fmaf_rn(-mR3, ry, ay);
         az = __fmaf_rn(-mR3, rz, az);
-        ph += mR;
+        ph = __fmaf_rn(a.w, Ri, ph);
     }
 }
 
-template <bool QUAD>
-__device__ __forceinline__ void pc_loop(const GravSmem &S, int buf, int nc, int split, int js, float xi, float yi,
-                                        float zi, float e2i, float &ax, float &ay, float &az, float &ph)
+template <int NI, bool QUAD>
+__device__ __forceinline__ void pc_loopN(const GravSmem &S, int buf, int nc, int split, int js, const float4 (&pi)[NI],
+                                         float4 (&acc)[NI])
 {
-#pragma unroll 2
-    for (int c = split; c < nc; c += js)
-        pc_one<QUAD>(S.c0[buf][c], S.c1[buf][c], S.c2[buf][c], xi, yi, zi, e2i, ax, ay, az, ph);
-}
-
-template <bool QUAD>
-__device__ __forceinline__ void pc_loop2(const GravSmem &S, int buf, int nc, int split, int js, const float4 &i0,
-                                         const float4 &i1, float4 &a0, float4 &a1)
-{
-#pragma unroll 2
+    constexpr int UNR = NI >= 2 ? 1 : 2;
+#pragma unroll UNR
     for (int c = split; c < nc; c += js) {
         const float4 a = S.c0[buf][c], b = S.c1[buf][c], d = S.c2[buf][c];
-        pc_one<QUAD>(a, b, d, i0.x, i0.y, i0.z, i0.w, a0.x, a0.y, a0.z, a0.w);
-        pc_one<QUAD>(a, b, d, i1.x, i1.y, i1.z, i1.w, a1.x, a1.y, a1.z, a1.w);
+#pragma unroll
+        for (int k = 0; k < NI; k++)
+            pc_one<QUAD>(a, b, d, pi[k].x, pi[k].y, pi[k].z, pi[k].w, acc[k].x, acc[k].y, acc[k].z, acc[k].w);
     }
 }
 
@@ -438,9 +450,147 @@ __global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
     }
 }
 
-// Evaluation of the walk's lists, one group per CTA (see the file comment).
+// One chunk of up to GW_NI_MAX * GW_THREADS i-particles of a group against
+// the group's lists, NI i-particles per thread.  j-splits: each of the js
+// thread sets holds all icnt i-particles (slot s and s + k ilanes, k < NI)
+// and takes every js-th j entry, so a small group keeps the CTA busy; with
+// more i-particles per thread each staged j entry is read once for all of
+// them and fewer partial sums are left to reduce.
+template <int NI, bool MASK, bool QUAD>
+__device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int first, int icnt, const int4 &gh,
+                                           const int *gref, float unit)
+{
+    const int tid = threadIdx.x;
+    const int ilanes = (icnt + NI - 1) / NI;
+    const int js = GW_THREADS / ilanes;
+    const int islot = tid % ilanes, split = tid / ilanes;
+    const bool ivalid = split < js;
+    float4 pi[NI], acc[NI];
+#pragma unroll
+    for (int k = 0; k < NI; k++) {
+        const int sl = islot + k * ilanes;
+        const int ip = first + (sl < icnt ? sl : islot);  // an empty slot repeats the first particle
+        const float ep = p.eps[ip];
+        pi[k] = make_float4(grid_off(p.cx[ip], gref[0], p.rx[ip], unit), grid_off(p.cy[ip], gref[1], p.ry[ip], unit),
+                            grid_off(p.cz[ip], gref[2], p.rz[ip], unit), ep * ep);
+        acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // accepted cells, one chunk at a time, double buffered: while a chunk is
+    // evaluated, cp.async fills the other buffer with the next chunk (whose
+    // node indices were loaded one chunk earlier).  The first chunk's copy is
+    // issued here and lands while the opened leaves below are evaluated.
+    int ch = gh.x, cb = 0;
+    int idx[2] = {0, 0}, cnx = -1;
+    if (ch >= 0) {
+        idx[0] = p.pool[(size_t)ch * GL_CH + tid];
+        idx[1] = p.pool[(size_t)ch * GL_CH + tid + GW_THREADS];
+        cells_issue(S, p, 0, idx);
+        cnx = p.cnext[ch];
+        if (cnx >= 0) {
+            idx[0] = p.pool[(size_t)cnx * GL_CH + tid];
+            idx[1] = p.pool[(size_t)cnx * GL_CH + tid + GW_THREADS];
+        }
+    }
+    // opened leaves, one chunk at a time: each entry holds the leaf's first
+    // particle and its offset in the group's leaf particles (from the walk),
+    // so particles are staged in batches of GW_JP without a scan or a node
+    // lookup
+    for (int lch = gh.y; lch >= 0;) {
+        const int nl = p.ccnt[lch];
+        const int lnx = p.cnext[lch];
+        // only a chain's head chunk can be empty (a group with no opened leaf)
+        const int base = nl > 0 ? p.lcum[(size_t)lch * GL_CH] : 0;
+        const int end = lnx >= 0 ? p.lcum[(size_t)lnx * GL_CH] : gh.z;
+        const int total = nl > 0 ? end - base : 0;
+        for (int q = tid; q < nl; q += GW_THREADS) {
+            S.leaf[q] = p.pool[(size_t)lch * GL_CH + q];
+            S.leafoff[q] = p.lcum[(size_t)lch * GL_CH + q] - base;
+        }
+        if (tid == 0) S.leafoff[nl] = total;
+        __syncthreads();
+        for (int c0 = 0; c0 < total; c0 += GW_JP) {
+            const int np = min(GW_JP, total - c0);
+            for (int k = tid; k < np; k += GW_THREADS) {
+                const int pos = c0 + k;
+                int lo = 0, hi = nl - 1;  // the leaf holding position pos
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (S.leafoff[mid] <= pos) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int j = S.leaf[lo] + (pos - S.leafoff[lo]);
+                const float ej = p.eps[j];
+                S.jp[k] = make_float4(grid_off(p.cx[j], gref[0], p.rx[j], unit),
+                                      grid_off(p.cy[j], gref[1], p.ry[j], unit),
+                                      grid_off(p.cz[j], gref[2], p.rz[j], unit), p.m[j]);
+                S.je[k] = ej * ej;
+            }
+            __syncthreads();
+            if (ivalid) pp_loopN<NI, MASK>(S, np, split, js, pi, acc);
+            __syncthreads();
+        }
+        lch = lnx;
+    }
+    if (ch >= 0) {
+        cp_async_wait_all_g();
+        cells_convert(S, 0, gref, unit);
+        __syncthreads();
+    }
+    while (ch >= 0) {
+        const int nc = p.ccnt[ch];
+        int nxt2 = -1, idx2[2] = {0, 0};
+        if (cnx >= 0) {
+            cells_issue(S, p, cb ^ 1, idx);
+            nxt2 = p.cnext[cnx];
+            if (nxt2 >= 0) {
+                idx2[0] = p.pool[(size_t)nxt2 * GL_CH + tid];
+                idx2[1] = p.pool[(size_t)nxt2 * GL_CH + tid + GW_THREADS];
+            }
+        }
+        if (ivalid) pc_loopN<NI, QUAD>(S, cb, nc, split, js, pi, acc);
+        if (cnx >= 0) {
+            cp_async_wait_all_g();
+            cells_convert(S, cb ^ 1, gref, unit);
+        }
+        __syncthreads();  // buffer cb evaluated by all; buffer cb ^ 1 converted by all
+        ch = cnx;
+        cnx = nxt2;
+        idx[0] = idx2[0];
+        idx[1] = idx2[1];
+        cb ^= 1;
+    }
+    // reduce the j-splits: the partial sums of particle slot k go through the
+    // PP staging buffer (idle here), NI x GW_THREADS float4
+    static_assert(GW_NI_MAX * GW_THREADS <= GW_JP, "reduction buffer");
+#pragma unroll
+    for (int k = 0; k < NI; k++) S.jp[k * GW_THREADS + tid] = acc[k];
+    __syncthreads();
+    if (split == 0 && ivalid) {
+#pragma unroll
+        for (int k = 0; k < NI; k++) {
+            const int sl = islot + k * ilanes;
+            if (sl >= icnt) continue;
+            float4 a = acc[k];
+            for (int s2 = 1; s2 < js; s2++) {
+                const float4 r = S.jp[k * GW_THREADS + tid + s2 * ilanes];
+                a.x += r.x; a.y += r.y; a.z += r.z; a.w += r.w;
+            }
+            const int ip = first + sl;
+            if (!MASK) a.w -= p.m[ip] * rsqrtf(2.f * pi[k].w);  // remove the j == i term
+            p.ax[ip] = p.G * a.x;
+            p.ay[ip] = p.G * a.y;
+            p.az[ip] = p.G * a.z;
+            p.pot[ip] = -p.G * a.w;
+        }
+    }
+    __syncthreads();
+}
+
+// Evaluation of the walk's lists, one group per CTA (see the file comment):
+// the group's particles in chunks of up to GW_NI_MAX * GW_THREADS, four per
+// thread above 64 particles in a chunk, two above 16, else one.
 template <bool MASK, bool QUAD>
-__global__ void __launch_bounds__(GW_THREADS, 5) k_grav_eval(GravParams p)
+__global__ void __launch_bounds__(GW_THREADS, GW_EVAL_CTAS) k_grav_eval(GravParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GravSmem &S = *reinterpret_cast<GravSmem *>(smem_raw);
@@ -457,153 +607,11 @@ __global__ void __launch_bounds__(GW_THREADS, 5) k_grav_eval(GravParams p)
         const int4 gh = p.ghead[gi];
         const int4 gr = p.gref[gi];
         const int gref[3] = {gr.x, gr.y, gr.z};
-        // up to two i-particles per thread: a group of up to 2 GW_THREADS
-        // particles streams its lists once
-        for (int i0 = 0; i0 < gcount; i0 += 2 * GW_THREADS) {
-            const int icnt = min(2 * GW_THREADS, gcount - i0);
-            // j-splits: each of the js thread sets holds all icnt i-particles
-            // and takes every js-th j entry.  Above 16 i-particles a thread
-            // holds two (slot s and s + ilanes), which halves the threads a
-            // set needs, so more sets fit in the CTA and each staged j entry
-            // is read once for both.
-            const bool two = icnt > 16;
-            const int ilanes = two ? (icnt + 1) >> 1 : icnt;
-            const int js = GW_THREADS / ilanes;
-            const int islot = tid % ilanes, split = tid / ilanes;
-            const bool ivalid = split < js;
-            const int ip = gfirst + i0 + islot;
-            const bool has2 = two && islot + ilanes < icnt;
-            const int ip2 = has2 ? ip + ilanes : ip;  // a duplicate of ip when there is no second particle
-            const float xi = grid_off(p.cx[ip], gref[0], p.rx[ip], unit);
-            const float yi = grid_off(p.cy[ip], gref[1], p.ry[ip], unit);
-            const float zi = grid_off(p.cz[ip], gref[2], p.rz[ip], unit);
-            const float epi = p.eps[ip];
-            const float e2i = epi * epi;
-            const float ep2 = p.eps[ip2];
-            const float4 pi0 = make_float4(xi, yi, zi, e2i);
-            const float4 pi1 = make_float4(grid_off(p.cx[ip2], gref[0], p.rx[ip2], unit),
-                                           grid_off(p.cy[ip2], gref[1], p.ry[ip2], unit),
-                                           grid_off(p.cz[ip2], gref[2], p.rz[ip2], unit), ep2 * ep2);
-            float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
-            // accepted cells, one chunk at a time, double buffered: while a
-            // chunk is evaluated, cp.async fills the other buffer with the
-            // next chunk (whose node indices were loaded one chunk earlier).
-            // The first chunk's copy is issued here and lands while the
-            // opened leaves below are evaluated.
-            int ch = gh.x, cb = 0;
-            int idx[2] = {0, 0}, cnx = -1;
-            if (ch >= 0) {
-                idx[0] = p.pool[(size_t)ch * GL_CH + tid];
-                idx[1] = p.pool[(size_t)ch * GL_CH + tid + GW_THREADS];
-                cells_issue(S, p, 0, idx);
-                cnx = p.cnext[ch];
-                if (cnx >= 0) {
-                    idx[0] = p.pool[(size_t)cnx * GL_CH + tid];
-                    idx[1] = p.pool[(size_t)cnx * GL_CH + tid + GW_THREADS];
-                }
-            }
-            // opened leaves, one chunk at a time: each entry holds the leaf's
-            // first particle and its offset in the group's leaf particles (from
-            // the walk), so particles are staged in batches of GW_JP without a
-            // scan or a node lookup
-            for (int lch = gh.y; lch >= 0;) {
-                const int nl = p.ccnt[lch];
-                const int lnx = p.cnext[lch];
-                // only a chain's head chunk can be empty (a group with no opened leaf)
-                const int base = nl > 0 ? p.lcum[(size_t)lch * GL_CH] : 0;
-                const int end = lnx >= 0 ? p.lcum[(size_t)lnx * GL_CH] : gh.z;
-                const int total = nl > 0 ? end - base : 0;
-                for (int q = tid; q < nl; q += GW_THREADS) {
-                    S.leaf[q] = p.pool[(size_t)lch * GL_CH + q];
-                    S.leafoff[q] = p.lcum[(size_t)lch * GL_CH + q] - base;
-                }
-                if (tid == 0) S.leafoff[nl] = total;
-                __syncthreads();
-                for (int c0 = 0; c0 < total; c0 += GW_JP) {
-                    const int np = min(GW_JP, total - c0);
-                    for (int k = tid; k < np; k += GW_THREADS) {
-                        const int pos = c0 + k;
-                        int lo = 0, hi = nl - 1;  // the leaf holding position pos
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (S.leafoff[mid] <= pos) lo = mid;
-                            else hi = mid - 1;
-                        }
-                        const int j = S.leaf[lo] + (pos - S.leafoff[lo]);
-                        const float ej = p.eps[j];
-                        S.jp[k] = make_float4(grid_off(p.cx[j], gref[0], p.rx[j], unit),
-                                              grid_off(p.cy[j], gref[1], p.ry[j], unit),
-                                              grid_off(p.cz[j], gref[2], p.rz[j], unit), p.m[j]);
-                        S.je[k] = ej * ej;
-                    }
-                    __syncthreads();
-                    if (ivalid) {
-                        if (two) pp_loop2<MASK>(S, np, split, js, pi0, pi1, acc0, acc1);
-                        else pp_loop<MASK>(S, np, split, js, xi, yi, zi, e2i, acc0.x, acc0.y, acc0.z, acc0.w);
-                    }
-                    __syncthreads();
-                }
-                lch = lnx;
-            }
-            if (ch >= 0) {
-                cp_async_wait_all_g();
-                cells_convert(S, 0, gref, unit);
-                __syncthreads();
-            }
-            while (ch >= 0) {
-                const int nc = p.ccnt[ch];
-                int nxt2 = -1, idx2[2] = {0, 0};
-                if (cnx >= 0) {
-                    cells_issue(S, p, cb ^ 1, idx);
-                    nxt2 = p.cnext[cnx];
-                    if (nxt2 >= 0) {
-                        idx2[0] = p.pool[(size_t)nxt2 * GL_CH + tid];
-                        idx2[1] = p.pool[(size_t)nxt2 * GL_CH + tid + GW_THREADS];
-                    }
-                }
-                if (ivalid) {
-                    if (two) pc_loop2<QUAD>(S, cb, nc, split, js, pi0, pi1, acc0, acc1);
-                    else pc_loop<QUAD>(S, cb, nc, split, js, xi, yi, zi, e2i, acc0.x, acc0.y, acc0.z, acc0.w);
-                }
-                if (cnx >= 0) {
-                    cp_async_wait_all_g();
-                    cells_convert(S, cb ^ 1, gref, unit);
-                }
-                __syncthreads();  // buffer cb evaluated by all; buffer cb ^ 1 converted by all
-                ch = cnx;
-                cnx = nxt2;
-                idx[0] = idx2[0];
-                idx[1] = idx2[1];
-                cb ^= 1;
-            }
-            // reduce j-splits (the second particles' partial sums go through
-            // the PP staging buffer, idle here)
-            S.red[tid] = acc0;
-            if (two) S.jp[tid] = acc1;
-            __syncthreads();
-            if (split == 0 && ivalid) {
-                for (int s2 = 1; s2 < js; s2++) {
-                    const float4 r = S.red[tid + s2 * ilanes];
-                    acc0.x += r.x; acc0.y += r.y; acc0.z += r.z; acc0.w += r.w;
-                }
-                if (!MASK) acc0.w -= p.m[ip] * rsqrtf(2.f * e2i);  // remove the j == i term
-                p.ax[ip] = p.G * acc0.x;
-                p.ay[ip] = p.G * acc0.y;
-                p.az[ip] = p.G * acc0.z;
-                p.pot[ip] = -p.G * acc0.w;
-                if (has2) {
-                    for (int s2 = 1; s2 < js; s2++) {
-                        const float4 r = S.jp[tid + s2 * ilanes];
-                        acc1.x += r.x; acc1.y += r.y; acc1.z += r.z; acc1.w += r.w;
-                    }
-                    if (!MASK) acc1.w -= p.m[ip2] * rsqrtf(2.f * pi1.w);
-                    p.ax[ip2] = p.G * acc1.x;
-                    p.ay[ip2] = p.G * acc1.y;
-                    p.az[ip2] = p.G * acc1.z;
-                    p.pot[ip2] = -p.G * acc1.w;
-                }
-            }
-            __syncthreads();
+        for (int i0 = 0; i0 < gcount; i0 += GW_NI_MAX * GW_THREADS) {
+            const int icnt = min(GW_NI_MAX * GW_THREADS, gcount - i0);
+            if (icnt > 64) eval_chunk<4, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
+            else if (icnt > 16) eval_chunk<2, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
+            else eval_chunk<1, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
         }
     }
 }
@@ -814,6 +822,22 @@ int gravity_direct(gnb_ctx *c)
 // ---------------------------------------------------------------- NFW halo
 // M(<r) = Ms [ln(1+r/rs) - (r/rs)/(1+r/rs)], a = -G M(<r) x / r^3,
 // Phi = -G Ms ln(1 + r/rs) / r.
+//
+// The bracket cancels for small s = r/rs (both terms ~ s, the difference
+// ~ s^2/2), which in FP32 would cost ~ 2^-24 / s of relative accuracy.  With
+// t = s/(1+s), ln(1+s) = -ln(1-t) = sum_k t^k/k, so the bracket is
+// sum_{k>=2} t^k / k, a series of positive terms; below s = 1/4 (t = 1/5)
+// its first 11 terms leave a relative truncation error below 2e-8, and above
+// it the direct form loses at most a factor 10 (< 1e-6).
+__device__ __forceinline__ float nfw_bracket(float s)
+{
+    if (s >= 0.25f) return log1pf(s) - s / (1.f + s);
+    const float t = s / (1.f + s);
+    float sum = 1.f / 12.f;  // Horner in t over 1/2 + t/3 + ... + t^10/12
+    for (int k = 11; k >= 2; k--) sum = __fmaf_rn(sum, t, 1.f / (float)k);
+    return t * t * sum;
+}
+
 __global__ void k_nfw(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                       int n, float G, float ms, float rs, float *__restrict__ ax, float *__restrict__ ay,
                       float *__restrict__ az, float *__restrict__ pext)
@@ -824,7 +848,7 @@ __global__ void k_nfw(const double *__restrict__ x, const double *__restrict__ y
     float r = sqrtf(px * px + py * py + pz * pz);
     float s = r / rs;
     float l1 = log1pf(s);
-    float menc = ms * (l1 - s / (1.f + s));
+    float menc = ms * nfw_bracket(s);
     float f = r > 0.f ? -G * menc / (r * r * r) : 0.f;
     ax[i] = f * px;
     ay[i] = f * py;
