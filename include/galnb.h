@@ -341,6 +341,19 @@ int gnb_unet_get_grads(gnb_unet *net, float *dst, int on_device);
  * of `centers`).  Errors: GNB_EINVAL (batch < 1 or above the batch of the
  * largest pass so far, NULL), GNB_ECUDA. */
 int gnb_unet_get_output(gnb_unet *net, int batch, float *dst, int on_device);
+/* A tensor the last forward pass stored, as FP32 [batch][g^3][C] (g the
+ * grid of its level, C its channels), first `batch` samples.  Slots in the
+ * order the forward pass writes them: 0 the BF16 network input (cin
+ * channels), then for each level l = 0 .. levels-1 the outputs of enc l a
+ * and enc l b and, below the coarsest level, the max-pooled tensor (level
+ * l+1 grid); then for each decoder level l = levels-2 .. 0 the outputs of
+ * up l (the transposed convolution), dec l a and dec l b.  Read them after
+ * gnb_unet_forward: a training step reuses the dec l a buffers for
+ * gradients.  With the gradients of gnb_unet_get_grads this lets
+ * back-propagation be checked layer by layer on the activations the network
+ * actually stored.  Errors: GNB_EINVAL (slot
+ * out of range, batch, NULL), GNB_ENOMEM, GNB_ECUDA. */
+int gnb_unet_get_activation(gnb_unet *net, int slot, int batch, float *dst, int on_device);
 /* Convolution kernels of the 3^3 layers.  GNB_CONV_AUTO (the default): the
  * tcgen05 tensor-core kernel (TMA halo tiles, TMEM accumulators) wherever the
  * channel counts are multiples of 16 and its weights fit in shared memory,

@@ -157,6 +157,51 @@ def forward(p, x, levels=4, bf=False):
     return y, cache
 
 
+def stored_slots(cin=5, base=16, levels=4, grid=16):
+    """(name, grid, channels) of the tensors a forward pass stores, in the
+    order: input; per level enc a, enc b (and the pooled tensor below the
+    coarsest level); per decoder level, coarse to fine, up, dec a, dec b."""
+    out = [("x", grid, cin)]
+    for l in range(levels):
+        w, g = base << l, grid >> l
+        out += [(f"enc{l}a.out", g, w), (f"enc{l}b.out", g, w)]
+        if l < levels - 1:
+            out.append((f"pool{l}.out", g // 2, w))
+    for l in range(levels - 2, -1, -1):
+        w, g = base << l, grid >> l
+        out += [(f"up{l}.out", g, w), (f"dec{l}a.out", g, w), (f"dec{l}b.out", g, w)]
+    return out
+
+
+def cache_at(p, acts, levels=4, bf=True):
+    """The backward pass's cache for given stored forward tensors ``acts``
+    (name -> array, names as in ``stored_slots``): the same cache ``forward``
+    builds, with the max-pool routing (first maximum) recomputed from the
+    stored enc b outputs.  Evaluating ``backward`` on it checks
+    back-propagation layer by layer at that forward state."""
+    R = bf16 if bf else (lambda a: a)
+    q = {k: (R(v) if k.endswith(".w") else v) for k, v in p.items()}
+    cache = {"q": q, "x": acts["x"]}
+    h = acts["x"]
+    for l in range(levels):
+        cache[f"enc{l}a.in"], cache[f"enc{l}a.out"] = h, acts[f"enc{l}a.out"]
+        cache[f"enc{l}b.in"], cache[f"enc{l}b.out"] = acts[f"enc{l}a.out"], acts[f"enc{l}b.out"]
+        if l < levels - 1:
+            _, idx = maxpool2(acts[f"enc{l}b.out"])
+            cache[f"pool{l}.idx"], cache[f"pool{l}.shape"] = idx, acts[f"enc{l}b.out"].shape
+            h = acts[f"pool{l}.out"]
+        else:
+            h = acts[f"enc{l}b.out"]
+    for l in range(levels - 2, -1, -1):
+        cache[f"up{l}.in"] = h
+        cat = np.concatenate([acts[f"enc{l}b.out"], acts[f"up{l}.out"]], axis=-1)
+        cache[f"dec{l}a.in"], cache[f"dec{l}a.out"] = cat, acts[f"dec{l}a.out"]
+        cache[f"dec{l}b.in"], cache[f"dec{l}b.out"] = acts[f"dec{l}a.out"], acts[f"dec{l}b.out"]
+        h = acts[f"dec{l}b.out"]
+    cache["head.in"] = h
+    return cache
+
+
 def mse(y, target):
     d = y - target
     return float(np.mean(d * d)), 2.0 * d / d.size

@@ -441,6 +441,16 @@ __global__ void k_maxpool_bwd(const bf16 *__restrict__ dout, const unsigned char
     din[e] = __float2bfloat16_rn(g);
 }
 
+// Blocked BF16 [B][C/8][V][8] -> FP32 [B][V][keep] (the first `keep` channels).
+__global__ void k_unblock(const bf16 *__restrict__ in, int B, int C, long long V, int keep, float *__restrict__ out)
+{
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)B * V * keep) return;
+    int c = (int)(e % keep);
+    long long bv = e / keep, b = bv / V, v = bv - b * V;
+    out[e] = __bfloat162float(in[((b * (C >> 3) + (c >> 3)) * V + v) * 8 + (c & 7)]);
+}
+
 __global__ void k_relu_mask(const bf16 *__restrict__ dy, const bf16 *__restrict__ y, bf16 *__restrict__ dz, long long n)
 {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -490,17 +500,23 @@ __global__ void k_colsum(const bf16 *__restrict__ g, long long V, long long Vs, 
     if (c < N) atomicAdd(&db[c], s);
 }
 
+// Adam (Kingma and Ba): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+// p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).  The constants
+// 1 - b1, 1 - b2 and the bias corrections 1 / (1 - b^t) come from the host in
+// FP64, rounded once: formed in FP32, 1 - 0.999f and 1 - 0.999^t lose five
+// significant digits to cancellation.
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
-                       float *__restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1, float c2)
+                       float *__restrict__ v, long long n, float lr, float b1, float ob1, float b2, float ob2,
+                       float eps, float ic1, float ic2)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float gi = g[i];
-    float mi = b1 * m[i] + (1.f - b1) * gi;
-    float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    float mi = __fmaf_rn(b1, m[i], ob1 * gi);
+    float vi = __fmaf_rn(b2, v[i], ob2 * (gi * gi));
     m[i] = mi;
     v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] -= lr * (mi * ic1) / (sqrtf(vi * ic2) + eps);
 }
 
 // master [taps][cin][cout] FP32 -> forward BF16 [taps][Npad][Kpad] (transposed, zero padded)
@@ -1074,6 +1090,56 @@ int gnb_unet_get_grads(gnb_unet *u, float *dst, int on_device)
     return unet_check(u, GNB_OK);
 }
 
+int gnb_unet_get_activation(gnb_unet *u, int slot, int batch, float *dst, int on_device)
+{
+    if (!u || !dst || batch < 1 || batch > u->bcap || slot < 0) return GNB_EINVAL;
+    // slot order: the input, then per level enc a, enc b (and the pooled
+    // tensor below the coarsest level), then per decoder level (coarse to
+    // fine) up, dec a, dec b
+    const bf16 *src = nullptr;
+    int C = 0, keep = 0, lev = 0;
+    int k = slot;
+    if (k == 0) {
+        src = u->xin; C = 16; keep = u->cin; lev = 0;
+    } else {
+        k -= 1;
+        for (int l = 0; l < u->levels && !src; l++) {
+            const int w = width(u, l);
+            const int nl = l + 1 < u->levels ? 3 : 2;
+            if (k < nl) {
+                src = u->act[k == 0 ? S_ENCA(l) : k == 1 ? S_ENCB(l) : S_POOL(l)];
+                C = keep = w;
+                lev = k == 2 ? l + 1 : l;
+            }
+            k -= nl;
+        }
+        for (int l = u->levels - 2; l >= 0 && !src; l--) {
+            if (k < 3) {
+                src = u->act[k == 0 ? S_UP(u, l) : k == 1 ? S_DECA(u, l) : S_DECB(u, l)];
+                C = keep = width(u, l);
+                lev = l;
+            }
+            k -= 3;
+        }
+    }
+    if (!src) return GNB_EINVAL;
+    const long long V = vox(u, lev, 1);
+    const long long n = (long long)batch * V * keep;
+    float *out = dst, *tmp = nullptr;
+    if (!on_device) {
+        if (cudaMalloc((void **)&tmp, n * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return GNB_ENOMEM;
+        }
+        out = tmp;
+    }
+    counted(k_unblock)<<<(unsigned)((n + 255) / 256), 256, 0, u->s>>>(src, batch, C, V, keep, out);
+    if (!on_device) cudaMemcpyAsync(dst, tmp, n * 4, cudaMemcpyDeviceToHost, u->s);
+    int rc = unet_check(u, GNB_OK);
+    if (tmp) cudaFree(tmp);
+    return rc;
+}
+
 int gnb_unet_get_output(gnb_unet *u, int batch, float *dst, int on_device)
 {
     if (!u || !dst || batch < 1 || batch > u->bcap || !u->yout) return GNB_EINVAL;
@@ -1140,10 +1206,12 @@ int gnb_unet_train_step(gnb_unet *u, int batch, const float *x, const float *tar
     if (rc == GNB_OK) rc = unet_backward(u, batch);
     if (rc == GNB_OK && lr > 0.0) {
         u->adam_t++;
-        float b1 = 0.9f, b2 = 0.999f;
-        float c1 = 1.f - powf(b1, (float)u->adam_t), c2 = 1.f - powf(b2, (float)u->adam_t);
-        counted(k_adam)<<<(unsigned)((u->nparam + 255) / 256), 256, 0, u->s>>>(u->p, u->g, u->m, u->v, u->nparam,
-                                                                             (float)lr, b1, b2, 1e-8f, c1, c2);
+        const double b1 = 0.9, b2 = 0.999;
+        const double ic1 = 1.0 / (1.0 - std::pow(b1, (double)u->adam_t));
+        const double ic2 = 1.0 / (1.0 - std::pow(b2, (double)u->adam_t));
+        counted(k_adam)<<<(unsigned)((u->nparam + 255) / 256), 256, 0, u->s>>>(
+            u->p, u->g, u->m, u->v, u->nparam, (float)lr, (float)b1, (float)(1.0 - b1), (float)b2, (float)(1.0 - b2),
+            1e-8f, (float)ic1, (float)ic2);
         rc = unet_pack(u);
     }
     double l = 0.0;

@@ -137,6 +137,8 @@ def _declare(L):
         getattr(L, name).restype = C.c_int
     L.gnb_unet_get_output.argtypes = [_vp, C.c_int, _vp, C.c_int]
     L.gnb_unet_get_output.restype = C.c_int
+    L.gnb_unet_get_activation.argtypes = [_vp, C.c_int, C.c_int, _vp, C.c_int]
+    L.gnb_unet_get_activation.restype = C.c_int
     L.gnb_unet_set_conv_impl.argtypes = [_vp, C.c_int]
     L.gnb_unet_set_conv_impl.restype = C.c_int
     L.gnb_unet_test_wait_timeout.argtypes = [_vp]
@@ -286,6 +288,10 @@ def gnb_unet_get_output(net, batch, dst, on_device):
     return lib().gnb_unet_get_output(net, batch, dst, on_device)
 
 
+def gnb_unet_get_activation(net, slot, batch, dst, on_device):
+    return lib().gnb_unet_get_activation(net, slot, batch, dst, on_device)
+
+
 def gnb_unet_forward(net, batch, x, y, on_device):
     return lib().gnb_unet_forward(net, batch, x, y, on_device)
 
@@ -342,6 +348,13 @@ class UNet:
         g = self.grid
         out = np.empty((batch, g, g, g, self.cout), np.float32)
         self._chk(gnb_unet_get_output(self.h, batch, out.ctypes.data, 0), "get_output")
+        return out
+
+    def get_activation(self, slot, batch, grid, channels):
+        """Stored tensor `slot` of the last forward pass as FP32
+        [batch, grid, grid, grid, channels] (see gnb_unet_get_activation)."""
+        out = np.empty((batch, grid, grid, grid, channels), np.float32)
+        self._chk(gnb_unet_get_activation(self.h, slot, batch, out.ctypes.data, 0), "get_activation")
         return out
 
     def set_params(self, flat):

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import unet
+from oracle import unet as U
 
 
 def test_conv_delta_returns_mirrored_kernel():
@@ -83,3 +84,32 @@ def test_adam_first_step_closed_form():
     q = unet.adam_step(p, g, st, lr=0.1)
     # after one step m_hat = g, v_hat = g^2: the update is lr * sign(g) (up to eps)
     assert np.allclose(q["w"], p["w"] - 0.1 * np.sign(g["w"]), atol=1e-7)
+
+
+def test_cache_at_own_activations_reproduces_backward():
+    """The cache rebuilt from a forward pass's own stored tensors gives the
+    same gradients as the forward pass's cache (bit for bit)."""
+    rng = np.random.default_rng(4)
+    levels, grid = 3, 8
+    p = U.init_params(2, 5, 5, 8, levels)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = rng.normal(0, 0.1, p[k].shape)
+    x = U.bf16(rng.normal(size=(2, grid, grid, grid, 5)))
+    y, cache = U.forward(p, x, levels=levels, bf=True)
+    _, dy = U.mse(y, rng.normal(size=y.shape))
+    acts = {"x": cache["x"]}
+    for name, g, c in U.stored_slots(5, 8, levels, grid)[1:]:
+        if name.startswith("pool"):
+            l = int(name[4])
+            acts[name] = U.maxpool2(cache[f"enc{l}b.out"])[0]
+        elif name.startswith("up"):
+            l = int(name[2])
+            acts[name] = cache[f"dec{l}a.in"][..., cache[f"enc{l}b.out"].shape[-1]:]
+        else:
+            acts[name] = cache[name]
+        assert acts[name].shape[1:] == (g, g, g, c)
+    g0 = U.backward(p, cache, dy, levels=levels, bf=True)
+    g1 = U.backward(p, U.cache_at(p, acts, levels=levels, bf=True), dy, levels=levels, bf=True)
+    for k in g0:
+        assert np.array_equal(g0[k], g1[k]), k
