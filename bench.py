@@ -19,9 +19,11 @@ The same JSON line carries the supernova half of the metric under "sn"
 (rank 0, one GPU): SN regions per second of the surrogate path (256 ragged
 regions of 2e4 - 3e5 gas particles, log-uniform, voxelised to 64^3, BF16 U-Net
 forward, Gibbs remap, one CUDA-graph replay per batch) against the plain
-CFL-limited integration of a 1e5-particle region over 0.1 Myr on the same GPU,
-with the surrogate's field error from the committed training report and the
-U-Net forward's tensor throughput against the measured BF16 peak.
+CFL-limited integration of 1e5-particle regions over 0.1 Myr on the same GPU
+(one region alone, 32 regions in one context, and with hierarchical
+individual timesteps), with the trained network's field error on held-out
+seeds computed in the same run and the U-Net forward's tensor throughput
+against the measured BF16 peak.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sn]
 
@@ -60,7 +62,6 @@ FLOP_PC = 59
 # U-Net forward per 64^3 region: 3^3 convolutions, transposed convolutions
 # and the head with the network's own 5 input channels (algorithmic count)
 UNET_GFLOP_64 = 29.0497
-SN_REPORT = os.path.join(ROOT, "profiles", "surrogate_sn_region_1e5_grid64.txt")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Algorithmic bytes per unit of the HBM-bound phases:
 #  tree build, per particle: positions read 24 + key write 8 + 4 radix passes
@@ -221,15 +222,6 @@ def cpu_baseline(p, name, knn_seconds=6.0, n_g=64):
             "seconds_per_step_estimate": total}
 
 
-def read_kv(path):
-    try:
-        text = open(path).read()
-    except OSError:
-        return {}
-    return {k.strip(): v.strip() for k, v in (line.split(":", 1) for line in text.splitlines()
-                                                if ":" in line and not line.startswith("#"))}
-
-
 def sn_regions(nreg, distinct, lo, hi, seed):
     """nreg supernova regions with gas counts log-uniform in [lo, hi], built
     from `distinct` generated regions, each placed nreg / distinct times on a
@@ -261,7 +253,10 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True):
     from paper_2510_23330_gb300 import surrogate as S
     sp = stream.cuda_stream
     net = galnb.UNet(5, 5, 16, 4, 64, stream=sp)
-    net.set_params(S.he_init(seed=0))
+    trained = os.path.exists(S.WEIGHTS)
+    meta = S.load_weights(net, S.WEIGHTS) if trained else {}
+    if not trained:
+        net.set_params(S.he_init(seed=0))
     # --- surrogate: one graph replay per batch of nreg ragged regions
     p, centers, counts = sn_regions(nreg, 16, 20000, 300000, seed=7)
     ctx = galnb.Context(stream=sp)
@@ -300,13 +295,29 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True):
     torch.cuda.synchronize()
     fwd_ms = e0.elapsed_time(e1) / 3
     del xb, yb
-    net.close()
-    # --- plain: CFL-limited integration of a 1e5-particle region over 0.1 Myr
-    plain, ys = [], {}
+    # --- plain: CFL-limited integration of a 1e5-particle region over 0.1 Myr,
+    # one region at a time (held-out seeds 1900, 1901; also pairs for the
+    # field error), and many regions in one context (the GPU full)
+    plain, pairs = [], []
     for seed in ((1900, 1901) if plain_runs else ()):
-        _, ys[seed], info = S.make_pair(seed, n=100000, grid=64, stream=sp)
+        x, y, info = S.make_pair(seed, n=100000, grid=64, stream=sp)
         plain.append(info)
+        pairs.append((x, y))
     plain_s = float(np.median([i["seconds"] for i in plain])) if plain else float("nan")
+    field = None
+    if plain_runs:
+        Xh, Yh, _ = S.make_pairs(list(range(1902, 1910)), n=100000, grid=64, workers=4)
+        X = np.concatenate([np.stack([q[0] for q in pairs]).reshape((-1,) + Xh.shape[1:]), Xh.astype(np.float32)])
+        Y = np.concatenate([np.stack([q[1] for q in pairs]).reshape((-1,) + Yh.shape[1:]), Yh.astype(np.float32)])
+        ev = S.evaluate_arrays(net, X, Y)
+        field = {"rmse_surrogate": ev["rmse_surrogate_all"], "rmse_no_feedback": ev["rmse_identity_all"],
+                 "rmse_surrogate_per_channel": ev["rmse_surrogate"], "held_out_seeds": [1900, 1909],
+                 "trained": trained, "weights": os.path.relpath(S.WEIGHTS, ROOT) if trained else None,
+                 "train_seeds": meta.get("train_seeds"), "epochs": meta.get("epochs"),
+                 "units": "standardised channels, mean over 5 channels and 10 held-out seeds, computed in this run "
+                          "with the network timed above"}
+    batched = plain_batched(galnb, torch, stream, steps_single=float(np.median([i["steps"] for i in plain]))
+                            if plain else 175.0) if plain_runs else None
     # --- plain with hierarchical individual timesteps, same region as the first run
     hier = None
     if plain_runs:
@@ -314,40 +325,81 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True):
         hier = {"seconds_per_region": hi["seconds"], "regions_per_s": 1.0 / hi["seconds"],
                 "block_steps": hi["steps"], "particle_updates": hi["updates"], "wakeups": hi["wakeups"],
                 "updates_vs_shared": hi["updates"] / plain[0]["updates"],
-                "rmse_vs_shared": float(np.mean(S.rmse(yh, ys[1900]))), "max_level": 20,
+                "rmse_vs_shared": float(np.mean(S.rmse(yh, pairs[0][1]))), "max_level": 20,
                 "note": "all particles drifted, predicted and evaluated at every block step; the particles whose "
                         "step ends (or whose CFL level became finer) are kicked"}
+    net.close()
     sur_ms = float(np.median(ms))
-    kv = read_kv(SN_REPORT)
     try:
         peaks = json.load(open(PEAKS))
         peak, peak_note = float(peaks["bf16_tflops"]), "of measured (cuBLAS bf16 burst, MEASURED_PEAKS.json)"
     except (OSError, KeyError, ValueError):
         peak, peak_note = 1900.0, "of fallback"
     tflops = UNET_GFLOP_64 * 32 / fwd_ms  # GFLOP per ms = TFLOP/s
+    sur_rate = nreg / (sur_ms * 1e-3)
+    plain_rates = [r for r in (1.0 / plain_s if plain else None,
+                               hier["regions_per_s"] if hier else None,
+                               batched["regions_per_s_equivalent"] if batched else None) if r]
+    best_plain = max(plain_rates) if plain_rates else None
     return {
         "metric": "SN regions/s: surrogate vs plain at fixed error",
-        "surrogate_regions_per_s": nreg / (sur_ms * 1e-3),
+        "surrogate_regions_per_s": sur_rate,
         "plain_regions_per_s": 1.0 / plain_s,
-        "speedup": nreg / (sur_ms * 1e-3) * plain_s,
+        "best_plain_regions_per_s": best_plain,
+        "speedup_vs_best_plain": sur_rate / best_plain if best_plain else None,
         "surrogate": {"regions": nreg, "gas_particles": int(counts.sum()),
                       "counts_min_max": [int(counts.min()), int(counts.max())], "grid": 64, "side_pc": 60.0,
-                      "ms_per_batch": sur_ms, "batch_ms": ms, "graph": True,
+                      "ms_per_batch": sur_ms, "batch_ms": ms, "graph": True, "trained_weights": trained,
                       "stage_ms": {k: ph[k] for k in ("VOXELISE", "UNET", "REMAP")},
                       "note": "16 generated regions placed 16 times each; density from the global step not timed"},
         "plain": {"particles": 100000, "t_end_myr": 0.1, "seconds_per_region": plain_s,
-                  "steps": [int(i["steps"]) for i in plain], "gravity": "none (SN region integrator)"},
+                  "steps": [int(i["steps"]) for i in plain], "gravity": "none (SN region integrator)",
+                  "note": "one region per context, integrated alone"},
+        "plain_batched": batched,
         "plain_hier": hier,
-        "speedup_vs_best_plain": (nreg / (sur_ms * 1e-3) * min(plain_s, hier["seconds_per_region"])
-                                  if hier else None),
-        "field_error": {"rmse_surrogate": float(kv["rmse_surrogate_all"]) if "rmse_surrogate_all" in kv else None,
-                        "rmse_no_feedback": float(kv["rmse_identity_all"]) if "rmse_identity_all" in kv else None,
-                        "units": "standardised channels, mean over 5 channels and 8 held-out seeds",
-                        "source": os.path.relpath(SN_REPORT, ROOT)},
+        "field_error": field,
         "unet_roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                           "frac": tflops / peak, "note": f"whole forward, {UNET_GFLOP_64} GFLOP per 64^3 region, "
                                                           f"batch 32, {peak_note}", "ms_per_region": fwd_ms / 32},
     }
+
+
+def plain_batched(galnb, torch, stream, nreg=32, n=100000, steps=8, steps_single=175.0):
+    """The plain CFL-limited integrator with nreg supernova regions of n gas
+    particles in one context (centres 180 pc apart, 10^51 erg injected in each;
+    seeds 1900 + k): particle-steps per second of the KDK step with the GPU
+    full, and the per-region time that rate gives a region taking
+    steps_single steps (its own CFL step count when integrated alone)."""
+    parts, centers = {}, []
+    for k in range(nreg):
+        r = dict(ics.sn_region(n, seed=1900 + k))
+        o = (180.0 * (k % 8), 180.0 * (k // 8), 0.0)
+        r["x"], r["y"] = r["x"] + o[0], r["y"] + o[1]
+        centers.append(o)
+        for key, val in r.items():
+            parts.setdefault(key, []).append(val)
+    p = {k: np.concatenate(v) for k, v in parts.items()}
+    p["id"] = np.arange(p["x"].size, dtype=np.int64)
+    ctx = galnb.Context(stream=stream.cuda_stream)
+    ctx.set_particles(p)
+    ctx.compute_sph_density()
+    for o in centers:
+        ctx.inject_energy(o, ics.E_SN_CODE)
+    ctx.integrate_cfl(1.0, max_steps=2)  # initial forces and two steps untimed
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, nst = ctx.integrate_cfl(1.0, max_steps=steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.close()
+    ms = e0.elapsed_time(e1)
+    pss = p["x"].size * nst / (ms * 1e-3)
+    sec = n * steps_single / pss
+    return {"regions": nreg, "particles": int(p["x"].size), "steps_timed": int(nst), "ms_per_step": ms / max(nst, 1),
+            "particle_steps_per_s": pss, "seconds_per_region_equivalent": sec, "regions_per_s_equivalent": 1.0 / sec,
+            "note": f"{nreg} regions in one context share the CFL step; per region: {n} particles x "
+                    f"{steps_single:.0f} steps (its own step count) at the batched rate"}
 
 
 def dist_init():

@@ -77,7 +77,7 @@ __global__ void k_morton(PArr p, int n, const double *__restrict__ box, uint64_t
 // Tiles of RS_TILE keys; per pass: digit histogram per tile, per-digit scan
 // over tiles, stable scatter with per-warp match ranks.
 #define RS_THREADS 256
-#define RS_ITEMS 8
+#define RS_ITEMS 16
 #define RS_TILE (RS_THREADS * RS_ITEMS)
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restrict__ k, int n, int shift,
@@ -142,50 +142,105 @@ __global__ void __launch_bounds__(1024) k_rs_scan(int *__restrict__ counts, int 
     }
 }
 
+// Scatter of one tile: the tile's pairs are first sorted by digit in shared
+// memory (stable: rounds of RS_THREADS pairs in order, warps in order within
+// a round, lanes in order within a warp), then written out in that order, so
+// consecutive threads write consecutive addresses of a digit's run (about
+// RS_TILE / 256 pairs per digit) instead of one scattered 8-byte store each.
+struct RsSmem {
+    uint64_t k[RS_TILE];
+    int v[RS_TILE];
+    int w[RS_THREADS / 32][256];  // per-warp digit counts of a round, then their exclusive prefixes
+    int run[256];                 // pairs of each digit ranked so far (then the tile histogram)
+    int lstart[256];              // first local position of each digit
+    int goff[256];                // global position of each digit's first pair of this tile
+};
+
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__restrict__ kin,
                                                           const int *__restrict__ vin,
                                                           uint64_t *__restrict__ kout,
                                                           int *__restrict__ vout, int n, int shift,
                                                           const int *__restrict__ offs, int ntiles)
 {
-    __shared__ int s_w[8][256];
-    __shared__ int s_run[256];
-    __shared__ int s_off[256];
-    int t = threadIdx.x, tile = blockIdx.x, w = t >> 5, lane = t & 31;
-    s_run[t] = 0;
-    s_off[t] = offs[t * ntiles + tile];
-    unsigned lt = (1u << lane) - 1u;
-    int base = tile * RS_TILE;
+    extern __shared__ __align__(16) unsigned char rs_raw[];
+    RsSmem &S = *reinterpret_cast<RsSmem *>(rs_raw);
+    const int t = threadIdx.x, tile = blockIdx.x, w = t >> 5, lane = t & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int base = tile * RS_TILE;
+    const int cnt = min(RS_TILE, n - base);
+    S.run[t] = 0;
+    S.goff[t] = offs[t * ntiles + tile];
+    __syncthreads();
+    uint64_t key[RS_ITEMS];
+    int val[RS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; r++) {
+        const int i = r * RS_THREADS + t;
+        key[r] = i < cnt ? kin[base + i] : 0ull;
+        val[r] = i < cnt ? vin[base + i] : 0;
+        if (i < cnt) atomicAdd(&S.run[(int)((key[r] >> shift) & 255u)], 1);
+    }
+    __syncthreads();
+    {   // exclusive scan of the tile histogram over the 256 digits
+        const int c = S.run[t];
+        int x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) S.w[0][w] = x;
+        __syncthreads();
+        int pre = 0;
+        for (int q = 0; q < w; q++) pre += S.w[0][q];
+        S.lstart[t] = pre + x - c;
+        S.run[t] = 0;
+        __syncthreads();
+    }
+#pragma unroll
     for (int r = 0; r < RS_ITEMS; r++) {
 #pragma unroll
-        for (int q = 0; q < 8; q++) s_w[q][t] = 0;
+        for (int q = 0; q < RS_THREADS / 32; q++) S.w[q][t] = 0;
         __syncthreads();
-        int i = base + r * RS_THREADS + t;
-        bool valid = i < n;
-        uint64_t key = valid ? kin[i] : 0ull;
-        int d = valid ? (int)((key >> shift) & 255u) : 256;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int rank = __popc(peers & lt);
-        if (valid && rank == 0) s_w[w][d] = __popc(peers);
+        const bool valid = r * RS_THREADS + t < cnt;
+        const int d = valid ? (int)((key[r] >> shift) & 255u) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt);
+        if (valid && rank == 0) S.w[w][d] = __popc(peers);
         __syncthreads();
         {
-            int run = s_run[t];
+            int run = S.run[t];
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                int cnt = s_w[q][t];
-                s_w[q][t] = run;
-                run += cnt;
+            for (int q = 0; q < RS_THREADS / 32; q++) {
+                const int c = S.w[q][t];
+                S.w[q][t] = run;
+                run += c;
             }
-            s_run[t] = run;
+            S.run[t] = run;
         }
         __syncthreads();
         if (valid) {
-            int dst = s_off[d] + s_w[w][d] + rank;
-            kout[dst] = key;
-            vout[dst] = vin[i];
+            const int lp = S.lstart[d] + S.w[w][d] + rank;
+            S.k[lp] = key[r];
+            S.v[lp] = val[r];
         }
         __syncthreads();
     }
+    for (int pos = t; pos < cnt; pos += RS_THREADS) {
+        const uint64_t k = S.k[pos];
+        const int d = (int)((k >> shift) & 255u);
+        const int dst = S.goff[d] + pos - S.lstart[d];
+        kout[dst] = k;
+        vout[dst] = S.v[pos];
+    }
+}
+
+// The scatter's tile (about 59 KB) needs the opt-in to more than 48 KB of
+// dynamic shared memory.
+static int rs_scatter_attr(gnb_ctx *c)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(RsSmem));
+    return e == cudaSuccess ? GNB_OK : cuda_check(c, e, "radix sort shared memory attribute");
 }
 
 // Stable sort of n (64-bit key, 32-bit value) pairs held in (k0, v0), with
@@ -193,6 +248,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
 int radix_sort_pairs(gnb_ctx *c, uint64_t *k0, int *v0, uint64_t *k1, int *v1, int n)
 {
     int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    GNB_TRY(rs_scatter_attr(c));
     uint64_t *kin = k0, *kout = k1;
     int *vin = v0, *vout = v1;
     for (int pass = 0; pass < 8; pass++) {
@@ -200,7 +256,8 @@ int radix_sort_pairs(gnb_ctx *c, uint64_t *k0, int *v0, uint64_t *k1, int *v1, i
         cudaMemsetAsync(c->rs_total, 0, 256 * sizeof(int), c->s);
         gnb::counted(k_rs_hist)<<<ntiles, RS_THREADS, 0, c->s>>>(kin, n, shift, c->rs_counts, ntiles, c->rs_total);
         gnb::counted(k_rs_scan)<<<256, 1024, 0, c->s>>>(c->rs_counts, ntiles, c->rs_total);
-        gnb::counted(k_rs_scatter)<<<ntiles, RS_THREADS, 0, c->s>>>(kin, vin, kout, vout, n, shift, c->rs_counts,
+        gnb::counted(k_rs_scatter)<<<ntiles, RS_THREADS, sizeof(RsSmem), c->s>>>(kin, vin, kout, vout, n, shift,
+                                                                                  c->rs_counts,
                                                                     ntiles);
         uint64_t *tk = kin; kin = kout; kout = tk;
         int *tv = vin; vin = vout; vout = tv;
@@ -242,6 +299,7 @@ int morton_and_sort(gnb_ctx *c)
     gnb::counted(k_morton)<<<nb, 256, 0, c->s>>>(a, n, c->box_d, c->key, c->skey, c->sval, c->slot_of_orig);
     GNB_LAUNCH_CHECK(c, "morton");
     int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    GNB_TRY(rs_scatter_attr(c));
     uint64_t *kin = c->skey, *kout = c->skey2;
     int *vin = c->sval, *vout = c->sval2;
     for (int pass = 0; pass < 8; pass++) {
@@ -249,7 +307,8 @@ int morton_and_sort(gnb_ctx *c)
         cudaMemsetAsync(c->rs_total, 0, 256 * sizeof(int), c->s);
         gnb::counted(k_rs_hist)<<<ntiles, RS_THREADS, 0, c->s>>>(kin, n, shift, c->rs_counts, ntiles, c->rs_total);
         gnb::counted(k_rs_scan)<<<256, 1024, 0, c->s>>>(c->rs_counts, ntiles, c->rs_total);
-        gnb::counted(k_rs_scatter)<<<ntiles, RS_THREADS, 0, c->s>>>(kin, vin, kout, vout, n, shift, c->rs_counts,
+        gnb::counted(k_rs_scatter)<<<ntiles, RS_THREADS, sizeof(RsSmem), c->s>>>(kin, vin, kout, vout, n, shift,
+                                                                                  c->rs_counts,
                                                       ntiles);
         uint64_t *tk = kin; kin = kout; kout = tk;
         int *tv = vin; vin = vout; vout = tv;
