@@ -247,10 +247,14 @@ def sn_regions(nreg, distinct, lo, hi, seed):
     return p, centers, np.asarray(counts)
 
 
-def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True):
+def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True, global_step=None):
     """SN regions/s: batched surrogate vs plain integration (see module doc).
-    nreg and plain_runs=False only serve profiling (--sn-only --sn-regions)."""
+    nreg and plain_runs=False only serve profiling (--sn-only --sn-regions).
+    global_step (a callable running one global KDK step on its own stream):
+    also time the coupled step of config 5 (coupled_bench).  The supernova
+    work runs on its own non-default stream, which graph capture needs."""
     from paper_2510_23330_gb300 import surrogate as S
+    stream = torch.cuda.Stream(device=stream.device)
     sp = stream.cuda_stream
     net = galnb.UNet(5, 5, 16, 4, 64, stream=sp)
     trained = os.path.exists(S.WEIGHTS)
@@ -273,6 +277,7 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True):
         e1.record(stream)
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
+    coupled = coupled_bench(torch, global_step, ctx, net, centers) if global_step else None
     # stage split, eager with the phase timers
     ctx.compute_sph_density()
     ctx.set_timing(True)
@@ -356,12 +361,59 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True):
                   "steps": [int(i["steps"]) for i in plain], "gravity": "none (SN region integrator)",
                   "note": "one region per context, integrated alone"},
         "plain_batched": batched,
+        "coupled_step": coupled,
         "plain_hier": hier,
         "field_error": field,
         "unet_roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                           "frac": tflops / peak, "note": f"whole forward, {UNET_GFLOP_64} GFLOP per 64^3 region, "
                                                           f"batch 32, {peak_note}", "ms_per_region": fwd_ms / 32},
     }
+
+
+def coupled_bench(torch, global_step, ctx_sn, net, centers, reps=3):
+    """The batched coupled step (config 5, Sec. 3.2: the pool nodes predict
+    the supernova regions while the main nodes integrate the galaxy): one
+    global KDK step of the galaxy context (its own stream) and one
+    graph-replayed surrogate batch of the region context (another stream),
+    issued from two host threads so that they share the GPU, against the two
+    run one after the other.  Wall-clock milliseconds, the median of reps;
+    the regions' density before each batch is computed outside the timing."""
+    import threading
+
+    def prep():
+        ctx_sn.compute_sph_density()
+        torch.cuda.synchronize()
+
+    def batch(seed):
+        ctx_sn.sn_surrogate_batch(net, centers, seed=seed)
+
+    res = {"global": [], "batch": [], "sequential": [], "concurrent": []}
+    for r in range(reps):
+        prep()
+        t0 = time.perf_counter()
+        global_step()
+        res["global"].append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        batch(100 + r)
+        res["batch"].append(time.perf_counter() - t0)
+        prep()
+        t0 = time.perf_counter()
+        global_step()
+        batch(200 + r)
+        res["sequential"].append(time.perf_counter() - t0)
+        prep()
+        th = threading.Thread(target=batch, args=(300 + r,))
+        t0 = time.perf_counter()
+        th.start()
+        global_step()
+        th.join()
+        res["concurrent"].append(time.perf_counter() - t0)
+    med = {k: 1e3 * float(np.median(v)) for k, v in res.items()}
+    return {"global_step_ms": med["global"], "batch_ms": med["batch"], "sequential_ms": med["sequential"],
+            "concurrent_ms": med["concurrent"], "overlap_gain": med["sequential"] / med["concurrent"],
+            "regions": len(centers),
+            "note": "wall clock, median of 3: one 2^24 global KDK step and one 256-region surrogate batch, one "
+                    "after the other or issued together from two host threads on two streams"}
 
 
 def plain_batched(galnb, torch, stream, nreg=32, n=100000, steps=8, steps_single=175.0):
@@ -553,9 +605,9 @@ def run_ours(args, world, rank, local):
         out["e2e"] = e2e(args, p, pr, stream, galnb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(p, desc, n_g=int(pr["cfg"].get("n_group", 64)))
-    ctx.close()
     if rank == 0 and world == 1 and not args.no_sn:
-        out["sn"] = sn_bench(stream, galnb, torch)
+        out["sn"] = sn_bench(stream, galnb, torch, global_step=lambda: ctx.step_kdk(args.dt, 1, mode))
+    ctx.close()
     return out
 
 

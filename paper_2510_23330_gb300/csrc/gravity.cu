@@ -32,8 +32,6 @@ namespace gnb {
 #define GW_LEAF 256
 #define GW_JP 512
 #define GW_JC 256
-#define GW_NI_MAX 4     // i-particles per thread at most
-#define GW_EVAL_CTAS 5  // evaluation CTAs per SM the registers are sized for (96 per thread)
 
 struct GravParams {
     int4 *na, *nb;
@@ -450,7 +448,7 @@ __global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
     }
 }
 
-// One chunk of up to GW_NI_MAX * GW_THREADS i-particles of a group against
+// One chunk of up to NI * GW_THREADS i-particles of a group against
 // the group's lists, NI i-particles per thread.  j-splits: each of the js
 // thread sets holds all icnt i-particles (slot s and s + k ilanes, k < NI)
 // and takes every js-th j entry, so a small group keeps the CTA busy; with
@@ -559,38 +557,43 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
         idx[1] = idx2[1];
         cb ^= 1;
     }
-    // reduce the j-splits: the partial sums of particle slot k go through the
-    // PP staging buffer (idle here), NI x GW_THREADS float4
-    static_assert(GW_NI_MAX * GW_THREADS <= GW_JP, "reduction buffer");
+    // reduce the j-splits: the partial sums of particle slots k0 .. k0 + RB - 1
+    // at a time go through the PP staging buffer (idle here)
+    constexpr int RB = GW_JP / GW_THREADS;
 #pragma unroll
-    for (int k = 0; k < NI; k++) S.jp[k * GW_THREADS + tid] = acc[k];
-    __syncthreads();
-    if (split == 0 && ivalid) {
+    for (int k0 = 0; k0 < NI; k0 += RB) {
 #pragma unroll
-        for (int k = 0; k < NI; k++) {
-            const int sl = islot + k * ilanes;
-            if (sl >= icnt) continue;
-            float4 a = acc[k];
-            for (int s2 = 1; s2 < js; s2++) {
-                const float4 r = S.jp[k * GW_THREADS + tid + s2 * ilanes];
-                a.x += r.x; a.y += r.y; a.z += r.z; a.w += r.w;
+        for (int k = k0; k < NI && k < k0 + RB; k++) S.jp[(k - k0) * GW_THREADS + tid] = acc[k];
+        __syncthreads();
+        if (split == 0 && ivalid) {
+#pragma unroll
+            for (int k = k0; k < NI && k < k0 + RB; k++) {
+                const int sl = islot + k * ilanes;
+                if (sl >= icnt) continue;
+                float4 a = acc[k];
+                for (int s2 = 1; s2 < js; s2++) {
+                    const float4 r = S.jp[(k - k0) * GW_THREADS + tid + s2 * ilanes];
+                    a.x += r.x; a.y += r.y; a.z += r.z; a.w += r.w;
+                }
+                const int ip = first + sl;
+                if (!MASK) a.w -= p.m[ip] * rsqrtf(2.f * pi[k].w);  // remove the j == i term
+                p.ax[ip] = p.G * a.x;
+                p.ay[ip] = p.G * a.y;
+                p.az[ip] = p.G * a.z;
+                p.pot[ip] = -p.G * a.w;
             }
-            const int ip = first + sl;
-            if (!MASK) a.w -= p.m[ip] * rsqrtf(2.f * pi[k].w);  // remove the j == i term
-            p.ax[ip] = p.G * a.x;
-            p.ay[ip] = p.G * a.y;
-            p.az[ip] = p.G * a.z;
-            p.pot[ip] = -p.G * a.w;
         }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // Evaluation of the walk's lists, one group per CTA (see the file comment):
-// the group's particles in chunks of up to GW_NI_MAX * GW_THREADS, four per
-// thread above 64 particles in a chunk, two above 16, else one.
-template <bool MASK, bool QUAD>
-__global__ void __launch_bounds__(GW_THREADS, GW_EVAL_CTAS) k_grav_eval(GravParams p)
+// the group's particles in chunks of up to NIMAX * GW_THREADS, eight per
+// thread above 128 particles in a chunk (NIMAX = 8), four above 64, two above
+// 16, else one.  The eight-particle variant holds 64 more registers of
+// i-particles and runs 4 CTAs per SM instead of 5.
+template <bool MASK, bool QUAD, int NIMAX>
+__global__ void __launch_bounds__(GW_THREADS, NIMAX >= 8 ? 4 : 5) k_grav_eval(GravParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GravSmem &S = *reinterpret_cast<GravSmem *>(smem_raw);
@@ -607,9 +610,10 @@ __global__ void __launch_bounds__(GW_THREADS, GW_EVAL_CTAS) k_grav_eval(GravPara
         const int4 gh = p.ghead[gi];
         const int4 gr = p.gref[gi];
         const int gref[3] = {gr.x, gr.y, gr.z};
-        for (int i0 = 0; i0 < gcount; i0 += GW_NI_MAX * GW_THREADS) {
-            const int icnt = min(GW_NI_MAX * GW_THREADS, gcount - i0);
-            if (icnt > 64) eval_chunk<4, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
+        for (int i0 = 0; i0 < gcount; i0 += NIMAX * GW_THREADS) {
+            const int icnt = min(NIMAX * GW_THREADS, gcount - i0);
+            if (NIMAX >= 8 && icnt > 128) eval_chunk<NIMAX >= 8 ? 8 : 4, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
+            else if (icnt > 64) eval_chunk<4, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
             else if (icnt > 16) eval_chunk<2, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
             else eval_chunk<1, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
         }
@@ -799,12 +803,21 @@ int gravity_tree(gnb_ctx *c)
         const int used = c->pinned_i[40];
         if (used <= c->gl_cap) {
             const bool q = c->cfg.multipole != 0;
-            if (c->min_eps_zero) {
-                if (q) return launch_persistent(c, k_grav_eval<true, true>, p, next_d);
-                return launch_persistent(c, k_grav_eval<true, false>, p, next_d);
+            // groups of more than 128 particles: eight i-particles per thread
+            if (c->cfg.n_group > 128) {
+                if (c->min_eps_zero) {
+                    if (q) return launch_persistent(c, k_grav_eval<true, true, 8>, p, next_d);
+                    return launch_persistent(c, k_grav_eval<true, false, 8>, p, next_d);
+                }
+                if (q) return launch_persistent(c, k_grav_eval<false, true, 8>, p, next_d);
+                return launch_persistent(c, k_grav_eval<false, false, 8>, p, next_d);
             }
-            if (q) return launch_persistent(c, k_grav_eval<false, true>, p, next_d);
-            return launch_persistent(c, k_grav_eval<false, false>, p, next_d);
+            if (c->min_eps_zero) {
+                if (q) return launch_persistent(c, k_grav_eval<true, true, 4>, p, next_d);
+                return launch_persistent(c, k_grav_eval<true, false, 4>, p, next_d);
+            }
+            if (q) return launch_persistent(c, k_grav_eval<false, true, 4>, p, next_d);
+            return launch_persistent(c, k_grav_eval<false, false, 4>, p, next_d);
         }
         if (attempt >= 4) return fail(c, GNB_ECAPACITY, "interaction-list pool");
         GNB_TRY(lists_alloc(c, used + used / 2 + 1024));
