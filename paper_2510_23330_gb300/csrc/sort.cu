@@ -72,6 +72,55 @@ __global__ void k_morton(PArr p, int n, const double *__restrict__ box, uint64_t
     slot_of_orig[o] = i;
 }
 
+// Key of every slot, paired with the slot itself for a sort in slot order
+// (ties are put into caller order afterwards, see k_tie_fix).
+__global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z, int n,
+                       const double *__restrict__ box, uint64_t *__restrict__ key, int *__restrict__ val)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double scale = 2097152.0 / box[3];
+    key[i] = morton_key(grid_cell(x[i], box[0], scale), grid_cell(y[i], box[1], scale), grid_cell(z[i], box[2], scale));
+    val[i] = i;
+}
+
+// ---------------------------------------------------------------- ties
+// The stable sort in slot order leaves equal keys in old-slot order; the
+// order wanted is (key, caller index).  Equal keys are particles in the same
+// finest grid cell, rare in any real set: one thread per run of equal keys
+// puts its run in caller order by insertion sort, for runs of at most
+// TIE_MAX entries.  st[0] = 1 when some key repeats, st[1] = the longest run
+// (capped at TIE_MAX + 1); a longer run is left to the caller-order sort.
+#define TIE_MAX 4096
+__global__ void k_tie_detect(const uint64_t *__restrict__ k, int n, int *__restrict__ st)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i + 1 >= n || k[i] != k[i + 1]) return;
+    if (i > 0 && k[i - 1] == k[i]) return;  // not the run's start
+    int e = i + 1;
+    while (e < n && e - i <= TIE_MAX && k[e] == k[i]) e++;
+    atomicOr(&st[0], 1);
+    atomicMax(&st[1], e - i);
+}
+
+__global__ void k_tie_fix(const uint64_t *__restrict__ k, int n, int *__restrict__ val, const int *__restrict__ orig)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i + 1 >= n || k[i] != k[i + 1]) return;
+    if (i > 0 && k[i - 1] == k[i]) return;
+    int e = i + 1;
+    while (e < n && k[e] == k[i]) e++;
+    for (int a = i + 1; a < e; a++) {  // insertion sort of val[i, e) by orig[val]
+        const int v = val[a], ov = orig[v];
+        int b = a - 1;
+        while (b >= i && orig[val[b]] > ov) {
+            val[b + 1] = val[b];
+            b--;
+        }
+        val[b + 1] = v;
+    }
+}
+
 // ---------------------------------------------------------------- radix sort
 // Stable LSD radix sort of (64-bit key, 32-bit value), 8 bits per pass.
 // Tiles of RS_TILE keys; per pass: digit histogram per tile, per-digit scan
@@ -275,19 +324,26 @@ __global__ void k_src(const int *__restrict__ sval, const int *__restrict__ slot
     if (i < n) src[i] = slot_of_orig[sval[i]];
 }
 
-__global__ void k_permute(PArr a, PArr b, const int *__restrict__ src, int n)
+// The grid cell and residual of each particle are computed here from its
+// position (the same arithmetic as its key), not gathered.
+__global__ void k_permute(PArr a, PArr b, const int *__restrict__ src, int n, const double *__restrict__ box)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int s = src[i];
-    b.x[i] = a.x[s]; b.y[i] = a.y[s]; b.z[i] = a.z[s]; b.h2[i] = a.h2[s]; b.id[i] = a.id[s];
+    const double x = a.x[s], y = a.y[s], z = a.z[s];
+    b.x[i] = x; b.y[i] = y; b.z[i] = z; b.h2[i] = a.h2[s]; b.id[i] = a.id[s];
     b.vx[i] = a.vx[s]; b.vy[i] = a.vy[s]; b.vz[i] = a.vz[s];
     b.m[i] = a.m[s]; b.eps[i] = a.eps[s]; b.u[i] = a.u[s];
-    b.rx[i] = a.rx[s]; b.ry[i] = a.ry[s]; b.rz[i] = a.rz[s];
     b.vpx[i] = a.vpx[s]; b.vpy[i] = a.vpy[s]; b.vpz[i] = a.vpz[s]; b.up[i] = a.up[s];
     b.orig[i] = a.orig[s]; b.grank[i] = a.grank[s];
-    b.cx[i] = a.cx[s]; b.cy[i] = a.cy[s]; b.cz[i] = a.cz[s];
     b.type[i] = a.type[s];
+    const double unit = box[4], scale = 2097152.0 / box[3];
+    float r0, r1, r2;
+    b.cx[i] = cell_of(x, box[0], scale, unit, &r0);
+    b.cy[i] = cell_of(y, box[1], scale, unit, &r1);
+    b.cz[i] = cell_of(z, box[2], scale, unit, &r2);
+    b.rx[i] = r0; b.ry[i] = r1; b.rz[i] = r2;
 }
 
 int morton_and_sort(gnb_ctx *c)
@@ -296,28 +352,35 @@ int morton_and_sort(gnb_ctx *c)
     GNB_TRY(root_box(c));
     int nb = (n + 255) / 256;
     PArr &a = c->P[c->cur];
-    gnb::counted(k_morton)<<<nb, 256, 0, c->s>>>(a, n, c->box_d, c->key, c->skey, c->sval, c->slot_of_orig);
-    GNB_LAUNCH_CHECK(c, "morton");
-    int ntiles = (n + RS_TILE - 1) / RS_TILE;
-    GNB_TRY(rs_scatter_attr(c));
-    uint64_t *kin = c->skey, *kout = c->skey2;
-    int *vin = c->sval, *vout = c->sval2;
-    for (int pass = 0; pass < 8; pass++) {
-        int shift = 8 * pass;
-        cudaMemsetAsync(c->rs_total, 0, 256 * sizeof(int), c->s);
-        gnb::counted(k_rs_hist)<<<ntiles, RS_THREADS, 0, c->s>>>(kin, n, shift, c->rs_counts, ntiles, c->rs_total);
-        gnb::counted(k_rs_scan)<<<256, 1024, 0, c->s>>>(c->rs_counts, ntiles, c->rs_total);
-        gnb::counted(k_rs_scatter)<<<ntiles, RS_THREADS, sizeof(RsSmem), c->s>>>(kin, vin, kout, vout, n, shift,
-                                                                                  c->rs_counts,
-                                                      ntiles);
-        uint64_t *tk = kin; kin = kout; kout = tk;
-        int *tv = vin; vin = vout; vout = tv;
+    // keys in slot order (the particles are near their previous Morton
+    // order), stable sort, then ties into caller order
+    gnb::counted(k_keys)<<<nb, 256, 0, c->s>>>(a.x, a.y, a.z, n, c->box_d, c->skey, c->sval);
+    GNB_LAUNCH_CHECK(c, "keys");
+    GNB_TRY(radix_sort_pairs(c, c->skey, c->sval, c->skey2, c->sval2, n));
+    cudaMemsetAsync(c->work_d + 2, 0, 2 * sizeof(int), c->s);
+    gnb::counted(k_tie_detect)<<<nb, 256, 0, c->s>>>(c->skey, n, c->work_d + 2);
+    GNB_LAUNCH_CHECK(c, "tie detect");
+    GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->pinned_i + 60, c->work_d + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                          c->s), "tie flag"));
+    GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "tie flag sync"));
+    const int *src = c->sval;  // the old slot of each sorted particle
+    if (c->pinned_i[60] && c->pinned_i[61] <= TIE_MAX) {
+        gnb::counted(k_tie_fix)<<<nb, 256, 0, c->s>>>(c->skey, n, c->sval, a.orig);
+        GNB_LAUNCH_CHECK(c, "tie fix");
+    } else if (c->pinned_i[60]) {
+        // a run of more than TIE_MAX equal keys: sort in caller order
+        // (keys scattered to the caller index, stable sort, slot map)
+        gnb::counted(k_morton)<<<nb, 256, 0, c->s>>>(a, n, c->box_d, c->key, c->skey, c->sval, c->slot_of_orig);
+        GNB_LAUNCH_CHECK(c, "morton");
+        GNB_TRY(radix_sort_pairs(c, c->skey, c->sval, c->skey2, c->sval2, n));
+        gnb::counted(k_src)<<<nb, 256, 0, c->s>>>(c->sval, c->slot_of_orig, c->src, n);
+        src = c->src;
     }
-    GNB_LAUNCH_CHECK(c, "radix sort");
-    // after 8 passes the sorted data is back in skey / sval
-    gnb::counted(k_src)<<<nb, 256, 0, c->s>>>(vin, c->slot_of_orig, c->src, n);
+    if (src != c->src)
+        GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->src, src, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, c->s),
+                           "slot map copy"));
     PArr &b = c->P[1 - c->cur];
-    gnb::counted(k_permute)<<<nb, 256, 0, c->s>>>(a, b, c->src, n);
+    gnb::counted(k_permute)<<<nb, 256, 0, c->s>>>(a, b, c->src, n, c->box_d);
     GNB_LAUNCH_CHECK(c, "permute");
     c->cur = 1 - c->cur;
     if (c->hier_on) GNB_TRY(hier_permute(c));  // per-particle step state follows the particles
