@@ -188,7 +188,7 @@ def cpu_model():
     return "unknown"
 
 
-def cpu_baseline(p, name, knn_seconds=6.0, n_g=64):
+def cpu_baseline(p, name, knn_seconds=6.0, n_g=64, n_leaf=16):
     """The FP64 oracle on a bounded sample of one force evaluation (about
     15-25 s of CPU work): the full tree build plus every k-th group's walk
     (k = N / 2^18, scaled by k) and brute-force kNN of as many sampled gas
@@ -199,7 +199,7 @@ def cpu_baseline(p, name, knn_seconds=6.0, n_g=64):
     gi = np.nonzero(p["type"] == 1)[0]
     stride = max(1, n >> 18)
     t0 = time.perf_counter()
-    tb, tw, st = oracle.tree_gravity_sampled(p, stride, theta=0.5, n_leaf=16, n_g=n_g, quad=True)
+    tb, tw, st = oracle.tree_gravity_sampled(p, stride, theta=0.5, n_leaf=n_leaf, n_g=n_g, quad=True)
     t_grav = tb + tw * stride
     g = {k: np.asarray(p[k][gi], np.float64) for k in ("x", "y", "z")}
     rng = np.random.default_rng(0)
@@ -502,14 +502,17 @@ def run_ours(args, world, rank, local):
     ctx = galnb.Context(stream=stream.cuda_stream, **pr["cfg"])
     ctx.set_particles(p)
     tuning = None
+    if args.n_leaf:
+        pr["cfg"]["n_leaf"] = args.n_leaf
+        ctx.set_params(n_leaf=args.n_leaf)
     if args.n_group:
         pr["cfg"]["n_group"] = args.n_group
         ctx.set_params(n_group=args.n_group)
     elif mode == 1 and not args.no_autotune:
         from paper_2510_23330_gb300 import autotune
-        best, table = autotune.tune_group_size(ctx, mode)
-        pr["cfg"]["n_group"] = best
-        tuning = {str(k): round(v, 4) for k, v in table.items()}
+        (nl, ng), table = autotune.tune_tree(ctx, mode)
+        pr["cfg"]["n_leaf"], pr["cfg"]["n_group"] = nl, ng
+        tuning = {k: round(v, 4) for k, v in table.items()}
     ctx.compute_forces(mode)
     for _ in range(args.warmup):
         ctx.step_kdk(args.dt, 1, mode)
@@ -589,7 +592,7 @@ def run_ours(args, world, rank, local):
                      "ms_per_launch": g_ms},
         "rooflines_hbm": rooflines,
         "interactions_per_step": {"pp": npp / args.steps, "pc": npc / args.steps},
-        "n_group_tuning_ms": tuning,
+        "tree_tuning_ms": tuning,
         "phases_ms_per_step": {k: v / args.steps for k, v in phases.items()},
         "gpu_launches": int(launches),
         "step_ms": step_ms,
@@ -604,7 +607,8 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_e2e:
         out["e2e"] = e2e(args, p, pr, stream, galnb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(p, desc, n_g=int(pr["cfg"].get("n_group", 64)))
+        out["cpu_baseline"] = cpu_baseline(p, desc, n_g=int(pr["cfg"].get("n_group", 64)),
+                                           n_leaf=int(pr["cfg"].get("n_leaf", 16)))
     if rank == 0 and world == 1 and not args.no_sn:
         out["sn"] = sn_bench(stream, galnb, torch, global_step=lambda: ctx.step_kdk(args.dt, 1, mode))
     ctx.close()
@@ -674,6 +678,7 @@ def main():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--n-group", type=int, default=0, help="fixed group size n_g (skips the autotuner)")
+    ap.add_argument("--n-leaf", type=int, default=0, help="leaf size n_leaf (with --n-group: no autotuner)")
     ap.add_argument("--sph", default="density", choices=["density", "pressure"],
                     help="SPH formulation: density-energy (default) or pressure-energy")
     ap.add_argument("--no-sn", action="store_true", help="skip the supernova surrogate-vs-plain section")
