@@ -698,6 +698,188 @@ __global__ void __launch_bounds__(128) k_up2_tc(const Up2Args p)
     }
 }
 
+
+// ------------------------------------------------------------------ WGRAD
+// Weight gradient of a 3^3 "same" convolution on the tensor cores:
+//   dW[t][c][n] = sum_v x(v + tap t)[c] * g(v)[n]
+// as a GEMM whose M = 128 rows are (tap slot s, input channel c) pairs --
+// 128 / C taps of one tap group side by side, so every row is a real weight
+// even for C = 16 -- whose N columns are the output channels and whose K is
+// the voxels.  A CTA takes one tap group and one chunk of voxels; per stage of
+// 64 voxels the threads gather the shifted inputs and the output gradient
+// (zero outside the grid) and write them transposed into the canonical
+// K-major core-matrix layout (8 rows x 16 bytes, rows = channels, the 16
+// bytes = 8 voxels), one elected lane issues four K = 16 MMAs into a TMEM
+// accumulator, and the stage buffers are double buffered behind the MMAs'
+// commit barriers.  At the end each warp reads its 32 TMEM lanes (rows) and
+// adds them to dW with FP32 atomics (the voxel chunks are split-K).
+struct WgTcArgs {
+    const bf16 *x1, *x2;   // input channels [0, C1) from x1, [C1, C) from x2; blocked [B][C/8][V][8]
+    int C1, C;
+    const bf16 *g;         // output gradient, blocked with Cg channels
+    int Cg, N, Cw;         // channels of g, output channels of dW, input channels of dW (<= C)
+    float *dw;             // [27][Cw][N]
+    int B, D;              // grid (cube of edge D) and batch
+    int ntap;              // taps per group: 128 / C
+    long long V, chunk;    // voxels in all, voxels per CTA (multiple of 64)
+    int nchunk;
+    unsigned tmem_cols, idesc, abytes, bbytes;
+    int *err;
+};
+constexpr unsigned WG_HDR = 256;
+constexpr int WG_VS = 64;  // voxels per stage
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// offset of (row r, voxel k) in a K-major stage of WG_VS voxels whose M (or N)
+// has rows rows: [k / 16][r / 8][(k % 16) / 8][r % 8][k % 8]
+__device__ __forceinline__ unsigned wg_off(int r, int k, int rows)
+{
+    return (unsigned)(k >> 4) * (unsigned)rows * 32u + (unsigned)(r >> 3) * 256u + (unsigned)((k >> 3) & 1) * 128u +
+           (unsigned)(r & 7) * 16u + (unsigned)(k & 7) * 2u;
+}
+
+__global__ void __launch_bounds__(128) k_wgrad_tc(const WgTcArgs p)
+{
+    extern __shared__ unsigned char dsm[];
+    const unsigned raw = smem_u32(dsm);
+    const unsigned sb = (raw + (ALIGN_SLACK - 1)) & ~(ALIGN_SLACK - 1);
+    unsigned char *gb = dsm + (sb - raw);
+    unsigned *slot = reinterpret_cast<unsigned *>(gb + 16);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(gb + 20);
+    const unsigned bar0 = sb, bar1 = sb + 8;  // commit barriers of the two stage buffers
+    const unsigned stage_bytes = p.abytes + p.bbytes;
+    unsigned char *stg = gb + WG_HDR;
+    const unsigned sStg = sb + WG_HDR;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tg = blockIdx.y;                // tap group
+    const int t0 = tg * p.ntap;
+    const int ntap = min(p.ntap, 27 - t0);
+    const long long r0 = (long long)blockIdx.x * p.chunk, r1 = min(p.V, r0 + p.chunk);
+    const int nstage = (int)((r1 - r0 + WG_VS - 1) / WG_VS);
+    const long long D = p.D, Vs = D * D * D;
+    if (tid == 0) {
+        mb_init(bar0, 1);
+        mb_init(bar1, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slot)),
+                     "r"(p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = *slot;
+    // rows of tap slots beyond ntap (a short last group) stay zero: cleared once
+    for (unsigned o = (unsigned)tid * 16u; o < 2u * stage_bytes; o += 128u * 16u)
+        *reinterpret_cast<uint4 *>(stg + o) = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    const int cg8 = p.C >> 3, ng8 = p.N >> 3;
+    bool ok = true;
+    int issued = -1;  // the last stage whose MMAs were issued
+    for (int st = 0; st < nstage && ok; st++) {
+        const int b = st & 1;
+        const unsigned bar = b ? bar1 : bar0;
+        // the MMAs that read this buffer two stages ago have finished
+        if (st >= 2) ok = __syncthreads_and(mb_wait(bar, (unsigned)(((st - 2) >> 1) & 1), abort_flag, p.err, 21));
+        if (!ok) break;
+        unsigned char *sA = stg + (size_t)b * stage_bytes;
+        unsigned char *sB = sA + p.abytes;
+        const long long vb = r0 + (long long)st * WG_VS;
+        // A: (tap slot, channel group, voxel) pieces of 8 channels
+        for (int e = tid; e < ntap * cg8 * WG_VS; e += 128) {
+            const int k = e % WG_VS, q = e / WG_VS;
+            const int cg = q % cg8, s = q / cg8;
+            const long long v = vb + k;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (v < r1) {
+                const long long bb = v / Vs, rem = v - bb * Vs;
+                const long long x = rem % D, y = (rem / D) % D, z = rem / (D * D);
+                const int t = t0 + s;
+                const long long zz = z + (t / 9 - 1), yy = y + ((t / 3) % 3 - 1), xx = x + (t % 3 - 1);
+                if (zz >= 0 && zz < D && yy >= 0 && yy < D && xx >= 0 && xx < D) {
+                    const long long src = (zz * D + yy) * D + xx;
+                    const int c = cg * 8;
+                    val = c < p.C1 ? *reinterpret_cast<const uint4 *>(p.x1 + ((bb * (p.C1 >> 3) + cg) * Vs + src) * 8)
+                                   : *reinterpret_cast<const uint4 *>(
+                                         p.x2 + ((bb * ((p.C - p.C1) >> 3) + (cg - (p.C1 >> 3))) * Vs + src) * 8);
+                }
+            }
+            const unsigned short *h = reinterpret_cast<const unsigned short *>(&val);
+            const int r = s * p.C + cg * 8;
+#pragma unroll
+            for (int j = 0; j < 8; j++) *reinterpret_cast<unsigned short *>(sA + wg_off(r + j, k, 128)) = h[j];
+        }
+        // B: (output channel group, voxel) pieces
+        for (int e = tid; e < ng8 * WG_VS; e += 128) {
+            const int k = e % WG_VS, ng = e / WG_VS;
+            const long long v = vb + k;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (v < r1) {
+                const long long bb = v / Vs, rem = v - bb * Vs;
+                val = *reinterpret_cast<const uint4 *>(p.g + ((bb * (p.Cg >> 3) + ng) * Vs + rem) * 8);
+            }
+            const unsigned short *h = reinterpret_cast<const unsigned short *>(&val);
+#pragma unroll
+            for (int j = 0; j < 8; j++) *reinterpret_cast<unsigned short *>(sB + wg_off(ng * 8 + j, k, p.N)) = h[j];
+        }
+        fence_proxy_async_smem();  // the generic-proxy stores become visible to the tensor cores
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tc_fence_after();
+            const unsigned a0 = sStg + (unsigned)b * stage_bytes, b0 = a0 + p.abytes;
+            const unsigned hi = sdesc_hi(256u);
+#pragma unroll
+            for (int ks = 0; ks < WG_VS / 16; ks++)
+                tc_mma_elect(tmem, dpair(sdesc_lo(a0 + (unsigned)ks * 128u * 32u, 128u), hi),
+                             dpair(sdesc_lo(b0 + (unsigned)ks * (unsigned)p.N * 32u, 128u), hi), p.idesc,
+                             (st > 0 || ks > 0) ? 1u : 0u);
+            tc_commit_elect(bar);
+        }
+        issued = st;
+    }
+    // the last stage's MMAs (every commit of a barrier before it completed in order)
+    if (ok && nstage > 0) {
+        const int sl = nstage - 1;
+        ok = __all_sync(0xffffffffu, mb_wait((sl & 1) ? bar1 : bar0, (unsigned)((sl >> 1) & 1), abort_flag, p.err, 22));
+        ok = __syncthreads_and(ok);
+    }
+    if (ok && nstage > 0) {
+        tc_fence_after();
+        const int r = 32 * warp + lane;
+        const int s = r / p.C, c = r - s * p.C;
+        const bool live = s < ntap && c < p.Cw;
+        const unsigned lane_addr = (unsigned)(32 * warp) << 16;
+        for (int n0 = 0; n0 < p.N; n0 += 16) {
+            float v[16];
+            __syncwarp();
+            tc_ld16(tmem + lane_addr + (unsigned)n0, v);
+            if (live) {
+                float *d = p.dw + ((long long)(t0 + s) * p.Cw + c) * p.N + n0;
+#pragma unroll
+                for (int j = 0; j < 16; j++) atomicAdd(d + j, v[j]);
+            }
+        }
+    }
+    if (!ok && issued >= 0 && tid == 0)  // no MMA outlives the CTA: its last commit covers the earlier ones
+        mb_wait((issued & 1) ? bar1 : bar0, (unsigned)((issued >> 1) & 1), abort_flag, p.err, 23, false);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(p.tmem_cols)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 // z-taps in N for the thin layers, which are otherwise bound by the
@@ -959,6 +1141,50 @@ int pack_w_tc(const bf16 *src, int taps, int Npad, int Kpad, bf16 *dst, cudaStre
     long long tot = (long long)taps * Npad * Kpad;
     counted(k_pack_w_tc)<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(src, taps, Npad, Kpad, dst);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+
+int wgrad3_tc(const bf16 *x1, int C1, const bf16 *x2, int C2, const bf16 *g, int Cg, int N, int Cw, float *dw, int B,
+              int D, int *err, cudaStream_t s)
+{
+    const int C = C1 + C2;
+    if (!(C == 16 || C == 32 || C == 64 || C == 128) || (C1 & 7) || N < 16 || N > 128 || (N & 15) || Cg < N ||
+        (Cg & 7) || Cw > C || B < 1 || D < 1)
+        return 0;
+    if ((reinterpret_cast<uintptr_t>(x1) & 15) || (C2 > 0 && (reinterpret_cast<uintptr_t>(x2) & 15)) ||
+        (reinterpret_cast<uintptr_t>(g) & 15))
+        return 0;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, []() {
+        attr_err = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+    });
+    if (attr_err != cudaSuccess) return -1;
+    WgTcArgs a;
+    a.x1 = x1; a.x2 = C2 > 0 ? x2 : x1; a.C1 = C1; a.C = C;
+    a.g = g; a.Cg = Cg; a.N = N; a.Cw = Cw; a.dw = dw; a.B = B; a.D = D;
+    a.ntap = 128 / C;
+    const int ntg = (27 + a.ntap - 1) / a.ntap;
+    a.V = (long long)B * D * D * D;
+    const long long target = std::max(1LL, 4LL * device_sms() / ntg);
+    long long chunk = (a.V + target - 1) / target;
+    chunk = std::max<long long>(WG_VS, (chunk + WG_VS - 1) / WG_VS * WG_VS);
+    a.chunk = chunk;
+    a.nchunk = (int)((a.V + chunk - 1) / chunk);
+    a.abytes = 128u * WG_VS * 2u;
+    a.bbytes = (unsigned)N * WG_VS * 2u;
+    a.tmem_cols = pow2_at_least((unsigned)N);
+    a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | (((unsigned)N >> 3) << 17) | ((128u >> 4) << 24);
+    a.err = err;
+    // at most as many CTAs per SM as their TMEM allocations fit
+    const unsigned need = ALIGN_SLACK + WG_HDR + 2u * (a.abytes + a.bbytes);
+    const unsigned per_sm = 512u / a.tmem_cols;
+    unsigned smem = TC_SMEM_SM / per_sm - 1024u;
+    if (smem > TC_SMEM_MAX) smem = TC_SMEM_MAX;
+    if (smem < need) smem = need;
+    if (smem > TC_SMEM_MAX) return 0;
+    counted(k_wgrad_tc)<<<dim3((unsigned)a.nchunk, (unsigned)ntg), 128, smem, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace gnb

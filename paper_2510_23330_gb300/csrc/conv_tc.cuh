@@ -58,6 +58,16 @@ bool up2_tc_ok(int N, int K, long long Vc);
 int up2_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, __nv_bfloat16 *out, int B, int Dc,
            int K, int N, int *err, cudaStream_t s);
 
+// Weight gradient of a 3^3 "same" convolution, dw[t][c][n] += sum_v
+// x(v + tap t)[c] g(v)[n] (FP32 atomics into dw, [27][Cw][N]), on the tensor
+// cores; x is the concatenation of x1 (C1 channels) and x2 (C2), g has Cg
+// channels (the first N used), blocked BF16 tensors on a (B, D^3) grid.
+// Returns 1 when launched, 0 when the shape is not supported (C1 + C2 not
+// in {16, 32, 64, 128}, N not a multiple of 16 in [16, 128], ...), -1 on a
+// launch error.
+int wgrad3_tc(const __nv_bfloat16 *x1, int C1, const __nv_bfloat16 *x2, int C2, const __nv_bfloat16 *g, int Cg, int N,
+              int Cw, float *dw, int B, int D, int *err, cudaStream_t s);
+
 // Whether a 3^3 layer with N output and K input channels runs with its
 // three z-taps in one MMA (N <= 32; see conv_tc.cu).
 bool conv3_tc_dzn(int N, int K);

@@ -796,7 +796,14 @@ void conv_wgrad(gnb_unet *u, const ULayer &ly, int mode, int B, int D, const bf1
     a.mode = mode; a.x1 = x1; a.x2 = x2 ? x2 : x1; a.C1 = C1; a.C2 = C2; a.g = g; a.Cg = Cg; a.N = ly.cout;
     a.Cw = ly.cin;
     a.dw = u->g + ly.woff; a.B = B; a.D = D; a.H = D; a.W = D;
-    launch_wg(a, ly.taps, u->s);
+    // 3^3 layers on the tensor cores where the shape allows (tcgen05 GEMM
+    // over (tap, channel) rows); the mma.sync GEMM otherwise
+    int tc = 0;
+    if (mode == IG_CONV3 && u->conv_impl == GNB_CONV_AUTO) {
+        tc = wgrad3_tc(x1, C1, x2, x2 ? C2 : 0, g, Cg, ly.cout, ly.cin, a.dw, B, D, u->err_d, u->s);
+        if (tc < 0) u->launch_failed = true;
+    }
+    if (tc == 0) launch_wg(a, ly.taps, u->s);
     // bias gradient: column sums of the output gradient
     long long Vs = mode == IG_UP2 ? 8LL * D * D * D : (long long)D * D * D;
     long long V = (long long)B * Vs;
