@@ -299,6 +299,22 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True, global_ste
     e1.record(stream)
     torch.cuda.synchronize()
     fwd_ms = e0.elapsed_time(e1) / 3
+    # --- one training step (forward, MSE, back-propagation, Adam) at batch 1,
+    # on a separate network so the timed weights stay the trained ones
+    tnet = galnb.UNet(5, 5, 16, 4, 64, stream=sp)
+    tnet.set_params(S.he_init(seed=1))
+    x1, y1 = xb[:1].contiguous(), yb[:1].contiguous()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        tnet.train_step(x1, y1, 1e-5)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(10):
+        tnet.train_step(x1, y1, 1e-5)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1) / 10
+    tnet.close()
     del xb, yb
     # --- plain: CFL-limited integration of a 1e5-particle region over 0.1 Myr,
     # one region at a time (held-out seeds 1900, 1901; also pairs for the
@@ -367,6 +383,11 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True, global_ste
         "unet_roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                           "frac": tflops / peak, "note": f"whole forward, {UNET_GFLOP_64} GFLOP per 64^3 region, "
                                                           f"batch 32, {peak_note}", "ms_per_region": fwd_ms / 32},
+        "unet_training_step": {"ms": train_ms, "batch": 1, "grid": 64,
+                               "achieved_tflops": 3 * UNET_GFLOP_64 / train_ms,
+                               "frac": 3 * UNET_GFLOP_64 / train_ms / peak,
+                               "note": "forward + MSE + back-propagation (input and weight gradients on tcgen05) + "
+                                       "Adam, counted as 3x the forward's flops; batch 1 as the paper trains"},
     }
 
 
