@@ -364,15 +364,6 @@ int gnb_unet_get_activation(gnb_unet *net, int slot, int batch, float *dst, int 
 #define GNB_CONV_AUTO 0
 #define GNB_CONV_MMA_SYNC 2
 int gnb_unet_set_conv_impl(gnb_unet *net, int impl);
-/* Test of the failure path of the tensor-core convolutions (no counterpart
- * in the paper): runs one forward pass on zeros in which the first
- * convolution's halo barriers expect 16 bytes more than its TMA loads
- * deliver, so none of its halo waits can complete.  Each bounded wait (1 s)
- * runs out, the kernel drains its copies and MMAs, frees TMEM and exits, and
- * the call returns GNB_ETIMEOUT; the network and the CUDA context stay
- * usable.  Takes a few seconds.  Errors: GNB_EINVAL (NULL, or the mma.sync
- * path selected). */
-int gnb_unet_test_wait_timeout(gnb_unet *net);
 /* Inference: x [batch][grid^3][cin] -> y [batch][grid^3][cout] (FP32).
  * Errors: GNB_EINVAL, GNB_ENOMEM, GNB_ECUDA, GNB_ETIMEOUT. */
 int gnb_unet_forward(gnb_unet *net, int batch, const float *x, float *y, int on_device);

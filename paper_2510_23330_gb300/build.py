@@ -49,7 +49,8 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     """Compile and link libgalnb.so if any source changed; returns its path."""
     srcs = _sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(ROOT, "include", "galnb.h"))
+    inc = os.path.join(ROOT, "include")
+    headers += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     dig = _digest(srcs + headers)
     stamp = os.path.join(BUILD, "stamp")
     if os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read().strip() == dig:

@@ -27,6 +27,7 @@
 
 #include "common.cuh"
 #include "conv_tc.cuh"
+#include "../../include/galnb_testing.h"
 
 typedef __nv_bfloat16 bf16;
 
