@@ -261,6 +261,8 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True, global_ste
     meta = S.load_weights(net, S.WEIGHTS) if trained else {}
     if not trained:
         net.set_params(S.he_init(seed=0))
+    # --- tile shapes of the tensor-core convolutions for the batch, by timing
+    tune_ms = net.autotune(nreg)
     # --- surrogate: one graph replay per batch of nreg ragged regions
     p, centers, counts = sn_regions(nreg, 16, 20000, 300000, seed=7)
     ctx = galnb.Context(stream=sp)
@@ -383,6 +385,7 @@ def sn_bench(stream, galnb, torch, nreg=256, reps=3, plain_runs=True, global_ste
         "unet_roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                           "frac": tflops / peak, "note": f"whole forward, {UNET_GFLOP_64} GFLOP per 64^3 region, "
                                                           f"batch 32, {peak_note}", "ms_per_region": fwd_ms / 32},
+        "unet_tile_autotune_ms": {"forward_before": tune_ms[0], "forward_after": tune_ms[1], "batch": nreg},
         "unet_training_step": {"ms": train_ms, "batch": 1, "grid": 64,
                                "achieved_tflops": 3 * UNET_GFLOP_64 / train_ms,
                                "frac": 3 * UNET_GFLOP_64 / train_ms / peak,

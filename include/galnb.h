@@ -341,6 +341,19 @@ int gnb_unet_get_grads(gnb_unet *net, float *dst, int on_device);
  * of `centers`).  Errors: GNB_EINVAL (batch < 1 or above the batch of the
  * largest pass so far, NULL), GNB_ECUDA. */
 int gnb_unet_get_output(gnb_unet *net, int batch, float *dst, int on_device);
+/* Tile autotuner of the tensor-core convolutions (the paper runs its network
+ * on CPUs and has no counterpart): one forward pass of `batch` samples on the network's current
+ * input buffer times every supported tile plan of each 3^3 layer (tile depth,
+ * halo buffering, resident or streamed weights) on that layer's real tensors
+ * and keeps the fastest for every later forward pass, including those of
+ * gnb_sn_surrogate_batch; if the whole pass with the chosen plans is not
+ * faster than with the built-in rule, the rule is kept.  out_ms (may be
+ * NULL) receives the forward pass's time before and after.  Synchronises the
+ * network's stream: do not call it during a stream capture.  Changing the
+ * network's parameters keeps the plans.  Errors: GNB_EINVAL, GNB_ENOMEM,
+ * GNB_ECUDA, GNB_ETIMEOUT. */
+int gnb_unet_autotune(gnb_unet *net, int batch, double out_ms[2]);
+
 /* A tensor the last forward pass stored, as FP32 [batch][g^3][C] (g the
  * grid of its level, C its channels), first `batch` samples.  Slots in the
  * order the forward pass writes them: 0 the BF16 network input (cin

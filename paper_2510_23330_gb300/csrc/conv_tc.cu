@@ -904,29 +904,33 @@ bool conv3_tc_dzn(int N, int K)
     return N >= 16 && N <= 32 && (N % 16) == 0 && K >= 16 && (K % 16) == 0 && dzn_fits(N, K, 2, 2, &a, &b, &c, &d, &e);
 }
 
-bool conv3_tc_plan(int N, int K, int D, TcPlan *pl)
+int conv3_tc_plans(int N, int K, int D, TcPlan *out, int cap)
 {
-    if (N < 16 || N > 256 || (N % 16) || K < 16 || (K % 16)) return false;
+    if (N < 16 || N > 256 || (N % 16) || K < 16 || (K % 16) || cap < 1) return 0;
+    int np = 0;
     if (conv3_tc_dzn(N, K)) {
+        // the weights are packed for the dz-in-N MMA: only such plans apply
         static const int zd[] = {8, 4, 2};
         const int nbuf = 2;
         for (int zt : zd) {
             if (zt > 2 && zt > D) continue;
             unsigned smem, cols, plane, halo, off_h;
             if (!dzn_fits(N, K, zt, nbuf, &smem, &cols, &plane, &halo, &off_h)) continue;
-            pl->Zt = zt;
-            pl->nbuf = nbuf;
-            pl->wstages = 0;
-            pl->dzn = 1;
-            pl->plane = plane;
-            pl->halo = halo;
-            pl->off_w = HDR;
-            pl->off_h = off_h;
-            pl->wbytes = 27u * (unsigned)N * (unsigned)K * 2u;
-            pl->smem = smem;
-            pl->tmem_cols = cols;
-            return true;
+            TcPlan &pl = out[np];
+            pl.Zt = zt;
+            pl.nbuf = nbuf;
+            pl.wstages = 0;
+            pl.dzn = 1;
+            pl.plane = plane;
+            pl.halo = halo;
+            pl.off_w = HDR;
+            pl.off_h = off_h;
+            pl.wbytes = 27u * (unsigned)N * (unsigned)K * 2u;
+            pl.smem = smem;
+            pl.tmem_cols = cols;
+            if (++np == cap) return np;
         }
+        return np;
     }
     const unsigned wtap = (unsigned)N * (unsigned)K * 2u;
     static const int zts[] = {4, 2, 1};
@@ -945,22 +949,28 @@ bool conv3_tc_plan(int N, int K, int D, TcPlan *pl)
                 const unsigned smem = ALIGN_SLACK + off_h + (unsigned)nbuf * halo;
                 const unsigned cols = pow2_at_least((unsigned)(nbuf * zt * N));
                 if (smem > TC_SMEM_MAX || cols > 512) continue;
-                pl->Zt = zt;
-                pl->nbuf = nbuf;
-                pl->wstages = stages;
-                pl->dzn = 0;
-                pl->plane = plane;
-                pl->halo = halo;
-                pl->off_w = off_w;
-                pl->off_h = off_h;
-                pl->wbytes = wbytes;
-                pl->smem = smem;
-                pl->tmem_cols = cols;
-                return true;
+                TcPlan &pl = out[np];
+                pl.Zt = zt;
+                pl.nbuf = nbuf;
+                pl.wstages = stages;
+                pl.dzn = 0;
+                pl.plane = plane;
+                pl.halo = halo;
+                pl.off_w = off_w;
+                pl.off_h = off_h;
+                pl.wbytes = wbytes;
+                pl.smem = smem;
+                pl.tmem_cols = cols;
+                if (++np == cap) return np;
             }
         }
     }
-    return false;
+    return np;
+}
+
+bool conv3_tc_plan(int N, int K, int D, TcPlan *pl)
+{
+    return conv3_tc_plans(N, K, D, pl, 1) == 1;
 }
 
 using TcKernel = void (*)(const CUtensorMap, const CUtensorMap, const TcArgs);
@@ -988,8 +998,10 @@ TcKernel pick_kernel(const TcPlan &pl, int K)
 int conv3_tc(const TcConv &c, int *err, cudaStream_t s)
 {
     const int K = c.C1 + c.C2, N = c.N;
-    TcPlan pl;
-    if ((c.C1 % 8) || (c.C2 % 8) || (c.O1 % 16) || c.O1 > N || !conv3_tc_plan(N, K, c.D, &pl)) return 0;
+    TcPlan plans[TC_MAX_PLANS];
+    const int np = conv3_tc_plans(N, K, c.D, plans, TC_MAX_PLANS);
+    if ((c.C1 % 8) || (c.C2 % 8) || (c.O1 % 16) || c.O1 > N || np < 1) return 0;
+    const TcPlan pl = plans[c.plan >= 0 && c.plan < np ? c.plan : 0];
     if ((reinterpret_cast<uintptr_t>(c.w) & 15) || (reinterpret_cast<uintptr_t>(c.in1) & 15) ||
         (c.C2 && (reinterpret_cast<uintptr_t>(c.in2) & 15)))
         return 0;

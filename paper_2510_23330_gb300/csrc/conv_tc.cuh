@@ -26,7 +26,10 @@ struct TcConv {
     int relu;
     int B, D, H, W;
     unsigned tx_extra;  // 0; > 0 only in the wait-timeout test (bytes the halo barrier expects beyond the loads)
+    int plan;           // index into conv3_tc_plans' list (< 0 or out of range: the first, the rule's choice)
 };
+
+constexpr int TC_MAX_PLANS = 24;
 
 struct TcPlan {
     int Zt, nbuf, wstages, dzn;
@@ -39,6 +42,9 @@ struct TcPlan {
 // shape is not supported (N or K not a multiple of 16, N > 256, or not even a
 // two-stage ring fits).
 bool conv3_tc_plan(int N, int K, int D, TcPlan *pl);
+// Every supported plan for the shape, the rule's choice first (at most cap);
+// the number written.  The tile autotuner times them on the real layer.
+int conv3_tc_plans(int N, int K, int D, TcPlan *out, int cap);
 
 // Launches the convolution on s.  Returns 1 when launched, 0 when the shape
 // or alignment is not supported (nothing launched; the caller uses another

@@ -560,6 +560,7 @@ namespace {
 enum { L_CONV3 = 0, L_UP2 = 1, L_CONV1 = 2 };
 
 struct ULayer {
+    mutable int plan_f = -1;    // tile plan of the tensor-core forward convolution (-1: the rule's choice)
     int kind, cin, cout, taps;
     long long woff, boff;       // offsets in the flat parameter array
     int Npad, Kpad, Nd, Kd;     // padded forward / input-gradient GEMM shapes
@@ -591,6 +592,8 @@ struct gnb_unet {
     int conv_impl = GNB_CONV_AUTO;
     unsigned tx_extra = 0;       // wait-timeout test only
     bool launch_failed = false;
+    bool tuning = false;         // forward passes time every tile plan of each 3^3 layer (gnb_unet_autotune)
+    int tuned_layers = 0;
     std::string err;
 };
 
@@ -735,10 +738,11 @@ int LI_HEAD(const gnb_unet *u) { return 2 * u->levels + 3 * (u->levels - 1); }
 
 // The tcgen05 path for a 3^3 convolution: 1 launched, 0 not applicable, -1 error.
 int conv3_try_tc(gnb_unet *u, const bf16 *wtc, int N, int B, int D, const bf16 *in1, int C1, const bf16 *in2, int C2,
-                 const float *bias, bf16 *out1, int O1, bf16 *out2, int relu)
+                 const float *bias, bf16 *out1, int O1, bf16 *out2, int relu, int plan = -1)
 {
     if (!wtc || u->conv_impl == GNB_CONV_MMA_SYNC) return 0;
     TcConv c;
+    c.plan = plan;
     c.in1 = in1; c.in2 = in2 ? in2 : in1; c.C1 = C1; c.C2 = C2;
     c.w = wtc; c.bias = bias; c.N = N;
     c.out1 = out1; c.out2 = out2 ? out2 : out1; c.O1 = O1; c.relu = relu;
@@ -748,12 +752,50 @@ int conv3_try_tc(gnb_unet *u, const bf16 *wtc, int N, int B, int D, const bf16 *
     return conv3_tc(c, u->err_d, u->s);
 }
 
+// Tile autotuner of one tensor-core 3^3 layer: every supported plan (tile
+// depth, halo buffers, resident or streamed weights) runs on the layer's real
+// tensors, twice untimed and three times timed with CUDA events on the
+// network's stream, and the fastest is kept for the layer's forward passes.
+void tune_conv3(gnb_unet *u, const ULayer &ly, int B, int D, const bf16 *in1, int C1, const bf16 *in2, int C2,
+                bf16 *out, int relu)
+{
+    TcPlan plans[TC_MAX_PLANS];
+    const int np = conv3_tc_plans(ly.Npad, C1 + C2, D, plans, TC_MAX_PLANS);
+    if (np < 2) return;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return; }
+    float best = 3.0e38f;
+    int bi = -1;
+    for (int k = 0; k < np; k++) {
+        bool ok = true;
+        for (int rep = 0; rep < 5 && ok; rep++) {
+            if (rep == 2) cudaEventRecord(e0, u->s);
+            ok = conv3_try_tc(u, ly.wtc, ly.Npad, B, D, in1, C1, in2, C2, u->p + ly.boff, out, ly.cout, nullptr, relu,
+                              k) == 1;
+        }
+        cudaEventRecord(e1, u->s);
+        float ms = 0.f;
+        if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms < best) {
+            best = ms;
+            bi = k;
+        }
+    }
+    cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bi >= 0) ly.plan_f = bi;
+    u->tuned_layers++;
+}
+
 void conv_fwd(gnb_unet *u, const ULayer &ly, int mode, int B, int D, const bf16 *in1, int C1, const bf16 *in2, int C2,
               bf16 *out, float *outf, int relu)
 {
     if (mode == IG_CONV3 && !outf) {
+        if (u->tuning && ly.wtc && u->conv_impl != GNB_CONV_MMA_SYNC) tune_conv3(u, ly, B, D, in1, C1, in2, C2, out, relu);
         int rc = conv3_try_tc(u, ly.wtc, ly.Npad, B, D, in1, C1, in2, C2, u->p + ly.boff, out, ly.cout, nullptr,
-                              relu);
+                              relu, ly.plan_f);
         if (rc != 0) { if (rc < 0) u->launch_failed = true; return; }
     }
     if (mode == IG_UP2 && !outf && !in2 && !relu && ly.wtc && C1 == ly.Kpad && ly.cout == ly.Npad &&
@@ -1146,6 +1188,54 @@ int gnb_unet_get_activation(gnb_unet *u, int slot, int batch, float *dst, int on
     int rc = unet_check(u, GNB_OK);
     if (tmp) cudaFree(tmp);
     return rc;
+}
+
+int gnb_unet_autotune(gnb_unet *u, int batch, double out_ms[2])
+{
+    if (!u || batch < 1) return GNB_EINVAL;
+    int rc = unet_alloc_acts(u, batch);
+    if (rc != GNB_OK) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return GNB_ECUDA;
+    }
+    auto timed = [&](double *ms) -> int {
+        for (int w = 0; w < 2; w++) {
+            int r = unet_forward(u, batch);
+            if (r != GNB_OK) return r;
+        }
+        cudaEventRecord(e0, u->s);
+        for (int w = 0; w < 3; w++) {
+            int r = unet_forward(u, batch);
+            if (r != GNB_OK) return r;
+        }
+        cudaEventRecord(e1, u->s);
+        float f = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&f, e0, e1) != cudaSuccess) return GNB_ECUDA;
+        *ms = f / 3.0;
+        return GNB_OK;
+    };
+    for (auto &ly : u->L) ly.plan_f = -1;
+    double before = 0.0, after = 0.0;
+    rc = timed(&before);
+    if (rc == GNB_OK) {
+        u->tuning = true;
+        u->tuned_layers = 0;
+        rc = unet_forward(u, batch);
+        u->tuning = false;
+    }
+    if (rc == GNB_OK) rc = timed(&after);
+    if (rc == GNB_OK && after > before)  // the timings of single layers did not add up: keep the rule
+        for (auto &ly : u->L) ly.plan_f = -1;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (out_ms) {
+        out_ms[0] = before;
+        out_ms[1] = after;
+    }
+    return unet_check(u, rc);
 }
 
 int gnb_unet_get_output(gnb_unet *u, int batch, float *dst, int on_device)

@@ -139,6 +139,8 @@ def _declare(L):
     L.gnb_unet_get_output.restype = C.c_int
     L.gnb_unet_get_activation.argtypes = [_vp, C.c_int, C.c_int, _vp, C.c_int]
     L.gnb_unet_get_activation.restype = C.c_int
+    L.gnb_unet_autotune.argtypes = [_vp, C.c_int, C.POINTER(C.c_double)]
+    L.gnb_unet_autotune.restype = C.c_int
     L.gnb_unet_set_conv_impl.argtypes = [_vp, C.c_int]
     L.gnb_unet_set_conv_impl.restype = C.c_int
     L.gnb_unet_test_wait_timeout.argtypes = [_vp]
@@ -288,6 +290,10 @@ def gnb_unet_get_output(net, batch, dst, on_device):
     return lib().gnb_unet_get_output(net, batch, dst, on_device)
 
 
+def gnb_unet_autotune(net, batch, out_ms):
+    return lib().gnb_unet_autotune(net, batch, out_ms)
+
+
 def gnb_unet_get_activation(net, slot, batch, dst, on_device):
     return lib().gnb_unet_get_activation(net, slot, batch, dst, on_device)
 
@@ -349,6 +355,13 @@ class UNet:
         out = np.empty((batch, g, g, g, self.cout), np.float32)
         self._chk(gnb_unet_get_output(self.h, batch, out.ctypes.data, 0), "get_output")
         return out
+
+    def autotune(self, batch):
+        """Pick each 3^3 layer's tensor-core tile plan by timing; returns the
+        forward pass's milliseconds (before, after)."""
+        out = (C.c_double * 2)()
+        self._chk(gnb_unet_autotune(self.h, batch, out), "autotune")
+        return out[0], out[1]
 
     def get_activation(self, slot, batch, grid, channels):
         """Stored tensor `slot` of the last forward pass as FP32

@@ -148,3 +148,17 @@ def test_bounded_wait_timeout_reports_and_recovers(G):
     y = net.forward(x.astype(np.float32))
     ref, _ = U.forward(p, x, bf=True)
     assert rel_l2(y, ref) < 1e-2
+
+
+def test_tile_autotune_keeps_results(G):
+    """The tile autotuner times every supported plan of each tensor-core
+    layer and keeps the fastest; the forward output stays within the
+    forward tolerance of the oracle and of the output before tuning."""
+    spec, p, x, net = _setup(G, 32, 2)
+    y0 = net.forward(x.astype(np.float32))
+    before, after = net.autotune(2)
+    assert before > 0 and after > 0
+    y1 = net.forward(x.astype(np.float32))
+    ref, _ = U.forward(p, x, levels=4, bf=True)
+    assert rel_l2(y1, ref) < 1e-2
+    assert rel_l2(y1, y0) < 1e-2
