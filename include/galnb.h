@@ -107,6 +107,8 @@ enum gnb_field {
     GNB_F_LEVEL,                    /* timestep level k (step t_span 2^-k) of each particle's last step
                                        in gnb_integrate_hier [int32, n] */
     GNB_F_POT_EXT,                  /* potential of the static NFW halo, 0 when it is off [float, n] */
+    GNB_F_NODE_LINKS,               /* links of the tree nodes, in GNB_F_NODES order: 3 int64 per node
+                                       (first child or -1, children, parent or -1) [int64, 3 * nodes] */
     GNB_F_COUNT_
 };
 

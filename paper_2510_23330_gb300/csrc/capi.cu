@@ -62,12 +62,13 @@ static void free_particles(gnb_ctx *c)
     parr_free(c, c->P[0]);
     parr_free(c, c->P[1]);
     void *all[] = {c->ax, c->ay, c->az, c->pot, c->dudt, c->gax, c->gay, c->gaz, c->pext, c->rho, c->pres,
-                   c->cs, c->key, c->skey, c->skey2, c->sval, c->sval2, c->slot_of_orig, c->src, c->rs_counts,
+                   c->cs, c->kres, c->skey, c->skey2, c->sval, c->sval2, c->slot_of_orig, c->src, c->rs_counts,
                    c->gas_flag, c->pscan, c->tmp_out};
     for (void *q : all) dfree(c, q);
     c->ax = c->ay = c->az = c->pot = c->dudt = c->gax = c->gay = c->gaz = c->pext = nullptr;
     c->rho = c->pres = c->cs = nullptr;
-    c->key = c->skey = c->skey2 = nullptr;
+    c->kres = nullptr;
+    c->skey = c->skey2 = nullptr;
     c->sval = c->sval2 = c->slot_of_orig = c->src = c->rs_counts = c->gas_flag = c->pscan = nullptr;
     c->tmp_out = nullptr;
     tree_free(c, c->t);
@@ -107,7 +108,7 @@ static int alloc_particles(gnb_ctx *c, int64_t n)
     GNB_TRY(dalloc(c, &c->gax, N)); GNB_TRY(dalloc(c, &c->gay, N)); GNB_TRY(dalloc(c, &c->gaz, N));
     GNB_TRY(dalloc(c, &c->pext, N)); GNB_TRY(dalloc(c, &c->rho, N)); GNB_TRY(dalloc(c, &c->pres, N));
     GNB_TRY(dalloc(c, &c->cs, N));
-    GNB_TRY(dalloc(c, &c->key, N)); GNB_TRY(dalloc(c, &c->skey, N)); GNB_TRY(dalloc(c, &c->skey2, N));
+    GNB_TRY(dalloc(c, &c->kres, 3 * N)); GNB_TRY(dalloc(c, &c->skey, N)); GNB_TRY(dalloc(c, &c->skey2, N));
     GNB_TRY(dalloc(c, &c->sval, N)); GNB_TRY(dalloc(c, &c->sval2, N));
     GNB_TRY(dalloc(c, &c->slot_of_orig, N)); GNB_TRY(dalloc(c, &c->src, N));
     GNB_TRY(dalloc(c, &c->gas_flag, N + 1)); GNB_TRY(dalloc(c, &c->pscan, N + 1));
@@ -832,6 +833,7 @@ static int64_t field_count(gnb_ctx *c, int f, size_t *esz)
     case GNB_F_KEY: case GNB_F_ORDER: case GNB_F_ID: *esz = 8; return c->n;
     case GNB_F_NBR: *esz = 8; return c->n_gas * 64;
     case GNB_F_NODES: *esz = 8; return 4 * (int64_t)c->t.nnodes;
+    case GNB_F_NODE_LINKS: *esz = 8; return 3 * (int64_t)c->t.nnodes;
     case GNB_F_GROUPS: *esz = 8; return c->t.ngroups;
     default: *esz = 4; return c->n;
     }
@@ -844,7 +846,7 @@ int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
     if (!dst || field < 0 || field >= GNB_F_COUNT_) return fail(c, GNB_EINVAL, "field or destination");
     if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
     bool need_sort = field == GNB_F_KEY || field == GNB_F_ORDER;
-    bool need_tree = field == GNB_F_NODES || field == GNB_F_GROUPS;
+    bool need_tree = field == GNB_F_NODES || field == GNB_F_NODE_LINKS || field == GNB_F_GROUPS;
     bool need_grav = field == GNB_F_AX || field == GNB_F_AY || field == GNB_F_AZ || field == GNB_F_POT ||
                      field == GNB_F_POT_EXT ||
                      field == GNB_F_AGRAV_X || field == GNB_F_AGRAV_Y || field == GNB_F_AGRAV_Z;
@@ -868,7 +870,7 @@ int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
     } else {
         void *tmp = c->tmp_out;
         bool own = false;
-        if ((size_t)cnt * esz > (size_t)c->cap * 8 + 64 * 8) {
+        if ((size_t)cnt * esz > (size_t)c->cap * 8 + 64) {  // the staging buffer holds 8 cap + 64 bytes
             if (cudaMalloc(&tmp, (size_t)cnt * esz) != cudaSuccess) return fail(c, GNB_ENOMEM, "export buffer");
             own = true;
         }

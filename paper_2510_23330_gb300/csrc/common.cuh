@@ -46,15 +46,10 @@ enum : int {
     ST_BAD_INPUT = 16,
 };
 
-// The octree's top levels find their child boundaries in a table of the first
-// slot of every key prefix at this level (one parallel search per build).
-constexpr int GNB_PTAB_LEVEL = 6;
-
 struct Tree {
     int cap = 0;       // node capacity
     int nnodes = 0;    // nodes of the last build (host copy)
-    int maxlev = 0;
-    int depth = GNB_MAXLEV;  // deepest non-empty level of the last build (host; bounds the next one's launches)
+    int depth = GNB_MAXLEV;  // deepest non-empty level of the last build (host copy)
     // node arrays
     int4 *na = nullptr;   // {first, count, child, (nchild << 8) | level}
     int4 *nb = nullptr;   // {corner x, corner y, corner z, parent}
@@ -62,15 +57,15 @@ struct Tree {
     float4 *mo1 = nullptr; // {Qxx, Qyy, Qzz, Qxy}
     float4 *mo2 = nullptr; // {Qxz, Qyz, eps2, 0}
     int *lvl = nullptr;    // device: level begin offsets [GNB_MAXLEV + 2]
-    int *cb = nullptr;     // first slot of each child digit of split nodes [8 per node]
-    int *partial = nullptr;
-    int *poff = nullptr;
-    int *gmark = nullptr;  // per particle: node starting a group there, else -1
-    int *gflag = nullptr, *goff = nullptr;  // group compaction scratch
+    int *head = nullptr;   // build: the parent of a first child, else -1 [cap]
+    // build scratch, per sorted slot and per tile of slots
+    int *span = nullptr;   // nodes starting at each slot: first and last level, group level
+    int *tcnt = nullptr;   // nodes of each level (and groups) per tile, then their offsets
+    int *tot = nullptr;    // nodes of each level (and groups) in all
+    int scap = 0, tcap = 0;
     int *groups = nullptr; // group node ids, ascending first particle
     int *ngroups_d = nullptr;
     int ngroups = 0;
-    int *ptab = nullptr;   // first slot of every level-GNB_PTAB_LEVEL key prefix (8^L + 1 entries)
 };
 
 struct Buf {
@@ -109,7 +104,8 @@ struct gnb_ctx {
     float *pext = nullptr;                                  // external potential
     float *rho = nullptr, *pres = nullptr, *cs = nullptr;   // gas fields per slot
     // sort scratch
-    uint64_t *key = nullptr, *skey = nullptr, *skey2 = nullptr;
+    uint64_t *skey = nullptr, *skey2 = nullptr;
+    float *kres = nullptr;    // remainders of the coordinates within their grid cells [3][cap], slot order
     int *sval = nullptr, *sval2 = nullptr, *slot_of_orig = nullptr, *src = nullptr;
     int *pscan = nullptr;     // per-slot scan scratch
     unsigned char *tmp_out = nullptr;  // export staging (8 bytes per particle)

@@ -187,6 +187,17 @@ __global__ void k_nodes_out(int4 *__restrict__ na, const uint64_t *__restrict__ 
     dst[4 * k + 3] = a.y;
 }
 
+__global__ void k_links_out(const int4 *__restrict__ na, const int4 *__restrict__ nb, int nn,
+                            int64_t *__restrict__ dst)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nn) return;
+    const int4 a = na[k];
+    dst[3 * k + 0] = a.z;
+    dst[3 * k + 1] = a.w >> 8;
+    dst[3 * k + 2] = nb[k].w;
+}
+
 __global__ void k_groups_out(const int *__restrict__ groups, int ng, int64_t *__restrict__ dst)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,6 +258,10 @@ int scatter_out(gnb_ctx *c, int field, void *dst)
     case GNB_F_ORDER: gnb::counted(k_order_out)<<<nb, 256, 0, c->s>>>(a.orig, n, (int64_t *)dst); break;
     case GNB_F_NODES:
         gnb::counted(k_nodes_out)<<<(c->t.nnodes + 255) / 256, 256, 0, c->s>>>(c->t.na, c->skey, c->t.nnodes, (int64_t *)dst);
+        break;
+    case GNB_F_NODE_LINKS:
+        gnb::counted(k_links_out)<<<(c->t.nnodes + 255) / 256, 256, 0, c->s>>>(c->t.na, c->t.nb, c->t.nnodes,
+                                                                                  (int64_t *)dst);
         break;
     case GNB_F_GROUPS:
         gnb::counted(k_groups_out)<<<(c->t.ngroups + 255) / 256, 256, 0, c->s>>>(c->t.groups, c->t.ngroups, (int64_t *)dst);

@@ -104,12 +104,47 @@ __host__ __device__ __forceinline__ uint64_t spread3(uint32_t v)
     return x;
 }
 
-// Morton grid cell of coordinate x: floor((x - lo) * scale) clamped to
-// [0, 2^21 - 1], scale = 2^21 / L (exact FP64 subtraction and product).
-__device__ __forceinline__ int grid_cell(double x, double lo, double scale)
+// Inverse of spread3: the 21 bits at positions 0, 3, 6, ... packed together.
+__host__ __device__ __forceinline__ int compact3(uint64_t x)
 {
-    double f = floor(__dmul_rn(__dsub_rn(x, lo), scale));
-    return f < 0.0 ? 0 : (f > (double)GNB_GRID_MAX ? GNB_GRID_MAX : (int)f);
+    x &= 0x1249249249249249ull;
+    x = (x | x >> 2) & 0x10c30c30c30c30c3ull;
+    x = (x | x >> 4) & 0x100f00f00f00f00full;
+    x = (x | x >> 8) & 0x1f0000ff0000ffull;
+    x = (x | x >> 16) & 0x1f00000000ffffull;
+    x = (x | x >> 32) & 0x1fffffull;
+    return (int)x;
+}
+
+// Exponent of the root box side L (a power of two).
+__device__ __forceinline__ int box_lexp(double L)
+{
+    return (int)((__double_as_longlong(L) >> 52) & 0x7ff) - 1023;
+}
+
+// Morton grid cell of coordinate x: floor((x - lo) * 2^21 / L) clamped to
+// [0, 2^21 - 1], L = 2^lexp, with x - lo the rounded FP64 difference.  The
+// scale is a power of two, so the floor is read exactly from the bits of the
+// difference with integer operations (GB300's FP64 pipe is narrow).  *res,
+// when given, is the remainder x - lo - cell L / 2^21 (exact in FP64) in
+// FP32, within one FP32 rounding.
+__device__ __forceinline__ int grid_cell(double x, double lo, int lexp, float *res = nullptr)
+{
+    const double d = __dsub_rn(x, lo);  // >= 0
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    int e = (int)(b >> 52);
+    unsigned long long m = b & 0xfffffffffffffull;
+    if (e == 0) e = 1;  // subnormal
+    else m |= 1ull << 52;
+    const int s = 1054 + lexp - e;  // d = m 2^(e - 1075); one cell = 2^s units of m
+    unsigned long long c = s >= 64 ? 0ull : (s <= 0 ? (unsigned long long)GNB_GRID_MAX : m >> s);
+    if (c > GNB_GRID_MAX) c = GNB_GRID_MAX;
+    if (res) {
+        const unsigned long long f = s >= 64 ? m : (s <= 0 ? 0ull : m - (c << s));
+        const float v = __uint2float_rn((unsigned)(f >> 32)) * 4294967296.f + __uint2float_rn((unsigned)f);
+        *res = ldexpf(v, e - 1075);
+    }
+    return (int)c;
 }
 
 __device__ __forceinline__ uint64_t morton_key(int c0, int c1, int c2)

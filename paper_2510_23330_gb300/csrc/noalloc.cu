@@ -71,9 +71,8 @@ __global__ void k_na_keys(const double *__restrict__ x, const double *__restrict
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double *box = (const double *)(scr + OFF_BOX);
-    double scale = 2097152.0 / box[3];
-    keys[i] = morton_key(grid_cell(x[i], box[0], scale), grid_cell(y[i], box[1], scale),
-                         grid_cell(z[i], box[2], scale));
+    const int lexp = box_lexp(box[3]);
+    keys[i] = morton_key(grid_cell(x[i], box[0], lexp), grid_cell(y[i], box[1], lexp), grid_cell(z[i], box[2], lexp));
 }
 
 __global__ void __launch_bounds__(NA_THREADS) k_na_hist(const uint64_t *__restrict__ k, int n, int shift,

@@ -3,7 +3,7 @@
 //
 // Root box: lo_k = min x_k, ext = max_k(max x_k - lo_k), L = 2^ceil(log2 ext)
 // (L = 1 when ext = 0), unit = L / 2^21.  Cell c_k = min(floor((x_k - lo_k) *
-// 2^21 / L), 2^21 - 1) from exact FP64 operations; the key interleaves bit b
+// 2^21 / L), 2^21 - 1) with the FP64-rounded difference; the key interleaves bit b
 // of c_x, c_y, c_z at 3b+2, 3b+1, 3b.  Particles are ordered by (key, caller
 // index): the keys are scattered to caller order and sorted by a stable LSD
 // radix sort, so equal keys keep caller order.
@@ -41,31 +41,16 @@ int root_box(gnb_ctx *c)
 }
 
 // ---------------------------------------------------------------- Morton
-__device__ __forceinline__ int cell_of(double x, double lo, double scale, double unit, float *r)
-{
-    int c = grid_cell(x, lo, scale);
-    *r = (float)__dsub_rn(__dsub_rn(x, lo), __dmul_rn((double)c, unit));
-    return c;
-}
-
-// Keys, cells and residuals of every slot; keys and the slot map are also
-// scattered to caller order for the sort.
-__global__ void k_morton(PArr p, int n, const double *__restrict__ box, uint64_t *__restrict__ key,
-                         uint64_t *__restrict__ keyo, int *__restrict__ valo,
-                         int *__restrict__ slot_of_orig)
+// Keys (and the caller-order copies) for the sort when long runs of equal
+// keys need it (see morton_and_sort).
+__global__ void k_morton(PArr p, int n, const double *__restrict__ box, uint64_t *__restrict__ keyo,
+                         int *__restrict__ valo, int *__restrict__ slot_of_orig)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double lo0 = box[0], lo1 = box[1], lo2 = box[2], L = box[3], unit = box[4];
-    double scale = 2097152.0 / L;
-    float r0, r1, r2;
-    int c0 = cell_of(p.x[i], lo0, scale, unit, &r0);
-    int c1 = cell_of(p.y[i], lo1, scale, unit, &r1);
-    int c2 = cell_of(p.z[i], lo2, scale, unit, &r2);
-    p.cx[i] = c0; p.cy[i] = c1; p.cz[i] = c2;
-    p.rx[i] = r0; p.ry[i] = r1; p.rz[i] = r2;
-    uint64_t k = morton_key(c0, c1, c2);
-    key[i] = k;
+    const int lexp = box_lexp(box[3]);
+    const uint64_t k = morton_key(grid_cell(p.x[i], box[0], lexp), grid_cell(p.y[i], box[1], lexp),
+                                  grid_cell(p.z[i], box[2], lexp));
     int o = p.orig[i];
     keyo[o] = k;
     valo[o] = o;
@@ -73,15 +58,25 @@ __global__ void k_morton(PArr p, int n, const double *__restrict__ box, uint64_t
 }
 
 // Key of every slot, paired with the slot itself for a sort in slot order
-// (ties are put into caller order afterwards, see k_tie_fix).
+// (ties are put into caller order afterwards, see k_tie_fix), and the FP32
+// remainder of each coordinate within its grid cell (res: three arrays of n,
+// slot order) for the permutation.
 __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z, int n,
-                       const double *__restrict__ box, uint64_t *__restrict__ key, int *__restrict__ val)
+                       const double *__restrict__ box, uint64_t *__restrict__ key, int *__restrict__ val,
+                       float *__restrict__ res)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double scale = 2097152.0 / box[3];
-    key[i] = morton_key(grid_cell(x[i], box[0], scale), grid_cell(y[i], box[1], scale), grid_cell(z[i], box[2], scale));
+    const int lexp = box_lexp(box[3]);
+    float r0, r1, r2;
+    const int c0 = grid_cell(x[i], box[0], lexp, &r0);
+    const int c1 = grid_cell(y[i], box[1], lexp, &r1);
+    const int c2 = grid_cell(z[i], box[2], lexp, &r2);
+    key[i] = morton_key(c0, c1, c2);
     val[i] = i;
+    res[i] = r0;
+    res[(size_t)n + i] = r1;
+    res[2 * (size_t)n + i] = r2;
 }
 
 // ---------------------------------------------------------------- ties
@@ -324,26 +319,27 @@ __global__ void k_src(const int *__restrict__ sval, const int *__restrict__ slot
     if (i < n) src[i] = slot_of_orig[sval[i]];
 }
 
-// The grid cell and residual of each particle are computed here from its
-// position (the same arithmetic as its key), not gathered.
-__global__ void k_permute(PArr a, PArr b, const int *__restrict__ src, int n, const double *__restrict__ box)
+// New slot i takes old slot src[i]; its grid cell comes from its sorted key
+// and its remainder within the cell from the key pass (res, old-slot order).
+__global__ void k_permute(PArr a, PArr b, const int *__restrict__ src, int n, const uint64_t *__restrict__ skey,
+                          const float *__restrict__ res)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int s = src[i];
-    const double x = a.x[s], y = a.y[s], z = a.z[s];
-    b.x[i] = x; b.y[i] = y; b.z[i] = z; b.h2[i] = a.h2[s]; b.id[i] = a.id[s];
+    b.x[i] = a.x[s]; b.y[i] = a.y[s]; b.z[i] = a.z[s]; b.h2[i] = a.h2[s]; b.id[i] = a.id[s];
     b.vx[i] = a.vx[s]; b.vy[i] = a.vy[s]; b.vz[i] = a.vz[s];
     b.m[i] = a.m[s]; b.eps[i] = a.eps[s]; b.u[i] = a.u[s];
     b.vpx[i] = a.vpx[s]; b.vpy[i] = a.vpy[s]; b.vpz[i] = a.vpz[s]; b.up[i] = a.up[s];
     b.orig[i] = a.orig[s]; b.grank[i] = a.grank[s];
     b.type[i] = a.type[s];
-    const double unit = box[4], scale = 2097152.0 / box[3];
-    float r0, r1, r2;
-    b.cx[i] = cell_of(x, box[0], scale, unit, &r0);
-    b.cy[i] = cell_of(y, box[1], scale, unit, &r1);
-    b.cz[i] = cell_of(z, box[2], scale, unit, &r2);
-    b.rx[i] = r0; b.ry[i] = r1; b.rz[i] = r2;
+    const uint64_t k = skey[i];
+    b.cx[i] = compact3(k >> 2);
+    b.cy[i] = compact3(k >> 1);
+    b.cz[i] = compact3(k);
+    b.rx[i] = res[s];
+    b.ry[i] = res[(size_t)n + s];
+    b.rz[i] = res[2 * (size_t)n + s];
 }
 
 int morton_and_sort(gnb_ctx *c)
@@ -354,7 +350,7 @@ int morton_and_sort(gnb_ctx *c)
     PArr &a = c->P[c->cur];
     // keys in slot order (the particles are near their previous Morton
     // order), stable sort, then ties into caller order
-    gnb::counted(k_keys)<<<nb, 256, 0, c->s>>>(a.x, a.y, a.z, n, c->box_d, c->skey, c->sval);
+    gnb::counted(k_keys)<<<nb, 256, 0, c->s>>>(a.x, a.y, a.z, n, c->box_d, c->skey, c->sval, c->kres);
     GNB_LAUNCH_CHECK(c, "keys");
     GNB_TRY(radix_sort_pairs(c, c->skey, c->sval, c->skey2, c->sval2, n));
     cudaMemsetAsync(c->work_d + 2, 0, 2 * sizeof(int), c->s);
@@ -370,7 +366,7 @@ int morton_and_sort(gnb_ctx *c)
     } else if (c->pinned_i[60]) {
         // a run of more than TIE_MAX equal keys: sort in caller order
         // (keys scattered to the caller index, stable sort, slot map)
-        gnb::counted(k_morton)<<<nb, 256, 0, c->s>>>(a, n, c->box_d, c->key, c->skey, c->sval, c->slot_of_orig);
+        gnb::counted(k_morton)<<<nb, 256, 0, c->s>>>(a, n, c->box_d, c->skey, c->sval, c->slot_of_orig);
         GNB_LAUNCH_CHECK(c, "morton");
         GNB_TRY(radix_sort_pairs(c, c->skey, c->sval, c->skey2, c->sval2, n));
         gnb::counted(k_src)<<<nb, 256, 0, c->s>>>(c->sval, c->slot_of_orig, c->src, n);
@@ -380,7 +376,7 @@ int morton_and_sort(gnb_ctx *c)
         GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->src, src, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, c->s),
                            "slot map copy"));
     PArr &b = c->P[1 - c->cur];
-    gnb::counted(k_permute)<<<nb, 256, 0, c->s>>>(a, b, c->src, n, c->box_d);
+    gnb::counted(k_permute)<<<nb, 256, 0, c->s>>>(a, b, c->src, n, c->skey, c->kres);
     GNB_LAUNCH_CHECK(c, "permute");
     c->cur = 1 - c->cur;
     if (c->hier_on) GNB_TRY(hier_permute(c));  // per-particle step state follows the particles

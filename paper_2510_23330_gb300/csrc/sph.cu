@@ -103,7 +103,7 @@ __global__ void k_gas_gather(GasGather g)
     } else {
         g.gvx[k] = g.p.vx[s]; g.gvy[k] = g.p.vy[s]; g.gvz[k] = g.p.vz[s]; g.gu[k] = g.p.u[s];
     }
-    g.gRprev[k] = g.have_h ? (float)sqrt(g.p.h2[s]) : 0.f;
+    g.gRprev[k] = g.have_h ? sqrtf((float)g.p.h2[s]) : 0.f;  // a starting radius only
 }
 
 // ---------------------------------------------------------------- search radius

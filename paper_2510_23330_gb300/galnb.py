@@ -35,10 +35,10 @@ GNB_CONV_MMA_SYNC = 2
 
 FIELDS = ["X", "Y", "Z", "VX", "VY", "VZ", "AX", "AY", "AZ", "POT", "U", "DUDT", "RHO", "PRES", "CS", "H2",
           "KEY", "ORDER", "NBR", "NODES", "GROUPS", "ID", "AGRAV_X", "AGRAV_Y", "AGRAV_Z", "LEVEL",
-          "POT_EXT"]
+          "POT_EXT", "NODE_LINKS"]
 F = {name: i for i, name in enumerate(FIELDS)}
 FIELD_DTYPE = {"X": np.float64, "Y": np.float64, "Z": np.float64, "H2": np.float64, "KEY": np.uint64,
-               "ORDER": np.int64, "NBR": np.int64, "NODES": np.int64, "GROUPS": np.int64, "ID": np.int64,
+               "ORDER": np.int64, "NBR": np.int64, "NODES": np.int64, "NODE_LINKS": np.int64, "GROUPS": np.int64, "ID": np.int64,
                "LEVEL": np.int32}
 STATS = ["N", "NGAS", "NODES", "GROUPS", "NPP", "NPC", "GAS_NODES", "KNN_PASSES", "NSYM", "MAXLEVEL"]
 
@@ -534,6 +534,8 @@ class Context:
             return self.n_gas * 64
         if field == "NODES":
             return 4 * st["NODES"]
+        if field == "NODE_LINKS":
+            return 3 * st["NODES"]
         if field == "GROUPS":
             return st["GROUPS"]
         return self.n

@@ -38,6 +38,20 @@ def _oracle_tree(orc, p, cfg):
     return key, order, tree
 
 
+def _check_links(c, tree):
+    """first child, child count and parent of every node against the oracle's
+    breadth-first tree (the parent of node k is the node whose children hold k)"""
+    links = c.get("NODE_LINKS").reshape(-1, 3)
+    nn = tree["level"].shape[0]
+    assert links.shape == (nn, 3)
+    assert np.array_equal(links[:, 0], tree["child"])
+    assert np.array_equal(links[:, 1], tree["nchild"])
+    par = np.full(nn, -1, np.int64)
+    for k in np.nonzero(tree["nchild"])[0]:
+        par[tree["child"][k]:tree["child"][k] + tree["nchild"][k]] = k
+    assert np.array_equal(links[:, 2], par)
+
+
 def _acc_err(g, ref):
     """max_i |a_gpu - a_ref| / sum_j |a_ij|"""
     d = np.sqrt((g[0] - ref["ax"]) ** 2 + (g[1] - ref["ay"]) ** 2 + (g[2] - ref["az"]) ** 2)
@@ -59,9 +73,11 @@ def test_keys_order_topology_exact(G, orc, n):
     ref = np.stack([tree["level"], tree["prefix"].astype(np.int64), tree["first"], tree["count"]], axis=1)
     assert nodes.shape == ref.shape
     assert np.array_equal(nodes, ref)
+    _check_links(c, tree)
     groups = c.get("GROUPS")
     gref = orc.groups(tree, 32)
     assert np.array_equal(np.sort(groups), np.sort(gref))
+    assert np.all(np.diff(tree["first"][groups]) > 0)  # ascending first particle
 
 
 def test_topology_duplicates_and_level21(G, orc):
@@ -74,7 +90,10 @@ def test_topology_duplicates_and_level21(G, orc):
     assert np.array_equal(c.get("ORDER"), order)
     ref = np.stack([tree["level"], tree["prefix"].astype(np.int64), tree["first"], tree["count"]], axis=1)
     assert np.array_equal(c.get("NODES"), ref)
+    _check_links(c, tree)
     assert tree["level"].max() == 21
+    groups = c.get("GROUPS")
+    assert np.array_equal(np.sort(groups), np.sort(orc.groups(tree, 16)))
 
 
 def test_disk_keys_and_topology_exact_full_size(G, orc):
@@ -86,6 +105,9 @@ def test_disk_keys_and_topology_exact_full_size(G, orc):
     assert np.array_equal(c.get("ORDER"), order)
     ref = np.stack([tree["level"], tree["prefix"].astype(np.int64), tree["first"], tree["count"]], axis=1)
     assert np.array_equal(c.get("NODES"), ref)
+    _check_links(c, tree)
+    groups = c.get("GROUPS")
+    assert np.array_equal(np.sort(groups), np.sort(orc.groups(tree, 64)))
 
 
 @pytest.mark.parametrize("n", [2, 31, 1000, 8192])
