@@ -288,7 +288,7 @@ void phase_end(gnb_ctx *c);
 
 // sort.cu
 int morton_and_sort(gnb_ctx *c);
-int radix_sort_pairs(gnb_ctx *c, uint64_t *k0, int *v0, uint64_t *k1, int *v1, int n);
+int radix_sort_pairs(gnb_ctx *c, uint64_t *k0, int *v0, uint64_t *k1, int *v1, int n, int first_digit);
 // replace.cu
 int replace_particles(gnb_ctx *c, int64_t n, const int64_t *id, const double *x, const double *y, const double *z,
                       const float *vx, const float *vy, const float *vz, const float *u, int on_device);

@@ -120,7 +120,7 @@ int replace_particles(gnb_ctx *c, int64_t m64, const int64_t *id, const double *
     if (!c->rid_valid) {
         gnb::counted(k_rid_init)<<<nb, 256, 0, c->s>>>(p.id, p.orig, n, c->rid_key, c->rid_orig);
         GNB_LAUNCH_CHECK(c, "replace: ID table");
-        GNB_TRY(radix_sort_pairs(c, c->rid_key, c->rid_orig, c->rid_key2, c->rid_orig2, n));
+        GNB_TRY(radix_sort_pairs(c, c->rid_key, c->rid_orig, c->rid_key2, c->rid_orig2, n, 0));
         c->rid_valid = true;
     }
     gnb::counted(k_rid_inverse)<<<nb, 256, 0, c->s>>>(p.orig, n, c->rid_inv, c->rid_mark);

@@ -5,8 +5,9 @@
 // (L = 1 when ext = 0), unit = L / 2^21.  Cell c_k = min(floor((x_k - lo_k) *
 // 2^21 / L), 2^21 - 1) with the FP64-rounded difference; the key interleaves bit b
 // of c_x, c_y, c_z at 3b+2, 3b+1, 3b.  Particles are ordered by (key, caller
-// index): the keys are scattered to caller order and sorted by a stable LSD
-// radix sort, so equal keys keep caller order.
+// index): a stable LSD radix sort of the keys in their current slot order by
+// the top 48 bits, then the short runs that agree there put in (key, caller
+// index) order (see the ties section).
 #include "common.cuh"
 #include "morton.cuh"
 
@@ -41,8 +42,8 @@ int root_box(gnb_ctx *c)
 }
 
 // ---------------------------------------------------------------- Morton
-// Keys (and the caller-order copies) for the sort when long runs of equal
-// keys need it (see morton_and_sort).
+// Keys scattered to caller order, for the whole-key sort that a long run of
+// equal 48-bit prefixes needs (see morton_and_sort).
 __global__ void k_morton(PArr p, int n, const double *__restrict__ box, uint64_t *__restrict__ keyo,
                          int *__restrict__ valo, int *__restrict__ slot_of_orig)
 {
@@ -80,38 +81,47 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
 }
 
 // ---------------------------------------------------------------- ties
-// The stable sort in slot order leaves equal keys in old-slot order; the
-// order wanted is (key, caller index).  Equal keys are particles in the same
-// finest grid cell, rare in any real set: one thread per run of equal keys
-// puts its run in caller order by insertion sort, for runs of at most
-// TIE_MAX entries.  st[0] = 1 when some key repeats, st[1] = the longest run
+// The slot-order sort runs over the top 48 key bits only (levels 1 to 16),
+// stably, so pairs whose keys agree there are left in old-slot order; the
+// order wanted is (key, caller index).  Such runs are particles in the same
+// level-16 cell (a 2^-16 part of the box side), a few at most in any real
+// set: one thread per run puts it in order by insertion sort, for runs of at
+// most TIE_MAX entries.  st[0] = 1 when some run exists, st[1] = the longest
 // (capped at TIE_MAX + 1); a longer run is left to the caller-order sort.
 #define TIE_MAX 4096
+#define TIE_SHIFT 16  // key bits below the sorted ones
+#define TIE_FIRST_DIGIT (TIE_SHIFT / 8)
+
+__device__ __forceinline__ bool tie(uint64_t a, uint64_t b) { return (a >> TIE_SHIFT) == (b >> TIE_SHIFT); }
+
 __global__ void k_tie_detect(const uint64_t *__restrict__ k, int n, int *__restrict__ st)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i + 1 >= n || k[i] != k[i + 1]) return;
-    if (i > 0 && k[i - 1] == k[i]) return;  // not the run's start
+    if (i + 1 >= n || !tie(k[i], k[i + 1])) return;
+    if (i > 0 && tie(k[i - 1], k[i])) return;  // not the run's start
     int e = i + 1;
-    while (e < n && e - i <= TIE_MAX && k[e] == k[i]) e++;
+    while (e < n && e - i <= TIE_MAX && tie(k[e], k[i])) e++;
     atomicOr(&st[0], 1);
     atomicMax(&st[1], e - i);
 }
 
-__global__ void k_tie_fix(const uint64_t *__restrict__ k, int n, int *__restrict__ val, const int *__restrict__ orig)
+__global__ void k_tie_fix(uint64_t *__restrict__ k, int n, int *__restrict__ val, const int *__restrict__ orig)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i + 1 >= n || k[i] != k[i + 1]) return;
-    if (i > 0 && k[i - 1] == k[i]) return;
+    if (i + 1 >= n || !tie(k[i], k[i + 1])) return;
+    if (i > 0 && tie(k[i - 1], k[i])) return;
     int e = i + 1;
-    while (e < n && k[e] == k[i]) e++;
-    for (int a = i + 1; a < e; a++) {  // insertion sort of val[i, e) by orig[val]
+    while (e < n && tie(k[e], k[i])) e++;
+    for (int a = i + 1; a < e; a++) {  // insertion sort of the pairs [i, e) by (key, orig[val])
+        const uint64_t kv = k[a];
         const int v = val[a], ov = orig[v];
         int b = a - 1;
-        while (b >= i && orig[val[b]] > ov) {
+        while (b >= i && (k[b] > kv || (k[b] == kv && orig[val[b]] > ov))) {
+            k[b + 1] = k[b];
             val[b + 1] = val[b];
             b--;
         }
+        k[b + 1] = kv;
         val[b + 1] = v;
     }
 }
@@ -287,15 +297,16 @@ static int rs_scatter_attr(gnb_ctx *c)
     return e == cudaSuccess ? GNB_OK : cuda_check(c, e, "radix sort shared memory attribute");
 }
 
-// Stable sort of n (64-bit key, 32-bit value) pairs held in (k0, v0), with
-// (k1, v1) as the ping-pong buffers; the sorted pairs end in (k0, v0).
-int radix_sort_pairs(gnb_ctx *c, uint64_t *k0, int *v0, uint64_t *k1, int *v1, int n)
+// Stable sort of n (64-bit key, 32-bit value) pairs held in (k0, v0) by the
+// key bits from 8 first_digit up (first_digit even), with (k1, v1) as the
+// ping-pong buffers; the sorted pairs end in (k0, v0).
+int radix_sort_pairs(gnb_ctx *c, uint64_t *k0, int *v0, uint64_t *k1, int *v1, int n, int first_digit)
 {
     int ntiles = (n + RS_TILE - 1) / RS_TILE;
     GNB_TRY(rs_scatter_attr(c));
     uint64_t *kin = k0, *kout = k1;
     int *vin = v0, *vout = v1;
-    for (int pass = 0; pass < 8; pass++) {
+    for (int pass = first_digit; pass < 8; pass++) {
         int shift = 8 * pass;
         cudaMemsetAsync(c->rs_total, 0, 256 * sizeof(int), c->s);
         gnb::counted(k_rs_hist)<<<ntiles, RS_THREADS, 0, c->s>>>(kin, n, shift, c->rs_counts, ntiles, c->rs_total);
@@ -349,10 +360,11 @@ int morton_and_sort(gnb_ctx *c)
     int nb = (n + 255) / 256;
     PArr &a = c->P[c->cur];
     // keys in slot order (the particles are near their previous Morton
-    // order), stable sort, then ties into caller order
+    // order), stable sort by the top 48 bits, then runs into (key, caller
+    // index) order
     gnb::counted(k_keys)<<<nb, 256, 0, c->s>>>(a.x, a.y, a.z, n, c->box_d, c->skey, c->sval, c->kres);
     GNB_LAUNCH_CHECK(c, "keys");
-    GNB_TRY(radix_sort_pairs(c, c->skey, c->sval, c->skey2, c->sval2, n));
+    GNB_TRY(radix_sort_pairs(c, c->skey, c->sval, c->skey2, c->sval2, n, TIE_FIRST_DIGIT));
     cudaMemsetAsync(c->work_d + 2, 0, 2 * sizeof(int), c->s);
     gnb::counted(k_tie_detect)<<<nb, 256, 0, c->s>>>(c->skey, n, c->work_d + 2);
     GNB_LAUNCH_CHECK(c, "tie detect");
@@ -364,11 +376,11 @@ int morton_and_sort(gnb_ctx *c)
         gnb::counted(k_tie_fix)<<<nb, 256, 0, c->s>>>(c->skey, n, c->sval, a.orig);
         GNB_LAUNCH_CHECK(c, "tie fix");
     } else if (c->pinned_i[60]) {
-        // a run of more than TIE_MAX equal keys: sort in caller order
+        // a run of more than TIE_MAX: sort by the whole key in caller order
         // (keys scattered to the caller index, stable sort, slot map)
         gnb::counted(k_morton)<<<nb, 256, 0, c->s>>>(a, n, c->box_d, c->skey, c->sval, c->slot_of_orig);
         GNB_LAUNCH_CHECK(c, "morton");
-        GNB_TRY(radix_sort_pairs(c, c->skey, c->sval, c->skey2, c->sval2, n));
+        GNB_TRY(radix_sort_pairs(c, c->skey, c->sval, c->skey2, c->sval2, n, 0));
         gnb::counted(k_src)<<<nb, 256, 0, c->s>>>(c->sval, c->slot_of_orig, c->src, n);
         src = c->src;
     }

@@ -181,9 +181,14 @@ struct KnnSmem {
     int ui[KN_WARPS][KN_U];
     long long uD[KN_WARPS][KN_U];  // exact FP64 d^2 as bit patterns (non-negative: they order like the values)
     int ug[KN_WARPS][KN_U];        // gas ranks of the uncertain entries
-    int nc, sp, g, wb, under, over, split, bmin[3], bmax[3];
+    int nc, sp, g, wb, under, over, split, nleaf, bmin[3], bmax[3];
     unsigned amax;
 };
+// During the gather the bucket buffers hold the list of leaves within the
+// radius (first, count) and its prefix sums over the counts.
+#define KN_LEAF 256
+static_assert(sizeof(float) * KN_WARPS * KN_BKT >= (sizeof(int2) + sizeof(int)) * KN_LEAF + sizeof(int),
+              "leaf list must fit the bucket buffers");
 
 // A particle of a group could not be ranked within the buffers: the FP32
 // error band (2^-17 A^2, A the group's largest offset) is wide when a dense
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
         const int4 ga = make_int4(gitem.x, gitem.y, 0, 0);
         const float R = p.kR[gi];
         if (tid < 3) { S.bmin[tid] = 0x7fffffff; S.bmax[tid] = -1; }
-        if (tid == 0) { S.nc = 0; S.sp = 1; S.stack[0] = 0; S.under = 0; S.over = 0; S.split = 0; S.amax = 0u; }
+        if (tid == 0) { S.nc = 0; S.sp = 1; S.stack[0] = 0; S.under = 0; S.over = 0; S.split = 0; S.amax = 0u; S.nleaf = 0; }
         __syncthreads();
         for (int i = ga.x + tid; i < ga.x + ga.y; i += KN_THREADS) {
             atomicMin(&S.bmin[0], p.gcx[i]); atomicMax(&S.bmax[0], p.gcx[i]);
@@ -302,7 +307,10 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
         // exactly when gap2 <= floor(Rg2m) (no FP64 per visited node)
         const long long Rg2i = Rg2m >= 4.0e18 ? 0x7fffffffffffffffll : (long long)Rg2m;
         const float R2stage = R * R * (1.f + 1e-4f) + 4.f * unit * unit;
-        // gather candidates within R of the group box
+        int2 *leafl = reinterpret_cast<int2 *>(&S.bkt[0][0]);
+        int *lpre = reinterpret_cast<int *>(leafl + KN_LEAF);
+        // gather candidates within R of the group box: the walk lists the
+        // leaves it reaches, then all threads test their particles together
         for (;;) {
             __syncthreads();
             int sp = S.sp;
@@ -338,6 +346,9 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
                             S.over = 1;
                         }
                     } else {
+                        const int q = atomicAdd(&S.nleaf, 1);
+                        if (q < KN_LEAF) leafl[q] = make_int2(a.x, a.y);
+                        else  // the list is full: this thread tests the leaf's particles
                         for (int j = a.x; j < a.x + a.y; j++) {
                             float ox = grid_off(p.gcx[j], gref[0], p.grx[j], unit);
                             float oy = grid_off(p.gcy[j], gref[1], p.gry[j], unit);
@@ -358,6 +369,66 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
                         }
                     }
                 }
+            }
+        }
+        __syncthreads();
+        {   // the listed leaves' particles, flattened over all threads
+            const int nl = min(S.nleaf, KN_LEAF);
+            if (w == 0) {  // prefix sums of the leaf counts
+                int carry = 0;
+                for (int b0 = 0; b0 < nl; b0 += 32) {
+                    const int q = b0 + lane;
+                    const int v = q < nl ? leafl[q].y : 0;
+                    int inc = v;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    if (q < nl) lpre[q] = carry + inc - v;
+                    carry += __shfl_sync(0xffffffffu, inc, 31);
+                }
+                if (lane == 0) lpre[nl] = carry;
+            }
+            __syncthreads();
+            const int total = lpre[nl];
+            for (int f0 = w * 32; f0 < total; f0 += KN_THREADS) {
+                const int f = f0 + lane;
+                bool in = false;
+                float ox = 0.f, oy = 0.f, oz = 0.f;
+                int j = 0;
+                if (f < total) {
+                    int lo = 0, hi = nl - 1;  // the last leaf starting at or before f
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (lpre[mid] <= f) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    j = leafl[lo].x + (f - lpre[lo]);
+                    ox = grid_off(p.gcx[j], gref[0], p.grx[j], unit);
+                    oy = grid_off(p.gcy[j], gref[1], p.gry[j], unit);
+                    oz = grid_off(p.gcz[j], gref[2], p.grz[j], unit);
+                    const float gx = fmaxf(0.f, fmaxf(blo[0] - ox, ox - bhi[0]));
+                    const float gy = fmaxf(0.f, fmaxf(blo[1] - oy, oy - bhi[1]));
+                    const float gz = fmaxf(0.f, fmaxf(blo[2] - oz, oz - bhi[2]));
+                    in = gx * gx + gy * gy + gz * gz <= R2stage;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (bal == 0u) continue;
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&S.nc, __popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                unsigned a2 = 0u;
+                if (in) {
+                    const int slot = base + __popc(bal & ltmask);
+                    if (slot < KN_CAP) {
+                        S.cand[slot] = make_float4(ox, oy, oz, __int_as_float(j));
+                        a2 = __float_as_uint(ox * ox + oy * oy + oz * oz);
+                    } else {
+                        S.over = 1;
+                    }
+                }
+                a2 = __reduce_max_sync(0xffffffffu, a2);
+                if (lane == 0) atomicMax(&S.amax, a2);
             }
         }
         __syncthreads();
