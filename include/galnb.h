@@ -285,6 +285,27 @@ int gnb_replace_region(gnb_ctx *ctx, int64_t n, const int64_t *id, const double 
  * not computed yet), GNB_ECUDA. */
 int gnb_get(gnb_ctx *ctx, int field, void *dst, int64_t cap, int on_device);
 
+/* Checkpoint of the particle state (no counterpart in the paper, which
+ * describes no checkpoints).  gnb_save writes to `path`, in the caller's
+ * particle order: IDs, types, FP64 positions, velocities, masses, softening
+ * lengths, internal energies, the squared kernel supports, and the results
+ * of the last force evaluation (accelerations, potentials, du/dt, density,
+ * pressure, sound speed) with flags saying which are current.  gnb_load
+ * replaces the context's particles by the file's (as gnb_set_particles
+ * does, so the caller order is the file's) and restores the supports and
+ * the current results: gnb_step_kdk then continues with the same kicks, and
+ * every field reads back equal to the saved context's, except GNB_F_NBR,
+ * which needs a new kernel-size search.  Not saved: the hierarchical
+ * integrator's step state and surrogate batches.  Errors: GNB_EINVAL (NULL,
+ * a file that cannot be opened, read or written or is not a state file, or
+ * invalid particles in it), GNB_ESTATE (gnb_save without particles or with
+ * an asynchronous surrogate batch pending), GNB_EMISMATCH (the file's gas
+ * count disagrees with its particle types), GNB_ENOMEM, GNB_ECUDA.  If
+ * gnb_load fails after its particles were set, the context holds them
+ * without the restored results. */
+int gnb_save(gnb_ctx *ctx, const char *path);
+int gnb_load(gnb_ctx *ctx, const char *path);
+
 /* FP64 totals: out = {E_kin, E_pot (1/2 sum m phi), E_ext (sum m Phi_nfw),
  * E_th (sum m u over gas), P_x, P_y, P_z, L_x, L_y, L_z}.  Requires a force
  * evaluation at the current positions.  Errors: GNB_ESTATE, GNB_ECUDA. */
@@ -335,6 +356,16 @@ int64_t gnb_unet_num_params(const gnb_unet *net);
  * Errors: GNB_EINVAL, GNB_ECUDA. */
 int gnb_unet_get_params(gnb_unet *net, float *dst, int on_device);
 int gnb_unet_set_params(gnb_unet *net, const float *src, int on_device);
+/* Checkpoint of a network (no counterpart in the paper, which describes no
+ * checkpoints): gnb_unet_save writes the FP32 master parameters, Adam's two
+ * moments and its step count to `path` (a 64-byte header, then three arrays
+ * of gnb_unet_num_params floats); gnb_unet_load reads such a file into a
+ * network of the same shape (cin, cout, base, levels, grid), after which
+ * training continues exactly where the saved network stopped.  Errors:
+ * GNB_EINVAL (NULL, a file that cannot be opened, read or written, or is not
+ * a network checkpoint), GNB_EMISMATCH (another network shape), GNB_ECUDA. */
+int gnb_unet_save(gnb_unet *net, const char *path);
+int gnb_unet_load(gnb_unet *net, const char *path);
 /* Gradients of the last gnb_unet_train_step (before its Adam update). */
 int gnb_unet_get_grads(gnb_unet *net, float *dst, int on_device);
 /* The FP32 output [batch][grid^3][cout] of the network's last forward pass,

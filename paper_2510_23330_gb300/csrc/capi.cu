@@ -858,6 +858,7 @@ int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
     if (need_grav && !c->gravity_valid && !(total_acc && c->sphf_valid))
         return fail(c, GNB_ESTATE, "forces not computed");
     if (need_den && !c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed");
+    if (field == GNB_F_NBR && !c->nbr_valid) return fail(c, GNB_ESTATE, "neighbour lists not computed");
     if (field == GNB_F_DUDT && !c->sphf_valid) return fail(c, GNB_ESTATE, "SPH force not computed");
     if (field == GNB_F_LEVEL && !c->hier_valid) return fail(c, GNB_ESTATE, "no hierarchical integration");
     size_t esz;
@@ -881,6 +882,22 @@ int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
         if (own) cudaFree(tmp);
     }
     return finish(c, rc);
+}
+
+int gnb_save(gnb_ctx *c, const char *path)
+{
+    if (!c || !path) return GNB_EINVAL;
+    c->err.clear();
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    if (c->sna_pending) return fail(c, GNB_ESTATE, "an asynchronous surrogate batch is pending");
+    return finish(c, save_state(c, path));
+}
+
+int gnb_load(gnb_ctx *c, const char *path)
+{
+    if (!c || !path) return GNB_EINVAL;
+    c->err.clear();
+    return finish(c, load_state(c, path));
 }
 
 int gnb_diagnostics(gnb_ctx *c, double out[10])

@@ -257,6 +257,7 @@ struct gnb_ctx {
     bool density_valid = false, force_valid = false, have_h = false, sphf_valid = false;
     bool use_pred = false;      // SPH uses predicted v, u (inside a KDK step)
     int last_grav_mode = -1;
+    bool nbr_valid = false;   // neighbour lists of the current kernel-size search (not restored by gnb_load)
 };
 
 namespace gnb {
@@ -310,6 +311,8 @@ int build_tree(gnb_ctx *c, Tree &t, const uint64_t *skey, int n, const int *n_d,
 int tree_alloc(gnb_ctx *c, Tree &t, int cap);
 void tree_free(gnb_ctx *c, Tree &t);
 int device_scan(gnb_ctx *c, const int *in, int *out, const int *n_d, int nmax, int *total_d);
+int save_state(gnb_ctx *c, const char *path);
+int load_state(gnb_ctx *c, const char *path);
 // gravity.cu
 int gravity_tree(gnb_ctx *c);
 int gravity_direct(gnb_ctx *c);

@@ -973,6 +973,7 @@ int sph_density(gnb_ctx *c)
     GNB_LAUNCH_CHECK(c, "density scatter");
     phase_end(c);
     c->have_h = true;
+    c->nbr_valid = true;
     return GNB_OK;
 }
 

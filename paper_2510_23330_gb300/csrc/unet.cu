@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -1253,6 +1254,74 @@ int gnb_unet_set_params(gnb_unet *u, const float *src, int on_device)
     cudaMemsetAsync(u->m, 0, u->nparam * 4, u->s);
     cudaMemsetAsync(u->v, 0, u->nparam * 4, u->s);
     u->adam_t = 0;
+    return unet_check(u, unet_pack(u));
+}
+
+// Checkpoint of a network: a 64-byte header ("GNBUNET1", uint32 version 1,
+// int32 cin, cout, base, levels, grid, int64 parameter count, int64 Adam
+// steps taken, zero padding), then the FP32 master parameters and Adam's
+// first and second moments, each [parameter count], in the order of
+// gnb_unet_get_params.
+namespace {
+struct UnetCkHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t cin, cout, base, levels, grid;
+    int64_t nparam, adam_t;
+    unsigned char pad[64 - 8 - 4 - 20 - 16];
+};
+static_assert(sizeof(UnetCkHeader) == 64, "network checkpoint header is 64 bytes");
+constexpr char UNET_MAGIC[8] = {'G', 'N', 'B', 'U', 'N', 'E', 'T', '1'};
+}  // namespace
+
+int gnb_unet_save(gnb_unet *u, const char *path)
+{
+    if (!u || !path) return GNB_EINVAL;
+    std::vector<float> host((size_t)u->nparam * 3);
+    for (int k = 0; k < 3; k++) {
+        const float *src = k == 0 ? u->p : (k == 1 ? u->m : u->v);
+        cudaMemcpyAsync(host.data() + (size_t)k * u->nparam, src, u->nparam * 4, cudaMemcpyDeviceToHost, u->s);
+    }
+    const int rc = unet_check(u, GNB_OK);
+    if (rc != GNB_OK) return rc;
+    UnetCkHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, UNET_MAGIC, 8);
+    h.version = 1;
+    h.cin = u->cin; h.cout = u->cout; h.base = u->base; h.levels = u->levels; h.grid = u->grid;
+    h.nparam = u->nparam;
+    h.adam_t = u->adam_t;
+    FILE *f = fopen(path, "wb");
+    if (!f) return GNB_EINVAL;
+    const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(host.data(), 4, host.size(), f) == host.size();
+    const bool closed = fclose(f) == 0;
+    return ok && closed ? GNB_OK : GNB_EINVAL;
+}
+
+int gnb_unet_load(gnb_unet *u, const char *path)
+{
+    if (!u || !path) return GNB_EINVAL;
+    FILE *f = fopen(path, "rb");
+    if (!f) return GNB_EINVAL;
+    UnetCkHeader h;
+    std::vector<float> host;
+    int rc = GNB_OK;
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, UNET_MAGIC, 8) != 0 || h.version != 1) {
+        rc = GNB_EINVAL;
+    } else if (h.cin != u->cin || h.cout != u->cout || h.base != u->base || h.levels != u->levels ||
+               h.grid != u->grid || h.nparam != u->nparam || h.adam_t < 0) {
+        rc = GNB_EMISMATCH;
+    } else {
+        host.resize((size_t)u->nparam * 3);
+        if (fread(host.data(), 4, host.size(), f) != host.size()) rc = GNB_EINVAL;
+    }
+    fclose(f);
+    if (rc != GNB_OK) return rc;
+    for (int k = 0; k < 3; k++) {
+        float *dst = k == 0 ? u->p : (k == 1 ? u->m : u->v);
+        cudaMemcpyAsync(dst, host.data() + (size_t)k * u->nparam, u->nparam * 4, cudaMemcpyHostToDevice, u->s);
+    }
+    u->adam_t = (int)h.adam_t;
     return unet_check(u, unet_pack(u));
 }
 

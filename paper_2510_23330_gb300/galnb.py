@@ -145,6 +145,9 @@ def _declare(L):
     L.gnb_unet_set_conv_impl.restype = C.c_int
     L.gnb_unet_test_wait_timeout.argtypes = [_vp]
     L.gnb_unet_test_wait_timeout.restype = C.c_int
+    for name in ("gnb_save", "gnb_load", "gnb_unet_save", "gnb_unet_load"):
+        getattr(L, name).argtypes = [_vp, C.c_char_p]
+        getattr(L, name).restype = C.c_int
     L.gnb_unet_forward.argtypes = [_vp, C.c_int, _vp, _vp, C.c_int]
     L.gnb_unet_forward.restype = C.c_int
     L.gnb_unet_train_step.argtypes = [_vp, C.c_int, _vp, _vp, C.c_double, C.POINTER(C.c_double), C.c_int]
@@ -282,6 +285,22 @@ def gnb_unet_set_params(net, src, on_device):
     return lib().gnb_unet_set_params(net, src, on_device)
 
 
+def gnb_unet_save(net, path):
+    return lib().gnb_unet_save(net, os.fsencode(path))
+
+
+def gnb_unet_load(net, path):
+    return lib().gnb_unet_load(net, os.fsencode(path))
+
+
+def gnb_save(ctx, path):
+    return lib().gnb_save(ctx, os.fsencode(path))
+
+
+def gnb_load(ctx, path):
+    return lib().gnb_load(ctx, os.fsencode(path))
+
+
 def gnb_unet_get_grads(net, dst, on_device):
     return lib().gnb_unet_get_grads(net, dst, on_device)
 
@@ -374,6 +393,14 @@ class UNet:
         flat = np.ascontiguousarray(flat, dtype=np.float32)
         assert flat.size == self.num_params()
         self._chk(gnb_unet_set_params(self.h, flat.ctypes.data, 0), "set_params")
+
+    def save(self, path):
+        """Parameters and Adam state to a checkpoint file (gnb_unet_save)."""
+        self._chk(gnb_unet_save(self.h, path), "save")
+
+    def load(self, path):
+        """Parameters and Adam state from a checkpoint of a same-shape network."""
+        self._chk(gnb_unet_load(self.h, path), "load")
 
     def forward(self, x, out=None):
         """x: [B, G, G, G, cin] (numpy float32 or a CUDA tensor)."""
@@ -576,6 +603,17 @@ class Context:
         out = (C.c_double * 10)()
         self._chk(gnb_diagnostics(self.h, out))
         return np.array(out[:])
+
+    def save(self, path):
+        """Particle state and the last force evaluation's results to a file
+        (gnb_save)."""
+        self._chk(gnb_save(self.h, path))
+
+    def load(self, path):
+        """Replace the particles by a saved state (gnb_load)."""
+        self._chk(gnb_load(self.h, path))
+        self.n = int(self.stats()["N"])
+        self.n_gas = int(self.stats()["NGAS"])
 
     def stats(self):
         out = (C.c_int64 * len(STATS))()

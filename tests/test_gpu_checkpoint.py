@@ -1,0 +1,146 @@
+"""Checkpoint and resume through the C ABI (gnb_save / gnb_load for the
+particle state, gnb_unet_save / gnb_unet_load for the network with its Adam
+state).
+
+Round trip: every field a loaded context returns equals the saving
+context's bit for bit.  Resume: a star-only tree-gravity run continued from
+the file matches the uninterrupted run bit for bit (the tree build, walk and
+evaluation are deterministic, and the sort order depends only on the keys and
+caller indices); with gas, the kernel-size search appends candidates with
+atomics, so the density sums may take another order and the comparison is
+within FP32 rounding.  A network resumed from its checkpoint trains on as
+the saved one does, which a network given only its parameters (Adam state
+reset) does not.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_23330_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+STATE = ["X", "Y", "Z", "VX", "VY", "VZ", "U", "ID"]
+GRAV = ["AX", "AY", "AZ", "POT", "POT_EXT", "AGRAV_X", "AGRAV_Y", "AGRAV_Z"]
+GAS = ["DUDT", "RHO", "PRES", "CS", "H2"]
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_23330_gb300 import galnb
+    return galnb
+
+
+def _fields(c, names):
+    return {k: c.get(k) for k in names}
+
+
+def _same(a, b):
+    for k in a:
+        assert a[k].dtype == b[k].dtype and np.array_equal(a[k].view(np.uint8), b[k].view(np.uint8)), k
+
+
+def test_star_only_resume_is_bit_exact(G, tmp_path):
+    p = ics.plummer(8192, seed=11, n_gas=0)
+    kw = dict(theta=0.5, multipole=1, n_group=64)
+    a = G.Context(**kw)
+    a.set_particles(p)
+    a.step_kdk(1e-3, 2)
+    path = tmp_path / "stars.gnb"
+    a.save(str(path))
+    b = G.Context(**kw)
+    b.load(str(path))
+    assert b.n == a.n and b.n_gas == 0
+    _same(_fields(a, STATE + GRAV), _fields(b, STATE + GRAV))
+    a.step_kdk(1e-3, 3)
+    b.step_kdk(1e-3, 3)
+    _same(_fields(a, STATE + GRAV), _fields(b, STATE + GRAV))
+
+
+def test_gas_round_trip_and_resume(G, tmp_path):
+    p = ics.config_disk(1 << 15, seed=5)
+    kw = dict(theta=0.5, multipole=1, n_group=64, nfw_ms=ics.NFW_MS, nfw_rs=ics.NFW_RS)
+    a = G.Context(**kw)
+    a.set_particles(p)
+    a.step_kdk(1e-3, 2)
+    path = tmp_path / "disk.gnb"
+    a.save(str(path))
+    b = G.Context(**kw)
+    b.load(str(path))
+    assert (b.n, b.n_gas) == (a.n, a.n_gas)
+    _same(_fields(a, STATE + GRAV + GAS), _fields(b, STATE + GRAV + GAS))
+    with pytest.raises(G.GalnbError):
+        b.get("NBR")  # neighbour lists are not in the file
+    a.step_kdk(1e-3, 2)
+    b.step_kdk(1e-3, 2)
+    fa, fb = _fields(a, STATE), _fields(b, STATE)
+    assert np.array_equal(fa["ID"], fb["ID"])
+    scale = max(np.ptp(fa["X"]), np.ptp(fa["Y"]), np.ptp(fa["Z"]))
+    for k in ("X", "Y", "Z"):
+        assert np.max(np.abs(fa[k] - fb[k])) <= 1e-12 * scale, k
+    vmax = max(np.max(np.abs(fa[k])) for k in ("VX", "VY", "VZ"))
+    for k in ("VX", "VY", "VZ"):
+        assert np.max(np.abs(fa[k].astype(np.float64) - fb[k])) <= 1e-6 * vmax, k
+    gas = p["type"] == 1
+    du = np.abs(fa["U"].astype(np.float64) - fb["U"])[gas]
+    assert np.max(du / fa["U"][gas]) <= 1e-5
+
+
+def test_state_file_errors(G, tmp_path):
+    c = G.Context()
+    with pytest.raises(G.GalnbError) as e:
+        c.load(str(tmp_path / "missing.gnb"))
+    assert e.value.code == G.GNB_EINVAL
+    with pytest.raises(G.GalnbError) as e:
+        c.save(str(tmp_path / "empty.gnb"))  # no particles yet
+    assert e.value.code == G.GNB_ESTATE
+    c.set_particles(ics.plummer(256, seed=2, n_gas=0))
+    path = tmp_path / "short.gnb"
+    c.save(str(path))
+    data = path.read_bytes()
+    path.write_bytes(data[: len(data) // 2])
+    d = G.Context()
+    with pytest.raises(G.GalnbError) as e:
+        d.load(str(path))
+    assert e.value.code == G.GNB_EINVAL
+    path.write_bytes(b"not a state file" + data[16:])
+    with pytest.raises(G.GalnbError) as e:
+        d.load(str(path))
+    assert e.value.code == G.GNB_EINVAL
+
+
+def test_unet_checkpoint_resumes_training(G, tmp_path):
+    from paper_2510_23330_gb300 import surrogate as S
+    shape = dict(cin=5, cout=5, base=16, levels=3, grid=16)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((2, 16, 16, 16, 5)).astype(np.float32)
+    y = rng.standard_normal((2, 16, 16, 16, 5)).astype(np.float32)
+    a = G.UNet(**shape)
+    a.set_params(S.he_init(cin=5, cout=5, base=16, levels=3, seed=4))
+    for _ in range(3):
+        a.train_step(x[:1], y[:1], 1e-3)
+    path = tmp_path / "net.gnbu"
+    a.save(str(path))
+    b = G.UNet(**shape)
+    b.load(str(path))
+    assert np.array_equal(a.get_params(), b.get_params())
+    assert np.array_equal(a.forward(x), b.forward(x))
+    # one more step on both: the same update (the weight gradients add
+    # split-K partial sums with atomics, so within FP32 rounding)
+    c = G.UNet(**shape)
+    c.set_params(a.get_params())  # parameters only: Adam restarts at step 1
+    a.train_step(x[1:], y[1:], 1e-3)
+    b.train_step(x[1:], y[1:], 1e-3)
+    c.train_step(x[1:], y[1:], 1e-3)
+    pa, pb, pc = a.get_params(), b.get_params(), c.get_params()
+    step = np.abs(pa - S.he_init(cin=5, cout=5, base=16, levels=3, seed=4)).max()
+    assert np.max(np.abs(pa - pb)) <= 1e-3 * step
+    assert np.max(np.abs(pa - pc)) > 1e-2 * step
+    other = G.UNet(cin=5, cout=5, base=8, levels=3, grid=16)
+    with pytest.raises(G.GalnbError) as e:
+        other.load(str(path))
+    assert e.value.code == G.GNB_EMISMATCH
+    for n in (a, b, c, other):
+        n.close()
