@@ -182,6 +182,7 @@ struct KnnSmem {
     long long uD[KN_WARPS][KN_U];  // exact FP64 d^2 as bit patterns (non-negative: they order like the values)
     int ug[KN_WARPS][KN_U];        // gas ranks of the uncertain entries
     int nc, sp, g, wb, under, over, split, nleaf, bmin[3], bmax[3];
+    long long rg2i;
     unsigned amax;
 };
 // During the gather the bucket buffers hold the list of leaves within the
@@ -284,7 +285,15 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
         const int4 ga = make_int4(gitem.x, gitem.y, 0, 0);
         const float R = p.kR[gi];
         if (tid < 3) { S.bmin[tid] = 0x7fffffff; S.bmax[tid] = -1; }
-        if (tid == 0) { S.nc = 0; S.sp = 1; S.stack[0] = 0; S.under = 0; S.over = 0; S.split = 0; S.amax = 0u; S.nleaf = 0; }
+        if (tid == 0) {
+            S.nc = 0; S.sp = 1; S.stack[0] = 0; S.under = 0; S.over = 0; S.split = 0; S.amax = 0u; S.nleaf = 0;
+            // the node test's threshold: (R in grid units)^2 (1 + 1e-5) + 4, in
+            // FP64 by one thread (GB300's FP64 pipe is narrow).  gap2 is an
+            // integer, so gap2 <= that exactly when gap2 <= its floor
+            const double Rg = (double)R / (double)unit;
+            const double Rg2m = Rg * Rg * (1.0 + 1e-5) + 4.0;
+            S.rg2i = Rg2m >= 4.0e18 ? 0x7fffffffffffffffll : (long long)Rg2m;
+        }
         __syncthreads();
         for (int i = ga.x + tid; i < ga.x + ga.y; i += KN_THREADS) {
             atomicMin(&S.bmin[0], p.gcx[i]); atomicMax(&S.bmax[0], p.gcx[i]);
@@ -301,11 +310,7 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
             blo[a] = (float)(b0[a] - gref[a]) * unit;
             bhi[a] = (float)(b1[a] + 1 - gref[a]) * unit;
         }
-        const double Rg = (double)R / (double)unit;  // radius in grid units
-        const double Rg2m = Rg * Rg * (1.0 + 1e-5) + 4.0;
-        // the node test compares integers: gap2 is an integer, so gap2 <= Rg2m
-        // exactly when gap2 <= floor(Rg2m) (no FP64 per visited node)
-        const long long Rg2i = Rg2m >= 4.0e18 ? 0x7fffffffffffffffll : (long long)Rg2m;
+        const long long Rg2i = S.rg2i;
         const float R2stage = R * R * (1.f + 1e-4f) + 4.f * unit * unit;
         int2 *leafl = reinterpret_cast<int2 *>(&S.bkt[0][0]);
         int *lpre = reinterpret_cast<int *>(leafl + KN_LEAF);
@@ -612,7 +617,7 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
                 h64 = __shfl_sync(0xffffffffu, h64, hs);
                 __syncwarp();
                 // density and EOS over the 64 neighbours
-                const float hh = (float)sqrt(hsq);
+                const float hh = sqrtf((float)hsq);  // within one FP32 rounding of sqrt(h^2)
                 const float hinv = 1.f / hh;
                 float rs = 0.f, qs = 0.f;
                 for (int e = lane; e < NGB; e += 32) {
