@@ -214,30 +214,35 @@ __global__ void __launch_bounds__(256) k_vox_scatter(int n, const int *__restric
 }
 
 // standardised channels; FP32 [r][v][5] and/or BF16 [r][2][v][8] (the U-Net's
-// input: 16 channels blocked by 8, vs voxels per region)
-__global__ void k_vox_finalize(const float *__restrict__ acc, long long nv, long long vs, float *__restrict__ out,
-                               bf16 *__restrict__ outb)
+// input: 16 channels blocked by 8, vs voxels per region).  blockIdx.y is the
+// region; each voxel's sums are read as two float4 and its eight BF16
+// channels of each block stored as one 16-byte word.
+__global__ void __launch_bounds__(256) k_vox_finalize(const float *__restrict__ acc, int vs, float *__restrict__ out,
+                                                     bf16 *__restrict__ outb)
 {
-    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nv) return;
-    const float *a = acc + v * 8;
-    float rho_v = a[0], den = a[1];
-    float T = den > 0.f ? a[2] / den : 10.f;
+    const int sv = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sv >= vs) return;
+    const size_t r = blockIdx.y, v = r * (size_t)vs + sv;
+    const float4 a0 = reinterpret_cast<const float4 *>(acc)[2 * v];
+    const float4 a1 = reinterpret_cast<const float4 *>(acc)[2 * v + 1];
+    const float rho_v = a0.x, den = a0.y;
+    const float T = den > 0.f ? a0.z / den : 10.f;
     float z[5];
     z[0] = log10f(fmaxf(rho_v, 1e-4f)) + 0.33f;
     z[1] = (log10f(fmaxf(T, 10.f)) - 2.f) * 0.5f;
-    for (int c = 0; c < 3; c++) z[2 + c] = den > 0.f ? a[3 + c] / den / 20.f : 0.f;
+    z[2] = den > 0.f ? a0.w / den / 20.f : 0.f;
+    z[3] = den > 0.f ? a1.x / den / 20.f : 0.f;
+    z[4] = den > 0.f ? a1.y / den / 20.f : 0.f;
     if (out)
         for (int c = 0; c < 5; c++) out[v * 5 + c] = z[c];
     if (outb) {
-        long long r = v / vs, sv = v - r * vs;
-        bf16 *b0 = outb + (r * 2 * vs + sv) * 8;
-        for (int c = 0; c < 8; c++) b0[c] = __float2bfloat16_rn(c < 5 ? z[c] : 0.f);
-        bf16 *b1 = b0 + vs * 8;
-        for (int c = 0; c < 8; c++) b1[c] = __float2bfloat16_rn(0.f);
+        __nv_bfloat162 h[4] = {__floats2bfloat162_rn(z[0], z[1]), __floats2bfloat162_rn(z[2], z[3]),
+                               __floats2bfloat162_rn(z[4], 0.f), __floats2bfloat162_rn(0.f, 0.f)};
+        uint4 *b0 = reinterpret_cast<uint4 *>(outb + (r * 2 * vs + sv) * 8);
+        *b0 = *reinterpret_cast<const uint4 *>(h);
+        b0[vs] = make_uint4(0u, 0u, 0u, 0u);  // channels 8..15 of the block layout
     }
 }
-
 
 __global__ void k_remap_weights(const float *__restrict__ pred, long long nv, int cout, double *__restrict__ w)
 {
@@ -551,8 +556,12 @@ static int vox_regions_view(gnb_ctx *c, const PArr &a, int n, const int *reg, co
                                                           c->vpb, c->vpc, c->vbox);
     counted(k_vox_scatter)<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, reg, r0, r1, c->vpa, c->vpb, c->vpc,
                                                                        c->vbox, side, grid, c->vacc);
-    counted(k_vox_finalize)<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(
-        c->vacc, (long long)nv, V, out ? out + (size_t)r0 * V * 5 : nullptr, outb ? outb + (size_t)r0 * V * 16 : nullptr);
+    for (int q0 = r0; q0 < r1; q0 += 65535) {  // gridDim.y holds at most 65,535 regions
+        const int q1 = std::min(r1, q0 + 65535);
+        counted(k_vox_finalize)<<<dim3((unsigned)((V + 255) / 256), (unsigned)(q1 - q0)), 256, 0, st>>>(
+            c->vacc + (size_t)(q0 - r0) * V * 8, (int)V, out ? out + (size_t)q0 * V * 5 : nullptr,
+            outb ? outb + (size_t)q0 * V * 16 : nullptr);
+    }
     GNB_LAUNCH_CHECK(c, "voxelise");
     return GNB_OK;
 }
