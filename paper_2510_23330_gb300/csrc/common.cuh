@@ -157,7 +157,7 @@ struct gnb_ctx {
     // supernova surrogate (surrogate.cu)
     int *sreg = nullptr;          // region of each particle slot (-1: none)
     int *rcount = nullptr;        // members per region
-    float *vacc = nullptr;        // voxel accumulators [nreg][grid^3][8] (six used)
+    float *vacc = nullptr;        // voxel accumulators: [voxels][4], then [voxels / 2][4] (see k_vox_scatter)
     float *vout = nullptr;        // standardised channels [nreg][grid^3][5]
     double *vw = nullptr;         // remap weights [nreg][grid^3]
     double *vcdf = nullptr;       // remap line CDFs [nreg][axis][grid^2 lines][grid]

@@ -151,16 +151,20 @@ __device__ __forceinline__ float m4_shape(float q)
 
 // Pass 2, one thread per member particle: the six kernel-weighted terms
 // {m W, (m/rho) W, T (m/rho) W, v (m/rho) W} of every voxel inside the
-// particle's support are added to acc[r][v][8] (six used, padded to 32 bytes)
-// with two vector reductions (red.global.add.v4.f32 + .v2.f32, resolved at
-// L2).  The thread walks the (y, z) rows of the footprint box and, in each
-// row, only the x-range that can lie inside the support (conservatively
-// wide; the exact r^2 test decides), so only voxels near the support sphere
-// are visited.  Neighbouring threads take neighbouring particles (Morton
-// order): their smoothing lengths and footprints are alike, so the lanes of
-// a warp run loops of similar length, and their reductions hit voxels that
-// are close in memory.  The L2 reduction rate bounds this pass (one atomic
-// operation per vector reduction); no FP64 arithmetic runs here.
+// particle's support are added with vector reductions resolved at L2: the
+// first four to accA[r][v][4] (red.global.add.v4.f32), the last two to
+// accB[r][v / 2][4], which holds them for the voxel pair (2u, 2u + 1) side
+// by side, so that two neighbouring voxels of a row take one v4 reduction
+// (a voxel without its partner, one v2).  One reduction costs one L2
+// operation at any width, and the pass is bound by their number: 1.5 per
+// deposit instead of 2.  The thread walks the (y, z) rows of the footprint
+// box and, in each row, only the x-range that can lie inside the support
+// (conservatively wide; the exact r^2 test decides), so only voxels near the
+// support sphere are visited.  Neighbouring threads take neighbouring
+// particles (Morton order): their smoothing lengths and footprints are
+// alike, so the lanes of a warp run loops of similar length, and their
+// reductions hit voxels that are close in memory.  No FP64 arithmetic runs
+// here.
 __device__ __forceinline__ void red_v4(float *a, float x, float y, float z, float w)
 {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(a), "f"(x), "f"(y), "f"(z), "f"(w)
@@ -174,9 +178,10 @@ __device__ __forceinline__ void red_v2(float *a, float x, float y)
 __global__ void __launch_bounds__(256) k_vox_scatter(int n, const int *__restrict__ reg, int r0, int r1,
                                                      const float4 *__restrict__ vpa, const float4 *__restrict__ vpb,
                                                      const float4 *__restrict__ vpc, const int *__restrict__ vbox,
-                                                     double side, int grid, float *__restrict__ acc8)
+                                                     double side, int grid, float *__restrict__ accA,
+                                                     float *__restrict__ accB)
 {
-    // members of regions [r0, r1); acc8 holds those regions
+    // members of regions [r0, r1); accA and accB hold those regions
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int r = reg[i];
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(256) k_vox_scatter(int n, const int *__restric
     const int bx = vbox[i], bz = __float_as_int(pc.w);
     const int x0 = bx & 0xff, x1 = (bx >> 8) & 0xff, y0 = (bx >> 16) & 0xff, y1 = (bx >> 24) & 0xff;
     const int z0 = bz >> 16, z1 = bz & 0xffff;
-    float *base = acc8 + (size_t)(r - r0) * G * G * G * 8;
+    const size_t vbase = (size_t)(r - r0) * G * G * G;
     for (int iz = z0; iz <= z1; iz++) {
         const float dz = (iz + 0.5f) * df - pa.z;
         for (int iy = y0; iy <= y1; iy++) {
@@ -198,16 +203,31 @@ __global__ void __launch_bounds__(256) k_vox_scatter(int n, const int *__restric
             const float sx = sqrtf(rem);
             const int lo = max(x0, (int)floorf((pa.x - sx) * idf - 0.5f));
             const int hi = min(x1, (int)ceilf((pa.x + sx) * idf - 0.5f));
-            float *q = base + (((size_t)iz * G + iy) * G + lo) * 8;
-            for (int ix = lo; ix <= hi; ix++, q += 8) {
+            const size_t vrow = vbase + ((size_t)iz * G + iy) * G;
+            // (vy, vz) terms of an even voxel wait for their odd partner
+            bool pend = false;
+            float p4 = 0.f, p5 = 0.f;
+            for (int ix = lo; ix <= hi; ix++) {
+                const size_t v = vrow + ix;
                 const float dx = (ix + 0.5f) * df - pa.x;
                 const float r2 = dx * dx + dyz2;
-                if (r2 >= pa.w) continue;
-                const float w = m4_shape(sqrtf(r2) * pb.x);
-                if (w <= 0.f) continue;
+                float w = 0.f;
+                if (r2 < pa.w) w = m4_shape(sqrtf(r2) * pb.x);
+                const bool dep = w > 0.f;
                 const float ww = pb.z * w;
-                red_v4(q, pb.y * w, ww, pb.w * ww, pc.x * ww);
-                red_v2(q + 4, pc.y * ww, pc.z * ww);
+                if (dep) red_v4(accA + v * 4, pb.y * w, ww, pb.w * ww, pc.x * ww);
+                float *qb = accB + (v >> 1) * 4;
+                if ((v & 1) == 0) {
+                    if (dep) {
+                        if (ix == hi) red_v2(qb, pc.y * ww, pc.z * ww);
+                        else { pend = true; p4 = pc.y * ww; p5 = pc.z * ww; }
+                    }
+                } else {
+                    if (pend && dep) red_v4(qb, p4, p5, pc.y * ww, pc.z * ww);
+                    else if (pend) red_v2(qb, p4, p5);
+                    else if (dep) red_v2(qb + 2, pc.y * ww, pc.z * ww);
+                    pend = false;
+                }
             }
         }
     }
@@ -217,14 +237,15 @@ __global__ void __launch_bounds__(256) k_vox_scatter(int n, const int *__restric
 // input: 16 channels blocked by 8, vs voxels per region).  blockIdx.y is the
 // region; each voxel's sums are read as two float4 and its eight BF16
 // channels of each block stored as one 16-byte word.
-__global__ void __launch_bounds__(256) k_vox_finalize(const float *__restrict__ acc, int vs, float *__restrict__ out,
+__global__ void __launch_bounds__(256) k_vox_finalize(const float *__restrict__ accA, const float *__restrict__ accB,
+                                                     size_t v0, int vs, float *__restrict__ out,
                                                      bf16 *__restrict__ outb)
 {
     const int sv = blockIdx.x * blockDim.x + threadIdx.x;
     if (sv >= vs) return;
-    const size_t r = blockIdx.y, v = r * (size_t)vs + sv;
-    const float4 a0 = reinterpret_cast<const float4 *>(acc)[2 * v];
-    const float4 a1 = reinterpret_cast<const float4 *>(acc)[2 * v + 1];
+    const size_t r = blockIdx.y, v = r * (size_t)vs + sv, va = v0 + v;  // va: index in the accumulators
+    const float4 a0 = reinterpret_cast<const float4 *>(accA)[va];
+    const float2 a1 = reinterpret_cast<const float2 *>(accB)[(va >> 1) * 2 + (va & 1)];
     const float rho_v = a0.x, den = a0.y;
     const float T = den > 0.f ? a0.z / den : 10.f;
     float z[5];
@@ -551,15 +572,17 @@ static int vox_regions_view(gnb_ctx *c, const PArr &a, int n, const int *reg, co
 {
     const long long V = (long long)grid * grid * grid;
     size_t nv = (size_t)(r1 - r0) * V;
-    cudaMemsetAsync(c->vacc, 0, sizeof(float) * nv * 8, st);
+    // accumulators: accA [nv][4], then accB [(nv + 1) / 2][4] (see k_vox_scatter)
+    float *accA = c->vacc, *accB = c->vacc + nv * 4;
+    cudaMemsetAsync(c->vacc, 0, sizeof(float) * (nv * 4 + (nv + 1) / 2 * 4), st);
     counted(k_vox_stage)<<<(n + 255) / 256, 256, 0, st>>>(a, n, reg, r0, r1, rho, c->cent_d, side, grid, c->vpa,
                                                           c->vpb, c->vpc, c->vbox);
     counted(k_vox_scatter)<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, reg, r0, r1, c->vpa, c->vpb, c->vpc,
-                                                                       c->vbox, side, grid, c->vacc);
+                                                                       c->vbox, side, grid, accA, accB);
     for (int q0 = r0; q0 < r1; q0 += 65535) {  // gridDim.y holds at most 65,535 regions
         const int q1 = std::min(r1, q0 + 65535);
         counted(k_vox_finalize)<<<dim3((unsigned)((V + 255) / 256), (unsigned)(q1 - q0)), 256, 0, st>>>(
-            c->vacc + (size_t)(q0 - r0) * V * 8, (int)V, out ? out + (size_t)q0 * V * 5 : nullptr,
+            accA, accB, (size_t)(q0 - r0) * V, (int)V, out ? out + (size_t)q0 * V * 5 : nullptr,
             outb ? outb + (size_t)q0 * V * 16 : nullptr);
     }
     GNB_LAUNCH_CHECK(c, "voxelise");
