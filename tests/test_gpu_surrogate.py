@@ -164,18 +164,22 @@ def test_batched_surrogate_step_matches_oracle_remap(G, orc):
 
 def test_pipelined_batch_matches_sequential(G, orc):
     """The batch pipelined over region chunks (voxelise / U-Net / remap of
-    different chunks on three streams, one captured graph) against the same
-    batch with its stages in sequence.  Without Gibbs sweeps each member
-    keeps its voxel and draws a new offset inside it, so positions must be
-    bit-identical; u and v come from that voxel's prediction.  The voxel sums
-    are FP32 reductions in no fixed order, and the last-bit differences reach
-    the network's BF16 input, so two sequential runs already differ: the
-    pipelined run must differ from a sequential one no more than two
-    sequential runs do (a chunk that read another chunk's grid or
-    predictions would differ by far more)."""
-    from oracle import unet as U
+    different chunks on three streams, one captured graph), with eight Gibbs
+    sweeps.  Every member of region r ends where the oracle's remap of r puts
+    it, given the prediction the pipelined batch itself computed (voxel
+    choices bit for bit, positions within 1e-12 of the side, u and v within
+    1e-6 relative): each chunk's remap read its own regions' prediction and
+    line sums.  And that prediction equals the sequential batch's up to the
+    network's BF16 rounding of its input: the voxel sums are FP32 reductions
+    in no fixed order, so a few inputs may round to the other BF16
+    neighbour, which moves a region's prediction by ~1e-3 (relative L2);
+    a chunk that read another chunk's grid would move it by O(1).  (The
+    difference between two sequential runs is no yardstick: they often
+    agree bit for bit, and sometimes by the same ~1e-3.)"""
     import torch
+    from oracle import surrogate as S
     stream = torch.cuda.Stream()
+    side, grid, seed = 60.0, 32, 5
     with torch.cuda.stream(stream):
         regions = [ics.sn_region(6000 + 2000 * k, seed=30 + k, grid=32) for k in range(5)]
         offs = [(150.0 * k, 40.0 * k, 0.0) for k in range(5)]
@@ -187,35 +191,42 @@ def test_pipelined_batch_matches_sequential(G, orc):
             for key, val in r.items():
                 parts.setdefault(key, []).append(val)
         p = {k: np.concatenate(v) for k, v in parts.items()}
-        p["id"] = np.arange(p["x"].size, dtype=np.int64)
-        net = G.UNet(5, 5, 16, 4, 32, stream=stream.cuda_stream)
-        spec = U.layer_spec(5, 5, 16, 4)
-        prm = U.init_params(3, 5, 5, 16, 4)
-        net.set_params(np.concatenate([np.concatenate([prm[n + ".w"].ravel(), prm[n + ".b"]])
-                                       for n, *_ in spec]).astype(np.float32))
-        out = []
-        for chunks in (1, 1, 3):
+        p["id"] = np.arange(p["x"].size, dtype=np.int64) * 3 + 1
+        net = _net32(G, stream)
+        preds, outs = [], []
+        for chunks in (1, 3):
             c = G.Context(stream=stream.cuda_stream)
             c.set_particles(p)
             c.set_sn_chunks(chunks)
             c.compute_sph_density()
-            c.sn_surrogate_batch(net, offs, side=60.0, seed=5, sweeps=0, use_graph=True)
-            out.append({k: c.get(k) for k in ("X", "Y", "Z", "U", "VX", "VY", "VZ", "ID")})
+            c.sn_surrogate_batch(net, offs, side=side, seed=seed, sweeps=8, use_graph=True)
+            preds.append(net.get_output(len(offs)))
+            outs.append({k: c.get(k) for k in ("X", "Y", "Z", "U", "VX", "VY", "VZ", "ID")})
             c.close()
     stream.synchronize()
-    s1, s2, pp = out
-    assert np.array_equal(pp["ID"], p["id"])
-    assert (pp["X"] != p["x"]).mean() > 0.9  # the members were remapped
-    for k in ("X", "Y", "Z"):
-        assert np.array_equal(s1[k], pp[k]) and np.array_equal(s1[k], s2[k])
-
-    def spread(a, b):
-        d = [np.abs(a["U"] / b["U"] - 1.0)] + [np.abs(a[k] - b[k]) / 20.0 for k in ("VX", "VY", "VZ")]
-        return np.median(np.concatenate(d)), max(float(np.max(x)) for x in d)
-
-    med_ss, max_ss = spread(s1, s2)
-    med_sp, max_sp = spread(s1, pp)
-    assert med_sp <= 2.0 * med_ss + 2e-3 and max_sp <= 2.0 * max_ss + 0.05, (med_sp, med_ss, max_sp, max_ss)
+    pred_s, pred_p = preds
+    got = outs[1]
+    for r in range(len(offs)):
+        d = np.linalg.norm(pred_p[r] - pred_s[r]) / np.linalg.norm(pred_s[r])
+        assert d < 2e-2, (r, d)
+    s = orc.state(p)
+    reg = S.members(s, offs, side)
+    newp = np.stack([got["X"], got["Y"], got["Z"]], axis=1)
+    pos0 = np.stack([s["x"], s["y"], s["z"]], axis=1)
+    assert np.array_equal(got["ID"], p["id"])
+    assert np.array_equal(newp[reg < 0], pos0[reg < 0])
+    for r, cen in enumerate(offs):
+        mem = np.nonzero(reg == r)[0]
+        assert mem.size > 1000
+        vox, rp, ru, rv = S.remap(pred_p[r].reshape(-1, 5).astype(np.float64), p["id"][mem], pos0[mem], cen, side,
+                                  grid, seed=seed, sweeps=8)
+        lo = np.asarray(cen) - 0.5 * side
+        gv = np.floor((newp[mem] - lo) / (side / grid)).astype(np.int64)
+        assert np.array_equal(gv, vox), r
+        assert np.max(np.abs(newp[mem] - rp)) < 1e-12 * side
+        assert np.allclose(got["U"][mem], ru, rtol=1e-6)
+        v = np.stack([got["VX"], got["VY"], got["VZ"]], axis=1)[mem]
+        assert np.allclose(v, rv, rtol=1e-6, atol=1e-6)
 
 
 def _net32(G, stream):
