@@ -199,6 +199,113 @@ __device__ __forceinline__ void pc_loopN(const GravSmem &S, int buf, int nc, int
     }
 }
 
+// Packed form for two or more i-particles per thread: the thread's particles
+// in pairs, one per lane of a float2, evaluated with the FP32x2 instructions
+// of sm_100 and later (fma.rn.f32x2, add.rn.f32x2, mul.rn.f32x2: two FP32
+// operations per issued instruction, each lane rounded as the scalar one).
+// The same operations as pp_one / pc_one on each lane, so the sums are the
+// scalar ones bit for bit; the positions are held negated (nx = -x_i), which
+// turns x_j - x_i into one addition, and the cell terms are written for
+// -r = com - x_i (every sign flip is exact).
+template <int NP>
+struct IPair {
+    float2 nx[NP], ny[NP], nz[NP], e2[NP];
+};
+template <int NP>
+struct APair {
+    float2 ax[NP], ay[NP], az[NP], ph[NP];
+};
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+template <bool MASK>
+__device__ __forceinline__ float2 rsqrt2(float2 r2)
+{
+    float2 r;
+    if (MASK) {
+        r.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
+        r.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+    } else {
+        r.x = rsqrt_pos(r2.x);
+        r.y = rsqrt_pos(r2.y);
+    }
+    return r;
+}
+
+template <bool MASK>
+__device__ __forceinline__ void pp_two(float4 q, float e, float2 nx, float2 ny, float2 nz, float2 e2i, float2 &ax,
+                                       float2 &ay, float2 &az, float2 &ph)
+{
+    const float2 dx = __fadd2_rn(bc2(q.x), nx), dy = __fadd2_rn(bc2(q.y), ny), dz = __fadd2_rn(bc2(q.z), nz);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, __fadd2_rn(bc2(e), e2i))));
+    const float2 ri = rsqrt2<MASK>(r2);
+    const float2 mr = __fmul2_rn(bc2(q.w), ri);
+    const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
+    ax = __ffma2_rn(mr3, dx, ax);
+    ay = __ffma2_rn(mr3, dy, ay);
+    az = __ffma2_rn(mr3, dz, az);
+    ph = __fadd2_rn(ph, mr);
+}
+
+// pc_one on two lanes with s = -r: R^2 and r.Q.r are even in r, Q s = -Q r,
+// so  a += (Q r)/R^5 - t r  becomes  a += (Q s)(-1/R^5) + t s.
+template <bool QUAD>
+__device__ __forceinline__ void pc_two(float4 a, float4 b, float4 d, float2 nx, float2 ny, float2 nz, float2 e2i,
+                                       float2 &ax, float2 &ay, float2 &az, float2 &ph)
+{
+    const float2 sx = __fadd2_rn(bc2(a.x), nx), sy = __fadd2_rn(bc2(a.y), ny), sz = __fadd2_rn(bc2(a.z), nz);
+    const float2 R2 = __ffma2_rn(sx, sx, __ffma2_rn(sy, sy, __ffma2_rn(sz, sz, __fadd2_rn(e2i, bc2(d.z)))));
+    const float2 Ri = rsqrt2<false>(R2);
+    const float2 Ri2 = __fmul2_rn(Ri, Ri);
+    const float2 Ri3 = __fmul2_rn(Ri, Ri2);
+    if (QUAD) {
+        const float2 qx = __ffma2_rn(bc2(b.x), sx, __ffma2_rn(bc2(b.w), sy, __fmul2_rn(bc2(d.x), sz)));
+        const float2 qy = __ffma2_rn(bc2(b.w), sx, __ffma2_rn(bc2(b.y), sy, __fmul2_rn(bc2(d.y), sz)));
+        const float2 qz = __ffma2_rn(bc2(d.x), sx, __ffma2_rn(bc2(d.y), sy, __fmul2_rn(bc2(b.z), sz)));
+        const float2 rqr = __ffma2_rn(sx, qx, __ffma2_rn(sy, qy, __fmul2_rn(sz, qz)));
+        const float2 Ri5 = __fmul2_rn(Ri3, Ri2);
+        const float2 rqr5 = __fmul2_rn(rqr, Ri5);
+        const float2 t = __ffma2_rn(rqr5, __fmul2_rn(bc2(2.5f), Ri2), __fmul2_rn(bc2(a.w), Ri3));
+        const float2 nR5 = make_float2(-Ri5.x, -Ri5.y);
+        ax = __ffma2_rn(t, sx, __ffma2_rn(qx, nR5, ax));
+        ay = __ffma2_rn(t, sy, __ffma2_rn(qy, nR5, ay));
+        az = __ffma2_rn(t, sz, __ffma2_rn(qz, nR5, az));
+        ph = __ffma2_rn(bc2(0.5f), rqr5, __ffma2_rn(bc2(a.w), Ri, ph));
+    } else {
+        const float2 mR3 = __fmul2_rn(bc2(a.w), Ri3);
+        ax = __ffma2_rn(mR3, sx, ax);
+        ay = __ffma2_rn(mR3, sy, ay);
+        az = __ffma2_rn(mR3, sz, az);
+        ph = __ffma2_rn(bc2(a.w), Ri, ph);
+    }
+}
+
+template <int NP, bool MASK>
+__device__ __forceinline__ void pp_loopP(const GravSmem &S, int np, int split, int js, const IPair<NP> &I,
+                                         APair<NP> &A)
+{
+#pragma unroll 2
+    for (int j = split; j < np; j += js) {
+        const float4 q = S.jp[j];
+        const float e = S.je[j];
+#pragma unroll
+        for (int k = 0; k < NP; k++)
+            pp_two<MASK>(q, e, I.nx[k], I.ny[k], I.nz[k], I.e2[k], A.ax[k], A.ay[k], A.az[k], A.ph[k]);
+    }
+}
+
+template <int NP, bool QUAD>
+__device__ __forceinline__ void pc_loopP(const GravSmem &S, int buf, int nc, int split, int js, const IPair<NP> &I,
+                                         APair<NP> &A)
+{
+    for (int c = split; c < nc; c += js) {
+        const float4 a = S.c0[buf][c], b = S.c1[buf][c], d = S.c2[buf][c];
+#pragma unroll
+        for (int k = 0; k < NP; k++)
+            pc_two<QUAD>(a, b, d, I.nx[k], I.ny[k], I.nz[k], I.e2[k], A.ax[k], A.ay[k], A.az[k], A.ph[k]);
+    }
+}
+
 __device__ __forceinline__ int block_scan_excl(int v, int *ws, int *tot)
 {
     int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
@@ -463,7 +570,12 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
     const int js = GW_THREADS / ilanes;
     const int islot = tid % ilanes, split = tid / ilanes;
     const bool ivalid = split < js;
+    // one i-particle: scalar arithmetic; more: packed pairs (pp_two, pc_two)
+    constexpr bool PK = NI >= 2;
+    constexpr int NP = PK ? NI / 2 : 1;
     float4 pi[NI], acc[NI];
+    IPair<NP> I;
+    APair<NP> A;
 #pragma unroll
     for (int k = 0; k < NI; k++) {
         const int sl = islot + k * ilanes;
@@ -472,6 +584,16 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
         pi[k] = make_float4(grid_off(p.cx[ip], gref[0], p.rx[ip], unit), grid_off(p.cy[ip], gref[1], p.ry[ip], unit),
                             grid_off(p.cz[ip], gref[2], p.rz[ip], unit), ep * ep);
         acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if constexpr (PK) {
+#pragma unroll
+        for (int h = 0; h < NP; h++) {
+            I.nx[h] = make_float2(-pi[2 * h].x, -pi[2 * h + 1].x);
+            I.ny[h] = make_float2(-pi[2 * h].y, -pi[2 * h + 1].y);
+            I.nz[h] = make_float2(-pi[2 * h].z, -pi[2 * h + 1].z);
+            I.e2[h] = make_float2(pi[2 * h].w, pi[2 * h + 1].w);
+            A.ax[h] = A.ay[h] = A.az[h] = A.ph[h] = make_float2(0.f, 0.f);
+        }
     }
     // accepted cells, one chunk at a time, double buffered: while a chunk is
     // evaluated, cp.async fills the other buffer with the next chunk (whose
@@ -524,7 +646,10 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
                 S.je[k] = ej * ej;
             }
             __syncthreads();
-            if (ivalid) pp_loopN<NI, MASK>(S, np, split, js, pi, acc);
+            if (ivalid) {
+                if constexpr (PK) pp_loopP<NP, MASK>(S, np, split, js, I, A);
+                else pp_loopN<NI, MASK>(S, np, split, js, pi, acc);
+            }
             __syncthreads();
         }
         lch = lnx;
@@ -545,7 +670,10 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
                 idx2[1] = p.pool[(size_t)nxt2 * GL_CH + tid + GW_THREADS];
             }
         }
-        if (ivalid) pc_loopN<NI, QUAD>(S, cb, nc, split, js, pi, acc);
+        if (ivalid) {
+            if constexpr (PK) pc_loopP<NP, QUAD>(S, cb, nc, split, js, I, A);
+            else pc_loopN<NI, QUAD>(S, cb, nc, split, js, pi, acc);
+        }
         if (cnx >= 0) {
             cp_async_wait_all_g();
             cells_convert(S, cb ^ 1, gref, unit);
@@ -560,6 +688,13 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
     // reduce the j-splits: the partial sums of particle slots k0 .. k0 + RB - 1
     // at a time go through the PP staging buffer (idle here)
     constexpr int RB = GW_JP / GW_THREADS;
+    if constexpr (PK) {
+#pragma unroll
+        for (int h = 0; h < NP; h++) {
+            acc[2 * h] = make_float4(A.ax[h].x, A.ay[h].x, A.az[h].x, A.ph[h].x);
+            acc[2 * h + 1] = make_float4(A.ax[h].y, A.ay[h].y, A.az[h].y, A.ph[h].y);
+        }
+    }
 #pragma unroll
     for (int k0 = 0; k0 < NI; k0 += RB) {
 #pragma unroll
