@@ -188,6 +188,7 @@ __global__ void k_validate(PArr p, int n, int *bad)
     if (!(p.m[i] > 0.f) || !isfinite(p.m[i])) b |= 4;
     if (!(p.eps[i] >= 0.f) || !isfinite(p.eps[i])) b |= 8;
     if (p.eps[i] == 0.f) b |= 16;
+    if (p.eps[i] != p.eps[0]) b |= 32;
     if (b) atomicOr(bad, b);
 }
 
@@ -356,6 +357,7 @@ int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *t
     GNB_LAUNCH_CHECK(c, "set particles");
     cudaMemcpyAsync(c->pinned_i + 1, c->work_d, sizeof(int), cudaMemcpyDeviceToHost, c->s);
     cudaMemcpyAsync(c->pinned_i + 2, c->ngas_d, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(c->pinned_i + 3, p.eps, sizeof(float), cudaMemcpyDeviceToHost, c->s);
     GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "set particles sync"));
     int bad = c->pinned_i[1];
     int ng = c->pinned_i[2];
@@ -365,6 +367,8 @@ int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *t
     if (bad & 8) return fail(c, GNB_EINVAL, "softening must be non-negative and finite");
     if (ng > 0 && ng < c->cfg.n_ngb) return fail(c, GNB_EINVAL, "fewer gas particles than SPH neighbours");
     c->min_eps_zero = (bad & 16) != 0;
+    memcpy(&c->eps0, c->pinned_i + 3, sizeof(float));
+    c->eps_uniform = !(bad & (16 | 32));
     c->n = n;
     c->n_gas = ng;
     GNB_TRY(alloc_gas(c, ng));

@@ -95,6 +95,8 @@ struct gnb_ctx {
     int64_t n = 0, n_gas = 0;
     int64_t cap = 0;          // particle capacity
     bool min_eps_zero = false;
+    bool eps_uniform = false;  // every particle has the softening eps0 > 0
+    float eps0 = 0.f;
 
     gnb::PArr P[2];
     int cur = 0;              // P[cur] holds the particles

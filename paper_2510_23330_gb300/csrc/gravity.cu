@@ -44,6 +44,7 @@ struct GravParams {
     double theta2;
     long long open_d2max[GNB_MAXLEV + 1];  // per level: largest d2 that opens a cell (see must_open)
     float G;
+    float e2u;  // 2 fl(eps^2) when every particle has the same softening eps > 0
     int quad;
     int n;
     int *next;
@@ -105,9 +106,11 @@ __device__ __forceinline__ float rsqrt_pos(float x)
     return r;
 }
 
-// Particle-particle: accumulate sum m_j (x_j - x_i)/R^3 and sum m_j/R, with
-// R^2 = |x_j - x_i|^2 + eps_i^2 + eps_j^2.  MASK (some softening is zero): a
-// pair at R = 0 (the particle itself) contributes nothing.
+// Particle-particle: with q.w = -m_j (staged negated), accumulate
+// -sum m_j (x_j - x_i)/R^3 and -sum m_j/R, with R^2 = |x_j - x_i|^2 + eps_i^2
+// + eps_j^2.  Every sum is accumulated negated (the cell terms below need no
+// sign flips that way) and negated once at the end.  MASK (some softening is
+// zero): a pair at R = 0 (the particle itself) contributes nothing.
 template <bool MASK>
 __device__ __forceinline__ void pp_one(float4 q, float e, float xi, float yi, float zi, float e2i, float &ax,
                                        float &ay, float &az, float &ph)
@@ -153,34 +156,38 @@ __device__ __forceinline__ void pp_loopN(const GravSmem &S, int np, int split, i
 // Particle-cell with monopole (+ traceless quadrupole), r = x_i - com:
 //   a   += -M r/R^3 + Q r/R^5 - 5/2 (r.Q.r) r/R^7
 //   phi += -M/R - 1/2 r.Q.r/R^5         (accumulated with the sign flipped)
-// evaluated as t = M/R^3 + 5/2 (r.Q.r/R^5)/R^2, a += (Q r)/R^5 - t r.
+// evaluated as t = M/R^3 + 5/2 (r.Q.r/R^5)/R^2, a += (Q r)/R^5 - t r.  In the
+// negated sums, with s = com - x_i = -r and a.w = -M (staged negated):
+// Q s = -Q r and s.Q.s = r.Q.r, so  -a += (Q s)/R^5 + (-t) s  and
+// -phi' += -M/R - 1/2 s.Q.s/R^5, every product the exact negation of the
+// one above (no sign flip costs an instruction).
 template <bool QUAD>
 __device__ __forceinline__ void pc_one(float4 a, float4 b, float4 d, float xi, float yi, float zi, float e2i,
                                        float &ax, float &ay, float &az, float &ph)
 {
-    float rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
-    float R2 = __fmaf_rn(rx, rx, __fmaf_rn(ry, ry, __fmaf_rn(rz, rz, e2i + d.z)));
+    float sx = a.x - xi, sy = a.y - yi, sz = a.z - zi;
+    float R2 = __fmaf_rn(sx, sx, __fmaf_rn(sy, sy, __fmaf_rn(sz, sz, e2i + d.z)));
     float Ri = rsqrt_pos(R2);
     float Ri2 = Ri * Ri;
     float Ri3 = Ri * Ri2;
     if (QUAD) {
-        float qx = __fmaf_rn(b.x, rx, __fmaf_rn(b.w, ry, d.x * rz));
-        float qy = __fmaf_rn(b.w, rx, __fmaf_rn(b.y, ry, d.y * rz));
-        float qz = __fmaf_rn(d.x, rx, __fmaf_rn(d.y, ry, b.z * rz));
-        float rqr = __fmaf_rn(rx, qx, __fmaf_rn(ry, qy, rz * qz));
+        float qx = __fmaf_rn(b.x, sx, __fmaf_rn(b.w, sy, d.x * sz));
+        float qy = __fmaf_rn(b.w, sx, __fmaf_rn(b.y, sy, d.y * sz));
+        float qz = __fmaf_rn(d.x, sx, __fmaf_rn(d.y, sy, b.z * sz));
+        float rqr = __fmaf_rn(sx, qx, __fmaf_rn(sy, qy, sz * qz));
         float Ri5 = Ri3 * Ri2;
         float rqr5 = rqr * Ri5;
-        float t = __fmaf_rn(rqr5, 2.5f * Ri2, a.w * Ri3);
-        // two chained FMAs per component (Q r/R^5, then -t r)
-        ax = __fmaf_rn(-t, rx, __fmaf_rn(qx, Ri5, ax));
-        ay = __fmaf_rn(-t, ry, __fmaf_rn(qy, Ri5, ay));
-        az = __fmaf_rn(-t, rz, __fmaf_rn(qz, Ri5, az));
-        ph = __fmaf_rn(0.5f, rqr5, __fmaf_rn(a.w, Ri, ph));
+        float nt = __fmaf_rn(rqr5, -2.5f * Ri2, a.w * Ri3);  // -t
+        // two chained FMAs per component (Q s/R^5, then -t s)
+        ax = __fmaf_rn(nt, sx, __fmaf_rn(qx, Ri5, ax));
+        ay = __fmaf_rn(nt, sy, __fmaf_rn(qy, Ri5, ay));
+        az = __fmaf_rn(nt, sz, __fmaf_rn(qz, Ri5, az));
+        ph = __fmaf_rn(-0.5f, rqr5, __fmaf_rn(a.w, Ri, ph));
     } else {
-        float mR3 = a.w * Ri3;
-        ax = __fmaf_rn(-mR3, rx, ax);
-        ay = __fmaf_rn(-mR3, ry, ay);
-        az = __fmaf_rn(-mR3, rz, az);
+        float mR3 = a.w * Ri3;  // -M/R^3
+        ax = __fmaf_rn(mR3, sx, ax);
+        ay = __fmaf_rn(mR3, sy, ay);
+        az = __fmaf_rn(mR3, sz, az);
         ph = __fmaf_rn(a.w, Ri, ph);
     }
 }
@@ -205,8 +212,11 @@ __device__ __forceinline__ void pc_loopN(const GravSmem &S, int buf, int nc, int
 // operations per issued instruction, each lane rounded as the scalar one).
 // The same operations as pp_one / pc_one on each lane, so the sums are the
 // scalar ones bit for bit; the positions are held negated (nx = -x_i), which
-// turns x_j - x_i into one addition, and the cell terms are written for
-// -r = com - x_i (every sign flip is exact).
+// turns x_j - x_i and com - x_i into one addition.  UNI (every particle has
+// the same softening eps > 0): eps_i^2 + eps_j^2 is the constant E2 =
+// 2 fl(eps^2) for every pair (the same value the general form adds up), and a
+// cell's mass-weighted eps^2 is eps^2, so the pair's softening term is E2
+// without an addition.
 template <int NP>
 struct IPair {
     float2 nx[NP], ny[NP], nz[NP], e2[NP];
@@ -232,12 +242,13 @@ __device__ __forceinline__ float2 rsqrt2(float2 r2)
     return r;
 }
 
-template <bool MASK>
-__device__ __forceinline__ void pp_two(float4 q, float e, float2 nx, float2 ny, float2 nz, float2 e2i, float2 &ax,
-                                       float2 &ay, float2 &az, float2 &ph)
+template <bool MASK, bool UNI>
+__device__ __forceinline__ void pp_two(float4 q, float e, float2 nx, float2 ny, float2 nz, float2 e2i, float2 E2,
+                                       float2 &ax, float2 &ay, float2 &az, float2 &ph)
 {
     const float2 dx = __fadd2_rn(bc2(q.x), nx), dy = __fadd2_rn(bc2(q.y), ny), dz = __fadd2_rn(bc2(q.z), nz);
-    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, __fadd2_rn(bc2(e), e2i))));
+    const float2 es = UNI ? E2 : __fadd2_rn(bc2(e), e2i);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, es)));
     const float2 ri = rsqrt2<MASK>(r2);
     const float2 mr = __fmul2_rn(bc2(q.w), ri);
     const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
@@ -247,14 +258,14 @@ __device__ __forceinline__ void pp_two(float4 q, float e, float2 nx, float2 ny, 
     ph = __fadd2_rn(ph, mr);
 }
 
-// pc_one on two lanes with s = -r: R^2 and r.Q.r are even in r, Q s = -Q r,
-// so  a += (Q r)/R^5 - t r  becomes  a += (Q s)(-1/R^5) + t s.
-template <bool QUAD>
+// pc_one on two lanes (s = com - x_i, a.w = -M, negated sums).
+template <bool QUAD, bool UNI>
 __device__ __forceinline__ void pc_two(float4 a, float4 b, float4 d, float2 nx, float2 ny, float2 nz, float2 e2i,
-                                       float2 &ax, float2 &ay, float2 &az, float2 &ph)
+                                       float2 E2, float2 &ax, float2 &ay, float2 &az, float2 &ph)
 {
     const float2 sx = __fadd2_rn(bc2(a.x), nx), sy = __fadd2_rn(bc2(a.y), ny), sz = __fadd2_rn(bc2(a.z), nz);
-    const float2 R2 = __ffma2_rn(sx, sx, __ffma2_rn(sy, sy, __ffma2_rn(sz, sz, __fadd2_rn(e2i, bc2(d.z)))));
+    const float2 es = UNI ? E2 : __fadd2_rn(e2i, bc2(d.z));
+    const float2 R2 = __ffma2_rn(sx, sx, __ffma2_rn(sy, sy, __ffma2_rn(sz, sz, es)));
     const float2 Ri = rsqrt2<false>(R2);
     const float2 Ri2 = __fmul2_rn(Ri, Ri);
     const float2 Ri3 = __fmul2_rn(Ri, Ri2);
@@ -265,12 +276,11 @@ __device__ __forceinline__ void pc_two(float4 a, float4 b, float4 d, float2 nx, 
         const float2 rqr = __ffma2_rn(sx, qx, __ffma2_rn(sy, qy, __fmul2_rn(sz, qz)));
         const float2 Ri5 = __fmul2_rn(Ri3, Ri2);
         const float2 rqr5 = __fmul2_rn(rqr, Ri5);
-        const float2 t = __ffma2_rn(rqr5, __fmul2_rn(bc2(2.5f), Ri2), __fmul2_rn(bc2(a.w), Ri3));
-        const float2 nR5 = make_float2(-Ri5.x, -Ri5.y);
-        ax = __ffma2_rn(t, sx, __ffma2_rn(qx, nR5, ax));
-        ay = __ffma2_rn(t, sy, __ffma2_rn(qy, nR5, ay));
-        az = __ffma2_rn(t, sz, __ffma2_rn(qz, nR5, az));
-        ph = __ffma2_rn(bc2(0.5f), rqr5, __ffma2_rn(bc2(a.w), Ri, ph));
+        const float2 nt = __ffma2_rn(rqr5, __fmul2_rn(bc2(-2.5f), Ri2), __fmul2_rn(bc2(a.w), Ri3));
+        ax = __ffma2_rn(nt, sx, __ffma2_rn(qx, Ri5, ax));
+        ay = __ffma2_rn(nt, sy, __ffma2_rn(qy, Ri5, ay));
+        az = __ffma2_rn(nt, sz, __ffma2_rn(qz, Ri5, az));
+        ph = __ffma2_rn(bc2(-0.5f), rqr5, __ffma2_rn(bc2(a.w), Ri, ph));
     } else {
         const float2 mR3 = __fmul2_rn(bc2(a.w), Ri3);
         ax = __ffma2_rn(mR3, sx, ax);
@@ -280,29 +290,29 @@ __device__ __forceinline__ void pc_two(float4 a, float4 b, float4 d, float2 nx, 
     }
 }
 
-template <int NP, bool MASK>
+template <int NP, bool MASK, bool UNI>
 __device__ __forceinline__ void pp_loopP(const GravSmem &S, int np, int split, int js, const IPair<NP> &I,
-                                         APair<NP> &A)
+                                         float2 E2, APair<NP> &A)
 {
 #pragma unroll 2
     for (int j = split; j < np; j += js) {
         const float4 q = S.jp[j];
-        const float e = S.je[j];
+        const float e = UNI ? 0.f : S.je[j];
 #pragma unroll
         for (int k = 0; k < NP; k++)
-            pp_two<MASK>(q, e, I.nx[k], I.ny[k], I.nz[k], I.e2[k], A.ax[k], A.ay[k], A.az[k], A.ph[k]);
+            pp_two<MASK, UNI>(q, e, I.nx[k], I.ny[k], I.nz[k], I.e2[k], E2, A.ax[k], A.ay[k], A.az[k], A.ph[k]);
     }
 }
 
-template <int NP, bool QUAD>
+template <int NP, bool QUAD, bool UNI>
 __device__ __forceinline__ void pc_loopP(const GravSmem &S, int buf, int nc, int split, int js, const IPair<NP> &I,
-                                         APair<NP> &A)
+                                         float2 E2, APair<NP> &A)
 {
     for (int c = split; c < nc; c += js) {
         const float4 a = S.c0[buf][c], b = S.c1[buf][c], d = S.c2[buf][c];
 #pragma unroll
         for (int k = 0; k < NP; k++)
-            pc_two<QUAD>(a, b, d, I.nx[k], I.ny[k], I.nz[k], I.e2[k], A.ax[k], A.ay[k], A.az[k], A.ph[k]);
+            pc_two<QUAD, UNI>(a, b, d, I.nx[k], I.ny[k], I.nz[k], I.e2[k], E2, A.ax[k], A.ay[k], A.az[k], A.ph[k]);
     }
 }
 
@@ -410,7 +420,8 @@ __device__ __forceinline__ void cells_issue(GravSmem &S, const GravParams &p, in
     cp_async_commit_g();
 }
 
-// Centre of mass as an FP32 offset from the group's reference grid cell.
+// Centre of mass as an FP32 offset from the group's reference grid cell, and
+// the mass negated (the sums are accumulated negated, see pc_one).
 __device__ __forceinline__ void cells_convert(GravSmem &S, int b, const int *gref, float unit)
 {
     for (int h = 0; h < 2; h++) {
@@ -418,7 +429,7 @@ __device__ __forceinline__ void cells_convert(GravSmem &S, int b, const int *gre
         const int4 C = S.cnb[s];
         const float4 m0 = S.c0[b][s];
         S.c0[b][s] = make_float4(grid_off(C.x, gref[0], m0.x, unit), grid_off(C.y, gref[1], m0.y, unit),
-                                 grid_off(C.z, gref[2], m0.z, unit), m0.w);
+                                 grid_off(C.z, gref[2], m0.z, unit), -m0.w);
     }
 }
 
@@ -561,7 +572,7 @@ __global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
 // and takes every js-th j entry, so a small group keeps the CTA busy; with
 // more i-particles per thread each staged j entry is read once for all of
 // them and fewer partial sums are left to reduce.
-template <int NI, bool MASK, bool QUAD>
+template <int NI, bool MASK, bool QUAD, bool UNI>
 __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int first, int icnt, const int4 &gh,
                                            const int *gref, float unit)
 {
@@ -576,6 +587,7 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
     float4 pi[NI], acc[NI];
     IPair<NP> I;
     APair<NP> A;
+    const float2 E2 = bc2(p.e2u);
 #pragma unroll
     for (int k = 0; k < NI; k++) {
         const int sl = islot + k * ilanes;
@@ -642,12 +654,12 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
                 const float ej = p.eps[j];
                 S.jp[k] = make_float4(grid_off(p.cx[j], gref[0], p.rx[j], unit),
                                       grid_off(p.cy[j], gref[1], p.ry[j], unit),
-                                      grid_off(p.cz[j], gref[2], p.rz[j], unit), p.m[j]);
+                                      grid_off(p.cz[j], gref[2], p.rz[j], unit), -p.m[j]);
                 S.je[k] = ej * ej;
             }
             __syncthreads();
             if (ivalid) {
-                if constexpr (PK) pp_loopP<NP, MASK>(S, np, split, js, I, A);
+                if constexpr (PK) pp_loopP<NP, MASK, UNI>(S, np, split, js, I, E2, A);
                 else pp_loopN<NI, MASK>(S, np, split, js, pi, acc);
             }
             __syncthreads();
@@ -671,7 +683,7 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
             }
         }
         if (ivalid) {
-            if constexpr (PK) pc_loopP<NP, QUAD>(S, cb, nc, split, js, I, A);
+            if constexpr (PK) pc_loopP<NP, QUAD, UNI>(S, cb, nc, split, js, I, E2, A);
             else pc_loopN<NI, QUAD>(S, cb, nc, split, js, pi, acc);
         }
         if (cnx >= 0) {
@@ -688,12 +700,16 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
     // reduce the j-splits: the partial sums of particle slots k0 .. k0 + RB - 1
     // at a time go through the PP staging buffer (idle here)
     constexpr int RB = GW_JP / GW_THREADS;
+    // the sums were accumulated negated
     if constexpr (PK) {
 #pragma unroll
         for (int h = 0; h < NP; h++) {
-            acc[2 * h] = make_float4(A.ax[h].x, A.ay[h].x, A.az[h].x, A.ph[h].x);
-            acc[2 * h + 1] = make_float4(A.ax[h].y, A.ay[h].y, A.az[h].y, A.ph[h].y);
+            acc[2 * h] = make_float4(-A.ax[h].x, -A.ay[h].x, -A.az[h].x, -A.ph[h].x);
+            acc[2 * h + 1] = make_float4(-A.ax[h].y, -A.ay[h].y, -A.az[h].y, -A.ph[h].y);
         }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NI; k++) acc[k] = make_float4(-acc[k].x, -acc[k].y, -acc[k].z, -acc[k].w);
     }
 #pragma unroll
     for (int k0 = 0; k0 < NI; k0 += RB) {
@@ -727,7 +743,7 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
 // thread above 128 particles in a chunk (NIMAX = 8), four above 64, two above
 // 16, else one.  The eight-particle variant holds 64 more registers of
 // i-particles and runs 4 CTAs per SM instead of 5.
-template <bool MASK, bool QUAD, int NIMAX>
+template <bool MASK, bool QUAD, int NIMAX, bool UNI>
 __global__ void __launch_bounds__(GW_THREADS, NIMAX >= 8 ? 4 : 5) k_grav_eval(GravParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -747,10 +763,11 @@ __global__ void __launch_bounds__(GW_THREADS, NIMAX >= 8 ? 4 : 5) k_grav_eval(Gr
         const int gref[3] = {gr.x, gr.y, gr.z};
         for (int i0 = 0; i0 < gcount; i0 += NIMAX * GW_THREADS) {
             const int icnt = min(NIMAX * GW_THREADS, gcount - i0);
-            if (NIMAX >= 8 && icnt > 128) eval_chunk<NIMAX >= 8 ? 8 : 4, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
-            else if (icnt > 64) eval_chunk<4, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
-            else if (icnt > 16) eval_chunk<2, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
-            else eval_chunk<1, MASK, QUAD>(S, p, gfirst + i0, icnt, gh, gref, unit);
+            if (NIMAX >= 8 && icnt > 128)
+                eval_chunk<NIMAX >= 8 ? 8 : 4, MASK, QUAD, UNI>(S, p, gfirst + i0, icnt, gh, gref, unit);
+            else if (icnt > 64) eval_chunk<4, MASK, QUAD, UNI>(S, p, gfirst + i0, icnt, gh, gref, unit);
+            else if (icnt > 16) eval_chunk<2, MASK, QUAD, UNI>(S, p, gfirst + i0, icnt, gh, gref, unit);
+            else eval_chunk<1, MASK, QUAD, UNI>(S, p, gfirst + i0, icnt, gh, gref, unit);
         }
     }
 }
@@ -791,13 +808,14 @@ __global__ void __launch_bounds__(GW_THREADS, 4) k_gravity_direct(GravParams p)
                     float ej = p.eps[j];
                     S.jp[k] = make_float4(grid_off(p.cx[j], gref[0], p.rx[j], unit),
                                           grid_off(p.cy[j], gref[1], p.ry[j], unit),
-                                          grid_off(p.cz[j], gref[2], p.rz[j], unit), p.m[j]);
+                                          grid_off(p.cz[j], gref[2], p.rz[j], unit), -p.m[j]);
                     S.je[k] = ej * ej;
                 }
                 __syncthreads();
                 if (ivalid) pp_loop<MASK>(S, np, split, js, xi, yi, zi, e2i, ax, ay, az, ph);
             }
             __syncthreads();
+            ax = -ax; ay = -ay; az = -az; ph = -ph;  // the sums were accumulated negated
             S.red[tid] = make_float4(ax, ay, az, ph);
             __syncthreads();
             if (split == 0 && ivalid) {
@@ -847,6 +865,7 @@ static GravParams make_params(gnb_ctx *c)
         }
     }
     p.G = (float)c->cfg.G;
+    p.e2u = c->eps_uniform ? 2.f * (c->eps0 * c->eps0) : 0.f;
     p.quad = c->cfg.multipole;
     p.n = (int)c->n;
     p.next = c->pinned_i ? nullptr : nullptr;
@@ -941,18 +960,26 @@ int gravity_tree(gnb_ctx *c)
             // groups of more than 128 particles: eight i-particles per thread
             if (c->cfg.n_group > 128) {
                 if (c->min_eps_zero) {
-                    if (q) return launch_persistent(c, k_grav_eval<true, true, 8>, p, next_d);
-                    return launch_persistent(c, k_grav_eval<true, false, 8>, p, next_d);
+                    if (q) return launch_persistent(c, k_grav_eval<true, true, 8, false>, p, next_d);
+                    return launch_persistent(c, k_grav_eval<true, false, 8, false>, p, next_d);
                 }
-                if (q) return launch_persistent(c, k_grav_eval<false, true, 8>, p, next_d);
-                return launch_persistent(c, k_grav_eval<false, false, 8>, p, next_d);
+                if (c->eps_uniform) {
+                    if (q) return launch_persistent(c, k_grav_eval<false, true, 8, true>, p, next_d);
+                    return launch_persistent(c, k_grav_eval<false, false, 8, true>, p, next_d);
+                }
+                if (q) return launch_persistent(c, k_grav_eval<false, true, 8, false>, p, next_d);
+                return launch_persistent(c, k_grav_eval<false, false, 8, false>, p, next_d);
             }
             if (c->min_eps_zero) {
-                if (q) return launch_persistent(c, k_grav_eval<true, true, 4>, p, next_d);
-                return launch_persistent(c, k_grav_eval<true, false, 4>, p, next_d);
+                if (q) return launch_persistent(c, k_grav_eval<true, true, 4, false>, p, next_d);
+                return launch_persistent(c, k_grav_eval<true, false, 4, false>, p, next_d);
             }
-            if (q) return launch_persistent(c, k_grav_eval<false, true, 4>, p, next_d);
-            return launch_persistent(c, k_grav_eval<false, false, 4>, p, next_d);
+            if (c->eps_uniform) {
+                if (q) return launch_persistent(c, k_grav_eval<false, true, 4, true>, p, next_d);
+                return launch_persistent(c, k_grav_eval<false, false, 4, true>, p, next_d);
+            }
+            if (q) return launch_persistent(c, k_grav_eval<false, true, 4, false>, p, next_d);
+            return launch_persistent(c, k_grav_eval<false, false, 4, false>, p, next_d);
         }
         if (attempt >= 4) return fail(c, GNB_ECAPACITY, "interaction-list pool");
         GNB_TRY(lists_alloc(c, used + used / 2 + 1024));

@@ -151,6 +151,24 @@ def test_tree_gravity_matches_oracle_walk(G, orc, quad, n_group):
     assert st["GROUPS"] == ref["groups"] and st["NODES"] == ref["nodes"]
 
 
+@pytest.mark.parametrize("quad", [0, 1])
+@pytest.mark.parametrize("n_group", [64, 300])
+def test_tree_gravity_mixed_softening(G, orc, quad, n_group):
+    """Softening that differs between particles (the kernel's general form:
+    eps_i^2 + eps_j^2 per pair and the cells' mass-weighted eps^2); the other
+    tests use one softening for all particles, which takes the constant-term
+    form.  Both group sizes cover four and eight i-particles per thread."""
+    p = ics.config_tiny()
+    rng = np.random.default_rng(5)
+    p["eps"] = (p["eps"] * rng.uniform(0.5, 2.0, p["eps"].shape[0])).astype(np.float32)
+    c = _ctx(G, p, n_leaf=16, n_group=n_group, multipole=quad, theta=0.5)
+    c.compute_gravity(G.GNB_GRAV_TREE)
+    ref = orc.tree_gravity(p, theta=0.5, n_leaf=16, n_g=n_group, quad=bool(quad))
+    g = [c.get("AGRAV_X"), c.get("AGRAV_Y"), c.get("AGRAV_Z")]
+    assert _acc_err(g, ref).max() < TOL
+    assert np.max(np.abs(c.get("POT") - ref["phi"]) / np.abs(ref["phi"])) < TOL
+
+
 def test_tree_vs_direct_accuracy(G, orc):
     p = ics.config_tiny()
     c = _ctx(G, p, theta=0.5, n_group=64)
