@@ -727,7 +727,10 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
                     a.x += r.x; a.y += r.y; a.z += r.z; a.w += r.w;
                 }
                 const int ip = first + sl;
-                if (!MASK) a.w -= p.m[ip] * rsqrtf(2.f * pi[k].w);  // remove the j == i term
+                if (!MASK) {  // remove the j == i term (eps reloaded: no register holds it through the loops)
+                    const float ep = p.eps[ip];
+                    a.w -= p.m[ip] * rsqrtf(2.f * (ep * ep));
+                }
                 p.ax[ip] = p.G * a.x;
                 p.ay[ip] = p.G * a.y;
                 p.az[ip] = p.G * a.z;
@@ -741,10 +744,11 @@ __device__ __forceinline__ void eval_chunk(GravSmem &S, const GravParams &p, int
 // Evaluation of the walk's lists, one group per CTA (see the file comment):
 // the group's particles in chunks of up to NIMAX * GW_THREADS, eight per
 // thread above 128 particles in a chunk (NIMAX = 8), four above 64, two above
-// 16, else one.  The eight-particle variant holds 64 more registers of
-// i-particles and runs 4 CTAs per SM instead of 5.
+// 16, else one.  Five CTAs per SM (96 registers a thread; the eight-particle
+// variant spills a few bytes outside its inner loops and still runs faster
+// than at 4 CTAs and 128 registers).
 template <bool MASK, bool QUAD, int NIMAX, bool UNI>
-__global__ void __launch_bounds__(GW_THREADS, NIMAX >= 8 ? 4 : 5) k_grav_eval(GravParams p)
+__global__ void __launch_bounds__(GW_THREADS, 5) k_grav_eval(GravParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GravSmem &S = *reinterpret_cast<GravSmem *>(smem_raw);
