@@ -197,20 +197,23 @@ __global__ void __launch_bounds__(1024) k_rs_scan(int *__restrict__ counts, int 
 }
 
 // Scatter of one tile: the tile's pairs are first sorted by digit in shared
-// memory (stable: rounds of RS_THREADS pairs in order, warps in order within
-// a round, lanes in order within a warp), then written out in that order, so
-// consecutive threads write consecutive addresses of a digit's run (about
-// RS_TILE / 256 pairs per digit) instead of one scattered 8-byte store each.
+// memory, stably, then written out in that order, so consecutive threads
+// write consecutive addresses of each digit's run (about RS_TILE / 256 pairs
+// per digit) instead of one scattered 8-byte store each.  Each warp ranks its
+// own contiguous RS_ITEMS * 32 pairs of the tile (rounds of 32 in order,
+// lanes in order within a round) against per-warp digit counters, with warp
+// synchronisation only; one block-wide step then turns the counters into each
+// warp's offset within the digit's run of the tile.
 struct RsSmem {
     uint64_t k[RS_TILE];
     int v[RS_TILE];
-    int w[RS_THREADS / 32][256];  // per-warp digit counts of a round, then their exclusive prefixes
-    int run[256];                 // pairs of each digit ranked so far (then the tile histogram)
-    int lstart[256];              // first local position of each digit
-    int goff[256];                // global position of each digit's first pair of this tile
+    int wc[RS_THREADS / 32][256];  // per-warp digit counts, then each warp's offset in the digit's run
+    int lstart[256];               // first local position of each digit
+    int goff[256];                 // global position of each digit's first pair of this tile
+    int ws[RS_THREADS / 32];
 };
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__restrict__ kin,
+__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const uint64_t *__restrict__ kin,
                                                           const int *__restrict__ vin,
                                                           uint64_t *__restrict__ kout,
                                                           int *__restrict__ vout, int n, int shift,
@@ -222,63 +225,63 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__res
     const unsigned lt = (1u << lane) - 1u;
     const int base = tile * RS_TILE;
     const int cnt = min(RS_TILE, n - base);
-    S.run[t] = 0;
+#pragma unroll
+    for (int q = 0; q < RS_THREADS / 32; q++) S.wc[q][t] = 0;
     S.goff[t] = offs[t * ntiles + tile];
     __syncthreads();
     uint64_t key[RS_ITEMS];
-    int val[RS_ITEMS];
+    int val[RS_ITEMS], lr[RS_ITEMS];
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; r++) {
-        const int i = r * RS_THREADS + t;
-        key[r] = i < cnt ? kin[base + i] : 0ull;
-        val[r] = i < cnt ? vin[base + i] : 0;
-        if (i < cnt) atomicAdd(&S.run[(int)((key[r] >> shift) & 255u)], 1);
+        const int i = w * (RS_ITEMS * 32) + r * 32 + lane;
+        const bool valid = i < cnt;
+        key[r] = valid ? kin[base + i] : 0ull;
+        val[r] = valid ? vin[base + i] : 0;
+        const int d = valid ? (int)((key[r] >> shift) & 255u) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        int old = 0;
+        if (valid && lane == leader) {
+            old = S.wc[w][d];
+            S.wc[w][d] = old + __popc(peers);
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        lr[r] = old + __popc(peers & lt);
+        __syncwarp();
     }
     __syncthreads();
-    {   // exclusive scan of the tile histogram over the 256 digits
-        const int c = S.run[t];
-        int x = c;
+    {   // digit t: offsets of the warps within the digit's run, then the
+        // exclusive scan of the tile histogram over the 256 digits
+        int run = 0;
+#pragma unroll
+        for (int q = 0; q < RS_THREADS / 32; q++) {
+            const int c = S.wc[q][t];
+            S.wc[q][t] = run;
+            run += c;
+        }
+        int x = run;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) S.w[0][w] = x;
+        if (lane == 31) S.ws[w] = x;
         __syncthreads();
         int pre = 0;
-        for (int q = 0; q < w; q++) pre += S.w[0][q];
-        S.lstart[t] = pre + x - c;
-        S.run[t] = 0;
+        for (int q = 0; q < w; q++) pre += S.ws[q];
+        S.lstart[t] = pre + x - run;
         __syncthreads();
     }
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; r++) {
-#pragma unroll
-        for (int q = 0; q < RS_THREADS / 32; q++) S.w[q][t] = 0;
-        __syncthreads();
-        const bool valid = r * RS_THREADS + t < cnt;
-        const int d = valid ? (int)((key[r] >> shift) & 255u) : 256;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int rank = __popc(peers & lt);
-        if (valid && rank == 0) S.w[w][d] = __popc(peers);
-        __syncthreads();
-        {
-            int run = S.run[t];
-#pragma unroll
-            for (int q = 0; q < RS_THREADS / 32; q++) {
-                const int c = S.w[q][t];
-                S.w[q][t] = run;
-                run += c;
-            }
-            S.run[t] = run;
-        }
-        __syncthreads();
-        if (valid) {
-            const int lp = S.lstart[d] + S.w[w][d] + rank;
+        const int i = w * (RS_ITEMS * 32) + r * 32 + lane;
+        if (i < cnt) {
+            const int d = (int)((key[r] >> shift) & 255u);
+            const int lp = S.lstart[d] + S.wc[w][d] + lr[r];
             S.k[lp] = key[r];
             S.v[lp] = val[r];
         }
-        __syncthreads();
     }
+    __syncthreads();
     for (int pos = t; pos < cnt; pos += RS_THREADS) {
         const uint64_t k = S.k[pos];
         const int d = (int)((k >> shift) & 255u);
