@@ -96,6 +96,7 @@ struct gnb_ctx {
     int64_t cap = 0;          // particle capacity
     bool min_eps_zero = false;
     bool eps_uniform = false;  // every particle has the softening eps0 > 0
+    float knn_margin = 1.1f;   // kernel-size search radius over the previous support (adapted per evaluation)
     float eps0 = 0.f;
 
     gnb::PArr P[2];
@@ -313,6 +314,7 @@ int build_tree(gnb_ctx *c, Tree &t, const uint64_t *skey, int n, const int *n_d,
 int tree_alloc(gnb_ctx *c, Tree &t, int cap);
 void tree_free(gnb_ctx *c, Tree &t);
 int device_scan(gnb_ctx *c, const int *in, int *out, const int *n_d, int nmax, int *total_d);
+int gas_slots(gnb_ctx *c, const uint8_t *type, const int *n_d, int *gslot);
 int save_state(gnb_ctx *c, const char *path);
 int load_state(gnb_ctx *c, const char *path);
 // gravity.cu

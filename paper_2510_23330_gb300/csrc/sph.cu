@@ -61,19 +61,6 @@ __device__ __forceinline__ float kern_dw(float r, float hinv)
 }
 
 // ---------------------------------------------------------------- gas extraction
-__global__ void k_gas_flag(const uint8_t *__restrict__ type, int *__restrict__ flag, int n)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = type[i] == GNB_GAS;
-}
-
-__global__ void k_gas_compact(const int *__restrict__ flag, const int *__restrict__ off, int n,
-                              int *__restrict__ gslot)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && flag[i]) gslot[off[i]] = i;
-}
-
 struct GasGather {
     const uint64_t *skey;
     PArr p;
@@ -107,10 +94,15 @@ __global__ void k_gas_gather(GasGather g)
 }
 
 // ---------------------------------------------------------------- search radius
-// Initial radius per hydro group: 1.1 x the largest previous support in the
-// group, or, without history, a density estimate from the smallest ancestor
-// cell holding at least n_ngb particles.
-__global__ void k_knn_init(Tree t, const float *__restrict__ hprev, int have_h, const double *__restrict__ box,
+// Initial radius per hydro group: margin x the largest previous support in
+// the group, or, without history, a density estimate from the smallest
+// ancestor cell holding at least n_ngb particles.  A group split into
+// single-particle items gives each particle margin x its own previous
+// support (at most the group's radius).  The margin trades retried items (a
+// support that grew past it) against candidates per item (the search volume
+// grows as its cube); the host adapts it to the retries it sees (see
+// sph_density).
+__global__ void k_knn_init(Tree t, const float *__restrict__ hprev, int have_h, float margin, const double *__restrict__ box,
                            float *__restrict__ kR, float2 *__restrict__ kRb, int *__restrict__ kflag,
                            int2 *__restrict__ kitem, int *__restrict__ nitems)
 {
@@ -124,7 +116,7 @@ __global__ void k_knn_init(Tree t, const float *__restrict__ hprev, int have_h, 
         float R = 0.f;
         if (have_h) {
             for (int i = a.x; i < a.x + a.y; i++) R = fmaxf(R, hprev[i]);
-            R *= 1.1f;
+            R *= margin;
         }
         if (!(R > 0.f)) {
             int q = node;
@@ -155,6 +147,9 @@ struct KnnParams {
     const float *grx, *gry, *grz, *gm, *gu;
     const double *gx, *gy, *gz;
     const double *box;
+    const float *rprev;  // previous support per gas particle (0: none)
+    float margin;        // search radius over the previous support
+    int *nunder;         // work items whose radius held too few candidates
     float *kR;
     float2 *kRb;
     int *kflag;
@@ -660,7 +655,10 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
                 const bool fits = base + k < p.item_cap;
                 if (fits) {
                     p.item[base + k] = make_int2(ga.x + k, 1);
-                    p.kR[base + k] = R;
+                    // the particle's own previous support when it has one:
+                    // the group's radius is its largest member's
+                    const float hp = p.rprev[ga.x + k];
+                    p.kR[base + k] = hp > 0.f ? fminf(R, p.margin * hp) : R;
                     p.kRb[base + k] = make_float2(0.f, 0.f);
                     p.kflag[base + k] = 1;
                 } else {
@@ -682,6 +680,7 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
                 rb.x = R;
                 p.kR[gi] = rb.y > 0.f ? 0.5f * (R + rb.y) : 1.6f * R;
                 done = 0;
+                atomicAdd(p.nunder, 1);
             }
             p.kRb[gi] = rb;
             p.kflag[gi] = done ? 0 : 1;
@@ -894,15 +893,13 @@ static int g_knn_blocks = 0;
 
 int sph_density(gnb_ctx *c)
 {
-    int n = (int)c->n, ng = (int)c->n_gas;
+    int ng = (int)c->n_gas;
     if (ng == 0) return GNB_OK;
     phase_begin(c, GNB_T_HYDRO_TREE);
     PArr &a = c->P[c->cur];
-    int nb = (n + 255) / 256, gb = (ng + 255) / 256;
+    int gb = (ng + 255) / 256;
     // gas slots in Morton order
-    gnb::counted(k_gas_flag)<<<nb, 256, 0, c->s>>>(a.type, c->gas_flag, n);
-    GNB_TRY(device_scan(c, c->gas_flag, c->pscan, c->n_d, n, nullptr));
-    gnb::counted(k_gas_compact)<<<nb, 256, 0, c->s>>>(c->gas_flag, c->pscan, n, c->gslot);
+    GNB_TRY(gas_slots(c, a.type, c->n_d, c->gslot));
     GasGather gg;
     gg.skey = c->skey; gg.p = a; gg.gslot = c->gslot; gg.gkey = c->gkey;
     gg.gcx = c->gcx; gg.gcy = c->gcy; gg.gcz = c->gcz; gg.ggrank = c->ggrank;
@@ -918,7 +915,7 @@ int sph_density(gnb_ctx *c)
                        c->gry, c->grz, c->gm, c->gm, false));
     phase_begin(c, GNB_T_KNN);
     // work_d: [0] next item, [1] items left unfinished, [2] live item count, [3] per-pass snapshot
-    gnb::counted(k_knn_init)<<<304, 256, 0, c->s>>>(c->gt, c->gRprev, c->have_h ? 1 : 0, c->box_d, c->kR,
+    gnb::counted(k_knn_init)<<<304, 256, 0, c->s>>>(c->gt, c->gRprev, c->have_h ? 1 : 0, c->knn_margin, c->box_d, c->kR,
                                       c->kRb, c->kflag, c->kitem, c->work_d + 2);
     GNB_LAUNCH_CHECK(c, "knn init");
     KnnParams p;
@@ -928,6 +925,10 @@ int sph_density(gnb_ctx *c)
     p.grx = c->grx; p.gry = c->gry; p.grz = c->grz; p.gm = c->gm; p.gu = c->gu;
     p.gx = c->gx; p.gy = c->gy; p.gz = c->gz; p.box = c->box_d;
     p.kR = c->kR; p.kRb = c->kRb; p.kflag = c->kflag;
+    p.rprev = c->gRprev;
+    p.margin = c->knn_margin;
+    p.nunder = c->work_d + 6;
+    cudaMemsetAsync(c->work_d + 6, 0, sizeof(int), c->s);
     p.next = c->work_d; p.remaining = c->work_d + 1; p.status = c->status_d;
     p.nbr = c->nbr; p.nd2 = c->nd2; p.h2 = c->gh2; p.h2lo = c->gh2lo; p.h2hi = c->gh2hi; p.h = c->gh; p.E = c->gE; p.rho = c->grho; p.P = c->gP;
     p.cs = c->gcs; p.g64 = c->g64; p.gamma = (float)c->cfg.gamma; p.pressure = c->cfg.sph_variant;
@@ -965,6 +966,8 @@ int sph_density(gnb_ctx *c)
         }
         GNB_LAUNCH_CHECK(c, "knn");
         cudaMemcpyAsync(c->pinned_i, c->work_d + 1, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+        cudaMemcpyAsync(c->pinned_i + 20, c->work_d + 3, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+        cudaMemcpyAsync(c->pinned_i + 21, c->work_d + 6, sizeof(int), cudaMemcpyDeviceToHost, c->s);
         cudaMemcpyAsync(c->pinned_i + 1, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->s);
         GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "knn sync"));
         if (c->pinned_i[1] & ST_KNN_OVERFLOW) return fail(c, GNB_ECAPACITY, "kNN selection buffer overflow");
@@ -972,6 +975,13 @@ int sph_density(gnb_ctx *c)
         if (round == rounds - 1) return fail(c, GNB_ECAPACITY, "kNN search radius did not converge");
     }
     c->stats[GNB_S_KNN_PASSES] = passes;
+    // the next evaluation's margin: wider when more than 4 % of the work
+    // items needed a larger radius, narrower (to 1.01) below 1 %
+    if (c->have_h) {
+        const double under = (double)c->pinned_i[21] / (double)std::max(1, c->pinned_i[20]);
+        if (under > 0.04) c->knn_margin = std::min(1.5f, c->knn_margin * 1.05f);
+        else if (under < 0.01) c->knn_margin = std::max(1.01f, c->knn_margin / 1.01f);
+    }
     c->stats[GNB_S_GAS_NODES] = c->gt.nnodes;
     gnb::counted(k_gas_scatter_density)<<<gb, 256, 0, c->s>>>(ng, c->gslot, c->grho, c->gP, c->gcs, c->gh2, c->rho, c->pres,
                                                 c->cs, a.h2);

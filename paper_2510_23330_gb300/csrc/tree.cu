@@ -22,14 +22,33 @@ namespace gnb {
 #define TB_BLOCKS 304
 
 // ----------------------------------------------------------------- scan
+// Block b scans the contiguous chunk [b chunk, (b + 1) chunk) of the input,
+// four elements a thread per round (one 16-byte load; the inputs are
+// allocation bases, so 16-byte aligned), with chunk a multiple of the
+// TB_THREADS * 4 elements of a round.
+__device__ __forceinline__ int scan_chunk(int n, int G)
+{
+    const int per = (n + G - 1) / G;
+    return (per + TB_THREADS * 4 - 1) / (TB_THREADS * 4) * (TB_THREADS * 4);
+}
+
+__device__ __forceinline__ int4 load4(const int *__restrict__ in, int i0, int end)
+{
+    if (i0 + 3 < end) return *reinterpret_cast<const int4 *>(in + i0);
+    return make_int4(i0 < end ? in[i0] : 0, i0 + 1 < end ? in[i0 + 1] : 0, i0 + 2 < end ? in[i0 + 2] : 0, 0);
+}
+
 __global__ void k_scan_partial(const int *__restrict__ in, const int *__restrict__ n_d, int *partial)
 {
     __shared__ int ws[32];
     int n = *n_d, G = gridDim.x;
-    int chunk = (n + G - 1) / G;
-    int beg = blockIdx.x * chunk, end = min(n, beg + chunk);
+    int chunk = scan_chunk(n, G);
+    int beg = min(n, blockIdx.x * chunk), end = min(n, beg + chunk);
     int s = 0;
-    for (int i = beg + threadIdx.x; i < end; i += blockDim.x) s += in[i];
+    for (int i0 = beg + 4 * threadIdx.x; i0 < end; i0 += 4 * blockDim.x) {
+        const int4 v = load4(in, i0, end);
+        s += v.x + v.y + v.z + v.w;
+    }
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -102,17 +121,104 @@ __global__ void k_scan_apply(const int *__restrict__ in, int *__restrict__ out, 
 {
     __shared__ int ws[32];
     int n = *n_d, G = gridDim.x;
-    int chunk = (n + G - 1) / G;
-    int beg = blockIdx.x * chunk, end = min(n, beg + chunk);
+    int chunk = scan_chunk(n, G);
+    int beg = min(n, blockIdx.x * chunk), end = min(n, beg + chunk);
     int carry = poff[blockIdx.x];
-    for (int b0 = beg; b0 < end; b0 += blockDim.x) {
-        int i = b0 + threadIdx.x;
-        int v = i < end ? in[i] : 0;
+    for (int b0 = beg; b0 < end; b0 += 4 * blockDim.x) {
+        const int i0 = b0 + 4 * threadIdx.x;
+        const int4 v = load4(in, i0, end);
         int tot;
-        int e = block_excl_scan(v, ws, &tot);
-        if (i < end) out[i] = carry + e;
+        const int e = carry + block_excl_scan(v.x + v.y + v.z + v.w, ws, &tot);
+        const int4 o = make_int4(e, e + v.x, e + v.x + v.y, e + v.x + v.y + v.z);
+        if (i0 + 3 < end) {
+            *reinterpret_cast<int4 *>(out + i0) = o;
+        } else {
+            if (i0 < end) out[i0] = o.x;
+            if (i0 + 1 < end) out[i0 + 1] = o.y;
+            if (i0 + 2 < end) out[i0 + 2] = o.z;
+        }
         carry += tot;
     }
+}
+
+// Slots of the gas particles in slot order, straight from the type bytes:
+// per-block gas counts over the same chunks as the scan (16 types a thread
+// per round, one 16-byte load), then each block writes its gas slots from the
+// scanned counts.
+#define GC_ITEMS 16
+__device__ __forceinline__ int gas_chunk(int n, int G)
+{
+    const int per = (n + G - 1) / G;
+    return (per + TB_THREADS * GC_ITEMS - 1) / (TB_THREADS * GC_ITEMS) * (TB_THREADS * GC_ITEMS);
+}
+
+// bit k set when type byte k of the 16 at i0 is gas (bytes past end: not gas)
+__device__ __forceinline__ unsigned gas_mask16(const uint8_t *__restrict__ type, int i0, int end)
+{
+    unsigned m = 0u;
+    if (i0 + GC_ITEMS <= end) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(type + i0);
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+                if (((w[q] >> (8 * b)) & 255u) == GNB_GAS) m |= 1u << (4 * q + b);
+    } else {
+        for (int k = 0; k < GC_ITEMS && i0 + k < end; k++)
+            if (type[i0 + k] == GNB_GAS) m |= 1u << k;
+    }
+    return m;
+}
+
+__global__ void k_gas_count(const uint8_t *__restrict__ type, const int *__restrict__ n_d, int *partial)
+{
+    __shared__ int ws[32];
+    const int n = *n_d, G = gridDim.x;
+    const int chunk = gas_chunk(n, G);
+    const int beg = min(n, blockIdx.x * chunk), end = min(n, beg + chunk);
+    int s = 0;
+    for (int i0 = beg + GC_ITEMS * threadIdx.x; i0 < end; i0 += GC_ITEMS * blockDim.x)
+        s += __popc(gas_mask16(type, i0, end));
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) partial[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_gas_slots(const uint8_t *__restrict__ type, const int *__restrict__ n_d,
+                            const int *__restrict__ poff, int *__restrict__ gslot)
+{
+    __shared__ int ws[32];
+    const int n = *n_d, G = gridDim.x;
+    const int chunk = gas_chunk(n, G);
+    const int beg = min(n, blockIdx.x * chunk), end = min(n, beg + chunk);
+    int carry = poff[blockIdx.x];
+    for (int b0 = beg; b0 < end; b0 += GC_ITEMS * blockDim.x) {
+        const int i0 = b0 + GC_ITEMS * threadIdx.x;
+        unsigned m = i0 < end ? gas_mask16(type, i0, end) : 0u;
+        int tot;
+        int pos = carry + block_excl_scan(__popc(m), ws, &tot);
+        while (m) {
+            const int k = __ffs(m) - 1;
+            gslot[pos++] = i0 + k;
+            m &= m - 1u;
+        }
+        carry += tot;
+    }
+}
+
+int gas_slots(gnb_ctx *c, const uint8_t *type, const int *n_d, int *gslot)
+{
+    gnb::counted(k_gas_count)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(type, n_d, c->scan_part);
+    gnb::counted(k_scan_partials)<<<1, 1024, 0, c->s>>>(c->scan_part, c->scan_poff, TB_BLOCKS, nullptr);
+    gnb::counted(k_gas_slots)<<<TB_BLOCKS, TB_THREADS, 0, c->s>>>(type, n_d, c->scan_poff, gslot);
+    GNB_LAUNCH_CHECK(c, "gas slots");
+    return GNB_OK;
 }
 
 int device_scan(gnb_ctx *c, const int *in, int *out, const int *n_d, int nmax, int *total_d)
