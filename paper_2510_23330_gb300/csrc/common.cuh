@@ -96,7 +96,7 @@ struct gnb_ctx {
     int64_t cap = 0;          // particle capacity
     bool min_eps_zero = false;
     bool eps_uniform = false;  // every particle has the softening eps0 > 0
-    float knn_margin = 1.1f;   // kernel-size search radius over the previous support (adapted per evaluation)
+    float knn_margin = 1.05f;   // kernel-size search radius over the previous support (adapted per evaluation)
     float eps0 = 0.f;
 
     gnb::PArr P[2];
