@@ -171,6 +171,27 @@ int gnb_set_particles(gnb_ctx *ctx, int64_t n, const int64_t *id, const uint8_t 
                       const float *vx, const float *vy, const float *vz,
                       const float *m, const float *eps, const float *u, int on_device);
 
+/* Load n particles with the state a kick-drift-kick integration carries
+ * from one step to the next (Sec. 3.1: the kick at the start of a step uses
+ * the accelerations of the step's end): the arrays of gnb_set_particles,
+ * plus the total acceleration ax, ay, az and du/dt (the fields GNB_F_AX,
+ * GNB_F_AY, GNB_F_AZ and GNB_F_DUDT of a context) evaluated on this state
+ * with gravity mode grav_mode, and optionally the squared kernel supports h2
+ * (GNB_F_H2; 0 for stars; NULL: none), the kernel-size search's starting
+ * radii.  A following gnb_step_kdk with the same mode kicks with the given
+ * accelerations instead of evaluating the forces first; the other results
+ * (gravity alone, potentials, density) are not current until the next force
+ * evaluation.  All arrays are in the caller's order, host or device as
+ * on_device says.  Errors: as gnb_set_particles, and GNB_EINVAL for a null
+ * acceleration or du/dt array or an invalid mode.  If the call fails after
+ * the particles were set, the context holds them without forces. */
+int gnb_set_state(gnb_ctx *ctx, int64_t n, const int64_t *id, const uint8_t *type,
+                  const double *x, const double *y, const double *z,
+                  const float *vx, const float *vy, const float *vz,
+                  const float *m, const float *eps, const float *u, const double *h2,
+                  const float *ax, const float *ay, const float *az, const float *dudt,
+                  int grav_mode, int on_device);
+
 /* Sort particles along the Morton curve and build the octree, its cell
  * moments and the groups (Sec. 3.4, 5.2.2).  Errors: GNB_ESTATE (no
  * particles), GNB_ECUDA. */

@@ -378,6 +378,31 @@ int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *t
     return GNB_OK;
 }
 
+int gnb_set_state(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *type, const double *x, const double *y,
+                  const double *z, const float *vx, const float *vy, const float *vz, const float *m, const float *eps,
+                  const float *u, const double *h2, const float *ax, const float *ay, const float *az,
+                  const float *dudt, int grav_mode, int on_device)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!ax || !ay || !az || !dudt) return fail(c, GNB_EINVAL, "null acceleration or du/dt array");
+    if (grav_mode != GNB_GRAV_DIRECT && grav_mode != GNB_GRAV_TREE && grav_mode != GNB_GRAV_NONE)
+        return fail(c, GNB_EINVAL, "gravity mode");
+    const int rc = gnb_set_particles(c, n, id, type, x, y, z, vx, vy, vz, m, eps, u, on_device);
+    if (rc != GNB_OK) return rc;
+    // right after gnb_set_particles the slots are in caller order
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t N = (size_t)n;
+    if (h2) GNB_TRY(cuda_check(c, cudaMemcpyAsync(c->P[c->cur].h2, h2, 8 * N, k, c->s), "state copy"));
+    struct { float *d; const float *s; } cp[] = {{c->ax, ax}, {c->ay, ay}, {c->az, az}, {c->dudt, dudt}};
+    for (auto &q : cp) GNB_TRY(cuda_check(c, cudaMemcpyAsync(q.d, q.s, 4 * N, k, c->s), "state copy"));
+    GNB_TRY(cuda_check(c, cudaStreamSynchronize(c->s), "state copy sync"));
+    c->have_h = h2 != nullptr;
+    c->force_valid = true;
+    c->last_grav_mode = grav_mode;
+    return GNB_OK;
+}
+
 }  // extern "C"
 
 namespace gnb {
@@ -854,16 +879,19 @@ int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
     bool need_grav = field == GNB_F_AX || field == GNB_F_AY || field == GNB_F_AZ || field == GNB_F_POT ||
                      field == GNB_F_POT_EXT ||
                      field == GNB_F_AGRAV_X || field == GNB_F_AGRAV_Y || field == GNB_F_AGRAV_Z;
-    bool need_den = field == GNB_F_RHO || field == GNB_F_PRES || field == GNB_F_CS || field == GNB_F_H2 ||
-                    field == GNB_F_NBR;
+    bool need_den = field == GNB_F_RHO || field == GNB_F_PRES || field == GNB_F_CS || field == GNB_F_NBR;
     if (need_sort && !c->sorted_valid) return fail(c, GNB_ESTATE, "particles not sorted for the current positions");
     if (need_tree && !c->tree_valid) return fail(c, GNB_ESTATE, "tree not built");
     bool total_acc = field == GNB_F_AX || field == GNB_F_AY || field == GNB_F_AZ;
-    if (need_grav && !c->gravity_valid && !(total_acc && c->sphf_valid))
+    // the total acceleration, du/dt and the supports are also current when
+    // they came with the state (gnb_set_state)
+    if (need_grav && !c->gravity_valid && !(total_acc && (c->sphf_valid || c->force_valid)))
         return fail(c, GNB_ESTATE, "forces not computed");
     if (need_den && !c->density_valid) return fail(c, GNB_ESTATE, "SPH density not computed");
+    if (field == GNB_F_H2 && !c->density_valid && !(c->have_h && c->force_valid))
+        return fail(c, GNB_ESTATE, "SPH density not computed");
     if (field == GNB_F_NBR && !c->nbr_valid) return fail(c, GNB_ESTATE, "neighbour lists not computed");
-    if (field == GNB_F_DUDT && !c->sphf_valid) return fail(c, GNB_ESTATE, "SPH force not computed");
+    if (field == GNB_F_DUDT && !c->sphf_valid && !c->force_valid) return fail(c, GNB_ESTATE, "SPH force not computed");
     if (field == GNB_F_LEVEL && !c->hier_valid) return fail(c, GNB_ESTATE, "no hierarchical integration");
     size_t esz;
     int64_t cnt = field_count(c, field, &esz);

@@ -78,6 +78,7 @@ def _declare(L):
     L.gnb_destroy.argtypes = [_vp]
     L.gnb_destroy.restype = None
     L.gnb_set_particles.argtypes = [_vp, C.c_int64] + [_vp] * 11 + [C.c_int]
+    L.gnb_set_state.argtypes = [_vp, C.c_int64] + [_vp] * 16 + [C.c_int, C.c_int]
     L.gnb_build_tree.argtypes = [_vp]
     L.gnb_compute_gravity.argtypes = [_vp, C.c_int]
     L.gnb_compute_sph_density.argtypes = [_vp]
@@ -152,7 +153,7 @@ def _declare(L):
     L.gnb_unet_forward.restype = C.c_int
     L.gnb_unet_train_step.argtypes = [_vp, C.c_int, _vp, _vp, C.c_double, C.POINTER(C.c_double), C.c_int]
     L.gnb_unet_train_step.restype = C.c_int
-    for name in ("gnb_create", "gnb_set_particles", "gnb_build_tree", "gnb_compute_gravity",
+    for name in ("gnb_create", "gnb_set_particles", "gnb_set_state", "gnb_build_tree", "gnb_compute_gravity",
                  "gnb_compute_sph_density", "gnb_compute_sph_force", "gnb_compute_forces", "gnb_step_kdk",
                  "gnb_get", "gnb_diagnostics", "gnb_stats"):
         getattr(L, name).restype = C.c_int
@@ -177,6 +178,11 @@ def gnb_set_config(ctx, cfg):
 
 def gnb_set_particles(ctx, n, id, type, x, y, z, vx, vy, vz, m, eps, u, on_device):
     return lib().gnb_set_particles(ctx, n, id, type, x, y, z, vx, vy, vz, m, eps, u, on_device)
+
+
+def gnb_set_state(ctx, n, id, type, x, y, z, vx, vy, vz, m, eps, u, h2, ax, ay, az, dudt, grav_mode, on_device):
+    return lib().gnb_set_state(ctx, n, id, type, x, y, z, vx, vy, vz, m, eps, u, h2, ax, ay, az, dudt, grav_mode,
+                               on_device)
 
 
 def gnb_build_tree(ctx):
@@ -534,6 +540,28 @@ class Context:
         n = int(arrs[2].shape[0])
         self._keep = arrs
         self._chk(gnb_set_particles(self.h, n, *[q for q, _ in ptrs], on_dev.pop()))
+        self.n = n
+        self.n_gas = int(self.stats()["NGAS"])
+
+    def set_state(self, p: dict, mode=GNB_GRAV_TREE):
+        """Particles with the accelerations and du/dt of their state (keys
+        "ax", "ay", "az", "dudt", optionally "h2"), so that step_kdk with the
+        same mode continues without evaluating the forces first."""
+        keys = ("id", "type", "x", "y", "z", "vx", "vy", "vz", "m", "eps", "u", "h2", "ax", "ay", "az", "dudt")
+        dt = dict(self._DT, h2=np.float64, ax=np.float32, ay=np.float32, az=np.float32, dudt=np.float32)
+        arrs = []
+        for k in keys:
+            a = p.get(k) if k == "h2" else p[k]
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=dt[k])
+            arrs.append(a)
+        ptrs = [_ptr(a) if a is not None else (None, None) for a in arrs]
+        on_dev = {d for _, d in ptrs if d is not None}
+        if len(on_dev) != 1:
+            raise ValueError("all arrays must be on the same side (host or device)")
+        n = int(arrs[2].shape[0])
+        self._keep = arrs
+        self._chk(gnb_set_state(self.h, n, *[q for q, _ in ptrs], mode, on_dev.pop()))
         self.n = n
         self.n_gas = int(self.stats()["NGAS"])
 

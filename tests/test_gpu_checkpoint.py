@@ -147,3 +147,73 @@ def test_unet_checkpoint_resumes_training(G, tmp_path):
     assert e.value.code == G.GNB_EMISMATCH
     for n in (a, b, c, other):
         n.close()
+
+
+def _state(c, p):
+    """The particles of context c with the accelerations of their state, in
+    the caller's order."""
+    s = {k: p[k] for k in ("id", "type", "m", "eps")}
+    for k, f in (("x", "X"), ("y", "Y"), ("z", "Z"), ("vx", "VX"), ("vy", "VY"), ("vz", "VZ"), ("u", "U"),
+                 ("ax", "AX"), ("ay", "AY"), ("az", "AZ"), ("dudt", "DUDT"), ("h2", "H2")):
+        s[k] = c.get(f)
+    return s
+
+
+def test_set_state_continues_without_a_force_pass(G):
+    """gnb_set_state with a context's state and accelerations: the next KDK
+    step kicks with them (one force evaluation per step, not two) and, for
+    stars (deterministic tree gravity), gives the context's own next step bit
+    for bit."""
+    p = ics.plummer(8192, seed=12, n_gas=0)
+    kw = dict(theta=0.5, multipole=1, n_group=64)
+    a = G.Context(**kw)
+    a.set_particles(p)
+    a.step_kdk(1e-3, 2)
+    b = G.Context(**kw)
+    b.set_state(_state(a, p))
+    for f in ("AX", "AY", "AZ"):
+        assert np.array_equal(a.get(f), b.get(f)), f
+    b.set_timing(True)
+    a.step_kdk(1e-3, 1)
+    b.step_kdk(1e-3, 1)
+    _, calls, _ = b.phase_times()
+    assert calls["GRAVITY"] == 1
+    _same(_fields(a, STATE + ["AX", "AY", "AZ"]), _fields(b, STATE + ["AX", "AY", "AZ"]))
+    # a plain upload evaluates the forces first
+    c = G.Context(**kw)
+    c.set_particles({k: v for k, v in _state(b, p).items() if k in p})
+    c.set_timing(True)
+    c.step_kdk(1e-3, 1)
+    assert c.phase_times()[1]["GRAVITY"] == 2
+    for x in (a, b, c):
+        x.close()
+
+
+def test_set_state_gas(G):
+    """With gas: the supports and du/dt go with the state; the continued
+    step matches the context's own within the run-to-run spread of the
+    kernel-size search's atomics (see the module docstring)."""
+    p = ics.config_disk(1 << 15, seed=6)
+    kw = dict(theta=0.5, multipole=1, n_group=64, nfw_ms=ics.NFW_MS, nfw_rs=ics.NFW_RS)
+    a = G.Context(**kw)
+    a.set_particles(p)
+    a.step_kdk(1e-3, 2)
+    b = G.Context(**kw)
+    b.set_state(_state(a, p))
+    assert b.n_gas == a.n_gas
+    a.step_kdk(1e-3, 1)
+    b.step_kdk(1e-3, 1)
+    fa, fb = _fields(a, STATE), _fields(b, STATE)
+    scale = max(np.ptp(fa["X"]), np.ptp(fa["Y"]), np.ptp(fa["Z"]))
+    for k in ("X", "Y", "Z"):
+        assert np.max(np.abs(fa[k] - fb[k])) <= 1e-9 * scale, k
+    vmax = max(np.max(np.abs(fa[k])) for k in ("VX", "VY", "VZ"))
+    for k in ("VX", "VY", "VZ"):
+        assert np.max(np.abs(fa[k].astype(np.float64) - fb[k])) <= 1e-4 * vmax, k
+    gas = p["type"] == 1
+    assert np.max(np.abs(fa["U"].astype(np.float64) - fb["U"])[gas] / fa["U"][gas]) <= 1e-4
+    with pytest.raises(G.GalnbError) as e:
+        b.set_state(_state(a, p), mode=7)
+    assert e.value.code == G.GNB_EINVAL
+    for x in (a, b):
+        x.close()
