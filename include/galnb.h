@@ -306,6 +306,14 @@ int gnb_replace_region(gnb_ctx *ctx, int64_t n, const int64_t *id, const double 
  * not computed yet), GNB_ECUDA. */
 int gnb_get(gnb_ctx *ctx, int field, void *dst, int64_t cap, int on_device);
 
+/* gnb_get of nf fields at once: field fields[k] into dst[k], which holds
+ * cap[k] elements of its type; all host or all device as on_device says.
+ * Every field is checked before any is copied; host copies are queued on
+ * the context's stream and the call waits once for all of them.  Errors: as
+ * gnb_get (nothing is copied then), and GNB_EINVAL for nf < 0 or a null
+ * list with nf > 0. */
+int gnb_get_fields(gnb_ctx *ctx, int nf, const int *fields, void *const *dst, const int64_t *cap, int on_device);
+
 /* Checkpoint of the particle state (no counterpart in the paper, which
  * describes no checkpoints).  gnb_save writes to `path`, in the caller's
  * particle order: IDs, types, FP64 positions, velocities, masses, softening

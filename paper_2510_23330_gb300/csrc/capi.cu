@@ -367,6 +367,7 @@ int gnb_set_particles(gnb_ctx *c, int64_t n, const int64_t *id, const uint8_t *t
     if (bad & 8) return fail(c, GNB_EINVAL, "softening must be non-negative and finite");
     if (ng > 0 && ng < c->cfg.n_ngb) return fail(c, GNB_EINVAL, "fewer gas particles than SPH neighbours");
     c->min_eps_zero = (bad & 16) != 0;
+    c->slots_caller = true;
     memcpy(&c->eps0, c->pinned_i + 3, sizeof(float));
     c->eps_uniform = !(bad & (16 | 32));
     c->n = n;
@@ -550,9 +551,7 @@ static int kdk_one(gnb_ctx *c, double dt, int mode)
 {
     float hdt = (float)(0.5 * dt);
     phase_begin(c, GNB_T_KDK);
-    int rc = kick(c, hdt, true);
-    if (rc == GNB_OK) rc = drift(c, dt);
-    if (rc == GNB_OK) rc = predict(c, hdt);
+    int rc = kick_drift_predict(c, hdt, dt);
     phase_end(c);
     c->sorted_valid = c->tree_valid = c->gravity_valid = c->density_valid = c->force_valid = c->sphf_valid = false;
     c->use_pred = true;
@@ -868,12 +867,10 @@ static int64_t field_count(gnb_ctx *c, int f, size_t *esz)
     }
 }
 
-int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
+// Whether `field` holds current values (GNB_OK) or why not.
+static int field_ready(gnb_ctx *c, int field)
 {
-    if (!c) return GNB_EINVAL;
-    c->err.clear();
-    if (!dst || field < 0 || field >= GNB_F_COUNT_) return fail(c, GNB_EINVAL, "field or destination");
-    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    if (field < 0 || field >= GNB_F_COUNT_) return fail(c, GNB_EINVAL, "field");
     bool need_sort = field == GNB_F_KEY || field == GNB_F_ORDER;
     bool need_tree = field == GNB_F_NODES || field == GNB_F_NODE_LINKS || field == GNB_F_GROUPS;
     bool need_grav = field == GNB_F_AX || field == GNB_F_AY || field == GNB_F_AZ || field == GNB_F_POT ||
@@ -893,6 +890,16 @@ int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
     if (field == GNB_F_NBR && !c->nbr_valid) return fail(c, GNB_ESTATE, "neighbour lists not computed");
     if (field == GNB_F_DUDT && !c->sphf_valid && !c->force_valid) return fail(c, GNB_ESTATE, "SPH force not computed");
     if (field == GNB_F_LEVEL && !c->hier_valid) return fail(c, GNB_ESTATE, "no hierarchical integration");
+    return GNB_OK;
+}
+
+int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (!dst || field < 0 || field >= GNB_F_COUNT_) return fail(c, GNB_EINVAL, "field or destination");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    GNB_TRY(field_ready(c, field));
     size_t esz;
     int64_t cnt = field_count(c, field, &esz);
     if (cap < cnt) return fail(c, GNB_EINVAL, "destination too small");
@@ -913,6 +920,49 @@ int gnb_get(gnb_ctx *c, int field, void *dst, int64_t cap, int on_device)
         if (rc == GNB_OK) rc = cuda_check(c, cudaStreamSynchronize(c->s), "export sync");
         if (own) cudaFree(tmp);
     }
+    return finish(c, rc);
+}
+
+int gnb_get_fields(gnb_ctx *c, int nf, const int *fields, void *const *dst, const int64_t *cap, int on_device)
+{
+    if (!c) return GNB_EINVAL;
+    c->err.clear();
+    if (nf < 0 || (nf > 0 && (!fields || !dst || !cap))) return fail(c, GNB_EINVAL, "field list");
+    if (!c->have_particles) return fail(c, GNB_ESTATE, "no particles");
+    // every field is checked before any is copied
+    std::vector<int64_t> cnt((size_t)nf);
+    std::vector<size_t> esz((size_t)nf);
+    size_t big = 0;
+    for (int k = 0; k < nf; k++) {
+        if (!dst[k] || fields[k] < 0 || fields[k] >= GNB_F_COUNT_) return fail(c, GNB_EINVAL, "field or destination");
+        GNB_TRY(field_ready(c, fields[k]));
+        cnt[k] = field_count(c, fields[k], &esz[k]);
+        if (cap[k] < cnt[k]) return fail(c, GNB_EINVAL, "destination too small");
+        big = std::max(big, (size_t)cnt[k] * esz[k]);
+    }
+    // host destinations: every field through the one staging buffer, its
+    // copy queued behind its gather on the stream (the next gather waits for
+    // it there), one synchronisation for all
+    void *tmp = c->tmp_out;
+    bool own = false;
+    if (!on_device && big > (size_t)c->cap * 8 + 64) {
+        if (cudaMalloc(&tmp, big) != cudaSuccess) return fail(c, GNB_ENOMEM, "export buffer");
+        own = true;
+    }
+    int rc = GNB_OK;
+    for (int k = 0; k < nf && rc == GNB_OK; k++) {
+        if (cnt[k] == 0) continue;
+        if (on_device) {
+            rc = scatter_out(c, fields[k], dst[k]);
+        } else {
+            rc = scatter_out(c, fields[k], tmp);
+            if (rc == GNB_OK)
+                rc = cuda_check(c, cudaMemcpyAsync(dst[k], tmp, (size_t)cnt[k] * esz[k], cudaMemcpyDeviceToHost, c->s),
+                                "export copy");
+        }
+    }
+    if (rc == GNB_OK && !on_device) rc = cuda_check(c, cudaStreamSynchronize(c->s), "export sync");
+    if (own) cudaFree(tmp);
     return finish(c, rc);
 }
 

@@ -96,6 +96,7 @@ struct gnb_ctx {
     int64_t cap = 0;          // particle capacity
     bool min_eps_zero = false;
     bool eps_uniform = false;  // every particle has the softening eps0 > 0
+    bool slots_caller = false; // the slots still hold the caller's order (no sort since the upload)
     float knn_margin = 1.05f;   // kernel-size search radius over the previous support (adapted per evaluation)
     float eps0 = 0.f;
 
@@ -344,6 +345,7 @@ int cfl_min_h_over_vsig(gnb_ctx *c, double *out);
 int kick(gnb_ctx *c, float hdt, bool gas_u);
 int drift(gnb_ctx *c, double dt);
 int predict(gnb_ctx *c, float hdt);
+int kick_drift_predict(gnb_ctx *c, float hdt, double dt);
 int diagnostics(gnb_ctx *c, double out[10]);
 int scatter_out(gnb_ctx *c, int field, void *dst_dev);
 int zero_forces(gnb_ctx *c);

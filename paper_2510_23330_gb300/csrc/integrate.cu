@@ -44,6 +44,46 @@ __global__ void k_predict(PArr p, const float *__restrict__ ax, const float *__r
     p.up[i] = p.type[i] == GNB_GAS ? __fmaf_rn(dudt[i], hdt, p.u[i]) : 0.f;
 }
 
+// The first half of a KDK step in one pass: kick (k_kick), drift (k_drift)
+// and the prediction (k_predict), with the same operations in the same
+// order, so every result equals the three kernels' bit for bit; each
+// particle's arrays are read and written once instead of three times.
+__global__ void k_kick_drift_predict(PArr p, const float *__restrict__ ax, const float *__restrict__ ay,
+                                     const float *__restrict__ az, const float *__restrict__ dudt, int n, float hdt,
+                                     double dt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float a0 = ax[i], a1 = ay[i], a2 = az[i];
+    const float vx = __fmaf_rn(a0, hdt, p.vx[i]), vy = __fmaf_rn(a1, hdt, p.vy[i]), vz = __fmaf_rn(a2, hdt, p.vz[i]);
+    p.vx[i] = vx;
+    p.vy[i] = vy;
+    p.vz[i] = vz;
+    p.x[i] = __dadd_rn(p.x[i], __dmul_rn((double)vx, dt));
+    p.y[i] = __dadd_rn(p.y[i], __dmul_rn((double)vy, dt));
+    p.z[i] = __dadd_rn(p.z[i], __dmul_rn((double)vz, dt));
+    p.vpx[i] = __fmaf_rn(a0, hdt, vx);
+    p.vpy[i] = __fmaf_rn(a1, hdt, vy);
+    p.vpz[i] = __fmaf_rn(a2, hdt, vz);
+    if (p.type[i] == GNB_GAS) {
+        const float du = dudt[i];
+        const float u = __fmaf_rn(du, hdt, p.u[i]);
+        p.u[i] = u;
+        p.up[i] = __fmaf_rn(du, hdt, u);
+    } else {
+        p.up[i] = 0.f;
+    }
+}
+
+int kick_drift_predict(gnb_ctx *c, float hdt, double dt)
+{
+    int n = (int)c->n;
+    gnb::counted(k_kick_drift_predict)<<<(n + 255) / 256, 256, 0, c->s>>>(c->P[c->cur], c->ax, c->ay, c->az,
+                                                                           c->dudt, n, hdt, dt);
+    GNB_LAUNCH_CHECK(c, "kick, drift, predict");
+    return GNB_OK;
+}
+
 int kick(gnb_ctx *c, float hdt, bool)
 {
     int n = (int)c->n;

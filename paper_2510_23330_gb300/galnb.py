@@ -79,6 +79,7 @@ def _declare(L):
     L.gnb_destroy.restype = None
     L.gnb_set_particles.argtypes = [_vp, C.c_int64] + [_vp] * 11 + [C.c_int]
     L.gnb_set_state.argtypes = [_vp, C.c_int64] + [_vp] * 16 + [C.c_int, C.c_int]
+    L.gnb_get_fields.argtypes = [_vp, C.c_int, _vp, _vp, _vp, C.c_int]
     L.gnb_build_tree.argtypes = [_vp]
     L.gnb_compute_gravity.argtypes = [_vp, C.c_int]
     L.gnb_compute_sph_density.argtypes = [_vp]
@@ -153,7 +154,8 @@ def _declare(L):
     L.gnb_unet_forward.restype = C.c_int
     L.gnb_unet_train_step.argtypes = [_vp, C.c_int, _vp, _vp, C.c_double, C.POINTER(C.c_double), C.c_int]
     L.gnb_unet_train_step.restype = C.c_int
-    for name in ("gnb_create", "gnb_set_particles", "gnb_set_state", "gnb_build_tree", "gnb_compute_gravity",
+    for name in ("gnb_create", "gnb_set_particles", "gnb_set_state", "gnb_get_fields", "gnb_build_tree",
+                 "gnb_compute_gravity",
                  "gnb_compute_sph_density", "gnb_compute_sph_force", "gnb_compute_forces", "gnb_step_kdk",
                  "gnb_get", "gnb_diagnostics", "gnb_stats"):
         getattr(L, name).restype = C.c_int
@@ -178,6 +180,10 @@ def gnb_set_config(ctx, cfg):
 
 def gnb_set_particles(ctx, n, id, type, x, y, z, vx, vy, vz, m, eps, u, on_device):
     return lib().gnb_set_particles(ctx, n, id, type, x, y, z, vx, vy, vz, m, eps, u, on_device)
+
+
+def gnb_get_fields(ctx, nf, fields, dst, cap, on_device):
+    return lib().gnb_get_fields(ctx, nf, fields, dst, cap, on_device)
 
 
 def gnb_set_state(ctx, n, id, type, x, y, z, vx, vy, vz, m, eps, u, h2, ax, ay, az, dudt, grav_mode, on_device):
@@ -609,6 +615,21 @@ class Context:
         if field == "NODES" and isinstance(out, np.ndarray):
             return out.reshape(-1, 4)
         return out
+
+    def get_fields(self, outs: dict):
+        """Several fields at once into existing arrays ({field name: host
+        array or device tensor}, all on one side), one wait for all."""
+        names = list(outs)
+        ptrs = [_ptr(outs[k]) for k in names]
+        on_dev = {d for _, d in ptrs}
+        if len(on_dev) != 1:
+            raise ValueError("all arrays must be on the same side (host or device)")
+        nf = len(names)
+        fids = (C.c_int * nf)(*[F[k] for k in names])
+        dsts = (C.c_void_p * nf)(*[q for q, _ in ptrs])
+        caps = (C.c_int64 * nf)(*[(outs[k].numel() if hasattr(outs[k], "numel") else outs[k].size) for k in names])
+        self._chk(gnb_get_fields(self.h, nf, fids, dsts, caps, on_dev.pop()))
+        return outs
 
     def replace_region(self, p: dict):
         """Overwrite the particles with IDs p["id"] by p's position, velocity

@@ -217,3 +217,31 @@ def test_set_state_gas(G):
     assert e.value.code == G.GNB_EINVAL
     for x in (a, b):
         x.close()
+
+
+def test_get_fields_equals_get(G):
+    """gnb_get_fields: the same values as one gnb_get per field, host and
+    device destinations; a field that is not current fails before any copy."""
+    torch = pytest.importorskip("torch")
+    p = ics.config_disk(1 << 14, seed=8)
+    c = G.Context(theta=0.5, multipole=1, n_group=64, nfw_ms=ics.NFW_MS, nfw_rs=ics.NFW_RS)
+    c.set_particles(p)
+    c.step_kdk(1e-3, 1)
+    names = ["X", "VZ", "U", "AX", "DUDT", "H2", "ID"]
+    ref = {k: c.get(k) for k in names}
+    host = {k: np.zeros_like(v) for k, v in ref.items()}
+    c.get_fields(host)
+    dev = {k: torch.zeros(v.shape[0], dtype=getattr(torch, str(v.dtype)), device="cuda") for k, v in ref.items()}
+    c.get_fields(dev)
+    for k in names:
+        assert np.array_equal(host[k], ref[k]), k
+        assert np.array_equal(dev[k].cpu().numpy(), ref[k]), k
+    d = G.Context()
+    d.set_particles(p)
+    out = {"X": np.zeros(p["x"].shape[0]), "AX": np.full(p["x"].shape[0], 7.0, np.float32)}
+    with pytest.raises(G.GalnbError) as e:
+        d.get_fields(out)  # no forces yet
+    assert e.value.code == G.GNB_ESTATE
+    assert np.all(out["X"] == 0.0) and np.all(out["AX"] == 7.0)
+    for x in (c, d):
+        x.close()
