@@ -294,7 +294,7 @@ template <int NP, bool MASK, bool UNI>
 __device__ __forceinline__ void pp_loopP(const GravSmem &S, int np, int split, int js, const IPair<NP> &I,
                                          float2 E2, APair<NP> &A)
 {
-#pragma unroll 2
+#pragma unroll 4
     for (int j = split; j < np; j += js) {
         const float4 q = S.jp[j];
         const float e = UNI ? 0.f : S.je[j];
@@ -479,7 +479,7 @@ __device__ __forceinline__ void chain_append_leaf(bool flag, int first, int coun
 }
 
 // Tree walk of one group per warp (see the file comment).
-__global__ void __launch_bounds__(GL_WARPS * 32) k_grav_walk(GravParams p)
+__global__ void __launch_bounds__(GL_WARPS * 32, 5) k_grav_walk(GravParams p)
 {
     __shared__ int stack[GL_WARPS][GL_STACK];
     __shared__ long long d2max[GNB_MAXLEV + 1];  // lanes index it by level: shared, not the parameter bank
