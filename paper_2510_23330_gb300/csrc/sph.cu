@@ -909,9 +909,12 @@ int sph_density(gnb_ctx *c)
     gg.ng = ng; gg.pred = c->use_pred ? 1 : 0; gg.have_h = c->have_h ? 1 : 0;
     gnb::counted(k_gas_gather)<<<gb, 256, 0, c->s>>>(gg);
     GNB_LAUNCH_CHECK(c, "gas gather");
-    // hydro tree and groups of <= 16 gas particles (measured on the 2^24 disk:
-    // 10.8 ms for the kernel-size pass against 11.5 with 32 and 14.3 with 64)
-    GNB_TRY(build_tree(c, c->gt, c->gkey, ng, c->ngas_d, c->cfg.n_leaf, 16, c->gcx, c->gcy, c->gcz, c->grx,
+    // hydro tree and groups of <= 32 gas particles (measured on the 2^24 disk
+    // with the adaptive search margin: 7.05 ms for the kernel-size pass
+    // against 7.12 with 24, 7.17 with 48 and 7.57 with 16; with the fixed
+    // 1.1 margin 16 was best, since a wider radius makes a larger group's
+    // candidates overflow)
+    GNB_TRY(build_tree(c, c->gt, c->gkey, ng, c->ngas_d, c->cfg.n_leaf, 32, c->gcx, c->gcy, c->gcz, c->grx,
                        c->gry, c->grz, c->gm, c->gm, false));
     phase_begin(c, GNB_T_KNN);
     // work_d: [0] next item, [1] items left unfinished, [2] live item count, [3] per-pass snapshot
