@@ -670,7 +670,7 @@ def e2e(args, p, pr, stream, galnb, torch):
     outs = {"X": "x", "Y": "y", "Z": "z", "VX": "vx", "VY": "vy", "VZ": "vz", "U": "u",
             "AX": "ax", "AY": "ay", "AZ": "az", "DUDT": "dudt", "H2": "h2"}
     ctx = galnb.Context(stream=stream.cuda_stream, **pr["cfg"])
-    steps = max(1, min(args.steps, 3))
+    steps = max(1, min(args.steps, 5))
     h2d = sum(t.numel() * t.element_size() for t in host.values())
     d2h = sum(host[k].numel() * host[k].element_size() for k in outs.values())
     ctx.set_particles(host)
