@@ -14,7 +14,8 @@
 //    staging accepted cells (monopole + quadrupole) and the particles of
 //    opened leaves as FP32 offsets from the group's reference grid point
 //    (Sec. 4.3 mixed precision); every thread evaluates its i-particles
-//    (one, two above 16 and four above 64 particles per group chunk)
+//    (one, two above 16, four above 64 and eight above 128 particles per
+//    group chunk; from two on in float2 pairs on the FP32x2 instructions)
 //    against the staged j entries, read as warp-wide broadcasts, and the j
 //    loop is split over as many thread sets as fit ("j-splits") so all
 //    warps stay busy.
@@ -210,9 +211,9 @@ __device__ __forceinline__ void pc_loopN(const GravSmem &S, int buf, int nc, int
 // in pairs, one per lane of a float2, evaluated with the FP32x2 instructions
 // of sm_100 and later (fma.rn.f32x2, add.rn.f32x2, mul.rn.f32x2: two FP32
 // operations per issued instruction, each lane rounded as the scalar one).
-// The same operations as pp_one / pc_one on each lane, so the sums are the
-// scalar ones bit for bit; the positions are held negated (nx = -x_i), which
-// turns x_j - x_i and com - x_i into one addition.  UNI (every particle has
+// Without UNI, the same operations as pp_one / pc_one on each lane, so the
+// sums are the scalar ones bit for bit; the positions are held negated
+// (nx = -x_i), which turns x_j - x_i and com - x_i into one addition.  UNI (every particle has
 // the same softening eps > 0): eps_i^2 + eps_j^2 is the constant E2 =
 // 2 fl(eps^2) for every pair (the same value the general form adds up), and a
 // cell's mass-weighted eps^2 is eps^2, so the pair's softening term is E2
