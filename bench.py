@@ -675,11 +675,15 @@ def e2e(args, p, pr, stream, galnb, torch):
     d2h = sum(host[k].numel() * host[k].element_size() for k in outs.values())
     ctx.set_particles(host)
     ctx.step_kdk(args.dt, 1, pr["gravity"])
-    for f, k in outs.items():
-        ctx.get(f, host[k])
+    back = {f: host[k] for f, k in outs.items()}
+    ctx.get_fields(back)
+    # one untimed round of the measured path (upload with the state's
+    # accelerations, step, export) before the timed ones
+    ctx.set_state(host, pr["gravity"])
+    ctx.step_kdk(args.dt, 1, pr["gravity"])
+    ctx.get_fields(back)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    back = {f: host[k] for f, k in outs.items()}
     for _ in range(steps):
         ctx.set_state(host, pr["gravity"])
         ctx.step_kdk(args.dt, 1, pr["gravity"])

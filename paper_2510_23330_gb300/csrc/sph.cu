@@ -40,6 +40,7 @@ namespace gnb {
 #define KN_STACK 768
 #define KN_BKT 256
 #define KN_U 64
+#define KN_SUB 4  // particles per work item when a group splits (2^24 disk: 6.52 ms for the pass, 8: 6.77, singles: 7.05)
 #define NGB 64
 
 __device__ __forceinline__ float kern_w(float r, float hinv)
@@ -641,24 +642,35 @@ __global__ void __launch_bounds__(KN_THREADS, 9) k_knn(KnnParams p)
         __syncthreads();
         if ((S.over || S.split) && ga.y > 1) {
             // the members need a radius whose candidates do not fit: hand
-            // each particle to its own work item
+            // them to work items of at most KN_SUB consecutive particles
+            // (single particles once the item is that small), each starting
+            // from the margin x its members' largest previous support (at
+            // most the group's radius); an item that still does not fit
+            // splits again
+            const int sub = ga.y > KN_SUB ? KN_SUB : 1;
+            const int nsub = (ga.y + sub - 1) / sub;
             __syncthreads();
             if (tid == 0) {
-                S.g = atomicAdd(p.nitems, ga.y);
-                S.wb = atomicAdd(p.nwl_out, ga.y);
+                S.g = atomicAdd(p.nitems, nsub);
+                S.wb = atomicAdd(p.nwl_out, nsub);
                 p.kflag[gi] = 0;
                 atomicAdd(p.remaining, 1);
             }
             __syncthreads();
             const int base = S.g;
-            for (int k = tid; k < ga.y; k += KN_THREADS) {
+            for (int k = tid; k < nsub; k += KN_THREADS) {
                 const bool fits = base + k < p.item_cap;
                 if (fits) {
-                    p.item[base + k] = make_int2(ga.x + k, 1);
-                    // the particle's own previous support when it has one:
-                    // the group's radius is its largest member's
-                    const float hp = p.rprev[ga.x + k];
-                    p.kR[base + k] = hp > 0.f ? fminf(R, p.margin * hp) : R;
+                    const int f = ga.x + k * sub, cnt = min(sub, ga.y - k * sub);
+                    p.item[base + k] = make_int2(f, cnt);
+                    float hp = 0.f;
+                    bool all = true;
+                    for (int q = 0; q < cnt; q++) {
+                        const float h = p.rprev[f + q];
+                        hp = fmaxf(hp, h);
+                        all = all && h > 0.f;
+                    }
+                    p.kR[base + k] = all ? fminf(R, p.margin * hp) : R;
                     p.kRb[base + k] = make_float2(0.f, 0.f);
                     p.kflag[base + k] = 1;
                 } else {
