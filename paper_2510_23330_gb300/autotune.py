@@ -17,7 +17,7 @@ _FORCE_PHASES = ("SORT", "TREE", "GRAVITY", "EXTERNAL", "HYDRO_TREE", "KNN", "FO
 
 
 def tune_group_size(ctx: "galnb.Context", mode: int = galnb.GNB_GRAV_TREE,
-                    candidates=(32, 64, 128, 256, 384, 512), repeats: int = 2):
+                    candidates=(32, 64, 128, 192, 256, 384, 512), repeats: int = 2):
     """Returns (best n_group, {n_group: ms per gravity evaluation}), tree
     build + gravity, at the context's n_leaf."""
     ctx.set_timing(True)
@@ -39,7 +39,7 @@ def tune_group_size(ctx: "galnb.Context", mode: int = galnb.GNB_GRAV_TREE,
 
 
 def tune_tree(ctx: "galnb.Context", mode: int = galnb.GNB_GRAV_TREE, leaves=(16, 32),
-              groups=(128, 256, 384), repeats: int = 2):
+              groups=(128, 192, 256, 384), repeats: int = 2):
     """Joint choice of (n_leaf, n_group) by the time of a whole force
     evaluation (sort, trees, gravity, kernel size and density, hydro force),
     since the leaf size also shapes the hydro tree.  Returns
